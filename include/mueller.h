@@ -1,0 +1,274 @@
+/*
+ * mueller.h -- C ABI of the GB300 (sm_103a) implementation of the nodal,
+ * high-order Galerkin Mueller boundary-integral solver of
+ *   Y. Luo, "A High-Order Nodal Galerkin Formulation for the Mueller
+ *   Equation: Bypassing Divergence Conformity via Kernel Cancellation",
+ *   arXiv 2604.21181.
+ *
+ * Conventions used by every call
+ * ------------------------------
+ * Units: exterior eps_a = mu_a = 1, so omega = k_a; interior
+ *   eps_i = eps_r, mu_i = mu_r, k_i = k_a sqrt(eps_r mu_r) (principal root).
+ *   Time dependence exp(-i omega t) (Sec. 2.1).
+ * Mesh: curved six-node (P2) triangles, nodes (v0, v1, v2, m01, m12, m20),
+ *   corners counter-clockwise seen from outside (Sec. 3.3).  Inside the
+ *   library everything is stored in Morton order (Sec. 5, double Morton
+ *   permutation); node_perm[new] = old and elem_perm[new] = old map back.
+ * Unknowns: N = 4 * n_nodes.  x = [c_j ; c_jm] (Eq. global_system), each
+ *   half indexed 2 * node + alpha (alpha = 0, 1 = tangent t1, t2), nodes in
+ *   Morton order.
+ * Matrix Z (Eq. global_system): dense, row-major, leading dimension ldz
+ *   (elements), row    h*(N/2) + 2*i + alpha  (h = 0 electric equation,
+ *   1 magnetic equation), column g*(N/2) + 2*j + beta (g = 0: c_j,
+ *   1: c_jm):  Z00 = (i/omega) K1, Z01 = a_eps M + K2^eps,
+ *   Z10 = a_mu M + K2^mu, Z11 = -(i/omega) K1, a_chi = (chi_i + chi_a)/2.
+ * Complex numbers: interleaved (re, im); complex128 = 2 doubles,
+ *   complex64 = 2 floats.
+ * Right-hand sides / solutions: r vectors of length N stored one after the
+ *   other (vector s at offset s*N).
+ * Memory: pointers named *_dev are device pointers owned by the caller
+ *   (e.g. torch tensors); pointers without the suffix are host pointers.
+ *   The library owns only the mesh handle and what it allocates inside it.
+ * Streams: every call takes a cudaStream_t passed as void* (NULL = legacy
+ *   default stream) and only enqueues work on it, except where a call is
+ *   documented as synchronising.
+ * Errors: every call returns a mueller_status; nothing aborts.  The text of
+ *   the last error of the calling thread is returned by mueller_last_error().
+ *   Asynchronous device faults surface at the next synchronising call.
+ */
+#ifndef MUELLER_H_
+#define MUELLER_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MUELLER_OK = 0,
+  MUELLER_ERR_INVALID_ARG = 1,      /* null pointer, bad size or option       */
+  MUELLER_ERR_MESH = 2,             /* non-manifold, unoriented, degenerate   */
+  MUELLER_ERR_DEGENERATE_FRAME = 3, /* Gram-Schmidt norm below threshold      */
+  MUELLER_ERR_SINGULAR_BLOCK = 4,   /* zero pivot in a block-Jacobi block     */
+  MUELLER_ERR_NOT_CONVERGED = 5,    /* GMRES hit maxit (info still filled)    */
+  MUELLER_ERR_TIMEOUT = 6,          /* a bounded device wait gave up          */
+  MUELLER_ERR_CUDA = 7,             /* CUDA runtime error                     */
+  MUELLER_ERR_OOM = 8,              /* device allocation failed               */
+  MUELLER_ERR_STATE = 9             /* call order violated (e.g. no frame)    */
+} mueller_status;
+
+/* Matrix storage types */
+enum {
+  MUELLER_C128 = 0,       /* dense complex128 Z holding the whole operator */
+  MUELLER_C64_NEAR64 = 1  /* dense complex64 Z of the regular (non-touching)
+                             element pairs + FP64 near part (touching pairs
+                             and mass) in the mesh's block-sparse layout   */
+};
+
+/* Solver modes */
+enum {
+  MUELLER_SOLVE_DENSE_LU = 0,   /* dense LU with partial pivoting (C128 only) */
+  MUELLER_SOLVE_GMRES = 1,      /* GMRES(m) in the operator's own precision   */
+  MUELLER_SOLVE_GMRES_IR = 2    /* complex64 inner GMRES + FP64 refinement    */
+};
+
+/* Reference-axis rule of the nodal tangent frame (Sec. 3.2). */
+enum {
+  MUELLER_FRAME_PAPER = 0, /* v_ref = x if |n.z| > 0.9 else z (Eqs. t1, t2)  */
+  MUELLER_FRAME_POLAR = 1  /* v_ref = z except within 1e-8 of the poles      */
+};
+
+typedef struct mueller_mesh mueller_mesh;
+
+typedef struct {
+  double ka;          /* exterior wavenumber k_a = omega                     */
+  double eps_r[2];    /* interior relative permittivity (re, im)            */
+  double mu_r[2];     /* interior relative permeability (re, im)            */
+  int32_t q_regular;  /* triangle rule: 6 (degree 4) or 12 (degree 6)        */
+  int32_t ssq_order;  /* Sauter-Schwab Gauss points per dimension, 1..16    */
+  int32_t frame_rule; /* MUELLER_FRAME_*                                     */
+  int32_t reserved;   /* must be 0                                           */
+} mueller_params;
+
+typedef struct {
+  int64_t n_nodes, n_tri, n_dof;
+  int64_t n_touching;   /* ordered touching element pairs (incl. coincident) */
+  int64_t n_near_blocks;/* node-pair blocks of the near part                 */
+  double min_gs_norm;   /* smallest Gram-Schmidt norm (after tangent_frame)  */
+} mueller_mesh_info;
+
+typedef struct {
+  int32_t mode;        /* MUELLER_SOLVE_*                                    */
+  int32_t restart;     /* GMRES restart length m (>= 1)                      */
+  int32_t maxit;       /* total Arnoldi steps allowed (per RHS)              */
+  int32_t warm_start;  /* nonzero: X_dev holds x0 on entry                   */
+  double tol;          /* ||b - Zx|| <= tol ||b|| (FP64, on the stored operator) */
+  double inner_tol;    /* GMRES_IR: relative tolerance of each inner solve   */
+  int32_t max_refine;  /* GMRES_IR: outer refinement steps allowed           */
+  int32_t use_precond; /* nonzero: right Morton block-Jacobi preconditioner  */
+} mueller_solver_opts;
+
+typedef struct {
+  int32_t iters;       /* Arnoldi steps, summed over RHS                     */
+  int32_t restarts;    /* restart cycles, summed over RHS                    */
+  int32_t refinements; /* GMRES_IR outer steps, summed over RHS              */
+  int32_t converged;   /* number of RHS that reached tol                     */
+  double relres;       /* worst final FP64 relative residual over the RHS    */
+  double t_ms;         /* wall time of the call                              */
+} mueller_solve_info;
+
+/* The operator handed to the preconditioner and the solver. */
+typedef struct {
+  const mueller_mesh* mesh; /* for the near-part layout (C64_NEAR64)         */
+  const void* Z_dev;        /* dense Z, dtype below, row-major, ldz          */
+  int64_t ldz;
+  int32_t dtype;            /* MUELLER_C128 or MUELLER_C64_NEAR64            */
+  int32_t pad;
+  const void* near_dev;     /* complex128 near blocks (C64_NEAR64) or NULL   */
+  const void* precond_dev;  /* factors from mueller_precond_build or NULL    */
+  int64_t block;            /* cluster size B used to build precond_dev      */
+} mueller_operator;
+
+/* Library version; text of the calling thread's last error. */
+int32_t mueller_version(void);
+const char* mueller_last_error(void);
+const char* mueller_status_string(mueller_status s);
+
+/*
+ * mueller_mesh_load -- Sec. 3.3 (P2 isoparametric mesh) and Sec. 5 (double
+ * Morton permutation).  Validates the mesh (every corner edge shared by two
+ * triangles with opposite orientation and the same edge node, finite
+ * coordinates, non-degenerate elements), computes the Morton node and element
+ * orders (21-bit keys in the node bounding box scaled by its largest extent,
+ * x in the least significant bit, ties by original index; elements keyed by
+ * the centroid of their corners), classifies the touching element pairs
+ * (shared corners: 3 coincident, 2 common edge, 1 common vertex) and uploads
+ * everything to the device on 'stream'.
+ *   xyz   host, n_nodes x 3 float64, read only, copied.
+ *   tri6  host, n_tri x 6 int32 node ids, read only, copied.
+ *   flags bit 0: keep the input order (no Morton permutation).
+ *   out   receives the handle (owned by the library; free with
+ *         mueller_mesh_free).
+ * Errors: INVALID_ARG (null/sizes), MESH (validation), OOM, CUDA.
+ */
+mueller_status mueller_mesh_load(const double* xyz, int64_t n_nodes, const int32_t* tri6,
+                                 int64_t n_tri, int32_t flags, void* stream,
+                                 mueller_mesh** out);
+void mueller_mesh_free(mueller_mesh* mesh);
+mueller_status mueller_mesh_get_info(const mueller_mesh* mesh, mueller_mesh_info* info);
+/* host outputs: node_perm[n_nodes], elem_perm[n_tri] (new -> old); either may be NULL */
+mueller_status mueller_mesh_perm(const mueller_mesh* mesh, int32_t* node_perm,
+                                 int32_t* elem_perm);
+
+/*
+ * mueller_tangent_frame -- Sec. 3.1 Eq. (U_contribution) and Sec. 3.2
+ * Eqs. (t1), (t2): metric-weighted nodal normal n_v = sum U / |sum U| with
+ * U = (a1 x a2)/(g11 g22) (corner nodes: the element relabelled so that the
+ * node is the parametric origin; edge nodes: canonical derivatives), then
+ * t1 = v_ref x n/|.|, t2 = n x t1 with the given frame_rule.  Stores the
+ * frame in the handle.
+ *   frame_dev  optional device output, n_nodes x 9 float64 (n, t1, t2).
+ * Errors: INVALID_ARG, CUDA.
+ */
+mueller_status mueller_tangent_frame(mueller_mesh* mesh, int32_t frame_rule, double* frame_dev,
+                                     void* stream);
+
+/*
+ * mueller_assemble -- Sec. 4 (Eqs. kappa1_alphabeta, K1_matrix_entry,
+ * Hdiff_exact, kappa_S, kappa2_alpha_beta, K2_matrix_entry, kappa2_S,
+ * global_system, mass_matrix, rhs_E, rhs_H) and Sec. 5.1 (fused pass).
+ * Regular element pairs: product rule q_regular x q_regular with the exact
+ * kernels evaluated through a stable series at |k R| < 1.  Touching pairs:
+ * the singular parts (Eqs. kappa_S, kappa2_S) by Sauter-Schwab quadrature of
+ * order ssq_order, the remainder kappa - kappa^s by the product rule.
+ *   dtype    MUELLER_C128: Z_dev = complex128 N x ldz, whole operator.
+ *            MUELLER_C64_NEAR64: Z_dev = complex64 N x ldz with the regular
+ *            pairs (computed in FP32), near_dev = complex128 near blocks
+ *            (mueller_near_bytes) with touching pairs and mass (FP64).
+ *   Z_dev, near_dev are overwritten (zeroed first).
+ *   B_dev    optional complex128 r x N right-hand sides (Eqs. rhs_E, rhs_H)
+ *            for the plane waves inc (host, r x 6: k-hat, real p-hat with
+ *            p.k = 0; E_inc = p exp(i k_a k.x), H_inc = k x E_inc).
+ * Requires mueller_tangent_frame first (else STATE).
+ * Errors: INVALID_ARG, STATE, DEGENERATE_FRAME, CUDA.
+ */
+mueller_status mueller_assemble(mueller_mesh* mesh, const mueller_params* params, int32_t dtype,
+                                void* Z_dev, int64_t ldz, void* near_dev, void* B_dev,
+                                const double* inc, int32_t r, void* stream);
+/* bytes of the complex128 near-part buffer of a loaded mesh */
+size_t mueller_near_bytes(const mueller_mesh* mesh);
+
+/*
+ * mueller_precond_build -- Sec. 5, Eq. (precond_block): the Morton block
+ * Jacobi preconditioner.  Per-current indices (2*node + alpha) are split into
+ * ceil((N/2)/block) contiguous clusters I_m (the last one smaller); block m
+ * is the 2|I_m| x 2|I_m| restriction of the operator to I_m in both halves
+ * (all four quadrants).  Each block is factorised by LU with partial
+ * pivoting in FP64 and stored as its explicit inverse (complex128).
+ *   precond_dev  caller-owned, mueller_precond_bytes(N, block) bytes.
+ *   status_dev   optional device int32: set to the first singular block + 1.
+ * The operator's precond_dev/block fields are ignored.
+ * Errors: INVALID_ARG, SINGULAR_BLOCK (checked when the call synchronises:
+ * it reads the pivot status before returning), CUDA.
+ */
+mueller_status mueller_precond_build(const mueller_operator* op, int64_t block,
+                                     void* precond_dev, void* stream);
+size_t mueller_precond_bytes(int64_t n_dof, int64_t block);
+
+/*
+ * mueller_solve -- Sec. 5 (GMRES with right block-Jacobi preconditioning)
+ * and the mixed-precision refinement.  Solves Z X = B for r right-hand
+ * sides.  Synchronising: returns when X is final.
+ *   B_dev, X_dev  complex128 r x N (X_dev holds x0 if opts->warm_start).
+ *   work_dev      caller scratch of mueller_solve_workspace_bytes() bytes, or
+ *                 NULL to let the call allocate (and free) it on the stream.
+ *   info          host, filled on OK and on NOT_CONVERGED.
+ * Errors: INVALID_ARG, NOT_CONVERGED, SINGULAR_BLOCK, TIMEOUT, OOM, CUDA.
+ */
+mueller_status mueller_solve(const mueller_operator* op, const void* B_dev, void* X_dev,
+                             int32_t r, const mueller_solver_opts* opts, mueller_solve_info* info,
+                             void* work_dev, size_t work_bytes, void* stream);
+size_t mueller_solve_workspace_bytes(const mueller_operator* op, int32_t r,
+                                     const mueller_solver_opts* opts);
+
+/*
+ * mueller_matvec -- Y = Z X for r vectors (complex128 in and out), using the
+ * operator's storage (C128: FP64 arithmetic; C64_NEAR64: complex64 far part
+ * on the tensor cores when r >= 8, else CUDA cores, FP32 accumulation, plus
+ * the FP64 near part).  Used by GMRES and exposed for tests and benchmarks.
+ *   work_dev  NULL or scratch of mueller_matvec_workspace_bytes() bytes.
+ */
+mueller_status mueller_matvec(const mueller_operator* op, const void* X_dev, void* Y_dev,
+                              int32_t r, void* work_dev, size_t work_bytes, void* stream);
+size_t mueller_matvec_workspace_bytes(const mueller_operator* op, int32_t r);
+
+/*
+ * mueller_far_field -- scattered far field of the solved currents and the
+ * cross sections (the paper reports C_ext, C_sca, C_abs and their balance;
+ * the formulas follow from the current definitions of Sec. 2.1):
+ *   F(r) = (i k_a/4 pi)[(N~ - r (r.N~)) - r x L~],
+ *   N~ = int j e^{-i k_a r.y}, L~ = int j_m e^{-i k_a r.y};
+ *   C_ext = (4 pi/k_a) Im(p . F(k)), C_sca = int |F|^2 dOmega
+ *   (Gauss-Legendre n_theta in cos(theta) x n_phi trapezoid in phi),
+ *   C_abs = Re int j_m . (conj(j) x n).
+ *   X_dev    complex128 r x N solutions.
+ *   inc      host r x 6 incident waves (for C_ext).
+ *   dirs     host n_dir x 3 unit directions (may be NULL if n_dir == 0).
+ *   F_dev    optional complex128 r x n_dir x 3 output.
+ *   xs       host r x 3 output (C_ext, C_sca, C_abs).  Synchronising.
+ * Errors: INVALID_ARG, STATE, CUDA.
+ */
+mueller_status mueller_far_field(mueller_mesh* mesh, const mueller_params* params,
+                                 const void* X_dev, int32_t r, const double* inc,
+                                 const double* dirs, int64_t n_dir, void* F_dev, double* xs,
+                                 int32_t n_theta, int32_t n_phi, void* stream);
+
+/* Block until all work queued on the stream is done; surfaces device faults. */
+mueller_status mueller_sync(void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MUELLER_H_ */

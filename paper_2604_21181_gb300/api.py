@@ -1,0 +1,363 @@
+"""Thin Python binding of libmueller.so (argument marshalling only).
+
+Every computation of the method runs in the library's CUDA kernels; PyTorch
+provides device memory (tensors) and the current CUDA stream.  The names
+follow the C ABI in ``include/mueller.h``.  There is no CPU fallback: if the
+library or a GPU is missing, the calls raise.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import build as _build
+
+MUELLER_C128 = 0
+MUELLER_C64_NEAR64 = 1
+SOLVE_DENSE_LU = 0
+SOLVE_GMRES = 1
+SOLVE_GMRES_IR = 2
+FRAME_PAPER = 0
+FRAME_POLAR = 1
+
+STATUS = {
+    0: "ok", 1: "invalid argument", 2: "invalid mesh", 3: "degenerate tangent frame",
+    4: "singular preconditioner block", 5: "not converged", 6: "device wait timed out",
+    7: "CUDA error", 8: "out of device memory", 9: "call order violated",
+}
+
+
+class MuellerError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class CParams(C.Structure):
+    _fields_ = [("ka", C.c_double), ("eps_r", C.c_double * 2), ("mu_r", C.c_double * 2),
+                ("q_regular", C.c_int32), ("ssq_order", C.c_int32), ("frame_rule", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class CMeshInfo(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("n_tri", C.c_int64), ("n_dof", C.c_int64),
+                ("n_touching", C.c_int64), ("n_near_blocks", C.c_int64),
+                ("min_gs_norm", C.c_double)]
+
+
+class CSolverOpts(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("restart", C.c_int32), ("maxit", C.c_int32),
+                ("warm_start", C.c_int32), ("tol", C.c_double), ("inner_tol", C.c_double),
+                ("max_refine", C.c_int32), ("use_precond", C.c_int32)]
+
+
+class CSolveInfo(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("restarts", C.c_int32), ("refinements", C.c_int32),
+                ("converged", C.c_int32), ("relres", C.c_double), ("t_ms", C.c_double)]
+
+
+class COperator(C.Structure):
+    _fields_ = [("mesh", C.c_void_p), ("Z_dev", C.c_void_p), ("ldz", C.c_int64),
+                ("dtype", C.c_int32), ("pad", C.c_int32), ("near_dev", C.c_void_p),
+                ("precond_dev", C.c_void_p), ("block", C.c_int64)]
+
+
+EXPORTS = [
+    "mueller_version", "mueller_last_error", "mueller_status_string", "mueller_mesh_load",
+    "mueller_mesh_free", "mueller_mesh_get_info", "mueller_mesh_perm", "mueller_tangent_frame",
+    "mueller_assemble", "mueller_near_bytes", "mueller_precond_build", "mueller_precond_bytes",
+    "mueller_solve", "mueller_solve_workspace_bytes", "mueller_matvec",
+    "mueller_matvec_workspace_bytes", "mueller_far_field", "mueller_sync",
+]
+
+_lib = None
+
+
+def load_library(build_if_missing: bool = True):
+    """Load libmueller.so (building it first if needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libmueller.so not found at {path}; run paper_2604_21181_gb300.build")
+    lib = C.CDLL(path)
+    vp, i32, i64, d, dp, ip = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_int32)
+    sig = {
+        "mueller_version": (i32, []),
+        "mueller_last_error": (C.c_char_p, []),
+        "mueller_status_string": (C.c_char_p, [C.c_int]),
+        "mueller_mesh_load": (C.c_int, [dp, i64, ip, i64, i32, vp, C.POINTER(vp)]),
+        "mueller_mesh_free": (None, [vp]),
+        "mueller_mesh_get_info": (C.c_int, [vp, C.POINTER(CMeshInfo)]),
+        "mueller_mesh_perm": (C.c_int, [vp, ip, ip]),
+        "mueller_tangent_frame": (C.c_int, [vp, i32, vp, vp]),
+        "mueller_assemble": (C.c_int, [vp, C.POINTER(CParams), i32, vp, i64, vp, vp, dp, i32, vp]),
+        "mueller_near_bytes": (C.c_size_t, [vp]),
+        "mueller_precond_build": (C.c_int, [C.POINTER(COperator), i64, vp, vp]),
+        "mueller_precond_bytes": (C.c_size_t, [i64, i64]),
+        "mueller_solve": (C.c_int, [C.POINTER(COperator), vp, vp, i32, C.POINTER(CSolverOpts),
+                                    C.POINTER(CSolveInfo), vp, C.c_size_t, vp]),
+        "mueller_solve_workspace_bytes": (C.c_size_t, [C.POINTER(COperator), i32, C.POINTER(CSolverOpts)]),
+        "mueller_matvec": (C.c_int, [C.POINTER(COperator), vp, vp, i32, vp, C.c_size_t, vp]),
+        "mueller_matvec_workspace_bytes": (C.c_size_t, [C.POINTER(COperator), i32]),
+        "mueller_far_field": (C.c_int, [vp, C.POINTER(CParams), vp, i32, dp, dp, i64, vp, dp,
+                                        i32, i32, vp]),
+        "mueller_sync": (C.c_int, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != 0:
+        msg = _lib.mueller_last_error().decode(errors="replace")
+        raise MuellerError(status, msg)
+
+
+def _torch():
+    import torch
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("a CUDA GPU is required (the library has no CPU path)")
+    return torch
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+@dataclass
+class Params:
+    ka: float
+    eps_r: tuple = (1.0, 0.0)
+    mu_r: tuple = (1.0, 0.0)
+    q_regular: int = 6
+    ssq_order: int = 5
+    frame_rule: int = FRAME_PAPER
+
+    def c(self) -> CParams:
+        p = CParams()
+        p.ka = float(self.ka)
+        p.eps_r[0], p.eps_r[1] = float(self.eps_r[0]), float(self.eps_r[1])
+        p.mu_r[0], p.mu_r[1] = float(self.mu_r[0]), float(self.mu_r[1])
+        p.q_regular = int(self.q_regular)
+        p.ssq_order = int(self.ssq_order)
+        p.frame_rule = int(self.frame_rule)
+        p.reserved = 0
+        return p
+
+    @classmethod
+    def from_workload(cls, w: dict, frame_rule: int = FRAME_PAPER):
+        return cls(ka=w["ka"], eps_r=tuple(w["eps_r"]), mu_r=tuple(w["mu_r"]),
+                   q_regular=w["q_regular"], ssq_order=w["ssq_order"], frame_rule=frame_rule)
+
+
+class Mesh:
+    """mueller_mesh_load + mueller_tangent_frame."""
+
+    def __init__(self, xyz, tri6, morton: bool = True, stream=None):
+        lib = load_library()
+        _torch()
+        self.xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        self.tri6 = np.ascontiguousarray(tri6, dtype=np.int32)
+        h = C.c_void_p()
+        st = lib.mueller_mesh_load(_dp(self.xyz), self.xyz.shape[0],
+                                   self.tri6.ctypes.data_as(C.POINTER(C.c_int32)),
+                                   self.tri6.shape[0], 0 if morton else 1, _stream(stream),
+                                   C.byref(h))
+        _check(st)
+        self.h = h
+        self._lib = lib
+        self.frame_rule = None
+        info = self.info()
+        self.nn, self.nt, self.N = info["n_nodes"], info["n_tri"], info["n_dof"]
+
+    def info(self) -> dict:
+        i = CMeshInfo()
+        _check(self._lib.mueller_mesh_get_info(self.h, C.byref(i)))
+        return {k: getattr(i, k) for k, _ in CMeshInfo._fields_}
+
+    def perm(self):
+        npm = np.zeros(self.xyz.shape[0], np.int32)
+        epm = np.zeros(self.tri6.shape[0], np.int32)
+        _check(self._lib.mueller_mesh_perm(self.h, npm.ctypes.data_as(C.POINTER(C.c_int32)),
+                                           epm.ctypes.data_as(C.POINTER(C.c_int32))))
+        return npm, epm
+
+    def tangent_frame(self, frame_rule: int = FRAME_PAPER, stream=None, out=True):
+        torch = _torch()
+        fr = torch.empty((self.nn, 9), dtype=torch.float64, device="cuda") if out else None
+        _check(self._lib.mueller_tangent_frame(self.h, int(frame_rule), _ptr(fr), _stream(stream)))
+        self.frame_rule = int(frame_rule)
+        return fr
+
+    def near_bytes(self) -> int:
+        return int(self._lib.mueller_near_bytes(self.h))
+
+    def free(self):
+        if getattr(self, "h", None):
+            self._lib.mueller_mesh_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def assemble(mesh: Mesh, params: Params, dtype: int = MUELLER_C128, inc=None, Z=None, near=None,
+             B=None, stream=None):
+    """mueller_assemble.  Returns (Z, near, B) as CUDA tensors."""
+    torch = _torch()
+    N = mesh.N
+    if Z is None:
+        Z = torch.empty((N, N), dtype=torch.complex128 if dtype == MUELLER_C128 else torch.complex64,
+                        device="cuda")
+    if dtype == MUELLER_C64_NEAR64 and near is None:
+        near = torch.empty(mesh.near_bytes() // 16, dtype=torch.complex128, device="cuda")
+    r = 0
+    incp = None
+    if inc is not None:
+        inc = np.ascontiguousarray(inc, dtype=np.float64).reshape(-1, 6)
+        r = inc.shape[0]
+        if B is None:
+            B = torch.empty((r, N), dtype=torch.complex128, device="cuda")
+        incp = _dp(inc)
+    p = params.c()
+    _check(mesh._lib.mueller_assemble(mesh.h, C.byref(p), int(dtype), _ptr(Z), Z.stride(0), _ptr(near),
+                                      _ptr(B), incp, r, _stream(stream)))
+    return Z, near, B
+
+
+class Operator:
+    """The operator struct handed to precond_build / solve / matvec."""
+
+    def __init__(self, mesh: Mesh, Z, near=None, dtype: int = MUELLER_C128, precond=None, block=0):
+        self.mesh, self.Z, self.near, self.dtype = mesh, Z, near, dtype
+        self.precond, self.block = precond, block
+
+    def c(self) -> COperator:
+        o = COperator()
+        o.mesh = self.mesh.h
+        o.Z_dev = self.Z.data_ptr()
+        o.ldz = self.Z.stride(0)
+        o.dtype = int(self.dtype)
+        o.near_dev = self.near.data_ptr() if self.near is not None else None
+        o.precond_dev = self.precond.data_ptr() if self.precond is not None else None
+        o.block = int(self.block)
+        return o
+
+
+def precond_build(op: Operator, block: int, stream=None):
+    torch = _torch()
+    lib = load_library()
+    nbytes = lib.mueller_precond_bytes(op.mesh.N, int(block))
+    P = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    o = op.c()
+    _check(lib.mueller_precond_build(C.byref(o), int(block), _ptr(P), _stream(stream)))
+    op.precond, op.block = P, int(block)
+    return P
+
+
+@dataclass
+class SolverOpts:
+    mode: int = SOLVE_GMRES
+    restart: int = 50
+    maxit: int = 5000
+    warm_start: int = 0
+    tol: float = 1e-8
+    inner_tol: float = 1e-5
+    max_refine: int = 20
+    use_precond: int = 1
+
+    def c(self) -> CSolverOpts:
+        o = CSolverOpts()
+        for k in ("mode", "restart", "maxit", "warm_start", "max_refine", "use_precond"):
+            setattr(o, k, int(getattr(self, k)))
+        o.tol = float(self.tol)
+        o.inner_tol = float(self.inner_tol)
+        return o
+
+
+def solve(op: Operator, B, opts: SolverOpts, X=None, work=None, stream=None, raise_on_nc=True):
+    """mueller_solve.  Returns (X, info dict)."""
+    torch = _torch()
+    lib = load_library()
+    r = B.shape[0] if B.dim() == 2 else 1
+    if X is None:
+        X = torch.zeros_like(B)
+    o = op.c()
+    so = opts.c()
+    info = CSolveInfo()
+    wb = 0
+    if work is not None:
+        wb = work.numel() * work.element_size()
+    st = lib.mueller_solve(C.byref(o), _ptr(B), _ptr(X), int(r), C.byref(so), C.byref(info),
+                           _ptr(work), wb, _stream(stream))
+    d = {k: getattr(info, k) for k, _ in CSolveInfo._fields_}
+    if st == 5 and not raise_on_nc:
+        return X, d
+    _check(st)
+    return X, d
+
+
+def solve_workspace_bytes(op: Operator, r: int, opts: SolverOpts) -> int:
+    o = op.c()
+    so = opts.c()
+    return int(load_library().mueller_solve_workspace_bytes(C.byref(o), int(r), C.byref(so)))
+
+
+def matvec(op: Operator, X, Y=None, stream=None):
+    torch = _torch()
+    lib = load_library()
+    r = X.shape[0] if X.dim() == 2 else 1
+    if Y is None:
+        Y = torch.empty_like(X)
+    o = op.c()
+    _check(lib.mueller_matvec(C.byref(o), _ptr(X), _ptr(Y), int(r), None, 0, _stream(stream)))
+    return Y
+
+
+def far_field(mesh: Mesh, params: Params, X, inc, dirs=None, n_theta: int = 48, n_phi: int = 96,
+              stream=None):
+    """mueller_far_field.  Returns (F tensor r x n_dir x 3 or None, xs numpy r x 3)."""
+    torch = _torch()
+    inc = np.ascontiguousarray(inc, dtype=np.float64).reshape(-1, 6)
+    r = inc.shape[0]
+    if dirs is None:
+        dirs = np.zeros((0, 3))
+    dirs = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 3)
+    nd = dirs.shape[0]
+    F = torch.empty((r, nd, 3), dtype=torch.complex128, device="cuda") if nd else None
+    xs = np.zeros((r, 3))
+    p = params.c()
+    _check(mesh._lib.mueller_far_field(mesh.h, C.byref(p), _ptr(X), r, _dp(inc),
+                                       _dp(dirs) if nd else None, nd, _ptr(F), _dp(xs),
+                                       int(n_theta), int(n_phi), _stream(stream)))
+    return F, xs
+
+
+def sync(stream=None):
+    _check(load_library().mueller_sync(_stream(stream)))

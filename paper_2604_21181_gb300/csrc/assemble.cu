@@ -1,0 +1,646 @@
+// Galerkin assembly of the Mueller system (Sec. 4, Sec. 5.1):
+//   * regular_kernel  : every ordered pair of non-touching elements, product
+//                       rule Q x Q, fused evaluation of the 12 kernel
+//                       components (K1, K2^eps, K2^mu for the four alpha,
+//                       beta) per point pair, FP64 or FP32;
+//   * touching_kernel : coincident / common-edge / common-vertex pairs in
+//                       FP64: singular parts (Eqs. kappa_S, kappa2_S) by
+//                       Sauter-Schwab, remainder kappa - kappa^s by the
+//                       product rule, plus the mass term on coincident pairs;
+//   * rhs_kernel      : Eqs. rhs_E, rhs_H;
+//   * mirror_kernel   : Z11 = -Z00 (both are +-(i/omega) K1).
+// Contributions of element pairs meet in Z (or in the near blocks) through
+// atomic additions.
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "p2.cuh"
+
+namespace mu {
+
+// ------------------------------------------------------------ rule tables
+__constant__ double c_phi64[MAX_Q * 6];   // N_k at the regular-rule points
+__constant__ float c_phi32[MAX_Q * 6];
+__constant__ double c_rxi[MAX_Q], c_reta[MAX_Q], c_rw[MAX_Q];
+__constant__ double c_gl[MAX_NS], c_glw[MAX_NS];  // Gauss-Legendre on [0,1]
+
+static int g_uploaded_q = -1, g_uploaded_ns = -1;
+static int g_uploaded_dev = -1;
+
+mueller_status upload_rules(const TriangleRule& rule, int ns) {
+  int dev = 0;
+  MU_CUDA(cudaGetDevice(&dev));
+  if (rule.q == g_uploaded_q && ns == g_uploaded_ns && dev == g_uploaded_dev) return MUELLER_OK;
+  double phi[MAX_Q * 6];
+  float phif[MAX_Q * 6];
+  for (int p = 0; p < rule.q; ++p) {
+    const double l0 = 1.0 - rule.xi[p] - rule.eta[p], l1 = rule.xi[p], l2 = rule.eta[p];
+    const double N[6] = {l0 * (2 * l0 - 1), l1 * (2 * l1 - 1), l2 * (2 * l2 - 1),
+                         4 * l0 * l1,       4 * l1 * l2,       4 * l2 * l0};
+    for (int k = 0; k < 6; ++k) {
+      phi[p * 6 + k] = N[k];
+      phif[p * 6 + k] = (float)N[k];
+    }
+  }
+  std::vector<double> g, gw;
+  gauss_legendre_unit(ns, g, gw);
+  MU_CUDA(cudaMemcpyToSymbol(c_phi64, phi, sizeof(double) * rule.q * 6));
+  MU_CUDA(cudaMemcpyToSymbol(c_phi32, phif, sizeof(float) * rule.q * 6));
+  MU_CUDA(cudaMemcpyToSymbol(c_rxi, rule.xi.data(), sizeof(double) * rule.q));
+  MU_CUDA(cudaMemcpyToSymbol(c_reta, rule.eta.data(), sizeof(double) * rule.q));
+  MU_CUDA(cudaMemcpyToSymbol(c_rw, rule.w.data(), sizeof(double) * rule.q));
+  MU_CUDA(cudaMemcpyToSymbol(c_gl, g.data(), sizeof(double) * ns));
+  MU_CUDA(cudaMemcpyToSymbol(c_glw, gw.data(), sizeof(double) * ns));
+  g_uploaded_q = rule.q;
+  g_uploaded_ns = ns;
+  g_uploaded_dev = dev;
+  return MUELLER_OK;
+}
+
+namespace {
+
+template <class R>
+__device__ __forceinline__ R phi_at(int p, int k);
+template <>
+__device__ __forceinline__ double phi_at<double>(int p, int k) {
+  return c_phi64[p * 6 + k];
+}
+template <>
+__device__ __forceinline__ float phi_at<float>(int p, int k) {
+  return c_phi32[p * 6 + k];
+}
+
+// complex accumulation into Z
+__device__ __forceinline__ void zadd(double* Z, int64_t idx, double re, double im) {
+  atomicAdd(Z + 2 * idx, re);
+  atomicAdd(Z + 2 * idx + 1, im);
+}
+__device__ __forceinline__ void zadd(float* Z, int64_t idx, float re, float im) {
+  atomicAdd(reinterpret_cast<float2*>(Z) + idx, make_float2(re, im));
+}
+
+template <class R>
+__device__ __forceinline__ bool share_corner(const int32_t* a, const int32_t* b) {
+  bool s = false;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) s |= (a[i] == b[j]);
+  return s;
+}
+
+// 12 kernel components of one point pair, times the weights:
+// out[4*op + 2*alpha + beta], op = 0 K1, 1 K2^eps, 2 K2^mu.
+template <class R>
+__device__ __forceinline__ void point_pair(const KConst<R>& K, const R* __restrict__ px,
+                                           const R* __restrict__ qy, bool remainder,
+                                           cx<R> out[12]) {
+  const R rx = px[0] - qy[0], ry = px[1] - qy[1], rz = px[2] - qy[2];
+  const R r2 = rx * rx + ry * ry + rz * rz;
+  const R W = px[18] * qy[18];
+  // x record: x 0-2, n 3-5, t1 6-8, t2 9-11, s1 12-14, s2 15-17, W 18
+  if (r2 == R(0)) {
+    // coincident rule points of a coincident pair (remainder only):
+    // kappa1 - kappa1^s -> i (ka^3 - ki^3)/(6 pi) s.t,  kappa2 - kappa2^s -> 0
+    const R ka3 = K.ka * K.ka * K.ka;
+    const cx<R> ki2 = cmk(K.ki_re * K.ki_re - K.ki_im * K.ki_im, R(2) * K.ki_re * K.ki_im);
+    const cx<R> ki3 = cmul(ki2, cmk(K.ki_re, K.ki_im));
+    const R inv6pi = R(0.0530516476972984452562945877908381257);
+    const cx<R> lim = cmk(ki3.im * inv6pi, (ka3 - ki3.re) * inv6pi);  // i (ka^3 - ki^3)/(6 pi)
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        const R* s = px + 12 + 3 * a;
+        const R* t = qy + 6 + 3 * b;
+        const R st = (s[0] * t[0] + s[1] * t[1] + s[2] * t[2]) * W;
+        out[2 * a + b] = crs(st, lim);
+        out[4 + 2 * a + b] = cmk<R>(0, 0);
+        out[8 + 2 * a + b] = cmk<R>(0, 0);
+      }
+    return;
+  }
+  const R r = sqrt(r2);
+  const R ir = R(1) / r;
+  const R hx = rx * ir, hy = ry * ir, hz = rz * ir;
+  cx<R> S1, S2, De, Dm;
+  kernel_scalars<R>(K, r, remainder, S1, S2, De, Dm);
+  const R nR = px[3] * hx + px[4] * hy + px[5] * hz;
+  R tR[2], sR[2], Rt[2], nt[2];
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    const R* t = px + 6 + 3 * a;
+    const R* s = px + 12 + 3 * a;
+    const R* u = qy + 6 + 3 * a;  // t_beta(y) with beta = a
+    tR[a] = t[0] * hx + t[1] * hy + t[2] * hz;
+    sR[a] = s[0] * hx + s[1] * hy + s[2] * hz;
+    Rt[a] = hx * u[0] + hy * u[1] + hz * u[2];
+    nt[a] = px[3] * u[0] + px[4] * u[1] + px[5] * u[2];
+  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const R* t = px + 6 + 3 * a;
+      const R* s = px + 12 + 3 * a;
+      const R* u = qy + 6 + 3 * b;
+      const R st = s[0] * u[0] + s[1] * u[1] + s[2] * u[2];
+      const R tt = t[0] * u[0] + t[1] * u[1] + t[2] * u[2];
+      const R G = (tt * nR - tR[a] * nt[b]) * W;
+      const R sRt = sR[a] * Rt[b] * W;
+      const R stw = st * W;
+      out[2 * a + b] = cmk(S1.re * stw + S2.re * sRt, S1.im * stw + S2.im * sRt);
+      out[4 + 2 * a + b] = crs(G, De);
+      out[8 + 2 * a + b] = crs(G, Dm);
+    }
+}
+
+// ------------------------------------------------------- regular pairs
+// CTA: 4 warps, each owns one test element ex; the CTA shares a tile of TY
+// trial elements staged in shared memory.  Per element pair a warp
+//   1. evaluates the Q*Q point pairs (lanes over point pairs) into Kt[p][q][c],
+//   2. contracts q -> j with the shape values (in place, lanes over (p, c)),
+//   3. contracts p -> i and adds the 6 x 6 x 12 block into Z (lanes over (j, c)).
+template <class R, int Q>
+struct RegCfg {
+  static constexpr int TY = (sizeof(R) == 8 && Q == 12) ? 16 : 32;
+  static constexpr int WARPS = 4;
+  static constexpr size_t smem =
+      sizeof(R) * ((size_t)TY * Q * QD_STRIDE + (size_t)WARPS * Q * QD_STRIDE +
+                   (size_t)WARPS * Q * Q * 24);
+};
+
+template <class R, int Q>
+__global__ void __launch_bounds__(128) regular_kernel(int64_t nt, const R* __restrict__ qd,
+                                                      const int32_t* __restrict__ T, KConst<R> K,
+                                                      R* __restrict__ Z, int64_t ldz, int64_t H) {
+  using C = RegCfg<R, Q>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* sY = reinterpret_cast<R*>(smem_raw);               // TY*Q*QD_STRIDE
+  R* sX = sY + (size_t)C::TY * Q * QD_STRIDE;           // WARPS*Q*QD_STRIDE
+  R* sK = sX + (size_t)C::WARPS * Q * QD_STRIDE;        // WARPS*Q*Q*24
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t ex = (int64_t)blockIdx.x * C::WARPS + warp;
+  const int64_t ey0 = (int64_t)blockIdx.y * C::TY;
+  const int ny = (int)((nt - ey0) < (int64_t)C::TY ? (nt - ey0) : (int64_t)C::TY);
+  // stage the trial tile and the test elements
+  for (int i = threadIdx.x; i < ny * Q * QD_STRIDE; i += blockDim.x)
+    sY[i] = qd[ey0 * Q * QD_STRIDE + i];
+  R* myX = sX + (size_t)warp * Q * QD_STRIDE;
+  if (ex < nt)
+    for (int i = lane; i < Q * QD_STRIDE; i += 32) myX[i] = qd[ex * Q * QD_STRIDE + i];
+  __syncthreads();
+  if (ex >= nt) return;
+  int32_t tx[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) tx[k] = T[6 * ex + k];
+  R* Kt = sK + (size_t)warp * Q * Q * 24;  // [p][q][c] complex (re, im)
+  const R wre = R(0), wim = R(1) / K.ka;   // i / omega
+  for (int yy = 0; yy < ny; ++yy) {
+    const int64_t ey = ey0 + yy;
+    int32_t ty[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) ty[k] = T[6 * ey + k];
+    if (share_corner<R>(tx, ty)) continue;  // touching pairs: touching_kernel
+    const R* Y = sY + (size_t)yy * Q * QD_STRIDE;
+    // 1. point pairs
+    for (int pq = lane; pq < Q * Q; pq += 32) {
+      const int p = pq / Q, q = pq % Q;
+      cx<R> kv[12];
+      point_pair<R>(K, myX + p * QD_STRIDE, Y + q * QD_STRIDE, false, kv);
+      R* o = Kt + (size_t)pq * 24;
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        o[2 * c] = kv[c].re;
+        o[2 * c + 1] = kv[c].im;
+      }
+    }
+    __syncwarp();
+    // 2. T[p][j][c] = sum_q Kt[p][q][c] N_j(q), written over Kt[p][j][c]
+    for (int pc = lane; pc < Q * 12; pc += 32) {
+      const int p = pc / 12, c = pc % 12;
+      R vre[Q], vim[Q];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        vre[q] = Kt[((size_t)p * Q + q) * 24 + 2 * c];
+        vim[q] = Kt[((size_t)p * Q + q) * 24 + 2 * c + 1];
+      }
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        R are = 0, aim = 0;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          const R ph = phi_at<R>(q, j);
+          are = fma(ph, vre[q], are);
+          aim = fma(ph, vim[q], aim);
+        }
+        Kt[((size_t)p * Q + j) * 24 + 2 * c] = are;
+        Kt[((size_t)p * Q + j) * 24 + 2 * c + 1] = aim;
+      }
+    }
+    __syncwarp();
+    // 3. L[i][j][c] = sum_p N_i(p) T[p][j][c]; scatter into Z
+    for (int jc = lane; jc < 6 * 12; jc += 32) {
+      const int j = jc / 12, c = jc % 12;
+      R vre[Q], vim[Q];
+#pragma unroll
+      for (int p = 0; p < Q; ++p) {
+        vre[p] = Kt[((size_t)p * Q + j) * 24 + 2 * c];
+        vim[p] = Kt[((size_t)p * Q + j) * 24 + 2 * c + 1];
+      }
+      const int op = c >> 2, a = (c >> 1) & 1, b = c & 1;
+      const int64_t col = 2 * (int64_t)ty[j] + b + (op == 1 ? H : 0);
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        R are = 0, aim = 0;
+#pragma unroll
+        for (int p = 0; p < Q; ++p) {
+          const R ph = phi_at<R>(p, i);
+          are = fma(ph, vre[p], are);
+          aim = fma(ph, vim[p], aim);
+        }
+        const int64_t row = 2 * (int64_t)tx[i] + a + (op == 2 ? H : 0);
+        if (op == 0) {  // (i/omega) K1
+          const R zr = wre * are - wim * aim, zi = wre * aim + wim * are;
+          zadd(Z, row * ldz + col, zr, zi);
+        } else {
+          zadd(Z, row * ldz + col, are, aim);
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------- touching pairs
+constexpr int TT = 96;  // threads per touching pair (= SSQ points per batch)
+
+__device__ __forceinline__ void ss_point(int cls, int ns, int64_t pt, double& xu, double& xv,
+                                         double& yu, double& yv, double& w) {
+  const int nreg = cls == 3 ? 6 : (cls == 2 ? 5 : 2);
+  const int reg = (int)(pt % nreg);
+  int64_t rest = pt / nreg;
+  const int d = (int)(rest % ns);
+  rest /= ns;
+  const int c = (int)(rest % ns);
+  rest /= ns;
+  const int b = (int)(rest % ns);
+  const int a = (int)(rest / ns);
+  const double xi = c_gl[a], e1 = c_gl[b], e2 = c_gl[c], e3 = c_gl[d];
+  const double W = c_glw[a] * c_glw[b] * c_glw[c] * c_glw[d];
+  const double x3 = xi * xi * xi;
+  if (cls == 3) {  // identical triangles: weight xi^3 e1^2 e2
+    w = W * x3 * e1 * e1 * e2;
+    switch (reg) {
+      case 0: xu = xi; xv = xi * (1 - e1 + e1 * e2); yu = xi * (1 - e1 * e2 * e3); yv = xi * (1 - e1); break;
+      case 1: xu = xi * (1 - e1 * e2 * e3); xv = xi * (1 - e1); yu = xi; yv = xi * (1 - e1 + e1 * e2); break;
+      case 2: xu = xi; xv = xi * e1 * (1 - e2 + e2 * e3); yu = xi * (1 - e1 * e2); yv = xi * e1 * (1 - e2); break;
+      case 3: xu = xi * (1 - e1 * e2); xv = xi * e1 * (1 - e2); yu = xi; yv = xi * e1 * (1 - e2 + e2 * e3); break;
+      case 4: xu = xi * (1 - e1 * e2 * e3); xv = xi * e1 * (1 - e2 * e3); yu = xi; yv = xi * e1 * (1 - e2); break;
+      default: xu = xi; xv = xi * e1 * (1 - e2); yu = xi * (1 - e1 * e2 * e3); yv = xi * e1 * (1 - e2 * e3); break;
+    }
+  } else if (cls == 2) {  // common edge v = 0
+    const double j1 = W * x3 * e1 * e1;
+    w = reg == 0 ? j1 : j1 * e2;
+    switch (reg) {
+      case 0: xu = xi; xv = xi * e1 * e3; yu = xi * (1 - e1 * e2); yv = xi * e1 * (1 - e2); break;
+      case 1: xu = xi; xv = xi * e1; yu = xi * (1 - e1 * e2 * e3); yv = xi * e1 * e2 * (1 - e3); break;
+      case 2: xu = xi * (1 - e1 * e2); xv = xi * e1 * (1 - e2); yu = xi; yv = xi * e1 * e2 * e3; break;
+      case 3: xu = xi * (1 - e1 * e2 * e3); xv = xi * e1 * e2 * (1 - e3); yu = xi; yv = xi * e1; break;
+      default: xu = xi * (1 - e1 * e2 * e3); xv = xi * e1 * (1 - e2 * e3); yu = xi; yv = xi * e1 * e2; break;
+    }
+  } else {  // common vertex (0, 0): weight xi^3 e2
+    w = W * x3 * e2;
+    if (reg == 0) {
+      xu = xi; xv = xi * e1; yu = xi * e2; yv = xi * e2 * e3;
+    } else {
+      xu = xi * e2; xv = xi * e2 * e3; yu = xi; yv = xi * e1;
+    }
+  }
+}
+
+// relabelled reference point (u, v) -> canonical (xi, eta); perm holds the
+// canonical corner of each relabelled corner in 2-bit fields
+__device__ __forceinline__ void to_canonical(int perm, double u, double v, double& xi, double& eta) {
+  const double lp[3] = {1.0 - u, u - v, v};
+  double l[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) l[(perm >> (2 * k)) & 3] = lp[k];
+  xi = l[1];
+  eta = l[2];
+}
+
+__global__ void __launch_bounds__(TT) touching_kernel(
+    int64_t n_touch, const TouchPair* __restrict__ tp, const double* __restrict__ X,
+    const int32_t* __restrict__ T, const double* __restrict__ frame,
+    const double* __restrict__ qd, int Q, int ns, KConst<double> K, double ae_re, double ae_im,
+    double am_re, double am_im, int dtype, void* __restrict__ Zv, int64_t ldz, int64_t H,
+    double* __restrict__ near, const int32_t* __restrict__ tp_slot) {
+  __shared__ d3 sXn[2][6], sT1[2][6], sT2[2][6];
+  __shared__ double sG[6 * 48];
+  // staging of the SSQ points (sU, sV), reused afterwards for the remainder
+  // point pairs (sK, Q*Q*24 <= TT*54 doubles)
+  __shared__ double sbuf[TT * 54];
+  static_assert(MAX_Q * MAX_Q * 24 <= TT * 54, "remainder buffer must fit in the staging buffer");
+  double(*sU)[6] = reinterpret_cast<double(*)[6]>(sbuf);
+  double(*sV)[48] = reinterpret_cast<double(*)[48]>(sbuf + TT * 6);
+  double* sK = sbuf;
+  const int64_t pid = blockIdx.x;
+  if (pid >= n_touch) return;
+  const TouchPair P = tp[pid];
+  const int tid = threadIdx.x;
+  if (tid < 12) {
+    const int side = tid / 6, k = tid % 6;
+    const int64_t e = side ? P.ey : P.ex;
+    const int64_t v = T[6 * e + k];
+    sXn[side][k] = mk(X[3 * v], X[3 * v + 1], X[3 * v + 2]);
+    const double* f = frame + 9 * v;
+    sT1[side][k] = mk(f[3], f[4], f[5]);
+    sT2[side][k] = mk(f[6], f[7], f[8]);
+  }
+  __syncthreads();
+  const int px = P.perm & 0x3f, py = (P.perm >> 8) & 0x3f;
+  const int nreg = P.cls == 3 ? 6 : (P.cls == 2 ? 5 : 2);
+  const int64_t npts = (int64_t)nreg * ns * ns * ns * ns;
+  // ---- singular parts by Sauter-Schwab (8 real geometric integrals)
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int64_t base = 0; base < npts; base += TT) {
+    const int64_t pt = base + tid;
+    if (pt < npts) {
+      double xu, xv, yu, yv, w, xi, eta, yxi, yeta;
+      ss_point(P.cls, ns, pt, xu, xv, yu, yv, w);
+      to_canonical(px, xu, xv, xi, eta);
+      to_canonical(py, yu, yv, yxi, yeta);
+      PointGeo gx, gy;
+      point_geo(sXn[0], sT1[0], sT2[0], xi, eta, gx);
+      point_geo(sXn[1], sT1[1], sT2[1], yxi, yeta, gy);
+      const d3 Rv = sub(gx.x, gy.x);
+      const double r = sqrt(dot(Rv, Rv));
+      const double ir = 1.0 / r;
+      const d3 h = scl(ir, Rv);
+      const double W = w * gx.J * gy.J;
+      const double nR = dot(gx.n, h);
+      const d3 sx[2] = {gx.s1, gx.s2}, tx[2] = {gx.t1, gx.t2}, ty[2] = {gy.t1, gy.t2};
+      double g[8];
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          g[2 * a + b] = (dot(sx[a], ty[b]) + dot(sx[a], h) * dot(h, ty[b])) * ir;
+          g[4 + 2 * a + b] = (dot(tx[a], ty[b]) * nR - dot(tx[a], h) * dot(gx.n, ty[b])) * ir * ir;
+        }
+#pragma unroll
+      for (int i = 0; i < 6; ++i) sU[tid][i] = gx.N[i];
+#pragma unroll
+      for (int j = 0; j < 6; ++j)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) sV[tid][j * 8 + c] = W * gy.N[j] * g[c];
+    } else {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) sU[tid][i] = 0.0;
+#pragma unroll
+      for (int c = 0; c < 48; ++c) sV[tid][c] = 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int o = tid + k * TT;  // output (i, jc), 288 of them
+      const int i = o / 48, jc = o % 48;
+      double s = acc[k];
+      for (int p = 0; p < TT; ++p) s = fma(sU[p][i], sV[p][jc], s);
+      acc[k] = s;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) sG[tid + k * TT] = acc[k];
+  // ---- remainder kappa - kappa^s by the product rule (Q x Q point pairs)
+  const double* QX = qd + (int64_t)P.ex * Q * QD_STRIDE;
+  const double* QY = qd + (int64_t)P.ey * Q * QD_STRIDE;
+  for (int pq = tid; pq < Q * Q; pq += TT) {
+    const int p = pq / Q, q = pq % Q;
+    double px_[QD_STRIDE], qy_[QD_STRIDE];
+    for (int c = 0; c < 19; ++c) {
+      px_[c] = QX[p * QD_STRIDE + c];
+      qy_[c] = QY[q * QD_STRIDE + c];
+    }
+    cx<double> kv[12];
+    point_pair<double>(K, px_, qy_, true, kv);
+    for (int c = 0; c < 12; ++c) {
+      sK[(size_t)pq * 24 + 2 * c] = kv[c].re;
+      sK[(size_t)pq * 24 + 2 * c + 1] = kv[c].im;
+    }
+  }
+  __syncthreads();
+  for (int pc = tid; pc < Q * 12; pc += TT) {
+    const int p = pc / 12, c = pc % 12;
+    double vre[MAX_Q], vim[MAX_Q];
+    for (int q = 0; q < Q; ++q) {
+      vre[q] = sK[((size_t)p * Q + q) * 24 + 2 * c];
+      vim[q] = sK[((size_t)p * Q + q) * 24 + 2 * c + 1];
+    }
+    for (int j = 0; j < 6; ++j) {
+      double are = 0, aim = 0;
+      for (int q = 0; q < Q; ++q) {
+        are = fma(c_phi64[q * 6 + j], vre[q], are);
+        aim = fma(c_phi64[q * 6 + j], vim[q], aim);
+      }
+      sK[((size_t)p * Q + j) * 24 + 2 * c] = are;
+      sK[((size_t)p * Q + j) * 24 + 2 * c + 1] = aim;
+    }
+  }
+  __syncthreads();
+  // ---- L = remainder + singular (+ mass on coincident pairs), scatter
+  const double C1re = (K.ka * K.ka - (K.ki_re * K.ki_re - K.ki_im * K.ki_im)) * 0.0397887357729738339422209408431285943;
+  const double C1im = -(2.0 * K.ki_re * K.ki_im) * 0.0397887357729738339422209408431285943;  // /(8 pi)
+  const double Cere = -(1.0 - K.eps_re) * 0.0795774715459476678844418816862571885;
+  const double Ceim = K.eps_im * 0.0795774715459476678844418816862571885;
+  const double Cmre = -(1.0 - K.mu_re) * 0.0795774715459476678844418816862571885;
+  const double Cmim = K.mu_im * 0.0795774715459476678844418816862571885;
+  const double wim = 1.0 / K.ka;  // i / omega
+  for (int jc = tid; jc < 6 * 12; jc += TT) {
+    const int j = jc / 12, c = jc % 12;
+    const int op = c >> 2, a = (c >> 1) & 1, b = c & 1, ab = c & 3;
+    double vre[MAX_Q], vim[MAX_Q];
+    for (int p = 0; p < Q; ++p) {
+      vre[p] = sK[((size_t)p * Q + j) * 24 + 2 * c];
+      vim[p] = sK[((size_t)p * Q + j) * 24 + 2 * c + 1];
+    }
+    for (int i = 0; i < 6; ++i) {
+      double are = 0, aim = 0;
+      for (int p = 0; p < Q; ++p) {
+        are = fma(c_phi64[p * 6 + i], vre[p], are);
+        aim = fma(c_phi64[p * 6 + i], vim[p], aim);
+      }
+      // singular part
+      if (op == 0) {
+        const double g = sG[i * 48 + j * 8 + ab];
+        are += C1re * g;
+        aim += C1im * g;
+      } else {
+        const double g = sG[i * 48 + j * 8 + 4 + ab];
+        are += (op == 1 ? Cere : Cmre) * g;
+        aim += (op == 1 ? Ceim : Cmim) * g;
+      }
+      // mass (Eq. mass_matrix) on coincident pairs: a_chi delta_ab int N_i N_j
+      if (P.cls == 3 && op > 0 && a == b) {
+        double mij = 0.0;
+        for (int p = 0; p < Q; ++p) mij += QX[p * QD_STRIDE + 18] * c_phi64[p * 6 + i] * c_phi64[p * 6 + j];
+        are += (op == 1 ? ae_re : am_re) * mij;
+        aim += (op == 1 ? ae_im : am_im) * mij;
+      }
+      if (op == 0) {  // times i / omega
+        const double t = are;
+        are = -wim * aim;
+        aim = wim * t;
+      }
+      if (dtype == MUELLER_C128) {
+        double* Z = (double*)Zv;
+        const int64_t row = 2 * (int64_t)T[6 * P.ex + i] + a + (op == 2 ? H : 0);
+        const int64_t col = 2 * (int64_t)T[6 * P.ey + j] + b + (op == 1 ? H : 0);
+        zadd(Z, row * ldz + col, are, aim);
+      } else {
+        // near block [h][alpha][g][beta]; K1 goes to (0,0) and, negated, (1,1)
+        const int64_t slot = tp_slot[pid * 36 + i * 6 + j];
+        double* blk = near + slot * 32;
+        if (op == 0) {
+          zadd(blk, ((0 * 2 + a) * 2 + 0) * 2 + b, are, aim);
+          zadd(blk, ((1 * 2 + a) * 2 + 1) * 2 + b, -are, -aim);
+        } else if (op == 1) {
+          zadd(blk, ((0 * 2 + a) * 2 + 1) * 2 + b, are, aim);
+        } else {
+          zadd(blk, ((1 * 2 + a) * 2 + 0) * 2 + b, are, aim);
+        }
+      }
+    }
+  }
+}
+
+// Eqs. (rhs_E), (rhs_H): one thread per (RHS, element, local node).
+__global__ void rhs_kernel(int64_t nt, int Q, const double* __restrict__ qd,
+                           const int32_t* __restrict__ T, const double* __restrict__ inc, int r,
+                           double ka, int64_t N, double* __restrict__ B) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)r * nt * 6) return;
+  const int i = (int)(t % 6);
+  const int64_t e = (t / 6) % nt;
+  const int s = (int)(t / (6 * nt));
+  const double* w = inc + 6 * s;
+  const d3 k = mk(w[0], w[1], w[2]), pp = mk(w[3], w[4], w[5]);
+  const d3 h = cross(k, pp);
+  double bE[2][2] = {{0, 0}, {0, 0}}, bH[2][2] = {{0, 0}, {0, 0}};
+  for (int p = 0; p < Q; ++p) {
+    const double* rec = qd + (e * Q + p) * QD_STRIDE;
+    double sn, cs;
+    sincos(ka * (k.x * rec[0] + k.y * rec[1] + k.z * rec[2]), &sn, &cs);
+    const double wn = rec[18] * c_phi64[p * 6 + i];
+    for (int a = 0; a < 2; ++a) {
+      const d3 s_ = mk(rec[12 + 3 * a], rec[13 + 3 * a], rec[14 + 3 * a]);
+      const double ce = -wn * dot(s_, pp), ch = wn * dot(s_, h);
+      bE[a][0] += ce * cs;
+      bE[a][1] += ce * sn;
+      bH[a][0] += ch * cs;
+      bH[a][1] += ch * sn;
+    }
+  }
+  const int64_t node = T[6 * e + i];
+  double* b = B + 2 * (int64_t)s * N;
+  for (int a = 0; a < 2; ++a) {
+    zadd(b, 2 * node + a, bE[a][0], bE[a][1]);
+    zadd(b, N / 2 + 2 * node + a, bH[a][0], bH[a][1]);
+  }
+}
+
+template <class R>
+__global__ void mirror_kernel(int64_t H, R* __restrict__ Z, int64_t ldz) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= H * H) return;
+  const int64_t r = t / H, c = t % H;
+  const int64_t src = r * ldz + c, dst = (H + r) * ldz + H + c;
+  Z[2 * dst] = -Z[2 * src];
+  Z[2 * dst + 1] = -Z[2 * src + 1];
+}
+
+template <class R>
+KConst<R> kconst(const PhysConsts& P) {
+  KConst<R> K;
+  K.ka = (R)P.ka;
+  K.ki_re = (R)P.ki_re;
+  K.ki_im = (R)P.ki_im;
+  K.eps_re = (R)P.eps_re;
+  K.eps_im = (R)P.eps_im;
+  K.mu_re = (R)P.mu_re;
+  K.mu_im = (R)P.mu_im;
+  K.sing = 0;
+  return K;
+}
+
+template <class R, int Q>
+mueller_status launch_regular_t(mueller_mesh* m, const PhysConsts& P, R* Z, int64_t ldz,
+                                cudaStream_t s) {
+  using C = RegCfg<R, Q>;
+  const R* qd;
+  if constexpr (sizeof(R) == 8)
+    qd = m->qd64;
+  else
+    qd = m->qd32;
+  auto kern = regular_kernel<R, Q>;
+  MU_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
+  dim3 grid((unsigned)((m->nt + C::WARPS - 1) / C::WARPS), (unsigned)((m->nt + C::TY - 1) / C::TY));
+  kern<<<grid, 32 * C::WARPS, C::smem, s>>>(m->nt, qd, m->T, kconst<R>(P), Z, ldz, 2 * m->nn);
+  MU_CHECK_LAUNCH("regular_kernel");
+  return MUELLER_OK;
+}
+
+}  // namespace
+
+mueller_status launch_regular(mueller_mesh* m, const PhysConsts& P, int Q, int dtype, void* Z,
+                              int64_t ldz, cudaStream_t s) {
+  if (dtype == MUELLER_C128) {
+    return Q == 6 ? launch_regular_t<double, 6>(m, P, (double*)Z, ldz, s)
+                  : launch_regular_t<double, 12>(m, P, (double*)Z, ldz, s);
+  }
+  return Q == 6 ? launch_regular_t<float, 6>(m, P, (float*)Z, ldz, s)
+                : launch_regular_t<float, 12>(m, P, (float*)Z, ldz, s);
+}
+
+mueller_status launch_touching(mueller_mesh* m, const PhysConsts& P, int Q, int ns, int dtype,
+                               void* Z, int64_t ldz, void* near, cudaStream_t s) {
+  if (m->n_touch == 0) return MUELLER_OK;
+  const double ae_re = 0.5 * (P.eps_re + 1.0), ae_im = 0.5 * P.eps_im;
+  const double am_re = 0.5 * (P.mu_re + 1.0), am_im = 0.5 * P.mu_im;
+  touching_kernel<<<(unsigned)m->n_touch, TT, 0, s>>>(
+      m->n_touch, m->tp, m->X, m->T, m->frame, m->qd64, Q, ns, kconst<double>(P), ae_re, ae_im,
+      am_re, am_im, dtype, Z, ldz, 2 * m->nn, (double*)near, m->tp_slot);
+  MU_CHECK_LAUNCH("touching_kernel");
+  return MUELLER_OK;
+}
+
+mueller_status launch_mass_rhs(mueller_mesh* m, const PhysConsts& P, int Q, int dtype, void* Z,
+                               int64_t ldz, void* near, void* B, const double* inc_dev, int r,
+                               cudaStream_t s) {
+  (void)dtype;
+  (void)Z;
+  (void)ldz;
+  (void)near;
+  if (!B || r == 0) return MUELLER_OK;
+  const int64_t n = (int64_t)r * m->nt * 6;
+  rhs_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(m->nt, Q, m->qd64, m->T, inc_dev, r,
+                                                         P.ka, 4 * m->nn, (double*)B);
+  MU_CHECK_LAUNCH("rhs_kernel");
+  return MUELLER_OK;
+}
+
+mueller_status launch_mirror_k1(int64_t N, int dtype, void* Z, int64_t ldz, cudaStream_t s) {
+  const int64_t H = N / 2;
+  const unsigned grid = (unsigned)((H * H + 255) / 256);
+  if (dtype == MUELLER_C128)
+    mirror_kernel<double><<<grid, 256, 0, s>>>(H, (double*)Z, ldz);
+  else
+    mirror_kernel<float><<<grid, 256, 0, s>>>(H, (float*)Z, ldz);
+  MU_CHECK_LAUNCH("mirror_kernel");
+  return MUELLER_OK;
+}
+
+}  // namespace mu

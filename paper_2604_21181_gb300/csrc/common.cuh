@@ -1,0 +1,125 @@
+// Internal declarations shared by the translation units of libmueller.so.
+// Not part of the public ABI (include/mueller.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mueller.h"
+
+namespace mu {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+mueller_status cuda_fail(cudaError_t e, const char* what);
+
+#define MU_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return mu::cuda_fail(e_, #call); \
+  } while (0)
+
+#define MU_CHECK_LAUNCH(what)                                \
+  do {                                                       \
+    cudaError_t e_ = cudaGetLastError();                     \
+    if (e_ != cudaSuccess) return mu::cuda_fail(e_, what);   \
+  } while (0)
+
+// --------------------------------------------------- quadrature tables
+// Triangle rule on the reference simplex (weights sum to 1/2) and Gauss-
+// Legendre on [0,1]; derived on the host (see quadrature.cu).
+struct TriangleRule {
+  int q = 0;
+  std::vector<double> xi, eta, w;
+};
+bool triangle_rule(int q, TriangleRule& out);
+void gauss_legendre_unit(int n, std::vector<double>& x, std::vector<double>& w);
+
+// Per-point record of the regular-rule geometry (Sec. 3.3):
+// x(3) n(3) t1(3) t2(3) s1(3) s2(3) W = w*J (1), padded to 20 values.
+constexpr int QD_STRIDE = 20;
+constexpr int MAX_Q = 12;
+constexpr int MAX_NS = 16;
+
+// touching pair record: ex, ey, class, packed relabellings (px | py << 8,
+// each 3 x 2 bits)
+struct TouchPair {
+  int32_t ex, ey, cls, perm;
+};
+
+}  // namespace mu
+
+// ---------------------------------------------------------------- handle
+struct mueller_mesh {
+  int64_t nn = 0, nt = 0;
+  std::vector<int32_t> node_perm, elem_perm;
+  std::vector<double> X_h;   // Morton order
+  std::vector<int32_t> T_h;  // Morton order
+  // device copies
+  double* X = nullptr;        // nn x 3
+  int32_t* T = nullptr;       // nt x 6
+  int32_t* n2e_ptr = nullptr; // nn + 1
+  int32_t* n2e = nullptr;     // (element << 3) | local node index
+  double* frame = nullptr;    // nn x 9
+  bool has_frame = false;
+  int frame_rule = 0;
+  // regular-rule point geometry, cached per rule
+  int qd_q = 0;
+  double* qd64 = nullptr;     // nt x Q x QD_STRIDE
+  float* qd32 = nullptr;
+  double min_gs = 0.0;
+  // touching pairs and the near-part block layout
+  int64_t n_touch = 0;
+  mu::TouchPair* tp = nullptr;
+  int64_t nnzb = 0;
+  int32_t* near_rowptr = nullptr;  // nn + 1
+  int32_t* near_col = nullptr;     // nnzb
+  int32_t* tp_slot = nullptr;      // n_touch x 36 near slots of the pair's node pairs
+  std::vector<int32_t> near_rowptr_h, near_col_h;
+  // small device scratch
+  int32_t* d_flags = nullptr;      // status words
+  double* d_scal = nullptr;        // 64 doubles
+};
+
+namespace mu {
+// ----------------------------------------------------------- launchers
+// geometry.cu
+mueller_status launch_frame(mueller_mesh* m, int frame_rule, cudaStream_t s);
+mueller_status launch_quad_geometry(mueller_mesh* m, const TriangleRule& rule, cudaStream_t s);
+
+// assemble.cu
+struct PhysConsts {
+  double ka;
+  double ki_re, ki_im;
+  double eps_re, eps_im, mu_re, mu_im;  // interior (exterior = 1)
+};
+mueller_status upload_rules(const TriangleRule& rule, int ns);
+mueller_status launch_regular(mueller_mesh* m, const PhysConsts& P, int Q, int dtype, void* Z,
+                              int64_t ldz, cudaStream_t s);
+mueller_status launch_touching(mueller_mesh* m, const PhysConsts& P, int Q, int ns, int dtype,
+                               void* Z, int64_t ldz, void* near, cudaStream_t s);
+mueller_status launch_mass_rhs(mueller_mesh* m, const PhysConsts& P, int Q, int dtype, void* Z,
+                               int64_t ldz, void* near, void* B, const double* inc_dev, int r,
+                               cudaStream_t s);
+mueller_status launch_mirror_k1(int64_t N, int dtype, void* Z, int64_t ldz, cudaStream_t s);
+
+// linalg.cu
+mueller_status op_matvec(const mueller_operator* op, const void* X, void* Y, int r, void* work,
+                         size_t work_bytes, cudaStream_t s);
+size_t op_matvec_work(const mueller_operator* op, int r);
+mueller_status precond_build(const mueller_operator* op, int64_t block, void* P, cudaStream_t s);
+mueller_status solve(const mueller_operator* op, const void* B, void* X, int r,
+                     const mueller_solver_opts* o, mueller_solve_info* info, void* work,
+                     size_t work_bytes, cudaStream_t s);
+size_t solve_work(const mueller_operator* op, int r, const mueller_solver_opts* o);
+
+// farfield.cu
+mueller_status far_field(mueller_mesh* m, const PhysConsts& P, int Q, const void* X, int r,
+                         const double* inc, const double* dirs, int64_t ndir, void* F,
+                         double* xs, int n_theta, int n_phi, cudaStream_t s);
+
+PhysConsts make_phys(const mueller_params* p);
+}  // namespace mu

@@ -1,0 +1,268 @@
+// Far field and cross sections of the solved surface currents.
+//
+// The currents j = sum c_j N t^ and j_m = sum c_jm N t^ (Sec. 4.1 basis)
+// radiate the scattered field; with exp(-i omega t) and eta_a = 1
+//   F(r) = (i k_a / 4 pi) [ (N~ - r (r.N~)) - r x L~ ],
+//   N~ = int j e^{-i k_a r.y} dGamma,  L~ = int j_m e^{-i k_a r.y} dGamma,
+//   C_ext = (4 pi / k_a) Im(p . F(k)),  C_sca = int |F|^2 dOmega,
+//   C_abs = Re int j_m . (conj(j) x n) dGamma
+// (j = n x H and j_m = -n x E, Sec. 2.1, give the Poynting flux).
+#include <math.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace mu {
+namespace {
+
+// weighted currents at the regular-rule points: rec[s][pt] =
+// (W j (3 complex), W j_m (3 complex)); one thread per (s, point)
+__global__ void currents_kernel(int64_t nt, int Q, const double* __restrict__ qd,
+                                const int32_t* __restrict__ T, const double2* __restrict__ X,
+                                int r, int64_t N, const double* __restrict__ phi,
+                                double2* __restrict__ rec, double* __restrict__ cabs_part) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t np = nt * Q;
+  double ca = 0.0;
+  const int s = blockIdx.y;
+  if (t < np && s < r) {
+    const int64_t e = t / Q;
+    const int p = (int)(t % Q);
+    const double* q = qd + t * QD_STRIDE;
+    const double2* x = X + (int64_t)s * N;
+    const int64_t H = N / 2;
+    double jr[3] = {0, 0, 0}, ji[3] = {0, 0, 0}, mr[3] = {0, 0, 0}, mi[3] = {0, 0, 0};
+    for (int k = 0; k < 6; ++k) {
+      const int64_t node = T[6 * e + k];
+      const double Nk = phi[p * 6 + k];
+      for (int b = 0; b < 2; ++b) {
+        const double* tb = q + 6 + 3 * b;
+        const double2 cj = x[2 * node + b], cm = x[H + 2 * node + b];
+        for (int a = 0; a < 3; ++a) {
+          jr[a] += Nk * cj.x * tb[a];
+          ji[a] += Nk * cj.y * tb[a];
+          mr[a] += Nk * cm.x * tb[a];
+          mi[a] += Nk * cm.y * tb[a];
+        }
+      }
+    }
+    const double W = q[18];
+    double2* o = rec + ((int64_t)s * np + t) * 6;
+    for (int a = 0; a < 3; ++a) {
+      o[a] = make_double2(W * jr[a], W * ji[a]);
+      o[3 + a] = make_double2(W * mr[a], W * mi[a]);
+    }
+    // Re j_m . (conj(j) x n)
+    const double n[3] = {q[3], q[4], q[5]};
+    const double cxr[3] = {jr[1] * n[2] - jr[2] * n[1], jr[2] * n[0] - jr[0] * n[2], jr[0] * n[1] - jr[1] * n[0]};
+    const double cxi[3] = {-(ji[1] * n[2] - ji[2] * n[1]), -(ji[2] * n[0] - ji[0] * n[2]),
+                           -(ji[0] * n[1] - ji[1] * n[0])};
+    for (int a = 0; a < 3; ++a) ca += mr[a] * cxr[a] - mi[a] * cxi[a];
+    ca *= W;
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = ca;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) cabs_part[(int64_t)s * gridDim.x + blockIdx.x] = red[0];
+}
+
+// F for every (direction, RHS): one CTA per pair, threads over points
+__global__ void __launch_bounds__(256) far_kernel(int64_t np, const double* __restrict__ qd,
+                                                  const double2* __restrict__ rec,
+                                                  const double* __restrict__ dirs, int64_t nd,
+                                                  double ka, double2* __restrict__ F) {
+  const int64_t d = blockIdx.x;
+  const int s = blockIdx.y;
+  const double rx = dirs[3 * d], ry = dirs[3 * d + 1], rz = dirs[3 * d + 2];
+  double acc[12];
+  for (int c = 0; c < 12; ++c) acc[c] = 0.0;
+  for (int64_t t = threadIdx.x; t < np; t += blockDim.x) {
+    const double* q = qd + t * QD_STRIDE;
+    double sn, cs;
+    sincos(-ka * (rx * q[0] + ry * q[1] + rz * q[2]), &sn, &cs);
+    const double2* o = rec + ((int64_t)s * np + t) * 6;
+    for (int c = 0; c < 6; ++c) {
+      const double2 v = o[c];
+      acc[2 * c] += v.x * cs - v.y * sn;
+      acc[2 * c + 1] += v.x * sn + v.y * cs;
+    }
+  }
+  __shared__ double red[12][256];
+  for (int c = 0; c < 12; ++c) red[c][threadIdx.x] = acc[c];
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int c = 0; c < 12; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double Nr[3], Ni[3], Lr[3], Li[3];
+    for (int a = 0; a < 3; ++a) {
+      Nr[a] = red[2 * a][0];
+      Ni[a] = red[2 * a + 1][0];
+      Lr[a] = red[6 + 2 * a][0];
+      Li[a] = red[7 + 2 * a][0];
+    }
+    const double r[3] = {rx, ry, rz};
+    const double rNr = r[0] * Nr[0] + r[1] * Nr[1] + r[2] * Nr[2];
+    const double rNi = r[0] * Ni[0] + r[1] * Ni[1] + r[2] * Ni[2];
+    const double cLr[3] = {r[1] * Lr[2] - r[2] * Lr[1], r[2] * Lr[0] - r[0] * Lr[2], r[0] * Lr[1] - r[1] * Lr[0]};
+    const double cLi[3] = {r[1] * Li[2] - r[2] * Li[1], r[2] * Li[0] - r[0] * Li[2], r[0] * Li[1] - r[1] * Li[0]};
+    const double pre = ka / (4.0 * 3.14159265358979323846);  // i k / 4 pi -> multiply by i
+    for (int a = 0; a < 3; ++a) {
+      const double vr = Nr[a] - r[a] * rNr - cLr[a];
+      const double vi = Ni[a] - r[a] * rNi - cLi[a];
+      F[((int64_t)s * nd + d) * 3 + a] = make_double2(-pre * vi, pre * vr);
+    }
+  }
+}
+
+// cross sections per RHS from the far fields: C_ext from the forward
+// direction (index 0), C_sca from the sphere rule (indices 1..), C_abs from
+// the block partials
+__global__ void xs_kernel(const double2* __restrict__ F, int64_t nd, int nth, int nph,
+                          const double* __restrict__ wth, const double* __restrict__ inc,
+                          double ka, const double* __restrict__ cabs_part, int nparts,
+                          double* __restrict__ xs) {
+  const int s = blockIdx.x;
+  __shared__ double red[256];
+  double acc = 0.0;
+  const int64_t nsph = (int64_t)nth * nph;
+  for (int64_t k = threadIdx.x; k < nsph; k += blockDim.x) {
+    const int it = (int)(k / nph);
+    const double2* f = F + ((int64_t)s * nd + 1 + k) * 3;
+    const double a = f[0].x * f[0].x + f[0].y * f[0].y + f[1].x * f[1].x + f[1].y * f[1].y +
+                     f[2].x * f[2].x + f[2].y * f[2].y;
+    acc += a * 2.0 * wth[it] * (2.0 * 3.14159265358979323846 / nph);
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double csca = red[0];
+  __syncthreads();
+  double ca = 0.0;
+  for (int k = threadIdx.x; k < nparts; k += blockDim.x) ca += cabs_part[(int64_t)s * nparts + k];
+  red[threadIdx.x] = ca;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double2* f = F + ((int64_t)s * nd) * 3;
+    const double* p = inc + 6 * s + 3;
+    const double im = p[0] * f[0].y + p[1] * f[1].y + p[2] * f[2].y;
+    xs[3 * s] = 4.0 * 3.14159265358979323846 / ka * im;
+    xs[3 * s + 1] = csca;
+    xs[3 * s + 2] = red[0];
+  }
+}
+
+__global__ void copy_user_dirs_kernel(const double2* __restrict__ Fall, int64_t nd_all, int64_t off,
+                                      int64_t ndir, int r, double2* __restrict__ Fout) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)r * ndir * 3) return;
+  const int64_t a = t % 3, d = (t / 3) % ndir, s = t / (3 * ndir);
+  Fout[t] = Fall[((s * nd_all) + off + d) * 3 + a];
+}
+
+}  // namespace
+
+mueller_status far_field(mueller_mesh* m, const PhysConsts& P, int Q, const void* X, int r,
+                         const double* inc, const double* dirs, int64_t ndir, void* F, double* xs,
+                         int n_theta, int n_phi, cudaStream_t s) {
+  TriangleRule rule;
+  if (!triangle_rule(Q, rule)) return MUELLER_ERR_INVALID_ARG;
+  const int64_t np = m->nt * Q, N = 4 * m->nn;
+  // direction list per RHS: forward k, sphere rule (theta-major), user dirs
+  std::vector<double> gth, wth;
+  gauss_legendre_unit(n_theta, gth, wth);
+  const int64_t nsph = (int64_t)n_theta * n_phi;
+  const int64_t nd = 1 + nsph + ndir;
+  std::vector<double> hd((size_t)r * nd * 3);
+  for (int sidx = 0; sidx < r; ++sidx) {
+    double* o = hd.data() + (size_t)sidx * nd * 3;
+    o[0] = inc[6 * sidx];
+    o[1] = inc[6 * sidx + 1];
+    o[2] = inc[6 * sidx + 2];
+    for (int it = 0; it < n_theta; ++it) {
+      const double ct = 2.0 * gth[it] - 1.0, st = sqrt(fmax(0.0, 1.0 - ct * ct));
+      for (int ip = 0; ip < n_phi; ++ip) {
+        const double ph = 2.0 * 3.14159265358979323846 * ip / n_phi;
+        double* dd = o + 3 * (1 + (int64_t)it * n_phi + ip);
+        dd[0] = st * cos(ph);
+        dd[1] = st * sin(ph);
+        dd[2] = ct;
+      }
+    }
+    for (int64_t d = 0; d < ndir; ++d)
+      for (int a = 0; a < 3; ++a) o[3 * (1 + nsph + d) + a] = dirs[3 * d + a];
+  }
+  double phi[MAX_Q * 6];
+  for (int p = 0; p < Q; ++p) {
+    const double l0 = 1.0 - rule.xi[p] - rule.eta[p], l1 = rule.xi[p], l2 = rule.eta[p];
+    const double Nv[6] = {l0 * (2 * l0 - 1), l1 * (2 * l1 - 1), l2 * (2 * l2 - 1),
+                          4 * l0 * l1,       4 * l1 * l2,       4 * l2 * l0};
+    for (int k = 0; k < 6; ++k) phi[p * 6 + k] = Nv[k];
+  }
+  const unsigned nblk_pts = (unsigned)((np + 255) / 256);
+  // scratch
+  size_t off = 0;
+  auto al = [&](size_t b) {
+    size_t o = off;
+    off += (b + 255) & ~size_t(255);
+    return o;
+  };
+  const size_t o_rec = al((size_t)r * np * 6 * 16);
+  const size_t o_dirs = al(hd.size() * 8);
+  const size_t o_F = al((size_t)r * nd * 3 * 16);
+  const size_t o_wth = al(wth.size() * 8);
+  const size_t o_inc = al((size_t)r * 6 * 8);
+  const size_t o_phi = al(sizeof(phi));
+  const size_t o_cab = al((size_t)r * nblk_pts * 8);
+  const size_t o_xs = al((size_t)r * 3 * 8);
+  char* buf = nullptr;
+  MU_CUDA(cudaMallocAsync((void**)&buf, off, s));
+  double2* rec = (double2*)(buf + o_rec);
+  double* ddirs = (double*)(buf + o_dirs);
+  double2* Fall = (double2*)(buf + o_F);
+  double* dwth = (double*)(buf + o_wth);
+  double* dinc = (double*)(buf + o_inc);
+  double* dphi = (double*)(buf + o_phi);
+  double* cab = (double*)(buf + o_cab);
+  double* dxs = (double*)(buf + o_xs);
+  mueller_status st = MUELLER_OK;
+  cudaError_t e = cudaMemcpyAsync(ddirs, hd.data(), hd.size() * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dwth, wth.data(), wth.size() * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dinc, inc, (size_t)r * 6 * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dphi, phi, sizeof(phi), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) st = cuda_fail(e, "far-field setup");
+  if (!st) {
+    currents_kernel<<<dim3(nblk_pts, r), 256, 0, s>>>(m->nt, Q, m->qd64, m->T, (const double2*)X, r,
+                                                       N, dphi, rec, cab);
+    for (int sidx = 0; sidx < r; ++sidx)
+      far_kernel<<<dim3((unsigned)nd, 1), 256, 0, s>>>(np, m->qd64, rec + (size_t)sidx * np * 6,
+                                                       ddirs + (size_t)sidx * nd * 3, nd, P.ka,
+                                                       Fall + (size_t)sidx * nd * 3);
+    xs_kernel<<<r, 256, 0, s>>>(Fall, nd, n_theta, n_phi, dwth, dinc, P.ka, cab, (int)nblk_pts, dxs);
+    if (ndir > 0)
+      copy_user_dirs_kernel<<<(unsigned)(((int64_t)r * ndir * 3 + 255) / 256), 256, 0, s>>>(
+          Fall, nd, 1 + nsph, ndir, r, (double2*)F);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(xs, dxs, (size_t)r * 3 * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_fail(e, "far field");
+  }
+  cudaFreeAsync(buf, s);
+  return st;
+}
+
+}  // namespace mu

@@ -1,0 +1,541 @@
+// C ABI entry points of libmueller.so and the host side of the mesh:
+// validation, the double Morton permutation (Sec. 5), node-element
+// adjacency, touching-pair classification (Sec. 4.2) and the near-part
+// block layout.  All compute of the method runs in the CUDA kernels of the
+// other translation units; this file only prepares integer tables and
+// orchestrates launches.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <complex>
+#include <map>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace mu {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+mueller_status cuda_fail(cudaError_t e, const char* what) {
+  set_error(std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? MUELLER_ERR_OOM : MUELLER_ERR_CUDA;
+}
+
+static mueller_status fail(mueller_status s, const std::string& msg) {
+  set_error(msg);
+  return s;
+}
+
+PhysConsts make_phys(const mueller_params* p) {
+  PhysConsts P;
+  P.ka = p->ka;
+  std::complex<double> er(p->eps_r[0], p->eps_r[1]), mr(p->mu_r[0], p->mu_r[1]);
+  std::complex<double> ki = p->ka * std::sqrt(er * mr);
+  if (ki.imag() < 0) ki = -ki;
+  P.ki_re = ki.real();
+  P.ki_im = ki.imag();
+  P.eps_re = er.real();
+  P.eps_im = er.imag();
+  P.mu_re = mr.real();
+  P.mu_im = mr.imag();
+  return P;
+}
+
+// ------------------------------------------------------------- Morton
+// 21 bits per axis interleaved, x in the least significant bit.
+static uint64_t interleave3(uint64_t v) {
+  v &= 0x1fffffull;
+  v = (v | (v << 32)) & 0x1f00000000ffffull;
+  v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+  v = (v | (v << 8)) & 0x100f00f00f00f00full;
+  v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+  v = (v | (v << 2)) & 0x1249249249249249ull;
+  return v;
+}
+
+static uint64_t zkey(const double p[3], const double lo[3], double ext) {
+  uint64_t c[3];
+  for (int a = 0; a < 3; ++a) {
+    double s = (p[a] - lo[a]) / ext * 2097152.0;
+    s = (s > 0.0) ? s : 0.0;  // also maps NaN-free negatives and -0 to 0
+    s = (s < 2097151.0) ? s : 2097151.0;
+    c[a] = (uint64_t)floor(s);
+  }
+  return interleave3(c[0]) | (interleave3(c[1]) << 1) | (interleave3(c[2]) << 2);
+}
+
+static void z_order(const std::vector<uint64_t>& key, std::vector<int32_t>& perm) {
+  perm.resize(key.size());
+  std::iota(perm.begin(), perm.end(), 0);
+  std::stable_sort(perm.begin(), perm.end(),
+                   [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+}
+
+// --------------------------------------------------------- validation
+static mueller_status validate(const double* xyz, int64_t nn, const int32_t* T, int64_t nt) {
+  for (int64_t i = 0; i < 3 * nn; ++i)
+    if (!std::isfinite(xyz[i])) return fail(MUELLER_ERR_MESH, "non-finite node coordinate");
+  for (int64_t e = 0; e < nt; ++e) {
+    for (int k = 0; k < 6; ++k) {
+      int32_t v = T[6 * e + k];
+      if (v < 0 || v >= nn)
+        return fail(MUELLER_ERR_MESH, "triangle " + std::to_string(e) + " has a node id out of range");
+      for (int l = 0; l < k; ++l)
+        if (T[6 * e + l] == v)
+          return fail(MUELLER_ERR_MESH, "triangle " + std::to_string(e) + " repeats a node");
+    }
+    const double* a = xyz + 3 * T[6 * e];
+    const double* b = xyz + 3 * T[6 * e + 1];
+    const double* c = xyz + 3 * T[6 * e + 2];
+    double u[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+    double v[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+    double cr[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
+    if (!(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2] > 0.0))
+      return fail(MUELLER_ERR_MESH, "triangle " + std::to_string(e) + " is degenerate");
+  }
+  // every corner edge in exactly two triangles, opposite directions, same edge node
+  struct Use {
+    int64_t tri;
+    int32_t from, mid;
+  };
+  std::map<std::pair<int32_t, int32_t>, std::vector<Use>> edges;
+  const int emid[3] = {3, 4, 5};
+  for (int64_t e = 0; e < nt; ++e)
+    for (int k = 0; k < 3; ++k) {
+      int32_t a = T[6 * e + k], b = T[6 * e + (k + 1) % 3];
+      edges[{std::min(a, b), std::max(a, b)}].push_back({e, a, T[6 * e + emid[k]]});
+    }
+  for (auto& kv : edges) {
+    const auto& u = kv.second;
+    if (u.size() != 2)
+      return fail(MUELLER_ERR_MESH, "edge (" + std::to_string(kv.first.first) + "," +
+                                        std::to_string(kv.first.second) + ") is used by " +
+                                        std::to_string(u.size()) + " triangles (not a closed manifold)");
+    if (u[0].from == u[1].from)
+      return fail(MUELLER_ERR_MESH, "triangles " + std::to_string(u[0].tri) + " and " +
+                                        std::to_string(u[1].tri) + " are inconsistently oriented");
+    if (u[0].mid != u[1].mid)
+      return fail(MUELLER_ERR_MESH, "edge node mismatch between triangles " +
+                                        std::to_string(u[0].tri) + " and " + std::to_string(u[1].tri));
+  }
+  return MUELLER_OK;
+}
+
+// touching classification by shared corner vertices, and the relabellings
+// putting the shared edge at (v0', v1') (ordered as it runs in ex) or the
+// shared vertex at v0' in both triangles.  Conventions of Sec. 4.2 maps:
+// reference triangle {0 <= v <= u <= 1}, shared edge v = 0, vertex (0,0).
+static int classify_pair(const int32_t* a, const int32_t* b, int32_t& packed) {
+  int ia[3], ib[3], ns = 0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      if (a[i] == b[j]) {
+        ia[ns] = i;
+        ib[ns] = j;
+        ++ns;
+      }
+  int px[3] = {0, 1, 2}, py[3] = {0, 1, 2};
+  if (ns == 2) {
+    int i0 = ia[0], i1 = ia[1], j0 = ib[0], j1 = ib[1];
+    if ((i0 + 1) % 3 != i1) {
+      std::swap(i0, i1);
+      std::swap(j0, j1);
+    }
+    px[0] = i0;
+    px[1] = i1;
+    px[2] = 3 - i0 - i1;
+    py[0] = j0;
+    py[1] = j1;
+    py[2] = 3 - j0 - j1;
+  } else if (ns == 1) {
+    for (int k = 0; k < 3; ++k) {
+      px[k] = (ia[0] + k) % 3;
+      py[k] = (ib[0] + k) % 3;
+    }
+  }
+  packed = 0;
+  for (int k = 0; k < 3; ++k) packed |= (px[k] << (2 * k)) | (py[k] << (8 + 2 * k));
+  return ns;
+}
+
+template <class Tp>
+static mueller_status upload(Tp** dst, const Tp* src, size_t n, cudaStream_t s) {
+  MU_CUDA(cudaMalloc((void**)dst, std::max<size_t>(1, n) * sizeof(Tp)));
+  if (n) MU_CUDA(cudaMemcpyAsync(*dst, src, n * sizeof(Tp), cudaMemcpyHostToDevice, s));
+  return MUELLER_OK;
+}
+
+}  // namespace mu
+
+using namespace mu;
+
+extern "C" {
+
+int32_t mueller_version(void) { return 1; }
+
+const char* mueller_last_error(void) { return g_last_error.c_str(); }
+
+const char* mueller_status_string(mueller_status s) {
+  switch (s) {
+    case MUELLER_OK: return "ok";
+    case MUELLER_ERR_INVALID_ARG: return "invalid argument";
+    case MUELLER_ERR_MESH: return "invalid mesh";
+    case MUELLER_ERR_DEGENERATE_FRAME: return "degenerate tangent frame";
+    case MUELLER_ERR_SINGULAR_BLOCK: return "singular preconditioner block";
+    case MUELLER_ERR_NOT_CONVERGED: return "not converged";
+    case MUELLER_ERR_TIMEOUT: return "device wait timed out";
+    case MUELLER_ERR_CUDA: return "CUDA error";
+    case MUELLER_ERR_OOM: return "out of device memory";
+    case MUELLER_ERR_STATE: return "call order violated";
+  }
+  return "unknown status";
+}
+
+void mueller_mesh_free(mueller_mesh* m) {
+  if (!m) return;
+  void* ptrs[] = {m->X, m->T, m->n2e_ptr, m->n2e, m->frame, m->qd64, m->qd32, m->tp,
+                  m->near_rowptr, m->near_col, m->tp_slot, m->d_flags, m->d_scal};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete m;
+}
+
+mueller_status mueller_mesh_load(const double* xyz, int64_t nn, const int32_t* tri6, int64_t nt,
+                                 int32_t flags, void* stream, mueller_mesh** out) {
+  if (!out) return fail(MUELLER_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!xyz || !tri6) return fail(MUELLER_ERR_INVALID_ARG, "xyz or tri6 is NULL");
+  if (nn < 6 || nt < 4) return fail(MUELLER_ERR_INVALID_ARG, "mesh too small (closed surface needs >= 4 triangles)");
+  if (nn > (1ll << 28) || nt > (1ll << 27)) return fail(MUELLER_ERR_INVALID_ARG, "mesh too large");
+  mueller_status st = validate(xyz, nn, tri6, nt);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  mueller_mesh* m = new mueller_mesh();
+  m->nn = nn;
+  m->nt = nt;
+  // ---- double Morton permutation (Sec. 5)
+  if (flags & 1) {
+    m->node_perm.resize(nn);
+    m->elem_perm.resize(nt);
+    std::iota(m->node_perm.begin(), m->node_perm.end(), 0);
+    std::iota(m->elem_perm.begin(), m->elem_perm.end(), 0);
+  } else {
+    double lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) lo[a] = hi[a] = xyz[a];
+    for (int64_t i = 0; i < nn; ++i)
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = std::min(lo[a], xyz[3 * i + a]);
+        hi[a] = std::max(hi[a], xyz[3 * i + a]);
+      }
+    double ext = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+    if (!(ext > 0.0)) ext = 1.0;
+    std::vector<uint64_t> key(nn);
+    for (int64_t i = 0; i < nn; ++i) key[i] = zkey(xyz + 3 * i, lo, ext);
+    z_order(key, m->node_perm);
+    std::vector<uint64_t> ek(nt);
+    for (int64_t e = 0; e < nt; ++e) {
+      double c[3];
+      for (int a = 0; a < 3; ++a)
+        c[a] = (xyz[3 * tri6[6 * e] + a] + xyz[3 * tri6[6 * e + 1] + a] + xyz[3 * tri6[6 * e + 2] + a]) / 3.0;
+      ek[e] = zkey(c, lo, ext);
+    }
+    z_order(ek, m->elem_perm);
+  }
+  std::vector<int32_t> inv(nn);
+  for (int64_t i = 0; i < nn; ++i) inv[m->node_perm[i]] = (int32_t)i;
+  m->X_h.resize(3 * nn);
+  for (int64_t i = 0; i < nn; ++i)
+    for (int a = 0; a < 3; ++a) m->X_h[3 * i + a] = xyz[3 * m->node_perm[i] + a];
+  m->T_h.resize(6 * nt);
+  for (int64_t e = 0; e < nt; ++e)
+    for (int k = 0; k < 6; ++k) m->T_h[6 * e + k] = inv[tri6[6 * m->elem_perm[e] + k]];
+  const int32_t* T = m->T_h.data();
+  // ---- node -> (element, local index), ascending element order
+  std::vector<int32_t> ptr(nn + 1, 0), n2e(6 * nt);
+  for (int64_t e = 0; e < nt; ++e)
+    for (int k = 0; k < 6; ++k) ptr[T[6 * e + k] + 1]++;
+  for (int64_t i = 0; i < nn; ++i) ptr[i + 1] += ptr[i];
+  {
+    std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+    for (int64_t e = 0; e < nt; ++e)
+      for (int k = 0; k < 6; ++k) n2e[fill[T[6 * e + k]]++] = (int32_t)((e << 3) | k);
+  }
+  // ---- touching pairs (sorted by ex, then ey)
+  std::vector<TouchPair> tp;
+  {
+    std::vector<int32_t> cand;
+    for (int64_t ex = 0; ex < nt; ++ex) {
+      cand.clear();
+      for (int k = 0; k < 3; ++k) {
+        int32_t v = T[6 * ex + k];
+        for (int32_t q = ptr[v]; q < ptr[v + 1]; ++q) cand.push_back(n2e[q] >> 3);
+      }
+      std::sort(cand.begin(), cand.end());
+      cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+      for (int32_t ey : cand) {
+        int32_t packed;
+        int cls = classify_pair(T + 6 * ex, T + 6 * ey, packed);
+        if (cls > 0) tp.push_back({(int32_t)ex, ey, cls, packed});
+      }
+    }
+  }
+  m->n_touch = (int64_t)tp.size();
+  // ---- near-part block layout: node pairs of the touching element pairs
+  std::vector<std::vector<int32_t>> rows(nn);
+  for (const TouchPair& p : tp)
+    for (int i = 0; i < 6; ++i)
+      for (int j = 0; j < 6; ++j) rows[T[6 * p.ex + i]].push_back(T[6 * p.ey + j]);
+  m->near_rowptr_h.assign(nn + 1, 0);
+  for (int64_t i = 0; i < nn; ++i) {
+    auto& r = rows[i];
+    std::sort(r.begin(), r.end());
+    r.erase(std::unique(r.begin(), r.end()), r.end());
+    m->near_rowptr_h[i + 1] = m->near_rowptr_h[i] + (int32_t)r.size();
+  }
+  m->nnzb = m->near_rowptr_h[nn];
+  m->near_col_h.resize(m->nnzb);
+  for (int64_t i = 0; i < nn; ++i)
+    std::copy(rows[i].begin(), rows[i].end(), m->near_col_h.begin() + m->near_rowptr_h[i]);
+  std::vector<int32_t> slot((size_t)m->n_touch * 36);
+  for (int64_t p = 0; p < m->n_touch; ++p)
+    for (int i = 0; i < 6; ++i) {
+      int32_t ni = T[6 * tp[p].ex + i];
+      const int32_t* b = m->near_col_h.data() + m->near_rowptr_h[ni];
+      const int32_t* e = m->near_col_h.data() + m->near_rowptr_h[ni + 1];
+      for (int j = 0; j < 6; ++j) {
+        int32_t nj = T[6 * tp[p].ey + j];
+        slot[(size_t)p * 36 + i * 6 + j] = (int32_t)(std::lower_bound(b, e, nj) - m->near_col_h.data());
+      }
+    }
+  // ---- upload
+  st = upload(&m->X, m->X_h.data(), m->X_h.size(), s);
+  if (!st) st = upload(&m->T, m->T_h.data(), m->T_h.size(), s);
+  if (!st) st = upload(&m->n2e_ptr, ptr.data(), ptr.size(), s);
+  if (!st) st = upload(&m->n2e, n2e.data(), n2e.size(), s);
+  if (!st) st = upload(&m->tp, tp.data(), tp.size(), s);
+  if (!st) st = upload(&m->near_rowptr, m->near_rowptr_h.data(), m->near_rowptr_h.size(), s);
+  if (!st) st = upload(&m->near_col, m->near_col_h.data(), m->near_col_h.size(), s);
+  if (!st) st = upload(&m->tp_slot, slot.data(), slot.size(), s);
+  if (!st) {
+    cudaError_t e = cudaMalloc((void**)&m->d_flags, 64 * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&m->d_scal, 64 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->d_flags, 0, 64 * sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host vectors above are temporaries
+    if (e != cudaSuccess) st = cuda_fail(e, "mesh upload");
+  }
+  if (st) {
+    mueller_mesh_free(m);
+    return st;
+  }
+  *out = m;
+  return MUELLER_OK;
+}
+
+mueller_status mueller_mesh_get_info(const mueller_mesh* m, mueller_mesh_info* info) {
+  if (!m || !info) return fail(MUELLER_ERR_INVALID_ARG, "NULL argument");
+  info->n_nodes = m->nn;
+  info->n_tri = m->nt;
+  info->n_dof = 4 * m->nn;
+  info->n_touching = m->n_touch;
+  info->n_near_blocks = m->nnzb;
+  info->min_gs_norm = m->min_gs;
+  return MUELLER_OK;
+}
+
+mueller_status mueller_mesh_perm(const mueller_mesh* m, int32_t* node_perm, int32_t* elem_perm) {
+  if (!m) return fail(MUELLER_ERR_INVALID_ARG, "mesh is NULL");
+  if (node_perm) std::copy(m->node_perm.begin(), m->node_perm.end(), node_perm);
+  if (elem_perm) std::copy(m->elem_perm.begin(), m->elem_perm.end(), elem_perm);
+  return MUELLER_OK;
+}
+
+mueller_status mueller_tangent_frame(mueller_mesh* m, int32_t frame_rule, double* frame_dev,
+                                     void* stream) {
+  if (!m) return fail(MUELLER_ERR_INVALID_ARG, "mesh is NULL");
+  if (frame_rule != MUELLER_FRAME_PAPER && frame_rule != MUELLER_FRAME_POLAR)
+    return fail(MUELLER_ERR_INVALID_ARG, "unknown frame_rule");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!m->frame) MU_CUDA(cudaMalloc((void**)&m->frame, 9 * m->nn * sizeof(double)));
+  mueller_status st = launch_frame(m, frame_rule, s);
+  if (st) return st;
+  m->has_frame = true;
+  m->frame_rule = frame_rule;
+  m->qd_q = 0;  // point geometry depends on the frame
+  if (frame_dev)
+    MU_CUDA(cudaMemcpyAsync(frame_dev, m->frame, 9 * m->nn * sizeof(double),
+                            cudaMemcpyDeviceToDevice, s));
+  return MUELLER_OK;
+}
+
+size_t mueller_near_bytes(const mueller_mesh* m) {
+  return m ? (size_t)m->nnzb * 16 * 2 * sizeof(double) : 0;
+}
+
+static mueller_status check_params(const mueller_params* p) {
+  if (!p) return fail(MUELLER_ERR_INVALID_ARG, "params is NULL");
+  if (!(p->ka > 0.0) || !std::isfinite(p->ka)) return fail(MUELLER_ERR_INVALID_ARG, "ka must be positive");
+  if (p->q_regular != 6 && p->q_regular != 12) return fail(MUELLER_ERR_INVALID_ARG, "q_regular must be 6 or 12");
+  if (p->ssq_order < 1 || p->ssq_order > MAX_NS) return fail(MUELLER_ERR_INVALID_ARG, "ssq_order must be in 1..16");
+  for (double v : {p->eps_r[0], p->eps_r[1], p->mu_r[0], p->mu_r[1]})
+    if (!std::isfinite(v)) return fail(MUELLER_ERR_INVALID_ARG, "non-finite material");
+  if (p->eps_r[0] == 0.0 && p->eps_r[1] == 0.0) return fail(MUELLER_ERR_INVALID_ARG, "eps_r = 0");
+  if (p->mu_r[0] == 0.0 && p->mu_r[1] == 0.0) return fail(MUELLER_ERR_INVALID_ARG, "mu_r = 0");
+  return MUELLER_OK;
+}
+
+// point geometry for rule q (cached in the handle); reads back the smallest
+// Gram-Schmidt norm (synchronises the stream once per rule change)
+static mueller_status ensure_geometry(mueller_mesh* m, int q, cudaStream_t s) {
+  if (!m->has_frame) return fail(MUELLER_ERR_STATE, "mueller_tangent_frame must be called first");
+  if (m->qd_q == q) return MUELLER_OK;
+  TriangleRule rule;
+  if (!triangle_rule(q, rule)) return fail(MUELLER_ERR_INVALID_ARG, "triangle rule derivation failed");
+  if (m->qd64) cudaFree(m->qd64);
+  if (m->qd32) cudaFree(m->qd32);
+  m->qd64 = nullptr;
+  m->qd32 = nullptr;
+  size_t n = (size_t)m->nt * q * QD_STRIDE;
+  MU_CUDA(cudaMalloc((void**)&m->qd64, n * sizeof(double)));
+  MU_CUDA(cudaMalloc((void**)&m->qd32, n * sizeof(float)));
+  mueller_status st = launch_quad_geometry(m, rule, s);
+  if (st) return st;
+  double gs = 0.0;
+  MU_CUDA(cudaMemcpyAsync(&gs, m->d_scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+  MU_CUDA(cudaStreamSynchronize(s));
+  m->min_gs = gs;
+  m->qd_q = q;
+  if (!(gs > 1e-6))
+    return fail(MUELLER_ERR_DEGENERATE_FRAME,
+                "interpolated tangent frame degenerates (Gram-Schmidt norm " + std::to_string(gs) + ")");
+  return MUELLER_OK;
+}
+
+mueller_status mueller_assemble(mueller_mesh* m, const mueller_params* p, int32_t dtype,
+                                void* Z, int64_t ldz, void* near, void* B, const double* inc,
+                                int32_t r, void* stream) {
+  if (!m) return fail(MUELLER_ERR_INVALID_ARG, "mesh is NULL");
+  mueller_status st = check_params(p);
+  if (st) return st;
+  const int64_t N = 4 * m->nn;
+  if (dtype != MUELLER_C128 && dtype != MUELLER_C64_NEAR64)
+    return fail(MUELLER_ERR_INVALID_ARG, "unknown dtype");
+  if (!Z || ldz < N) return fail(MUELLER_ERR_INVALID_ARG, "Z is NULL or ldz < N");
+  if (dtype == MUELLER_C64_NEAR64 && !near) return fail(MUELLER_ERR_INVALID_ARG, "near buffer required");
+  if (B && (r < 1 || !inc)) return fail(MUELLER_ERR_INVALID_ARG, "B given without r >= 1 and inc");
+  if (p->frame_rule != m->frame_rule || !m->has_frame)
+    return fail(MUELLER_ERR_STATE, "call mueller_tangent_frame with params->frame_rule first");
+  cudaStream_t s = (cudaStream_t)stream;
+  st = ensure_geometry(m, p->q_regular, s);
+  if (st) return st;
+  TriangleRule rule;
+  triangle_rule(p->q_regular, rule);
+  st = upload_rules(rule, p->ssq_order);
+  if (st) return st;
+  PhysConsts P = make_phys(p);
+  size_t esz = dtype == MUELLER_C128 ? 16 : 8;
+  MU_CUDA(cudaMemsetAsync(Z, 0, (size_t)N * ldz * esz, s));
+  if (dtype == MUELLER_C64_NEAR64) MU_CUDA(cudaMemsetAsync(near, 0, mueller_near_bytes(m), s));
+  double* inc_dev = nullptr;
+  if (B) {
+    MU_CUDA(cudaMemsetAsync(B, 0, (size_t)r * N * 16, s));
+    MU_CUDA(cudaMallocAsync((void**)&inc_dev, (size_t)r * 6 * sizeof(double), s));
+    MU_CUDA(cudaMemcpyAsync(inc_dev, inc, (size_t)r * 6 * sizeof(double), cudaMemcpyHostToDevice, s));
+  }
+  st = launch_regular(m, P, p->q_regular, dtype, Z, ldz, s);
+  if (!st) st = launch_touching(m, P, p->q_regular, p->ssq_order, dtype, Z, ldz, near, s);
+  if (!st) st = launch_mass_rhs(m, P, p->q_regular, dtype, Z, ldz, near, B, inc_dev, B ? r : 0, s);
+  if (!st) st = launch_mirror_k1(N, dtype, Z, ldz, s);
+  if (inc_dev) cudaFreeAsync(inc_dev, s);
+  return st;
+}
+
+size_t mueller_precond_bytes(int64_t n_dof, int64_t block) {
+  if (n_dof <= 0 || block <= 0) return 0;
+  int64_t H = n_dof / 2, nb = (H + block - 1) / block;
+  int64_t d = 2 * block;
+  return (size_t)nb * d * d * 16 + (size_t)nb * d * sizeof(int32_t) + 256;
+}
+
+mueller_status mueller_precond_build(const mueller_operator* op, int64_t block, void* P,
+                                     void* stream) {
+  if (!op || !op->mesh || !op->Z_dev || !P) return fail(MUELLER_ERR_INVALID_ARG, "NULL argument");
+  if (block < 1) return fail(MUELLER_ERR_INVALID_ARG, "block must be >= 1");
+  if (op->dtype == MUELLER_C64_NEAR64 && !op->near_dev)
+    return fail(MUELLER_ERR_INVALID_ARG, "operator lacks its near part");
+  return precond_build(op, block, P, (cudaStream_t)stream);
+}
+
+size_t mueller_solve_workspace_bytes(const mueller_operator* op, int32_t r,
+                                     const mueller_solver_opts* o) {
+  if (!op || !o || r < 1) return 0;
+  return solve_work(op, r, o);
+}
+
+mueller_status mueller_solve(const mueller_operator* op, const void* B, void* X, int32_t r,
+                             const mueller_solver_opts* o, mueller_solve_info* info, void* work,
+                             size_t work_bytes, void* stream) {
+  if (!op || !op->mesh || !op->Z_dev || !B || !X || !o || !info)
+    return fail(MUELLER_ERR_INVALID_ARG, "NULL argument");
+  if (r < 1) return fail(MUELLER_ERR_INVALID_ARG, "r must be >= 1");
+  if (o->mode < 0 || o->mode > 2) return fail(MUELLER_ERR_INVALID_ARG, "unknown solve mode");
+  if (o->mode != MUELLER_SOLVE_DENSE_LU && (o->restart < 1 || o->maxit < 1 || !(o->tol > 0)))
+    return fail(MUELLER_ERR_INVALID_ARG, "restart, maxit and tol must be positive");
+  if (o->mode == MUELLER_SOLVE_DENSE_LU && op->dtype != MUELLER_C128)
+    return fail(MUELLER_ERR_INVALID_ARG, "dense LU needs a complex128 operator");
+  if (o->mode == MUELLER_SOLVE_GMRES_IR && op->dtype != MUELLER_C64_NEAR64)
+    return fail(MUELLER_ERR_INVALID_ARG, "GMRES_IR needs a C64_NEAR64 operator");
+  if (o->use_precond && !op->precond_dev)
+    return fail(MUELLER_ERR_INVALID_ARG, "use_precond set but operator has no precond_dev");
+  size_t need = solve_work(op, r, o);
+  if (work && work_bytes < need) return fail(MUELLER_ERR_INVALID_ARG, "workspace too small");
+  auto t0 = std::chrono::steady_clock::now();
+  mueller_status st = solve(op, B, X, r, o, info, work, work_bytes, (cudaStream_t)stream);
+  info->t_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return st;
+}
+
+size_t mueller_matvec_workspace_bytes(const mueller_operator* op, int32_t r) {
+  if (!op || r < 1) return 0;
+  return op_matvec_work(op, r);
+}
+
+mueller_status mueller_matvec(const mueller_operator* op, const void* X, void* Y, int32_t r,
+                              void* work, size_t work_bytes, void* stream) {
+  if (!op || !op->mesh || !op->Z_dev || !X || !Y) return fail(MUELLER_ERR_INVALID_ARG, "NULL argument");
+  if (r < 1) return fail(MUELLER_ERR_INVALID_ARG, "r must be >= 1");
+  if (op->dtype == MUELLER_C64_NEAR64 && !op->near_dev)
+    return fail(MUELLER_ERR_INVALID_ARG, "operator lacks its near part");
+  if (work && work_bytes < op_matvec_work(op, r)) return fail(MUELLER_ERR_INVALID_ARG, "workspace too small");
+  return op_matvec(op, X, Y, r, work, work_bytes, (cudaStream_t)stream);
+}
+
+mueller_status mueller_far_field(mueller_mesh* m, const mueller_params* p, const void* X,
+                                 int32_t r, const double* inc, const double* dirs, int64_t ndir,
+                                 void* F, double* xs, int32_t n_theta, int32_t n_phi,
+                                 void* stream) {
+  if (!m || !X || !inc || !xs) return fail(MUELLER_ERR_INVALID_ARG, "NULL argument");
+  mueller_status st = check_params(p);
+  if (st) return st;
+  if (r < 1 || ndir < 0 || (ndir > 0 && (!dirs || !F))) return fail(MUELLER_ERR_INVALID_ARG, "bad r/n_dir");
+  if (n_theta < 2 || n_phi < 3 || n_theta > 512 || n_phi > 1024)
+    return fail(MUELLER_ERR_INVALID_ARG, "n_theta in 2..512, n_phi in 3..1024");
+  cudaStream_t s = (cudaStream_t)stream;
+  st = ensure_geometry(m, p->q_regular, s);
+  if (st) return st;
+  return far_field(m, make_phys(p), p->q_regular, X, r, inc, dirs, ndir, F, xs, n_theta, n_phi, s);
+}
+
+mueller_status mueller_sync(void* stream) {
+  MU_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  return MUELLER_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,1241 @@
+// Dense complex linear algebra of the solver (Sec. 5):
+//   * matrix-vector products with Z (complex128 FP64, complex64 FP32, and
+//     complex64 storage with FP64 arithmetic for the refinement residual),
+//     plus the near blocks of the mixed operator;
+//   * batched blocked LU with partial pivoting (FP64) of the Morton
+//     block-Jacobi blocks (Eq. precond_block) and their explicit inverses;
+//   * restarted GMRES with right preconditioning (classical Gram-Schmidt
+//     applied twice, complex Givens rotations) and the mixed-precision
+//     iterative refinement around it.
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace mu {
+namespace {
+
+__host__ __device__ __forceinline__ int64_t mn64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+// ===================================================================== GEMV
+// y = Z x, Z row-major complex128 (N x ldz).  One warp per 4 rows, lanes
+// stride over columns; FP64 FMA bound on GB300.
+__global__ void __launch_bounds__(256) gemv_c128_kernel(int64_t N, const double2* __restrict__ Z,
+                                                        int64_t ldz, const double2* __restrict__ x,
+                                                        double2* __restrict__ y, int64_t xs,
+                                                        int64_t ys, int r) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t row0 = ((int64_t)blockIdx.x * 8 + warp) * 4;
+  const int s = blockIdx.y;
+  if (row0 >= N || s >= r) return;
+  const double2* xv = x + s * xs;
+  double ar[4] = {0, 0, 0, 0}, ai[4] = {0, 0, 0, 0};
+  const int nr = (int)mn64(4, N - row0);
+  for (int64_t c = lane; c < N; c += 32) {
+    const double2 xc = __ldg(xv + c);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (k < nr) {
+        const double2 z = __ldg(Z + (row0 + k) * ldz + c);
+        ar[k] = fma(z.x, xc.x, fma(-z.y, xc.y, ar[k]));
+        ai[k] = fma(z.x, xc.y, fma(z.y, xc.x, ai[k]));
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ar[k] += __shfl_xor_sync(0xffffffffu, ar[k], o);
+      ai[k] += __shfl_xor_sync(0xffffffffu, ai[k], o);
+    }
+  }
+  if (lane < nr) {
+    double vr = ar[0], vi = ai[0];
+#pragma unroll
+    for (int k = 1; k < 4; ++k)
+      if (lane == k) {
+        vr = ar[k];
+        vi = ai[k];
+      }
+    y[s * ys + row0 + lane] = make_double2(vr, vi);
+  }
+}
+
+// y = Z x with Z complex64; ACC = float (inner solves) or double (the FP64
+// refinement residual, x and y complex128).  Each warp owns 2 rows and reads
+// two complex64 entries per lane per step (16-byte loads).
+template <class ACC>
+__global__ void __launch_bounds__(256) gemv_c64_kernel(int64_t N, const float4* __restrict__ Z4,
+                                                       int64_t ldz, const void* __restrict__ xv_,
+                                                       void* __restrict__ yv_, int64_t xs,
+                                                       int64_t ys, int r) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t row0 = ((int64_t)blockIdx.x * 8 + warp) * 2;
+  const int s = blockIdx.y;
+  if (row0 >= N || s >= r) return;
+  const int nr = (int)mn64(2, N - row0);
+  ACC ar[2] = {0, 0}, ai[2] = {0, 0};
+  const int64_t npair = N / 2;  // full float4 pairs (N even)
+  const int64_t ld4 = ldz / 2;
+  for (int64_t c2 = lane; c2 < npair; c2 += 32) {
+    ACC x0r, x0i, x1r, x1i;
+    if constexpr (sizeof(ACC) == 4) {
+      const float4 xx = __ldg(reinterpret_cast<const float4*>(xv_) + s * (xs / 2) + c2);
+      x0r = xx.x; x0i = xx.y; x1r = xx.z; x1i = xx.w;
+    } else {
+      const double2* xd = reinterpret_cast<const double2*>(xv_) + s * xs + 2 * c2;
+      const double2 a = __ldg(xd), b = __ldg(xd + 1);
+      x0r = a.x; x0i = a.y; x1r = b.x; x1i = b.y;
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      if (k < nr) {
+        const float4 z = __ldg(Z4 + (row0 + k) * ld4 + c2);
+        ar[k] = fma((ACC)z.x, x0r, fma(-(ACC)z.y, x0i, ar[k]));
+        ai[k] = fma((ACC)z.x, x0i, fma((ACC)z.y, x0r, ai[k]));
+        ar[k] = fma((ACC)z.z, x1r, fma(-(ACC)z.w, x1i, ar[k]));
+        ai[k] = fma((ACC)z.z, x1i, fma((ACC)z.w, x1r, ai[k]));
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ar[k] += __shfl_xor_sync(0xffffffffu, ar[k], o);
+      ai[k] += __shfl_xor_sync(0xffffffffu, ai[k], o);
+    }
+  }
+  if (lane < nr) {
+    const ACC vr = lane == 0 ? ar[0] : ar[1];
+    const ACC vi = lane == 0 ? ai[0] : ai[1];
+    if constexpr (sizeof(ACC) == 4)
+      reinterpret_cast<float2*>(yv_)[s * ys + row0 + lane] = make_float2(vr, vi);
+    else
+      reinterpret_cast<double2*>(yv_)[s * ys + row0 + lane] = make_double2(vr, vi);
+  }
+}
+
+// y += near * x for the near blocks (test node rows, 4 x 4 complex blocks
+// [h][alpha][g][beta]); NB = complex128 or complex64 blocks, V = vector type
+template <class BT, class VT>
+__global__ void near_spmv_kernel(int64_t nn, const int32_t* __restrict__ rowptr,
+                                 const int32_t* __restrict__ col, const BT* __restrict__ blk,
+                                 const VT* __restrict__ x, VT* __restrict__ y, int64_t xs,
+                                 int64_t ys, int r) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int s = blockIdx.y;
+  if (t >= nn * 4 || s >= r) return;
+  const int64_t i = t >> 2;
+  const int ha = (int)(t & 3), h = ha >> 1, a = ha & 1;
+  const int64_t H = 2 * nn;
+  using R = decltype(x[0].x);
+  R accr = 0, acci = 0;
+  const VT* xv = x + s * xs;
+  for (int32_t q = rowptr[i]; q < rowptr[i + 1]; ++q) {
+    const int64_t j = col[q];
+    const BT* b = blk + (int64_t)q * 16 + ha * 4;
+#pragma unroll
+    for (int gb = 0; gb < 4; ++gb) {
+      const int g = gb >> 1, be = gb & 1;
+      const VT xv_ = xv[g * H + 2 * j + be];
+      const R br = (R)b[gb].x, bi = (R)b[gb].y;
+      accr = fma(br, xv_.x, fma(-bi, xv_.y, accr));
+      acci = fma(br, xv_.y, fma(bi, xv_.x, acci));
+    }
+  }
+  VT* yo = y + s * ys + h * H + 2 * i + a;
+  yo->x += accr;
+  yo->y += acci;
+}
+
+// ============================================================ batched LU
+// Blocks are d x d complex128 row-major, block b at offset b*d*d, its
+// active size sz[b] <= d.  Right-looking blocked LU, panel width NBK.
+constexpr int NBK = 32;
+
+__device__ __forceinline__ double cabs1(double2 a) { return fabs(a.x) + fabs(a.y); }
+__device__ __forceinline__ double2 cmul2(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cdiv2(double2 a, double2 b) {
+  const double den = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den);
+}
+
+// factor panel columns [k0, k0+NBK) of every block; row swaps are applied
+// to whole rows.  READING: pivot = first row maximising |Re| + |Im|.
+__global__ void __launch_bounds__(256) lu_panel_kernel(double2* __restrict__ A, int64_t d,
+                                                       const int32_t* __restrict__ sz, int k0,
+                                                       int32_t* __restrict__ piv,
+                                                       int32_t* __restrict__ status) {
+  const int b = blockIdx.x;
+  const int n = sz[b];
+  if (k0 >= n) return;
+  double2* M = A + (int64_t)b * d * d;
+  __shared__ double sv[256];
+  __shared__ int si[256];
+  __shared__ double2 spiv;
+  const int kend = min(k0 + NBK, n);
+  for (int k = k0; k < kend; ++k) {
+    // pivot search in column k, rows k..n-1
+    double best = -1.0;
+    int bi = k;
+    for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+      const double v = cabs1(M[(int64_t)i * d + k]);
+      if (v > best) {
+        best = v;
+        bi = i;
+      }
+    }
+    sv[threadIdx.x] = best;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+      if (threadIdx.x < o) {
+        const double v2 = sv[threadIdx.x + o];
+        const int i2 = si[threadIdx.x + o];
+        if (v2 > sv[threadIdx.x] || (v2 == sv[threadIdx.x] && i2 < si[threadIdx.x])) {
+          sv[threadIdx.x] = v2;
+          si[threadIdx.x] = i2;
+        }
+      }
+      __syncthreads();
+    }
+    const int p = si[0];
+    const bool singular = !(sv[0] > 0.0);
+    if (threadIdx.x == 0) {
+      piv[(int64_t)b * d + k] = p;
+      if (singular) atomicCAS(status, 0, b + 1);
+    }
+    if (p != k)
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const double2 t = M[(int64_t)k * d + j];
+        M[(int64_t)k * d + j] = M[(int64_t)p * d + j];
+        M[(int64_t)p * d + j] = t;
+      }
+    __syncthreads();
+    if (threadIdx.x == 0) spiv = singular ? make_double2(1.0, 0.0) : M[(int64_t)k * d + k];
+    __syncthreads();
+    const double2 pv = spiv;
+    // multipliers and rank-1 update of the panel columns
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) {
+      const double2 l = cdiv2(M[(int64_t)i * d + k], pv);
+      M[(int64_t)i * d + k] = l;
+      for (int j = k + 1; j < kend; ++j) {
+        const double2 u = M[(int64_t)k * d + j];
+        double2 a = M[(int64_t)i * d + j];
+        a.x -= l.x * u.x - l.y * u.y;
+        a.y -= l.x * u.y + l.y * u.x;
+        M[(int64_t)i * d + j] = a;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// B[k0:k0+w, c0:c1] <- L_kk^{-1} B[...] (unit lower, L from A) or
+// U_kk^{-1} B[...] (upper, non-unit); one thread per column.
+__global__ void trsm_tile_kernel(const double2* __restrict__ A, double2* __restrict__ B, int64_t d,
+                                 int64_t ldb, int64_t bstride, const int32_t* __restrict__ sz,
+                                 int k0, int w_max, int64_t c0, int64_t c1_cap, int upper) {
+  const int b = blockIdx.y;
+  const int n = sz[b];
+  if (k0 >= n) return;
+  const int w = min(w_max, n - k0);
+  const int64_t c1 = c1_cap < 0 ? n : mn64(c1_cap, n);
+  const int64_t c = c0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= c1) return;
+  const double2* M = A + (int64_t)b * d * d;
+  double2* X = B + (int64_t)b * bstride;
+  double2 v[NBK];
+  for (int i = 0; i < w; ++i) v[i] = X[(int64_t)(k0 + i) * ldb + c];
+  if (!upper) {
+    for (int i = 0; i < w; ++i)
+      for (int j = 0; j < i; ++j) {
+        const double2 l = M[(int64_t)(k0 + i) * d + k0 + j];
+        v[i].x -= l.x * v[j].x - l.y * v[j].y;
+        v[i].y -= l.x * v[j].y + l.y * v[j].x;
+      }
+  } else {
+    for (int i = w - 1; i >= 0; --i) {
+      for (int j = i + 1; j < w; ++j) {
+        const double2 u = M[(int64_t)(k0 + i) * d + k0 + j];
+        v[i].x -= u.x * v[j].x - u.y * v[j].y;
+        v[i].y -= u.x * v[j].y + u.y * v[j].x;
+      }
+      v[i] = cdiv2(v[i], M[(int64_t)(k0 + i) * d + k0 + i]);
+    }
+  }
+  for (int i = 0; i < w; ++i) X[(int64_t)(k0 + i) * ldb + c] = v[i];
+}
+
+// C[r0:r1, c0:c1] -= A[r0:r1, k0:k0+w] * Bm[k0:k0+w, c0:c1] per block:
+// 64 x 64 output tiles, 256 threads with 4 x 4 complex accumulators each.
+// Row range is [r0, r1) with r1 = n (the block's size) if r1_cap < 0.
+__global__ void __launch_bounds__(256) gemm_update_kernel(const double2* __restrict__ A,
+                                                          const double2* __restrict__ Bm,
+                                                          double2* __restrict__ Cm, int64_t d,
+                                                          int64_t ldb, int64_t bstride,
+                                                          const int32_t* __restrict__ sz, int k0,
+                                                          int64_t r0, int64_t r1_cap, int64_t c0,
+                                                          int64_t c1_cap) {
+  const int b = blockIdx.z;
+  const int n = sz[b];
+  if (k0 >= n) return;
+  const int w = min(NBK, n - k0);
+  const int64_t r1 = r1_cap < 0 ? n : mn64(r1_cap, n);
+  const int64_t c1 = c1_cap < 0 ? n : mn64(c1_cap, n);
+  const int64_t tr = r0 + (int64_t)blockIdx.y * 64, tc = c0 + (int64_t)blockIdx.x * 64;
+  if (tr >= r1 || tc >= c1) return;
+  const double2* M = A + (int64_t)b * d * d;
+  const double2* Bb = Bm + (int64_t)b * bstride;
+  double2* Cb = Cm + (int64_t)b * bstride;
+  __shared__ double2 sA[64][NBK + 1];
+  __shared__ double2 sB[NBK][64 + 1];
+  for (int t = threadIdx.x; t < 64 * NBK; t += 256) {
+    const int i = t / NBK, k = t % NBK;
+    const int64_t gr = tr + i;
+    sA[i][k] = (gr < r1 && k < w) ? M[gr * d + k0 + k] : make_double2(0, 0);
+  }
+  for (int t = threadIdx.x; t < NBK * 64; t += 256) {
+    const int k = t / 64, j = t % 64;
+    const int64_t gc = tc + j;
+    sB[k][j] = (gc < c1 && k < w) ? Bb[(int64_t)(k0 + k) * ldb + gc] : make_double2(0, 0);
+  }
+  __syncthreads();
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  double2 acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_double2(0, 0);
+  for (int k = 0; k < NBK; ++k) {
+    double2 a[4], bb[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = sA[ty + 16 * i][k];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) bb[j] = sB[k][tx + 16 * j];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        acc[i][j].x = fma(a[i].x, bb[j].x, fma(-a[i].y, bb[j].y, acc[i][j].x));
+        acc[i][j].y = fma(a[i].x, bb[j].y, fma(a[i].y, bb[j].x, acc[i][j].y));
+      }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t gr = tr + ty + 16 * i, gc = tc + tx + 16 * j;
+      if (gr < r1 && gc < c1) {
+        double2 v = Cb[gr * ldb + gc];
+        v.x -= acc[i][j].x;
+        v.y -= acc[i][j].y;
+        Cb[gr * ldb + gc] = v;
+      }
+    }
+}
+
+// X <- P I: row k of the identity permuted by the recorded swaps
+__global__ void perm_identity_kernel(double2* __restrict__ X, int64_t d,
+                                     const int32_t* __restrict__ sz,
+                                     const int32_t* __restrict__ piv) {
+  const int b = blockIdx.y;
+  const int n = sz[b];
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  double2* M = X + (int64_t)b * d * d;
+  // column c of P: start from e_c and apply the swaps in order
+  int64_t pos = c;
+  for (int k = 0; k < n; ++k) {
+    const int p = piv[(int64_t)b * d + k];
+    if (pos == k)
+      pos = p;
+    else if (pos == p)
+      pos = k;
+  }
+  for (int64_t i = 0; i < n; ++i) M[i * d + c] = make_double2(i == pos ? 1.0 : 0.0, 0.0);
+}
+
+// gather the MBJ blocks of the operator: block b rows/cols I_b in both halves
+template <int DT>
+__global__ void gather_blocks_kernel(const void* __restrict__ Zv, int64_t ldz, int64_t H,
+                                     int64_t B, int64_t d, const int32_t* __restrict__ sz,
+                                     double2* __restrict__ out) {
+  const int b = blockIdx.z;
+  const int s = sz[b] / 2;
+  const int64_t i = blockIdx.y, j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= 2 * s || j >= 2 * s) return;
+  const int64_t o = (int64_t)b * B;
+  const int64_t gi = i < s ? o + i : H + o + (i - s);
+  const int64_t gj = j < s ? o + j : H + o + (j - s);
+  double2 v;
+  if (DT == MUELLER_C128) {
+    v = reinterpret_cast<const double2*>(Zv)[gi * ldz + gj];
+  } else {
+    const float2 f = reinterpret_cast<const float2*>(Zv)[gi * ldz + gj];
+    v = make_double2(f.x, f.y);
+  }
+  out[(int64_t)b * d * d + i * d + j] = v;
+}
+
+// add the near blocks that fall inside MBJ block b (C64_NEAR64 operator)
+__global__ void gather_near_kernel(int64_t nn, const int32_t* __restrict__ rowptr,
+                                   const int32_t* __restrict__ col,
+                                   const double2* __restrict__ nearb, int64_t B, int64_t d,
+                                   const int32_t* __restrict__ sz, double2* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;  // test node
+  if (i >= nn) return;
+  for (int32_t q = rowptr[i]; q < rowptr[i + 1]; ++q) {
+    const int64_t j = col[q];
+    for (int ha = 0; ha < 4; ++ha)
+      for (int gb = 0; gb < 4; ++gb) {
+        const int h = ha >> 1, a = ha & 1, g = gb >> 1, be = gb & 1;
+        const int64_t ri = 2 * i + a, cj = 2 * j + be;  // per-current indices
+        const int64_t bi = ri / B, bj = cj / B;
+        if (bi != bj) continue;
+        const int s = sz[bi] / 2;
+        const int64_t li = (ri - bi * B) + (h ? s : 0), lj = (cj - bj * B) + (g ? s : 0);
+        const double2 v = nearb[(int64_t)q * 16 + ha * 4 + gb];
+        double2* t = out + bi * d * d + li * d + lj;
+        t->x += v.x;
+        t->y += v.y;
+      }
+  }
+}
+
+// ============================================================ MBJ apply
+// z = P^{-1} v: block b multiplies its explicit inverse with the gathered
+// piece of v; one warp per row, lanes over columns.  Blocks of d x d.
+template <class BT, class VT>
+__global__ void __launch_bounds__(256) mbj_apply_kernel(const BT* __restrict__ inv, int64_t d,
+                                                        const int32_t* __restrict__ sz, int64_t B,
+                                                        int64_t H, const VT* __restrict__ v,
+                                                        VT* __restrict__ z) {
+  const int b = blockIdx.y;
+  const int n = sz[b], s = n / 2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * 8 + warp;
+  if (i >= n) return;
+  using R = decltype(v[0].x);
+  const int64_t o = (int64_t)b * B;
+  const BT* row = inv + (int64_t)b * d * d + i * d;
+  R ar = 0, ai = 0;
+  for (int j = lane; j < n; j += 32) {
+    const int64_t gj = j < s ? o + j : H + o + (j - s);
+    const VT x = v[gj];
+    const BT m = row[j];
+    ar = fma((R)m.x, x.x, fma(-(R)m.y, x.y, ar));
+    ai = fma((R)m.x, x.y, fma((R)m.y, x.x, ai));
+  }
+#pragma unroll
+  for (int o2 = 16; o2 > 0; o2 >>= 1) {
+    ar += __shfl_xor_sync(0xffffffffu, ar, o2);
+    ai += __shfl_xor_sync(0xffffffffu, ai, o2);
+  }
+  if (lane == 0) {
+    const int64_t gi = i < s ? o + i : H + o + (i - s);
+    z[gi].x = ar;
+    z[gi].y = ai;
+  }
+}
+
+__global__ void c128_to_c64_kernel(const double2* __restrict__ a, float2* __restrict__ b, int64_t n) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < n) b[t] = make_float2((float)a[t].x, (float)a[t].y);
+}
+
+// ============================================================ GMRES pieces
+// partial sums of conj(V_l) . w over G chunks: part[l*G + g]
+template <class VT>
+__global__ void __launch_bounds__(256) dots_kernel(const VT* __restrict__ V, int64_t N, int nl,
+                                                   const VT* __restrict__ w,
+                                                   double2* __restrict__ part, int G) {
+  const int l = blockIdx.y, g = blockIdx.x;
+  if (l >= nl) return;
+  const VT* v = V + (int64_t)l * N;
+  double sr = 0, si = 0;
+  for (int64_t i = (int64_t)g * blockDim.x + threadIdx.x; i < N; i += (int64_t)G * blockDim.x) {
+    const VT a = v[i], b = w[i];
+    sr += (double)a.x * b.x + (double)a.y * b.y;
+    si += (double)a.x * b.y - (double)a.y * b.x;
+  }
+  __shared__ double rr[256], ri[256];
+  rr[threadIdx.x] = sr;
+  ri[threadIdx.x] = si;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      rr[threadIdx.x] += rr[threadIdx.x + o];
+      ri[threadIdx.x] += ri[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[(int64_t)l * G + g] = make_double2(rr[0], ri[0]);
+}
+
+// h[l] = sum_g part[l*G+g]; hacc[l] += h[l]; w -= sum_l h[l] V_l
+template <class VT>
+__global__ void __launch_bounds__(256) orth_update_kernel(const VT* __restrict__ V, int64_t N,
+                                                          int nl, const double2* __restrict__ part,
+                                                          int G, VT* __restrict__ w,
+                                                          double2* __restrict__ hacc) {
+  __shared__ double2 h[128];
+  for (int l = threadIdx.x; l < nl; l += blockDim.x) {
+    double2 s = make_double2(0, 0);
+    for (int g = 0; g < G; ++g) {
+      s.x += part[(int64_t)l * G + g].x;
+      s.y += part[(int64_t)l * G + g].y;
+    }
+    h[l] = s;
+    if (blockIdx.x == 0) {
+      hacc[l].x += s.x;
+      hacc[l].y += s.y;
+    }
+  }
+  __syncthreads();
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  using R = decltype(w[0].x);
+  double ar = w[i].x, ai = w[i].y;
+  for (int l = 0; l < nl; ++l) {
+    const VT v = V[(int64_t)l * N + i];
+    ar -= h[l].x * v.x - h[l].y * v.y;
+    ai -= h[l].x * v.y + h[l].y * v.x;
+  }
+  w[i].x = (R)ar;
+  w[i].y = (R)ai;
+}
+
+// sum of squares partials
+template <class VT>
+__global__ void __launch_bounds__(256) nrm2_kernel(const VT* __restrict__ w, int64_t N,
+                                                   double* __restrict__ part, int G) {
+  double s = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)G * blockDim.x)
+    s += (double)w[i].x * w[i].x + (double)w[i].y * w[i].y;
+  __shared__ double r[256];
+  r[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) r[threadIdx.x] += r[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = r[0];
+}
+
+// v_out = w / ||w|| (norm from the partials); stores ||w|| to *nrm
+template <class VT>
+__global__ void normalize_kernel(const VT* __restrict__ w, int64_t N, const double* __restrict__ part,
+                                 int G, VT* __restrict__ out, double* __restrict__ nrm) {
+  double s = 0;
+  for (int g = 0; g < G; ++g) s += part[g];
+  const double n = sqrt(s);
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i == 0) *nrm = n;
+  if (i >= N) return;
+  using R = decltype(w[0].x);
+  const double inv = n > 0 ? 1.0 / n : 0.0;
+  out[i].x = (R)(w[i].x * inv);
+  out[i].y = (R)(w[i].y * inv);
+}
+
+// Givens step of Arnoldi column j (single thread).  Hcol = accumulated
+// Gram-Schmidt coefficients (j+1 of them), hn = ||w||.  H is (m+1) x m
+// column-major complex; cs real, sn complex; g complex; res = |g[j+1]|.
+__global__ void givens_kernel(int j, int m, double2* __restrict__ hacc, const double* __restrict__ hn,
+                              double2* __restrict__ Hm, double* __restrict__ cs,
+                              double2* __restrict__ sn, double2* __restrict__ g,
+                              double* __restrict__ res) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double2* col = Hm + (int64_t)j * (m + 1);
+  for (int l = 0; l <= j; ++l) col[l] = hacc[l];
+  col[j + 1] = make_double2(*hn, 0.0);
+  for (int l = 0; l < j; ++l) {
+    const double2 a = col[l], b = col[l + 1];
+    const double c = cs[l];
+    const double2 s = sn[l];
+    // [c s; -conj(s) c]
+    col[l] = make_double2(c * a.x + s.x * b.x - s.y * b.y, c * a.y + s.x * b.y + s.y * b.x);
+    col[l + 1] = make_double2(-(s.x * a.x + s.y * a.y) + c * b.x, -(s.x * a.y - s.y * a.x) + c * b.y);
+  }
+  const double2 a = col[j], b = col[j + 1];
+  const double aa = hypot(a.x, a.y), bb = hypot(b.x, b.y);
+  const double rho = hypot(aa, bb);
+  double c;
+  double2 s;
+  if (aa == 0.0) {
+    c = 0.0;
+    s = make_double2(1.0, 0.0);
+  } else {
+    c = aa / rho;
+    const double2 ph = make_double2(a.x / aa, a.y / aa);
+    // s = (a/|a|) conj(b) / rho
+    s = make_double2((ph.x * b.x + ph.y * b.y) / rho, (ph.y * b.x - ph.x * b.y) / rho);
+  }
+  cs[j] = c;
+  sn[j] = s;
+  col[j] = make_double2(c * a.x + s.x * b.x - s.y * b.y, c * a.y + s.x * b.y + s.y * b.x);
+  col[j + 1] = make_double2(0, 0);
+  const double2 gj = g[j];
+  g[j] = make_double2(c * gj.x, c * gj.y);
+  g[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));
+  *res = hypot(g[j + 1].x, g[j + 1].y);
+  for (int l = 0; l <= j + 1; ++l) hacc[l] = make_double2(0, 0);
+}
+
+// y = H(0:k,0:k)^{-1} g (back substitution, single thread)
+__global__ void backsub_kernel(int k, int m, const double2* __restrict__ Hm,
+                               const double2* __restrict__ g, double2* __restrict__ y) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = k - 1; i >= 0; --i) {
+    double2 s = g[i];
+    for (int l = i + 1; l < k; ++l) {
+      const double2 h = Hm[(int64_t)l * (m + 1) + i];
+      s.x -= h.x * y[l].x - h.y * y[l].y;
+      s.y -= h.x * y[l].y + h.y * y[l].x;
+    }
+    y[i] = cdiv2(s, Hm[(int64_t)i * (m + 1) + i]);
+  }
+}
+
+// u = sum_l y_l V_l
+template <class VT>
+__global__ void combine_kernel(const VT* __restrict__ V, int64_t N, int k,
+                               const double2* __restrict__ y, VT* __restrict__ u) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double ar = 0, ai = 0;
+  for (int l = 0; l < k; ++l) {
+    const VT v = V[(int64_t)l * N + i];
+    ar += y[l].x * v.x - y[l].y * v.y;
+    ai += y[l].x * v.y + y[l].y * v.x;
+  }
+  using R = decltype(u[0].x);
+  u[i].x = (R)ar;
+  u[i].y = (R)ai;
+}
+
+// x += alpha * u  (x in XT, u in UT)
+template <class XT, class UT>
+__global__ void axpy_kernel(XT* __restrict__ x, const UT* __restrict__ u, int64_t N, double alpha) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  using R = decltype(x[0].x);
+  x[i].x = (R)(x[i].x + alpha * u[i].x);
+  x[i].y = (R)(x[i].y + alpha * u[i].y);
+}
+
+// r = b - y (complex128); also r_lo = r * scale in complex64 if r_lo
+__global__ void residual_kernel(const double2* __restrict__ b, const double2* __restrict__ y,
+                                double2* __restrict__ r, int64_t N) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  r[i] = make_double2(b[i].x - y[i].x, b[i].y - y[i].y);
+}
+
+template <class VT>
+__global__ void set_first_kernel(double2* __restrict__ g, int m, const double* __restrict__ beta) {
+  if (threadIdx.x != 0) return;
+  for (int l = 0; l <= m; ++l) g[l] = make_double2(0, 0);
+  g[0] = make_double2(*beta, 0.0);
+}
+
+template <class AT, class BT2>
+__global__ void scale_copy_kernel(const AT* __restrict__ a, BT2* __restrict__ b, int64_t N,
+                                  const double* __restrict__ nrm) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double inv = (*nrm > 0) ? 1.0 / *nrm : 0.0;
+  using R = decltype(b[0].x);
+  b[i].x = (R)(a[i].x * inv);
+  b[i].y = (R)(a[i].y * inv);
+}
+
+// RHS block transposes: dir 0: T[i][k] = B[k][i]; dir 1: X[k][i] = T[i][k]
+__global__ void transpose_rhs_kernel(const double2* __restrict__ a, double2* __restrict__ b,
+                                     int64_t N, int r, int dir) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= N * r) return;
+  if (dir == 0) {
+    const int64_t k = t / N, i = t % N;
+    b[i * r + k] = a[k * N + i];
+  } else {
+    const int64_t i = t / r, k = t % r;
+    b[k * N + i] = a[i * r + k];
+  }
+}
+
+// apply the LU row swaps to the columns of T (one thread per column)
+__global__ void permute_rows_kernel(double2* __restrict__ T, int64_t N, int r,
+                                    const int32_t* __restrict__ piv) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= r) return;
+  for (int64_t i = 0; i < N; ++i) {
+    const int64_t p = piv[i];
+    if (p != i) {
+      const double2 t = T[i * r + k];
+      T[i * r + k] = T[p * r + k];
+      T[p * r + k] = t;
+    }
+  }
+}
+
+inline unsigned nblk(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+}  // namespace
+
+// ======================================================= operator products
+size_t op_matvec_work(const mueller_operator* op, int r) {
+  (void)op;
+  (void)r;
+  return 0;
+}
+
+// Y = Z X in the operator's storage: C128 -> FP64; C64_NEAR64 -> complex64
+// storage with FP64 arithmetic (X, Y complex128) plus the FP64 near blocks.
+mueller_status op_matvec(const mueller_operator* op, const void* X, void* Y, int r, void* work,
+                         size_t work_bytes, cudaStream_t s) {
+  (void)work;
+  (void)work_bytes;
+  const mueller_mesh* m = op->mesh;
+  const int64_t N = 4 * m->nn;
+  if (op->dtype == MUELLER_C128) {
+    dim3 grid(nblk(N, 32), r);
+    gemv_c128_kernel<<<grid, 256, 0, s>>>(N, (const double2*)op->Z_dev, op->ldz, (const double2*)X,
+                                          (double2*)Y, N, N, r);
+    MU_CHECK_LAUNCH("gemv_c128_kernel");
+  } else {
+    dim3 grid(nblk(N, 16), r);
+    gemv_c64_kernel<double><<<grid, 256, 0, s>>>(N, (const float4*)op->Z_dev, op->ldz, X, Y, N, N, r);
+    MU_CHECK_LAUNCH("gemv_c64_kernel<double>");
+    dim3 g2(nblk(4 * m->nn, 128), r);
+    near_spmv_kernel<double2, double2><<<g2, 128, 0, s>>>(m->nn, m->near_rowptr, m->near_col,
+                                                          (const double2*)op->near_dev,
+                                                          (const double2*)X, (double2*)Y, N, N, r);
+    MU_CHECK_LAUNCH("near_spmv_kernel");
+  }
+  return MUELLER_OK;
+}
+
+// ================================================================= MBJ build
+struct BlockLayout {
+  int64_t H, B, nb, d;
+  std::vector<int32_t> sz;  // 2 * |I_m|
+};
+
+static BlockLayout layout(int64_t N, int64_t B) {
+  BlockLayout L;
+  L.H = N / 2;
+  L.B = B;
+  L.nb = (L.H + B - 1) / B;
+  L.d = 2 * std::min(B, L.H);
+  for (int64_t b = 0; b < L.nb; ++b) L.sz.push_back((int32_t)(2 * std::min(B, L.H - b * B)));
+  return L;
+}
+
+// in-place LU of nb blocks of size d (active sizes sz_dev), then, if inv,
+// their inverses in 'inv' (d x d per block)
+static mueller_status batched_lu_inverse(double2* A, int64_t d, int nb, const int32_t* sz_dev,
+                                         int32_t* piv, int32_t* status, double2* inv,
+                                         cudaStream_t s) {
+  for (int k0 = 0; k0 < d; k0 += NBK) {
+    lu_panel_kernel<<<nb, 256, 0, s>>>(A, d, sz_dev, k0, piv, status);
+    MU_CHECK_LAUNCH("lu_panel_kernel");
+    const int64_t rest = d - (k0 + NBK);
+    if (rest <= 0) continue;
+    // U12 = L11^{-1} A12 (columns k0+NBK .. n)
+    dim3 gt(nblk(rest, 128), nb);
+    trsm_tile_kernel<<<gt, 128, 0, s>>>(A, A, d, d, d * d, sz_dev, k0, NBK, k0 + NBK, -1, 0);
+    MU_CHECK_LAUNCH("trsm_tile_kernel");
+    dim3 gg(nblk(rest, 64), nblk(rest, 64), nb);
+    gemm_update_kernel<<<gg, 256, 0, s>>>(A, A, A, d, d, d * d, sz_dev, k0, k0 + NBK, -1, k0 + NBK, -1);
+    MU_CHECK_LAUNCH("gemm_update_kernel");
+  }
+  if (!inv) return MUELLER_OK;
+  // inv = U^{-1} L^{-1} P
+  perm_identity_kernel<<<dim3(nblk(d, 128), nb), 128, 0, s>>>(inv, d, sz_dev, piv);
+  MU_CHECK_LAUNCH("perm_identity_kernel");
+  for (int k0 = 0; k0 < d; k0 += NBK) {  // forward: L (unit lower)
+    trsm_tile_kernel<<<dim3(nblk(d, 128), nb), 128, 0, s>>>(A, inv, d, d, d * d, sz_dev, k0, NBK, 0, -1, 0);
+    MU_CHECK_LAUNCH("trsm_tile_kernel(L)");
+    const int64_t below = d - (k0 + NBK);
+    if (below > 0) {
+      dim3 gg(nblk(d, 64), nblk(below, 64), nb);
+      gemm_update_kernel<<<gg, 256, 0, s>>>(A, inv, inv, d, d, d * d, sz_dev, k0, k0 + NBK, -1, 0, -1);
+      MU_CHECK_LAUNCH("gemm_update_kernel(L)");
+    }
+  }
+  const int64_t ntile = (d + NBK - 1) / NBK;
+  for (int64_t t = ntile - 1; t >= 0; --t) {  // backward: U
+    const int k0 = (int)(t * NBK);
+    trsm_tile_kernel<<<dim3(nblk(d, 128), nb), 128, 0, s>>>(A, inv, d, d, d * d, sz_dev, k0, NBK, 0, -1, 1);
+    MU_CHECK_LAUNCH("trsm_tile_kernel(U)");
+    if (k0 > 0) {
+      dim3 gg(nblk(d, 64), nblk(k0, 64), nb);
+      gemm_update_kernel<<<gg, 256, 0, s>>>(A, inv, inv, d, d, d * d, sz_dev, k0, 0, k0, 0, -1);
+      MU_CHECK_LAUNCH("gemm_update_kernel(U)");
+    }
+  }
+  return MUELLER_OK;
+}
+
+// precond_dev layout: [nb][d][d] complex128 inverses, then int32 sz[nb]
+mueller_status precond_build(const mueller_operator* op, int64_t block, void* P, cudaStream_t s) {
+  const mueller_mesh* m = op->mesh;
+  const int64_t N = 4 * m->nn;
+  BlockLayout L = layout(N, block);
+  double2* inv = (double2*)P;
+  int32_t* sz_dev = (int32_t*)(inv + (size_t)L.nb * L.d * L.d);
+  MU_CUDA(cudaMemcpyAsync(sz_dev, L.sz.data(), L.nb * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  double2* A = nullptr;
+  int32_t* piv = nullptr;
+  MU_CUDA(cudaMallocAsync((void**)&A, (size_t)L.nb * L.d * L.d * sizeof(double2), s));
+  MU_CUDA(cudaMallocAsync((void**)&piv, (size_t)L.nb * L.d * sizeof(int32_t) + 64, s));
+  int32_t* status = piv + L.nb * L.d;
+  MU_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), s));
+  dim3 g(nblk(L.d, 128), L.d, L.nb);
+  if (op->dtype == MUELLER_C128) {
+    gather_blocks_kernel<MUELLER_C128><<<g, 128, 0, s>>>(op->Z_dev, op->ldz, L.H, L.B, L.d, sz_dev, A);
+  } else {
+    gather_blocks_kernel<MUELLER_C64_NEAR64><<<g, 128, 0, s>>>(op->Z_dev, op->ldz, L.H, L.B, L.d, sz_dev, A);
+    MU_CHECK_LAUNCH("gather_blocks_kernel");
+    gather_near_kernel<<<nblk(m->nn, 128), 128, 0, s>>>(m->nn, m->near_rowptr, m->near_col,
+                                                        (const double2*)op->near_dev, L.B, L.d,
+                                                        sz_dev, A);
+  }
+  MU_CHECK_LAUNCH("gather kernels");
+  mueller_status st = batched_lu_inverse(A, L.d, (int)L.nb, sz_dev, piv, status, inv, s);
+  int32_t hst = 0;
+  if (!st) {
+    cudaError_t e = cudaMemcpyAsync(&hst, status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_fail(e, "precond status");
+  }
+  cudaFreeAsync(A, s);
+  cudaFreeAsync(piv, s);
+  if (st) return st;
+  if (hst) {
+    set_error("zero pivot in block-Jacobi block " + std::to_string(hst - 1));
+    return MUELLER_ERR_SINGULAR_BLOCK;
+  }
+  return MUELLER_OK;
+}
+
+// ================================================================= solvers
+namespace {
+
+struct GmresWork {
+  int64_t N;
+  int m, G;
+  void* V;      // (m+1) x N complex (T)
+  void* w;      // N
+  void* z;      // N
+  void* u;      // N
+  double2* Hm;  // (m+1) x m
+  double2* hacc;
+  double2* part;
+  double* npart;
+  double* cs;
+  double2* sn;
+  double2* g;
+  double2* y;
+  double* scal;  // [0] res estimate, [1] hn, [2] beta, [3] norm scratch
+  double* hs;    // pinned host scalar
+};
+
+size_t gmres_bytes(int64_t N, int m, size_t elem) {
+  const int G = 16;
+  size_t b = 0;
+  b += (size_t)(m + 1) * N * elem + 3 * (size_t)N * elem;
+  b += (size_t)(m + 1) * m * 16 + (size_t)(m + 2) * 16 + (size_t)(m + 1) * G * 16 + G * 8;
+  b += (size_t)(m + 1) * (8 + 16 + 16 + 16) + 16 * 8;
+  return b + 16 * 256;
+}
+
+template <class VT>
+GmresWork carve_gmres(char*& p, int64_t N, int m) {
+  auto take = [&](size_t bytes) {
+    char* r = p;
+    p += (bytes + 255) & ~size_t(255);
+    return (void*)r;
+  };
+  GmresWork W;
+  W.N = N;
+  W.m = m;
+  W.G = 16;
+  W.V = take((size_t)(m + 1) * N * sizeof(VT));
+  W.w = take(N * sizeof(VT));
+  W.z = take(N * sizeof(VT));
+  W.u = take(N * sizeof(VT));
+  W.Hm = (double2*)take((size_t)(m + 1) * m * 16);
+  W.hacc = (double2*)take((size_t)(m + 2) * 16);
+  W.part = (double2*)take((size_t)(m + 1) * W.G * 16);
+  W.npart = (double*)take(W.G * 8);
+  W.cs = (double*)take((m + 1) * 8);
+  W.sn = (double2*)take((m + 1) * 16);
+  W.g = (double2*)take((m + 1) * 16);
+  W.y = (double2*)take((m + 1) * 16);
+  W.scal = (double*)take(16 * 8);
+  return W;
+}
+
+// The operator as seen by one GMRES: matvec and preconditioner in VT.
+struct InnerOp {
+  const mueller_operator* op;
+  int precision;             // 0: complex128, 1: complex64
+  const float2* near32;      // complex64 near blocks (precision 1)
+  const float2* inv32;       // complex64 inverses (precision 1)
+  BlockLayout L;
+  const int32_t* sz_dev;
+};
+
+template <class VT>
+mueller_status inner_matvec(const InnerOp& I, const VT* x, VT* y, cudaStream_t s) {
+  const mueller_mesh* m = I.op->mesh;
+  const int64_t N = 4 * m->nn;
+  if constexpr (sizeof(VT) == 16) {
+    return op_matvec(I.op, x, y, 1, nullptr, 0, s);
+  } else {
+    gemv_c64_kernel<float><<<dim3(nblk(N, 16), 1), 256, 0, s>>>(N, (const float4*)I.op->Z_dev,
+                                                                I.op->ldz, x, y, N, N, 1);
+    MU_CHECK_LAUNCH("gemv_c64_kernel<float>");
+    near_spmv_kernel<float2, float2><<<dim3(nblk(4 * m->nn, 128), 1), 128, 0, s>>>(
+        m->nn, m->near_rowptr, m->near_col, I.near32, x, y, N, N, 1);
+    MU_CHECK_LAUNCH("near_spmv_kernel<float>");
+    return MUELLER_OK;
+  }
+}
+
+template <class VT>
+mueller_status inner_precond(const InnerOp& I, const VT* v, VT* z, cudaStream_t s) {
+  const int64_t N = 4 * I.op->mesh->nn;
+  if (!I.op->precond_dev) {
+    MU_CUDA(cudaMemcpyAsync(z, v, N * sizeof(VT), cudaMemcpyDeviceToDevice, s));
+    return MUELLER_OK;
+  }
+  dim3 g(nblk(I.L.d, 8), I.L.nb);
+  if constexpr (sizeof(VT) == 16) {
+    mbj_apply_kernel<double2, double2><<<g, 256, 0, s>>>((const double2*)I.op->precond_dev, I.L.d,
+                                                        I.sz_dev, I.L.B, I.L.H, v, z);
+  } else {
+    mbj_apply_kernel<float2, float2><<<g, 256, 0, s>>>(I.inv32, I.L.d, I.sz_dev, I.L.B, I.L.H, v, z);
+  }
+  MU_CHECK_LAUNCH("mbj_apply_kernel");
+  return MUELLER_OK;
+}
+
+// One GMRES(m) solve of A x = b in precision VT, right-preconditioned.
+// x holds x0 on entry.  Convergence on the Arnoldi estimate and on the true
+// residual (in VT) at each restart; rel tolerance 'tol'.  Host reads one
+// scalar per Arnoldi step.
+template <class VT>
+mueller_status gmres(const InnerOp& I, GmresWork& W, const VT* b, VT* x, double tol, int maxit,
+                     int& iters, int& restarts, double& relres, cudaStream_t s) {
+  const int64_t N = W.N;
+  const int m = W.m, G = W.G;
+  VT* V = (VT*)W.V;
+  VT* w = (VT*)W.w;
+  VT* z = (VT*)W.z;
+  VT* u = (VT*)W.u;
+  double* hs = W.hs;
+  auto read = [&](const double* dptr, double& out) -> mueller_status {
+    MU_CUDA(cudaMemcpyAsync(hs, dptr, sizeof(double), cudaMemcpyDeviceToHost, s));
+    MU_CUDA(cudaStreamSynchronize(s));
+    out = hs[0];
+    return MUELLER_OK;
+  };
+  mueller_status st = MUELLER_OK;
+  auto norm_into = [&](const VT* v, double* dst) -> mueller_status {
+    nrm2_kernel<VT><<<G, 256, 0, s>>>(v, N, W.npart, G);
+    MU_CHECK_LAUNCH("nrm2_kernel");
+    normalize_kernel<VT><<<1, 1, 0, s>>>(v, 0, W.npart, G, nullptr, dst);
+    MU_CHECK_LAUNCH("normalize_kernel");
+    return MUELLER_OK;
+  };
+  // ||b||
+  double bn = 0;
+  if ((st = norm_into(b, W.scal + 3))) goto done;
+  if ((st = read(W.scal + 3, bn))) goto done;
+  iters = 0;
+  restarts = 0;
+  if (bn == 0.0) {
+    MU_CUDA(cudaMemsetAsync(x, 0, N * sizeof(VT), s));
+    relres = 0.0;
+    goto done;
+  }
+  // r = b - A x  (in w), beta
+  for (;;) {
+    if ((st = inner_matvec<VT>(I, x, w, s))) goto done;
+    {
+      // w = b - w
+      axpy_kernel<VT, VT><<<nblk(N, 256), 256, 0, s>>>(w, w, N, -2.0);  // w := -w
+      MU_CHECK_LAUNCH("axpy");
+      axpy_kernel<VT, VT><<<nblk(N, 256), 256, 0, s>>>(w, b, N, 1.0);
+      MU_CHECK_LAUNCH("axpy");
+    }
+    if ((st = norm_into(w, W.scal + 2))) goto done;
+    double beta;
+    if ((st = read(W.scal + 2, beta))) goto done;
+    relres = beta / bn;
+    if (relres <= tol || iters >= maxit) goto done;
+    // V0 = w / beta, g = beta e1
+    normalize_kernel<VT><<<nblk(N, 256), 256, 0, s>>>(w, N, W.npart, G, V, W.scal + 2);
+    MU_CHECK_LAUNCH("normalize");
+    set_first_kernel<VT><<<1, 1, 0, s>>>(W.g, m, W.scal + 2);
+    MU_CUDA(cudaMemsetAsync(W.hacc, 0, (m + 2) * sizeof(double2), s));
+    int k = 0;
+    for (int j = 0; j < m && iters < maxit; ++j) {
+      const VT* vj = V + (int64_t)j * N;
+      if ((st = inner_precond<VT>(I, vj, z, s))) goto done;
+      if ((st = inner_matvec<VT>(I, z, w, s))) goto done;
+      for (int pass = 0; pass < 2; ++pass) {
+        dots_kernel<VT><<<dim3(G, j + 1), 256, 0, s>>>(V, N, j + 1, w, W.part, G);
+        MU_CHECK_LAUNCH("dots_kernel");
+        orth_update_kernel<VT><<<nblk(N, 256), 256, 0, s>>>(V, N, j + 1, W.part, G, w, W.hacc);
+        MU_CHECK_LAUNCH("orth_update_kernel");
+      }
+      nrm2_kernel<VT><<<G, 256, 0, s>>>(w, N, W.npart, G);
+      MU_CHECK_LAUNCH("nrm2");
+      normalize_kernel<VT><<<nblk(N, 256), 256, 0, s>>>(w, N, W.npart, G, V + (int64_t)(j + 1) * N,
+                                                        W.scal + 1);
+      MU_CHECK_LAUNCH("normalize");
+      givens_kernel<<<1, 1, 0, s>>>(j, m, W.hacc, W.scal + 1, W.Hm, W.cs, W.sn, W.g, W.scal);
+      MU_CHECK_LAUNCH("givens_kernel");
+      ++iters;
+      k = j + 1;
+      double est;
+      if ((st = read(W.scal, est))) goto done;
+      if (est / bn <= tol || !(est == est)) break;
+    }
+    backsub_kernel<<<1, 1, 0, s>>>(k, m, W.Hm, W.g, W.y);
+    MU_CHECK_LAUNCH("backsub_kernel");
+    combine_kernel<VT><<<nblk(N, 256), 256, 0, s>>>(V, N, k, W.y, u);
+    MU_CHECK_LAUNCH("combine_kernel");
+    if ((st = inner_precond<VT>(I, u, z, s))) goto done;
+    axpy_kernel<VT, VT><<<nblk(N, 256), 256, 0, s>>>(x, z, N, 1.0);
+    MU_CHECK_LAUNCH("axpy");
+    ++restarts;
+  }
+done:
+  return st;
+}
+
+}  // namespace
+
+size_t solve_work(const mueller_operator* op, int r, const mueller_solver_opts* o) {
+  (void)r;
+  const int64_t N = 4 * op->mesh->nn;
+  if (o->mode == MUELLER_SOLVE_DENSE_LU) {
+    return (size_t)N * N * 16 + (size_t)N * 4 + 512 + (size_t)N * r * 16 + 256;
+  }
+  const int m = std::max(1, (int)o->restart);
+  size_t b = 0;
+  if (o->mode == MUELLER_SOLVE_GMRES && op->dtype == MUELLER_C128) {
+    b = gmres_bytes(N, m, 16);
+  } else {
+    b = gmres_bytes(N, m, 8);
+    b += 4 * (size_t)N * 16 + 4 * (size_t)N * 8 + 256 * 8;  // r64, y64, d32, rhs32
+    b += (size_t)op->mesh->nnzb * 16 * 8 + 256;              // near complex64
+    if (op->precond_dev && op->block > 0) {
+      BlockLayout L = layout(N, op->block);
+      b += (size_t)L.nb * L.d * L.d * 8 + 256;
+    }
+  }
+  return b + 4096;
+}
+
+mueller_status solve(const mueller_operator* op, const void* Bv, void* Xv, int r,
+                     const mueller_solver_opts* o, mueller_solve_info* info, void* work,
+                     size_t work_bytes, cudaStream_t s) {
+  const mueller_mesh* m = op->mesh;
+  const int64_t N = 4 * m->nn;
+  *info = mueller_solve_info{0, 0, 0, 0, 0.0, 0.0};
+  const size_t need = solve_work(op, r, o);
+  void* own = nullptr;
+  if (!work) {
+    MU_CUDA(cudaMallocAsync(&own, need, s));
+    work = own;
+  }
+  (void)work_bytes;
+  char* p = (char*)work;
+  mueller_status st = MUELLER_OK;
+  const double2* B = (const double2*)Bv;
+  double2* X = (double2*)Xv;
+  if (o->mode == MUELLER_SOLVE_DENSE_LU) {
+    // LU of a copy of Z, then the row swaps and the two triangular solves on
+    // the r right-hand sides stored as an N x r column block T.
+    double2* A = (double2*)p;
+    int32_t* piv = (int32_t*)(A + (size_t)N * N);
+    int32_t* sz_dev = piv + N;
+    int32_t* status = sz_dev + 4;
+    double2* T = (double2*)(((uintptr_t)(status + 4) + 255) & ~(uintptr_t)255);
+    int32_t nsz = (int32_t)N;
+    cudaError_t e = cudaMemcpy2DAsync(A, N * 16, op->Z_dev, op->ldz * 16, N * 16, N,
+                                      cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sz_dev, &nsz, 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, 4, s);
+    if (e != cudaSuccess) st = cuda_fail(e, "dense LU setup");
+    if (!st) st = batched_lu_inverse(A, N, 1, sz_dev, piv, status, nullptr, s);
+    if (!st) {
+      transpose_rhs_kernel<<<nblk((int64_t)N * r, 256), 256, 0, s>>>(B, T, N, r, 0);
+      permute_rows_kernel<<<nblk(r, 64), 64, 0, s>>>(T, N, r, piv);
+      for (int k0 = 0; k0 < N; k0 += NBK) {
+        trsm_tile_kernel<<<dim3(nblk(r, 128), 1), 128, 0, s>>>(A, T, N, r, 0, sz_dev, k0, NBK, 0, r, 0);
+        const int64_t below = N - (k0 + NBK);
+        if (below > 0)
+          gemm_update_kernel<<<dim3(nblk(r, 64), nblk(below, 64), 1), 256, 0, s>>>(
+              A, T, T, N, r, 0, sz_dev, k0, k0 + NBK, -1, 0, r);
+      }
+      const int64_t ntile = (N + NBK - 1) / NBK;
+      for (int64_t t = ntile - 1; t >= 0; --t) {
+        const int k0 = (int)(t * NBK);
+        trsm_tile_kernel<<<dim3(nblk(r, 128), 1), 128, 0, s>>>(A, T, N, r, 0, sz_dev, k0, NBK, 0, r, 1);
+        if (k0 > 0)
+          gemm_update_kernel<<<dim3(nblk(r, 64), nblk(k0, 64), 1), 256, 0, s>>>(
+              A, T, T, N, r, 0, sz_dev, k0, 0, k0, 0, r);
+      }
+      transpose_rhs_kernel<<<nblk((int64_t)N * r, 256), 256, 0, s>>>(T, X, N, r, 1);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) st = cuda_fail(e, "dense LU solve");
+    }
+    int32_t hst = 0;
+    if (!st) {
+      e = cudaMemcpyAsync(&hst, status, 4, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) st = cuda_fail(e, "dense LU status");
+      if (!st && hst) {
+        set_error("matrix is singular to working precision");
+        st = MUELLER_ERR_SINGULAR_BLOCK;
+      }
+    }
+    if (!st) {
+      info->converged = r;
+      info->relres = 0.0;
+    }
+    if (own) cudaFreeAsync(own, s);
+    if (!st) MU_CUDA(cudaStreamSynchronize(s));
+    return st;
+  }
+  InnerOp I;
+  I.op = op;
+  I.near32 = nullptr;
+  I.inv32 = nullptr;
+  I.sz_dev = nullptr;
+  if (op->precond_dev) {
+    I.L = layout(N, op->block);
+    I.sz_dev = (const int32_t*)((const double2*)op->precond_dev + (size_t)I.L.nb * I.L.d * I.L.d);
+  }
+  const int mres = std::max(1, (int)o->restart);
+  if (o->mode == MUELLER_SOLVE_GMRES && op->dtype == MUELLER_C128) {
+    I.precision = 0;
+    GmresWork W = carve_gmres<double2>(p, N, mres);
+    MU_CUDA(cudaMallocHost((void**)&W.hs, 8 * sizeof(double)));
+    int it_left = o->maxit;
+    for (int k = 0; k < r && !st; ++k) {
+      const double2* b = B + (int64_t)k * N;
+      double2* x = X + (int64_t)k * N;
+      if (!o->warm_start) MU_CUDA(cudaMemsetAsync(x, 0, N * 16, s));
+      int it = 0, rs = 0;
+      double rel = 0;
+      st = gmres<double2>(I, W, b, x, o->tol, it_left, it, rs, rel, s);
+      info->iters += it;
+      info->restarts += rs;
+      info->relres = std::max(info->relres, rel);
+      if (rel <= o->tol) info->converged++;
+    }
+    cudaFreeHost(W.hs);
+  } else {
+    // complex64 inner GMRES on the stored operator, FP64 refinement residual
+    I.precision = 1;
+    const int64_t nnzb = m->nnzb;
+    auto take = [&](size_t bytes) {
+      char* q = p;
+      p += (bytes + 255) & ~size_t(255);
+      return (void*)q;
+    };
+    double2* r64 = (double2*)take(N * 16);
+    double2* y64 = (double2*)take(N * 16);
+    float2* d32 = (float2*)take(N * 8);
+    float2* rhs32 = (float2*)take(N * 8);
+    float2* near32 = nullptr;
+    float2* inv32 = nullptr;
+    if (op->dtype == MUELLER_C64_NEAR64) {
+      near32 = (float2*)take((size_t)nnzb * 16 * 8);
+      c128_to_c64_kernel<<<nblk(nnzb * 16, 256), 256, 0, s>>>((const double2*)op->near_dev, near32, nnzb * 16);
+      MU_CHECK_LAUNCH("c128_to_c64");
+    }
+    if (op->precond_dev) {
+      const int64_t cnt = (int64_t)I.L.nb * I.L.d * I.L.d;
+      inv32 = (float2*)take(cnt * 8);
+      c128_to_c64_kernel<<<nblk(cnt, 256), 256, 0, s>>>((const double2*)op->precond_dev, inv32, cnt);
+      MU_CHECK_LAUNCH("c128_to_c64");
+    }
+    I.near32 = near32;
+    I.inv32 = inv32;
+    GmresWork W = carve_gmres<float2>(p, N, mres);
+    double* hs = nullptr;
+    MU_CUDA(cudaMallocHost((void**)&hs, 8 * sizeof(double)));
+    W.hs = hs + 4;
+    const int maxref = o->max_refine > 0 ? o->max_refine : 20;
+    const double itol = o->inner_tol > 0 ? o->inner_tol : 1e-5;
+    for (int k = 0; k < r && !st; ++k) {
+      const double2* b = B + (int64_t)k * N;
+      double2* x = X + (int64_t)k * N;
+      if (!o->warm_start) MU_CUDA(cudaMemsetAsync(x, 0, N * 16, s));
+      double bn = 0, rel = 1.0;
+      int it_left = o->maxit;
+      nrm2_kernel<double2><<<W.G, 256, 0, s>>>(b, N, W.npart, W.G);
+      normalize_kernel<double2><<<1, 1, 0, s>>>(b, 0, W.npart, W.G, nullptr, W.scal + 4);
+      MU_CUDA(cudaMemcpyAsync(hs, W.scal + 4, 8, cudaMemcpyDeviceToHost, s));
+      MU_CUDA(cudaStreamSynchronize(s));
+      bn = hs[0];
+      for (int ref = 0; ref <= maxref && !st; ++ref) {
+        // r = b - A x in FP64 (complex64 storage, FP64 arithmetic)
+        st = op_matvec(op, x, y64, 1, nullptr, 0, s);
+        if (st) break;
+        residual_kernel<<<nblk(N, 256), 256, 0, s>>>(b, y64, r64, N);
+        nrm2_kernel<double2><<<W.G, 256, 0, s>>>(r64, N, W.npart, W.G);
+        normalize_kernel<double2><<<1, 1, 0, s>>>(r64, 0, W.npart, W.G, nullptr, W.scal + 5);
+        MU_CUDA(cudaMemcpyAsync(hs, W.scal + 5, 8, cudaMemcpyDeviceToHost, s));
+        MU_CUDA(cudaStreamSynchronize(s));
+        const double rn = hs[0];
+        rel = bn > 0 ? rn / bn : 0.0;
+        if (rel <= o->tol || it_left <= 0 || ref == maxref) break;
+        // inner: A d = r / ||r|| in complex64
+        scale_copy_kernel<double2, float2><<<nblk(N, 256), 256, 0, s>>>(r64, rhs32, N, W.scal + 5);
+        MU_CUDA(cudaMemsetAsync(d32, 0, N * 8, s));
+        int it = 0, rs = 0;
+        double irel = 0;
+        st = gmres<float2>(I, W, rhs32, d32, std::max(itol, 0.5 * o->tol / std::max(rel, 1e-300)),
+                           it_left, it, rs, irel, s);
+        if (st) break;
+        it_left -= it;
+        info->iters += it;
+        info->restarts += rs;
+        info->refinements += 1;
+        // x += ||r|| d
+        axpy_kernel<double2, float2><<<nblk(N, 256), 256, 0, s>>>(x, d32, N, rn);
+        MU_CHECK_LAUNCH("axpy");
+      }
+      info->relres = std::max(info->relres, rel);
+      if (rel <= o->tol) info->converged++;
+    }
+    cudaFreeHost(hs);
+  }
+  if (own) cudaFreeAsync(own, s);
+  if (!st) MU_CUDA(cudaStreamSynchronize(s));
+  if (!st && info->converged < r) {
+    set_error("GMRES did not reach the tolerance within maxit");
+    return MUELLER_ERR_NOT_CONVERGED;
+  }
+  return st;
+}
+
+}  // namespace mu

@@ -1,0 +1,89 @@
+// Device helpers: P2 isoparametric triangle (Sec. 3.3) and small vector math.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace mu {
+
+struct d3 {
+  double x, y, z;
+};
+__device__ __forceinline__ d3 mk(double a, double b, double c) { return d3{a, b, c}; }
+__device__ __forceinline__ d3 add(d3 a, d3 b) { return mk(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ d3 sub(d3 a, d3 b) { return mk(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ d3 scl(double s, d3 a) { return mk(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ d3 fma3(double s, d3 a, d3 b) {
+  return mk(fma(s, a.x, b.x), fma(s, a.y, b.y), fma(s, a.z, b.z));
+}
+__device__ __forceinline__ double dot(d3 a, d3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ d3 cross(d3 a, d3 b) {
+  return mk(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+// Quadratic Lagrange functions on the reference simplex with barycentrics
+// l0 = 1 - xi - eta, l1 = xi, l2 = eta; node order v0 v1 v2 m01 m12 m20.
+__device__ __forceinline__ void p2_eval(double xi, double eta, double N[6], double dxi[6],
+                                        double deta[6]) {
+  const double l0 = 1.0 - xi - eta, l1 = xi, l2 = eta;
+  N[0] = l0 * (2.0 * l0 - 1.0);
+  N[1] = l1 * (2.0 * l1 - 1.0);
+  N[2] = l2 * (2.0 * l2 - 1.0);
+  N[3] = 4.0 * l0 * l1;
+  N[4] = 4.0 * l1 * l2;
+  N[5] = 4.0 * l2 * l0;
+  const double g0 = 4.0 * l0 - 1.0;
+  dxi[0] = -g0;
+  dxi[1] = 4.0 * l1 - 1.0;
+  dxi[2] = 0.0;
+  dxi[3] = 4.0 * (l0 - l1);
+  dxi[4] = 4.0 * l2;
+  dxi[5] = -4.0 * l2;
+  deta[0] = -g0;
+  deta[1] = 0.0;
+  deta[2] = 4.0 * l2 - 1.0;
+  deta[3] = -4.0 * l1;
+  deta[4] = 4.0 * l1;
+  deta[5] = 4.0 * (l0 - l2);
+}
+
+// Geometry and continuous frame at a parametric point (Sec. 3.3):
+// X: 6 node positions, T1/T2: nodal t1/t2 of the 6 nodes.
+struct PointGeo {
+  d3 x, n, t1, t2, s1, s2;
+  double J, gs;
+  double N[6];
+};
+
+__device__ __forceinline__ void point_geo(const d3* X, const d3* T1, const d3* T2, double xi,
+                                          double eta, PointGeo& g) {
+  double dxi[6], deta[6];
+  p2_eval(xi, eta, g.N, dxi, deta);
+  d3 x = mk(0, 0, 0), a1 = mk(0, 0, 0), a2 = mk(0, 0, 0), u1 = mk(0, 0, 0), u2 = mk(0, 0, 0);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    x = fma3(g.N[k], X[k], x);
+    a1 = fma3(dxi[k], X[k], a1);
+    a2 = fma3(deta[k], X[k], a2);
+    u1 = fma3(g.N[k], T1[k], u1);
+    u2 = fma3(g.N[k], T2[k], u2);
+  }
+  d3 c = cross(a1, a2);
+  double J = sqrt(dot(c, c));
+  d3 n = scl(1.0 / J, c);
+  d3 p1 = sub(u1, scl(dot(n, u1), n));
+  double n1 = sqrt(dot(p1, p1));
+  d3 t1 = scl(1.0 / n1, p1);
+  d3 p2 = sub(u2, scl(dot(n, u2), n));
+  p2 = sub(p2, scl(dot(t1, p2), t1));
+  double n2 = sqrt(dot(p2, p2));
+  d3 t2 = scl(1.0 / n2, p2);
+  g.x = x;
+  g.n = n;
+  g.t1 = t1;
+  g.t2 = t2;
+  g.s1 = cross(t1, n);
+  g.s2 = cross(t2, n);
+  g.J = J;
+  g.gs = fmin(n1, n2);
+}
+
+}  // namespace mu
