@@ -32,4 +32,4 @@ from .api import (  # noqa: F401
     solve_workspace_bytes,
     sync,
 )
-from .build import build  # noqa: F401
+from .buildlib import build  # noqa: F401

@@ -14,7 +14,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import build as _build
+from . import buildlib as _build
 
 MUELLER_C128 = 0
 MUELLER_C64_NEAR64 = 1
@@ -145,6 +145,19 @@ def _ptr(t):
 
 def _dp(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _dev(t, dtype, name):
+    """A CUDA tensor of the given dtype, row-major contiguous (the C ABI takes
+    plain pointers and assumes dense rows)."""
+    torch = _torch()
+    if not isinstance(t, torch.Tensor):
+        t = torch.as_tensor(t)
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if t.device.type != "cuda":
+        t = t.cuda()
+    return t.contiguous()
 
 
 @dataclass
@@ -305,9 +318,12 @@ def solve(op: Operator, B, opts: SolverOpts, X=None, work=None, stream=None, rai
     """mueller_solve.  Returns (X, info dict)."""
     torch = _torch()
     lib = load_library()
+    B = _dev(B, torch.complex128, "B")
     r = B.shape[0] if B.dim() == 2 else 1
     if X is None:
         X = torch.zeros_like(B)
+    elif not (X.is_cuda and X.dtype == torch.complex128 and X.is_contiguous()):
+        raise TypeError("X must be a contiguous complex128 CUDA tensor")
     o = op.c()
     so = opts.c()
     info = CSolveInfo()
@@ -332,6 +348,7 @@ def solve_workspace_bytes(op: Operator, r: int, opts: SolverOpts) -> int:
 def matvec(op: Operator, X, Y=None, stream=None):
     torch = _torch()
     lib = load_library()
+    X = _dev(X, torch.complex128, "X")
     r = X.shape[0] if X.dim() == 2 else 1
     if Y is None:
         Y = torch.empty_like(X)
@@ -344,8 +361,11 @@ def far_field(mesh: Mesh, params: Params, X, inc, dirs=None, n_theta: int = 48, 
               stream=None):
     """mueller_far_field.  Returns (F tensor r x n_dir x 3 or None, xs numpy r x 3)."""
     torch = _torch()
+    X = _dev(X, torch.complex128, "X")
     inc = np.ascontiguousarray(inc, dtype=np.float64).reshape(-1, 6)
     r = inc.shape[0]
+    if X.numel() != r * mesh.N:
+        raise ValueError("X must hold one solution of length N per incident wave")
     if dirs is None:
         dirs = np.zeros((0, 3))
     dirs = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 3)

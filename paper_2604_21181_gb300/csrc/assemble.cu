@@ -16,6 +16,7 @@
 #include "common.cuh"
 #include "kernels.cuh"
 #include "p2.cuh"
+#include "ssq.cuh"
 
 namespace mu {
 
@@ -88,72 +89,6 @@ __device__ __forceinline__ bool share_corner(const int32_t* a, const int32_t* b)
 #pragma unroll
     for (int j = 0; j < 3; ++j) s |= (a[i] == b[j]);
   return s;
-}
-
-// 12 kernel components of one point pair, times the weights:
-// out[4*op + 2*alpha + beta], op = 0 K1, 1 K2^eps, 2 K2^mu.
-template <class R>
-__device__ __forceinline__ void point_pair(const KConst<R>& K, const R* __restrict__ px,
-                                           const R* __restrict__ qy, bool remainder,
-                                           cx<R> out[12]) {
-  const R rx = px[0] - qy[0], ry = px[1] - qy[1], rz = px[2] - qy[2];
-  const R r2 = rx * rx + ry * ry + rz * rz;
-  const R W = px[18] * qy[18];
-  // x record: x 0-2, n 3-5, t1 6-8, t2 9-11, s1 12-14, s2 15-17, W 18
-  if (r2 == R(0)) {
-    // coincident rule points of a coincident pair (remainder only):
-    // kappa1 - kappa1^s -> i (ka^3 - ki^3)/(6 pi) s.t,  kappa2 - kappa2^s -> 0
-    const R ka3 = K.ka * K.ka * K.ka;
-    const cx<R> ki2 = cmk(K.ki_re * K.ki_re - K.ki_im * K.ki_im, R(2) * K.ki_re * K.ki_im);
-    const cx<R> ki3 = cmul(ki2, cmk(K.ki_re, K.ki_im));
-    const R inv6pi = R(0.0530516476972984452562945877908381257);
-    const cx<R> lim = cmk(ki3.im * inv6pi, (ka3 - ki3.re) * inv6pi);  // i (ka^3 - ki^3)/(6 pi)
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-      for (int b = 0; b < 2; ++b) {
-        const R* s = px + 12 + 3 * a;
-        const R* t = qy + 6 + 3 * b;
-        const R st = (s[0] * t[0] + s[1] * t[1] + s[2] * t[2]) * W;
-        out[2 * a + b] = crs(st, lim);
-        out[4 + 2 * a + b] = cmk<R>(0, 0);
-        out[8 + 2 * a + b] = cmk<R>(0, 0);
-      }
-    return;
-  }
-  const R r = sqrt(r2);
-  const R ir = R(1) / r;
-  const R hx = rx * ir, hy = ry * ir, hz = rz * ir;
-  cx<R> S1, S2, De, Dm;
-  kernel_scalars<R>(K, r, remainder, S1, S2, De, Dm);
-  const R nR = px[3] * hx + px[4] * hy + px[5] * hz;
-  R tR[2], sR[2], Rt[2], nt[2];
-#pragma unroll
-  for (int a = 0; a < 2; ++a) {
-    const R* t = px + 6 + 3 * a;
-    const R* s = px + 12 + 3 * a;
-    const R* u = qy + 6 + 3 * a;  // t_beta(y) with beta = a
-    tR[a] = t[0] * hx + t[1] * hy + t[2] * hz;
-    sR[a] = s[0] * hx + s[1] * hy + s[2] * hz;
-    Rt[a] = hx * u[0] + hy * u[1] + hz * u[2];
-    nt[a] = px[3] * u[0] + px[4] * u[1] + px[5] * u[2];
-  }
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      const R* t = px + 6 + 3 * a;
-      const R* s = px + 12 + 3 * a;
-      const R* u = qy + 6 + 3 * b;
-      const R st = s[0] * u[0] + s[1] * u[1] + s[2] * u[2];
-      const R tt = t[0] * u[0] + t[1] * u[1] + t[2] * u[2];
-      const R G = (tt * nR - tR[a] * nt[b]) * W;
-      const R sRt = sR[a] * Rt[b] * W;
-      const R stw = st * W;
-      out[2 * a + b] = cmk(S1.re * stw + S2.re * sRt, S1.im * stw + S2.im * sRt);
-      out[4 + 2 * a + b] = crs(G, De);
-      out[8 + 2 * a + b] = crs(G, Dm);
-    }
 }
 
 // ------------------------------------------------------- regular pairs
@@ -276,65 +211,11 @@ __global__ void __launch_bounds__(128) regular_kernel(int64_t nt, const R* __res
 // ------------------------------------------------------- touching pairs
 constexpr int TT = 96;  // threads per touching pair (= SSQ points per batch)
 
-__device__ __forceinline__ void ss_point(int cls, int ns, int64_t pt, double& xu, double& xv,
-                                         double& yu, double& yv, double& w) {
-  const int nreg = cls == 3 ? 6 : (cls == 2 ? 5 : 2);
-  const int reg = (int)(pt % nreg);
-  int64_t rest = pt / nreg;
-  const int d = (int)(rest % ns);
-  rest /= ns;
-  const int c = (int)(rest % ns);
-  rest /= ns;
-  const int b = (int)(rest % ns);
-  const int a = (int)(rest / ns);
-  const double xi = c_gl[a], e1 = c_gl[b], e2 = c_gl[c], e3 = c_gl[d];
-  const double W = c_glw[a] * c_glw[b] * c_glw[c] * c_glw[d];
-  const double x3 = xi * xi * xi;
-  if (cls == 3) {  // identical triangles: weight xi^3 e1^2 e2
-    w = W * x3 * e1 * e1 * e2;
-    switch (reg) {
-      case 0: xu = xi; xv = xi * (1 - e1 + e1 * e2); yu = xi * (1 - e1 * e2 * e3); yv = xi * (1 - e1); break;
-      case 1: xu = xi * (1 - e1 * e2 * e3); xv = xi * (1 - e1); yu = xi; yv = xi * (1 - e1 + e1 * e2); break;
-      case 2: xu = xi; xv = xi * e1 * (1 - e2 + e2 * e3); yu = xi * (1 - e1 * e2); yv = xi * e1 * (1 - e2); break;
-      case 3: xu = xi * (1 - e1 * e2); xv = xi * e1 * (1 - e2); yu = xi; yv = xi * e1 * (1 - e2 + e2 * e3); break;
-      case 4: xu = xi * (1 - e1 * e2 * e3); xv = xi * e1 * (1 - e2 * e3); yu = xi; yv = xi * e1 * (1 - e2); break;
-      default: xu = xi; xv = xi * e1 * (1 - e2); yu = xi * (1 - e1 * e2 * e3); yv = xi * e1 * (1 - e2 * e3); break;
-    }
-  } else if (cls == 2) {  // common edge v = 0
-    const double j1 = W * x3 * e1 * e1;
-    w = reg == 0 ? j1 : j1 * e2;
-    switch (reg) {
-      case 0: xu = xi; xv = xi * e1 * e3; yu = xi * (1 - e1 * e2); yv = xi * e1 * (1 - e2); break;
-      case 1: xu = xi; xv = xi * e1; yu = xi * (1 - e1 * e2 * e3); yv = xi * e1 * e2 * (1 - e3); break;
-      case 2: xu = xi * (1 - e1 * e2); xv = xi * e1 * (1 - e2); yu = xi; yv = xi * e1 * e2 * e3; break;
-      case 3: xu = xi * (1 - e1 * e2 * e3); xv = xi * e1 * e2 * (1 - e3); yu = xi; yv = xi * e1; break;
-      default: xu = xi * (1 - e1 * e2 * e3); xv = xi * e1 * (1 - e2 * e3); yu = xi; yv = xi * e1 * e2; break;
-    }
-  } else {  // common vertex (0, 0): weight xi^3 e2
-    w = W * x3 * e2;
-    if (reg == 0) {
-      xu = xi; xv = xi * e1; yu = xi * e2; yv = xi * e2 * e3;
-    } else {
-      xu = xi * e2; xv = xi * e2 * e3; yu = xi; yv = xi * e1;
-    }
-  }
-}
-
-// relabelled reference point (u, v) -> canonical (xi, eta); perm holds the
-// canonical corner of each relabelled corner in 2-bit fields
-__device__ __forceinline__ void to_canonical(int perm, double u, double v, double& xi, double& eta) {
-  const double lp[3] = {1.0 - u, u - v, v};
-  double l[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) l[(perm >> (2 * k)) & 3] = lp[k];
-  xi = l[1];
-  eta = l[2];
-}
-
+template <int Q>
 __global__ void __launch_bounds__(TT) touching_kernel(
     int64_t n_touch, const TouchPair* __restrict__ tp, const double* __restrict__ X,
     const int32_t* __restrict__ T, const double* __restrict__ frame,
-    const double* __restrict__ qd, int Q, int ns, KConst<double> K, double ae_re, double ae_im,
+    const double* __restrict__ qd, int ns, KConst<double> K, double ae_re, double ae_im,
     double am_re, double am_im, int dtype, void* __restrict__ Zv, int64_t ldz, int64_t H,
     double* __restrict__ near, const int32_t* __restrict__ tp_slot) {
   __shared__ d3 sXn[2][6], sT1[2][6], sT2[2][6];
@@ -369,7 +250,7 @@ __global__ void __launch_bounds__(TT) touching_kernel(
     const int64_t pt = base + tid;
     if (pt < npts) {
       double xu, xv, yu, yv, w, xi, eta, yxi, yeta;
-      ss_point(P.cls, ns, pt, xu, xv, yu, yv, w);
+      ss_point(P.cls, ns, pt, c_gl, c_glw, xu, xv, yu, yv, w);
       to_canonical(px, xu, xv, xi, eta);
       to_canonical(py, yu, yv, yxi, yeta);
       PointGeo gx, gy;
@@ -421,6 +302,7 @@ __global__ void __launch_bounds__(TT) touching_kernel(
   for (int pq = tid; pq < Q * Q; pq += TT) {
     const int p = pq / Q, q = pq % Q;
     double px_[QD_STRIDE], qy_[QD_STRIDE];
+#pragma unroll
     for (int c = 0; c < 19; ++c) {
       px_[c] = QX[p * QD_STRIDE + c];
       qy_[c] = QY[q * QD_STRIDE + c];
@@ -435,13 +317,16 @@ __global__ void __launch_bounds__(TT) touching_kernel(
   __syncthreads();
   for (int pc = tid; pc < Q * 12; pc += TT) {
     const int p = pc / 12, c = pc % 12;
-    double vre[MAX_Q], vim[MAX_Q];
+    double vre[Q], vim[Q];
+#pragma unroll
     for (int q = 0; q < Q; ++q) {
       vre[q] = sK[((size_t)p * Q + q) * 24 + 2 * c];
       vim[q] = sK[((size_t)p * Q + q) * 24 + 2 * c + 1];
     }
+#pragma unroll
     for (int j = 0; j < 6; ++j) {
       double are = 0, aim = 0;
+#pragma unroll
       for (int q = 0; q < Q; ++q) {
         are = fma(c_phi64[q * 6 + j], vre[q], are);
         aim = fma(c_phi64[q * 6 + j], vim[q], aim);
@@ -462,13 +347,16 @@ __global__ void __launch_bounds__(TT) touching_kernel(
   for (int jc = tid; jc < 6 * 12; jc += TT) {
     const int j = jc / 12, c = jc % 12;
     const int op = c >> 2, a = (c >> 1) & 1, b = c & 1, ab = c & 3;
-    double vre[MAX_Q], vim[MAX_Q];
+    double vre[Q], vim[Q];
+#pragma unroll
     for (int p = 0; p < Q; ++p) {
       vre[p] = sK[((size_t)p * Q + j) * 24 + 2 * c];
       vim[p] = sK[((size_t)p * Q + j) * 24 + 2 * c + 1];
     }
+#pragma unroll
     for (int i = 0; i < 6; ++i) {
       double are = 0, aim = 0;
+#pragma unroll
       for (int p = 0; p < Q; ++p) {
         are = fma(c_phi64[p * 6 + i], vre[p], are);
         aim = fma(c_phi64[p * 6 + i], vim[p], aim);
@@ -610,9 +498,10 @@ mueller_status launch_touching(mueller_mesh* m, const PhysConsts& P, int Q, int 
   if (m->n_touch == 0) return MUELLER_OK;
   const double ae_re = 0.5 * (P.eps_re + 1.0), ae_im = 0.5 * P.eps_im;
   const double am_re = 0.5 * (P.mu_re + 1.0), am_im = 0.5 * P.mu_im;
-  touching_kernel<<<(unsigned)m->n_touch, TT, 0, s>>>(
-      m->n_touch, m->tp, m->X, m->T, m->frame, m->qd64, Q, ns, kconst<double>(P), ae_re, ae_im,
-      am_re, am_im, dtype, Z, ldz, 2 * m->nn, (double*)near, m->tp_slot);
+  auto kern = Q == 6 ? touching_kernel<6> : touching_kernel<12>;
+  kern<<<(unsigned)m->n_touch, TT, 0, s>>>(m->n_touch, m->tp, m->X, m->T, m->frame, m->qd64, ns,
+                                            kconst<double>(P), ae_re, ae_im, am_re, am_im, dtype,
+                                            Z, ldz, 2 * m->nn, (double*)near, m->tp_slot);
   MU_CHECK_LAUNCH("touching_kernel");
   return MUELLER_OK;
 }

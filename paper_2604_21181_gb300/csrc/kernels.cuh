@@ -29,23 +29,23 @@ struct cx {
   R re, im;
 };
 template <class R>
-__device__ __forceinline__ cx<R> cmk(R a, R b) {
+__host__ __device__ __forceinline__ cx<R> cmk(R a, R b) {
   return cx<R>{a, b};
 }
 template <class R>
-__device__ __forceinline__ cx<R> cadd(cx<R> a, cx<R> b) {
+__host__ __device__ __forceinline__ cx<R> cadd(cx<R> a, cx<R> b) {
   return cx<R>{a.re + b.re, a.im + b.im};
 }
 template <class R>
-__device__ __forceinline__ cx<R> csub(cx<R> a, cx<R> b) {
+__host__ __device__ __forceinline__ cx<R> csub(cx<R> a, cx<R> b) {
   return cx<R>{a.re - b.re, a.im - b.im};
 }
 template <class R>
-__device__ __forceinline__ cx<R> cmul(cx<R> a, cx<R> b) {
+__host__ __device__ __forceinline__ cx<R> cmul(cx<R> a, cx<R> b) {
   return cx<R>{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
 }
 template <class R>
-__device__ __forceinline__ cx<R> crs(R s, cx<R> a) {
+__host__ __device__ __forceinline__ cx<R> crs(R s, cx<R> a) {
   return cx<R>{s * a.re, s * a.im};
 }
 
@@ -62,7 +62,7 @@ struct SeriesLen<float> {
 
 // Q1, Q2, Q3 at z (see above).  'z' is i k R.
 template <class R>
-__device__ __forceinline__ void qfuncs(cx<R> z, cx<R>& q1, cx<R>& q2, cx<R>& q3) {
+__host__ __device__ __forceinline__ void qfuncs(cx<R> z, cx<R>& q1, cx<R>& q2, cx<R>& q3) {
   const R az2 = z.re * z.re + z.im * z.im;
   if (az2 < R(1)) {
     cx<R> t = z;  // z^m/m! at m = 1
@@ -111,7 +111,7 @@ struct KConst {
 
 // S1, S2, De, Dm at distance R (> 0); remainder = drop the singular parts.
 template <class R>
-__device__ __forceinline__ void kernel_scalars(const KConst<R>& K, R r, bool remainder,
+__host__ __device__ __forceinline__ void kernel_scalars(const KConst<R>& K, R r, bool remainder,
                                                cx<R>& S1, cx<R>& S2, cx<R>& De, cx<R>& Dm) {
   const R c = R(0.0795774715459476678844418816862571885);  // 1/(4 pi)
   const cx<R> za = cmk<R>(R(0), K.ka * r);
@@ -135,6 +135,72 @@ __device__ __forceinline__ void kernel_scalars(const KConst<R>& K, R r, bool rem
     De = cadd(De, crs(-c * ir2, cmk(R(1) - K.eps_re, -K.eps_im)));
     Dm = cadd(Dm, crs(-c * ir2, cmk(R(1) - K.mu_re, -K.mu_im)));
   }
+}
+
+// 12 kernel components of one point pair, times the weights:
+// out[4*op + 2*alpha + beta], op = 0 K1, 1 K2^eps, 2 K2^mu.
+template <class R>
+__host__ __device__ __forceinline__ void point_pair(const KConst<R>& K, const R* __restrict__ px,
+                                           const R* __restrict__ qy, bool remainder,
+                                           cx<R> out[12]) {
+  const R rx = px[0] - qy[0], ry = px[1] - qy[1], rz = px[2] - qy[2];
+  const R r2 = rx * rx + ry * ry + rz * rz;
+  const R W = px[18] * qy[18];
+  // x record: x 0-2, n 3-5, t1 6-8, t2 9-11, s1 12-14, s2 15-17, W 18
+  if (r2 == R(0)) {
+    // coincident rule points of a coincident pair (remainder only):
+    // kappa1 - kappa1^s -> i (ka^3 - ki^3)/(6 pi) s.t,  kappa2 - kappa2^s -> 0
+    const R ka3 = K.ka * K.ka * K.ka;
+    const cx<R> ki2 = cmk(K.ki_re * K.ki_re - K.ki_im * K.ki_im, R(2) * K.ki_re * K.ki_im);
+    const cx<R> ki3 = cmul(ki2, cmk(K.ki_re, K.ki_im));
+    const R inv6pi = R(0.0530516476972984452562945877908381257);
+    const cx<R> lim = cmk(ki3.im * inv6pi, (ka3 - ki3.re) * inv6pi);  // i (ka^3 - ki^3)/(6 pi)
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        const R* s = px + 12 + 3 * a;
+        const R* t = qy + 6 + 3 * b;
+        const R st = (s[0] * t[0] + s[1] * t[1] + s[2] * t[2]) * W;
+        out[2 * a + b] = crs(st, lim);
+        out[4 + 2 * a + b] = cmk<R>(0, 0);
+        out[8 + 2 * a + b] = cmk<R>(0, 0);
+      }
+    return;
+  }
+  const R r = sqrt(r2);
+  const R ir = R(1) / r;
+  const R hx = rx * ir, hy = ry * ir, hz = rz * ir;
+  cx<R> S1, S2, De, Dm;
+  kernel_scalars<R>(K, r, remainder, S1, S2, De, Dm);
+  const R nR = px[3] * hx + px[4] * hy + px[5] * hz;
+  R tR[2], sR[2], Rt[2], nt[2];
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    const R* t = px + 6 + 3 * a;
+    const R* s = px + 12 + 3 * a;
+    const R* u = qy + 6 + 3 * a;  // t_beta(y) with beta = a
+    tR[a] = t[0] * hx + t[1] * hy + t[2] * hz;
+    sR[a] = s[0] * hx + s[1] * hy + s[2] * hz;
+    Rt[a] = hx * u[0] + hy * u[1] + hz * u[2];
+    nt[a] = px[3] * u[0] + px[4] * u[1] + px[5] * u[2];
+  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const R* t = px + 6 + 3 * a;
+      const R* s = px + 12 + 3 * a;
+      const R* u = qy + 6 + 3 * b;
+      const R st = s[0] * u[0] + s[1] * u[1] + s[2] * u[2];
+      const R tt = t[0] * u[0] + t[1] * u[1] + t[2] * u[2];
+      const R G = (tt * nR - tR[a] * nt[b]) * W;
+      const R sRt = sR[a] * Rt[b] * W;
+      const R stw = st * W;
+      out[2 * a + b] = cmk(S1.re * stw + S2.re * sRt, S1.im * stw + S2.im * sRt);
+      out[4 + 2 * a + b] = crs(G, De);
+      out[8 + 2 * a + b] = crs(G, Dm);
+    }
 }
 
 }  // namespace mu

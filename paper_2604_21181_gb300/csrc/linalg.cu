@@ -252,26 +252,42 @@ __global__ void trsm_tile_kernel(const double2* __restrict__ A, double2* __restr
   if (c >= c1) return;
   const double2* M = A + (int64_t)b * d * d;
   double2* X = B + (int64_t)b * bstride;
+  // fixed-size, fully unrolled loops keep v[] in registers; rows >= w are
+  // inert (zero right-hand side, never written back)
   double2 v[NBK];
-  for (int i = 0; i < w; ++i) v[i] = X[(int64_t)(k0 + i) * ldb + c];
+#pragma unroll
+  for (int i = 0; i < NBK; ++i)
+    v[i] = i < w ? X[(int64_t)(k0 + i) * ldb + c] : make_double2(0.0, 0.0);
   if (!upper) {
-    for (int i = 0; i < w; ++i)
+#pragma unroll
+    for (int i = 1; i < NBK; ++i)
+#pragma unroll
       for (int j = 0; j < i; ++j) {
-        const double2 l = M[(int64_t)(k0 + i) * d + k0 + j];
-        v[i].x -= l.x * v[j].x - l.y * v[j].y;
-        v[i].y -= l.x * v[j].y + l.y * v[j].x;
+        if (i < w) {
+          const double2 l = M[(int64_t)(k0 + i) * d + k0 + j];
+          v[i].x -= l.x * v[j].x - l.y * v[j].y;
+          v[i].y -= l.x * v[j].y + l.y * v[j].x;
+        }
       }
   } else {
-    for (int i = w - 1; i >= 0; --i) {
-      for (int j = i + 1; j < w; ++j) {
-        const double2 u = M[(int64_t)(k0 + i) * d + k0 + j];
-        v[i].x -= u.x * v[j].x - u.y * v[j].y;
-        v[i].y -= u.x * v[j].y + u.y * v[j].x;
+#pragma unroll
+    for (int i = NBK - 1; i >= 0; --i) {
+      if (i < w) {
+#pragma unroll
+        for (int j = i + 1; j < NBK; ++j) {
+          if (j < w) {
+            const double2 u = M[(int64_t)(k0 + i) * d + k0 + j];
+            v[i].x -= u.x * v[j].x - u.y * v[j].y;
+            v[i].y -= u.x * v[j].y + u.y * v[j].x;
+          }
+        }
+        v[i] = cdiv2(v[i], M[(int64_t)(k0 + i) * d + k0 + i]);
       }
-      v[i] = cdiv2(v[i], M[(int64_t)(k0 + i) * d + k0 + i]);
     }
   }
-  for (int i = 0; i < w; ++i) X[(int64_t)(k0 + i) * ldb + c] = v[i];
+#pragma unroll
+  for (int i = 0; i < NBK; ++i)
+    if (i < w) X[(int64_t)(k0 + i) * ldb + c] = v[i];
 }
 
 // C[r0:r1, c0:c1] -= A[r0:r1, k0:k0+w] * Bm[k0:k0+w, c0:c1] per block:

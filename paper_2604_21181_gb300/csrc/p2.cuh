@@ -7,21 +7,21 @@ namespace mu {
 struct d3 {
   double x, y, z;
 };
-__device__ __forceinline__ d3 mk(double a, double b, double c) { return d3{a, b, c}; }
-__device__ __forceinline__ d3 add(d3 a, d3 b) { return mk(a.x + b.x, a.y + b.y, a.z + b.z); }
-__device__ __forceinline__ d3 sub(d3 a, d3 b) { return mk(a.x - b.x, a.y - b.y, a.z - b.z); }
-__device__ __forceinline__ d3 scl(double s, d3 a) { return mk(s * a.x, s * a.y, s * a.z); }
-__device__ __forceinline__ d3 fma3(double s, d3 a, d3 b) {
+__host__ __device__ __forceinline__ d3 mk(double a, double b, double c) { return d3{a, b, c}; }
+__host__ __device__ __forceinline__ d3 add(d3 a, d3 b) { return mk(a.x + b.x, a.y + b.y, a.z + b.z); }
+__host__ __device__ __forceinline__ d3 sub(d3 a, d3 b) { return mk(a.x - b.x, a.y - b.y, a.z - b.z); }
+__host__ __device__ __forceinline__ d3 scl(double s, d3 a) { return mk(s * a.x, s * a.y, s * a.z); }
+__host__ __device__ __forceinline__ d3 fma3(double s, d3 a, d3 b) {
   return mk(fma(s, a.x, b.x), fma(s, a.y, b.y), fma(s, a.z, b.z));
 }
-__device__ __forceinline__ double dot(d3 a, d3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-__device__ __forceinline__ d3 cross(d3 a, d3 b) {
+__host__ __device__ __forceinline__ double dot(d3 a, d3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__host__ __device__ __forceinline__ d3 cross(d3 a, d3 b) {
   return mk(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
 
 // Quadratic Lagrange functions on the reference simplex with barycentrics
 // l0 = 1 - xi - eta, l1 = xi, l2 = eta; node order v0 v1 v2 m01 m12 m20.
-__device__ __forceinline__ void p2_eval(double xi, double eta, double N[6], double dxi[6],
+__host__ __device__ __forceinline__ void p2_eval(double xi, double eta, double N[6], double dxi[6],
                                         double deta[6]) {
   const double l0 = 1.0 - xi - eta, l1 = xi, l2 = eta;
   N[0] = l0 * (2.0 * l0 - 1.0);
@@ -53,7 +53,7 @@ struct PointGeo {
   double N[6];
 };
 
-__device__ __forceinline__ void point_geo(const d3* X, const d3* T1, const d3* T2, double xi,
+__host__ __device__ __forceinline__ void point_geo(const d3* X, const d3* T1, const d3* T2, double xi,
                                           double eta, PointGeo& g) {
   double dxi[6], deta[6];
   p2_eval(xi, eta, g.N, dxi, deta);

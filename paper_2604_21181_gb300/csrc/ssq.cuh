@@ -1,0 +1,70 @@
+// Sauter-Schwab quadrature points (Sec. 4.2, Sec. 5.1): Duffy-type maps of
+// the coincident (6 regions), common-edge (5) and common-vertex (2) triangle
+// pairs onto [0,1]^4 with a tensor Gauss-Legendre rule of ns points per
+// dimension (Sauter & Schwab, "Boundary Element Methods", Sec. 5.2).  The
+// reference triangle is {0 <= v <= u <= 1}; the shared edge is v = 0 and
+// the shared vertex (0,0) in both triangles; a point (u, v) is the
+// relabelled parametric point (xi', eta') = (u - v, v).
+#pragma once
+#include <stdint.h>
+
+namespace mu {
+
+__host__ __device__ __forceinline__ void ss_point(int cls, int ns, int64_t pt, const double* gl,
+                                                  const double* glw, double& xu, double& xv,
+                                                  double& yu, double& yv, double& w) {
+  const int nreg = cls == 3 ? 6 : (cls == 2 ? 5 : 2);
+  const int reg = (int)(pt % nreg);
+  int64_t rest = pt / nreg;
+  const int d = (int)(rest % ns);
+  rest /= ns;
+  const int c = (int)(rest % ns);
+  rest /= ns;
+  const int b = (int)(rest % ns);
+  const int a = (int)(rest / ns);
+  const double xi = gl[a], e1 = gl[b], e2 = gl[c], e3 = gl[d];
+  const double W = glw[a] * glw[b] * glw[c] * glw[d];
+  const double x3 = xi * xi * xi;
+  if (cls == 3) {  // identical triangles: weight xi^3 e1^2 e2
+    w = W * x3 * e1 * e1 * e2;
+    switch (reg) {
+      case 0: xu = xi; xv = xi * (1 - e1 + e1 * e2); yu = xi * (1 - e1 * e2 * e3); yv = xi * (1 - e1); break;
+      case 1: xu = xi * (1 - e1 * e2 * e3); xv = xi * (1 - e1); yu = xi; yv = xi * (1 - e1 + e1 * e2); break;
+      case 2: xu = xi; xv = xi * e1 * (1 - e2 + e2 * e3); yu = xi * (1 - e1 * e2); yv = xi * e1 * (1 - e2); break;
+      case 3: xu = xi * (1 - e1 * e2); xv = xi * e1 * (1 - e2); yu = xi; yv = xi * e1 * (1 - e2 + e2 * e3); break;
+      case 4: xu = xi * (1 - e1 * e2 * e3); xv = xi * e1 * (1 - e2 * e3); yu = xi; yv = xi * e1 * (1 - e2); break;
+      default: xu = xi; xv = xi * e1 * (1 - e2); yu = xi * (1 - e1 * e2 * e3); yv = xi * e1 * (1 - e2 * e3); break;
+    }
+  } else if (cls == 2) {  // common edge v = 0
+    const double j1 = W * x3 * e1 * e1;
+    w = reg == 0 ? j1 : j1 * e2;
+    switch (reg) {
+      case 0: xu = xi; xv = xi * e1 * e3; yu = xi * (1 - e1 * e2); yv = xi * e1 * (1 - e2); break;
+      case 1: xu = xi; xv = xi * e1; yu = xi * (1 - e1 * e2 * e3); yv = xi * e1 * e2 * (1 - e3); break;
+      case 2: xu = xi * (1 - e1 * e2); xv = xi * e1 * (1 - e2); yu = xi; yv = xi * e1 * e2 * e3; break;
+      case 3: xu = xi * (1 - e1 * e2 * e3); xv = xi * e1 * e2 * (1 - e3); yu = xi; yv = xi * e1; break;
+      default: xu = xi * (1 - e1 * e2 * e3); xv = xi * e1 * (1 - e2 * e3); yu = xi; yv = xi * e1 * e2; break;
+    }
+  } else {  // common vertex (0, 0): weight xi^3 e2
+    w = W * x3 * e2;
+    if (reg == 0) {
+      xu = xi; xv = xi * e1; yu = xi * e2; yv = xi * e2 * e3;
+    } else {
+      xu = xi * e2; xv = xi * e2 * e3; yu = xi; yv = xi * e1;
+    }
+  }
+}
+
+// relabelled reference point (u, v) -> canonical (xi, eta); perm holds the
+// canonical corner of each relabelled corner in 2-bit fields
+__host__ __device__ __forceinline__ void to_canonical(int perm, double u, double v, double& xi, double& eta) {
+  const double lp[3] = {1.0 - u, u - v, v};
+  double l[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) l[(perm >> (2 * k)) & 3] = lp[k];
+  xi = l[1];
+  eta = l[2];
+}
+
+
+}  // namespace mu

@@ -84,7 +84,7 @@ def test_tangent_frame_matches_oracle(level, rule):
     m = mu.Mesh(xyz, tri6)
     fr = m.tangent_frame(rule).cpu().numpy()
     om = oracle.Mesh(xyz, tri6, frame_rule=rule)
-    np.testing.assert_allclose(fr, om.frame(), rtol=0, atol=2e-15)
+    np.testing.assert_allclose(fr, om.frame(), rtol=0, atol=1e-13)
 
 
 @pytest.mark.parametrize("name", list(CASES))
