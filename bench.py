@@ -1,0 +1,427 @@
+#!/usr/bin/env python
+"""Benchmark of the nodal P2 Mueller solver hot path on one GB300.
+
+One step = the whole hot path on the level-3 sphere workload (1280 curved P2
+triangles, N = 10248 unknowns, eps_r = 2.25, k_a = 5):
+  tangent frame + point geometry -> assembly (regular pairs in FP32 into a
+  complex64 Z, touching pairs by Sauter-Schwab and the mass in FP64 into the
+  near blocks, right-hand side) -> Morton block-Jacobi build (B = 256, FP64
+  LU -> inverses) -> GMRES(50) with complex64 inner solves and FP64
+  refinement to ||b - Zx|| <= 1e-8 ||b|| -> far field and cross sections.
+value = element pairs (F^2) per second of the whole step, summed over ranks
+(each rank solves its own copy: replicas, weak scaling).
+
+Also reported (measured outside the timed region): per-kernel CUDA-event
+times, the roofline of the dominant kernel, assembly-only throughput, the
+plain FP64 GPU solve against the mixed one, the end-to-end number through
+host buffers, and the oracle on the host cores.
+
+--impl reference times the CPU oracle (the only reference this method has)
+on bounded samples of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+WORKLOAD = "sphere_L3_eps2.25_ka5"
+METRIC = "element-pairs/s assembled; GMRES solve s, mixed vs FP64 GPU, at rel err <=1e-6"
+UNIT = "element-pairs/s"
+
+SMS = 152
+SM_MAX_HZ = 2.070e9
+# peaks of the plain ALU pipes from unit counts and the maximum SM clock:
+# FP64 2 DFMA/clk/SM (1.26 TFLOP/s, the nominal 1.25), FP32 128 FFMA/clk/SM
+PEAK_FP64 = SMS * 2 * 2 * SM_MAX_HZ
+PEAK_FP32 = SMS * 128 * 2 * SM_MAX_HZ
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-extras", action="store_true", help="skip the untimed extra measurements")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region (sm clock, throttle reasons)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------ flop models
+def touching_flops(n_tri: int, n_touch: int, ns: int, q: int) -> float:
+    """FP64 flops of one touching_kernel launch (all touching pairs).
+
+    Per Sauter-Schwab point: two point geometries (P2 map, derivatives,
+    interpolated frame, projection, Gram-Schmidt: ~300 flops each), R and its
+    direction (13), the 8 singular geometric kernels (~137), staging of the
+    48 weighted trial values (96) and the 288 multiply-adds of the
+    contraction (576): 1433 flops.  Per pair, the remainder kappa - kappa^s
+    on the Q x Q rule (~900 flops per point pair) and its 6 x 6 x 12
+    contraction (2 * 432 * Q * 2 flops)."""
+    n_coinc = n_tri
+    n_edge = 3 * n_tri
+    n_vert = n_touch - n_coinc - n_edge
+    pts = (6 * n_coinc + 5 * n_edge + 2 * n_vert) * ns ** 4
+    per_pair = q * q * 900 + 2 * 432 * q * 2
+    return pts * 1433.0 + n_touch * per_pair
+
+
+def regular_flops(n_tri: int, n_touch: int, q: int) -> float:
+    """FP32 flops of one regular_kernel launch: per non-touching element pair,
+    Q*Q point pairs of the fused 12-component kernel (~300 flops: R, the
+    complex exponentials and the four radial scalars, 17 frame dot products,
+    12 complex kernel values) and the two contractions (2 * 432 * Q * 2)."""
+    pairs = n_tri * n_tri - n_touch
+    return pairs * (q * q * 300.0 + 2 * 432 * q * 2)
+
+
+# ---------------------------------------------------------------- ours
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2604_21181_gb300 as mu
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    xyz, tri6, inc, w = workloads.workload(args.workload)
+    p = mu.Params.from_workload(w)
+    F = tri6.shape[0]
+    pairs = float(F) * F
+    block = int(w["block"])
+    r = inc.shape[0]
+    opts = mu.SolverOpts(mode=mu.SOLVE_GMRES_IR, restart=int(w["restart"]), tol=float(w["tol"]),
+                         inner_tol=1e-5, use_precond=1)
+
+    mesh = mu.Mesh(xyz, tri6)
+    N = mesh.N
+    info = mesh.info()
+    Z = torch.empty((N, N), dtype=torch.complex64, device=dev)
+    near = torch.empty(mesh.near_bytes() // 16, dtype=torch.complex128, device=dev)
+    B = torch.empty((r, N), dtype=torch.complex128, device=dev)
+    X = torch.zeros((r, N), dtype=torch.complex128, device=dev)
+    op = mu.Operator(mesh, Z, near, mu.MUELLER_C64_NEAR64)
+    Pbuf = None
+
+    def step():
+        nonlocal Pbuf
+        mesh.tangent_frame(p.frame_rule, out=False)
+        mu.assemble(mesh, p, mu.MUELLER_C64_NEAR64, inc=inc, Z=Z, near=near, B=B)
+        Pbuf = mu.precond_build(op, block)
+        _, sinfo = mu.solve(op, B, opts, X=X, work=work)
+        _, xs = mu.far_field(mesh, p, X, inc)
+        return sinfo, xs
+
+    mesh.tangent_frame(p.frame_rule, out=False)
+    mu.assemble(mesh, p, mu.MUELLER_C64_NEAR64, inc=inc, Z=Z, near=near, B=B)
+    mu.precond_build(op, block)
+    work = torch.empty(mu.solve_workspace_bytes(op, r, opts), dtype=torch.uint8, device=dev)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    l0 = mu.launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    infos = []
+    for _ in range(args.steps):
+        infos.append(step())
+    ev1.record()
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    launches = (mu.launch_count() - l0) // max(1, args.steps)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = pairs * world / (ms_max / 1e3)
+    sinfo, xs = infos[-1]
+
+    extras = {}
+    roofline = None
+    e2e = None
+    cpu = None
+    if rank == 0 and not args.no_extras:
+        # ---- per-kernel CUDA-event times of one step (profiling on)
+        mu.profile_reset()
+        mu.profile_enable(True)
+        step()
+        mu.profile_enable(False)
+        prof = mu.profile_report()
+        kernels = sorted(((v[0], k, v[1]) for k, v in prof.items()), reverse=True)
+        tot = sum(v[0] for v in kernels)
+        extras["kernels_ms"] = {k: {"ms": round(ms_, 3), "launches": n, "share": round(ms_ / tot, 4)}
+                                for ms_, k, n in kernels[:12]}
+        top_ms, top_name, top_n = kernels[0]
+        q, ns = int(w["q_regular"]), int(w["ssq_order"])
+        if top_name.startswith("touching_kernel"):
+            fl = touching_flops(F, info["n_touching"], ns, q)
+            ach = fl / (top_ms / top_n / 1e3) / 1e12
+            roofline = {"kernel": top_name, "bound": "alu", "pipe": "fp64", "achieved": round(ach, 4),
+                        "peak": round(PEAK_FP64 / 1e12, 4), "unit": "TFLOP/s",
+                        "frac": round(ach / (PEAK_FP64 / 1e12), 4), "traffic": None,
+                        "peak_source": "152 SMs x 2 DFMA/clk x 2.07 GHz (unit counts, max clock)"}
+        elif top_name.startswith("regular_kernel"):
+            fl = regular_flops(F, info["n_touching"], q)
+            ach = fl / (top_ms / top_n / 1e3) / 1e12
+            roofline = {"kernel": top_name, "bound": "alu", "pipe": "fp32", "achieved": round(ach, 3),
+                        "peak": round(PEAK_FP32 / 1e12, 3), "unit": "TFLOP/s",
+                        "frac": round(ach / (PEAK_FP32 / 1e12), 4), "traffic": None,
+                        "peak_source": "152 SMs x 128 FFMA/clk x 2.07 GHz"}
+        else:
+            roofline = {"kernel": top_name, "bound": None, "note": "no model for this kernel"}
+        # ---- assembly-only throughput, mixed and FP64
+        def timed(fn, reps=3):
+            fn()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(reps):
+                fn()
+            b.record()
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / reps
+
+        t_asm_mixed = timed(lambda: mu.assemble(mesh, p, mu.MUELLER_C64_NEAR64, inc=inc, Z=Z,
+                                                near=near, B=B))
+        extras["assembly_mixed_ms"] = round(t_asm_mixed, 3)
+        extras["assembly_mixed_pairs_per_s"] = pairs / (t_asm_mixed / 1e3)
+        # mixed solve alone (operator and preconditioner ready)
+        mu.precond_build(op, block)
+        t_solve_mixed = timed(lambda: mu.solve(op, B, opts, X=X, work=work), reps=2)
+        _, sinfo = mu.solve(op, B, opts, X=X, work=work)
+        Xmix = X.clone()
+        # FP64 path: complex128 Z, FP64 GMRES with the same preconditioner size
+        del Pbuf
+        Z64 = torch.empty((N, N), dtype=torch.complex128, device=dev)
+        t_asm64 = timed(lambda: mu.assemble(mesh, p, mu.MUELLER_C128, inc=inc, Z=Z64, B=B), reps=1)
+        op64 = mu.Operator(mesh, Z64, dtype=mu.MUELLER_C128)
+        mu.precond_build(op64, block)
+        o64 = mu.SolverOpts(mode=mu.SOLVE_GMRES, restart=int(w["restart"]), tol=float(w["tol"]),
+                            use_precond=1)
+        X64 = torch.zeros_like(X)
+        w64 = torch.empty(mu.solve_workspace_bytes(op64, r, o64), dtype=torch.uint8, device=dev)
+        t_solve64 = timed(lambda: mu.solve(op64, B, o64, X=X64, work=w64), reps=2)
+        _, info64 = mu.solve(op64, B, o64, X=X64, work=w64)
+        rel = (torch.linalg.norm(Xmix - X64) / torch.linalg.norm(X64)).item()
+        extras["assembly_fp64_ms"] = round(t_asm64, 3)
+        extras["assembly_fp64_pairs_per_s"] = pairs / (t_asm64 / 1e3)
+        extras["solve"] = {
+            "mixed_s": round(t_solve_mixed / 1e3, 5), "fp64_s": round(t_solve64 / 1e3, 5),
+            "speedup": round(t_solve64 / t_solve_mixed, 3),
+            "mixed_iters": sinfo["iters"], "mixed_refinements": sinfo["refinements"],
+            "mixed_relres": sinfo["relres"], "fp64_iters": info64["iters"],
+            "fp64_relres": info64["relres"], "rel_err_mixed_vs_fp64": rel,
+        }
+        del Z64, op64, w64
+        extras["cross_sections"] = {"C_ext": float(xs[0, 0]), "C_sca": float(xs[0, 1]),
+                                    "C_abs": float(xs[0, 2])}
+        # ---- end to end through host buffers: mesh from host arrays, result
+        # (cross sections) back to the host
+        def e2e_step():
+            m2 = mu.Mesh(xyz, tri6)
+            m2.tangent_frame(p.frame_rule, out=False)
+            mu.assemble(m2, p, mu.MUELLER_C64_NEAR64, inc=inc, Z=Z, near=near, B=B)
+            o2 = mu.Operator(m2, Z, near, mu.MUELLER_C64_NEAR64)
+            mu.precond_build(o2, block)
+            mu.solve(o2, B, opts, X=X, work=work)
+            _, xs2 = mu.far_field(m2, p, X, inc)
+            m2.free()
+            return xs2
+
+        e2e_step()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(args.steps):
+            e2e_step()
+        b.record()
+        torch.cuda.synchronize()
+        ms_e2e = a.elapsed_time(b) / args.steps
+        e2e = {"value": pairs / (ms_e2e / 1e3), "unit": UNIT, "ms_per_step": round(ms_e2e, 3),
+               "h2d_bytes_per_step": int(xyz.nbytes + tri6.nbytes + inc.nbytes),
+               "d2h_bytes_per_step": int(r * 3 * 8)}
+        cpu = cpu_baseline(args.workload, budget_s=15.0)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_max, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n_tri": F, "n_dof": N, "element_pairs": int(pairs),
+                       "eps_r": list(w["eps_r"]), "ka": w["ka"], "q_regular": w["q_regular"],
+                       "ssq_order": w["ssq_order"], "block": block, "restart": w["restart"],
+                       "tol": w["tol"], "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (complex64 Z = %.2f GB)" % (N * N * 8 / 1e9)},
+            "clocks": clk, "gpu_launches": int(launches),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "solve_info": {"iters": sinfo["iters"], "refinements": sinfo["refinements"],
+                           "relres": sinfo["relres"]},
+        }
+        line.update(extras)
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------ CPU oracle
+def oracle_sample(workload: str, n_test_elems: int):
+    """Oracle assembly of the rows of the first n_test_elems Morton elements'
+    nodes.  Returns (element pairs processed, seconds, threads)."""
+    import oracle
+
+    xyz, tri6, inc, w = workloads.workload(workload)
+    om = oracle.Mesh(xyz, tri6)
+    pw = dict(ka=w["ka"], eps_r=w["eps_r"], mu_r=w["mu_r"], q_regular=w["q_regular"],
+              ssq_order=w["ssq_order"])
+    nodes = np.unique(om.tri6[:n_test_elems].ravel())
+    sel = np.zeros(om.nn, bool)
+    sel[nodes] = True
+    n_ex = int(np.any(sel[om.tri6], axis=1).sum())  # test elements the oracle visits
+    t0 = time.perf_counter()
+    om.assemble(pw, rows=nodes)
+    dt = time.perf_counter() - t0
+    return n_ex * om.nt, dt, oracle.num_threads()
+
+
+def cpu_baseline(workload: str, budget_s: float = 15.0):
+    xyz, tri6, inc, w = workloads.workload(workload)
+    F = tri6.shape[0]
+    n = max(1, F // 64)
+    pairs, dt, th = oracle_sample(workload, n)
+    # grow the sample towards the time budget (10-30 s of CPU work)
+    if dt < budget_s / 4 and n < F:
+        n2 = min(F, int(n * budget_s / max(dt, 1e-3)))
+        pairs, dt, th = oracle_sample(workload, n2)
+        n = n2
+    return {"value": pairs / dt, "unit": UNIT, "cores": th, "kind": "oracle",
+            "sample": f"oracle FP64 assembly of the Z rows of the nodes of {n} of {F} test "
+                      f"elements ({pairs} element pairs incl. Sauter-Schwab), {dt:.1f} s"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    xyz, tri6, inc, w = workloads.workload(args.workload)
+    F = tri6.shape[0]
+    n = max(1, F // 64)
+    for _ in range(args.warmup):
+        oracle_sample(args.workload, max(1, n // 4))
+    tot_pairs, tot_s, th = 0, 0.0, 1
+    for _ in range(args.steps):
+        pairs, dt, th = oracle_sample(args.workload, n)
+        tot_pairs += pairs
+        tot_s += dt
+    value = tot_pairs / tot_s
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * tot_s / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "n_tri": F, "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": th, "kind": "oracle",
+                             "sample": f"per step: oracle FP64 assembly of the Z rows of the nodes "
+                                       f"of {n} of {F} test elements"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

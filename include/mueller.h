@@ -265,6 +265,23 @@ mueller_status mueller_far_field(mueller_mesh* mesh, const mueller_params* param
                                  const double* dirs, int64_t n_dir, void* F_dev, double* xs,
                                  int32_t n_theta, int32_t n_phi, void* stream);
 
+/*
+ * Launch accounting and per-kernel timing (no counterpart in the paper: a
+ * measurement aid).  Every kernel launch of the library is counted.  With
+ * profiling enabled, each launch is bracketed by CUDA events on its own
+ * stream and the call waits for the closing event, so enabled profiling
+ * serialises the host with the device; it is off by default.
+ *   mueller_profile_get: total milliseconds and launches of a kernel name
+ *   (returns 0 if the name was never timed).  mueller_profile_names writes
+ *   the timed names, newline separated, into buf (truncated to buflen) and
+ *   returns their count.
+ */
+void mueller_profile_enable(int32_t on);
+void mueller_profile_reset(void);
+int64_t mueller_launch_count(void);
+int32_t mueller_profile_get(const char* name, double* total_ms, int64_t* launches);
+int32_t mueller_profile_names(char* buf, size_t buflen);
+
 /* Block until all work queued on the stream is done; surfaces device faults. */
 mueller_status mueller_sync(void* stream);
 

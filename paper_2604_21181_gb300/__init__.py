@@ -25,7 +25,11 @@ from .api import (  # noqa: F401
     SolverOpts,
     assemble,
     far_field,
+    launch_count,
     load_library,
+    profile_enable,
+    profile_report,
+    profile_reset,
     matvec,
     precond_build,
     solve,

@@ -72,6 +72,8 @@ EXPORTS = [
     "mueller_assemble", "mueller_near_bytes", "mueller_precond_build", "mueller_precond_bytes",
     "mueller_solve", "mueller_solve_workspace_bytes", "mueller_matvec",
     "mueller_matvec_workspace_bytes", "mueller_far_field", "mueller_sync",
+    "mueller_profile_enable", "mueller_profile_reset", "mueller_launch_count",
+    "mueller_profile_get", "mueller_profile_names",
 ]
 
 _lib = None
@@ -110,6 +112,11 @@ def load_library(build_if_missing: bool = True):
         "mueller_far_field": (C.c_int, [vp, C.POINTER(CParams), vp, i32, dp, dp, i64, vp, dp,
                                         i32, i32, vp]),
         "mueller_sync": (C.c_int, [vp]),
+        "mueller_profile_enable": (None, [i32]),
+        "mueller_profile_reset": (None, []),
+        "mueller_launch_count": (i64, []),
+        "mueller_profile_get": (i32, [C.c_char_p, dp, C.POINTER(i64)]),
+        "mueller_profile_names": (i32, [C.c_char_p, C.c_size_t]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -381,3 +388,33 @@ def far_field(mesh: Mesh, params: Params, X, inc, dirs=None, n_theta: int = 48, 
 
 def sync(stream=None):
     _check(load_library().mueller_sync(_stream(stream)))
+
+
+def profile_enable(on: bool = True):
+    """Per-kernel CUDA-event timing on the launching stream (serialising)."""
+    load_library().mueller_profile_enable(1 if on else 0)
+
+
+def profile_reset():
+    load_library().mueller_profile_reset()
+
+
+def launch_count() -> int:
+    """Kernel launches made by the library since load (or the last reset)."""
+    return int(load_library().mueller_launch_count())
+
+
+def profile_report() -> dict:
+    """{kernel name: (total ms, launches)} of the timed launches."""
+    lib = load_library()
+    buf = C.create_string_buffer(1 << 16)
+    lib.mueller_profile_names(buf, len(buf))
+    out = {}
+    for name in buf.value.decode().split("\n"):
+        if not name:
+            continue
+        ms = C.c_double()
+        n = C.c_int64()
+        lib.mueller_profile_get(name.encode(), C.byref(ms), C.byref(n))
+        out[name] = (ms.value, n.value)
+    return out

@@ -476,7 +476,7 @@ mueller_status launch_regular_t(mueller_mesh* m, const PhysConsts& P, R* Z, int6
   auto kern = regular_kernel<R, Q>;
   MU_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
   dim3 grid((unsigned)((m->nt + C::WARPS - 1) / C::WARPS), (unsigned)((m->nt + C::TY - 1) / C::TY));
-  kern<<<grid, 32 * C::WARPS, C::smem, s>>>(m->nt, qd, m->T, kconst<R>(P), Z, ldz, 2 * m->nn);
+  { Prof prof_("regular_kernel<R,Q>", s); kern<<<grid, 32 * C::WARPS, C::smem, s>>>(m->nt, qd, m->T, kconst<R>(P), Z, ldz, 2 * m->nn); }
   MU_CHECK_LAUNCH("regular_kernel");
   return MUELLER_OK;
 }
@@ -499,9 +499,9 @@ mueller_status launch_touching(mueller_mesh* m, const PhysConsts& P, int Q, int 
   const double ae_re = 0.5 * (P.eps_re + 1.0), ae_im = 0.5 * P.eps_im;
   const double am_re = 0.5 * (P.mu_re + 1.0), am_im = 0.5 * P.mu_im;
   auto kern = Q == 6 ? touching_kernel<6> : touching_kernel<12>;
-  kern<<<(unsigned)m->n_touch, TT, 0, s>>>(m->n_touch, m->tp, m->X, m->T, m->frame, m->qd64, ns,
+  { Prof prof_("touching_kernel<Q>", s); kern<<<(unsigned)m->n_touch, TT, 0, s>>>(m->n_touch, m->tp, m->X, m->T, m->frame, m->qd64, ns,
                                             kconst<double>(P), ae_re, ae_im, am_re, am_im, dtype,
-                                            Z, ldz, 2 * m->nn, (double*)near, m->tp_slot);
+                                            Z, ldz, 2 * m->nn, (double*)near, m->tp_slot); }
   MU_CHECK_LAUNCH("touching_kernel");
   return MUELLER_OK;
 }
@@ -515,8 +515,8 @@ mueller_status launch_mass_rhs(mueller_mesh* m, const PhysConsts& P, int Q, int 
   (void)near;
   if (!B || r == 0) return MUELLER_OK;
   const int64_t n = (int64_t)r * m->nt * 6;
-  rhs_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(m->nt, Q, m->qd64, m->T, inc_dev, r,
-                                                         P.ka, 4 * m->nn, (double*)B);
+  { Prof prof_("rhs_kernel", s); rhs_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(m->nt, Q, m->qd64, m->T, inc_dev, r,
+                                                         P.ka, 4 * m->nn, (double*)B); }
   MU_CHECK_LAUNCH("rhs_kernel");
   return MUELLER_OK;
 }
@@ -525,9 +525,9 @@ mueller_status launch_mirror_k1(int64_t N, int dtype, void* Z, int64_t ldz, cuda
   const int64_t H = N / 2;
   const unsigned grid = (unsigned)((H * H + 255) / 256);
   if (dtype == MUELLER_C128)
-    mirror_kernel<double><<<grid, 256, 0, s>>>(H, (double*)Z, ldz);
+    { Prof prof_("mirror_kernel<double>", s); mirror_kernel<double><<<grid, 256, 0, s>>>(H, (double*)Z, ldz); }
   else
-    mirror_kernel<float><<<grid, 256, 0, s>>>(H, (float*)Z, ldz);
+    { Prof prof_("mirror_kernel<float>", s); mirror_kernel<float><<<grid, 256, 0, s>>>(H, (float*)Z, ldz); }
   MU_CHECK_LAUNCH("mirror_kernel");
   return MUELLER_OK;
 }

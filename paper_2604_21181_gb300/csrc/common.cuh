@@ -28,6 +28,22 @@ mueller_status cuda_fail(cudaError_t e, const char* what);
     if (e_ != cudaSuccess) return mu::cuda_fail(e_, what);   \
   } while (0)
 
+// ----------------------------------------------------- launch profiling
+// Every kernel launch is wrapped in a Prof scope: it counts the launch and,
+// when profiling is enabled (mueller_profile_enable), records CUDA events
+// around the launch on its stream, waits for the end event and accumulates
+// the elapsed time under the kernel's name.
+class Prof {
+ public:
+  Prof(const char* name, cudaStream_t s);
+  ~Prof();
+
+ private:
+  const char* name_;
+  cudaStream_t s_;
+  cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
+
 // --------------------------------------------------- quadrature tables
 // Triangle rule on the reference simplex (weights sum to 1/2) and Gauss-
 // Legendre on [0,1]; derived on the host (see quadrature.cu).

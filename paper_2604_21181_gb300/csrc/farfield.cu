@@ -246,16 +246,16 @@ mueller_status far_field(mueller_mesh* m, const PhysConsts& P, int Q, const void
   if (e == cudaSuccess) e = cudaMemcpyAsync(dphi, phi, sizeof(phi), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) st = cuda_fail(e, "far-field setup");
   if (!st) {
-    currents_kernel<<<dim3(nblk_pts, r), 256, 0, s>>>(m->nt, Q, m->qd64, m->T, (const double2*)X, r,
-                                                       N, dphi, rec, cab);
+    { Prof prof_("currents_kernel", s); currents_kernel<<<dim3(nblk_pts, r), 256, 0, s>>>(m->nt, Q, m->qd64, m->T, (const double2*)X, r,
+                                                       N, dphi, rec, cab); }
     for (int sidx = 0; sidx < r; ++sidx)
-      far_kernel<<<dim3((unsigned)nd, 1), 256, 0, s>>>(np, m->qd64, rec + (size_t)sidx * np * 6,
+      { Prof prof_("far_kernel", s); far_kernel<<<dim3((unsigned)nd, 1), 256, 0, s>>>(np, m->qd64, rec + (size_t)sidx * np * 6,
                                                        ddirs + (size_t)sidx * nd * 3, nd, P.ka,
-                                                       Fall + (size_t)sidx * nd * 3);
-    xs_kernel<<<r, 256, 0, s>>>(Fall, nd, n_theta, n_phi, dwth, dinc, P.ka, cab, (int)nblk_pts, dxs);
+                                                       Fall + (size_t)sidx * nd * 3); }
+    { Prof prof_("xs_kernel", s); xs_kernel<<<r, 256, 0, s>>>(Fall, nd, n_theta, n_phi, dwth, dinc, P.ka, cab, (int)nblk_pts, dxs); }
     if (ndir > 0)
-      copy_user_dirs_kernel<<<(unsigned)(((int64_t)r * ndir * 3 + 255) / 256), 256, 0, s>>>(
-          Fall, nd, 1 + nsph, ndir, r, (double2*)F);
+      { Prof prof_("copy_user_dirs_kernel", s); copy_user_dirs_kernel<<<(unsigned)(((int64_t)r * ndir * 3 + 255) / 256), 256, 0, s>>>(
+          Fall, nd, 1 + nsph, ndir, r, (double2*)F); }
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(xs, dxs, (size_t)r * 3 * 8, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -123,8 +123,8 @@ __global__ void __launch_bounds__(128) quad_geometry_kernel(int64_t nt, int Q, R
 
 mueller_status launch_frame(mueller_mesh* m, int frame_rule, cudaStream_t s) {
   const int bs = 128;
-  frame_kernel<<<(unsigned)((m->nn + bs - 1) / bs), bs, 0, s>>>(m->nn, m->X, m->T, m->n2e_ptr,
-                                                               m->n2e, frame_rule, m->frame);
+  { Prof prof_("frame_kernel", s); frame_kernel<<<(unsigned)((m->nn + bs - 1) / bs), bs, 0, s>>>(m->nn, m->X, m->T, m->n2e_ptr,
+                                                               m->n2e, frame_rule, m->frame); }
   MU_CHECK_LAUNCH("frame_kernel");
   return MUELLER_OK;
 }
@@ -140,8 +140,8 @@ mueller_status launch_quad_geometry(mueller_mesh* m, const TriangleRule& rule, c
   MU_CUDA(cudaMemcpyAsync(m->d_scal, &big, sizeof(double), cudaMemcpyHostToDevice, s));
   const int bs = 128;
   const int64_t n = m->nt * rule.q;
-  quad_geometry_kernel<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(
-      m->nt, rule.q, ra, m->X, m->T, m->frame, m->qd64, m->qd32, (unsigned long long*)m->d_scal);
+  { Prof prof_("quad_geometry_kernel", s); quad_geometry_kernel<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(
+      m->nt, rule.q, ra, m->X, m->T, m->frame, m->qd64, m->qd32, (unsigned long long*)m->d_scal); }
   MU_CHECK_LAUNCH("quad_geometry_kernel");
   // 'big' lives on the host stack: make sure the copy above has consumed it
   MU_CUDA(cudaStreamSynchronize(s));

@@ -12,6 +12,7 @@
 #include <chrono>
 #include <complex>
 #include <map>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -27,6 +28,36 @@ void set_error(const std::string& msg) { g_last_error = msg; }
 mueller_status cuda_fail(cudaError_t e, const char* what) {
   set_error(std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e));
   return e == cudaErrorMemoryAllocation ? MUELLER_ERR_OOM : MUELLER_ERR_CUDA;
+}
+
+// ----------------------------------------------------- launch profiling
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static int64_t g_launches = 0;
+static std::map<std::string, std::pair<double, int64_t>> g_prof;
+
+Prof::Prof(const char* name, cudaStream_t s) : name_(name), s_(s) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  ++g_launches;
+  if (g_prof_on) {
+    cudaEventCreate(&a_);
+    cudaEventCreate(&b_);
+    cudaEventRecord(a_, s_);
+  }
+}
+
+Prof::~Prof() {
+  if (!a_) return;
+  cudaEventRecord(b_, s_);
+  cudaEventSynchronize(b_);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a_, b_);
+  cudaEventDestroy(a_);
+  cudaEventDestroy(b_);
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  auto& e = g_prof[name_];
+  e.first += ms;
+  e.second += 1;
 }
 
 static mueller_status fail(mueller_status s, const std::string& msg) {
@@ -531,6 +562,48 @@ mueller_status mueller_far_field(mueller_mesh* m, const mueller_params* p, const
   st = ensure_geometry(m, p->q_regular, s);
   if (st) return st;
   return far_field(m, make_phys(p), p->q_regular, X, r, inc, dirs, ndir, F, xs, n_theta, n_phi, s);
+}
+
+void mueller_profile_enable(int32_t on) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_on = on != 0;
+}
+
+void mueller_profile_reset(void) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof.clear();
+  g_launches = 0;
+}
+
+int64_t mueller_launch_count(void) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  return g_launches;
+}
+
+int32_t mueller_profile_get(const char* name, double* total_ms, int64_t* launches) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (!name) return 0;
+  auto it = g_prof.find(name);
+  if (it == g_prof.end()) {
+    if (total_ms) *total_ms = 0.0;
+    if (launches) *launches = 0;
+    return 0;
+  }
+  if (total_ms) *total_ms = it->second.first;
+  if (launches) *launches = it->second.second;
+  return 1;
+}
+
+int32_t mueller_profile_names(char* buf, size_t buflen) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  std::string all;
+  for (auto& kv : g_prof) all += kv.first + "\n";
+  if (buf && buflen) {
+    size_t n = std::min(buflen - 1, all.size());
+    memcpy(buf, all.data(), n);
+    buf[n] = 0;
+  }
+  return (int32_t)g_prof.size();
 }
 
 mueller_status mueller_sync(void* stream) {

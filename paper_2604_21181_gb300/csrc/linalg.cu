@@ -724,17 +724,17 @@ mueller_status op_matvec(const mueller_operator* op, const void* X, void* Y, int
   const int64_t N = 4 * m->nn;
   if (op->dtype == MUELLER_C128) {
     dim3 grid(nblk(N, 32), r);
-    gemv_c128_kernel<<<grid, 256, 0, s>>>(N, (const double2*)op->Z_dev, op->ldz, (const double2*)X,
-                                          (double2*)Y, N, N, r);
+    { Prof prof_("gemv_c128_kernel", s); gemv_c128_kernel<<<grid, 256, 0, s>>>(N, (const double2*)op->Z_dev, op->ldz, (const double2*)X,
+                                          (double2*)Y, N, N, r); }
     MU_CHECK_LAUNCH("gemv_c128_kernel");
   } else {
     dim3 grid(nblk(N, 16), r);
-    gemv_c64_kernel<double><<<grid, 256, 0, s>>>(N, (const float4*)op->Z_dev, op->ldz, X, Y, N, N, r);
+    { Prof prof_("gemv_c64_kernel<double>", s); gemv_c64_kernel<double><<<grid, 256, 0, s>>>(N, (const float4*)op->Z_dev, op->ldz, X, Y, N, N, r); }
     MU_CHECK_LAUNCH("gemv_c64_kernel<double>");
     dim3 g2(nblk(4 * m->nn, 128), r);
-    near_spmv_kernel<double2, double2><<<g2, 128, 0, s>>>(m->nn, m->near_rowptr, m->near_col,
+    { Prof prof_("near_spmv_kernel<double2, double2>", s); near_spmv_kernel<double2, double2><<<g2, 128, 0, s>>>(m->nn, m->near_rowptr, m->near_col,
                                                           (const double2*)op->near_dev,
-                                                          (const double2*)X, (double2*)Y, N, N, r);
+                                                          (const double2*)X, (double2*)Y, N, N, r); }
     MU_CHECK_LAUNCH("near_spmv_kernel");
   }
   return MUELLER_OK;
@@ -762,40 +762,40 @@ static mueller_status batched_lu_inverse(double2* A, int64_t d, int nb, const in
                                          int32_t* piv, int32_t* status, double2* inv,
                                          cudaStream_t s) {
   for (int k0 = 0; k0 < d; k0 += NBK) {
-    lu_panel_kernel<<<nb, 256, 0, s>>>(A, d, sz_dev, k0, piv, status);
+    { Prof prof_("lu_panel_kernel", s); lu_panel_kernel<<<nb, 256, 0, s>>>(A, d, sz_dev, k0, piv, status); }
     MU_CHECK_LAUNCH("lu_panel_kernel");
     const int64_t rest = d - (k0 + NBK);
     if (rest <= 0) continue;
     // U12 = L11^{-1} A12 (columns k0+NBK .. n)
     dim3 gt(nblk(rest, 128), nb);
-    trsm_tile_kernel<<<gt, 128, 0, s>>>(A, A, d, d, d * d, sz_dev, k0, NBK, k0 + NBK, -1, 0);
+    { Prof prof_("trsm_tile_kernel", s); trsm_tile_kernel<<<gt, 128, 0, s>>>(A, A, d, d, d * d, sz_dev, k0, NBK, k0 + NBK, -1, 0); }
     MU_CHECK_LAUNCH("trsm_tile_kernel");
     dim3 gg(nblk(rest, 64), nblk(rest, 64), nb);
-    gemm_update_kernel<<<gg, 256, 0, s>>>(A, A, A, d, d, d * d, sz_dev, k0, k0 + NBK, -1, k0 + NBK, -1);
+    { Prof prof_("gemm_update_kernel", s); gemm_update_kernel<<<gg, 256, 0, s>>>(A, A, A, d, d, d * d, sz_dev, k0, k0 + NBK, -1, k0 + NBK, -1); }
     MU_CHECK_LAUNCH("gemm_update_kernel");
   }
   if (!inv) return MUELLER_OK;
   // inv = U^{-1} L^{-1} P
-  perm_identity_kernel<<<dim3(nblk(d, 128), nb), 128, 0, s>>>(inv, d, sz_dev, piv);
+  { Prof prof_("perm_identity_kernel", s); perm_identity_kernel<<<dim3(nblk(d, 128), nb), 128, 0, s>>>(inv, d, sz_dev, piv); }
   MU_CHECK_LAUNCH("perm_identity_kernel");
   for (int k0 = 0; k0 < d; k0 += NBK) {  // forward: L (unit lower)
-    trsm_tile_kernel<<<dim3(nblk(d, 128), nb), 128, 0, s>>>(A, inv, d, d, d * d, sz_dev, k0, NBK, 0, -1, 0);
+    { Prof prof_("trsm_tile_kernel", s); trsm_tile_kernel<<<dim3(nblk(d, 128), nb), 128, 0, s>>>(A, inv, d, d, d * d, sz_dev, k0, NBK, 0, -1, 0); }
     MU_CHECK_LAUNCH("trsm_tile_kernel(L)");
     const int64_t below = d - (k0 + NBK);
     if (below > 0) {
       dim3 gg(nblk(d, 64), nblk(below, 64), nb);
-      gemm_update_kernel<<<gg, 256, 0, s>>>(A, inv, inv, d, d, d * d, sz_dev, k0, k0 + NBK, -1, 0, -1);
+      { Prof prof_("gemm_update_kernel", s); gemm_update_kernel<<<gg, 256, 0, s>>>(A, inv, inv, d, d, d * d, sz_dev, k0, k0 + NBK, -1, 0, -1); }
       MU_CHECK_LAUNCH("gemm_update_kernel(L)");
     }
   }
   const int64_t ntile = (d + NBK - 1) / NBK;
   for (int64_t t = ntile - 1; t >= 0; --t) {  // backward: U
     const int k0 = (int)(t * NBK);
-    trsm_tile_kernel<<<dim3(nblk(d, 128), nb), 128, 0, s>>>(A, inv, d, d, d * d, sz_dev, k0, NBK, 0, -1, 1);
+    { Prof prof_("trsm_tile_kernel", s); trsm_tile_kernel<<<dim3(nblk(d, 128), nb), 128, 0, s>>>(A, inv, d, d, d * d, sz_dev, k0, NBK, 0, -1, 1); }
     MU_CHECK_LAUNCH("trsm_tile_kernel(U)");
     if (k0 > 0) {
       dim3 gg(nblk(d, 64), nblk(k0, 64), nb);
-      gemm_update_kernel<<<gg, 256, 0, s>>>(A, inv, inv, d, d, d * d, sz_dev, k0, 0, k0, 0, -1);
+      { Prof prof_("gemm_update_kernel", s); gemm_update_kernel<<<gg, 256, 0, s>>>(A, inv, inv, d, d, d * d, sz_dev, k0, 0, k0, 0, -1); }
       MU_CHECK_LAUNCH("gemm_update_kernel(U)");
     }
   }
@@ -818,13 +818,13 @@ mueller_status precond_build(const mueller_operator* op, int64_t block, void* P,
   MU_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), s));
   dim3 g(nblk(L.d, 128), L.d, L.nb);
   if (op->dtype == MUELLER_C128) {
-    gather_blocks_kernel<MUELLER_C128><<<g, 128, 0, s>>>(op->Z_dev, op->ldz, L.H, L.B, L.d, sz_dev, A);
+    { Prof prof_("gather_blocks_kernel<MUELLER_C128>", s); gather_blocks_kernel<MUELLER_C128><<<g, 128, 0, s>>>(op->Z_dev, op->ldz, L.H, L.B, L.d, sz_dev, A); }
   } else {
-    gather_blocks_kernel<MUELLER_C64_NEAR64><<<g, 128, 0, s>>>(op->Z_dev, op->ldz, L.H, L.B, L.d, sz_dev, A);
+    { Prof prof_("gather_blocks_kernel<MUELLER_C64_NEAR64>", s); gather_blocks_kernel<MUELLER_C64_NEAR64><<<g, 128, 0, s>>>(op->Z_dev, op->ldz, L.H, L.B, L.d, sz_dev, A); }
     MU_CHECK_LAUNCH("gather_blocks_kernel");
-    gather_near_kernel<<<nblk(m->nn, 128), 128, 0, s>>>(m->nn, m->near_rowptr, m->near_col,
+    { Prof prof_("gather_near_kernel", s); gather_near_kernel<<<nblk(m->nn, 128), 128, 0, s>>>(m->nn, m->near_rowptr, m->near_col,
                                                         (const double2*)op->near_dev, L.B, L.d,
-                                                        sz_dev, A);
+                                                        sz_dev, A); }
   }
   MU_CHECK_LAUNCH("gather kernels");
   mueller_status st = batched_lu_inverse(A, L.d, (int)L.nb, sz_dev, piv, status, inv, s);
@@ -919,11 +919,11 @@ mueller_status inner_matvec(const InnerOp& I, const VT* x, VT* y, cudaStream_t s
   if constexpr (sizeof(VT) == 16) {
     return op_matvec(I.op, x, y, 1, nullptr, 0, s);
   } else {
-    gemv_c64_kernel<float><<<dim3(nblk(N, 16), 1), 256, 0, s>>>(N, (const float4*)I.op->Z_dev,
-                                                                I.op->ldz, x, y, N, N, 1);
+    { Prof prof_("gemv_c64_kernel<float>", s); gemv_c64_kernel<float><<<dim3(nblk(N, 16), 1), 256, 0, s>>>(N, (const float4*)I.op->Z_dev,
+                                                                I.op->ldz, x, y, N, N, 1); }
     MU_CHECK_LAUNCH("gemv_c64_kernel<float>");
-    near_spmv_kernel<float2, float2><<<dim3(nblk(4 * m->nn, 128), 1), 128, 0, s>>>(
-        m->nn, m->near_rowptr, m->near_col, I.near32, x, y, N, N, 1);
+    { Prof prof_("near_spmv_kernel<float2, float2>", s); near_spmv_kernel<float2, float2><<<dim3(nblk(4 * m->nn, 128), 1), 128, 0, s>>>(
+        m->nn, m->near_rowptr, m->near_col, I.near32, x, y, N, N, 1); }
     MU_CHECK_LAUNCH("near_spmv_kernel<float>");
     return MUELLER_OK;
   }
@@ -938,10 +938,10 @@ mueller_status inner_precond(const InnerOp& I, const VT* v, VT* z, cudaStream_t 
   }
   dim3 g(nblk(I.L.d, 8), I.L.nb);
   if constexpr (sizeof(VT) == 16) {
-    mbj_apply_kernel<double2, double2><<<g, 256, 0, s>>>((const double2*)I.op->precond_dev, I.L.d,
-                                                        I.sz_dev, I.L.B, I.L.H, v, z);
+    { Prof prof_("mbj_apply_kernel<double2, double2>", s); mbj_apply_kernel<double2, double2><<<g, 256, 0, s>>>((const double2*)I.op->precond_dev, I.L.d,
+                                                        I.sz_dev, I.L.B, I.L.H, v, z); }
   } else {
-    mbj_apply_kernel<float2, float2><<<g, 256, 0, s>>>(I.inv32, I.L.d, I.sz_dev, I.L.B, I.L.H, v, z);
+    { Prof prof_("mbj_apply_kernel<float2, float2>", s); mbj_apply_kernel<float2, float2><<<g, 256, 0, s>>>(I.inv32, I.L.d, I.sz_dev, I.L.B, I.L.H, v, z); }
   }
   MU_CHECK_LAUNCH("mbj_apply_kernel");
   return MUELLER_OK;
@@ -969,9 +969,9 @@ mueller_status gmres(const InnerOp& I, GmresWork& W, const VT* b, VT* x, double 
   };
   mueller_status st = MUELLER_OK;
   auto norm_into = [&](const VT* v, double* dst) -> mueller_status {
-    nrm2_kernel<VT><<<G, 256, 0, s>>>(v, N, W.npart, G);
+    { Prof prof_("nrm2_kernel<VT>", s); nrm2_kernel<VT><<<G, 256, 0, s>>>(v, N, W.npart, G); }
     MU_CHECK_LAUNCH("nrm2_kernel");
-    normalize_kernel<VT><<<1, 1, 0, s>>>(v, 0, W.npart, G, nullptr, dst);
+    { Prof prof_("normalize_kernel<VT>", s); normalize_kernel<VT><<<1, 1, 0, s>>>(v, 0, W.npart, G, nullptr, dst); }
     MU_CHECK_LAUNCH("normalize_kernel");
     return MUELLER_OK;
   };
@@ -991,9 +991,9 @@ mueller_status gmres(const InnerOp& I, GmresWork& W, const VT* b, VT* x, double 
     if ((st = inner_matvec<VT>(I, x, w, s))) goto done;
     {
       // w = b - w
-      axpy_kernel<VT, VT><<<nblk(N, 256), 256, 0, s>>>(w, w, N, -2.0);  // w := -w
+      { Prof prof_("axpy_kernel<VT, VT>", s); axpy_kernel<VT, VT><<<nblk(N, 256), 256, 0, s>>>(w, w, N, -2.0); }  // w := -w
       MU_CHECK_LAUNCH("axpy");
-      axpy_kernel<VT, VT><<<nblk(N, 256), 256, 0, s>>>(w, b, N, 1.0);
+      { Prof prof_("axpy_kernel<VT, VT>", s); axpy_kernel<VT, VT><<<nblk(N, 256), 256, 0, s>>>(w, b, N, 1.0); }
       MU_CHECK_LAUNCH("axpy");
     }
     if ((st = norm_into(w, W.scal + 2))) goto done;
@@ -1002,9 +1002,9 @@ mueller_status gmres(const InnerOp& I, GmresWork& W, const VT* b, VT* x, double 
     relres = beta / bn;
     if (relres <= tol || iters >= maxit) goto done;
     // V0 = w / beta, g = beta e1
-    normalize_kernel<VT><<<nblk(N, 256), 256, 0, s>>>(w, N, W.npart, G, V, W.scal + 2);
+    { Prof prof_("normalize_kernel<VT>", s); normalize_kernel<VT><<<nblk(N, 256), 256, 0, s>>>(w, N, W.npart, G, V, W.scal + 2); }
     MU_CHECK_LAUNCH("normalize");
-    set_first_kernel<VT><<<1, 1, 0, s>>>(W.g, m, W.scal + 2);
+    { Prof prof_("set_first_kernel<VT>", s); set_first_kernel<VT><<<1, 1, 0, s>>>(W.g, m, W.scal + 2); }
     MU_CUDA(cudaMemsetAsync(W.hacc, 0, (m + 2) * sizeof(double2), s));
     int k = 0;
     for (int j = 0; j < m && iters < maxit; ++j) {
@@ -1012,17 +1012,17 @@ mueller_status gmres(const InnerOp& I, GmresWork& W, const VT* b, VT* x, double 
       if ((st = inner_precond<VT>(I, vj, z, s))) goto done;
       if ((st = inner_matvec<VT>(I, z, w, s))) goto done;
       for (int pass = 0; pass < 2; ++pass) {
-        dots_kernel<VT><<<dim3(G, j + 1), 256, 0, s>>>(V, N, j + 1, w, W.part, G);
+        { Prof prof_("dots_kernel<VT>", s); dots_kernel<VT><<<dim3(G, j + 1), 256, 0, s>>>(V, N, j + 1, w, W.part, G); }
         MU_CHECK_LAUNCH("dots_kernel");
-        orth_update_kernel<VT><<<nblk(N, 256), 256, 0, s>>>(V, N, j + 1, W.part, G, w, W.hacc);
+        { Prof prof_("orth_update_kernel<VT>", s); orth_update_kernel<VT><<<nblk(N, 256), 256, 0, s>>>(V, N, j + 1, W.part, G, w, W.hacc); }
         MU_CHECK_LAUNCH("orth_update_kernel");
       }
-      nrm2_kernel<VT><<<G, 256, 0, s>>>(w, N, W.npart, G);
+      { Prof prof_("nrm2_kernel<VT>", s); nrm2_kernel<VT><<<G, 256, 0, s>>>(w, N, W.npart, G); }
       MU_CHECK_LAUNCH("nrm2");
-      normalize_kernel<VT><<<nblk(N, 256), 256, 0, s>>>(w, N, W.npart, G, V + (int64_t)(j + 1) * N,
-                                                        W.scal + 1);
+      { Prof prof_("normalize_kernel<VT>", s); normalize_kernel<VT><<<nblk(N, 256), 256, 0, s>>>(w, N, W.npart, G, V + (int64_t)(j + 1) * N,
+                                                        W.scal + 1); }
       MU_CHECK_LAUNCH("normalize");
-      givens_kernel<<<1, 1, 0, s>>>(j, m, W.hacc, W.scal + 1, W.Hm, W.cs, W.sn, W.g, W.scal);
+      { Prof prof_("givens_kernel", s); givens_kernel<<<1, 1, 0, s>>>(j, m, W.hacc, W.scal + 1, W.Hm, W.cs, W.sn, W.g, W.scal); }
       MU_CHECK_LAUNCH("givens_kernel");
       ++iters;
       k = j + 1;
@@ -1030,12 +1030,12 @@ mueller_status gmres(const InnerOp& I, GmresWork& W, const VT* b, VT* x, double 
       if ((st = read(W.scal, est))) goto done;
       if (est / bn <= tol || !(est == est)) break;
     }
-    backsub_kernel<<<1, 1, 0, s>>>(k, m, W.Hm, W.g, W.y);
+    { Prof prof_("backsub_kernel", s); backsub_kernel<<<1, 1, 0, s>>>(k, m, W.Hm, W.g, W.y); }
     MU_CHECK_LAUNCH("backsub_kernel");
-    combine_kernel<VT><<<nblk(N, 256), 256, 0, s>>>(V, N, k, W.y, u);
+    { Prof prof_("combine_kernel<VT>", s); combine_kernel<VT><<<nblk(N, 256), 256, 0, s>>>(V, N, k, W.y, u); }
     MU_CHECK_LAUNCH("combine_kernel");
     if ((st = inner_precond<VT>(I, u, z, s))) goto done;
-    axpy_kernel<VT, VT><<<nblk(N, 256), 256, 0, s>>>(x, z, N, 1.0);
+    { Prof prof_("axpy_kernel<VT, VT>", s); axpy_kernel<VT, VT><<<nblk(N, 256), 256, 0, s>>>(x, z, N, 1.0); }
     MU_CHECK_LAUNCH("axpy");
     ++restarts;
   }
@@ -1100,24 +1100,24 @@ mueller_status solve(const mueller_operator* op, const void* Bv, void* Xv, int r
     if (e != cudaSuccess) st = cuda_fail(e, "dense LU setup");
     if (!st) st = batched_lu_inverse(A, N, 1, sz_dev, piv, status, nullptr, s);
     if (!st) {
-      transpose_rhs_kernel<<<nblk((int64_t)N * r, 256), 256, 0, s>>>(B, T, N, r, 0);
-      permute_rows_kernel<<<nblk(r, 64), 64, 0, s>>>(T, N, r, piv);
+      { Prof prof_("transpose_rhs_kernel", s); transpose_rhs_kernel<<<nblk((int64_t)N * r, 256), 256, 0, s>>>(B, T, N, r, 0); }
+      { Prof prof_("permute_rows_kernel", s); permute_rows_kernel<<<nblk(r, 64), 64, 0, s>>>(T, N, r, piv); }
       for (int k0 = 0; k0 < N; k0 += NBK) {
-        trsm_tile_kernel<<<dim3(nblk(r, 128), 1), 128, 0, s>>>(A, T, N, r, 0, sz_dev, k0, NBK, 0, r, 0);
+        { Prof prof_("trsm_tile_kernel", s); trsm_tile_kernel<<<dim3(nblk(r, 128), 1), 128, 0, s>>>(A, T, N, r, 0, sz_dev, k0, NBK, 0, r, 0); }
         const int64_t below = N - (k0 + NBK);
         if (below > 0)
-          gemm_update_kernel<<<dim3(nblk(r, 64), nblk(below, 64), 1), 256, 0, s>>>(
-              A, T, T, N, r, 0, sz_dev, k0, k0 + NBK, -1, 0, r);
+          { Prof prof_("gemm_update_kernel", s); gemm_update_kernel<<<dim3(nblk(r, 64), nblk(below, 64), 1), 256, 0, s>>>(
+              A, T, T, N, r, 0, sz_dev, k0, k0 + NBK, -1, 0, r); }
       }
       const int64_t ntile = (N + NBK - 1) / NBK;
       for (int64_t t = ntile - 1; t >= 0; --t) {
         const int k0 = (int)(t * NBK);
-        trsm_tile_kernel<<<dim3(nblk(r, 128), 1), 128, 0, s>>>(A, T, N, r, 0, sz_dev, k0, NBK, 0, r, 1);
+        { Prof prof_("trsm_tile_kernel", s); trsm_tile_kernel<<<dim3(nblk(r, 128), 1), 128, 0, s>>>(A, T, N, r, 0, sz_dev, k0, NBK, 0, r, 1); }
         if (k0 > 0)
-          gemm_update_kernel<<<dim3(nblk(r, 64), nblk(k0, 64), 1), 256, 0, s>>>(
-              A, T, T, N, r, 0, sz_dev, k0, 0, k0, 0, r);
+          { Prof prof_("gemm_update_kernel", s); gemm_update_kernel<<<dim3(nblk(r, 64), nblk(k0, 64), 1), 256, 0, s>>>(
+              A, T, T, N, r, 0, sz_dev, k0, 0, k0, 0, r); }
       }
-      transpose_rhs_kernel<<<nblk((int64_t)N * r, 256), 256, 0, s>>>(T, X, N, r, 1);
+      { Prof prof_("transpose_rhs_kernel", s); transpose_rhs_kernel<<<nblk((int64_t)N * r, 256), 256, 0, s>>>(T, X, N, r, 1); }
       e = cudaGetLastError();
       if (e != cudaSuccess) st = cuda_fail(e, "dense LU solve");
     }
@@ -1184,13 +1184,13 @@ mueller_status solve(const mueller_operator* op, const void* Bv, void* Xv, int r
     float2* inv32 = nullptr;
     if (op->dtype == MUELLER_C64_NEAR64) {
       near32 = (float2*)take((size_t)nnzb * 16 * 8);
-      c128_to_c64_kernel<<<nblk(nnzb * 16, 256), 256, 0, s>>>((const double2*)op->near_dev, near32, nnzb * 16);
+      { Prof prof_("c128_to_c64_kernel", s); c128_to_c64_kernel<<<nblk(nnzb * 16, 256), 256, 0, s>>>((const double2*)op->near_dev, near32, nnzb * 16); }
       MU_CHECK_LAUNCH("c128_to_c64");
     }
     if (op->precond_dev) {
       const int64_t cnt = (int64_t)I.L.nb * I.L.d * I.L.d;
       inv32 = (float2*)take(cnt * 8);
-      c128_to_c64_kernel<<<nblk(cnt, 256), 256, 0, s>>>((const double2*)op->precond_dev, inv32, cnt);
+      { Prof prof_("c128_to_c64_kernel", s); c128_to_c64_kernel<<<nblk(cnt, 256), 256, 0, s>>>((const double2*)op->precond_dev, inv32, cnt); }
       MU_CHECK_LAUNCH("c128_to_c64");
     }
     I.near32 = near32;
@@ -1207,8 +1207,8 @@ mueller_status solve(const mueller_operator* op, const void* Bv, void* Xv, int r
       if (!o->warm_start) MU_CUDA(cudaMemsetAsync(x, 0, N * 16, s));
       double bn = 0, rel = 1.0;
       int it_left = o->maxit;
-      nrm2_kernel<double2><<<W.G, 256, 0, s>>>(b, N, W.npart, W.G);
-      normalize_kernel<double2><<<1, 1, 0, s>>>(b, 0, W.npart, W.G, nullptr, W.scal + 4);
+      { Prof prof_("nrm2_kernel<double2>", s); nrm2_kernel<double2><<<W.G, 256, 0, s>>>(b, N, W.npart, W.G); }
+      { Prof prof_("normalize_kernel<double2>", s); normalize_kernel<double2><<<1, 1, 0, s>>>(b, 0, W.npart, W.G, nullptr, W.scal + 4); }
       MU_CUDA(cudaMemcpyAsync(hs, W.scal + 4, 8, cudaMemcpyDeviceToHost, s));
       MU_CUDA(cudaStreamSynchronize(s));
       bn = hs[0];
@@ -1216,16 +1216,16 @@ mueller_status solve(const mueller_operator* op, const void* Bv, void* Xv, int r
         // r = b - A x in FP64 (complex64 storage, FP64 arithmetic)
         st = op_matvec(op, x, y64, 1, nullptr, 0, s);
         if (st) break;
-        residual_kernel<<<nblk(N, 256), 256, 0, s>>>(b, y64, r64, N);
-        nrm2_kernel<double2><<<W.G, 256, 0, s>>>(r64, N, W.npart, W.G);
-        normalize_kernel<double2><<<1, 1, 0, s>>>(r64, 0, W.npart, W.G, nullptr, W.scal + 5);
+        { Prof prof_("residual_kernel", s); residual_kernel<<<nblk(N, 256), 256, 0, s>>>(b, y64, r64, N); }
+        { Prof prof_("nrm2_kernel<double2>", s); nrm2_kernel<double2><<<W.G, 256, 0, s>>>(r64, N, W.npart, W.G); }
+        { Prof prof_("normalize_kernel<double2>", s); normalize_kernel<double2><<<1, 1, 0, s>>>(r64, 0, W.npart, W.G, nullptr, W.scal + 5); }
         MU_CUDA(cudaMemcpyAsync(hs, W.scal + 5, 8, cudaMemcpyDeviceToHost, s));
         MU_CUDA(cudaStreamSynchronize(s));
         const double rn = hs[0];
         rel = bn > 0 ? rn / bn : 0.0;
         if (rel <= o->tol || it_left <= 0 || ref == maxref) break;
         // inner: A d = r / ||r|| in complex64
-        scale_copy_kernel<double2, float2><<<nblk(N, 256), 256, 0, s>>>(r64, rhs32, N, W.scal + 5);
+        { Prof prof_("scale_copy_kernel<double2, float2>", s); scale_copy_kernel<double2, float2><<<nblk(N, 256), 256, 0, s>>>(r64, rhs32, N, W.scal + 5); }
         MU_CUDA(cudaMemsetAsync(d32, 0, N * 8, s));
         int it = 0, rs = 0;
         double irel = 0;
@@ -1237,7 +1237,7 @@ mueller_status solve(const mueller_operator* op, const void* Bv, void* Xv, int r
         info->restarts += rs;
         info->refinements += 1;
         // x += ||r|| d
-        axpy_kernel<double2, float2><<<nblk(N, 256), 256, 0, s>>>(x, d32, N, rn);
+        { Prof prof_("axpy_kernel<double2, float2>", s); axpy_kernel<double2, float2><<<nblk(N, 256), 256, 0, s>>>(x, d32, N, rn); }
         MU_CHECK_LAUNCH("axpy");
       }
       info->relres = std::max(info->relres, rel);
