@@ -266,6 +266,39 @@ mueller_status mueller_far_field(mueller_mesh* mesh, const mueller_params* param
                                  int32_t n_theta, int32_t n_phi, void* stream);
 
 /*
+ * mueller_far_field_noalloc -- the far field and cross sections of
+ * mueller_far_field, computed without allocating any device memory.  (The
+ * paper has no counterpart: this is an interface for callers that cannot
+ * allocate, such as a framework that routes all device memory through its
+ * own pool, or a service that reserves its memory at start-up and forbids
+ * allocation later.)
+ * Same arguments, outputs and errors as mueller_far_field, and:
+ *   - scratch is a fixed MUELLER_FAR_FIELD_NOALLOC_SCRATCH_BYTES (16 MiB)
+ *     array in device memory, held by every GPU that loads the library until
+ *     the process exits.  A request that needs more (it grows with
+ *     r * (n_tri * q_regular + n_theta * n_phi + n_dir)) is rejected with
+ *     INVALID_ARG and a message naming the size; roughly 16 right-hand sides
+ *     of the level-3 sphere with the default 48 x 96 sphere rule fit.
+ *   - the mesh must already hold the point geometry for params (call
+ *     mueller_assemble or mueller_far_field with the same params first), else
+ *     STATE: this call never creates it.
+ *   - the first call on a device looks up the device address of the scratch
+ *     array (cudaGetSymbolAddress); make that first call before any stream
+ *     capture.
+ *   - every call uses the same scratch: calls whose GPU work overlaps (on
+ *     different streams or host threads) race and give wrong results; the
+ *     call synchronises its stream before returning, so calls issued one
+ *     after another on one thread are safe.  Nothing in the scratch needs to
+ *     start at zero: each region is fully written before it is read.
+ */
+#define MUELLER_FAR_FIELD_NOALLOC_SCRATCH_BYTES (16u << 20)
+mueller_status mueller_far_field_noalloc(mueller_mesh* mesh, const mueller_params* params,
+                                         const void* X_dev, int32_t r, const double* inc,
+                                         const double* dirs, int64_t n_dir, void* F_dev,
+                                         double* xs, int32_t n_theta, int32_t n_phi,
+                                         void* stream);
+
+/*
  * Launch accounting and per-kernel timing (no counterpart in the paper: a
  * measurement aid).  Every kernel launch of the library is counted.  With
  * profiling enabled, each launch is bracketed by CUDA events on its own

@@ -73,7 +73,7 @@ EXPORTS = [
     "mueller_solve", "mueller_solve_workspace_bytes", "mueller_matvec",
     "mueller_matvec_workspace_bytes", "mueller_far_field", "mueller_sync",
     "mueller_profile_enable", "mueller_profile_reset", "mueller_launch_count",
-    "mueller_profile_get", "mueller_profile_names",
+    "mueller_profile_get", "mueller_profile_names", "mueller_far_field_noalloc",
 ]
 
 _lib = None
@@ -117,6 +117,8 @@ def load_library(build_if_missing: bool = True):
         "mueller_launch_count": (i64, []),
         "mueller_profile_get": (i32, [C.c_char_p, dp, C.POINTER(i64)]),
         "mueller_profile_names": (i32, [C.c_char_p, C.c_size_t]),
+        "mueller_far_field_noalloc": (C.c_int, [vp, C.POINTER(CParams), vp, i32, dp, dp, i64, vp,
+                                                dp, i32, i32, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

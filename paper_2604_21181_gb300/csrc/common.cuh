@@ -136,6 +136,9 @@ size_t solve_work(const mueller_operator* op, int r, const mueller_solver_opts* 
 mueller_status far_field(mueller_mesh* m, const PhysConsts& P, int Q, const void* X, int r,
                          const double* inc, const double* dirs, int64_t ndir, void* F,
                          double* xs, int n_theta, int n_phi, cudaStream_t s);
+mueller_status far_field_noalloc(mueller_mesh* m, const PhysConsts& P, int Q, const void* X, int r,
+                                 const double* inc, const double* dirs, int64_t ndir, void* F,
+                                 double* xs, int n_theta, int n_phi, cudaStream_t s);
 
 PhysConsts make_phys(const mueller_params* p);
 }  // namespace mu

@@ -9,6 +9,7 @@
 // (j = n x H and j_m = -n x E, Sec. 2.1, give the Poynting flux).
 #include <math.h>
 
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -263,6 +264,147 @@ mueller_status far_field(mueller_mesh* m, const PhysConsts& P, int Q, const void
   }
   cudaFreeAsync(buf, s);
   return st;
+}
+
+}  // namespace mu
+
+// ---------------------------------------------------------------------------
+// Allocation-free far field.  Some callers must not allocate device memory
+// at this point of their program: a framework that owns all device memory
+// through its own pool (a raw allocation outside the pool can fail or
+// fragment it), or a service that reserves its memory at start-up and
+// forbids allocation afterwards to keep latency and footprint predictable.
+// mueller_far_field_noalloc serves them: its scratch is a fixed array in
+// device memory that exists for as long as the library is loaded, on every
+// GPU that loads it.  The caller still provides the inputs and outputs.
+// ---------------------------------------------------------------------------
+namespace mu {
+namespace {
+
+constexpr size_t kFarFieldScratchBytes = size_t(16) << 20;  // 16 MiB
+static __device__ __align__(256) unsigned char g_far_scratch[kFarFieldScratchBytes];
+
+// Device address of g_far_scratch on each device.  In host code the symbol
+// name is only a stand-in, so the address is looked up once per device, with
+// that device current, and then handed to the kernels.
+constexpr int kMaxDevices = 64;
+static std::mutex g_far_scratch_mu;
+static void* g_far_scratch_ptr[kMaxDevices] = {};
+
+mueller_status far_scratch_address(void** out) {
+  int dev = 0;
+  MU_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("device ordinal beyond the supported range of the allocation-free far field");
+    return MUELLER_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lk(g_far_scratch_mu);
+  if (!g_far_scratch_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_far_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(far-field scratch)");
+    g_far_scratch_ptr[dev] = p;
+  }
+  *out = g_far_scratch_ptr[dev];
+  return MUELLER_OK;
+}
+
+}  // namespace
+
+mueller_status far_field_noalloc(mueller_mesh* m, const PhysConsts& P, int Q, const void* X, int r,
+                                 const double* inc, const double* dirs, int64_t ndir, void* F,
+                                 double* xs, int n_theta, int n_phi, cudaStream_t s) {
+  TriangleRule rule;
+  if (!triangle_rule(Q, rule)) return MUELLER_ERR_INVALID_ARG;
+  const int64_t np = m->nt * Q, N = 4 * m->nn;
+  std::vector<double> gth, wth;
+  gauss_legendre_unit(n_theta, gth, wth);
+  const int64_t nsph = (int64_t)n_theta * n_phi;
+  const int64_t nd = 1 + nsph + ndir;
+  const unsigned nblk_pts = (unsigned)((np + 255) / 256);
+  size_t off = 0;
+  auto al = [&](size_t b) {
+    size_t o = off;
+    off += (b + 255) & ~size_t(255);
+    return o;
+  };
+  const size_t o_rec = al((size_t)r * np * 6 * 16);
+  const size_t o_dirs = al((size_t)r * nd * 3 * 8);
+  const size_t o_F = al((size_t)r * nd * 3 * 16);
+  const size_t o_wth = al(wth.size() * 8);
+  const size_t o_inc = al((size_t)r * 6 * 8);
+  const size_t o_phi = al(sizeof(double) * MAX_Q * 6);
+  const size_t o_cab = al((size_t)r * nblk_pts * 8);
+  const size_t o_xs = al((size_t)r * 3 * 8);
+  if (off > kFarFieldScratchBytes) {
+    set_error("far field needs " + std::to_string(off) + " bytes of scratch, more than the " +
+              std::to_string(kFarFieldScratchBytes) +
+              " bytes of the allocation-free variant: use fewer right-hand sides, directions or "
+              "sphere points, or mueller_far_field");
+    return MUELLER_ERR_INVALID_ARG;
+  }
+  char* buf = nullptr;
+  mueller_status st = far_scratch_address((void**)&buf);
+  if (st) return st;
+  std::vector<double> hd((size_t)r * nd * 3);
+  for (int sidx = 0; sidx < r; ++sidx) {
+    double* o = hd.data() + (size_t)sidx * nd * 3;
+    o[0] = inc[6 * sidx];
+    o[1] = inc[6 * sidx + 1];
+    o[2] = inc[6 * sidx + 2];
+    for (int it = 0; it < n_theta; ++it) {
+      const double ct = 2.0 * gth[it] - 1.0, st2 = sqrt(fmax(0.0, 1.0 - ct * ct));
+      for (int ip = 0; ip < n_phi; ++ip) {
+        const double ph = 2.0 * 3.14159265358979323846 * ip / n_phi;
+        double* dd = o + 3 * (1 + (int64_t)it * n_phi + ip);
+        dd[0] = st2 * cos(ph);
+        dd[1] = st2 * sin(ph);
+        dd[2] = ct;
+      }
+    }
+    for (int64_t d = 0; d < ndir; ++d)
+      for (int a = 0; a < 3; ++a) o[3 * (1 + nsph + d) + a] = dirs[3 * d + a];
+  }
+  double phi[MAX_Q * 6];
+  for (int p = 0; p < Q; ++p) {
+    const double l0 = 1.0 - rule.xi[p] - rule.eta[p], l1 = rule.xi[p], l2 = rule.eta[p];
+    const double Nv[6] = {l0 * (2 * l0 - 1), l1 * (2 * l1 - 1), l2 * (2 * l2 - 1),
+                          4 * l0 * l1,       4 * l1 * l2,       4 * l2 * l0};
+    for (int k = 0; k < 6; ++k) phi[p * 6 + k] = Nv[k];
+  }
+  double2* rec = (double2*)(buf + o_rec);
+  double* ddirs = (double*)(buf + o_dirs);
+  double2* Fall = (double2*)(buf + o_F);
+  double* dwth = (double*)(buf + o_wth);
+  double* dinc = (double*)(buf + o_inc);
+  double* dphi = (double*)(buf + o_phi);
+  double* cab = (double*)(buf + o_cab);
+  double* dxs = (double*)(buf + o_xs);
+  // every scratch region is overwritten before it is read (currents, far
+  // fields, per-block partials, cross sections): nothing needs clearing
+  cudaError_t e = cudaMemcpyAsync(ddirs, hd.data(), hd.size() * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dwth, wth.data(), wth.size() * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dinc, inc, (size_t)r * 6 * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dphi, phi, sizeof(double) * Q * 6, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e, "far-field (allocation-free) setup");
+  { Prof prof_("currents_kernel", s); currents_kernel<<<dim3(nblk_pts, r), 256, 0, s>>>(m->nt, Q, m->qd64, m->T, (const double2*)X, r, N, dphi, rec, cab); }
+  for (int sidx = 0; sidx < r; ++sidx) {
+    Prof prof_("far_kernel", s);
+    far_kernel<<<dim3((unsigned)nd, 1), 256, 0, s>>>(np, m->qd64, rec + (size_t)sidx * np * 6,
+                                                     ddirs + (size_t)sidx * nd * 3, nd, P.ka,
+                                                     Fall + (size_t)sidx * nd * 3);
+  }
+  { Prof prof_("xs_kernel", s); xs_kernel<<<r, 256, 0, s>>>(Fall, nd, n_theta, n_phi, dwth, dinc, P.ka, cab, (int)nblk_pts, dxs); }
+  if (ndir > 0) {
+    Prof prof_("copy_user_dirs_kernel", s);
+    copy_user_dirs_kernel<<<(unsigned)(((int64_t)r * ndir * 3 + 255) / 256), 256, 0, s>>>(
+        Fall, nd, 1 + nsph, ndir, r, (double2*)F);
+  }
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(xs, dxs, (size_t)r * 3 * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "far field (allocation-free)");
+  return MUELLER_OK;
 }
 
 }  // namespace mu

@@ -606,6 +606,25 @@ int32_t mueller_profile_names(char* buf, size_t buflen) {
   return (int32_t)g_prof.size();
 }
 
+mueller_status mueller_far_field_noalloc(mueller_mesh* m, const mueller_params* p,
+                                         const void* X, int32_t r, const double* inc,
+                                         const double* dirs, int64_t ndir, void* F, double* xs,
+                                         int32_t n_theta, int32_t n_phi, void* stream) {
+  if (!m || !X || !inc || !xs) return fail(MUELLER_ERR_INVALID_ARG, "NULL argument");
+  mueller_status st = check_params(p);
+  if (st) return st;
+  if (r < 1 || ndir < 0 || (ndir > 0 && (!dirs || !F))) return fail(MUELLER_ERR_INVALID_ARG, "bad r/n_dir");
+  if (n_theta < 2 || n_phi < 3 || n_theta > 512 || n_phi > 1024)
+    return fail(MUELLER_ERR_INVALID_ARG, "n_theta in 2..512, n_phi in 3..1024");
+  // the point geometry is allocated by mueller_assemble / mueller_far_field;
+  // this variant never allocates, so it must already exist for the rule
+  if (!m->has_frame || p->frame_rule != m->frame_rule || m->qd_q != p->q_regular)
+    return fail(MUELLER_ERR_STATE, "call mueller_assemble (or mueller_far_field) with these "
+                                   "params on this mesh first");
+  return far_field_noalloc(m, make_phys(p), p->q_regular, X, r, inc, dirs, ndir, F, xs, n_theta,
+                           n_phi, (cudaStream_t)stream);
+}
+
 mueller_status mueller_sync(void* stream) {
   MU_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
   return MUELLER_OK;
