@@ -118,19 +118,20 @@ class ClockSampler:
 def touching_flops(n_tri: int, n_touch: int, ns: int, q: int) -> float:
     """FP64 flops of one touching_kernel launch (all touching pairs).
 
-    Per Sauter-Schwab point: two point geometries (P2 map, derivatives,
-    interpolated frame, projection, Gram-Schmidt: ~300 flops each), R and its
-    direction (13), the 8 singular geometric kernels (~137), staging of the
-    48 weighted trial values (96) and the 288 multiply-adds of the
-    contraction (576): 1433 flops.  Per pair, the remainder kappa - kappa^s
-    on the Q x Q rule (~900 flops per point pair) and its 6 x 6 x 12
-    contraction (2 * 432 * Q * 2 flops)."""
+    The Sauter-Schwab points are processed in groups of ns that share one
+    side.  Per point: the other side's point geometry (P2 map, derivatives,
+    interpolated frame, projection, Gram-Schmidt: ~300 flops), R and its
+    direction (13), the 8 singular geometric kernels (~137) and the 48
+    weighted multiply-adds (96): 546 flops.  Per group: the shared point's
+    geometry (300) and the 6 x 48 contraction (576).  Per pair, the
+    remainder kappa - kappa^s on the Q x Q rule (~900 flops per point pair)
+    and its 6 x 6 x 12 contraction (2 * 432 * Q * 2 flops)."""
     n_coinc = n_tri
     n_edge = 3 * n_tri
     n_vert = n_touch - n_coinc - n_edge
-    pts = (6 * n_coinc + 5 * n_edge + 2 * n_vert) * ns ** 4
+    groups = (6 * n_coinc + 5 * n_edge + 2 * n_vert) * ns ** 3
     per_pair = q * q * 900 + 2 * 432 * q * 2
-    return pts * 1433.0 + n_touch * per_pair
+    return groups * ns * 546.0 + groups * 876.0 + n_touch * per_pair
 
 
 def regular_flops(n_tri: int, n_touch: int, q: int) -> float:

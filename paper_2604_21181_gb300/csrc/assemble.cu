@@ -211,6 +211,60 @@ __global__ void __launch_bounds__(128) regular_kernel(int64_t nt, const R* __res
 // ------------------------------------------------------- touching pairs
 constexpr int TT = 96;  // threads per touching pair (= SSQ points per batch)
 
+// One Sauter-Schwab group: the ns points of region 'reg' at Gauss indices
+// (a, b, c, 0..ns-1).  The side that does not depend on eta3 (x if SHX) is
+// evaluated once; U receives its 6 shape values and V the 6 x 8 sums over the
+// group of  W N_k(other) g_c  (g: the 8 singular geometric kernels).
+template <bool SHX>
+__device__ __forceinline__ void ssq_group(int cls, int reg, int a, int b, int c, int ns, int px,
+                                          int py, const d3 (*Xn)[6], const d3 (*T1)[6],
+                                          const d3 (*T2)[6], double* U, double* V) {
+  double xu, xv, yu, yv, w, xi, eta;
+  ss_point_idx(cls, reg, a, b, c, 0, c_gl, c_glw, xu, xv, yu, yv, w);
+  if (SHX)
+    to_canonical(px, xu, xv, xi, eta);
+  else
+    to_canonical(py, yu, yv, xi, eta);
+  PointGeo gs;
+  point_geo(Xn[SHX ? 0 : 1], T1[SHX ? 0 : 1], T2[SHX ? 0 : 1], xi, eta, gs);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) U[i] = gs.N[i];
+#pragma unroll
+  for (int k = 0; k < 48; ++k) V[k] = 0.0;
+  for (int d = 0; d < ns; ++d) {
+    ss_point_idx(cls, reg, a, b, c, d, c_gl, c_glw, xu, xv, yu, yv, w);
+    if (SHX)
+      to_canonical(py, yu, yv, xi, eta);
+    else
+      to_canonical(px, xu, xv, xi, eta);
+    PointGeo go;
+    point_geo(Xn[SHX ? 1 : 0], T1[SHX ? 1 : 0], T2[SHX ? 1 : 0], xi, eta, go);
+    const PointGeo& gx = SHX ? gs : go;
+    const PointGeo& gy = SHX ? go : gs;
+    const d3 Rv = sub(gx.x, gy.x);
+    const double r = sqrt(dot(Rv, Rv));
+    const double ir = 1.0 / r;
+    const d3 h = scl(ir, Rv);
+    const double W = w * gx.J * gy.J;
+    const double nR = dot(gx.n, h);
+    const d3 sx[2] = {gx.s1, gx.s2}, tx[2] = {gx.t1, gx.t2}, ty[2] = {gy.t1, gy.t2};
+    double g[8];
+#pragma unroll
+    for (int al = 0; al < 2; ++al)
+#pragma unroll
+      for (int be = 0; be < 2; ++be) {
+        g[2 * al + be] = (dot(sx[al], ty[be]) + dot(sx[al], h) * dot(h, ty[be])) * ir;
+        g[4 + 2 * al + be] = (dot(tx[al], ty[be]) * nR - dot(tx[al], h) * dot(gx.n, ty[be])) * ir * ir;
+      }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const double wn = W * go.N[k];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) V[k * 8 + q] = fma(wn, g[q], V[k * 8 + q]);
+    }
+  }
+}
+
 template <int Q>
 __global__ void __launch_bounds__(TT) touching_kernel(
     int64_t n_touch, const TouchPair* __restrict__ tp, const double* __restrict__ X,
@@ -220,6 +274,7 @@ __global__ void __launch_bounds__(TT) touching_kernel(
     double* __restrict__ near, const int32_t* __restrict__ tp_slot) {
   __shared__ d3 sXn[2][6], sT1[2][6], sT2[2][6];
   __shared__ double sG[6 * 48];
+  __shared__ int sFlag[TT];
   // staging of the SSQ points (sU, sV), reused afterwards for the remainder
   // point pairs (sK, Q*Q*24 <= TT*54 doubles)
   __shared__ double sbuf[TT * 54];
@@ -243,54 +298,52 @@ __global__ void __launch_bounds__(TT) touching_kernel(
   __syncthreads();
   const int px = P.perm & 0x3f, py = (P.perm >> 8) & 0x3f;
   const int nreg = P.cls == 3 ? 6 : (P.cls == 2 ? 5 : 2);
-  const int64_t npts = (int64_t)nreg * ns * ns * ns * ns;
-  // ---- singular parts by Sauter-Schwab (8 real geometric integrals)
+  // ---- singular parts by Sauter-Schwab (8 real geometric integrals).
+  // Work unit: a group of ns points that differ only in eta3, so that one
+  // side (x or y, ss_shared_x) is common to the group: its geometry is
+  // evaluated once and the 48 trial-side values are summed over the group
+  // before the 6 x 48 contraction (5x fewer multiply-adds).
+  const int ngroups = nreg * ns * ns * ns;
+  const int ns3 = ns * ns * ns;
   double acc[3] = {0.0, 0.0, 0.0};
-  for (int64_t base = 0; base < npts; base += TT) {
-    const int64_t pt = base + tid;
-    if (pt < npts) {
-      double xu, xv, yu, yv, w, xi, eta, yxi, yeta;
-      ss_point(P.cls, ns, pt, c_gl, c_glw, xu, xv, yu, yv, w);
-      to_canonical(px, xu, xv, xi, eta);
-      to_canonical(py, yu, yv, yxi, yeta);
-      PointGeo gx, gy;
-      point_geo(sXn[0], sT1[0], sT2[0], xi, eta, gx);
-      point_geo(sXn[1], sT1[1], sT2[1], yxi, yeta, gy);
-      const d3 Rv = sub(gx.x, gy.x);
-      const double r = sqrt(dot(Rv, Rv));
-      const double ir = 1.0 / r;
-      const d3 h = scl(ir, Rv);
-      const double W = w * gx.J * gy.J;
-      const double nR = dot(gx.n, h);
-      const d3 sx[2] = {gx.s1, gx.s2}, tx[2] = {gx.t1, gx.t2}, ty[2] = {gy.t1, gy.t2};
-      double g[8];
-#pragma unroll
-      for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-          g[2 * a + b] = (dot(sx[a], ty[b]) + dot(sx[a], h) * dot(h, ty[b])) * ir;
-          g[4 + 2 * a + b] = (dot(tx[a], ty[b]) * nR - dot(tx[a], h) * dot(gx.n, ty[b])) * ir * ir;
-        }
-#pragma unroll
-      for (int i = 0; i < 6; ++i) sU[tid][i] = gx.N[i];
-#pragma unroll
-      for (int j = 0; j < 6; ++j)
-#pragma unroll
-        for (int c = 0; c < 8; ++c) sV[tid][j * 8 + c] = W * gy.N[j] * g[c];
+  for (int base = 0; base < ngroups; base += TT) {
+    // region-major numbering keeps whole warps in one region (one branch)
+    const int grp = base + tid;
+    double* myV = sV[tid];
+    int shx = 1;
+    if (grp < ngroups) {
+      const int reg = grp / ns3;
+      int rest = grp % ns3;
+      const int ci = rest % ns;
+      rest /= ns;
+      const int bi = rest % ns;
+      const int ai = rest / ns;
+      shx = ss_shared_x(P.cls, reg);
+      if (shx)
+        ssq_group<true>(P.cls, reg, ai, bi, ci, ns, px, py, sXn, sT1, sT2, sU[tid], myV);
+      else
+        ssq_group<false>(P.cls, reg, ai, bi, ci, ns, px, py, sXn, sT1, sT2, sU[tid], myV);
     } else {
 #pragma unroll
       for (int i = 0; i < 6; ++i) sU[tid][i] = 0.0;
 #pragma unroll
-      for (int c = 0; c < 48; ++c) sV[tid][c] = 0.0;
+      for (int c = 0; c < 48; ++c) myV[c] = 0.0;
     }
+    sFlag[tid] = shx;
     __syncthreads();
+    // G[i][j][c] += N_i(x) V[j][c]  (x shared)  or  V[i][c] N_j(y)  (y shared)
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      const int o = tid + k * TT;  // output (i, jc), 288 of them
-      const int i = o / 48, jc = o % 48;
-      double s = acc[k];
-      for (int p = 0; p < TT; ++p) s = fma(sU[p][i], sV[p][jc], s);
-      acc[k] = s;
+      const int o = tid + k * TT;  // output (i, j, c), 288 of them
+      const int i = o / 48, jc = o % 48, j = jc >> 3, c = jc & 7;
+      double s2 = acc[k];
+      for (int q = 0; q < TT; ++q) {
+        const bool fx = sFlag[q] != 0;
+        const double u = sU[q][fx ? i : j];
+        const double v = sV[q][fx ? jc : i * 8 + c];
+        s2 = fma(u, v, s2);
+      }
+      acc[k] = s2;
     }
     __syncthreads();
   }

@@ -121,36 +121,57 @@ __global__ void __launch_bounds__(256) gemv_c64_kernel(int64_t N, const float4* 
 }
 
 // y += near * x for the near blocks (test node rows, 4 x 4 complex blocks
-// [h][alpha][g][beta]); NB = complex128 or complex64 blocks, V = vector type
+// [h][alpha][g][beta]).  One warp per test node: lanes take the row's
+// blocks, each block contributes to the node's 4 outputs, then a warp
+// reduction.  BT = block element type, VT = vector element type.
 template <class BT, class VT>
-__global__ void near_spmv_kernel(int64_t nn, const int32_t* __restrict__ rowptr,
-                                 const int32_t* __restrict__ col, const BT* __restrict__ blk,
-                                 const VT* __restrict__ x, VT* __restrict__ y, int64_t xs,
-                                 int64_t ys, int r) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) near_spmv_kernel(int64_t nn, const int32_t* __restrict__ rowptr,
+                                                        const int32_t* __restrict__ col,
+                                                        const BT* __restrict__ blk,
+                                                        const VT* __restrict__ x, VT* __restrict__ y,
+                                                        int64_t xs, int64_t ys, int r) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * 8 + warp;
   const int s = blockIdx.y;
-  if (t >= nn * 4 || s >= r) return;
-  const int64_t i = t >> 2;
-  const int ha = (int)(t & 3), h = ha >> 1, a = ha & 1;
+  if (i >= nn || s >= r) return;
   const int64_t H = 2 * nn;
   using R = decltype(x[0].x);
-  R accr = 0, acci = 0;
+  R ar[4] = {0, 0, 0, 0}, ai[4] = {0, 0, 0, 0};
   const VT* xv = x + s * xs;
-  for (int32_t q = rowptr[i]; q < rowptr[i + 1]; ++q) {
+  for (int32_t q = rowptr[i] + lane; q < rowptr[i + 1]; q += 32) {
     const int64_t j = col[q];
-    const BT* b = blk + (int64_t)q * 16 + ha * 4;
+    VT xj[4];
 #pragma unroll
-    for (int gb = 0; gb < 4; ++gb) {
-      const int g = gb >> 1, be = gb & 1;
-      const VT xv_ = xv[g * H + 2 * j + be];
-      const R br = (R)b[gb].x, bi = (R)b[gb].y;
-      accr = fma(br, xv_.x, fma(-bi, xv_.y, accr));
-      acci = fma(br, xv_.y, fma(bi, xv_.x, acci));
-    }
+    for (int gb = 0; gb < 4; ++gb) xj[gb] = xv[(gb >> 1) * H + 2 * j + (gb & 1)];
+    const BT* b = blk + (int64_t)q * 16;
+#pragma unroll
+    for (int ha = 0; ha < 4; ++ha)
+#pragma unroll
+      for (int gb = 0; gb < 4; ++gb) {
+        const BT m = b[ha * 4 + gb];
+        ar[ha] = fma((R)m.x, xj[gb].x, fma(-(R)m.y, xj[gb].y, ar[ha]));
+        ai[ha] = fma((R)m.x, xj[gb].y, fma((R)m.y, xj[gb].x, ai[ha]));
+      }
   }
-  VT* yo = y + s * ys + h * H + 2 * i + a;
-  yo->x += accr;
-  yo->y += acci;
+#pragma unroll
+  for (int ha = 0; ha < 4; ++ha)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ar[ha] += __shfl_xor_sync(0xffffffffu, ar[ha], o);
+      ai[ha] += __shfl_xor_sync(0xffffffffu, ai[ha], o);
+    }
+  if (lane < 4) {
+    R vr = ar[0], vi = ai[0];
+#pragma unroll
+    for (int ha = 1; ha < 4; ++ha)
+      if (lane == ha) {
+        vr = ar[ha];
+        vi = ai[ha];
+      }
+    VT* yo = y + s * ys + (lane >> 1) * H + 2 * i + (lane & 1);
+    yo->x += vr;
+    yo->y += vi;
+  }
 }
 
 // ============================================================ batched LU
@@ -161,6 +182,11 @@ constexpr int NBK = 32;
 __device__ __forceinline__ double cabs1(double2 a) { return fabs(a.x) + fabs(a.y); }
 __device__ __forceinline__ double2 cmul2(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <class CT>
+__device__ __forceinline__ CT cdivT(CT a, CT b) {
+  const auto den = b.x * b.x + b.y * b.y;
+  return CT{(a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den};
 }
 __device__ __forceinline__ double2 cdiv2(double2 a, double2 b) {
   const double den = b.x * b.x + b.y * b.y;
@@ -240,7 +266,8 @@ __global__ void __launch_bounds__(256) lu_panel_kernel(double2* __restrict__ A, 
 
 // B[k0:k0+w, c0:c1] <- L_kk^{-1} B[...] (unit lower, L from A) or
 // U_kk^{-1} B[...] (upper, non-unit); one thread per column.
-__global__ void trsm_tile_kernel(const double2* __restrict__ A, double2* __restrict__ B, int64_t d,
+template <class CT>
+__global__ void trsm_tile_kernel(const CT* __restrict__ A, CT* __restrict__ B, int64_t d,
                                  int64_t ldb, int64_t bstride, const int32_t* __restrict__ sz,
                                  int k0, int w_max, int64_t c0, int64_t c1_cap, int upper) {
   const int b = blockIdx.y;
@@ -250,21 +277,21 @@ __global__ void trsm_tile_kernel(const double2* __restrict__ A, double2* __restr
   const int64_t c1 = c1_cap < 0 ? n : mn64(c1_cap, n);
   const int64_t c = c0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= c1) return;
-  const double2* M = A + (int64_t)b * d * d;
-  double2* X = B + (int64_t)b * bstride;
+  const CT* M = A + (int64_t)b * d * d;
+  CT* X = B + (int64_t)b * bstride;
   // fixed-size, fully unrolled loops keep v[] in registers; rows >= w are
   // inert (zero right-hand side, never written back)
-  double2 v[NBK];
+  CT v[NBK];
 #pragma unroll
   for (int i = 0; i < NBK; ++i)
-    v[i] = i < w ? X[(int64_t)(k0 + i) * ldb + c] : make_double2(0.0, 0.0);
+    v[i] = i < w ? X[(int64_t)(k0 + i) * ldb + c] : CT{0, 0};
   if (!upper) {
 #pragma unroll
     for (int i = 1; i < NBK; ++i)
 #pragma unroll
       for (int j = 0; j < i; ++j) {
         if (i < w) {
-          const double2 l = M[(int64_t)(k0 + i) * d + k0 + j];
+          const CT l = M[(int64_t)(k0 + i) * d + k0 + j];
           v[i].x -= l.x * v[j].x - l.y * v[j].y;
           v[i].y -= l.x * v[j].y + l.y * v[j].x;
         }
@@ -276,12 +303,12 @@ __global__ void trsm_tile_kernel(const double2* __restrict__ A, double2* __restr
 #pragma unroll
         for (int j = i + 1; j < NBK; ++j) {
           if (j < w) {
-            const double2 u = M[(int64_t)(k0 + i) * d + k0 + j];
+            const CT u = M[(int64_t)(k0 + i) * d + k0 + j];
             v[i].x -= u.x * v[j].x - u.y * v[j].y;
             v[i].y -= u.x * v[j].y + u.y * v[j].x;
           }
         }
-        v[i] = cdiv2(v[i], M[(int64_t)(k0 + i) * d + k0 + i]);
+        v[i] = cdivT(v[i], M[(int64_t)(k0 + i) * d + k0 + i]);
       }
     }
   }
@@ -293,9 +320,10 @@ __global__ void trsm_tile_kernel(const double2* __restrict__ A, double2* __restr
 // C[r0:r1, c0:c1] -= A[r0:r1, k0:k0+w] * Bm[k0:k0+w, c0:c1] per block:
 // 64 x 64 output tiles, 256 threads with 4 x 4 complex accumulators each.
 // Row range is [r0, r1) with r1 = n (the block's size) if r1_cap < 0.
-__global__ void __launch_bounds__(256) gemm_update_kernel(const double2* __restrict__ A,
-                                                          const double2* __restrict__ Bm,
-                                                          double2* __restrict__ Cm, int64_t d,
+template <class CT>
+__global__ void __launch_bounds__(256) gemm_update_kernel(const CT* __restrict__ A,
+                                                          const CT* __restrict__ Bm,
+                                                          CT* __restrict__ Cm, int64_t d,
                                                           int64_t ldb, int64_t bstride,
                                                           const int32_t* __restrict__ sz, int k0,
                                                           int64_t r0, int64_t r1_cap, int64_t c0,
@@ -308,30 +336,30 @@ __global__ void __launch_bounds__(256) gemm_update_kernel(const double2* __restr
   const int64_t c1 = c1_cap < 0 ? n : mn64(c1_cap, n);
   const int64_t tr = r0 + (int64_t)blockIdx.y * 64, tc = c0 + (int64_t)blockIdx.x * 64;
   if (tr >= r1 || tc >= c1) return;
-  const double2* M = A + (int64_t)b * d * d;
-  const double2* Bb = Bm + (int64_t)b * bstride;
-  double2* Cb = Cm + (int64_t)b * bstride;
-  __shared__ double2 sA[64][NBK + 1];
-  __shared__ double2 sB[NBK][64 + 1];
+  const CT* M = A + (int64_t)b * d * d;
+  const CT* Bb = Bm + (int64_t)b * bstride;
+  CT* Cb = Cm + (int64_t)b * bstride;
+  __shared__ CT sA[64][NBK + 1];
+  __shared__ CT sB[NBK][64 + 1];
   for (int t = threadIdx.x; t < 64 * NBK; t += 256) {
     const int i = t / NBK, k = t % NBK;
     const int64_t gr = tr + i;
-    sA[i][k] = (gr < r1 && k < w) ? M[gr * d + k0 + k] : make_double2(0, 0);
+    sA[i][k] = (gr < r1 && k < w) ? M[gr * d + k0 + k] : CT{0, 0};
   }
   for (int t = threadIdx.x; t < NBK * 64; t += 256) {
     const int k = t / 64, j = t % 64;
     const int64_t gc = tc + j;
-    sB[k][j] = (gc < c1 && k < w) ? Bb[(int64_t)(k0 + k) * ldb + gc] : make_double2(0, 0);
+    sB[k][j] = (gc < c1 && k < w) ? Bb[(int64_t)(k0 + k) * ldb + gc] : CT{0, 0};
   }
   __syncthreads();
   const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
-  double2 acc[4][4];
+  CT acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = make_double2(0, 0);
+    for (int j = 0; j < 4; ++j) acc[i][j] = CT{0, 0};
   for (int k = 0; k < NBK; ++k) {
-    double2 a[4], bb[4];
+    CT a[4], bb[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) a[i] = sA[ty + 16 * i][k];
 #pragma unroll
@@ -350,7 +378,7 @@ __global__ void __launch_bounds__(256) gemm_update_kernel(const double2* __restr
     for (int j = 0; j < 4; ++j) {
       const int64_t gr = tr + ty + 16 * i, gc = tc + tx + 16 * j;
       if (gr < r1 && gc < c1) {
-        double2 v = Cb[gr * ldb + gc];
+        CT v = Cb[gr * ldb + gc];
         v.x -= acc[i][j].x;
         v.y -= acc[i][j].y;
         Cb[gr * ldb + gc] = v;
@@ -359,14 +387,15 @@ __global__ void __launch_bounds__(256) gemm_update_kernel(const double2* __restr
 }
 
 // X <- P I: row k of the identity permuted by the recorded swaps
-__global__ void perm_identity_kernel(double2* __restrict__ X, int64_t d,
+template <class CT>
+__global__ void perm_identity_kernel(CT* __restrict__ X, int64_t d,
                                      const int32_t* __restrict__ sz,
                                      const int32_t* __restrict__ piv) {
   const int b = blockIdx.y;
   const int n = sz[b];
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= n) return;
-  double2* M = X + (int64_t)b * d * d;
+  CT* M = X + (int64_t)b * d * d;
   // column c of P: start from e_c and apply the swaps in order
   int64_t pos = c;
   for (int k = 0; k < n; ++k) {
@@ -376,7 +405,7 @@ __global__ void perm_identity_kernel(double2* __restrict__ X, int64_t d,
     else if (pos == p)
       pos = k;
   }
-  for (int64_t i = 0; i < n; ++i) M[i * d + c] = make_double2(i == pos ? 1.0 : 0.0, 0.0);
+  for (int64_t i = 0; i < n; ++i) M[i * d + c] = CT{i == pos ? 1.0f : 0.0f, 0.0f};
 }
 
 // gather the MBJ blocks of the operator: block b rows/cols I_b in both halves
@@ -731,8 +760,8 @@ mueller_status op_matvec(const mueller_operator* op, const void* X, void* Y, int
     dim3 grid(nblk(N, 16), r);
     { Prof prof_("gemv_c64_kernel<double>", s); gemv_c64_kernel<double><<<grid, 256, 0, s>>>(N, (const float4*)op->Z_dev, op->ldz, X, Y, N, N, r); }
     MU_CHECK_LAUNCH("gemv_c64_kernel<double>");
-    dim3 g2(nblk(4 * m->nn, 128), r);
-    { Prof prof_("near_spmv_kernel<double2, double2>", s); near_spmv_kernel<double2, double2><<<g2, 128, 0, s>>>(m->nn, m->near_rowptr, m->near_col,
+    dim3 g2(nblk(m->nn, 8), r);
+    { Prof prof_("near_spmv_kernel<double2, double2>", s); near_spmv_kernel<double2, double2><<<g2, 256, 0, s>>>(m->nn, m->near_rowptr, m->near_col,
                                                           (const double2*)op->near_dev,
                                                           (const double2*)X, (double2*)Y, N, N, r); }
     MU_CHECK_LAUNCH("near_spmv_kernel");
@@ -756,6 +785,10 @@ static BlockLayout layout(int64_t N, int64_t B) {
   return L;
 }
 
+template <class CT>
+static mueller_status block_inverse(const CT* A, int64_t d, int nb, const int32_t* sz_dev,
+                                    const int32_t* piv, CT* inv, cudaStream_t s);
+
 // in-place LU of nb blocks of size d (active sizes sz_dev), then, if inv,
 // their inverses in 'inv' (d x d per block)
 static mueller_status batched_lu_inverse(double2* A, int64_t d, int nb, const int32_t* sz_dev,
@@ -768,47 +801,62 @@ static mueller_status batched_lu_inverse(double2* A, int64_t d, int nb, const in
     if (rest <= 0) continue;
     // U12 = L11^{-1} A12 (columns k0+NBK .. n)
     dim3 gt(nblk(rest, 128), nb);
-    { Prof prof_("trsm_tile_kernel", s); trsm_tile_kernel<<<gt, 128, 0, s>>>(A, A, d, d, d * d, sz_dev, k0, NBK, k0 + NBK, -1, 0); }
+    { Prof prof_("trsm_tile_kernel", s); trsm_tile_kernel<double2><<<gt, 128, 0, s>>>(A, A, d, d, d * d, sz_dev, k0, NBK, k0 + NBK, -1, 0); }
     MU_CHECK_LAUNCH("trsm_tile_kernel");
     dim3 gg(nblk(rest, 64), nblk(rest, 64), nb);
-    { Prof prof_("gemm_update_kernel", s); gemm_update_kernel<<<gg, 256, 0, s>>>(A, A, A, d, d, d * d, sz_dev, k0, k0 + NBK, -1, k0 + NBK, -1); }
+    { Prof prof_("gemm_update_kernel", s); gemm_update_kernel<double2><<<gg, 256, 0, s>>>(A, A, A, d, d, d * d, sz_dev, k0, k0 + NBK, -1, k0 + NBK, -1); }
     MU_CHECK_LAUNCH("gemm_update_kernel");
   }
   if (!inv) return MUELLER_OK;
-  // inv = U^{-1} L^{-1} P
-  { Prof prof_("perm_identity_kernel", s); perm_identity_kernel<<<dim3(nblk(d, 128), nb), 128, 0, s>>>(inv, d, sz_dev, piv); }
+  return block_inverse<double2>(A, d, nb, sz_dev, piv, inv, s);
+}
+
+// inv = U^{-1} L^{-1} P from the LU factors in A (complex type CT)
+template <class CT>
+static mueller_status block_inverse(const CT* A, int64_t d, int nb, const int32_t* sz_dev,
+                                    const int32_t* piv, CT* inv, cudaStream_t s) {
+  { Prof prof_("perm_identity_kernel", s); perm_identity_kernel<CT><<<dim3(nblk(d, 128), nb), 128, 0, s>>>(inv, d, sz_dev, piv); }
   MU_CHECK_LAUNCH("perm_identity_kernel");
   for (int k0 = 0; k0 < d; k0 += NBK) {  // forward: L (unit lower)
-    { Prof prof_("trsm_tile_kernel", s); trsm_tile_kernel<<<dim3(nblk(d, 128), nb), 128, 0, s>>>(A, inv, d, d, d * d, sz_dev, k0, NBK, 0, -1, 0); }
+    { Prof prof_("trsm_tile_kernel", s); trsm_tile_kernel<CT><<<dim3(nblk(d, 128), nb), 128, 0, s>>>(A, inv, d, d, d * d, sz_dev, k0, NBK, 0, -1, 0); }
     MU_CHECK_LAUNCH("trsm_tile_kernel(L)");
     const int64_t below = d - (k0 + NBK);
     if (below > 0) {
       dim3 gg(nblk(d, 64), nblk(below, 64), nb);
-      { Prof prof_("gemm_update_kernel", s); gemm_update_kernel<<<gg, 256, 0, s>>>(A, inv, inv, d, d, d * d, sz_dev, k0, k0 + NBK, -1, 0, -1); }
+      { Prof prof_("gemm_update_kernel", s); gemm_update_kernel<CT><<<gg, 256, 0, s>>>(A, inv, inv, d, d, d * d, sz_dev, k0, k0 + NBK, -1, 0, -1); }
       MU_CHECK_LAUNCH("gemm_update_kernel(L)");
     }
   }
   const int64_t ntile = (d + NBK - 1) / NBK;
   for (int64_t t = ntile - 1; t >= 0; --t) {  // backward: U
     const int k0 = (int)(t * NBK);
-    { Prof prof_("trsm_tile_kernel", s); trsm_tile_kernel<<<dim3(nblk(d, 128), nb), 128, 0, s>>>(A, inv, d, d, d * d, sz_dev, k0, NBK, 0, -1, 1); }
+    { Prof prof_("trsm_tile_kernel", s); trsm_tile_kernel<CT><<<dim3(nblk(d, 128), nb), 128, 0, s>>>(A, inv, d, d, d * d, sz_dev, k0, NBK, 0, -1, 1); }
     MU_CHECK_LAUNCH("trsm_tile_kernel(U)");
     if (k0 > 0) {
       dim3 gg(nblk(d, 64), nblk(k0, 64), nb);
-      { Prof prof_("gemm_update_kernel", s); gemm_update_kernel<<<gg, 256, 0, s>>>(A, inv, inv, d, d, d * d, sz_dev, k0, 0, k0, 0, -1); }
+      { Prof prof_("gemm_update_kernel", s); gemm_update_kernel<CT><<<gg, 256, 0, s>>>(A, inv, inv, d, d, d * d, sz_dev, k0, 0, k0, 0, -1); }
       MU_CHECK_LAUNCH("gemm_update_kernel(U)");
     }
   }
   return MUELLER_OK;
 }
 
-// precond_dev layout: [nb][d][d] complex128 inverses, then int32 sz[nb]
+// precond_dev layout: [nb][d][d] inverses, then int32 sz[nb].  The inverses
+// are complex128 for a C128 operator (FP64 GMRES applies them in FP64) and
+// complex64 for a C64_NEAR64 operator, whose inner GMRES applies them in
+// FP32: the LU factorisation is FP64 in both cases; for the mixed operator
+// the explicit inverse is then formed from the FP64 factors in FP32.
+static const int32_t* precond_sizes(const mueller_operator* op, const BlockLayout& L) {
+  const size_t elem = op->dtype == MUELLER_C128 ? 16 : 8;
+  return (const int32_t*)((const char*)op->precond_dev + (size_t)L.nb * L.d * L.d * elem);
+}
+
 mueller_status precond_build(const mueller_operator* op, int64_t block, void* P, cudaStream_t s) {
   const mueller_mesh* m = op->mesh;
   const int64_t N = 4 * m->nn;
   BlockLayout L = layout(N, block);
-  double2* inv = (double2*)P;
-  int32_t* sz_dev = (int32_t*)(inv + (size_t)L.nb * L.d * L.d);
+  const size_t elem = op->dtype == MUELLER_C128 ? 16 : 8;
+  int32_t* sz_dev = (int32_t*)((char*)P + (size_t)L.nb * L.d * L.d * elem);
   MU_CUDA(cudaMemcpyAsync(sz_dev, L.sz.data(), L.nb * sizeof(int32_t), cudaMemcpyHostToDevice, s));
   double2* A = nullptr;
   int32_t* piv = nullptr;
@@ -818,16 +866,31 @@ mueller_status precond_build(const mueller_operator* op, int64_t block, void* P,
   MU_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), s));
   dim3 g(nblk(L.d, 128), L.d, L.nb);
   if (op->dtype == MUELLER_C128) {
-    { Prof prof_("gather_blocks_kernel<MUELLER_C128>", s); gather_blocks_kernel<MUELLER_C128><<<g, 128, 0, s>>>(op->Z_dev, op->ldz, L.H, L.B, L.d, sz_dev, A); }
+    { Prof prof_("gather_blocks_kernel", s); gather_blocks_kernel<MUELLER_C128><<<g, 128, 0, s>>>(op->Z_dev, op->ldz, L.H, L.B, L.d, sz_dev, A); }
   } else {
-    { Prof prof_("gather_blocks_kernel<MUELLER_C64_NEAR64>", s); gather_blocks_kernel<MUELLER_C64_NEAR64><<<g, 128, 0, s>>>(op->Z_dev, op->ldz, L.H, L.B, L.d, sz_dev, A); }
+    { Prof prof_("gather_blocks_kernel", s); gather_blocks_kernel<MUELLER_C64_NEAR64><<<g, 128, 0, s>>>(op->Z_dev, op->ldz, L.H, L.B, L.d, sz_dev, A); }
     MU_CHECK_LAUNCH("gather_blocks_kernel");
     { Prof prof_("gather_near_kernel", s); gather_near_kernel<<<nblk(m->nn, 128), 128, 0, s>>>(m->nn, m->near_rowptr, m->near_col,
                                                         (const double2*)op->near_dev, L.B, L.d,
                                                         sz_dev, A); }
   }
   MU_CHECK_LAUNCH("gather kernels");
-  mueller_status st = batched_lu_inverse(A, L.d, (int)L.nb, sz_dev, piv, status, inv, s);
+  mueller_status st;
+  float2* A32 = nullptr;
+  if (op->dtype == MUELLER_C128) {
+    st = batched_lu_inverse(A, L.d, (int)L.nb, sz_dev, piv, status, (double2*)P, s);
+  } else {
+    st = batched_lu_inverse(A, L.d, (int)L.nb, sz_dev, piv, status, nullptr, s);
+    const int64_t cnt = (int64_t)L.nb * L.d * L.d;
+    if (!st) {
+      cudaError_t e = cudaMallocAsync((void**)&A32, cnt * sizeof(float2), s);
+      if (e != cudaSuccess) st = cuda_fail(e, "precond FP32 factors");
+    }
+    if (!st) {
+      { Prof prof_("c128_to_c64_kernel", s); c128_to_c64_kernel<<<nblk(cnt, 256), 256, 0, s>>>(A, A32, cnt); }
+      st = block_inverse<float2>(A32, L.d, (int)L.nb, sz_dev, piv, (float2*)P, s);
+    }
+  }
   int32_t hst = 0;
   if (!st) {
     cudaError_t e = cudaMemcpyAsync(&hst, status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
@@ -836,6 +899,7 @@ mueller_status precond_build(const mueller_operator* op, int64_t block, void* P,
   }
   cudaFreeAsync(A, s);
   cudaFreeAsync(piv, s);
+  if (A32) cudaFreeAsync(A32, s);
   if (st) return st;
   if (hst) {
     set_error("zero pivot in block-Jacobi block " + std::to_string(hst - 1));
@@ -922,7 +986,7 @@ mueller_status inner_matvec(const InnerOp& I, const VT* x, VT* y, cudaStream_t s
     { Prof prof_("gemv_c64_kernel<float>", s); gemv_c64_kernel<float><<<dim3(nblk(N, 16), 1), 256, 0, s>>>(N, (const float4*)I.op->Z_dev,
                                                                 I.op->ldz, x, y, N, N, 1); }
     MU_CHECK_LAUNCH("gemv_c64_kernel<float>");
-    { Prof prof_("near_spmv_kernel<float2, float2>", s); near_spmv_kernel<float2, float2><<<dim3(nblk(4 * m->nn, 128), 1), 128, 0, s>>>(
+    { Prof prof_("near_spmv_kernel<float2, float2>", s); near_spmv_kernel<float2, float2><<<dim3(nblk(m->nn, 8), 1), 256, 0, s>>>(
         m->nn, m->near_rowptr, m->near_col, I.near32, x, y, N, N, 1); }
     MU_CHECK_LAUNCH("near_spmv_kernel<float>");
     return MUELLER_OK;
@@ -1059,10 +1123,6 @@ size_t solve_work(const mueller_operator* op, int r, const mueller_solver_opts* 
     b = gmres_bytes(N, m, 8);
     b += 4 * (size_t)N * 16 + 4 * (size_t)N * 8 + 256 * 8;  // r64, y64, d32, rhs32
     b += (size_t)op->mesh->nnzb * 16 * 8 + 256;              // near complex64
-    if (op->precond_dev && op->block > 0) {
-      BlockLayout L = layout(N, op->block);
-      b += (size_t)L.nb * L.d * L.d * 8 + 256;
-    }
   }
   return b + 4096;
 }
@@ -1103,18 +1163,18 @@ mueller_status solve(const mueller_operator* op, const void* Bv, void* Xv, int r
       { Prof prof_("transpose_rhs_kernel", s); transpose_rhs_kernel<<<nblk((int64_t)N * r, 256), 256, 0, s>>>(B, T, N, r, 0); }
       { Prof prof_("permute_rows_kernel", s); permute_rows_kernel<<<nblk(r, 64), 64, 0, s>>>(T, N, r, piv); }
       for (int k0 = 0; k0 < N; k0 += NBK) {
-        { Prof prof_("trsm_tile_kernel", s); trsm_tile_kernel<<<dim3(nblk(r, 128), 1), 128, 0, s>>>(A, T, N, r, 0, sz_dev, k0, NBK, 0, r, 0); }
+        { Prof prof_("trsm_tile_kernel", s); trsm_tile_kernel<double2><<<dim3(nblk(r, 128), 1), 128, 0, s>>>(A, T, N, r, 0, sz_dev, k0, NBK, 0, r, 0); }
         const int64_t below = N - (k0 + NBK);
         if (below > 0)
-          { Prof prof_("gemm_update_kernel", s); gemm_update_kernel<<<dim3(nblk(r, 64), nblk(below, 64), 1), 256, 0, s>>>(
+          { Prof prof_("gemm_update_kernel", s); gemm_update_kernel<double2><<<dim3(nblk(r, 64), nblk(below, 64), 1), 256, 0, s>>>(
               A, T, T, N, r, 0, sz_dev, k0, k0 + NBK, -1, 0, r); }
       }
       const int64_t ntile = (N + NBK - 1) / NBK;
       for (int64_t t = ntile - 1; t >= 0; --t) {
         const int k0 = (int)(t * NBK);
-        { Prof prof_("trsm_tile_kernel", s); trsm_tile_kernel<<<dim3(nblk(r, 128), 1), 128, 0, s>>>(A, T, N, r, 0, sz_dev, k0, NBK, 0, r, 1); }
+        { Prof prof_("trsm_tile_kernel", s); trsm_tile_kernel<double2><<<dim3(nblk(r, 128), 1), 128, 0, s>>>(A, T, N, r, 0, sz_dev, k0, NBK, 0, r, 1); }
         if (k0 > 0)
-          { Prof prof_("gemm_update_kernel", s); gemm_update_kernel<<<dim3(nblk(r, 64), nblk(k0, 64), 1), 256, 0, s>>>(
+          { Prof prof_("gemm_update_kernel", s); gemm_update_kernel<double2><<<dim3(nblk(r, 64), nblk(k0, 64), 1), 256, 0, s>>>(
               A, T, T, N, r, 0, sz_dev, k0, 0, k0, 0, r); }
       }
       { Prof prof_("transpose_rhs_kernel", s); transpose_rhs_kernel<<<nblk((int64_t)N * r, 256), 256, 0, s>>>(T, X, N, r, 1); }
@@ -1146,7 +1206,7 @@ mueller_status solve(const mueller_operator* op, const void* Bv, void* Xv, int r
   I.sz_dev = nullptr;
   if (op->precond_dev) {
     I.L = layout(N, op->block);
-    I.sz_dev = (const int32_t*)((const double2*)op->precond_dev + (size_t)I.L.nb * I.L.d * I.L.d);
+    I.sz_dev = precond_sizes(op, I.L);
   }
   const int mres = std::max(1, (int)o->restart);
   if (o->mode == MUELLER_SOLVE_GMRES && op->dtype == MUELLER_C128) {
@@ -1187,12 +1247,7 @@ mueller_status solve(const mueller_operator* op, const void* Bv, void* Xv, int r
       { Prof prof_("c128_to_c64_kernel", s); c128_to_c64_kernel<<<nblk(nnzb * 16, 256), 256, 0, s>>>((const double2*)op->near_dev, near32, nnzb * 16); }
       MU_CHECK_LAUNCH("c128_to_c64");
     }
-    if (op->precond_dev) {
-      const int64_t cnt = (int64_t)I.L.nb * I.L.d * I.L.d;
-      inv32 = (float2*)take(cnt * 8);
-      { Prof prof_("c128_to_c64_kernel", s); c128_to_c64_kernel<<<nblk(cnt, 256), 256, 0, s>>>((const double2*)op->precond_dev, inv32, cnt); }
-      MU_CHECK_LAUNCH("c128_to_c64");
-    }
+    if (op->precond_dev) inv32 = (float2*)op->precond_dev;  // complex64 inverses
     I.near32 = near32;
     I.inv32 = inv32;
     GmresWork W = carve_gmres<float2>(p, N, mres);

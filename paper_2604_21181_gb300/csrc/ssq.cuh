@@ -10,18 +10,13 @@
 
 namespace mu {
 
-__host__ __device__ __forceinline__ void ss_point(int cls, int ns, int64_t pt, const double* gl,
-                                                  const double* glw, double& xu, double& xv,
-                                                  double& yu, double& yv, double& w) {
-  const int nreg = cls == 3 ? 6 : (cls == 2 ? 5 : 2);
-  const int reg = (int)(pt % nreg);
-  int64_t rest = pt / nreg;
-  const int d = (int)(rest % ns);
-  rest /= ns;
-  const int c = (int)(rest % ns);
-  rest /= ns;
-  const int b = (int)(rest % ns);
-  const int a = (int)(rest / ns);
+// Point (xu, xv) on the test triangle, (yu, yv) on the trial triangle and
+// weight of region 'reg' of class cls (3 coincident, 2 common edge, 1 common
+// vertex) at the Gauss-Legendre indices (a, b, c, d) of (xi, eta1, eta2, eta3).
+__host__ __device__ __forceinline__ void ss_point_idx(int cls, int reg, int a, int b, int c, int d,
+                                                      const double* gl, const double* glw,
+                                                      double& xu, double& xv, double& yu,
+                                                      double& yv, double& w) {
   const double xi = gl[a], e1 = gl[b], e2 = gl[c], e3 = gl[d];
   const double W = glw[a] * glw[b] * glw[c] * glw[d];
   const double x3 = xi * xi * xi;
@@ -53,6 +48,32 @@ __host__ __device__ __forceinline__ void ss_point(int cls, int ns, int64_t pt, c
       xu = xi * e2; xv = xi * e2 * e3; yu = xi; yv = xi * e1;
     }
   }
+}
+
+
+// the same, for the flat index pt = ((((a*ns + b)*ns + c)*ns + d)*nreg + reg)
+__host__ __device__ __forceinline__ void ss_point(int cls, int ns, int64_t pt, const double* gl,
+                                                  const double* glw, double& xu, double& xv,
+                                                  double& yu, double& yv, double& w) {
+  const int nreg = cls == 3 ? 6 : (cls == 2 ? 5 : 2);
+  const int reg = (int)(pt % nreg);
+  int64_t rest = pt / nreg;
+  const int d = (int)(rest % ns);
+  rest /= ns;
+  const int c = (int)(rest % ns);
+  rest /= ns;
+  const int b = (int)(rest % ns);
+  const int a = (int)(rest / ns);
+  ss_point_idx(cls, reg, a, b, c, d, gl, glw, xu, xv, yu, yv, w);
+}
+
+// In every region one of the two points does not depend on eta3 (index d):
+// 1 = the test point x, 0 = the trial point y.  Points that differ only in
+// d therefore share the geometry of that side.
+__host__ __device__ __forceinline__ int ss_shared_x(int cls, int reg) {
+  if (cls == 3) return (0x29 >> reg) & 1;  // regions 0, 3, 5
+  if (cls == 2) return (0x06 >> reg) & 1;  // regions 1, 2
+  return reg == 0;
 }
 
 // relabelled reference point (u, v) -> canonical (xi, eta); perm holds the
