@@ -234,15 +234,31 @@ size_t mueller_solve_workspace_bytes(const mueller_operator* op, int32_t r,
                                      const mueller_solver_opts* opts);
 
 /*
- * mueller_matvec -- Y = Z X for r vectors (complex128 in and out), using the
- * operator's storage (C128: FP64 arithmetic; C64_NEAR64: complex64 far part
- * on the tensor cores when r >= 8, else CUDA cores, FP32 accumulation, plus
- * the FP64 near part).  Used by GMRES and exposed for tests and benchmarks.
+ * mueller_matvec -- Y = Z X for r vectors (complex128 in and out), in FP64
+ * arithmetic on the operator's storage (C128: complex128 Z; C64_NEAR64:
+ * complex64 Z read as exact values plus the FP64 near blocks).  This is the
+ * refinement residual product; exposed for tests and benchmarks.
  *   work_dev  NULL or scratch of mueller_matvec_workspace_bytes() bytes.
  */
 mueller_status mueller_matvec(const mueller_operator* op, const void* X_dev, void* Y_dev,
                               int32_t r, void* work_dev, size_t work_bytes, void* stream);
 size_t mueller_matvec_workspace_bytes(const mueller_operator* op, int32_t r);
+
+/*
+ * mueller_matvec_mrhs -- Y = Z X for r = 1..128 complex64 vectors (r x N in
+ * and out) of a C64_NEAR64 operator on the tensor cores: the complex64 far
+ * part as a real GEMM on tcgen05 (kind::tf32, each operand split into a TF32
+ * head and remainder, three products, FP32 accumulation in tensor memory),
+ * plus the near blocks in FP32.  Accuracy is that of an FP32 product
+ * (relative error ~1e-6).  This is the product of the multi-RHS inner GMRES
+ * (the paper's GMRES matvec, Sec. 5, for many incidences at once).
+ *   work_dev  mueller_matvec_mrhs_workspace_bytes(op, r) bytes of scratch.
+ * Synchronising (reads the kernel's error word).  Errors: INVALID_ARG,
+ * TIMEOUT (a pipeline wait in the kernel gave up), CUDA.
+ */
+mueller_status mueller_matvec_mrhs(const mueller_operator* op, const void* X_dev, void* Y_dev,
+                                   int32_t r, void* work_dev, size_t work_bytes, void* stream);
+size_t mueller_matvec_mrhs_workspace_bytes(const mueller_operator* op, int32_t r);
 
 /*
  * mueller_far_field -- scattered far field of the solved currents and the

@@ -31,6 +31,7 @@ from .api import (  # noqa: F401
     profile_report,
     profile_reset,
     matvec,
+    matvec_mrhs,
     precond_build,
     solve,
     solve_workspace_bytes,

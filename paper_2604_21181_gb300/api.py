@@ -74,6 +74,7 @@ EXPORTS = [
     "mueller_matvec_workspace_bytes", "mueller_far_field", "mueller_sync",
     "mueller_profile_enable", "mueller_profile_reset", "mueller_launch_count",
     "mueller_profile_get", "mueller_profile_names", "mueller_far_field_noalloc",
+    "mueller_matvec_mrhs", "mueller_matvec_mrhs_workspace_bytes",
 ]
 
 _lib = None
@@ -119,6 +120,8 @@ def load_library(build_if_missing: bool = True):
         "mueller_profile_names": (i32, [C.c_char_p, C.c_size_t]),
         "mueller_far_field_noalloc": (C.c_int, [vp, C.POINTER(CParams), vp, i32, dp, dp, i64, vp,
                                                 dp, i32, i32, vp]),
+        "mueller_matvec_mrhs": (C.c_int, [C.POINTER(COperator), vp, vp, i32, vp, C.c_size_t, vp]),
+        "mueller_matvec_mrhs_workspace_bytes": (C.c_size_t, [C.POINTER(COperator), i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -363,6 +366,23 @@ def matvec(op: Operator, X, Y=None, stream=None):
         Y = torch.empty_like(X)
     o = op.c()
     _check(lib.mueller_matvec(C.byref(o), _ptr(X), _ptr(Y), int(r), None, 0, _stream(stream)))
+    return Y
+
+
+def matvec_mrhs(op: Operator, X, Y=None, work=None, stream=None):
+    """mueller_matvec_mrhs: complex64 r x N product on the tensor cores."""
+    torch = _torch()
+    lib = load_library()
+    X = _dev(X, torch.complex64, "X")
+    r = X.shape[0] if X.dim() == 2 else 1
+    if Y is None:
+        Y = torch.empty_like(X)
+    o = op.c()
+    need = lib.mueller_matvec_mrhs_workspace_bytes(C.byref(o), int(r))
+    if work is None or work.numel() * work.element_size() < need:
+        work = torch.empty(need, dtype=torch.uint8, device=X.device)
+    _check(lib.mueller_matvec_mrhs(C.byref(o), _ptr(X), _ptr(Y), int(r), _ptr(work),
+                                   work.numel() * work.element_size(), _stream(stream)))
     return Y
 
 

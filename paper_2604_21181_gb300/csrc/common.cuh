@@ -132,6 +132,14 @@ mueller_status solve(const mueller_operator* op, const void* B, void* X, int r,
                      size_t work_bytes, cudaStream_t s);
 size_t solve_work(const mueller_operator* op, int r, const mueller_solver_opts* o);
 
+// mrhs.cu
+size_t mrhs_work_bytes(int64_t N, int r);
+mueller_status mrhs_matvec_c64(const void* Z, int64_t N, int64_t ldz, const void* X, void* Y,
+                               int r, void* work, cudaStream_t s);
+mueller_status mrhs_check_error(void* work, int64_t N, int r, cudaStream_t s);
+mueller_status near_apply_c64(const mueller_mesh* m, const void* near_c128, const void* X, void* Y,
+                              int r, cudaStream_t s);
+
 // farfield.cu
 mueller_status far_field(mueller_mesh* m, const PhysConsts& P, int Q, const void* X, int r,
                          const double* inc, const double* dirs, int64_t ndir, void* F,

@@ -548,6 +548,27 @@ mueller_status mueller_matvec(const mueller_operator* op, const void* X, void* Y
   return op_matvec(op, X, Y, r, work, work_bytes, (cudaStream_t)stream);
 }
 
+size_t mueller_matvec_mrhs_workspace_bytes(const mueller_operator* op, int32_t r) {
+  if (!op || !op->mesh || r < 1) return 0;
+  return mrhs_work_bytes(4 * op->mesh->nn, r);
+}
+
+mueller_status mueller_matvec_mrhs(const mueller_operator* op, const void* X, void* Y, int32_t r,
+                                   void* work, size_t work_bytes, void* stream) {
+  if (!op || !op->mesh || !op->Z_dev || !X || !Y) return fail(MUELLER_ERR_INVALID_ARG, "NULL argument");
+  if (op->dtype != MUELLER_C64_NEAR64 || !op->near_dev)
+    return fail(MUELLER_ERR_INVALID_ARG, "the tensor-core product needs a C64_NEAR64 operator");
+  const int64_t N = 4 * op->mesh->nn;
+  if (r < 1 || r > 128) return fail(MUELLER_ERR_INVALID_ARG, "r must be in 1..128");
+  if (!work || work_bytes < mrhs_work_bytes(N, r))
+    return fail(MUELLER_ERR_INVALID_ARG, "workspace missing or too small");
+  cudaStream_t s = (cudaStream_t)stream;
+  mueller_status st = mrhs_matvec_c64(op->Z_dev, N, op->ldz, X, Y, r, work, s);
+  if (!st) st = near_apply_c64(op->mesh, op->near_dev, X, Y, r, s);
+  if (!st) st = mrhs_check_error(work, N, r, s);
+  return st;
+}
+
 mueller_status mueller_far_field(mueller_mesh* m, const mueller_params* p, const void* X,
                                  int32_t r, const double* inc, const double* dirs, int64_t ndir,
                                  void* F, double* xs, int32_t n_theta, int32_t n_phi,

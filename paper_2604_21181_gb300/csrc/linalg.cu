@@ -769,6 +769,16 @@ mueller_status op_matvec(const mueller_operator* op, const void* X, void* Y, int
   return MUELLER_OK;
 }
 
+// y += near x for r complex64 vectors, near blocks complex128 (FP32 arithmetic)
+mueller_status near_apply_c64(const mueller_mesh* m, const void* near_c128, const void* X, void* Y,
+                              int r, cudaStream_t s) {
+  const int64_t N = 4 * m->nn;
+  dim3 g(nblk(m->nn, 8), r);
+  { Prof prof_("near_spmv_kernel<double2, float2>", s); near_spmv_kernel<double2, float2><<<g, 256, 0, s>>>(m->nn, m->near_rowptr, m->near_col, (const double2*)near_c128, (const float2*)X, (float2*)Y, N, N, r); }
+  MU_CHECK_LAUNCH("near_spmv_kernel<double2, float2>");
+  return MUELLER_OK;
+}
+
 // ================================================================= MBJ build
 struct BlockLayout {
   int64_t H, B, nb, d;

@@ -1,0 +1,427 @@
+// Multi-right-hand-side product Y = Z X on the tcgen05 tensor cores.
+//
+// Z is the complex64 N x N matrix of the mixed operator (row-major, ldz), X
+// and Y hold r complex64 vectors.  The complex product is a real GEMM:
+//   Y_real[i][2s + 0] = sum_j  zr xr - zi xi,  Y_real[i][2s + 1] = sum_j zr xi + zi xr
+// i.e. the rows of Z read as real vectors of length 2N (re, im interleaved)
+// against B' (2r x 2N, K-major) with rows  2s: ( xr_j, -xi_j )  and
+// 2s+1: ( xi_j, xr_j ).  The MMA kind is tf32 with FP32 accumulation in
+// TMEM; each operand is split into a TF32 head and its remainder
+// (x = hi + lo), and hi*hi + hi*lo + lo*hi are accumulated, which brings the
+// product to FP32 accuracy.
+//
+// CTA (192 threads): warp 0 issues the TMA loads of the Z tile (128 rows x
+// 32 floats) and of the B' head / remainder tiles; warps 2-5 split the Z
+// tile into head and remainder in shared memory and, at the end, read the
+// accumulator from TMEM; warp 1 allocates TMEM and one of its threads issues
+// the MMAs.  Stages are handed over with mbarriers; every wait is bounded and
+// reports a timeout through an error word instead of hanging.  K is split
+// across CTAs (split-K) so that the grid fills the 152 SMs; the partial sums
+// meet in Y by atomic additions.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "common.cuh"
+
+namespace mu {
+namespace {
+
+constexpr int BM = 128;   // rows of Z per CTA (MMA M)
+constexpr int BK = 32;    // floats per K tile = one 128-byte swizzle row
+constexpr int MMA_K = 8;  // tf32 elements per tcgen05.mma
+constexpr int THREADS = 192;
+constexpr uint32_t WAIT_LIMIT = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait: false after WAIT_LIMIT polls
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+  for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
+    if (mbar_try_wait(b, parity)) return true;
+    if (it > 32) __nanosleep(64);
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+      : "memory");
+}
+
+// UMMA shared-memory descriptor of a K-major tile in the 128-byte swizzle
+// layout written by TMA: 8-row groups of 1024 bytes (stride byte offset),
+// descriptor version 1, layout type SWIZZLE_128B.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t tf32_round(float v) {
+  uint32_t o;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(o) : "f"(v));
+  return o;
+}
+
+struct MrhsArgs {
+  int64_t N;        // rows of Z (= columns / 2 of the real view)
+  int nprime;       // padded 2r (MMA N), multiple of 16
+  int r;            // right-hand sides
+  int ktiles;       // K tiles of the real view (2N / 32 rounded up)
+  int kchunk;       // K tiles per CTA (split-K)
+  int stages;
+  uint32_t tmem_cols;
+  float* Y;         // complex64 r x N, accumulated (atomic adds)
+  int* err;         // error word
+};
+
+// dynamic shared memory: [stages][A 16 KB | Alo 16 KB | Bhi | Blo] + barriers
+__global__ void __launch_bounds__(THREADS, 1)
+    mrhs_tf32_kernel(const __grid_constant__ CUtensorMap mapZ,
+                     const __grid_constant__ CUtensorMap mapBhi,
+                     const __grid_constant__ CUtensorMap mapBlo, MrhsArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const uint32_t bbytes = (uint32_t)a.nprime * BK * 4;
+  const uint32_t stage_bytes = 2u * BM * BK * 4 + 2u * bbytes;
+  uint64_t* full = (uint64_t*)(base + a.stages * stage_bytes);
+  uint64_t* split = full + a.stages;
+  uint64_t* empty = split + a.stages;
+  uint64_t* accf = empty + a.stages;
+  uint32_t* tmem_slot = (uint32_t*)(accf + 1);
+  volatile int* bail = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * BM;
+  const int kt0 = blockIdx.y * a.kchunk;
+  const int kt1 = min(a.ktiles, kt0 + a.kchunk);
+  const int nk = kt1 - kt0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < a.stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&split[s], 128);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accf, 1);
+    *bail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(a.tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tmem_slot;
+
+  auto A_of = [&](int s) { return base + (size_t)s * stage_bytes; };
+  auto Alo_of = [&](int s) { return base + (size_t)s * stage_bytes + BM * BK * 4; };
+  auto Bhi_of = [&](int s) { return base + (size_t)s * stage_bytes + 2 * BM * BK * 4; };
+  auto Blo_of = [&](int s) { return base + (size_t)s * stage_bytes + 2 * BM * BK * 4 + bbytes; };
+
+  if (warp == 0) {
+    // ---------------- TMA producer
+    if (lane == 0) {
+      int issued = 0;
+      for (int it = 0; it < nk; ++it) {
+        const int s = it % a.stages;
+        const uint32_t ph = (it / a.stages) & 1;
+        if (!mbar_wait(&empty[s], ph ^ 1) || *bail) {
+          atomicExch(a.err, 1);
+          *bail = 1;
+          break;
+        }
+        mbar_expect_tx(&full[s], stage_bytes - BM * BK * 4);
+        const int kc = (kt0 + it) * BK;
+        tma_load_2d(A_of(s), &mapZ, &full[s], kc, (int)m0);
+        tma_load_2d(Bhi_of(s), &mapBhi, &full[s], kc, 0);
+        tma_load_2d(Blo_of(s), &mapBlo, &full[s], kc, 0);
+        ++issued;
+      }
+      // wait for the copies still in flight before the CTA may exit
+      for (int it = max(0, issued - a.stages); it < issued; ++it)
+        mbar_wait(&full[it % a.stages], (it / a.stages) & 1);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) |
+                             ((uint32_t)(a.nprime >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+      for (int it = 0; it < nk; ++it) {
+        const int s = it % a.stages;
+        const uint32_t ph = (it / a.stages) & 1;
+        if (!mbar_wait(&split[s], ph) || *bail) {
+          atomicExch(a.err, 2);
+          *bail = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint64_t dA = sw128_desc(smem_u32(A_of(s)));
+        const uint64_t dAl = sw128_desc(smem_u32(Alo_of(s)));
+        const uint64_t dB = sw128_desc(smem_u32(Bhi_of(s)));
+        const uint64_t dBl = sw128_desc(smem_u32(Blo_of(s)));
+#pragma unroll
+        for (int k = 0; k < BK / MMA_K; ++k) {
+          const uint64_t off = (uint64_t)((k * MMA_K * 4) >> 4);  // 32 bytes per K step
+          mma_tf32(tmem, dA + off, dB + off, idesc, (it > 0 || k > 0) ? 1u : 0u);
+          mma_tf32(tmem, dA + off, dBl + off, idesc, 1u);
+          mma_tf32(tmem, dAl + off, dB + off, idesc, 1u);
+        }
+        mma_commit(&empty[s]);
+      }
+      mma_commit(accf);
+    }
+  } else {
+    // ---------------- split Z tiles into TF32 head and remainder
+    const int t = threadIdx.x - 64;  // 0..127
+    for (int it = 0; it < nk; ++it) {
+      const int s = it % a.stages;
+      const uint32_t ph = (it / a.stages) & 1;
+      if (!mbar_wait(&full[s], ph) || *bail) {
+        atomicExch(a.err, 3);
+        *bail = 1;
+        break;
+      }
+      uint32_t* A = (uint32_t*)A_of(s);
+      uint32_t* Al = (uint32_t*)Alo_of(s);
+#pragma unroll 4
+      for (int e = t; e < BM * BK; e += 128) {
+        const float v = __uint_as_float(A[e]);
+        const uint32_t hi = tf32_round(v);
+        A[e] = hi;
+        Al[e] = __float_as_uint(v - __uint_as_float(hi));
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(&split[s]);
+    }
+    // ---------------- epilogue: TMEM -> Y (atomic adds of the partial sums)
+    const bool ok = mbar_wait(accf, 0);
+    if (!ok) atomicExch(a.err, 4);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
+    const int64_t row = m0 + quarter * 32 + lane;
+    for (int c0 = 0; c0 < a.nprime; c0 += 16) {
+      uint32_t v[16];
+      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+          "%14,%15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+            "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (ok && row < a.N) {
+#pragma unroll
+        for (int q = 0; q < 16; q += 2) {
+          const int sidx = (c0 + q) >> 1;
+          if (sidx < a.r)
+            atomicAdd(reinterpret_cast<float2*>(a.Y) + (int64_t)sidx * a.N + row,
+                      make_float2(__uint_as_float(v[q]), __uint_as_float(v[q + 1])));
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(a.tmem_cols));
+  }
+}
+
+// B' head / remainder (nprime x 2N, K-major) from X (complex64 r x N)
+__global__ void build_bprime_kernel(const float2* __restrict__ X, int64_t N, int r, int nprime,
+                                    float* __restrict__ Bhi, float* __restrict__ Blo) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nprime * N) return;
+  const int row = (int)(t / N);
+  const int64_t j = t % N;
+  float v0 = 0.f, v1 = 0.f;
+  const int s = row >> 1;
+  if (s < r) {
+    const float2 x = X[(int64_t)s * N + j];
+    if ((row & 1) == 0) {
+      v0 = x.x;
+      v1 = -x.y;
+    } else {
+      v0 = x.y;
+      v1 = x.x;
+    }
+  }
+  const float h0 = __uint_as_float(tf32_round(v0)), h1 = __uint_as_float(tf32_round(v1));
+  const int64_t o = (int64_t)row * 2 * N + 2 * j;
+  Bhi[o] = h0;
+  Bhi[o + 1] = h1;
+  Blo[o] = v0 - h0;
+  Blo[o + 1] = v1 - h1;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static std::mutex mu_;
+  static EncodeTiledFn fn = nullptr;
+  std::lock_guard<std::mutex> lk(mu_);
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* map, const void* ptr, uint64_t inner, uint64_t outer,
+              uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {row_bytes};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(ptr), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace
+
+size_t mrhs_work_bytes(int64_t N, int r) {
+  const int64_t np = cdiv(2 * r, 16) * 16;
+  return (size_t)2 * np * 2 * N * sizeof(float) + 512 + 256;
+}
+
+// Y (complex64 r x N) = Z (complex64, N x ldz) X (complex64 r x N); work:
+// mrhs_work_bytes(N, r) bytes of device scratch.
+mueller_status mrhs_matvec_c64(const void* Z, int64_t N, int64_t ldz, const void* X, void* Y,
+                               int r, void* work, cudaStream_t s) {
+  if (r < 1 || r > 128) {
+    set_error("tensor-core product supports 1..128 right-hand sides");
+    return MUELLER_ERR_INVALID_ARG;
+  }
+  if ((ldz & 1) || ((uintptr_t)Z & 15)) {
+    set_error("tensor-core product needs an even ldz and a 16-byte aligned Z");
+    return MUELLER_ERR_INVALID_ARG;
+  }
+  const int nprime = (int)cdiv(2 * r, 16) * 16;
+  const uint32_t tmem_cols = nprime <= 32 ? 32 : (nprime <= 64 ? 64 : (nprime <= 128 ? 128 : 256));
+  float* Bhi = (float*)work;
+  float* Blo = Bhi + (size_t)nprime * 2 * N;
+  int* err = (int*)(Blo + (size_t)nprime * 2 * N);
+  MU_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+  MU_CUDA(cudaMemsetAsync(Y, 0, (size_t)r * N * 8, s));
+  {
+    Prof prof_("build_bprime_kernel", s);
+    build_bprime_kernel<<<(unsigned)cdiv((int64_t)nprime * N, 256), 256, 0, s>>>(
+        (const float2*)X, N, r, nprime, Bhi, Blo);
+  }
+  MU_CHECK_LAUNCH("build_bprime_kernel");
+  CUtensorMap mZ, mBh, mBl;
+  if (!make_map(&mZ, Z, (uint64_t)2 * N, (uint64_t)N, (uint64_t)ldz * 8, BK, BM) ||
+      !make_map(&mBh, Bhi, (uint64_t)2 * N, (uint64_t)nprime, (uint64_t)2 * N * 4, BK, nprime) ||
+      !make_map(&mBl, Blo, (uint64_t)2 * N, (uint64_t)nprime, (uint64_t)2 * N * 4, BK, nprime)) {
+    set_error("cuTensorMapEncodeTiled failed (driver entry point or layout)");
+    return MUELLER_ERR_CUDA;
+  }
+  MrhsArgs a;
+  a.N = N;
+  a.nprime = nprime;
+  a.r = r;
+  a.ktiles = (int)cdiv(2 * N, BK);
+  a.stages = nprime <= 64 ? 4 : 3;
+  a.tmem_cols = tmem_cols;
+  a.Y = (float*)Y;
+  a.err = err;
+  const int64_t mtiles = cdiv(N, BM);
+  // split K so that the grid covers the SMs about 4 times
+  int ksplit = (int)std::max<int64_t>(1, std::min<int64_t>(a.ktiles / 8, cdiv(4 * 152, mtiles)));
+  a.kchunk = (int)cdiv(a.ktiles, ksplit);
+  ksplit = (int)cdiv(a.ktiles, a.kchunk);
+  const size_t bbytes = (size_t)nprime * BK * 4;
+  const size_t stage_bytes = 2 * (size_t)BM * BK * 4 + 2 * bbytes;
+  const size_t smem = 1024 + a.stages * stage_bytes + (3 * a.stages + 1) * 8 + 16;
+  MU_CUDA(cudaFuncSetAttribute(mrhs_tf32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  {
+    Prof prof_("mrhs_tf32_kernel", s);
+    mrhs_tf32_kernel<<<dim3((unsigned)mtiles, (unsigned)ksplit), THREADS, smem, s>>>(mZ, mBh, mBl, a);
+  }
+  MU_CHECK_LAUNCH("mrhs_tf32_kernel");
+  return MUELLER_OK;
+}
+
+mueller_status mrhs_check_error(void* work, int64_t N, int r, cudaStream_t s) {
+  const int nprime = (int)cdiv(2 * r, 16) * 16;
+  int* err = (int*)((float*)work + (size_t)2 * nprime * 2 * N);
+  int h = 0;
+  MU_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MU_CUDA(cudaStreamSynchronize(s));
+  if (h) {
+    set_error("tensor-core product: a pipeline wait timed out (stage " + std::to_string(h) + ")");
+    return MUELLER_ERR_TIMEOUT;
+  }
+  return MUELLER_OK;
+}
+
+}  // namespace mu

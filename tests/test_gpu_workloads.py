@@ -54,12 +54,13 @@ def test_level4_plasmonic_sphere_16_rhs():
     rel = (torch.linalg.norm(R, dim=1) / torch.linalg.norm(B, dim=1)).max().item()
     assert rel <= 1e-8, rel
     _, xs = mu.far_field(m, p, X, inc)
-    # a sphere: every incidence gives the same cross sections
-    assert np.ptp(xs[:, 0]) <= 1e-3 * xs[0, 0]
+    # a sphere: every incidence gives the same cross sections, up to the
+    # discretisation (the mesh and the frame are not rotation invariant)
+    assert np.ptp(xs[:, 0]) <= 2e-2 * xs[0, 0]
     # energy balance and Mie, to discretisation accuracy
     assert np.abs(xs[:, 0] - xs[:, 1] - xs[:, 2]).max() <= 0.05 * xs[0, 0]
     ref = mie.mie_bh(w["ka"], complex(*w["eps_r"]))
-    assert abs(xs[:, 0].mean() - ref[0]) <= 0.1 * ref[0], (xs[:, 0].mean(), ref)
+    assert abs(xs[:, 0].mean() - ref[0]) <= 0.05 * ref[0], (xs[:, 0].mean(), ref)
 
 
 def test_small_sphere_matches_mie_with_polar_frames():
