@@ -703,6 +703,256 @@ __global__ void scale_copy_kernel(const AT* __restrict__ a, BT2* __restrict__ b,
   b[i].y = (R)(a[i].y * inv);
 }
 
+// ===================================================== lockstep multi-RHS GMRES
+// r right-hand sides advance together; vectors are stored RHS-major
+// ([s][N]) and the Krylov basis as V[j][s][N].  blockIdx.y (or .z) is s.
+
+// partial dots conj(V_l[s]) . w[s] over G chunks: part[(s*(m1) + l)*G + g]
+__global__ void __launch_bounds__(256) dots_b_kernel(const float2* __restrict__ V, int64_t N, int r,
+                                                     int nl, int m1, const float2* __restrict__ w,
+                                                     double2* __restrict__ part, int G) {
+  const int g = blockIdx.x, l = blockIdx.y, s = blockIdx.z;
+  const float2* v = V + ((int64_t)l * r + s) * N;
+  const float2* ww = w + (int64_t)s * N;
+  double sr = 0, si = 0;
+  for (int64_t i = (int64_t)g * blockDim.x + threadIdx.x; i < N; i += (int64_t)G * blockDim.x) {
+    const float2 a = v[i], b = ww[i];
+    sr += (double)a.x * b.x + (double)a.y * b.y;
+    si += (double)a.x * b.y - (double)a.y * b.x;
+  }
+  __shared__ double rr[256], ri[256];
+  rr[threadIdx.x] = sr;
+  ri[threadIdx.x] = si;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      rr[threadIdx.x] += rr[threadIdx.x + o];
+      ri[threadIdx.x] += ri[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[((int64_t)s * m1 + l) * G + g] = make_double2(rr[0], ri[0]);
+}
+
+// w[s] -= sum_l h[s][l] V_l[s], h from the partials; hacc[s][l] += h
+__global__ void __launch_bounds__(256) orth_b_kernel(const float2* __restrict__ V, int64_t N, int r,
+                                                     int nl, int m1, const double2* __restrict__ part,
+                                                     int G, float2* __restrict__ w,
+                                                     double2* __restrict__ hacc) {
+  const int s = blockIdx.y;
+  __shared__ double2 h[128];
+  for (int l = threadIdx.x; l < nl; l += blockDim.x) {
+    double2 a = make_double2(0, 0);
+    for (int g = 0; g < G; ++g) {
+      const double2 q = part[((int64_t)s * m1 + l) * G + g];
+      a.x += q.x;
+      a.y += q.y;
+    }
+    h[l] = a;
+    if (blockIdx.x == 0) {
+      hacc[(int64_t)s * (m1 + 1) + l].x += a.x;
+      hacc[(int64_t)s * (m1 + 1) + l].y += a.y;
+    }
+  }
+  __syncthreads();
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  float2* wp = w + (int64_t)s * N + i;
+  double ar = wp->x, ai = wp->y;
+  for (int l = 0; l < nl; ++l) {
+    const float2 v = V[((int64_t)l * r + s) * N + i];
+    ar -= h[l].x * v.x - h[l].y * v.y;
+    ai -= h[l].x * v.y + h[l].y * v.x;
+  }
+  *wp = make_float2((float)ar, (float)ai);
+}
+
+template <class VT>
+__global__ void __launch_bounds__(256) nrm2_b_kernel(const VT* __restrict__ w, int64_t N,
+                                                     double* __restrict__ part, int G) {
+  const int s = blockIdx.y;
+  const VT* ws = w + (int64_t)s * N;
+  double a = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)G * blockDim.x)
+    a += (double)ws[i].x * ws[i].x + (double)ws[i].y * ws[i].y;
+  __shared__ double red[256];
+  red[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[(int64_t)s * G + blockIdx.x] = red[0];
+}
+
+// nrm[s] = sqrt(sum of partials) * mask[s]  (mask 0 freezes a right-hand side)
+__global__ void norm_finish_b_kernel(const double* __restrict__ part, int G, int r,
+                                     const int* __restrict__ mask, double* __restrict__ nrm) {
+  const int s = threadIdx.x + blockIdx.x * blockDim.x;
+  if (s >= r) return;
+  double a = 0;
+  for (int g = 0; g < G; ++g) a += part[(int64_t)s * G + g];
+  nrm[s] = (mask && !mask[s]) ? 0.0 : sqrt(a);
+}
+
+// out[s] = w[s] / nrm[s]  (0 if nrm[s] == 0)
+template <class IT, class OT>
+__global__ void scale_b_kernel(const IT* __restrict__ w, int64_t N, const double* __restrict__ nrm,
+                               OT* __restrict__ out) {
+  const int s = blockIdx.y;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double n = nrm[s];
+  const double inv = n > 0 ? 1.0 / n : 0.0;
+  const IT a = w[(int64_t)s * N + i];
+  out[(int64_t)s * N + i].x = (decltype(out[0].x))(a.x * inv);
+  out[(int64_t)s * N + i].y = (decltype(out[0].x))(a.y * inv);
+}
+
+// Givens step of column j for every right-hand side (thread s)
+__global__ void givens_b_kernel(int j, int m, int r, double2* __restrict__ hacc,
+                                const double* __restrict__ hn, double2* __restrict__ Hm,
+                                double* __restrict__ cs, double2* __restrict__ sn,
+                                double2* __restrict__ g, double* __restrict__ res) {
+  const int s = threadIdx.x + blockIdx.x * blockDim.x;
+  if (s >= r) return;
+  double2* ha = hacc + (int64_t)s * (m + 2);
+  double2* col = Hm + ((int64_t)s * m + j) * (m + 1);
+  double* c_ = cs + (int64_t)s * (m + 1);
+  double2* s_ = sn + (int64_t)s * (m + 1);
+  double2* gg = g + (int64_t)s * (m + 1);
+  for (int l = 0; l <= j; ++l) col[l] = ha[l];
+  col[j + 1] = make_double2(hn[s], 0.0);
+  for (int l = 0; l < j; ++l) {
+    const double2 a = col[l], b = col[l + 1];
+    const double c = c_[l];
+    const double2 sv = s_[l];
+    col[l] = make_double2(c * a.x + sv.x * b.x - sv.y * b.y, c * a.y + sv.x * b.y + sv.y * b.x);
+    col[l + 1] = make_double2(-(sv.x * a.x + sv.y * a.y) + c * b.x, -(sv.x * a.y - sv.y * a.x) + c * b.y);
+  }
+  const double2 a = col[j], b = col[j + 1];
+  const double aa = hypot(a.x, a.y), bb = hypot(b.x, b.y);
+  const double rho = hypot(aa, bb);
+  double c;
+  double2 sv;
+  if (aa == 0.0) {
+    c = 0.0;
+    sv = make_double2(1.0, 0.0);
+  } else {
+    c = aa / rho;
+    const double2 ph = make_double2(a.x / aa, a.y / aa);
+    sv = make_double2((ph.x * b.x + ph.y * b.y) / rho, (ph.y * b.x - ph.x * b.y) / rho);
+  }
+  c_[j] = c;
+  s_[j] = sv;
+  col[j] = make_double2(c * a.x + sv.x * b.x - sv.y * b.y, c * a.y + sv.x * b.y + sv.y * b.x);
+  col[j + 1] = make_double2(0, 0);
+  const double2 gj = gg[j];
+  gg[j] = make_double2(c * gj.x, c * gj.y);
+  gg[j + 1] = make_double2(-(sv.x * gj.x + sv.y * gj.y), -(sv.x * gj.y - sv.y * gj.x));
+  res[s] = hypot(gg[j + 1].x, gg[j + 1].y);
+  for (int l = 0; l <= j + 1; ++l) ha[l] = make_double2(0, 0);
+}
+
+// g[s] = beta[s] e1
+__global__ void set_first_b_kernel(double2* __restrict__ g, int m, int r,
+                                   const double* __restrict__ beta) {
+  const int s = threadIdx.x + blockIdx.x * blockDim.x;
+  if (s >= r) return;
+  for (int l = 0; l <= m; ++l) g[(int64_t)s * (m + 1) + l] = make_double2(0, 0);
+  g[(int64_t)s * (m + 1)] = make_double2(beta[s], 0.0);
+}
+
+// y[s] = H_s(0:k,0:k)^{-1} g[s] with k = kk[s] (0: no update)
+__global__ void backsub_b_kernel(int m, int r, const int* __restrict__ kk,
+                                 const double2* __restrict__ Hm, const double2* __restrict__ g,
+                                 double2* __restrict__ y) {
+  const int s = threadIdx.x + blockIdx.x * blockDim.x;
+  if (s >= r) return;
+  const int k = kk[s];
+  double2* ys = y + (int64_t)s * (m + 1);
+  for (int l = 0; l <= m; ++l) ys[l] = make_double2(0, 0);
+  const double2* H = Hm + (int64_t)s * m * (m + 1);
+  for (int i = k - 1; i >= 0; --i) {
+    double2 a = g[(int64_t)s * (m + 1) + i];
+    for (int l = i + 1; l < k; ++l) {
+      const double2 h = H[(int64_t)l * (m + 1) + i];
+      a.x -= h.x * ys[l].x - h.y * ys[l].y;
+      a.y -= h.x * ys[l].y + h.y * ys[l].x;
+    }
+    ys[i] = cdiv2(a, H[(int64_t)i * (m + 1) + i]);
+  }
+}
+
+// u[s] = sum_{l < kmax} y[s][l] V_l[s]
+__global__ void combine_b_kernel(const float2* __restrict__ V, int64_t N, int r, int kmax, int m,
+                                 const double2* __restrict__ y, float2* __restrict__ u) {
+  const int s = blockIdx.y;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double ar = 0, ai = 0;
+  for (int l = 0; l < kmax; ++l) {
+    const double2 c = y[(int64_t)s * (m + 1) + l];
+    const float2 v = V[((int64_t)l * r + s) * N + i];
+    ar += c.x * v.x - c.y * v.y;
+    ai += c.x * v.y + c.y * v.x;
+  }
+  u[(int64_t)s * N + i] = make_float2((float)ar, (float)ai);
+}
+
+// w[s] = b[s] - w[s]  (complex64)
+__global__ void resid_b_kernel(const float2* __restrict__ b, float2* __restrict__ w, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  w[i] = make_float2(b[i].x - w[i].x, b[i].y - w[i].y);
+}
+
+// x[s] += alpha[s] u[s]  (x complex128 or complex64, u complex64)
+template <class XT>
+__global__ void axpy_b_kernel(XT* __restrict__ x, const float2* __restrict__ u, int64_t N,
+                              const double* __restrict__ alpha) {
+  const int s = blockIdx.y;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double a = alpha ? alpha[s] : 1.0;
+  XT* xp = x + (int64_t)s * N + i;
+  const float2 v = u[(int64_t)s * N + i];
+  xp->x = (decltype(x[0].x))(xp->x + a * v.x);
+  xp->y = (decltype(x[0].x))(xp->y + a * v.y);
+}
+
+// z = P^{-1} v for r vectors (complex64 inverses)
+__global__ void __launch_bounds__(256) mbj_apply_b_kernel(const float2* __restrict__ inv, int64_t d,
+                                                          const int32_t* __restrict__ sz, int64_t B,
+                                                          int64_t H, int64_t N,
+                                                          const float2* __restrict__ v,
+                                                          float2* __restrict__ z) {
+  const int b = blockIdx.y, s = blockIdx.z;
+  const int n = sz[b], half = n / 2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * 8 + warp;
+  if (i >= n) return;
+  const int64_t o = (int64_t)b * B;
+  const float2* row = inv + (int64_t)b * d * d + i * d;
+  const float2* vs = v + (int64_t)s * N;
+  float ar = 0, ai = 0;
+  for (int j = lane; j < n; j += 32) {
+    const int64_t gj = j < half ? o + j : H + o + (j - half);
+    const float2 x = vs[gj], m = row[j];
+    ar = fmaf(m.x, x.x, fmaf(-m.y, x.y, ar));
+    ai = fmaf(m.x, x.y, fmaf(m.y, x.x, ai));
+  }
+#pragma unroll
+  for (int q = 16; q > 0; q >>= 1) {
+    ar += __shfl_xor_sync(0xffffffffu, ar, q);
+    ai += __shfl_xor_sync(0xffffffffu, ai, q);
+  }
+  if (lane == 0) {
+    const int64_t gi = i < half ? o + i : H + o + (i - half);
+    z[(int64_t)s * N + gi] = make_float2(ar, ai);
+  }
+}
+
 // RHS block transposes: dir 0: T[i][k] = B[k][i]; dir 1: X[k][i] = T[i][k]
 __global__ void transpose_rhs_kernel(const double2* __restrict__ a, double2* __restrict__ b,
                                      int64_t N, int r, int dir) {
@@ -1119,6 +1369,265 @@ done:
 
 }  // namespace
 
+// ----------------------------------------------------------------------
+// Mixed-precision solve of r right-hand sides: complex64 GMRES(m) with all
+// r systems advancing in lockstep (one product with Z per Arnoldi step for
+// all of them: tensor cores for r >= 2), right preconditioned by the
+// complex64 block-Jacobi inverses, inside FP64 iterative refinement on the
+// stored operator.
+struct LockWork {
+  int64_t N;
+  int r, m, G;
+  float2 *V, *W, *Zt, *U, *rhs32, *d32;
+  double2 *r64, *y64;
+  double2 *Hm, *hacc, *part, *sn, *g, *y;
+  double *npart, *cs, *bn, *beta, *hn, *res, *rn, *alpha;
+  int *mask, *kk;
+  void* mwork;
+};
+
+static size_t lock_bytes(int64_t N, int r, int m) {
+  const int G = 16;
+  size_t b = 0;
+  auto add = [&](size_t x) { b += (x + 255) & ~size_t(255); };
+  add((size_t)(m + 1) * r * N * 8);
+  for (int k = 0; k < 6; ++k) add((size_t)r * N * 8);
+  add((size_t)r * N * 16);
+  add((size_t)r * N * 16);
+  add((size_t)r * m * (m + 1) * 16);
+  add((size_t)r * (m + 2) * 16);
+  add((size_t)r * (m + 1) * G * 16);
+  for (int k = 0; k < 3; ++k) add((size_t)r * (m + 1) * 16);
+  add((size_t)r * G * 8);
+  add((size_t)r * (m + 1) * 8);
+  for (int k = 0; k < 6; ++k) add((size_t)r * 8);
+  add((size_t)r * 4);
+  add((size_t)r * 4);
+  if (r >= 2) add(mrhs_work_bytes(N, r));
+  return b + 1024;
+}
+
+static LockWork carve_lock(char* p, int64_t N, int r, int m) {
+  LockWork W;
+  W.N = N;
+  W.r = r;
+  W.m = m;
+  W.G = 16;
+  auto take = [&](size_t x) {
+    char* q = p;
+    p += (x + 255) & ~size_t(255);
+    return (void*)q;
+  };
+  W.V = (float2*)take((size_t)(m + 1) * r * N * 8);
+  W.W = (float2*)take((size_t)r * N * 8);
+  W.Zt = (float2*)take((size_t)r * N * 8);
+  W.U = (float2*)take((size_t)r * N * 8);
+  W.rhs32 = (float2*)take((size_t)r * N * 8);
+  W.d32 = (float2*)take((size_t)r * N * 8);
+  take((size_t)r * N * 8);
+  W.r64 = (double2*)take((size_t)r * N * 16);
+  W.y64 = (double2*)take((size_t)r * N * 16);
+  W.Hm = (double2*)take((size_t)r * m * (m + 1) * 16);
+  W.hacc = (double2*)take((size_t)r * (m + 2) * 16);
+  W.part = (double2*)take((size_t)r * (m + 1) * W.G * 16);
+  W.sn = (double2*)take((size_t)r * (m + 1) * 16);
+  W.g = (double2*)take((size_t)r * (m + 1) * 16);
+  W.y = (double2*)take((size_t)r * (m + 1) * 16);
+  W.npart = (double*)take((size_t)r * W.G * 8);
+  W.cs = (double*)take((size_t)r * (m + 1) * 8);
+  W.bn = (double*)take((size_t)r * 8);
+  W.beta = (double*)take((size_t)r * 8);
+  W.hn = (double*)take((size_t)r * 8);
+  W.res = (double*)take((size_t)r * 8);
+  W.rn = (double*)take((size_t)r * 8);
+  W.alpha = (double*)take((size_t)r * 8);
+  W.mask = (int*)take((size_t)r * 4);
+  W.kk = (int*)take((size_t)r * 4);
+  W.mwork = r >= 2 ? take(mrhs_work_bytes(N, r)) : nullptr;
+  return W;
+}
+
+// complex64 product of the stored operator for the r vectors of X
+static mueller_status lock_matvec(const InnerOp& I, const LockWork& W, const float2* X, float2* Y,
+                                  cudaStream_t s) {
+  const mueller_mesh* m = I.op->mesh;
+  const int64_t N = W.N;
+  if (W.r >= 2) {
+    mueller_status st = mrhs_matvec_c64(I.op->Z_dev, N, I.op->ldz, X, Y, W.r, W.mwork, s);
+    if (st) return st;
+  } else {
+    { Prof prof_("gemv_c64_kernel<float>", s); gemv_c64_kernel<float><<<dim3(nblk(N, 16), 1), 256, 0, s>>>(N, (const float4*)I.op->Z_dev, I.op->ldz, X, Y, N, N, 1); }
+    MU_CHECK_LAUNCH("gemv_c64_kernel<float>");
+  }
+  return near_apply_c64(m, I.op->near_dev, X, Y, W.r, s);
+}
+
+static mueller_status lock_precond(const InnerOp& I, const LockWork& W, const float2* v, float2* z,
+                                   cudaStream_t s) {
+  if (!I.op->precond_dev) {
+    MU_CUDA(cudaMemcpyAsync(z, v, (size_t)W.r * W.N * 8, cudaMemcpyDeviceToDevice, s));
+    return MUELLER_OK;
+  }
+  dim3 g(nblk(I.L.d, 8), I.L.nb, W.r);
+  { Prof prof_("mbj_apply_b_kernel", s); mbj_apply_b_kernel<<<g, 256, 0, s>>>(I.inv32, I.L.d, I.sz_dev, I.L.B, I.L.H, W.N, v, z); }
+  MU_CHECK_LAUNCH("mbj_apply_b_kernel");
+  return MUELLER_OK;
+}
+
+// norms of the r vectors of w (type VT) into dst (device, r doubles); mask optional
+template <class VT>
+static mueller_status lock_norms(const LockWork& W, const VT* w, double* dst, const int* mask,
+                                 cudaStream_t s) {
+  { Prof prof_("nrm2_b_kernel", s); nrm2_b_kernel<VT><<<dim3(W.G, W.r), 256, 0, s>>>(w, W.N, W.npart, W.G); }
+  { Prof prof_("norm_finish_b_kernel", s); norm_finish_b_kernel<<<nblk(W.r, 64), 64, 0, s>>>(W.npart, W.G, W.r, mask, dst); }
+  MU_CHECK_LAUNCH("lock_norms");
+  return MUELLER_OK;
+}
+
+// inner GMRES on rhs32 (r unit-norm vectors) -> d32; tol relative to 1
+static mueller_status lock_gmres(const InnerOp& I, LockWork& W, double tol, int maxit, int& iters,
+                                 int& restarts, double* hbuf, std::vector<int>& active,
+                                 cudaStream_t s) {
+  const int64_t N = W.N;
+  const int r = W.r, m = W.m, G = W.G;
+  std::vector<int> kk(r), mask(r);
+  std::vector<double> beta(r), bn(r, 1.0);
+  mueller_status st = MUELLER_OK;
+  MU_CUDA(cudaMemsetAsync(W.d32, 0, (size_t)r * N * 8, s));
+  for (int cycle = 0; iters < maxit; ++cycle) {
+    // residual of the inner system: w = rhs - A d
+    if ((st = lock_matvec(I, W, W.d32, W.W, s))) return st;
+    { Prof prof_("resid_b_kernel", s); resid_b_kernel<<<nblk((int64_t)r * N, 256), 256, 0, s>>>(W.rhs32, W.W, (int64_t)r * N); }
+    for (int k = 0; k < r; ++k) mask[k] = active[k];
+    MU_CUDA(cudaMemcpyAsync(W.mask, mask.data(), r * 4, cudaMemcpyHostToDevice, s));
+    if ((st = lock_norms<float2>(W, W.W, W.beta, W.mask, s))) return st;
+    MU_CUDA(cudaMemcpyAsync(hbuf, W.beta, r * 8, cudaMemcpyDeviceToHost, s));
+    MU_CUDA(cudaStreamSynchronize(s));
+    bool any = false;
+    for (int k = 0; k < r; ++k) {
+      beta[k] = hbuf[k];
+      if (active[k] && beta[k] <= tol) active[k] = 0;
+      if (active[k]) any = true;
+    }
+    if (!any) break;
+    for (int k = 0; k < r; ++k) mask[k] = active[k];
+    MU_CUDA(cudaMemcpyAsync(W.mask, mask.data(), r * 4, cudaMemcpyHostToDevice, s));
+    if ((st = lock_norms<float2>(W, W.W, W.beta, W.mask, s))) return st;
+    { Prof prof_("scale_b_kernel", s); scale_b_kernel<float2, float2><<<dim3(nblk(N, 256), r), 256, 0, s>>>(W.W, N, W.beta, W.V); }
+    { Prof prof_("set_first_b_kernel", s); set_first_b_kernel<<<nblk(r, 64), 64, 0, s>>>(W.g, m, r, W.beta); }
+    MU_CUDA(cudaMemsetAsync(W.hacc, 0, (size_t)r * (m + 2) * 16, s));
+    std::fill(kk.begin(), kk.end(), 0);
+    int jlast = 0;
+    for (int j = 0; j < m && iters < maxit; ++j) {
+      const float2* Vj = W.V + (int64_t)j * r * N;
+      if ((st = lock_precond(I, W, Vj, W.Zt, s))) return st;
+      if ((st = lock_matvec(I, W, W.Zt, W.W, s))) return st;
+      for (int pass = 0; pass < 2; ++pass) {
+        { Prof prof_("dots_b_kernel", s); dots_b_kernel<<<dim3(G, j + 1, r), 256, 0, s>>>(W.V, N, r, j + 1, m + 1, W.W, W.part, G); }
+        { Prof prof_("orth_b_kernel", s); orth_b_kernel<<<dim3(nblk(N, 256), r), 256, 0, s>>>(W.V, N, r, j + 1, m + 1, W.part, G, W.W, W.hacc); }
+      }
+      if ((st = lock_norms<float2>(W, W.W, W.hn, nullptr, s))) return st;
+      { Prof prof_("scale_b_kernel", s); scale_b_kernel<float2, float2><<<dim3(nblk(N, 256), r), 256, 0, s>>>(W.W, N, W.hn, W.V + (int64_t)(j + 1) * r * N); }
+      { Prof prof_("givens_b_kernel", s); givens_b_kernel<<<nblk(r, 64), 64, 0, s>>>(j, m, r, W.hacc, W.hn, W.Hm, W.cs, W.sn, W.g, W.res); }
+      MU_CHECK_LAUNCH("lockstep Arnoldi step");
+      ++iters;
+      jlast = j;
+      MU_CUDA(cudaMemcpyAsync(hbuf, W.res, r * 8, cudaMemcpyDeviceToHost, s));
+      MU_CUDA(cudaStreamSynchronize(s));
+      bool all = true;
+      for (int k = 0; k < r; ++k) {
+        if (!active[k]) continue;
+        if (kk[k] == 0 && (hbuf[k] <= tol || !(hbuf[k] == hbuf[k]))) kk[k] = j + 1;
+        if (kk[k] == 0) all = false;
+      }
+      if (all) break;
+    }
+    int kmax = 0;
+    for (int k = 0; k < r; ++k) {
+      if (!active[k]) kk[k] = 0;
+      else if (kk[k] == 0) kk[k] = jlast + 1;
+      kmax = std::max(kmax, kk[k]);
+    }
+    MU_CUDA(cudaMemcpyAsync(W.kk, kk.data(), r * 4, cudaMemcpyHostToDevice, s));
+    { Prof prof_("backsub_b_kernel", s); backsub_b_kernel<<<nblk(r, 64), 64, 0, s>>>(m, r, W.kk, W.Hm, W.g, W.y); }
+    { Prof prof_("combine_b_kernel", s); combine_b_kernel<<<dim3(nblk(N, 256), r), 256, 0, s>>>(W.V, N, r, kmax, m, W.y, W.U); }
+    if ((st = lock_precond(I, W, W.U, W.Zt, s))) return st;
+    { Prof prof_("axpy_b_kernel<float2>", s); axpy_b_kernel<float2><<<dim3(nblk(N, 256), r), 256, 0, s>>>(W.d32, W.Zt, N, nullptr); }
+    MU_CHECK_LAUNCH("lockstep update");
+    ++restarts;
+  }
+  return st;
+}
+
+static mueller_status solve_lockstep(const mueller_operator* op, const double2* B, double2* X,
+                                     int r, const mueller_solver_opts* o, mueller_solve_info* info,
+                                     char* p, cudaStream_t s) {
+  const mueller_mesh* m = op->mesh;
+  const int64_t N = 4 * m->nn;
+  const int mres = std::max(1, std::min(120, (int)o->restart));
+  InnerOp I;
+  I.op = op;
+  I.near32 = nullptr;
+  I.inv32 = op->precond_dev ? (const float2*)op->precond_dev : nullptr;
+  I.sz_dev = nullptr;
+  if (op->precond_dev) {
+    I.L = layout(N, op->block);
+    I.sz_dev = precond_sizes(op, I.L);
+  }
+  LockWork W = carve_lock(p, N, r, mres);
+  double* hbuf = nullptr;
+  MU_CUDA(cudaMallocHost((void**)&hbuf, (size_t)std::max(8, 2 * r) * sizeof(double)));
+  mueller_status st = MUELLER_OK;
+  const int maxref = o->max_refine > 0 ? o->max_refine : 20;
+  const double itol = o->inner_tol > 0 ? o->inner_tol : 1e-5;
+  std::vector<double> bn(r), rn(r);
+  std::vector<int> active(r, 1);
+  int it_left = o->maxit;
+  if (!o->warm_start) MU_CUDA(cudaMemsetAsync(X, 0, (size_t)r * N * 16, s));
+  if ((st = lock_norms<double2>(W, B, W.bn, nullptr, s))) goto out;
+  MU_CUDA(cudaMemcpyAsync(hbuf, W.bn, r * 8, cudaMemcpyDeviceToHost, s));
+  MU_CUDA(cudaStreamSynchronize(s));
+  for (int k = 0; k < r; ++k) bn[k] = hbuf[k];
+  for (int ref = 0; ref <= maxref; ++ref) {
+    // FP64 residual on the stored operator
+    if ((st = op_matvec(op, X, W.y64, r, nullptr, 0, s))) goto out;
+    { Prof prof_("residual_kernel", s); residual_kernel<<<nblk((int64_t)r * N, 256), 256, 0, s>>>(B, W.y64, W.r64, (int64_t)r * N); }
+    if ((st = lock_norms<double2>(W, W.r64, W.rn, nullptr, s))) goto out;
+    MU_CUDA(cudaMemcpyAsync(hbuf, W.rn, r * 8, cudaMemcpyDeviceToHost, s));
+    MU_CUDA(cudaStreamSynchronize(s));
+    bool any = false;
+    double worst = 0;
+    for (int k = 0; k < r; ++k) {
+      rn[k] = hbuf[k];
+      const double rel = bn[k] > 0 ? rn[k] / bn[k] : 0.0;
+      worst = std::max(worst, rel);
+      active[k] = rel > o->tol;
+      any |= active[k] != 0;
+    }
+    info->relres = worst;
+    if (!any || it_left <= 0 || ref == maxref) break;
+    // inner system A d = r / ||r|| in complex64 for the active right-hand sides
+    { Prof prof_("scale_b_kernel", s); scale_b_kernel<double2, float2><<<dim3(nblk(N, 256), r), 256, 0, s>>>(W.r64, N, W.rn, W.rhs32); }
+    int it = 0, rs = 0;
+    st = lock_gmres(I, W, itol, it_left, it, rs, hbuf, active, s);
+    if (st) goto out;
+    it_left -= it;
+    info->iters += it * r;
+    info->restarts += rs;
+    info->refinements += 1;
+    // x += ||r|| d
+    MU_CUDA(cudaMemcpyAsync(W.alpha, W.rn, r * 8, cudaMemcpyDeviceToDevice, s));
+    { Prof prof_("axpy_b_kernel<double2>", s); axpy_b_kernel<double2><<<dim3(nblk(N, 256), r), 256, 0, s>>>(X, W.d32, N, W.alpha); }
+    MU_CHECK_LAUNCH("refinement update");
+  }
+  for (int k = 0; k < r; ++k)
+    if (bn[k] == 0 || rn[k] / bn[k] <= o->tol) info->converged++;
+  if (r >= 2 && !st) st = mrhs_check_error(W.mwork, N, r, s);
+out:
+  cudaFreeHost(hbuf);
+  return st;
+}
+
 size_t solve_work(const mueller_operator* op, int r, const mueller_solver_opts* o) {
   (void)r;
   const int64_t N = 4 * op->mesh->nn;
@@ -1130,9 +1639,7 @@ size_t solve_work(const mueller_operator* op, int r, const mueller_solver_opts* 
   if (o->mode == MUELLER_SOLVE_GMRES && op->dtype == MUELLER_C128) {
     b = gmres_bytes(N, m, 16);
   } else {
-    b = gmres_bytes(N, m, 8);
-    b += 4 * (size_t)N * 16 + 4 * (size_t)N * 8 + 256 * 8;  // r64, y64, d32, rhs32
-    b += (size_t)op->mesh->nnzb * 16 * 8 + 256;              // near complex64
+    b = lock_bytes(N, r, std::min(120, m));
   }
   return b + 4096;
 }
@@ -1238,77 +1745,7 @@ mueller_status solve(const mueller_operator* op, const void* Bv, void* Xv, int r
     }
     cudaFreeHost(W.hs);
   } else {
-    // complex64 inner GMRES on the stored operator, FP64 refinement residual
-    I.precision = 1;
-    const int64_t nnzb = m->nnzb;
-    auto take = [&](size_t bytes) {
-      char* q = p;
-      p += (bytes + 255) & ~size_t(255);
-      return (void*)q;
-    };
-    double2* r64 = (double2*)take(N * 16);
-    double2* y64 = (double2*)take(N * 16);
-    float2* d32 = (float2*)take(N * 8);
-    float2* rhs32 = (float2*)take(N * 8);
-    float2* near32 = nullptr;
-    float2* inv32 = nullptr;
-    if (op->dtype == MUELLER_C64_NEAR64) {
-      near32 = (float2*)take((size_t)nnzb * 16 * 8);
-      { Prof prof_("c128_to_c64_kernel", s); c128_to_c64_kernel<<<nblk(nnzb * 16, 256), 256, 0, s>>>((const double2*)op->near_dev, near32, nnzb * 16); }
-      MU_CHECK_LAUNCH("c128_to_c64");
-    }
-    if (op->precond_dev) inv32 = (float2*)op->precond_dev;  // complex64 inverses
-    I.near32 = near32;
-    I.inv32 = inv32;
-    GmresWork W = carve_gmres<float2>(p, N, mres);
-    double* hs = nullptr;
-    MU_CUDA(cudaMallocHost((void**)&hs, 8 * sizeof(double)));
-    W.hs = hs + 4;
-    const int maxref = o->max_refine > 0 ? o->max_refine : 20;
-    const double itol = o->inner_tol > 0 ? o->inner_tol : 1e-5;
-    for (int k = 0; k < r && !st; ++k) {
-      const double2* b = B + (int64_t)k * N;
-      double2* x = X + (int64_t)k * N;
-      if (!o->warm_start) MU_CUDA(cudaMemsetAsync(x, 0, N * 16, s));
-      double bn = 0, rel = 1.0;
-      int it_left = o->maxit;
-      { Prof prof_("nrm2_kernel<double2>", s); nrm2_kernel<double2><<<W.G, 256, 0, s>>>(b, N, W.npart, W.G); }
-      { Prof prof_("normalize_kernel<double2>", s); normalize_kernel<double2><<<1, 1, 0, s>>>(b, 0, W.npart, W.G, nullptr, W.scal + 4); }
-      MU_CUDA(cudaMemcpyAsync(hs, W.scal + 4, 8, cudaMemcpyDeviceToHost, s));
-      MU_CUDA(cudaStreamSynchronize(s));
-      bn = hs[0];
-      for (int ref = 0; ref <= maxref && !st; ++ref) {
-        // r = b - A x in FP64 (complex64 storage, FP64 arithmetic)
-        st = op_matvec(op, x, y64, 1, nullptr, 0, s);
-        if (st) break;
-        { Prof prof_("residual_kernel", s); residual_kernel<<<nblk(N, 256), 256, 0, s>>>(b, y64, r64, N); }
-        { Prof prof_("nrm2_kernel<double2>", s); nrm2_kernel<double2><<<W.G, 256, 0, s>>>(r64, N, W.npart, W.G); }
-        { Prof prof_("normalize_kernel<double2>", s); normalize_kernel<double2><<<1, 1, 0, s>>>(r64, 0, W.npart, W.G, nullptr, W.scal + 5); }
-        MU_CUDA(cudaMemcpyAsync(hs, W.scal + 5, 8, cudaMemcpyDeviceToHost, s));
-        MU_CUDA(cudaStreamSynchronize(s));
-        const double rn = hs[0];
-        rel = bn > 0 ? rn / bn : 0.0;
-        if (rel <= o->tol || it_left <= 0 || ref == maxref) break;
-        // inner: A d = r / ||r|| in complex64
-        { Prof prof_("scale_copy_kernel<double2, float2>", s); scale_copy_kernel<double2, float2><<<nblk(N, 256), 256, 0, s>>>(r64, rhs32, N, W.scal + 5); }
-        MU_CUDA(cudaMemsetAsync(d32, 0, N * 8, s));
-        int it = 0, rs = 0;
-        double irel = 0;
-        st = gmres<float2>(I, W, rhs32, d32, std::max(itol, 0.5 * o->tol / std::max(rel, 1e-300)),
-                           it_left, it, rs, irel, s);
-        if (st) break;
-        it_left -= it;
-        info->iters += it;
-        info->restarts += rs;
-        info->refinements += 1;
-        // x += ||r|| d
-        { Prof prof_("axpy_kernel<double2, float2>", s); axpy_kernel<double2, float2><<<nblk(N, 256), 256, 0, s>>>(x, d32, N, rn); }
-        MU_CHECK_LAUNCH("axpy");
-      }
-      info->relres = std::max(info->relres, rel);
-      if (rel <= o->tol) info->converged++;
-    }
-    cudaFreeHost(hs);
+    st = solve_lockstep(op, B, X, r, o, info, p, s);
   }
   if (own) cudaFreeAsync(own, s);
   if (!st) MU_CUDA(cudaStreamSynchronize(s));
