@@ -329,6 +329,7 @@ def run_ours(args):
         e2e = {"value": pairs / (ms_e2e / 1e3), "unit": UNIT, "ms_per_step": round(ms_e2e, 3),
                "h2d_bytes_per_step": int(xyz.nbytes + tri6.nbytes + inc.nbytes),
                "d2h_bytes_per_step": int(r * 3 * 8)}
+        extras["level4_16rhs"] = level4_16rhs(mu, torch, dev)
         cpu = cpu_baseline(args.workload, budget_s=15.0)
 
     if rank == 0:
@@ -351,6 +352,51 @@ def run_ours(args):
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def level4_16rhs(mu, torch, dev):
+    """The level-4 plasmonic sphere (N = 40968, complex64 Z of 13.4 GB) with
+    16 incidences: mixed assembly, block-Jacobi build (B = 512), the
+    lockstep GMRES-IR solve of all 16 right-hand sides, and the tensor-core
+    product alone (achieved HBM bandwidth of the complex64 Z read)."""
+    xyz, tri6, inc, w = workloads.workload("sphere_L4_eps-10+1i_ka10")
+    p = mu.Params.from_workload(w)
+    F = tri6.shape[0]
+    m = mu.Mesh(xyz, tri6)
+    m.tangent_frame(p.frame_rule, out=False)
+
+    def ev_time(fn, reps=1):
+        fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            out = fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps, out
+
+    Z = torch.empty((m.N, m.N), dtype=torch.complex64, device=dev)
+    near = torch.empty(m.near_bytes() // 16, dtype=torch.complex128, device=dev)
+    B = torch.empty((inc.shape[0], m.N), dtype=torch.complex128, device=dev)
+    t_asm, _ = ev_time(lambda: mu.assemble(m, p, mu.MUELLER_C64_NEAR64, inc=inc, Z=Z, near=near, B=B))
+    op = mu.Operator(m, Z, near, mu.MUELLER_C64_NEAR64)
+    t_pre, _ = ev_time(lambda: mu.precond_build(op, int(w["block"])))
+    opts = mu.SolverOpts(mode=mu.SOLVE_GMRES_IR, restart=50, tol=1e-8)
+    X = torch.zeros_like(B)
+    t_solve, (X, info) = ev_time(lambda: mu.solve(op, B, opts, X=X))
+    X32 = X.to(torch.complex64)
+    t_mm, _ = ev_time(lambda: mu.matvec_mrhs(op, X32), reps=5)
+    _, xs = mu.far_field(m, p, X, inc)
+    gbs = m.N * m.N * 8 / (t_mm / 1e3) / 1e9
+    return {"n_dof": m.N, "rhs": int(inc.shape[0]), "assembly_ms": round(t_asm, 2),
+            "assembly_pairs_per_s": F * F / (t_asm / 1e3), "precond_ms": round(t_pre, 2),
+            "solve_s": round(t_solve / 1e3, 4), "iters_lockstep": info["iters"] // inc.shape[0],
+            "refinements": info["refinements"], "relres": info["relres"],
+            "mrhs_product_ms": round(t_mm, 3), "mrhs_product_hbm_gbs": round(gbs, 1),
+            "mrhs_product_hbm_frac": round(gbs / 6783.5, 3),
+            "C_ext_mean": float(xs[:, 0].mean())}
 
 
 # ------------------------------------------------------------ CPU oracle

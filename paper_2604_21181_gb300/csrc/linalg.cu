@@ -1609,7 +1609,9 @@ static mueller_status solve_lockstep(const mueller_operator* op, const double2* 
     // inner system A d = r / ||r|| in complex64 for the active right-hand sides
     { Prof prof_("scale_b_kernel", s); scale_b_kernel<double2, float2><<<dim3(nblk(N, 256), r), 256, 0, s>>>(W.r64, N, W.rn, W.rhs32); }
     int it = 0, rs = 0;
-    st = lock_gmres(I, W, itol, it_left, it, rs, hbuf, active, s);
+    // each refinement only has to bring the worst residual down to tol
+    st = lock_gmres(I, W, std::max(itol, 0.5 * o->tol / std::max(worst, 1e-300)), it_left, it, rs,
+                    hbuf, active, s);
     if (st) goto out;
     it_left -= it;
     info->iters += it * r;

@@ -2,9 +2,10 @@
 
     python -m paper_2604_21181_gb300.profile_case --level 2 --what assemble
 
-Runs the mesh load, the tangent frame and one mixed-precision assembly (and,
-with --what solve, the block-Jacobi build and one GMRES-IR solve) of the
-level-L sphere with eps_r = 2.25, k_a = 5, then exits.
+Runs the mesh load, the tangent frame and one mixed-precision assembly of the
+level-L sphere with eps_r = 2.25, k_a = 5; with --what solve also the
+block-Jacobi build and one GMRES-IR solve, with --what mrhs one tensor-core
+product with --rhs random right-hand sides; then exits.
 """
 
 from __future__ import annotations
@@ -26,7 +27,8 @@ def main():
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--level", type=int, default=2)
-    ap.add_argument("--what", default="assemble", choices=["assemble", "solve"])
+    ap.add_argument("--what", default="assemble", choices=["assemble", "solve", "mrhs"])
+    ap.add_argument("--rhs", type=int, default=16)
     ap.add_argument("--ka", type=float, default=5.0)
     ap.add_argument("--eps", type=float, nargs=2, default=(2.25, 0.0))
     ap.add_argument("--block", type=int, default=256)
@@ -37,6 +39,11 @@ def main():
     mesh.tangent_frame(p.frame_rule, out=False)
     inc = workloads.plane_wave()
     Z, near, B = mu.assemble(mesh, p, mu.MUELLER_C64_NEAR64, inc=inc)
+    if a.what == "mrhs":
+        op = mu.Operator(mesh, Z, near, mu.MUELLER_C64_NEAR64)
+        g = torch.Generator().manual_seed(1)
+        X = torch.randn((a.rhs, mesh.N), dtype=torch.complex64, generator=g).cuda()
+        mu.matvec_mrhs(op, X)
     if a.what == "solve":
         op = mu.Operator(mesh, Z, near, mu.MUELLER_C64_NEAR64)
         mu.precond_build(op, a.block)
