@@ -6,7 +6,8 @@
 // i.e. the rows of Z read as real vectors of length 2N (re, im interleaved)
 // against B' (2r x 2N, K-major) with rows  2s: ( xr_j, -xi_j )  and
 // 2s+1: ( xi_j, xr_j ).  The MMA kind is tf32 with FP32 accumulation in
-// TMEM; each operand is split into a TF32 head and its remainder
+// TMEM; each operand is split into a TF32 head (its top 19 bits, which is
+// what the tensor core reads from an FP32 word) and the exact remainder
 // (x = hi + lo), and hi*hi + hi*lo + lo*hi are accumulated, which brings the
 // product to FP32 accuracy.
 //
@@ -104,12 +105,6 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(bar))
       : "memory");
-}
-
-__device__ __forceinline__ uint32_t tf32_round(float v) {
-  uint32_t o;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(o) : "f"(v));
-  return o;
 }
 
 struct MrhsArgs {
@@ -235,14 +230,19 @@ __global__ void __launch_bounds__(THREADS, 1)
         *bail = 1;
         break;
       }
-      uint32_t* A = (uint32_t*)A_of(s);
-      uint32_t* Al = (uint32_t*)Alo_of(s);
-#pragma unroll 4
-      for (int e = t; e < BM * BK; e += 128) {
-        const float v = __uint_as_float(A[e]);
-        const uint32_t hi = tf32_round(v);
-        A[e] = hi;
-        Al[e] = __float_as_uint(v - __uint_as_float(hi));
+      // the tensor core reads the raw FP32 tile as its TF32 head (the low 13
+      // mantissa bits are ignored); only the exact remainder is written
+      const uint4* A4 = (const uint4*)A_of(s);
+      uint4* Al4 = (uint4*)Alo_of(s);
+#pragma unroll
+      for (int e = t; e < BM * BK / 4; e += 128) {
+        const uint4 v = A4[e];
+        uint4 o;
+        o.x = __float_as_uint(__uint_as_float(v.x) - __uint_as_float(v.x & 0xFFFFE000u));
+        o.y = __float_as_uint(__uint_as_float(v.y) - __uint_as_float(v.y & 0xFFFFE000u));
+        o.z = __float_as_uint(__uint_as_float(v.z) - __uint_as_float(v.z & 0xFFFFE000u));
+        o.w = __float_as_uint(__uint_as_float(v.w) - __uint_as_float(v.w & 0xFFFFE000u));
+        Al4[e] = o;
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(&split[s]);
@@ -303,7 +303,8 @@ __global__ void build_bprime_kernel(const float2* __restrict__ X, int64_t N, int
       v1 = x.x;
     }
   }
-  const float h0 = __uint_as_float(tf32_round(v0)), h1 = __uint_as_float(tf32_round(v1));
+  const float h0 = __uint_as_float(__float_as_uint(v0) & 0xFFFFE000u);
+  const float h1 = __uint_as_float(__float_as_uint(v1) & 0xFFFFE000u);
   const int64_t o = (int64_t)row * 2 * N + 2 * j;
   Bhi[o] = h0;
   Bhi[o + 1] = h1;
@@ -390,7 +391,7 @@ mueller_status mrhs_matvec_c64(const void* Z, int64_t N, int64_t ldz, const void
   a.nprime = nprime;
   a.r = r;
   a.ktiles = (int)cdiv(2 * N, BK);
-  a.stages = nprime <= 64 ? 4 : 3;
+  a.stages = nprime <= 32 ? 5 : (nprime <= 64 ? 4 : 3);
   a.tmem_cols = tmem_cols;
   a.Y = (float*)Y;
   a.err = err;
