@@ -15,14 +15,20 @@
 // 32 floats) and of the B' head / remainder tiles; warps 2-5 split the Z
 // tile into head and remainder in shared memory and, at the end, read the
 // accumulator from TMEM; warp 1 allocates TMEM and one of its threads issues
-// the MMAs.  Stages are handed over with mbarriers; every wait is bounded and
-// reports a timeout through an error word instead of hanging.  K is split
+// the MMAs.  Each tcgen05.mma of kind tf32 with M = 128 costs about the same
+// whatever its N (up to 256), so the number of MMAs per Z byte bounds the
+// kernel: where 2 nprime <= 256 the head meets [B'hi; B'lo] in one MMA of
+// N = 2 nprime (the two halves are adjacent in shared memory), which makes
+// two MMAs per K step instead of three.  Stages are handed over with
+// mbarriers; every wait is bounded (in time) and reports a timeout through an
+// error word instead of hanging.  K is split
 // across CTAs (split-K) so that the grid fills the 152 SMs; the partial sums
 // meet in Y by atomic additions.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "common.cuh"
@@ -34,7 +40,9 @@ constexpr int BM = 128;   // rows of Z per CTA (MMA M)
 constexpr int BK = 32;    // floats per K tile = one 128-byte swizzle row
 constexpr int MMA_K = 8;  // tf32 elements per tcgen05.mma
 constexpr int THREADS = 192;
-constexpr uint32_t WAIT_LIMIT = 1u << 22;
+constexpr uint32_t WAIT_LIMIT = 1u << 30;
+constexpr uint64_t WAIT_NS = 2000000000ull;  // 2 s
+constexpr int SMEM_BUDGET = 224 * 1024;      // stages + barriers
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -61,11 +69,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait: false after WAIT_LIMIT polls
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// bounded wait: false after about WAIT_NS nanoseconds (or WAIT_LIMIT polls)
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+  if (mbar_try_wait(b, parity)) return true;
+  const uint64_t t0 = global_ns();
   for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
     if (mbar_try_wait(b, parity)) return true;
-    if (it > 32) __nanosleep(64);
+    if ((it & 255u) == 255u && global_ns() - t0 > WAIT_NS) return false;
   }
   return false;
 }
@@ -107,6 +122,17 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
       : "memory");
 }
 
+// 16 consecutive TMEM columns of this thread's lane -> v[0..15]
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+
 struct MrhsArgs {
   int64_t N;        // rows of Z (= columns / 2 of the real view)
   int nprime;       // padded 2r (MMA N), multiple of 16
@@ -114,6 +140,7 @@ struct MrhsArgs {
   int ktiles;       // K tiles of the real view (2N / 32 rounded up)
   int kchunk;       // K tiles per CTA (split-K)
   int stages;
+  int stacked;      // 1: the head meets [B'hi; B'lo] in one MMA of N = 2 nprime
   uint32_t tmem_cols;
   float* Y;         // complex64 r x N, accumulated (atomic adds)
   int* err;         // error word
@@ -193,8 +220,9 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else if (warp == 1) {
     // ---------------- MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) |
-                             ((uint32_t)(a.nprime >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+      const uint32_t id0 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BM >> 4) << 24);
+      const uint32_t idn = id0 | ((uint32_t)(a.nprime >> 3) << 17);
+      const uint32_t id2n = id0 | ((uint32_t)(a.nprime >> 2) << 17);
       for (int it = 0; it < nk; ++it) {
         const int s = it % a.stages;
         const uint32_t ph = (it / a.stages) & 1;
@@ -211,9 +239,17 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
         for (int k = 0; k < BK / MMA_K; ++k) {
           const uint64_t off = (uint64_t)((k * MMA_K * 4) >> 4);  // 32 bytes per K step
-          mma_tf32(tmem, dA + off, dB + off, idesc, (it > 0 || k > 0) ? 1u : 0u);
-          mma_tf32(tmem, dA + off, dBl + off, idesc, 1u);
-          mma_tf32(tmem, dAl + off, dB + off, idesc, 1u);
+          const uint32_t acc = (it > 0 || k > 0) ? 1u : 0u;
+          if (a.stacked) {
+            // B'hi and B'lo are adjacent in shared memory: one descriptor
+            // covers both, the MMA writes hi*B'hi | hi*B'lo side by side
+            mma_tf32(tmem, dA + off, dB + off, id2n, acc);
+            mma_tf32(tmem, dAl + off, dB + off, idn, 1u);
+          } else {
+            mma_tf32(tmem, dA + off, dB + off, idn, acc);
+            mma_tf32(tmem, dA + off, dBl + off, idn, 1u);
+            mma_tf32(tmem, dAl + off, dB + off, idn, 1u);
+          }
         }
         mma_commit(&empty[s]);
       }
@@ -232,17 +268,19 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       // the tensor core reads the raw FP32 tile as its TF32 head (the low 13
       // mantissa bits are ignored); only the exact remainder is written
-      const uint4* A4 = (const uint4*)A_of(s);
-      uint4* Al4 = (uint4*)Alo_of(s);
+      const uint4* __restrict__ A4 = (const uint4*)A_of(s);
+      uint4* __restrict__ Al4 = (uint4*)Alo_of(s);
+      uint4 v[BM * BK / 4 / 128];
 #pragma unroll
-      for (int e = t; e < BM * BK / 4; e += 128) {
-        const uint4 v = A4[e];
+      for (int e = 0; e < BM * BK / 4 / 128; ++e) v[e] = A4[t + 128 * e];
+#pragma unroll
+      for (int e = 0; e < BM * BK / 4 / 128; ++e) {
         uint4 o;
-        o.x = __float_as_uint(__uint_as_float(v.x) - __uint_as_float(v.x & 0xFFFFE000u));
-        o.y = __float_as_uint(__uint_as_float(v.y) - __uint_as_float(v.y & 0xFFFFE000u));
-        o.z = __float_as_uint(__uint_as_float(v.z) - __uint_as_float(v.z & 0xFFFFE000u));
-        o.w = __float_as_uint(__uint_as_float(v.w) - __uint_as_float(v.w & 0xFFFFE000u));
-        Al4[e] = o;
+        o.x = __float_as_uint(__uint_as_float(v[e].x) - __uint_as_float(v[e].x & 0xFFFFE000u));
+        o.y = __float_as_uint(__uint_as_float(v[e].y) - __uint_as_float(v[e].y & 0xFFFFE000u));
+        o.z = __float_as_uint(__uint_as_float(v[e].z) - __uint_as_float(v[e].z & 0xFFFFE000u));
+        o.w = __float_as_uint(__uint_as_float(v[e].w) - __uint_as_float(v[e].w & 0xFFFFE000u));
+        Al4[t + 128 * e] = o;
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(&split[s]);
@@ -253,24 +291,24 @@ __global__ void __launch_bounds__(THREADS, 1)
     asm volatile("tcgen05.fence::after_thread_sync;");
     const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
     const int64_t row = m0 + quarter * 32 + lane;
+    const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
     for (int c0 = 0; c0 < a.nprime; c0 += 16) {
-      uint32_t v[16];
-      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-          "%14,%15}, [%16];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
-            "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-          : "r"(taddr));
+      uint32_t v[16], w[16];
+      tmem_ld16(lane_addr + (uint32_t)c0, v);
+      if (a.stacked) tmem_ld16(lane_addr + (uint32_t)(a.nprime + c0), w);
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       if (ok && row < a.N) {
 #pragma unroll
         for (int q = 0; q < 16; q += 2) {
           const int sidx = (c0 + q) >> 1;
+          float re = __uint_as_float(v[q]), im = __uint_as_float(v[q + 1]);
+          if (a.stacked) {  // hi*B'hi + lo*B'hi  +  hi*B'lo
+            re += __uint_as_float(w[q]);
+            im += __uint_as_float(w[q + 1]);
+          }
           if (sidx < a.r)
             atomicAdd(reinterpret_cast<float2*>(a.Y) + (int64_t)sidx * a.N + row,
-                      make_float2(__uint_as_float(v[q]), __uint_as_float(v[q + 1])));
+                      make_float2(re, im));
         }
       }
     }
@@ -367,7 +405,10 @@ mueller_status mrhs_matvec_c64(const void* Z, int64_t N, int64_t ldz, const void
     return MUELLER_ERR_INVALID_ARG;
   }
   const int nprime = (int)cdiv(2 * r, 16) * 16;
-  const uint32_t tmem_cols = nprime <= 32 ? 32 : (nprime <= 64 ? 64 : (nprime <= 128 ? 128 : 256));
+  const int stacked = 2 * nprime <= 256 ? 1 : 0;
+  const int acc_cols = stacked ? 2 * nprime : nprime;
+  uint32_t tmem_cols = 32;
+  while ((int)tmem_cols < acc_cols) tmem_cols <<= 1;
   float* Bhi = (float*)work;
   float* Blo = Bhi + (size_t)nprime * 2 * N;
   int* err = (int*)(Blo + (size_t)nprime * 2 * N);
@@ -391,7 +432,7 @@ mueller_status mrhs_matvec_c64(const void* Z, int64_t N, int64_t ldz, const void
   a.nprime = nprime;
   a.r = r;
   a.ktiles = (int)cdiv(2 * N, BK);
-  a.stages = nprime <= 32 ? 5 : (nprime <= 64 ? 4 : 3);
+  a.stacked = stacked;
   a.tmem_cols = tmem_cols;
   a.Y = (float*)Y;
   a.err = err;
@@ -402,6 +443,7 @@ mueller_status mrhs_matvec_c64(const void* Z, int64_t N, int64_t ldz, const void
   ksplit = (int)cdiv(a.ktiles, a.kchunk);
   const size_t bbytes = (size_t)nprime * BK * 4;
   const size_t stage_bytes = 2 * (size_t)BM * BK * 4 + 2 * bbytes;
+  a.stages = (int)std::min<size_t>(6, (SMEM_BUDGET - 2048) / stage_bytes);
   const size_t smem = 1024 + a.stages * stage_bytes + (3 * a.stages + 1) * 8 + 16;
   MU_CUDA(cudaFuncSetAttribute(mrhs_tf32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   {

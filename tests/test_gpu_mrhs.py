@@ -1,7 +1,8 @@
 """Tensor-core multi-RHS product (tcgen05, TF32 head/remainder split) against
 the FP64 product of the same stored operator.  Sizes span several 128-row
-tiles with ragged M and K edges, several right-hand-side counts (padded MMA N),
-and the split-K path."""
+tiles with ragged M and K edges, several right-hand-side counts (padded MMA N;
+up to 64 the head meets [B'hi; B'lo] in one MMA, above it in two), and
+stream-K ranges that cross row tiles."""
 
 import numpy as np
 import pytest
@@ -30,7 +31,7 @@ def operator(level):
     return _ops[level]
 
 
-@pytest.mark.parametrize("level,r", [(1, 1), (2, 8), (2, 13), (2, 16), (3, 16), (3, 40)])
+@pytest.mark.parametrize("level,r", [(1, 1), (2, 8), (2, 13), (2, 16), (3, 16), (3, 40), (2, 72), (2, 128)])
 def test_tensor_core_product_matches_fp64(level, r):
     op = operator(level)
     N = op.mesh.N
