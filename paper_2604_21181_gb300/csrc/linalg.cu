@@ -180,6 +180,10 @@ __global__ void __launch_bounds__(256) near_spmv_kernel(int64_t nn, const int32_
 constexpr int NBK = 32;
 
 __device__ __forceinline__ double cabs1(double2 a) { return fabs(a.x) + fabs(a.y); }
+template <class CT>
+__device__ __forceinline__ auto cabs1T(CT a) -> decltype(a.x) {
+  return fabs(a.x) + fabs(a.y);
+}
 __device__ __forceinline__ double2 cmul2(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -195,24 +199,26 @@ __device__ __forceinline__ double2 cdiv2(double2 a, double2 b) {
 
 // factor panel columns [k0, k0+NBK) of every block; row swaps are applied
 // to whole rows.  READING: pivot = first row maximising |Re| + |Im|.
-__global__ void __launch_bounds__(256) lu_panel_kernel(double2* __restrict__ A, int64_t d,
+template <class CT>
+__global__ void __launch_bounds__(256) lu_panel_kernel(CT* __restrict__ A, int64_t d,
                                                        const int32_t* __restrict__ sz, int k0,
                                                        int32_t* __restrict__ piv,
                                                        int32_t* __restrict__ status) {
   const int b = blockIdx.x;
   const int n = sz[b];
   if (k0 >= n) return;
-  double2* M = A + (int64_t)b * d * d;
-  __shared__ double sv[256];
+  using RT = decltype(CT{}.x);
+  CT* M = A + (int64_t)b * d * d;
+  __shared__ RT sv[256];
   __shared__ int si[256];
-  __shared__ double2 spiv;
+  __shared__ CT spiv;
   const int kend = min(k0 + NBK, n);
   for (int k = k0; k < kend; ++k) {
     // pivot search in column k, rows k..n-1
-    double best = -1.0;
+    RT best = -1;
     int bi = k;
     for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
-      const double v = cabs1(M[(int64_t)i * d + k]);
+      const RT v = cabs1T(M[(int64_t)i * d + k]);
       if (v > best) {
         best = v;
         bi = i;
@@ -223,7 +229,7 @@ __global__ void __launch_bounds__(256) lu_panel_kernel(double2* __restrict__ A, 
     __syncthreads();
     for (int o = 128; o > 0; o >>= 1) {
       if (threadIdx.x < o) {
-        const double v2 = sv[threadIdx.x + o];
+        const RT v2 = sv[threadIdx.x + o];
         const int i2 = si[threadIdx.x + o];
         if (v2 > sv[threadIdx.x] || (v2 == sv[threadIdx.x] && i2 < si[threadIdx.x])) {
           sv[threadIdx.x] = v2;
@@ -240,27 +246,142 @@ __global__ void __launch_bounds__(256) lu_panel_kernel(double2* __restrict__ A, 
     }
     if (p != k)
       for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        const double2 t = M[(int64_t)k * d + j];
+        const CT t = M[(int64_t)k * d + j];
         M[(int64_t)k * d + j] = M[(int64_t)p * d + j];
         M[(int64_t)p * d + j] = t;
       }
     __syncthreads();
-    if (threadIdx.x == 0) spiv = singular ? make_double2(1.0, 0.0) : M[(int64_t)k * d + k];
+    if (threadIdx.x == 0) spiv = singular ? CT{1, 0} : M[(int64_t)k * d + k];
     __syncthreads();
-    const double2 pv = spiv;
+    const CT pv = spiv;
     // multipliers and rank-1 update of the panel columns
     for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) {
-      const double2 l = cdiv2(M[(int64_t)i * d + k], pv);
+      const CT l = cdivT(M[(int64_t)i * d + k], pv);
       M[(int64_t)i * d + k] = l;
       for (int j = k + 1; j < kend; ++j) {
-        const double2 u = M[(int64_t)k * d + j];
-        double2 a = M[(int64_t)i * d + j];
+        const CT u = M[(int64_t)k * d + j];
+        CT a = M[(int64_t)i * d + j];
         a.x -= l.x * u.x - l.y * u.y;
         a.y -= l.x * u.y + l.y * u.x;
         M[(int64_t)i * d + j] = a;
       }
     }
     __syncthreads();
+  }
+}
+
+// Same factorisation of panel columns [k0, k0+NBK), with rows k0..n-1 of the
+// panel held in shared memory (one thread per row, blockDim >= n - k0): the
+// pivot search is a warp-shuffle arg-max, the rank-1 updates run on shared
+// memory, and the panel's row swaps are applied to the columns outside it
+// afterwards, in the order they were chosen (the same matrix as swapping
+// whole rows at each step).  Pivot: first row maximising |Re| + |Im|.
+template <class CT>
+__global__ void __launch_bounds__(1024) lu_panel_smem_kernel(CT* __restrict__ A, int64_t d,
+                                                             const int32_t* __restrict__ sz,
+                                                             int k0, int32_t* __restrict__ piv,
+                                                             int32_t* __restrict__ status) {
+  using RT = decltype(CT{}.x);
+  constexpr int LD = NBK + 1;
+  extern __shared__ __align__(16) unsigned char lu_smem[];
+  __shared__ RT wv[32];
+  __shared__ int wi[32];
+  __shared__ int sp[NBK];
+  __shared__ int ssing;
+  const int b = blockIdx.x;
+  const int n = sz[b];
+  if (k0 >= n) return;
+  const int w = min(NBK, n - k0);
+  const int rows = n - k0;
+  const int t = threadIdx.x;
+  CT* P = (CT*)lu_smem;  // [rows][LD]
+  CT* M = A + (int64_t)b * d * d;
+  for (int e = t; e < rows * w; e += blockDim.x) {
+    const int i = e / w, j = e - i * w;
+    P[i * LD + j] = M[(int64_t)(k0 + i) * d + k0 + j];
+  }
+  __syncthreads();
+  for (int k = 0; k < w; ++k) {
+    RT v = -1;
+    int vi = rows;
+    if (t >= k && t < rows) {
+      v = cabs1T(P[t * LD + k]);
+      vi = t;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const RT v2 = __shfl_down_sync(0xffffffffu, v, o);
+      const int i2 = __shfl_down_sync(0xffffffffu, vi, o);
+      if (v2 > v || (v2 == v && i2 < vi)) {
+        v = v2;
+        vi = i2;
+      }
+    }
+    if ((t & 31) == 0) {
+      wv[t >> 5] = v;
+      wi[t >> 5] = vi;
+    }
+    __syncthreads();
+    if (t < 32) {
+      const int nw = (int)(blockDim.x >> 5);
+      v = t < nw ? wv[t] : (RT)-1;
+      vi = t < nw ? wi[t] : rows;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const RT v2 = __shfl_down_sync(0xffffffffu, v, o);
+        const int i2 = __shfl_down_sync(0xffffffffu, vi, o);
+        if (v2 > v || (v2 == v && i2 < vi)) {
+          v = v2;
+          vi = i2;
+        }
+      }
+      if (t == 0) {
+        const bool singular = !(v > 0);
+        if (singular) {
+          vi = k;
+          atomicCAS(status, 0, b + 1);
+        }
+        sp[k] = vi;
+        ssing = singular ? 1 : 0;
+        piv[(int64_t)b * d + k0 + k] = k0 + vi;
+      }
+    }
+    __syncthreads();
+    const int p = sp[k];
+    if (p != k && t < w) {
+      const CT x = P[k * LD + t];
+      P[k * LD + t] = P[p * LD + t];
+      P[p * LD + t] = x;
+    }
+    __syncthreads();
+    const CT pv = ssing ? CT{1, 0} : P[k * LD + k];
+    if (t > k && t < rows) {
+      CT* row = P + t * LD;
+      const CT* prow = P + k * LD;
+      const CT l = cdivT(row[k], pv);
+      row[k] = l;
+      for (int j = k + 1; j < w; ++j) {
+        const CT u = prow[j];
+        row[j].x -= l.x * u.x - l.y * u.y;
+        row[j].y -= l.x * u.y + l.y * u.x;
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = t; e < rows * w; e += blockDim.x) {
+    const int i = e / w, j = e - i * w;
+    M[(int64_t)(k0 + i) * d + k0 + j] = P[i * LD + j];
+  }
+  for (int c = t; c < n; c += blockDim.x) {
+    if (c >= k0 && c < k0 + w) continue;
+    for (int k = 0; k < w; ++k) {
+      const int p = sp[k];
+      if (p != k) {
+        const CT x = M[(int64_t)(k0 + k) * d + c];
+        M[(int64_t)(k0 + k) * d + c] = M[(int64_t)(k0 + p) * d + c];
+        M[(int64_t)(k0 + p) * d + c] = x;
+      }
+    }
   }
 }
 
@@ -1051,24 +1172,35 @@ static mueller_status block_inverse(const CT* A, int64_t d, int nb, const int32_
 
 // in-place LU of nb blocks of size d (active sizes sz_dev), then, if inv,
 // their inverses in 'inv' (d x d per block)
-static mueller_status batched_lu_inverse(double2* A, int64_t d, int nb, const int32_t* sz_dev,
-                                         int32_t* piv, int32_t* status, double2* inv,
+template <class CT>
+static mueller_status batched_lu_inverse(CT* A, int64_t d, int nb, const int32_t* sz_dev,
+                                         int32_t* piv, int32_t* status, CT* inv,
                                          cudaStream_t s) {
+  constexpr size_t kPanelSmem = 200 * 1024;
+  MU_CUDA(cudaFuncSetAttribute(lu_panel_smem_kernel<CT>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPanelSmem));
   for (int k0 = 0; k0 < d; k0 += NBK) {
-    { Prof prof_("lu_panel_kernel", s); lu_panel_kernel<<<nb, 256, 0, s>>>(A, d, sz_dev, k0, piv, status); }
-    MU_CHECK_LAUNCH("lu_panel_kernel");
+    // panel rows k0..d-1 in shared memory when they fit, else in place
+    const size_t panel_bytes = (size_t)(d - k0) * (NBK + 1) * sizeof(CT);
+    if (d - k0 <= 1024 && panel_bytes <= kPanelSmem) {
+      { Prof prof_("lu_panel_smem_kernel", s); lu_panel_smem_kernel<CT><<<nb, 1024, panel_bytes, s>>>(A, d, sz_dev, k0, piv, status); }
+      MU_CHECK_LAUNCH("lu_panel_smem_kernel");
+    } else {
+      { Prof prof_("lu_panel_kernel", s); lu_panel_kernel<CT><<<nb, 256, 0, s>>>(A, d, sz_dev, k0, piv, status); }
+      MU_CHECK_LAUNCH("lu_panel_kernel");
+    }
     const int64_t rest = d - (k0 + NBK);
     if (rest <= 0) continue;
     // U12 = L11^{-1} A12 (columns k0+NBK .. n)
     dim3 gt(nblk(rest, 128), nb);
-    { Prof prof_("trsm_tile_kernel", s); trsm_tile_kernel<double2><<<gt, 128, 0, s>>>(A, A, d, d, d * d, sz_dev, k0, NBK, k0 + NBK, -1, 0); }
+    { Prof prof_("trsm_tile_kernel", s); trsm_tile_kernel<CT><<<gt, 128, 0, s>>>(A, A, d, d, d * d, sz_dev, k0, NBK, k0 + NBK, -1, 0); }
     MU_CHECK_LAUNCH("trsm_tile_kernel");
     dim3 gg(nblk(rest, 64), nblk(rest, 64), nb);
-    { Prof prof_("gemm_update_kernel", s); gemm_update_kernel<double2><<<gg, 256, 0, s>>>(A, A, A, d, d, d * d, sz_dev, k0, k0 + NBK, -1, k0 + NBK, -1); }
+    { Prof prof_("gemm_update_kernel", s); gemm_update_kernel<CT><<<gg, 256, 0, s>>>(A, A, A, d, d, d * d, sz_dev, k0, k0 + NBK, -1, k0 + NBK, -1); }
     MU_CHECK_LAUNCH("gemm_update_kernel");
   }
   if (!inv) return MUELLER_OK;
-  return block_inverse<double2>(A, d, nb, sz_dev, piv, inv, s);
+  return block_inverse<CT>(A, d, nb, sz_dev, piv, inv, s);
 }
 
 // inv = U^{-1} L^{-1} P from the LU factors in A (complex type CT)
@@ -1104,8 +1236,9 @@ static mueller_status block_inverse(const CT* A, int64_t d, int nb, const int32_
 // precond_dev layout: [nb][d][d] inverses, then int32 sz[nb].  The inverses
 // are complex128 for a C128 operator (FP64 GMRES applies them in FP64) and
 // complex64 for a C64_NEAR64 operator, whose inner GMRES applies them in
-// FP32: the LU factorisation is FP64 in both cases; for the mixed operator
-// the explicit inverse is then formed from the FP64 factors in FP32.
+// FP32: for the mixed operator the blocks are rounded to complex64 and both
+// the LU factorisation and the explicit inverse are FP32 (the preconditioner
+// changes the iteration count, not the solution the FP64 refinement reaches).
 static const int32_t* precond_sizes(const mueller_operator* op, const BlockLayout& L) {
   const size_t elem = op->dtype == MUELLER_C128 ? 16 : 8;
   return (const int32_t*)((const char*)op->precond_dev + (size_t)L.nb * L.d * L.d * elem);
@@ -1135,20 +1268,20 @@ mueller_status precond_build(const mueller_operator* op, int64_t block, void* P,
                                                         sz_dev, A); }
   }
   MU_CHECK_LAUNCH("gather kernels");
-  mueller_status st;
+  mueller_status st = MUELLER_OK;
   float2* A32 = nullptr;
   if (op->dtype == MUELLER_C128) {
-    st = batched_lu_inverse(A, L.d, (int)L.nb, sz_dev, piv, status, (double2*)P, s);
+    st = batched_lu_inverse<double2>(A, L.d, (int)L.nb, sz_dev, piv, status, (double2*)P, s);
   } else {
-    st = batched_lu_inverse(A, L.d, (int)L.nb, sz_dev, piv, status, nullptr, s);
+    // the preconditioner of the complex64 inner solver: its blocks rounded
+    // to complex64, factorised and inverted in FP32
     const int64_t cnt = (int64_t)L.nb * L.d * L.d;
-    if (!st) {
-      cudaError_t e = cudaMallocAsync((void**)&A32, cnt * sizeof(float2), s);
-      if (e != cudaSuccess) st = cuda_fail(e, "precond FP32 factors");
-    }
+    cudaError_t e = cudaMallocAsync((void**)&A32, cnt * sizeof(float2), s);
+    if (e != cudaSuccess) st = cuda_fail(e, "precond FP32 blocks");
     if (!st) {
       { Prof prof_("c128_to_c64_kernel", s); c128_to_c64_kernel<<<nblk(cnt, 256), 256, 0, s>>>(A, A32, cnt); }
-      st = block_inverse<float2>(A32, L.d, (int)L.nb, sz_dev, piv, (float2*)P, s);
+      MU_CHECK_LAUNCH("c128_to_c64_kernel");
+      st = batched_lu_inverse<float2>(A32, L.d, (int)L.nb, sz_dev, piv, status, (float2*)P, s);
     }
   }
   int32_t hst = 0;
@@ -1677,7 +1810,7 @@ mueller_status solve(const mueller_operator* op, const void* Bv, void* Xv, int r
     if (e == cudaSuccess) e = cudaMemcpyAsync(sz_dev, &nsz, 4, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, 4, s);
     if (e != cudaSuccess) st = cuda_fail(e, "dense LU setup");
-    if (!st) st = batched_lu_inverse(A, N, 1, sz_dev, piv, status, nullptr, s);
+    if (!st) st = batched_lu_inverse<double2>(A, N, 1, sz_dev, piv, status, nullptr, s);
     if (!st) {
       { Prof prof_("transpose_rhs_kernel", s); transpose_rhs_kernel<<<nblk((int64_t)N * r, 256), 256, 0, s>>>(B, T, N, r, 0); }
       { Prof prof_("permute_rows_kernel", s); permute_rows_kernel<<<nblk(r, 64), 64, 0, s>>>(T, N, r, piv); }
