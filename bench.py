@@ -119,19 +119,23 @@ def touching_flops(n_tri: int, n_touch: int, ns: int, q: int) -> float:
     """FP64 flops of one touching_kernel launch (all touching pairs).
 
     The Sauter-Schwab points are processed in groups of ns that share one
-    side.  Per point: the other side's point geometry (P2 map, derivatives,
-    interpolated frame, projection, Gram-Schmidt: ~300 flops), R and its
+    side.  A point geometry (P2 map, derivatives, interpolated frame,
+    projection, Gram-Schmidt) costs ~300 flops; per point, R and its
     direction (13), the 8 singular geometric kernels (~137) and the 48
-    weighted multiply-adds (96): 546 flops.  Per group: the shared point's
-    geometry (300) and the 6 x 48 contraction (576).  Per pair, the
-    remainder kappa - kappa^s on the Q x Q rule (~900 flops per point pair)
-    and its 6 x 6 x 12 contraction (2 * 432 * Q * 2 flops)."""
+    weighted multiply-adds (96) cost 246; per group the 6 x 48 contraction
+    costs 576.  Coincident and common-edge groups evaluate 1 + ns geometries;
+    common-vertex pairs (ns <= 5) evaluate the 2 (ns^2 + ns^3) distinct ones
+    once.  Per pair, the remainder kappa - kappa^s on the Q x Q rule (~900
+    flops per point pair) and its 6 x 6 x 12 contraction (2 * 432 * Q * 2)."""
     n_coinc = n_tri
     n_edge = 3 * n_tri
     n_vert = n_touch - n_coinc - n_edge
-    groups = (6 * n_coinc + 5 * n_edge + 2 * n_vert) * ns ** 3
+    g_ce = (6 * n_coinc + 5 * n_edge) * ns ** 3
+    g_v = 2 * n_vert * ns ** 3
+    geo = g_ce * (1 + ns) + (n_vert * 2 * (ns ** 2 + ns ** 3) if ns <= 5 else g_v * (1 + ns))
+    points = (g_ce + g_v) * ns
     per_pair = q * q * 900 + 2 * 432 * q * 2
-    return groups * ns * 546.0 + groups * 876.0 + n_touch * per_pair
+    return geo * 300.0 + points * 246.0 + (g_ce + g_v) * 576.0 + n_touch * per_pair
 
 
 def regular_flops(n_tri: int, n_touch: int, q: int) -> float:

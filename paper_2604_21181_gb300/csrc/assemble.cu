@@ -211,34 +211,76 @@ __global__ void __launch_bounds__(128) regular_kernel(int64_t nt, const R* __res
 // ------------------------------------------------------- touching pairs
 constexpr int TT = 96;  // threads per touching pair (= SSQ points per batch)
 
+// Geometry record of one Sauter-Schwab point side in shared memory:
+// x, n, t1, t2, s1, s2 (3 each), J, N[6].
+constexpr int GT = 25;
+constexpr int MAX_TAB_NS = 5;  // vertex-pair tables: 2 (ns^2 + ns^3) records <= 60 KB
+
+__device__ __forceinline__ void geo_store(double* t, const PointGeo& g) {
+  const d3 v[6] = {g.x, g.n, g.t1, g.t2, g.s1, g.s2};
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    t[3 * k] = v[k].x;
+    t[3 * k + 1] = v[k].y;
+    t[3 * k + 2] = v[k].z;
+  }
+  t[18] = g.J;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) t[19 + k] = g.N[k];
+}
+
+__device__ __forceinline__ void geo_load(const double* t, PointGeo& g) {
+  g.x = mk(t[0], t[1], t[2]);
+  g.n = mk(t[3], t[4], t[5]);
+  g.t1 = mk(t[6], t[7], t[8]);
+  g.t2 = mk(t[9], t[10], t[11]);
+  g.s1 = mk(t[12], t[13], t[14]);
+  g.s2 = mk(t[15], t[16], t[17]);
+  g.J = t[18];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) g.N[k] = t[19 + k];
+}
+
 // One Sauter-Schwab group: the ns points of region 'reg' at Gauss indices
 // (a, b, c, 0..ns-1).  The side that does not depend on eta3 (x if SHX) is
 // evaluated once; U receives its 6 shape values and V the 6 x 8 sums over the
-// group of  W N_k(other) g_c  (g: the 8 singular geometric kernels).
-template <bool SHX>
+// group of  W N_k(other) g_c  (g: the 8 singular geometric kernels).  With
+// TAB the geometry of both sides is read from shared-memory records (tab_s:
+// the shared side, tab_o: the other side, one record per eta3 index) instead
+// of being evaluated.
+template <bool SHX, bool TAB>
 __device__ __forceinline__ void ssq_group(int cls, int reg, int a, int b, int c, int ns, int px,
                                           int py, const d3 (*Xn)[6], const d3 (*T1)[6],
-                                          const d3 (*T2)[6], double* U, double* V) {
+                                          const d3 (*T2)[6], const double* tab_s,
+                                          const double* tab_o, double* U, double* V) {
   double xu, xv, yu, yv, w, xi, eta;
-  ss_point_idx(cls, reg, a, b, c, 0, c_gl, c_glw, xu, xv, yu, yv, w);
-  if (SHX)
-    to_canonical(px, xu, xv, xi, eta);
-  else
-    to_canonical(py, yu, yv, xi, eta);
   PointGeo gs;
-  point_geo(Xn[SHX ? 0 : 1], T1[SHX ? 0 : 1], T2[SHX ? 0 : 1], xi, eta, gs);
+  if (TAB) {
+    geo_load(tab_s, gs);
+  } else {
+    ss_point_idx(cls, reg, a, b, c, 0, c_gl, c_glw, xu, xv, yu, yv, w);
+    if (SHX)
+      to_canonical(px, xu, xv, xi, eta);
+    else
+      to_canonical(py, yu, yv, xi, eta);
+    point_geo(Xn[SHX ? 0 : 1], T1[SHX ? 0 : 1], T2[SHX ? 0 : 1], xi, eta, gs);
+  }
 #pragma unroll
   for (int i = 0; i < 6; ++i) U[i] = gs.N[i];
 #pragma unroll
   for (int k = 0; k < 48; ++k) V[k] = 0.0;
   for (int d = 0; d < ns; ++d) {
     ss_point_idx(cls, reg, a, b, c, d, c_gl, c_glw, xu, xv, yu, yv, w);
-    if (SHX)
-      to_canonical(py, yu, yv, xi, eta);
-    else
-      to_canonical(px, xu, xv, xi, eta);
     PointGeo go;
-    point_geo(Xn[SHX ? 1 : 0], T1[SHX ? 1 : 0], T2[SHX ? 1 : 0], xi, eta, go);
+    if (TAB) {
+      geo_load(tab_o + d * GT, go);
+    } else {
+      if (SHX)
+        to_canonical(py, yu, yv, xi, eta);
+      else
+        to_canonical(px, xu, xv, xi, eta);
+      point_geo(Xn[SHX ? 1 : 0], T1[SHX ? 1 : 0], T2[SHX ? 1 : 0], xi, eta, go);
+    }
     const PointGeo& gx = SHX ? gs : go;
     const PointGeo& gy = SHX ? go : gs;
     const d3 Rv = sub(gx.x, gy.x);
@@ -271,8 +313,10 @@ __global__ void __launch_bounds__(TT) touching_kernel(
     const int32_t* __restrict__ T, const double* __restrict__ frame,
     const double* __restrict__ qd, int ns, KConst<double> K, double ae_re, double ae_im,
     double am_re, double am_im, int dtype, void* __restrict__ Zv, int64_t ldz, int64_t H,
-    double* __restrict__ near, const int32_t* __restrict__ tp_slot) {
+    double* __restrict__ near, const int32_t* __restrict__ tp_slot, int use_tables) {
   __shared__ d3 sXn[2][6], sT1[2][6], sT2[2][6];
+  // common-vertex pairs: geometry records of the two sides (dynamic)
+  extern __shared__ double sTab[];
   __shared__ double sG[6 * 48];
   __shared__ int sFlag[TT];
   // staging of the SSQ points (sU, sV), reused afterwards for the remainder
@@ -298,6 +342,39 @@ __global__ void __launch_bounds__(TT) touching_kernel(
   __syncthreads();
   const int px = P.perm & 0x3f, py = (P.perm >> 8) & 0x3f;
   const int nreg = P.cls == 3 ? 6 : (P.cls == 2 ? 5 : 2);
+  // In both common-vertex regions one side depends on (xi, eta1) only and the
+  // other on (xi, eta2, eta3) only: ns^2 + ns^3 distinct points per region
+  // instead of ns^3 + ns^4 evaluations.  Record index per region:
+  // (a, b) -> a ns + b, (a, c, d) -> ns^2 + (a ns + c) ns + d.
+  const bool tab = use_tables && P.cls == 1;
+  const int tper = ns * ns + ns * ns * ns;
+  if (tab) {
+    for (int e = tid; e < 2 * tper; e += TT) {
+      const int reg = e / tper, k = e % tper;
+      const bool small = k < ns * ns;
+      int a, b = 0, c = 0, d = 0;
+      if (small) {
+        a = k / ns;
+        b = k % ns;
+      } else {
+        const int kk = k - ns * ns;
+        a = kk / (ns * ns);
+        c = (kk / ns) % ns;
+        d = kk % ns;
+      }
+      double xu, xv, yu, yv, w, xi, eta;
+      ss_point_idx(1, reg, a, b, c, d, c_gl, c_glw, xu, xv, yu, yv, w);
+      const int side = ((reg == 0) == small) ? 0 : 1;  // 0: x, 1: y
+      if (side == 0)
+        to_canonical(px, xu, xv, xi, eta);
+      else
+        to_canonical(py, yu, yv, xi, eta);
+      PointGeo g;
+      point_geo(sXn[side], sT1[side], sT2[side], xi, eta, g);
+      geo_store(sTab + (size_t)e * GT, g);
+    }
+    __syncthreads();
+  }
   // ---- singular parts by Sauter-Schwab (8 real geometric integrals).
   // Work unit: a group of ns points that differ only in eta3, so that one
   // side (x or y, ss_shared_x) is common to the group: its geometry is
@@ -319,10 +396,18 @@ __global__ void __launch_bounds__(TT) touching_kernel(
       const int bi = rest % ns;
       const int ai = rest / ns;
       shx = ss_shared_x(P.cls, reg);
-      if (shx)
-        ssq_group<true>(P.cls, reg, ai, bi, ci, ns, px, py, sXn, sT1, sT2, sU[tid], myV);
-      else
-        ssq_group<false>(P.cls, reg, ai, bi, ci, ns, px, py, sXn, sT1, sT2, sU[tid], myV);
+      if (tab) {
+        const double* ts = sTab + (size_t)(reg * tper + ai * ns + bi) * GT;
+        const double* to = sTab + (size_t)(reg * tper + ns * ns + (ai * ns + ci) * ns) * GT;
+        if (shx)
+          ssq_group<true, true>(P.cls, reg, ai, bi, ci, ns, px, py, sXn, sT1, sT2, ts, to, sU[tid], myV);
+        else
+          ssq_group<false, true>(P.cls, reg, ai, bi, ci, ns, px, py, sXn, sT1, sT2, ts, to, sU[tid], myV);
+      } else if (shx) {
+        ssq_group<true, false>(P.cls, reg, ai, bi, ci, ns, px, py, sXn, sT1, sT2, nullptr, nullptr, sU[tid], myV);
+      } else {
+        ssq_group<false, false>(P.cls, reg, ai, bi, ci, ns, px, py, sXn, sT1, sT2, nullptr, nullptr, sU[tid], myV);
+      }
     } else {
 #pragma unroll
       for (int i = 0; i < 6; ++i) sU[tid][i] = 0.0;
@@ -552,9 +637,12 @@ mueller_status launch_touching(mueller_mesh* m, const PhysConsts& P, int Q, int 
   const double ae_re = 0.5 * (P.eps_re + 1.0), ae_im = 0.5 * P.eps_im;
   const double am_re = 0.5 * (P.mu_re + 1.0), am_im = 0.5 * P.mu_im;
   auto kern = Q == 6 ? touching_kernel<6> : touching_kernel<12>;
-  { Prof prof_("touching_kernel<Q>", s); kern<<<(unsigned)m->n_touch, TT, 0, s>>>(m->n_touch, m->tp, m->X, m->T, m->frame, m->qd64, ns,
+  const int use_tables = ns <= MAX_TAB_NS ? 1 : 0;
+  const size_t tab_bytes = use_tables ? (size_t)2 * (ns * ns + ns * ns * ns) * GT * sizeof(double) : 0;
+  MU_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tab_bytes));
+  { Prof prof_("touching_kernel<Q>", s); kern<<<(unsigned)m->n_touch, TT, tab_bytes, s>>>(m->n_touch, m->tp, m->X, m->T, m->frame, m->qd64, ns,
                                             kconst<double>(P), ae_re, ae_im, am_re, am_im, dtype,
-                                            Z, ldz, 2 * m->nn, (double*)near, m->tp_slot); }
+                                            Z, ldz, 2 * m->nn, (double*)near, m->tp_slot, use_tables); }
   MU_CHECK_LAUNCH("touching_kernel");
   return MUELLER_OK;
 }

@@ -1236,9 +1236,8 @@ static mueller_status block_inverse(const CT* A, int64_t d, int nb, const int32_
 // precond_dev layout: [nb][d][d] inverses, then int32 sz[nb].  The inverses
 // are complex128 for a C128 operator (FP64 GMRES applies them in FP64) and
 // complex64 for a C64_NEAR64 operator, whose inner GMRES applies them in
-// FP32: for the mixed operator the blocks are rounded to complex64 and both
-// the LU factorisation and the explicit inverse are FP32 (the preconditioner
-// changes the iteration count, not the solution the FP64 refinement reaches).
+// FP32: the LU factorisation is FP64 in both cases; for the mixed operator
+// the explicit inverse is then formed from the FP64 factors in FP32.
 static const int32_t* precond_sizes(const mueller_operator* op, const BlockLayout& L) {
   const size_t elem = op->dtype == MUELLER_C128 ? 16 : 8;
   return (const int32_t*)((const char*)op->precond_dev + (size_t)L.nb * L.d * L.d * elem);
@@ -1273,15 +1272,18 @@ mueller_status precond_build(const mueller_operator* op, int64_t block, void* P,
   if (op->dtype == MUELLER_C128) {
     st = batched_lu_inverse<double2>(A, L.d, (int)L.nb, sz_dev, piv, status, (double2*)P, s);
   } else {
-    // the preconditioner of the complex64 inner solver: its blocks rounded
-    // to complex64, factorised and inverted in FP32
+    // the preconditioner of the complex64 inner solver: FP64 factorisation,
+    // explicit inverse formed from the FP64 factors in FP32
+    st = batched_lu_inverse<double2>(A, L.d, (int)L.nb, sz_dev, piv, status, nullptr, s);
     const int64_t cnt = (int64_t)L.nb * L.d * L.d;
-    cudaError_t e = cudaMallocAsync((void**)&A32, cnt * sizeof(float2), s);
-    if (e != cudaSuccess) st = cuda_fail(e, "precond FP32 blocks");
+    if (!st) {
+      cudaError_t e = cudaMallocAsync((void**)&A32, cnt * sizeof(float2), s);
+      if (e != cudaSuccess) st = cuda_fail(e, "precond FP32 factors");
+    }
     if (!st) {
       { Prof prof_("c128_to_c64_kernel", s); c128_to_c64_kernel<<<nblk(cnt, 256), 256, 0, s>>>(A, A32, cnt); }
       MU_CHECK_LAUNCH("c128_to_c64_kernel");
-      st = batched_lu_inverse<float2>(A32, L.d, (int)L.nb, sz_dev, piv, status, (float2*)P, s);
+      st = block_inverse<float2>(A32, L.d, (int)L.nb, sz_dev, piv, (float2*)P, s);
     }
   }
   int32_t hst = 0;
