@@ -284,8 +284,7 @@ __device__ __forceinline__ void ssq_group(int cls, int reg, int a, int b, int c,
     const PointGeo& gx = SHX ? gs : go;
     const PointGeo& gy = SHX ? go : gs;
     const d3 Rv = sub(gx.x, gy.x);
-    const double r = sqrt(dot(Rv, Rv));
-    const double ir = 1.0 / r;
+    const double ir = inv_sqrt(dot(Rv, Rv));
     const d3 h = scl(ir, Rv);
     const double W = w * gx.J * gy.J;
     const double nR = dot(gx.n, h);

@@ -19,6 +19,16 @@ __host__ __device__ __forceinline__ d3 cross(d3 a, d3 b) {
   return mk(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
 
+// 1 / sqrt(x): the device's reciprocal square root (one rounding step
+// instead of a square root and a division)
+__host__ __device__ __forceinline__ double inv_sqrt(double x) {
+#ifdef __CUDA_ARCH__
+  return rsqrt(x);
+#else
+  return 1.0 / sqrt(x);
+#endif
+}
+
 // Quadratic Lagrange functions on the reference simplex with barycentrics
 // l0 = 1 - xi - eta, l1 = xi, l2 = eta; node order v0 v1 v2 m01 m12 m20.
 __host__ __device__ __forceinline__ void p2_eval(double xi, double eta, double N[6], double dxi[6],
@@ -67,15 +77,19 @@ __host__ __device__ __forceinline__ void point_geo(const d3* X, const d3* T1, co
     u2 = fma3(g.N[k], T2[k], u2);
   }
   d3 c = cross(a1, a2);
-  double J = sqrt(dot(c, c));
-  d3 n = scl(1.0 / J, c);
+  const double cc = dot(c, c);
+  const double iJ = inv_sqrt(cc);
+  const double J = cc * iJ;
+  d3 n = scl(iJ, c);
   d3 p1 = sub(u1, scl(dot(n, u1), n));
-  double n1 = sqrt(dot(p1, p1));
-  d3 t1 = scl(1.0 / n1, p1);
+  const double q1 = dot(p1, p1), i1 = inv_sqrt(q1);
+  const double n1 = q1 * i1;
+  d3 t1 = scl(i1, p1);
   d3 p2 = sub(u2, scl(dot(n, u2), n));
   p2 = sub(p2, scl(dot(t1, p2), t1));
-  double n2 = sqrt(dot(p2, p2));
-  d3 t2 = scl(1.0 / n2, p2);
+  const double q2 = dot(p2, p2), i2 = inv_sqrt(q2);
+  const double n2 = q2 * i2;
+  d3 t2 = scl(i2, p2);
   g.x = x;
   g.n = n;
   g.t1 = t1;
