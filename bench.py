@@ -247,8 +247,8 @@ def run_ours(args):
         if top_name.startswith("touching_kernel"):
             fl = touching_flops(F, info["n_touching"], ns, q)
             ach = fl / (top_ms / top_n / 1e3) / 1e12
-            # DRAM bytes per launch: ncu capture of this kernel on the level-2 sphere (9.507 MB
-            # for 4100 touching pairs, profiles/ncu_touching_kernel_sphere_L2.md), per pair
+            # DRAM bytes per launch, scaled per touching pair from an ncu capture of this kernel
+            # on the level-2 sphere (9.507 MB read + written for 4100 touching pairs)
             traffic = int(round(9.507e6 / 4100 * info["n_touching"]))
             roofline = {"kernel": top_name, "bound": "alu", "pipe": "fp64", "achieved": round(ach, 4),
                         "peak": round(PEAK_FP64 / 1e12, 4), "unit": "TFLOP/s",
