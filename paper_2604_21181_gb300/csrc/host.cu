@@ -134,28 +134,36 @@ static mueller_status validate(const double* xyz, int64_t nn, const int32_t* T, 
   }
   // every corner edge in exactly two triangles, opposite directions, same edge node
   struct Use {
+    int32_t lo, hi;
     int64_t tri;
     int32_t from, mid;
   };
-  std::map<std::pair<int32_t, int32_t>, std::vector<Use>> edges;
+  std::vector<Use> uses;
+  uses.reserve((size_t)3 * nt);
   const int emid[3] = {3, 4, 5};
   for (int64_t e = 0; e < nt; ++e)
     for (int k = 0; k < 3; ++k) {
       int32_t a = T[6 * e + k], b = T[6 * e + (k + 1) % 3];
-      edges[{std::min(a, b), std::max(a, b)}].push_back({e, a, T[6 * e + emid[k]]});
+      uses.push_back({std::min(a, b), std::max(a, b), e, a, T[6 * e + emid[k]]});
     }
-  for (auto& kv : edges) {
-    const auto& u = kv.second;
-    if (u.size() != 2)
-      return fail(MUELLER_ERR_MESH, "edge (" + std::to_string(kv.first.first) + "," +
-                                        std::to_string(kv.first.second) + ") is used by " +
-                                        std::to_string(u.size()) + " triangles (not a closed manifold)");
-    if (u[0].from == u[1].from)
-      return fail(MUELLER_ERR_MESH, "triangles " + std::to_string(u[0].tri) + " and " +
-                                        std::to_string(u[1].tri) + " are inconsistently oriented");
-    if (u[0].mid != u[1].mid)
+  std::sort(uses.begin(), uses.end(), [](const Use& x, const Use& y) {
+    return x.lo != y.lo ? x.lo < y.lo : (x.hi != y.hi ? x.hi < y.hi : x.tri < y.tri);
+  });
+  for (size_t k = 0; k < uses.size();) {
+    size_t l = k;
+    while (l < uses.size() && uses[l].lo == uses[k].lo && uses[l].hi == uses[k].hi) ++l;
+    if (l - k != 2)
+      return fail(MUELLER_ERR_MESH, "edge (" + std::to_string(uses[k].lo) + "," +
+                                        std::to_string(uses[k].hi) + ") is used by " +
+                                        std::to_string(l - k) + " triangles (not a closed manifold)");
+    const Use &u0 = uses[k], &u1 = uses[k + 1];
+    if (u0.from == u1.from)
+      return fail(MUELLER_ERR_MESH, "triangles " + std::to_string(u0.tri) + " and " +
+                                        std::to_string(u1.tri) + " are inconsistently oriented");
+    if (u0.mid != u1.mid)
       return fail(MUELLER_ERR_MESH, "edge node mismatch between triangles " +
-                                        std::to_string(u[0].tri) + " and " + std::to_string(u[1].tri));
+                                        std::to_string(u0.tri) + " and " + std::to_string(u1.tri));
+    k = l;
   }
   return MUELLER_OK;
 }
@@ -319,33 +327,45 @@ mueller_status mueller_mesh_load(const double* xyz, int64_t nn, const int32_t* t
     }
   }
   m->n_touch = (int64_t)tp.size();
-  // ---- near-part block layout: node pairs of the touching element pairs
-  std::vector<std::vector<int32_t>> rows(nn);
-  for (const TouchPair& p : tp)
-    for (int i = 0; i < 6; ++i)
-      for (int j = 0; j < 6; ++j) rows[T[6 * p.ex + i]].push_back(T[6 * p.ey + j]);
-  m->near_rowptr_h.assign(nn + 1, 0);
-  for (int64_t i = 0; i < nn; ++i) {
-    auto& r = rows[i];
-    std::sort(r.begin(), r.end());
-    r.erase(std::unique(r.begin(), r.end()), r.end());
-    m->near_rowptr_h[i + 1] = m->near_rowptr_h[i] + (int32_t)r.size();
-  }
-  m->nnzb = m->near_rowptr_h[nn];
-  m->near_col_h.resize(m->nnzb);
-  for (int64_t i = 0; i < nn; ++i)
-    std::copy(rows[i].begin(), rows[i].end(), m->near_col_h.begin() + m->near_rowptr_h[i]);
+  // ---- near-part block layout: node pairs of the touching element pairs.
+  // Row by row: the columns of test node ni are the nodes of every trial
+  // element touching an element that holds ni (deduplicated with a stamp
+  // array, then sorted), and the slot of (pair, i, j) is found through a
+  // column -> position array valid for the current row.
+  std::vector<int64_t> pfirst(nt + 1, 0);  // tp is sorted by ex
+  for (const TouchPair& q : tp) pfirst[q.ex + 1]++;
+  for (int64_t e = 0; e < nt; ++e) pfirst[e + 1] += pfirst[e];
   std::vector<int32_t> slot((size_t)m->n_touch * 36);
-  for (int64_t p = 0; p < m->n_touch; ++p)
-    for (int i = 0; i < 6; ++i) {
-      int32_t ni = T[6 * tp[p].ex + i];
-      const int32_t* b = m->near_col_h.data() + m->near_rowptr_h[ni];
-      const int32_t* e = m->near_col_h.data() + m->near_rowptr_h[ni + 1];
-      for (int j = 0; j < 6; ++j) {
-        int32_t nj = T[6 * tp[p].ey + j];
-        slot[(size_t)p * 36 + i * 6 + j] = (int32_t)(std::lower_bound(b, e, nj) - m->near_col_h.data());
+  {
+    std::vector<int32_t> stamp(nn, -1), pos(nn, 0);
+    m->near_rowptr_h.assign(nn + 1, 0);
+    m->near_col_h.clear();
+    m->near_col_h.reserve((size_t)nn * 64);
+    for (int64_t ni = 0; ni < nn; ++ni) {
+      const size_t start = m->near_col_h.size();
+      for (int32_t q = ptr[ni]; q < ptr[ni + 1]; ++q) {
+        const int64_t ex = n2e[q] >> 3;
+        for (int64_t p = pfirst[ex]; p < pfirst[ex + 1]; ++p)
+          for (int j = 0; j < 6; ++j) {
+            const int32_t nj = T[6 * tp[p].ey + j];
+            if (stamp[nj] != (int32_t)ni) {
+              stamp[nj] = (int32_t)ni;
+              m->near_col_h.push_back(nj);
+            }
+          }
+      }
+      std::sort(m->near_col_h.begin() + start, m->near_col_h.end());
+      m->near_rowptr_h[ni + 1] = (int32_t)m->near_col_h.size();
+      for (size_t k = start; k < m->near_col_h.size(); ++k) pos[m->near_col_h[k]] = (int32_t)k;
+      for (int32_t q = ptr[ni]; q < ptr[ni + 1]; ++q) {
+        const int64_t ex = n2e[q] >> 3;
+        const int i = n2e[q] & 7;
+        for (int64_t p = pfirst[ex]; p < pfirst[ex + 1]; ++p)
+          for (int j = 0; j < 6; ++j) slot[(size_t)p * 36 + i * 6 + j] = pos[T[6 * tp[p].ey + j]];
       }
     }
+    m->nnzb = m->near_rowptr_h[nn];
+  }
   // ---- upload
   st = upload(&m->X, m->X_h.data(), m->X_h.size(), s);
   if (!st) st = upload(&m->T, m->T_h.data(), m->T_h.size(), s);
