@@ -176,8 +176,12 @@ __global__ void __launch_bounds__(256) near_spmv_kernel(int64_t nn, const int32_
 
 // ============================================================ batched LU
 // Blocks are d x d complex128 row-major, block b at offset b*d*d, its
-// active size sz[b] <= d.  Right-looking blocked LU, panel width NBK.
+// active size sz[b] <= d.  Right-looking blocked LU with panels of LUW
+// columns (narrow: the panels run one block per CTA, on few SMs, and their
+// FP64 work per row grows with the width); the explicit inverses and the
+// dense solves use tiles of NBK columns.
 constexpr int NBK = 32;
+constexpr int LUW = 16;
 
 __device__ __forceinline__ double cabs1(double2 a) { return fabs(a.x) + fabs(a.y); }
 template <class CT>
@@ -197,9 +201,9 @@ __device__ __forceinline__ double2 cdiv2(double2 a, double2 b) {
   return make_double2((a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den);
 }
 
-// factor panel columns [k0, k0+NBK) of every block; row swaps are applied
+// factor panel columns [k0, k0+W) of every block; row swaps are applied
 // to whole rows.  READING: pivot = first row maximising |Re| + |Im|.
-template <class CT>
+template <class CT, int W>
 __global__ void __launch_bounds__(256) lu_panel_kernel(CT* __restrict__ A, int64_t d,
                                                        const int32_t* __restrict__ sz, int k0,
                                                        int32_t* __restrict__ piv,
@@ -212,7 +216,7 @@ __global__ void __launch_bounds__(256) lu_panel_kernel(CT* __restrict__ A, int64
   __shared__ RT sv[256];
   __shared__ int si[256];
   __shared__ CT spiv;
-  const int kend = min(k0 + NBK, n);
+  const int kend = min(k0 + W, n);
   for (int k = k0; k < kend; ++k) {
     // pivot search in column k, rows k..n-1
     RT best = -1;
@@ -254,9 +258,12 @@ __global__ void __launch_bounds__(256) lu_panel_kernel(CT* __restrict__ A, int64
     if (threadIdx.x == 0) spiv = singular ? CT{1, 0} : M[(int64_t)k * d + k];
     __syncthreads();
     const CT pv = spiv;
-    // multipliers and rank-1 update of the panel columns
+    const auto pden = pv.x * pv.x + pv.y * pv.y;
+    const CT rpv = CT{pv.x / pden, -pv.y / pden};
+    // multipliers (by the pivot's reciprocal) and rank-1 update of the panel
     for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) {
-      const CT l = cdivT(M[(int64_t)i * d + k], pv);
+      const CT a = M[(int64_t)i * d + k];
+      const CT l = CT{a.x * rpv.x - a.y * rpv.y, a.x * rpv.y + a.y * rpv.x};
       M[(int64_t)i * d + k] = l;
       for (int j = k + 1; j < kend; ++j) {
         const CT u = M[(int64_t)k * d + j];
@@ -270,28 +277,28 @@ __global__ void __launch_bounds__(256) lu_panel_kernel(CT* __restrict__ A, int64
   }
 }
 
-// Same factorisation of panel columns [k0, k0+NBK), with rows k0..n-1 of the
+// Same factorisation of panel columns [k0, k0+W), with rows k0..n-1 of the
 // panel held in shared memory (one thread per row, blockDim >= n - k0): the
 // pivot search is a warp-shuffle arg-max, the rank-1 updates run on shared
 // memory, and the panel's row swaps are applied to the columns outside it
 // afterwards, in the order they were chosen (the same matrix as swapping
 // whole rows at each step).  Pivot: first row maximising |Re| + |Im|.
-template <class CT>
+template <class CT, int W>
 __global__ void __launch_bounds__(1024) lu_panel_smem_kernel(CT* __restrict__ A, int64_t d,
                                                              const int32_t* __restrict__ sz,
                                                              int k0, int32_t* __restrict__ piv,
                                                              int32_t* __restrict__ status) {
   using RT = decltype(CT{}.x);
-  constexpr int LD = NBK + 1;
+  constexpr int LD = W + 1;
   extern __shared__ __align__(16) unsigned char lu_smem[];
   __shared__ RT wv[32];
   __shared__ int wi[32];
-  __shared__ int sp[NBK];
-  __shared__ int ssing;
+  __shared__ int sp[W];
+  __shared__ CT srpv;
   const int b = blockIdx.x;
   const int n = sz[b];
   if (k0 >= n) return;
-  const int w = min(NBK, n - k0);
+  const int w = min(W, n - k0);
   const int rows = n - k0;
   const int t = threadIdx.x;
   CT* P = (CT*)lu_smem;  // [rows][LD]
@@ -342,7 +349,10 @@ __global__ void __launch_bounds__(1024) lu_panel_smem_kernel(CT* __restrict__ A,
           atomicCAS(status, 0, b + 1);
         }
         sp[k] = vi;
-        ssing = singular ? 1 : 0;
+        // reciprocal of the pivot (row vi before the swap), once per column
+        const CT pv = singular ? CT{1, 0} : P[vi * LD + k];
+        const auto pden = pv.x * pv.x + pv.y * pv.y;
+        srpv = CT{pv.x / pden, -pv.y / pden};
         piv[(int64_t)b * d + k0 + k] = k0 + vi;
       }
     }
@@ -354,11 +364,12 @@ __global__ void __launch_bounds__(1024) lu_panel_smem_kernel(CT* __restrict__ A,
       P[p * LD + t] = x;
     }
     __syncthreads();
-    const CT pv = ssing ? CT{1, 0} : P[k * LD + k];
+    const CT rpv = srpv;  // multipliers by the pivot's reciprocal
     if (t > k && t < rows) {
       CT* row = P + t * LD;
       const CT* prow = P + k * LD;
-      const CT l = cdivT(row[k], pv);
+      const CT a = row[k];
+      const CT l = CT{a.x * rpv.x - a.y * rpv.y, a.x * rpv.y + a.y * rpv.x};
       row[k] = l;
       for (int j = k + 1; j < w; ++j) {
         const CT u = prow[j];
@@ -387,7 +398,7 @@ __global__ void __launch_bounds__(1024) lu_panel_smem_kernel(CT* __restrict__ A,
 
 // B[k0:k0+w, c0:c1] <- L_kk^{-1} B[...] (unit lower, L from A) or
 // U_kk^{-1} B[...] (upper, non-unit); one thread per column.
-template <class CT>
+template <class CT, int W>
 __global__ void trsm_tile_kernel(const CT* __restrict__ A, CT* __restrict__ B, int64_t d,
                                  int64_t ldb, int64_t bstride, const int32_t* __restrict__ sz,
                                  int k0, int w_max, int64_t c0, int64_t c1_cap, int upper) {
@@ -402,13 +413,13 @@ __global__ void trsm_tile_kernel(const CT* __restrict__ A, CT* __restrict__ B, i
   CT* X = B + (int64_t)b * bstride;
   // fixed-size, fully unrolled loops keep v[] in registers; rows >= w are
   // inert (zero right-hand side, never written back)
-  CT v[NBK];
+  CT v[W];
 #pragma unroll
-  for (int i = 0; i < NBK; ++i)
+  for (int i = 0; i < W; ++i)
     v[i] = i < w ? X[(int64_t)(k0 + i) * ldb + c] : CT{0, 0};
   if (!upper) {
 #pragma unroll
-    for (int i = 1; i < NBK; ++i)
+    for (int i = 1; i < W; ++i)
 #pragma unroll
       for (int j = 0; j < i; ++j) {
         if (i < w) {
@@ -419,10 +430,10 @@ __global__ void trsm_tile_kernel(const CT* __restrict__ A, CT* __restrict__ B, i
       }
   } else {
 #pragma unroll
-    for (int i = NBK - 1; i >= 0; --i) {
+    for (int i = W - 1; i >= 0; --i) {
       if (i < w) {
 #pragma unroll
-        for (int j = i + 1; j < NBK; ++j) {
+        for (int j = i + 1; j < W; ++j) {
           if (j < w) {
             const CT u = M[(int64_t)(k0 + i) * d + k0 + j];
             v[i].x -= u.x * v[j].x - u.y * v[j].y;
@@ -434,14 +445,14 @@ __global__ void trsm_tile_kernel(const CT* __restrict__ A, CT* __restrict__ B, i
     }
   }
 #pragma unroll
-  for (int i = 0; i < NBK; ++i)
+  for (int i = 0; i < W; ++i)
     if (i < w) X[(int64_t)(k0 + i) * ldb + c] = v[i];
 }
 
 // C[r0:r1, c0:c1] -= A[r0:r1, k0:k0+w] * Bm[k0:k0+w, c0:c1] per block:
 // 64 x 64 output tiles, 256 threads with 4 x 4 complex accumulators each.
 // Row range is [r0, r1) with r1 = n (the block's size) if r1_cap < 0.
-template <class CT>
+template <class CT, int W>
 __global__ void __launch_bounds__(256) gemm_update_kernel(const CT* __restrict__ A,
                                                           const CT* __restrict__ Bm,
                                                           CT* __restrict__ Cm, int64_t d,
@@ -452,7 +463,7 @@ __global__ void __launch_bounds__(256) gemm_update_kernel(const CT* __restrict__
   const int b = blockIdx.z;
   const int n = sz[b];
   if (k0 >= n) return;
-  const int w = min(NBK, n - k0);
+  const int w = min(W, n - k0);
   const int64_t r1 = r1_cap < 0 ? n : mn64(r1_cap, n);
   const int64_t c1 = c1_cap < 0 ? n : mn64(c1_cap, n);
   const int64_t tr = r0 + (int64_t)blockIdx.y * 64, tc = c0 + (int64_t)blockIdx.x * 64;
@@ -460,14 +471,14 @@ __global__ void __launch_bounds__(256) gemm_update_kernel(const CT* __restrict__
   const CT* M = A + (int64_t)b * d * d;
   const CT* Bb = Bm + (int64_t)b * bstride;
   CT* Cb = Cm + (int64_t)b * bstride;
-  __shared__ CT sA[64][NBK + 1];
-  __shared__ CT sB[NBK][64 + 1];
-  for (int t = threadIdx.x; t < 64 * NBK; t += 256) {
-    const int i = t / NBK, k = t % NBK;
+  __shared__ CT sA[64][W + 1];
+  __shared__ CT sB[W][64 + 1];
+  for (int t = threadIdx.x; t < 64 * W; t += 256) {
+    const int i = t / W, k = t % W;
     const int64_t gr = tr + i;
     sA[i][k] = (gr < r1 && k < w) ? M[gr * d + k0 + k] : CT{0, 0};
   }
-  for (int t = threadIdx.x; t < NBK * 64; t += 256) {
+  for (int t = threadIdx.x; t < W * 64; t += 256) {
     const int k = t / 64, j = t % 64;
     const int64_t gc = tc + j;
     sB[k][j] = (gc < c1 && k < w) ? Bb[(int64_t)(k0 + k) * ldb + gc] : CT{0, 0};
@@ -479,7 +490,7 @@ __global__ void __launch_bounds__(256) gemm_update_kernel(const CT* __restrict__
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = CT{0, 0};
-  for (int k = 0; k < NBK; ++k) {
+  for (int k = 0; k < W; ++k) {
     CT a[4], bb[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) a[i] = sA[ty + 16 * i][k];
@@ -1177,26 +1188,26 @@ static mueller_status batched_lu_inverse(CT* A, int64_t d, int nb, const int32_t
                                          int32_t* piv, int32_t* status, CT* inv,
                                          cudaStream_t s) {
   constexpr size_t kPanelSmem = 200 * 1024;
-  MU_CUDA(cudaFuncSetAttribute(lu_panel_smem_kernel<CT>,
+  MU_CUDA(cudaFuncSetAttribute(lu_panel_smem_kernel<CT, LUW>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPanelSmem));
-  for (int k0 = 0; k0 < d; k0 += NBK) {
+  for (int k0 = 0; k0 < d; k0 += LUW) {
     // panel rows k0..d-1 in shared memory when they fit, else in place
-    const size_t panel_bytes = (size_t)(d - k0) * (NBK + 1) * sizeof(CT);
+    const size_t panel_bytes = (size_t)(d - k0) * (LUW + 1) * sizeof(CT);
     if (d - k0 <= 1024 && panel_bytes <= kPanelSmem) {
-      { Prof prof_("lu_panel_smem_kernel", s); lu_panel_smem_kernel<CT><<<nb, 1024, panel_bytes, s>>>(A, d, sz_dev, k0, piv, status); }
+      { Prof prof_("lu_panel_smem_kernel", s); lu_panel_smem_kernel<CT, LUW><<<nb, 1024, panel_bytes, s>>>(A, d, sz_dev, k0, piv, status); }
       MU_CHECK_LAUNCH("lu_panel_smem_kernel");
     } else {
-      { Prof prof_("lu_panel_kernel", s); lu_panel_kernel<CT><<<nb, 256, 0, s>>>(A, d, sz_dev, k0, piv, status); }
+      { Prof prof_("lu_panel_kernel", s); lu_panel_kernel<CT, LUW><<<nb, 256, 0, s>>>(A, d, sz_dev, k0, piv, status); }
       MU_CHECK_LAUNCH("lu_panel_kernel");
     }
-    const int64_t rest = d - (k0 + NBK);
+    const int64_t rest = d - (k0 + LUW);
     if (rest <= 0) continue;
-    // U12 = L11^{-1} A12 (columns k0+NBK .. n)
+    // U12 = L11^{-1} A12 (columns k0+LUW .. n)
     dim3 gt(nblk(rest, 128), nb);
-    { Prof prof_("trsm_tile_kernel", s); trsm_tile_kernel<CT><<<gt, 128, 0, s>>>(A, A, d, d, d * d, sz_dev, k0, NBK, k0 + NBK, -1, 0); }
+    { Prof prof_("trsm_tile_kernel", s); trsm_tile_kernel<CT, LUW><<<gt, 128, 0, s>>>(A, A, d, d, d * d, sz_dev, k0, LUW, k0 + LUW, -1, 0); }
     MU_CHECK_LAUNCH("trsm_tile_kernel");
     dim3 gg(nblk(rest, 64), nblk(rest, 64), nb);
-    { Prof prof_("gemm_update_kernel", s); gemm_update_kernel<CT><<<gg, 256, 0, s>>>(A, A, A, d, d, d * d, sz_dev, k0, k0 + NBK, -1, k0 + NBK, -1); }
+    { Prof prof_("gemm_update_kernel", s); gemm_update_kernel<CT, LUW><<<gg, 256, 0, s>>>(A, A, A, d, d, d * d, sz_dev, k0, k0 + LUW, -1, k0 + LUW, -1); }
     MU_CHECK_LAUNCH("gemm_update_kernel");
   }
   if (!inv) return MUELLER_OK;
@@ -1210,23 +1221,23 @@ static mueller_status block_inverse(const CT* A, int64_t d, int nb, const int32_
   { Prof prof_("perm_identity_kernel", s); perm_identity_kernel<CT><<<dim3(nblk(d, 128), nb), 128, 0, s>>>(inv, d, sz_dev, piv); }
   MU_CHECK_LAUNCH("perm_identity_kernel");
   for (int k0 = 0; k0 < d; k0 += NBK) {  // forward: L (unit lower)
-    { Prof prof_("trsm_tile_kernel", s); trsm_tile_kernel<CT><<<dim3(nblk(d, 128), nb), 128, 0, s>>>(A, inv, d, d, d * d, sz_dev, k0, NBK, 0, -1, 0); }
+    { Prof prof_("trsm_tile_kernel", s); trsm_tile_kernel<CT, NBK><<<dim3(nblk(d, 128), nb), 128, 0, s>>>(A, inv, d, d, d * d, sz_dev, k0, NBK, 0, -1, 0); }
     MU_CHECK_LAUNCH("trsm_tile_kernel(L)");
     const int64_t below = d - (k0 + NBK);
     if (below > 0) {
       dim3 gg(nblk(d, 64), nblk(below, 64), nb);
-      { Prof prof_("gemm_update_kernel", s); gemm_update_kernel<CT><<<gg, 256, 0, s>>>(A, inv, inv, d, d, d * d, sz_dev, k0, k0 + NBK, -1, 0, -1); }
+      { Prof prof_("gemm_update_kernel", s); gemm_update_kernel<CT, NBK><<<gg, 256, 0, s>>>(A, inv, inv, d, d, d * d, sz_dev, k0, k0 + NBK, -1, 0, -1); }
       MU_CHECK_LAUNCH("gemm_update_kernel(L)");
     }
   }
   const int64_t ntile = (d + NBK - 1) / NBK;
   for (int64_t t = ntile - 1; t >= 0; --t) {  // backward: U
     const int k0 = (int)(t * NBK);
-    { Prof prof_("trsm_tile_kernel", s); trsm_tile_kernel<CT><<<dim3(nblk(d, 128), nb), 128, 0, s>>>(A, inv, d, d, d * d, sz_dev, k0, NBK, 0, -1, 1); }
+    { Prof prof_("trsm_tile_kernel", s); trsm_tile_kernel<CT, NBK><<<dim3(nblk(d, 128), nb), 128, 0, s>>>(A, inv, d, d, d * d, sz_dev, k0, NBK, 0, -1, 1); }
     MU_CHECK_LAUNCH("trsm_tile_kernel(U)");
     if (k0 > 0) {
       dim3 gg(nblk(d, 64), nblk(k0, 64), nb);
-      { Prof prof_("gemm_update_kernel", s); gemm_update_kernel<CT><<<gg, 256, 0, s>>>(A, inv, inv, d, d, d * d, sz_dev, k0, 0, k0, 0, -1); }
+      { Prof prof_("gemm_update_kernel", s); gemm_update_kernel<CT, NBK><<<gg, 256, 0, s>>>(A, inv, inv, d, d, d * d, sz_dev, k0, 0, k0, 0, -1); }
       MU_CHECK_LAUNCH("gemm_update_kernel(U)");
     }
   }
@@ -1817,18 +1828,18 @@ mueller_status solve(const mueller_operator* op, const void* Bv, void* Xv, int r
       { Prof prof_("transpose_rhs_kernel", s); transpose_rhs_kernel<<<nblk((int64_t)N * r, 256), 256, 0, s>>>(B, T, N, r, 0); }
       { Prof prof_("permute_rows_kernel", s); permute_rows_kernel<<<nblk(r, 64), 64, 0, s>>>(T, N, r, piv); }
       for (int k0 = 0; k0 < N; k0 += NBK) {
-        { Prof prof_("trsm_tile_kernel", s); trsm_tile_kernel<double2><<<dim3(nblk(r, 128), 1), 128, 0, s>>>(A, T, N, r, 0, sz_dev, k0, NBK, 0, r, 0); }
+        { Prof prof_("trsm_tile_kernel", s); trsm_tile_kernel<double2, NBK><<<dim3(nblk(r, 128), 1), 128, 0, s>>>(A, T, N, r, 0, sz_dev, k0, NBK, 0, r, 0); }
         const int64_t below = N - (k0 + NBK);
         if (below > 0)
-          { Prof prof_("gemm_update_kernel", s); gemm_update_kernel<double2><<<dim3(nblk(r, 64), nblk(below, 64), 1), 256, 0, s>>>(
+          { Prof prof_("gemm_update_kernel", s); gemm_update_kernel<double2, NBK><<<dim3(nblk(r, 64), nblk(below, 64), 1), 256, 0, s>>>(
               A, T, T, N, r, 0, sz_dev, k0, k0 + NBK, -1, 0, r); }
       }
       const int64_t ntile = (N + NBK - 1) / NBK;
       for (int64_t t = ntile - 1; t >= 0; --t) {
         const int k0 = (int)(t * NBK);
-        { Prof prof_("trsm_tile_kernel", s); trsm_tile_kernel<double2><<<dim3(nblk(r, 128), 1), 128, 0, s>>>(A, T, N, r, 0, sz_dev, k0, NBK, 0, r, 1); }
+        { Prof prof_("trsm_tile_kernel", s); trsm_tile_kernel<double2, NBK><<<dim3(nblk(r, 128), 1), 128, 0, s>>>(A, T, N, r, 0, sz_dev, k0, NBK, 0, r, 1); }
         if (k0 > 0)
-          { Prof prof_("gemm_update_kernel", s); gemm_update_kernel<double2><<<dim3(nblk(r, 64), nblk(k0, 64), 1), 256, 0, s>>>(
+          { Prof prof_("gemm_update_kernel", s); gemm_update_kernel<double2, NBK><<<dim3(nblk(r, 64), nblk(k0, 64), 1), 256, 0, s>>>(
               A, T, T, N, r, 0, sz_dev, k0, 0, k0, 0, r); }
       }
       { Prof prof_("transpose_rhs_kernel", s); transpose_rhs_kernel<<<nblk((int64_t)N * r, 256), 256, 0, s>>>(T, X, N, r, 1); }
