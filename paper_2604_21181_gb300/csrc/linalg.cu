@@ -1151,10 +1151,89 @@ mueller_status op_matvec(const mueller_operator* op, const void* X, void* Y, int
   return MUELLER_OK;
 }
 
+// The same for several complex64 right-hand sides at once: each near block
+// (complex128, read once and rounded to complex64) is applied to RS vectors,
+// so the blocks are read ceil(r / RS) times instead of r times.
+template <int RS>
+__global__ void __launch_bounds__(256, 2) near_spmv_c64_mrhs_kernel(
+    int64_t nn, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+    const double2* __restrict__ blk, const float2* __restrict__ x, float2* __restrict__ y,
+    int64_t xs, int64_t ys, int r) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * 8 + warp;
+  const int s0 = blockIdx.y * RS;
+  if (i >= nn) return;
+  const int64_t H = 2 * nn;
+  float ar[RS][4], ai[RS][4];
+#pragma unroll
+  for (int k = 0; k < RS; ++k)
+#pragma unroll
+    for (int h = 0; h < 4; ++h) ar[k][h] = ai[k][h] = 0.f;
+  for (int32_t q = rowptr[i] + lane; q < rowptr[i + 1]; q += 32) {
+    const int64_t j = col[q];
+    const double2* b = blk + (int64_t)q * 16;
+    float2 m[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      const double2 v = b[e];
+      m[e] = make_float2((float)v.x, (float)v.y);
+    }
+#pragma unroll
+    for (int k = 0; k < RS; ++k) {
+      if (s0 + k < r) {
+        const float2* xv = x + (int64_t)(s0 + k) * xs;
+        float2 xj[4];
+#pragma unroll
+        for (int gb = 0; gb < 4; ++gb) xj[gb] = xv[(gb >> 1) * H + 2 * j + (gb & 1)];
+#pragma unroll
+        for (int ha = 0; ha < 4; ++ha)
+#pragma unroll
+          for (int gb = 0; gb < 4; ++gb) {
+            const float2 mm = m[ha * 4 + gb];
+            ar[k][ha] = fmaf(mm.x, xj[gb].x, fmaf(-mm.y, xj[gb].y, ar[k][ha]));
+            ai[k][ha] = fmaf(mm.x, xj[gb].y, fmaf(mm.y, xj[gb].x, ai[k][ha]));
+          }
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < RS; ++k)
+#pragma unroll
+    for (int ha = 0; ha < 4; ++ha)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        ar[k][ha] += __shfl_xor_sync(0xffffffffu, ar[k][ha], o);
+        ai[k][ha] += __shfl_xor_sync(0xffffffffu, ai[k][ha], o);
+      }
+  // lane 4k + ha writes output ha of right-hand side s0 + k
+  float vr = 0.f, vi = 0.f;
+#pragma unroll
+  for (int k = 0; k < RS; ++k)
+#pragma unroll
+    for (int ha = 0; ha < 4; ++ha)
+      if (lane == 4 * k + ha) {
+        vr = ar[k][ha];
+        vi = ai[k][ha];
+      }
+  const int k = lane >> 2, ha = lane & 3;
+  if (k < RS && s0 + k < r) {
+    float2* yo = y + (int64_t)(s0 + k) * ys + (ha >> 1) * H + 2 * i + (ha & 1);
+    yo->x += vr;
+    yo->y += vi;
+  }
+}
+
 // y += near x for r complex64 vectors, near blocks complex128 (FP32 arithmetic)
 mueller_status near_apply_c64(const mueller_mesh* m, const void* near_c128, const void* X, void* Y,
                               int r, cudaStream_t s) {
   const int64_t N = 4 * m->nn;
+  if (r >= 2) {
+    constexpr int RS = 8;
+    dim3 g(nblk(m->nn, 8), (r + RS - 1) / RS);
+    { Prof prof_("near_spmv_c64_mrhs_kernel", s); near_spmv_c64_mrhs_kernel<RS><<<g, 256, 0, s>>>(m->nn, m->near_rowptr, m->near_col, (const double2*)near_c128, (const float2*)X, (float2*)Y, N, N, r); }
+    MU_CHECK_LAUNCH("near_spmv_c64_mrhs_kernel");
+    return MUELLER_OK;
+  }
   dim3 g(nblk(m->nn, 8), r);
   { Prof prof_("near_spmv_kernel<double2, float2>", s); near_spmv_kernel<double2, float2><<<g, 256, 0, s>>>(m->nn, m->near_rowptr, m->near_col, (const double2*)near_c128, (const float2*)X, (float2*)Y, N, N, r); }
   MU_CHECK_LAUNCH("near_spmv_kernel<double2, float2>");

@@ -322,6 +322,193 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same product with Z on the N side of the MMA: D (M = 128 lanes: rows of
+// X' = [B'hi; B'lo] stacked, or one of them) x (N = 256 columns: Z rows).  A
+// tcgen05 MMA costs about the same for any N up to 256, so one MMA now covers
+// 256 Z rows instead of 128.  K tiles are 16 floats (64-byte rows, 64-byte
+// swizzle) so that five stages of {Z 16 KB, Z remainder 16 KB, X' 8 KB} fit.
+// Stacked (2 nprime <= 128): per K step D += X'[hi;lo] Zhi + X'[hi;lo] Zlo,
+// lanes c and nprime + c both add into output component c.  Unstacked
+// (nprime <= 128): D += X'hi Zhi + X'lo Zhi + X'hi Zlo.
+constexpr int ZN = 256;   // Z rows per CTA (MMA N)
+constexpr int ZBK = 16;   // floats per K tile (64 bytes)
+
+// UMMA descriptor of a K-major tile in the 64-byte swizzle layout: 8-row
+// groups of 512 bytes, layout type SWIZZLE_64B.
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;
+  return d;
+}
+
+struct ZnArgs {
+  int64_t N;
+  int nprime, r, ktiles, kchunk, stages, stacked;
+  float* Y;  // complex64 r x N, accumulated (atomic adds of the real parts)
+  int* err;
+};
+
+// dynamic shared memory: [stages][Z 16 KB | Zlo 16 KB | A0 8 KB | A1 8 KB (unstacked)]
+__global__ void __launch_bounds__(THREADS, 1)
+    mrhs_zn_kernel(const __grid_constant__ CUtensorMap mapZ,
+                   const __grid_constant__ CUtensorMap mapA0,
+                   const __grid_constant__ CUtensorMap mapA1, ZnArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  constexpr uint32_t ZB = ZN * ZBK * 4;   // 16 KB
+  constexpr uint32_t AB = BM * ZBK * 4;   // 8 KB
+  const uint32_t stage_bytes = 2 * ZB + (a.stacked ? 1 : 2) * AB;
+  uint64_t* full = (uint64_t*)(base + (size_t)a.stages * stage_bytes);
+  uint64_t* split = full + a.stages;
+  uint64_t* empty = split + a.stages;
+  uint64_t* accf = empty + a.stages;
+  uint32_t* tmem_slot = (uint32_t*)(accf + 1);
+  volatile int* bail = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t n0 = (int64_t)blockIdx.x * ZN;
+  const int kt0 = blockIdx.y * a.kchunk;
+  const int nk = min(a.ktiles, kt0 + a.kchunk) - kt0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < a.stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&split[s], 128);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accf, 1);
+    *bail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(256));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tmem_slot;
+
+  auto Z_of = [&](int s) { return base + (size_t)s * stage_bytes; };
+  auto Zlo_of = [&](int s) { return base + (size_t)s * stage_bytes + ZB; };
+  auto A0_of = [&](int s) { return base + (size_t)s * stage_bytes + 2 * ZB; };
+  auto A1_of = [&](int s) { return base + (size_t)s * stage_bytes + 2 * ZB + AB; };
+
+  if (warp == 0) {
+    // ---------------- TMA producer
+    if (lane == 0) {
+      int issued = 0;
+      for (int it = 0; it < nk; ++it) {
+        const int s = it % a.stages;
+        if (!mbar_wait(&empty[s], ((it / a.stages) & 1) ^ 1) || *bail) {
+          atomicExch(a.err, 1);
+          *bail = 1;
+          break;
+        }
+        mbar_expect_tx(&full[s], ZB + (a.stacked ? 1 : 2) * AB);
+        const int kc = (kt0 + it) * ZBK;
+        tma_load_2d(Z_of(s), &mapZ, &full[s], kc, (int)n0);
+        tma_load_2d(A0_of(s), &mapA0, &full[s], kc, 0);
+        if (!a.stacked) tma_load_2d(A1_of(s), &mapA1, &full[s], kc, 0);
+        ++issued;
+      }
+      for (int it = max(0, issued - a.stages); it < issued; ++it)
+        mbar_wait(&full[it % a.stages], (it / a.stages) & 1);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(ZN >> 3) << 17) |
+                             ((uint32_t)(BM >> 4) << 24);
+      for (int it = 0; it < nk; ++it) {
+        const int s = it % a.stages;
+        if (!mbar_wait(&split[s], (it / a.stages) & 1) || *bail) {
+          atomicExch(a.err, 2);
+          *bail = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint64_t dZ = sw64_desc(smem_u32(Z_of(s)));
+        const uint64_t dZl = sw64_desc(smem_u32(Zlo_of(s)));
+        const uint64_t dA0 = sw64_desc(smem_u32(A0_of(s)));
+        const uint64_t dA1 = sw64_desc(smem_u32(A1_of(s)));
+#pragma unroll
+        for (int k = 0; k < ZBK / MMA_K; ++k) {
+          const uint64_t off = (uint64_t)((k * MMA_K * 4) >> 4);  // 32 bytes per K step
+          mma_tf32(tmem, dA0 + off, dZ + off, idesc, (it > 0 || k > 0) ? 1u : 0u);
+          if (!a.stacked) mma_tf32(tmem, dA1 + off, dZ + off, idesc, 1u);
+          mma_tf32(tmem, dA0 + off, dZl + off, idesc, 1u);
+        }
+        mma_commit(&empty[s]);
+      }
+      mma_commit(accf);
+    }
+  } else if (warp < 6) {
+    // ---------------- Z remainder (element-wise: same swizzled offsets)
+    const int t = threadIdx.x - 64;  // 0..127
+    for (int it = 0; it < nk; ++it) {
+      const int s = it % a.stages;
+      if (!mbar_wait(&full[s], (it / a.stages) & 1) || *bail) {
+        atomicExch(a.err, 3);
+        *bail = 1;
+        break;
+      }
+      const uint4* __restrict__ Z4 = (const uint4*)Z_of(s);
+      uint4* __restrict__ L4 = (uint4*)Zlo_of(s);
+      constexpr int PER = ZB / 16 / 128;  // 8
+      uint4 v[PER];
+#pragma unroll
+      for (int e = 0; e < PER; ++e) v[e] = Z4[t + 128 * e];
+#pragma unroll
+      for (int e = 0; e < PER; ++e) {
+        uint4 o;
+        o.x = __float_as_uint(__uint_as_float(v[e].x) - __uint_as_float(v[e].x & 0xFFFFE000u));
+        o.y = __float_as_uint(__uint_as_float(v[e].y) - __uint_as_float(v[e].y & 0xFFFFE000u));
+        o.z = __float_as_uint(__uint_as_float(v[e].z) - __uint_as_float(v[e].z & 0xFFFFE000u));
+        o.w = __float_as_uint(__uint_as_float(v[e].w) - __uint_as_float(v[e].w & 0xFFFFE000u));
+        L4[t + 128 * e] = o;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(&split[s]);
+    }
+    // ---------------- epilogue: lane l of D = component l (mod nprime if stacked)
+    const bool ok = mbar_wait(accf, 0);
+    if (!ok) atomicExch(a.err, 4);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const int quarter = warp & 3;
+    const int l = quarter * 32 + lane;
+    const int comp = a.stacked && l >= a.nprime ? l - a.nprime : l;
+    const bool valid = ok && l < (a.stacked ? 2 * a.nprime : a.nprime) && (comp >> 1) < a.r;
+    float* yb = a.Y + 2 * ((int64_t)(comp >> 1) * a.N) + (comp & 1);
+    const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
+    for (int c0 = 0; c0 < ZN; c0 += 16) {
+      uint32_t v[16];
+      tmem_ld16(lane_addr + (uint32_t)c0, v);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (valid) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const int64_t row = n0 + c0 + e;
+          if (row < a.N) atomicAdd(yb + 2 * row, __uint_as_float(v[e]));
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+  }
+}
+
 // B' head / remainder (nprime x 2N, K-major) from X (complex64 r x N)
 __global__ void build_bprime_kernel(const float2* __restrict__ X, int64_t N, int r, int nprime,
                                     float* __restrict__ Bhi, float* __restrict__ Blo) {
@@ -371,7 +558,8 @@ EncodeTiledFn encode_fn() {
 }
 
 bool make_map(CUtensorMap* map, const void* ptr, uint64_t inner, uint64_t outer,
-              uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer) {
+              uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer,
+              CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {inner, outer};
@@ -379,7 +567,7 @@ bool make_map(CUtensorMap* map, const void* ptr, uint64_t inner, uint64_t outer,
   cuuint32_t box[2] = {box_inner, box_outer};
   cuuint32_t estr[2] = {1, 1};
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(ptr), dims, strides, box,
-            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -420,6 +608,43 @@ mueller_status mrhs_matvec_c64(const void* Z, int64_t N, int64_t ldz, const void
         (const float2*)X, N, r, nprime, Bhi, Blo);
   }
   MU_CHECK_LAUNCH("build_bprime_kernel");
+  if (nprime <= BM) {
+    // Z on the N side: 256 Z rows per MMA
+    const int zstacked = 2 * nprime <= BM ? 1 : 0;
+    CUtensorMap mZ, mA0, mA1;
+    const uint64_t arows = zstacked ? 2 * (uint64_t)nprime : (uint64_t)nprime;
+    if (!make_map(&mZ, Z, (uint64_t)2 * N, (uint64_t)N, (uint64_t)ldz * 8, ZBK, ZN,
+                  CU_TENSOR_MAP_SWIZZLE_64B) ||
+        !make_map(&mA0, Bhi, (uint64_t)2 * N, arows, (uint64_t)2 * N * 4, ZBK, BM,
+                  CU_TENSOR_MAP_SWIZZLE_64B) ||
+        !make_map(&mA1, Blo, (uint64_t)2 * N, (uint64_t)nprime, (uint64_t)2 * N * 4, ZBK, BM,
+                  CU_TENSOR_MAP_SWIZZLE_64B)) {
+      set_error("cuTensorMapEncodeTiled failed (driver entry point or layout)");
+      return MUELLER_ERR_CUDA;
+    }
+    ZnArgs z;
+    z.N = N;
+    z.nprime = nprime;
+    z.r = r;
+    z.ktiles = (int)cdiv(2 * N, ZBK);
+    z.stacked = zstacked;
+    z.Y = (float*)Y;
+    z.err = err;
+    const int64_t ntiles = cdiv(N, ZN);
+    int ksplit = (int)std::max<int64_t>(1, std::min<int64_t>(z.ktiles / 16, cdiv(4 * 152, ntiles)));
+    z.kchunk = (int)cdiv(z.ktiles, ksplit);
+    ksplit = (int)cdiv(z.ktiles, z.kchunk);
+    const size_t stage_bytes = 2 * (size_t)ZN * ZBK * 4 + (zstacked ? 1 : 2) * (size_t)BM * ZBK * 4;
+    z.stages = (int)std::min<size_t>(8, (SMEM_BUDGET - 2048) / stage_bytes);
+    const size_t smem = 1024 + z.stages * stage_bytes + (3 * z.stages + 1) * 8 + 16;
+    MU_CUDA(cudaFuncSetAttribute(mrhs_zn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    {
+      Prof prof_("mrhs_zn_kernel", s);
+      mrhs_zn_kernel<<<dim3((unsigned)ntiles, (unsigned)ksplit), THREADS, smem, s>>>(mZ, mA0, mA1, z);
+    }
+    MU_CHECK_LAUNCH("mrhs_zn_kernel");
+    return MUELLER_OK;
+  }
   CUtensorMap mZ, mBh, mBl;
   if (!make_map(&mZ, Z, (uint64_t)2 * N, (uint64_t)N, (uint64_t)ldz * 8, BK, BM) ||
       !make_map(&mBh, Bhi, (uint64_t)2 * N, (uint64_t)nprime, (uint64_t)2 * N * 4, BK, nprime) ||
