@@ -1,4 +1,6 @@
-// Multi-right-hand-side product Y = Z X on the tcgen05 tensor cores.
+// Multi-right-hand-side product Y = Z X on the tcgen05 tensor cores.  Two
+// kernels: mrhs_zn_kernel (r <= 64, Z on the MMA's N side, described before
+// it) and mrhs_tf32_kernel (any r up to 128, Z on the M side), described here.
 //
 // Z is the complex64 N x N matrix of the mixed operator (row-major, ldz), X
 // and Y hold r complex64 vectors.  The complex product is a real GEMM:
