@@ -197,6 +197,29 @@ mueller_status mueller_tangent_frame(mueller_mesh* mesh, int32_t frame_rule, dou
 mueller_status mueller_assemble(mueller_mesh* mesh, const mueller_params* params, int32_t dtype,
                                 void* Z_dev, int64_t ldz, void* near_dev, void* B_dev,
                                 const double* inc, int32_t r, void* stream);
+/*
+ * mueller_assemble_batch -- what mueller_assemble computes, for n_bodies
+ * bodies at once: the regular pairs of every body run in one kernel launch
+ * and the touching pairs of every body in another (a work list of (body,
+ * tile) and (body, pair) entries, largest bodies first), so that many small
+ * bodies fill the GPU together.  The paper treats one body; batching many
+ * scatterers is an extension of this library.
+ *   meshes[b], params[b]   one loaded mesh (mueller_tangent_frame done) and
+ *            its parameters per body; every body must use the same q_regular
+ *            and ssq_order (else INVALID_ARG); k_a, eps_r, mu_r may differ.
+ *   dtype    as in mueller_assemble, for every body.
+ *   Z[b], ldz[b], near[b]   per-body outputs as in mueller_assemble (near may
+ *            be NULL for MUELLER_C128).
+ *   B, inc, r   optional (all NULL, or all given): B[b] may be NULL for a
+ *            body without right-hand sides; else inc[b] (host, r[b] x 6).
+ * Errors: INVALID_ARG (naming the body), STATE, DEGENERATE_FRAME, CUDA.
+ */
+mueller_status mueller_assemble_batch(int32_t n_bodies, mueller_mesh* const* meshes,
+                                      const mueller_params* params, int32_t dtype,
+                                      void* const* Z_dev, const int64_t* ldz,
+                                      void* const* near_dev, void* const* B_dev,
+                                      const double* const* inc, const int32_t* r, void* stream);
+
 /* bytes of the complex128 near-part buffer of a loaded mesh */
 size_t mueller_near_bytes(const mueller_mesh* mesh);
 

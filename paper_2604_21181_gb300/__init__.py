@@ -24,6 +24,7 @@ from .api import (  # noqa: F401
     Params,
     SolverOpts,
     assemble,
+    assemble_batch,
     far_field,
     launch_count,
     load_library,

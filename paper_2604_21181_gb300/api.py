@@ -74,7 +74,7 @@ EXPORTS = [
     "mueller_matvec_workspace_bytes", "mueller_far_field", "mueller_sync",
     "mueller_profile_enable", "mueller_profile_reset", "mueller_launch_count",
     "mueller_profile_get", "mueller_profile_names", "mueller_far_field_noalloc",
-    "mueller_matvec_mrhs", "mueller_matvec_mrhs_workspace_bytes",
+    "mueller_matvec_mrhs", "mueller_matvec_mrhs_workspace_bytes", "mueller_assemble_batch",
 ]
 
 _lib = None
@@ -122,6 +122,9 @@ def load_library(build_if_missing: bool = True):
                                                 dp, i32, i32, vp]),
         "mueller_matvec_mrhs": (C.c_int, [C.POINTER(COperator), vp, vp, i32, vp, C.c_size_t, vp]),
         "mueller_matvec_mrhs_workspace_bytes": (C.c_size_t, [C.POINTER(COperator), i32]),
+        "mueller_assemble_batch": (C.c_int, [i32, C.POINTER(vp), C.POINTER(CParams), i32,
+                                             C.POINTER(vp), C.POINTER(i64), C.POINTER(vp),
+                                             C.POINTER(vp), C.POINTER(dp), ip, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -274,6 +277,43 @@ def assemble(mesh: Mesh, params: Params, dtype: int = MUELLER_C128, inc=None, Z=
     _check(mesh._lib.mueller_assemble(mesh.h, C.byref(p), int(dtype), _ptr(Z), Z.stride(0), _ptr(near),
                                       _ptr(B), incp, r, _stream(stream)))
     return Z, near, B
+
+
+def assemble_batch(meshes, params, dtype: int = MUELLER_C64_NEAR64, incs=None, stream=None):
+    """mueller_assemble_batch: one launch of each assembly kernel for all bodies.
+    Returns a list of (Z, near, B) per body as CUDA tensors."""
+    torch = _torch()
+    lib = load_library()
+    nb = len(meshes)
+    if len(params) != nb or (incs is not None and len(incs) != nb):
+        raise ValueError("one params (and inc) entry per mesh")
+    out, keep = [], []
+    for b, m in enumerate(meshes):
+        N = m.N
+        Z = torch.empty((N, N), dtype=torch.complex128 if dtype == MUELLER_C128 else torch.complex64,
+                        device="cuda")
+        near = (torch.empty(m.near_bytes() // 16, dtype=torch.complex128, device="cuda")
+                if dtype == MUELLER_C64_NEAR64 else None)
+        B = None
+        if incs is not None:
+            inc = np.ascontiguousarray(incs[b], dtype=np.float64).reshape(-1, 6)
+            keep.append(inc)
+            B = torch.empty((inc.shape[0], N), dtype=torch.complex128, device="cuda")
+        out.append((Z, near, B))
+    vp = C.c_void_p
+    h = (vp * nb)(*[m.h for m in meshes])
+    cps = (CParams * nb)(*[p.c() for p in params])
+    zs = (vp * nb)(*[o[0].data_ptr() for o in out])
+    lds = (C.c_int64 * nb)(*[o[0].stride(0) for o in out])
+    ns = (vp * nb)(*[(o[1].data_ptr() if o[1] is not None else None) for o in out])
+    bs = incp = rs = None
+    if incs is not None:
+        bs = (vp * nb)(*[o[2].data_ptr() for o in out])
+        incp = (C.POINTER(C.c_double) * nb)(*[_dp(a) for a in keep])
+        rs = (C.c_int32 * nb)(*[a.shape[0] for a in keep])
+    _check(lib.mueller_assemble_batch(nb, h, cps, int(dtype), zs, lds, ns, bs, incp, rs,
+                                      _stream(stream)))
+    return out
 
 
 class Operator:

@@ -13,6 +13,9 @@
 // atomic additions.
 #include <math.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "common.cuh"
 #include "kernels.cuh"
 #include "p2.cuh"
@@ -106,18 +109,20 @@ struct RegCfg {
                    (size_t)WARPS * Q * Q * 24);
 };
 
+// One CTA tile (test elements bx*WARPS.., trial elements by*TY..) of one body.
 template <class R, int Q>
-__global__ void __launch_bounds__(128) regular_kernel(int64_t nt, const R* __restrict__ qd,
-                                                      const int32_t* __restrict__ T, KConst<R> K,
-                                                      R* __restrict__ Z, int64_t ldz, int64_t H) {
+__device__ __forceinline__ void regular_tile(int64_t bx, int64_t by, int64_t nt,
+                                             const R* __restrict__ qd,
+                                             const int32_t* __restrict__ T, const KConst<R>& K,
+                                             R* __restrict__ Z, int64_t ldz, int64_t H) {
   using C = RegCfg<R, Q>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* sY = reinterpret_cast<R*>(smem_raw);               // TY*Q*QD_STRIDE
   R* sX = sY + (size_t)C::TY * Q * QD_STRIDE;           // WARPS*Q*QD_STRIDE
   R* sK = sX + (size_t)C::WARPS * Q * QD_STRIDE;        // WARPS*Q*Q*24
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t ex = (int64_t)blockIdx.x * C::WARPS + warp;
-  const int64_t ey0 = (int64_t)blockIdx.y * C::TY;
+  const int64_t ex = bx * C::WARPS + warp;
+  const int64_t ey0 = by * C::TY;
   const int ny = (int)((nt - ey0) < (int64_t)C::TY ? (nt - ey0) : (int64_t)C::TY);
   // stage the trial tile and the test elements
   for (int i = threadIdx.x; i < ny * Q * QD_STRIDE; i += blockDim.x)
@@ -206,6 +211,52 @@ __global__ void __launch_bounds__(128) regular_kernel(int64_t nt, const R* __res
     }
     __syncwarp();
   }
+}
+
+template <class R, int Q>
+__global__ void __launch_bounds__(128) regular_kernel(int64_t nt, const R* __restrict__ qd,
+                                                      const int32_t* __restrict__ T, KConst<R> K,
+                                                      R* __restrict__ Z, int64_t ldz, int64_t H) {
+  regular_tile<R, Q>(blockIdx.x, blockIdx.y, nt, qd, T, K, Z, ldz, H);
+}
+
+// Many bodies in one launch: CTA t takes tile t - tile0 of the body whose
+// range [tile0, tile0 + tiles) holds t (bodies listed with increasing tile0).
+struct RegBody {
+  int64_t nt, H, ldz, tile0, tiles_x;
+  const void* qd;
+  const int32_t* T;
+  KConst<float> K32;
+  KConst<double> K64;
+  void* Z;
+};
+
+__device__ __forceinline__ int find_body(const int64_t* first, int nb, int64_t t) {
+  int lo = 0, hi = nb - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= t)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+template <class R, int Q>
+__global__ void __launch_bounds__(128) regular_batch_kernel(const RegBody* __restrict__ bodies,
+                                                            const int64_t* __restrict__ first,
+                                                            int nb) {
+  const int64_t t = blockIdx.x;
+  const RegBody& B = bodies[find_body(first, nb, t)];
+  const int64_t local = t - B.tile0;
+  KConst<R> K;
+  if constexpr (sizeof(R) == 4)
+    K = B.K32;
+  else
+    K = B.K64;
+  regular_tile<R, Q>(local % B.tiles_x, local / B.tiles_x, B.nt, (const R*)B.qd, B.T, K, (R*)B.Z,
+                     B.ldz, B.H);
 }
 
 // ------------------------------------------------------- touching pairs
@@ -306,11 +357,12 @@ __device__ __forceinline__ void ssq_group(int cls, int reg, int a, int b, int c,
   }
 }
 
+// One touching element pair (index pid of the body's pair list) per CTA.
 template <int Q>
-__global__ void __launch_bounds__(TT) touching_kernel(
-    int64_t n_touch, const TouchPair* __restrict__ tp, const double* __restrict__ X,
+__device__ __forceinline__ void touching_pair(
+    int64_t pid, const TouchPair* __restrict__ tp, const double* __restrict__ X,
     const int32_t* __restrict__ T, const double* __restrict__ frame,
-    const double* __restrict__ qd, int ns, KConst<double> K, double ae_re, double ae_im,
+    const double* __restrict__ qd, int ns, const KConst<double>& K, double ae_re, double ae_im,
     double am_re, double am_im, int dtype, void* __restrict__ Zv, int64_t ldz, int64_t H,
     double* __restrict__ near, const int32_t* __restrict__ tp_slot, int use_tables) {
   __shared__ d3 sXn[2][6], sT1[2][6], sT2[2][6];
@@ -325,8 +377,6 @@ __global__ void __launch_bounds__(TT) touching_kernel(
   double(*sU)[6] = reinterpret_cast<double(*)[6]>(sbuf);
   double(*sV)[48] = reinterpret_cast<double(*)[48]>(sbuf + TT * 6);
   double* sK = sbuf;
-  const int64_t pid = blockIdx.x;
-  if (pid >= n_touch) return;
   const TouchPair P = tp[pid];
   const int tid = threadIdx.x;
   if (tid < 12) {
@@ -542,6 +592,44 @@ __global__ void __launch_bounds__(TT) touching_kernel(
   }
 }
 
+template <int Q>
+__global__ void __launch_bounds__(TT) touching_kernel(
+    int64_t n_touch, const TouchPair* __restrict__ tp, const double* __restrict__ X,
+    const int32_t* __restrict__ T, const double* __restrict__ frame,
+    const double* __restrict__ qd, int ns, KConst<double> K, double ae_re, double ae_im,
+    double am_re, double am_im, int dtype, void* __restrict__ Zv, int64_t ldz, int64_t H,
+    double* __restrict__ near, const int32_t* __restrict__ tp_slot, int use_tables) {
+  if ((int64_t)blockIdx.x >= n_touch) return;
+  touching_pair<Q>(blockIdx.x, tp, X, T, frame, qd, ns, K, ae_re, ae_im, am_re, am_im, dtype, Zv,
+                   ldz, H, near, tp_slot, use_tables);
+}
+
+struct TouchBody {
+  int64_t n_touch, pair0, H, ldz;
+  const TouchPair* tp;
+  const double* X;
+  const int32_t* T;
+  const double* frame;
+  const double* qd;
+  const int32_t* tp_slot;
+  KConst<double> K;
+  double ae_re, ae_im, am_re, am_im;
+  void* Z;
+  double* near;
+};
+
+// Many bodies in one launch: CTA t takes pair t - pair0 of its body.
+template <int Q>
+__global__ void __launch_bounds__(TT) touching_batch_kernel(const TouchBody* __restrict__ bodies,
+                                                            const int64_t* __restrict__ first,
+                                                            int nb, int ns, int dtype,
+                                                            int use_tables) {
+  const int64_t t = blockIdx.x;
+  const TouchBody& B = bodies[find_body(first, nb, t)];
+  touching_pair<Q>(t - B.pair0, B.tp, B.X, B.T, B.frame, B.qd, ns, B.K, B.ae_re, B.ae_im, B.am_re,
+                   B.am_im, dtype, B.Z, B.ldz, B.H, B.near, B.tp_slot, use_tables);
+}
+
 // Eqs. (rhs_E), (rhs_H): one thread per (RHS, element, local node).
 __global__ void rhs_kernel(int64_t nt, int Q, const double* __restrict__ qd,
                            const int32_t* __restrict__ T, const double* __restrict__ inc, int r,
@@ -644,6 +732,137 @@ mueller_status launch_touching(mueller_mesh* m, const PhysConsts& P, int Q, int 
                                             Z, ldz, 2 * m->nn, (double*)near, m->tp_slot, use_tables); }
   MU_CHECK_LAUNCH("touching_kernel");
   return MUELLER_OK;
+}
+
+namespace {
+
+// bodies in decreasing order of work, so that the large ones start first
+template <class W>
+std::vector<int> by_decreasing(int nb, W work) {
+  std::vector<int> order(nb);
+  for (int b = 0; b < nb; ++b) order[b] = b;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work(x) > work(y); });
+  return order;
+}
+
+template <class Body>
+mueller_status upload_bodies(const std::vector<Body>& bodies, const std::vector<int64_t>& first,
+                             void** buf, Body** d_bodies, int64_t** d_first, cudaStream_t s) {
+  const size_t nb = bodies.size();
+  const size_t bytes_b = (nb * sizeof(Body) + 255) & ~size_t(255);
+  MU_CUDA(cudaMallocAsync(buf, bytes_b + nb * sizeof(int64_t), s));
+  *d_bodies = (Body*)*buf;
+  *d_first = (int64_t*)((char*)*buf + bytes_b);
+  // pageable sources: the copies have consumed them when the calls return
+  MU_CUDA(cudaMemcpyAsync(*d_bodies, bodies.data(), nb * sizeof(Body), cudaMemcpyHostToDevice, s));
+  MU_CUDA(cudaMemcpyAsync(*d_first, first.data(), nb * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  return MUELLER_OK;
+}
+
+template <class R, int Q>
+mueller_status regular_batch_t(int nb, mueller_mesh* const* meshes, const PhysConsts* P,
+                               void* const* Z, const int64_t* ldz, cudaStream_t s) {
+  using C = RegCfg<R, Q>;
+  std::vector<int> order = by_decreasing(nb, [&](int b) { return meshes[b]->nt; });
+  std::vector<RegBody> bodies;
+  std::vector<int64_t> first;
+  int64_t tiles = 0;
+  for (int b : order) {
+    const mueller_mesh* m = meshes[b];
+    RegBody B;
+    B.nt = m->nt;
+    B.H = 2 * m->nn;
+    B.ldz = ldz[b];
+    B.tiles_x = (m->nt + C::WARPS - 1) / C::WARPS;
+    B.tile0 = tiles;
+    B.qd = sizeof(R) == 8 ? (const void*)m->qd64 : (const void*)m->qd32;
+    B.T = m->T;
+    B.K32 = kconst<float>(P[b]);
+    B.K64 = kconst<double>(P[b]);
+    B.Z = Z[b];
+    bodies.push_back(B);
+    first.push_back(tiles);
+    tiles += B.tiles_x * ((m->nt + C::TY - 1) / C::TY);
+  }
+  void* buf = nullptr;
+  RegBody* d_bodies = nullptr;
+  int64_t* d_first = nullptr;
+  mueller_status st = upload_bodies(bodies, first, &buf, &d_bodies, &d_first, s);
+  if (st) return st;
+  auto kern = regular_batch_kernel<R, Q>;
+  MU_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
+  { Prof prof_("regular_batch_kernel<R,Q>", s); kern<<<(unsigned)tiles, 32 * C::WARPS, C::smem, s>>>(d_bodies, d_first, nb); }
+  MU_CHECK_LAUNCH("regular_batch_kernel");
+  cudaFreeAsync(buf, s);
+  return MUELLER_OK;
+}
+
+template <int Q>
+mueller_status touching_batch_t(int nb, mueller_mesh* const* meshes, const PhysConsts* P, int ns,
+                                int dtype, void* const* Z, const int64_t* ldz,
+                                void* const* near, cudaStream_t s) {
+  std::vector<int> order = by_decreasing(nb, [&](int b) { return meshes[b]->n_touch; });
+  std::vector<TouchBody> bodies;
+  std::vector<int64_t> first;
+  int64_t pairs = 0;
+  for (int b : order) {
+    const mueller_mesh* m = meshes[b];
+    if (m->n_touch == 0) continue;
+    TouchBody B;
+    B.n_touch = m->n_touch;
+    B.pair0 = pairs;
+    B.H = 2 * m->nn;
+    B.ldz = ldz[b];
+    B.tp = m->tp;
+    B.X = m->X;
+    B.T = m->T;
+    B.frame = m->frame;
+    B.qd = m->qd64;
+    B.tp_slot = m->tp_slot;
+    B.K = kconst<double>(P[b]);
+    B.ae_re = 0.5 * (P[b].eps_re + 1.0);
+    B.ae_im = 0.5 * P[b].eps_im;
+    B.am_re = 0.5 * (P[b].mu_re + 1.0);
+    B.am_im = 0.5 * P[b].mu_im;
+    B.Z = Z[b];
+    B.near = near ? (double*)near[b] : nullptr;
+    bodies.push_back(B);
+    first.push_back(pairs);
+    pairs += m->n_touch;
+  }
+  if (pairs == 0) return MUELLER_OK;
+  void* buf = nullptr;
+  TouchBody* d_bodies = nullptr;
+  int64_t* d_first = nullptr;
+  mueller_status st = upload_bodies(bodies, first, &buf, &d_bodies, &d_first, s);
+  if (st) return st;
+  auto kern = touching_batch_kernel<Q>;
+  const int use_tables = ns <= MAX_TAB_NS ? 1 : 0;
+  const size_t tab_bytes = use_tables ? (size_t)2 * (ns * ns + ns * ns * ns) * GT * sizeof(double) : 0;
+  MU_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tab_bytes));
+  { Prof prof_("touching_batch_kernel<Q>", s); kern<<<(unsigned)pairs, TT, tab_bytes, s>>>(d_bodies, d_first, (int)bodies.size(), ns, dtype, use_tables); }
+  MU_CHECK_LAUNCH("touching_batch_kernel");
+  cudaFreeAsync(buf, s);
+  return MUELLER_OK;
+}
+
+}  // namespace
+
+// regular and touching pairs of nb bodies (same rule Q and order ns), one
+// launch each
+mueller_status launch_assemble_batch(int nb, mueller_mesh* const* meshes, const PhysConsts* P,
+                                     int Q, int ns, int dtype, void* const* Z,
+                                     const int64_t* ldz, void* const* near, cudaStream_t s) {
+  mueller_status st;
+  if (dtype == MUELLER_C128)
+    st = Q == 6 ? regular_batch_t<double, 6>(nb, meshes, P, Z, ldz, s)
+                : regular_batch_t<double, 12>(nb, meshes, P, Z, ldz, s);
+  else
+    st = Q == 6 ? regular_batch_t<float, 6>(nb, meshes, P, Z, ldz, s)
+                : regular_batch_t<float, 12>(nb, meshes, P, Z, ldz, s);
+  if (st) return st;
+  return Q == 6 ? touching_batch_t<6>(nb, meshes, P, ns, dtype, Z, ldz, near, s)
+                : touching_batch_t<12>(nb, meshes, P, ns, dtype, Z, ldz, near, s);
 }
 
 mueller_status launch_mass_rhs(mueller_mesh* m, const PhysConsts& P, int Q, int dtype, void* Z,

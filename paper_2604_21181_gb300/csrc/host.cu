@@ -508,6 +508,66 @@ mueller_status mueller_assemble(mueller_mesh* m, const mueller_params* p, int32_
   return st;
 }
 
+mueller_status mueller_assemble_batch(int32_t n_bodies, mueller_mesh* const* meshes,
+                                      const mueller_params* params, int32_t dtype,
+                                      void* const* Z, const int64_t* ldz, void* const* near,
+                                      void* const* B, const double* const* inc, const int32_t* r,
+                                      void* stream) {
+  if (n_bodies < 1 || !meshes || !params || !Z || !ldz)
+    return fail(MUELLER_ERR_INVALID_ARG, "n_bodies < 1 or a NULL array");
+  if (dtype != MUELLER_C128 && dtype != MUELLER_C64_NEAR64)
+    return fail(MUELLER_ERR_INVALID_ARG, "unknown dtype");
+  if (dtype == MUELLER_C64_NEAR64 && !near) return fail(MUELLER_ERR_INVALID_ARG, "near buffers required");
+  if (B && (!inc || !r)) return fail(MUELLER_ERR_INVALID_ARG, "B given without inc and r");
+  const int q = params[0].q_regular, ns = params[0].ssq_order;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<PhysConsts> P(n_bodies);
+  for (int b = 0; b < n_bodies; ++b) {
+    mueller_mesh* m = meshes[b];
+    const mueller_params* p = params + b;
+    const std::string who = "body " + std::to_string(b) + ": ";
+    if (!m) return fail(MUELLER_ERR_INVALID_ARG, who + "mesh is NULL");
+    mueller_status st = check_params(p);
+    if (st) return st;
+    if (p->q_regular != q || p->ssq_order != ns)
+      return fail(MUELLER_ERR_INVALID_ARG, who + "all bodies must share q_regular and ssq_order");
+    const int64_t N = 4 * m->nn;
+    if (!Z[b] || ldz[b] < N) return fail(MUELLER_ERR_INVALID_ARG, who + "Z is NULL or ldz < N");
+    if (dtype == MUELLER_C64_NEAR64 && !near[b]) return fail(MUELLER_ERR_INVALID_ARG, who + "near is NULL");
+    if (B && B[b] && (r[b] < 1 || !inc[b])) return fail(MUELLER_ERR_INVALID_ARG, who + "B without r >= 1 and inc");
+    if (p->frame_rule != m->frame_rule || !m->has_frame)
+      return fail(MUELLER_ERR_STATE, who + "call mueller_tangent_frame with params->frame_rule first");
+    st = ensure_geometry(m, q, s);
+    if (st) return st;
+    P[b] = make_phys(p);
+  }
+  TriangleRule rule;
+  triangle_rule(q, rule);
+  mueller_status st = upload_rules(rule, ns);
+  if (st) return st;
+  const size_t esz = dtype == MUELLER_C128 ? 16 : 8;
+  for (int b = 0; b < n_bodies; ++b) {
+    const int64_t N = 4 * meshes[b]->nn;
+    MU_CUDA(cudaMemsetAsync(Z[b], 0, (size_t)N * ldz[b] * esz, s));
+    if (dtype == MUELLER_C64_NEAR64) MU_CUDA(cudaMemsetAsync(near[b], 0, mueller_near_bytes(meshes[b]), s));
+  }
+  st = launch_assemble_batch(n_bodies, meshes, P.data(), q, ns, dtype, Z, ldz, near, s);
+  for (int b = 0; b < n_bodies && !st; ++b) {
+    mueller_mesh* m = meshes[b];
+    const int64_t N = 4 * m->nn;
+    double* inc_dev = nullptr;
+    if (B && B[b]) {
+      MU_CUDA(cudaMemsetAsync(B[b], 0, (size_t)r[b] * N * 16, s));
+      MU_CUDA(cudaMallocAsync((void**)&inc_dev, (size_t)r[b] * 6 * sizeof(double), s));
+      MU_CUDA(cudaMemcpyAsync(inc_dev, inc[b], (size_t)r[b] * 6 * sizeof(double), cudaMemcpyHostToDevice, s));
+      st = launch_mass_rhs(m, P[b], q, dtype, Z[b], ldz[b], near ? near[b] : nullptr, B[b], inc_dev, r[b], s);
+    }
+    if (!st) st = launch_mirror_k1(N, dtype, Z[b], ldz[b], s);
+    if (inc_dev) cudaFreeAsync(inc_dev, s);
+  }
+  return st;
+}
+
 size_t mueller_precond_bytes(int64_t n_dof, int64_t block) {
   if (n_dof <= 0 || block <= 0) return 0;
   int64_t H = n_dof / 2, nb = (H + block - 1) / block;

@@ -9,7 +9,7 @@ the oracle can both consume the same arrays without sharing any method code.
 
 from .meshes import icosphere_p2, spheroid_p2, mesh_counts
 from .excitation import plane_wave, fibonacci_directions, fibonacci_plane_waves
-from .configs import WORKLOADS, workload
+from .configs import WORKLOADS, multibody_mesh, multibody_spec, workload
 
 __all__ = [
     "icosphere_p2",

@@ -63,3 +63,11 @@ def multibody_spec(n_bodies: int = 64, seed: int = 20260421):
         bodies.append(dict(prolate=prolate, rho=rho, level=level, eps_r=(eps_re, eps_im),
                            mu_r=(1.0, 0.0), ka=ka))
     return bodies
+
+
+def multibody_mesh(body: dict):
+    """P2 mesh of one multibody_spec entry: prolate (1, 1, rho) or oblate
+    (rho, rho, 1) spheroid at the entry's subdivision level."""
+    if body["prolate"]:
+        return spheroid_p2(body["level"], 1.0, body["rho"])
+    return spheroid_p2(body["level"], body["rho"], 1.0)
