@@ -14,6 +14,10 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -100,22 +104,29 @@ __device__ __forceinline__ bool share_corner(const int32_t* a, const int32_t* b)
 //   1. evaluates the Q*Q point pairs (lanes over point pairs) into Kt[p][q][c],
 //   2. contracts q -> j with the shape values (in place, lanes over (p, c)),
 //   3. contracts p -> i and adds the 6 x 6 x 12 block into Z (lanes over (j, c)).
-template <class R, int Q>
+// Pair-tile shapes (test elements per CTA = warps, trial elements staged):
+// the autotuner picks one per (precision, rule, mesh size).
+constexpr int NSHAPE = 4;
+constexpr int SHAPE_W[NSHAPE] = {4, 8, 2, 4};
+constexpr int SHAPE_TY[NSHAPE] = {32, 16, 64, 16};
+constexpr size_t kMaxRegSmem = 200 * 1024;
+
+template <class R, int Q, int W_, int TY_>
 struct RegCfg {
-  static constexpr int TY = (sizeof(R) == 8 && Q == 12) ? 16 : 32;
-  static constexpr int WARPS = 4;
+  static constexpr int TY = TY_;
+  static constexpr int WARPS = W_;
   static constexpr size_t smem =
       sizeof(R) * ((size_t)TY * Q * QD_STRIDE + (size_t)WARPS * Q * QD_STRIDE +
                    (size_t)WARPS * Q * Q * 24);
 };
 
 // One CTA tile (test elements bx*WARPS.., trial elements by*TY..) of one body.
-template <class R, int Q>
+template <class R, int Q, int W, int TYT>
 __device__ __forceinline__ void regular_tile(int64_t bx, int64_t by, int64_t nt,
                                              const R* __restrict__ qd,
                                              const int32_t* __restrict__ T, const KConst<R>& K,
                                              R* __restrict__ Z, int64_t ldz, int64_t H) {
-  using C = RegCfg<R, Q>;
+  using C = RegCfg<R, Q, W, TYT>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* sY = reinterpret_cast<R*>(smem_raw);               // TY*Q*QD_STRIDE
   R* sX = sY + (size_t)C::TY * Q * QD_STRIDE;           // WARPS*Q*QD_STRIDE
@@ -213,11 +224,11 @@ __device__ __forceinline__ void regular_tile(int64_t bx, int64_t by, int64_t nt,
   }
 }
 
-template <class R, int Q>
-__global__ void __launch_bounds__(128) regular_kernel(int64_t nt, const R* __restrict__ qd,
-                                                      const int32_t* __restrict__ T, KConst<R> K,
-                                                      R* __restrict__ Z, int64_t ldz, int64_t H) {
-  regular_tile<R, Q>(blockIdx.x, blockIdx.y, nt, qd, T, K, Z, ldz, H);
+template <class R, int Q, int W, int TYT>
+__global__ void __launch_bounds__(32 * W) regular_kernel(int64_t nt, const R* __restrict__ qd,
+                                                         const int32_t* __restrict__ T, KConst<R> K,
+                                                         R* __restrict__ Z, int64_t ldz, int64_t H) {
+  regular_tile<R, Q, W, TYT>(blockIdx.x, blockIdx.y, nt, qd, T, K, Z, ldz, H);
 }
 
 // Many bodies in one launch: CTA t takes tile t - tile0 of the body whose
@@ -243,10 +254,10 @@ __device__ __forceinline__ int find_body(const int64_t* first, int nb, int64_t t
   return lo;
 }
 
-template <class R, int Q>
-__global__ void __launch_bounds__(128) regular_batch_kernel(const RegBody* __restrict__ bodies,
-                                                            const int64_t* __restrict__ first,
-                                                            int nb) {
+template <class R, int Q, int W, int TYT>
+__global__ void __launch_bounds__(32 * W) regular_batch_kernel(const RegBody* __restrict__ bodies,
+                                                               const int64_t* __restrict__ first,
+                                                               int nb) {
   const int64_t t = blockIdx.x;
   const RegBody& B = bodies[find_body(first, nb, t)];
   const int64_t local = t - B.tile0;
@@ -255,8 +266,8 @@ __global__ void __launch_bounds__(128) regular_batch_kernel(const RegBody* __res
     K = B.K32;
   else
     K = B.K64;
-  regular_tile<R, Q>(local % B.tiles_x, local / B.tiles_x, B.nt, (const R*)B.qd, B.T, K, (R*)B.Z,
-                     B.ldz, B.H);
+  regular_tile<R, Q, W, TYT>(local % B.tiles_x, local / B.tiles_x, B.nt, (const R*)B.qd, B.T, K,
+                             (R*)B.Z, B.ldz, B.H);
 }
 
 // ------------------------------------------------------- touching pairs
@@ -689,19 +700,117 @@ KConst<R> kconst(const PhysConsts& P) {
   return K;
 }
 
+// one single-body launch of pair-tile shape S (false if it does not fit)
+template <class R, int Q, int S>
+bool regular_shape_launch(int64_t nt, const R* qd, const int32_t* T, const KConst<R>& K, R* Z,
+                          int64_t ldz, int64_t H, cudaStream_t s) {
+  constexpr int W = SHAPE_W[S], TYT = SHAPE_TY[S];
+  using C = RegCfg<R, Q, W, TYT>;
+  if (C::smem > kMaxRegSmem) return false;
+  auto kern = regular_kernel<R, Q, W, TYT>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem) != cudaSuccess)
+    return false;
+  dim3 grid((unsigned)((nt + W - 1) / W), (unsigned)((nt + TYT - 1) / TYT));
+  { Prof prof_("regular_kernel<R,Q>", s); kern<<<grid, 32 * W, C::smem, s>>>(nt, qd, T, K, Z, ldz, H); }
+  return true;
+}
+
+template <class R, int Q>
+bool regular_launch(int shape, int64_t nt, const R* qd, const int32_t* T, const KConst<R>& K, R* Z,
+                    int64_t ldz, int64_t H, cudaStream_t s) {
+  switch (shape) {
+    case 0: return regular_shape_launch<R, Q, 0>(nt, qd, T, K, Z, ldz, H, s);
+    case 1: return regular_shape_launch<R, Q, 1>(nt, qd, T, K, Z, ldz, H, s);
+    case 2: return regular_shape_launch<R, Q, 2>(nt, qd, T, K, Z, ldz, H, s);
+    default: return regular_shape_launch<R, Q, 3>(nt, qd, T, K, Z, ldz, H, s);
+  }
+}
+
+template <class R, int Q>
+constexpr int default_shape() {
+  return RegCfg<R, Q, SHAPE_W[0], SHAPE_TY[0]>::smem <= kMaxRegSmem ? 0 : 3;
+}
+
+// Autotuner of the regular-pair tile shape, per (precision, rule, mesh size
+// rounded up to a power of two).  MUELLER_REGULAR_TILE = 0..3 forces a shape,
+// MUELLER_AUTOTUNE = 0 keeps the default one.  Tuning times every shape that
+// fits once on the caller's mesh (adding into its Z, which is zeroed again
+// afterwards) and remembers the fastest for the process.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int64_t>, int> g_tuned;
+
+int forced_shape() {
+  const char* e = getenv("MUELLER_REGULAR_TILE");
+  if (!e || !*e) return -1;
+  const int v = atoi(e);
+  return v >= 0 && v < NSHAPE ? v : -1;
+}
+
+template <class R, int Q>
+mueller_status regular_shape_for(int64_t nt, const R* qd, const int32_t* T, const KConst<R>& K,
+                                 R* Z, int64_t ldz, int64_t H, cudaStream_t s, int* shape) {
+  const int f = forced_shape();
+  if (f >= 0) {
+    *shape = f;
+    return MUELLER_OK;
+  }
+  const char* a = getenv("MUELLER_AUTOTUNE");
+  if (a && a[0] == '0') {
+    *shape = default_shape<R, Q>();
+    return MUELLER_OK;
+  }
+  int64_t bucket = 1;
+  while (bucket < nt) bucket <<= 1;
+  const auto key = std::make_tuple((int)sizeof(R), Q, bucket);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tuned.find(key);
+  if (it != g_tuned.end()) {
+    *shape = it->second;
+    return MUELLER_OK;
+  }
+  cudaEvent_t e0, e1;
+  MU_CUDA(cudaEventCreate(&e0));
+  MU_CUDA(cudaEventCreate(&e1));
+  int best = default_shape<R, Q>();
+  float best_ms = 1e30f;
+  for (int sh = 0; sh < NSHAPE; ++sh) {
+    if (!regular_launch<R, Q>(sh, nt, qd, T, K, Z, ldz, H, s)) continue;  // warm-up
+    MU_CUDA(cudaEventRecord(e0, s));
+    regular_launch<R, Q>(sh, nt, qd, T, K, Z, ldz, H, s);
+    MU_CUDA(cudaEventRecord(e1, s));
+    MU_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    MU_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = sh;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  MU_CHECK_LAUNCH("regular_kernel (tuning)");
+  MU_CUDA(cudaMemsetAsync(Z, 0, (size_t)(2 * H) * ldz * 2 * sizeof(R), s));
+  g_tuned[key] = best;
+  *shape = best;
+  return MUELLER_OK;
+}
+
 template <class R, int Q>
 mueller_status launch_regular_t(mueller_mesh* m, const PhysConsts& P, R* Z, int64_t ldz,
                                 cudaStream_t s) {
-  using C = RegCfg<R, Q>;
   const R* qd;
   if constexpr (sizeof(R) == 8)
     qd = m->qd64;
   else
     qd = m->qd32;
-  auto kern = regular_kernel<R, Q>;
-  MU_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
-  dim3 grid((unsigned)((m->nt + C::WARPS - 1) / C::WARPS), (unsigned)((m->nt + C::TY - 1) / C::TY));
-  { Prof prof_("regular_kernel<R,Q>", s); kern<<<grid, 32 * C::WARPS, C::smem, s>>>(m->nt, qd, m->T, kconst<R>(P), Z, ldz, 2 * m->nn); }
+  const KConst<R> K = kconst<R>(P);
+  int shape = 0;
+  mueller_status st = regular_shape_for<R, Q>(m->nt, qd, m->T, K, Z, ldz, 2 * m->nn, s, &shape);
+  if (st) return st;
+  if (!regular_launch<R, Q>(shape, m->nt, qd, m->T, K, Z, ldz, 2 * m->nn, s)) {
+    set_error("regular-pair tile shape does not fit in shared memory");
+    return MUELLER_ERR_INVALID_ARG;
+  }
   MU_CHECK_LAUNCH("regular_kernel");
   return MUELLER_OK;
 }
@@ -759,10 +868,11 @@ mueller_status upload_bodies(const std::vector<Body>& bodies, const std::vector<
   return MUELLER_OK;
 }
 
-template <class R, int Q>
-mueller_status regular_batch_t(int nb, mueller_mesh* const* meshes, const PhysConsts* P,
-                               void* const* Z, const int64_t* ldz, cudaStream_t s) {
-  using C = RegCfg<R, Q>;
+template <class R, int Q, int S>
+mueller_status regular_batch_shape(int nb, mueller_mesh* const* meshes, const PhysConsts* P,
+                                   void* const* Z, const int64_t* ldz, cudaStream_t s) {
+  constexpr int W = SHAPE_W[S], TYT = SHAPE_TY[S];
+  using C = RegCfg<R, Q, W, TYT>;
   std::vector<int> order = by_decreasing(nb, [&](int b) { return meshes[b]->nt; });
   std::vector<RegBody> bodies;
   std::vector<int64_t> first;
@@ -773,7 +883,7 @@ mueller_status regular_batch_t(int nb, mueller_mesh* const* meshes, const PhysCo
     B.nt = m->nt;
     B.H = 2 * m->nn;
     B.ldz = ldz[b];
-    B.tiles_x = (m->nt + C::WARPS - 1) / C::WARPS;
+    B.tiles_x = (m->nt + W - 1) / W;
     B.tile0 = tiles;
     B.qd = sizeof(R) == 8 ? (const void*)m->qd64 : (const void*)m->qd32;
     B.T = m->T;
@@ -782,19 +892,40 @@ mueller_status regular_batch_t(int nb, mueller_mesh* const* meshes, const PhysCo
     B.Z = Z[b];
     bodies.push_back(B);
     first.push_back(tiles);
-    tiles += B.tiles_x * ((m->nt + C::TY - 1) / C::TY);
+    tiles += B.tiles_x * ((m->nt + TYT - 1) / TYT);
   }
   void* buf = nullptr;
   RegBody* d_bodies = nullptr;
   int64_t* d_first = nullptr;
   mueller_status st = upload_bodies(bodies, first, &buf, &d_bodies, &d_first, s);
   if (st) return st;
-  auto kern = regular_batch_kernel<R, Q>;
+  auto kern = regular_batch_kernel<R, Q, W, TYT>;
   MU_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
-  { Prof prof_("regular_batch_kernel<R,Q>", s); kern<<<(unsigned)tiles, 32 * C::WARPS, C::smem, s>>>(d_bodies, d_first, nb); }
+  { Prof prof_("regular_batch_kernel<R,Q>", s); kern<<<(unsigned)tiles, 32 * W, C::smem, s>>>(d_bodies, d_first, nb); }
   MU_CHECK_LAUNCH("regular_batch_kernel");
   cudaFreeAsync(buf, s);
   return MUELLER_OK;
+}
+
+// the shape tuned for the largest body (tuning on it if needed)
+template <class R, int Q>
+mueller_status regular_batch_t(int nb, mueller_mesh* const* meshes, const PhysConsts* P,
+                               void* const* Z, const int64_t* ldz, cudaStream_t s) {
+  int big = 0;
+  for (int b = 1; b < nb; ++b)
+    if (meshes[b]->nt > meshes[big]->nt) big = b;
+  const mueller_mesh* m = meshes[big];
+  const R* qd = sizeof(R) == 8 ? (const R*)(const void*)m->qd64 : (const R*)(const void*)m->qd32;
+  int shape = 0;
+  mueller_status st = regular_shape_for<R, Q>(m->nt, qd, m->T, kconst<R>(P[big]), (R*)Z[big],
+                                              ldz[big], 2 * m->nn, s, &shape);
+  if (st) return st;
+  switch (shape) {
+    case 0: return regular_batch_shape<R, Q, 0>(nb, meshes, P, Z, ldz, s);
+    case 1: return regular_batch_shape<R, Q, 1>(nb, meshes, P, Z, ldz, s);
+    case 2: return regular_batch_shape<R, Q, 2>(nb, meshes, P, Z, ldz, s);
+    default: return regular_batch_shape<R, Q, 3>(nb, meshes, P, Z, ldz, s);
+  }
 }
 
 template <int Q>
