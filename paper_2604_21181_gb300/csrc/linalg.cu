@@ -65,6 +65,35 @@ __global__ void __launch_bounds__(256) gemv_c128_kernel(int64_t N, const double2
   }
 }
 
+// float -> double with integer instructions only (exact for every input:
+// the exponent is rebiased and the mantissa shifted; subnormal floats are
+// normalised through a leading-zero count).  The conversion instruction
+// would take FP64-pipe slots that the FP64 residual needs for its FMAs.
+__device__ __forceinline__ double f2d_int(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint64_t sign = (uint64_t)(u & 0x80000000u) << 32;
+  const uint32_t e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+  uint64_t bits;
+  if (e == 0xFFu) {
+    bits = sign | (0x7FFull << 52) | ((uint64_t)m << 29);
+  } else if (e != 0u) {
+    bits = sign | ((uint64_t)(e + 896u) << 52) | ((uint64_t)m << 29);
+  } else if (m == 0u) {
+    bits = sign;
+  } else {
+    const int lz = __clz(m) - 8;
+    bits = sign | ((uint64_t)(1023 - 126 - lz) << 52) | ((uint64_t)((m << lz) & 0x7FFFFFu) << 29);
+  }
+  return __longlong_as_double((long long)bits);
+}
+template <class ACC>
+__device__ __forceinline__ ACC widen(float f) {
+  if constexpr (sizeof(ACC) == 8)
+    return f2d_int(f);
+  else
+    return f;
+}
+
 // y = Z x with Z complex64; ACC = float (inner solves) or double (the FP64
 // refinement residual, x and y complex128).  Each warp owns 2 rows and reads
 // two complex64 entries per lane per step (16-byte loads).
@@ -74,7 +103,7 @@ __global__ void __launch_bounds__(256) gemv_c64_kernel(int64_t N, const float4* 
                                                        void* __restrict__ yv_, int64_t xs,
                                                        int64_t ys, int r) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t row0 = ((int64_t)blockIdx.x * 8 + warp) * 2;
+  const int64_t row0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * 2;
   const int s = blockIdx.y;
   if (row0 >= N || s >= r) return;
   const int nr = (int)mn64(2, N - row0);
@@ -94,11 +123,13 @@ __global__ void __launch_bounds__(256) gemv_c64_kernel(int64_t N, const float4* 
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       if (k < nr) {
-        const float4 z = __ldg(Z4 + (row0 + k) * ld4 + c2);
-        ar[k] = fma((ACC)z.x, x0r, fma(-(ACC)z.y, x0i, ar[k]));
-        ai[k] = fma((ACC)z.x, x0i, fma((ACC)z.y, x0r, ai[k]));
-        ar[k] = fma((ACC)z.z, x1r, fma(-(ACC)z.w, x1i, ar[k]));
-        ai[k] = fma((ACC)z.z, x1i, fma((ACC)z.w, x1r, ai[k]));
+        const float4 z4 = __ldg(Z4 + (row0 + k) * ld4 + c2);
+        const ACC zx = widen<ACC>(z4.x), zy = widen<ACC>(z4.y), zz = widen<ACC>(z4.z),
+                  zw = widen<ACC>(z4.w);
+        ar[k] = fma(zx, x0r, fma(-zy, x0i, ar[k]));
+        ai[k] = fma(zx, x0i, fma(zy, x0r, ai[k]));
+        ar[k] = fma(zz, x1r, fma(-zw, x1i, ar[k]));
+        ai[k] = fma(zz, x1i, fma(zw, x1r, ai[k]));
       }
     }
   }
@@ -1139,8 +1170,9 @@ mueller_status op_matvec(const mueller_operator* op, const void* X, void* Y, int
                                           (double2*)Y, N, N, r); }
     MU_CHECK_LAUNCH("gemv_c128_kernel");
   } else {
-    dim3 grid(nblk(N, 16), r);
-    { Prof prof_("gemv_c64_kernel<double>", s); gemv_c64_kernel<double><<<grid, 256, 0, s>>>(N, (const float4*)op->Z_dev, op->ldz, X, Y, N, N, r); }
+    // FP64-bound: small blocks (2 warps, 4 rows) spread the rows evenly over the SMs
+    dim3 grid(nblk(N, 4), r);
+    { Prof prof_("gemv_c64_kernel<double>", s); gemv_c64_kernel<double><<<grid, 64, 0, s>>>(N, (const float4*)op->Z_dev, op->ldz, X, Y, N, N, r); }
     MU_CHECK_LAUNCH("gemv_c64_kernel<double>");
     dim3 g2(nblk(m->nn, 8), r);
     { Prof prof_("near_spmv_kernel<double2, double2>", s); near_spmv_kernel<double2, double2><<<g2, 256, 0, s>>>(m->nn, m->near_rowptr, m->near_col,
@@ -1814,9 +1846,13 @@ static mueller_status solve_lockstep(const mueller_operator* op, const double2* 
   MU_CUDA(cudaStreamSynchronize(s));
   for (int k = 0; k < r; ++k) bn[k] = hbuf[k];
   for (int ref = 0; ref <= maxref; ++ref) {
-    // FP64 residual on the stored operator
-    if ((st = op_matvec(op, X, W.y64, r, nullptr, 0, s))) goto out;
-    { Prof prof_("residual_kernel", s); residual_kernel<<<nblk((int64_t)r * N, 256), 256, 0, s>>>(B, W.y64, W.r64, (int64_t)r * N); }
+    // FP64 residual on the stored operator (r = b while x is still zero)
+    if (ref == 0 && !o->warm_start) {
+      MU_CUDA(cudaMemcpyAsync(W.r64, B, (size_t)r * N * 16, cudaMemcpyDeviceToDevice, s));
+    } else {
+      if ((st = op_matvec(op, X, W.y64, r, nullptr, 0, s))) goto out;
+      { Prof prof_("residual_kernel", s); residual_kernel<<<nblk((int64_t)r * N, 256), 256, 0, s>>>(B, W.y64, W.r64, (int64_t)r * N); }
+    }
     if ((st = lock_norms<double2>(W, W.r64, W.rn, nullptr, s))) goto out;
     MU_CUDA(cudaMemcpyAsync(hbuf, W.rn, r * 8, cudaMemcpyDeviceToHost, s));
     MU_CUDA(cudaStreamSynchronize(s));
