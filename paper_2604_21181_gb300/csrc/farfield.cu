@@ -72,28 +72,11 @@ __global__ void currents_kernel(int64_t nt, int Q, const double* __restrict__ qd
   if (threadIdx.x == 0) cabs_part[(int64_t)s * gridDim.x + blockIdx.x] = red[0];
 }
 
-// F for every (direction, RHS): one CTA per pair, threads over points
-__global__ void __launch_bounds__(256) far_kernel(int64_t np, const double* __restrict__ qd,
-                                                  const double2* __restrict__ rec,
-                                                  const double* __restrict__ dirs, int64_t nd,
-                                                  double ka, double2* __restrict__ F) {
-  const int64_t d = blockIdx.x;
-  const int s = blockIdx.y;
-  const double rx = dirs[3 * d], ry = dirs[3 * d + 1], rz = dirs[3 * d + 2];
-  double acc[12];
-  for (int c = 0; c < 12; ++c) acc[c] = 0.0;
-  for (int64_t t = threadIdx.x; t < np; t += blockDim.x) {
-    const double* q = qd + t * QD_STRIDE;
-    double sn, cs;
-    sincos(-ka * (rx * q[0] + ry * q[1] + rz * q[2]), &sn, &cs);
-    const double2* o = rec + ((int64_t)s * np + t) * 6;
-    for (int c = 0; c < 6; ++c) {
-      const double2 v = o[c];
-      acc[2 * c] += v.x * cs - v.y * sn;
-      acc[2 * c + 1] += v.x * sn + v.y * cs;
-    }
-  }
-  __shared__ double red[12][256];
+// Block reduction of the 12 partial sums (N~ and L~, complex) and
+// F = (i k / 4 pi)[(N~ - r (r.N~)) - r x L~] into F_out[0..2] (thread 0).
+__device__ __forceinline__ void far_finish(double (*red)[256], const double* acc, double rx,
+                                           double ry, double rz, double ka,
+                                           double2* __restrict__ F_out) {
   for (int c = 0; c < 12; ++c) red[c][threadIdx.x] = acc[c];
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
@@ -118,8 +101,76 @@ __global__ void __launch_bounds__(256) far_kernel(int64_t np, const double* __re
     for (int a = 0; a < 3; ++a) {
       const double vr = Nr[a] - r[a] * rNr - cLr[a];
       const double vi = Ni[a] - r[a] * rNi - cLi[a];
-      F[((int64_t)s * nd + d) * 3 + a] = make_double2(-pre * vi, pre * vr);
+      F_out[a] = make_double2(-pre * vi, pre * vr);
     }
+  }
+}
+
+// F for every (direction, RHS): one CTA per pair, threads over points
+__global__ void __launch_bounds__(256) far_kernel(int64_t np, const double* __restrict__ qd,
+                                                  const double2* __restrict__ rec,
+                                                  const double* __restrict__ dirs, int64_t nd,
+                                                  double ka, double2* __restrict__ F) {
+  const int64_t d = blockIdx.x;
+  const int s = blockIdx.y;
+  const double rx = dirs[3 * d], ry = dirs[3 * d + 1], rz = dirs[3 * d + 2];
+  double acc[12];
+  for (int c = 0; c < 12; ++c) acc[c] = 0.0;
+  for (int64_t t = threadIdx.x; t < np; t += blockDim.x) {
+    const double* q = qd + t * QD_STRIDE;
+    double sn, cs;
+    sincos(-ka * (rx * q[0] + ry * q[1] + rz * q[2]), &sn, &cs);
+    const double2* o = rec + ((int64_t)s * np + t) * 6;
+    for (int c = 0; c < 6; ++c) {
+      const double2 v = o[c];
+      acc[2 * c] += v.x * cs - v.y * sn;
+      acc[2 * c + 1] += v.x * sn + v.y * cs;
+    }
+  }
+  __shared__ double red[12][256];
+  far_finish(red, acc, rx, ry, rz, ka, F + ((int64_t)s * nd + d) * 3);
+}
+
+// The directions shared by all right-hand sides (sphere rule, user list:
+// indices 1 .. nd-1) for RS right-hand sides per CTA: each phase
+// exp(-i k r.y) is computed once and applied to the RS current records.
+// Per right-hand side the sums run in the same order as in far_kernel.
+template <int RS>
+__global__ void __launch_bounds__(256) far_multi_kernel(int64_t np, const double* __restrict__ qd,
+                                                        const double2* __restrict__ rec, int r,
+                                                        const double* __restrict__ dirs,
+                                                        int64_t nd, double ka,
+                                                        double2* __restrict__ F) {
+  const int64_t d = 1 + blockIdx.x;
+  const int s0 = blockIdx.y * RS;
+  const double rx = dirs[3 * d], ry = dirs[3 * d + 1], rz = dirs[3 * d + 2];
+  double acc[RS][12];
+#pragma unroll
+  for (int k = 0; k < RS; ++k)
+#pragma unroll
+    for (int c = 0; c < 12; ++c) acc[k][c] = 0.0;
+  for (int64_t t = threadIdx.x; t < np; t += blockDim.x) {
+    const double* q = qd + t * QD_STRIDE;
+    double sn, cs;
+    sincos(-ka * (rx * q[0] + ry * q[1] + rz * q[2]), &sn, &cs);
+#pragma unroll
+    for (int k = 0; k < RS; ++k) {
+      if (s0 + k < r) {
+        const double2* o = rec + ((int64_t)(s0 + k) * np + t) * 6;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          const double2 v = o[c];
+          acc[k][2 * c] += v.x * cs - v.y * sn;
+          acc[k][2 * c + 1] += v.x * sn + v.y * cs;
+        }
+      }
+    }
+  }
+  __shared__ double red[12][256];
+#pragma unroll
+  for (int k = 0; k < RS; ++k) {
+    if (s0 + k < r) far_finish(red, acc[k], rx, ry, rz, ka, F + ((int64_t)(s0 + k) * nd + d) * 3);
+    __syncthreads();
   }
 }
 
@@ -249,10 +300,18 @@ mueller_status far_field(mueller_mesh* m, const PhysConsts& P, int Q, const void
   if (!st) {
     { Prof prof_("currents_kernel", s); currents_kernel<<<dim3(nblk_pts, r), 256, 0, s>>>(m->nt, Q, m->qd64, m->T, (const double2*)X, r,
                                                        N, dphi, rec, cab); }
-    for (int sidx = 0; sidx < r; ++sidx)
-      { Prof prof_("far_kernel", s); far_kernel<<<dim3((unsigned)nd, 1), 256, 0, s>>>(np, m->qd64, rec + (size_t)sidx * np * 6,
-                                                       ddirs + (size_t)sidx * nd * 3, nd, P.ka,
-                                                       Fall + (size_t)sidx * nd * 3); }
+    if (r == 1) {
+      { Prof prof_("far_kernel", s); far_kernel<<<dim3((unsigned)nd, 1), 256, 0, s>>>(np, m->qd64, rec, ddirs, nd, P.ka, Fall); }
+    } else {
+      // forward direction (one per right-hand side), then the shared
+      // directions for 4 right-hand sides per CTA
+      for (int sidx = 0; sidx < r; ++sidx)
+        { Prof prof_("far_kernel", s); far_kernel<<<dim3(1, 1), 256, 0, s>>>(np, m->qd64, rec + (size_t)sidx * np * 6,
+                                                         ddirs + (size_t)sidx * nd * 3, nd, P.ka,
+                                                         Fall + (size_t)sidx * nd * 3); }
+      { Prof prof_("far_multi_kernel", s); far_multi_kernel<4><<<dim3((unsigned)(nd - 1), (unsigned)((r + 3) / 4)), 256, 0, s>>>(
+          np, m->qd64, rec, r, ddirs, nd, P.ka, Fall); }
+    }
     { Prof prof_("xs_kernel", s); xs_kernel<<<r, 256, 0, s>>>(Fall, nd, n_theta, n_phi, dwth, dinc, P.ka, cab, (int)nblk_pts, dxs); }
     if (ndir > 0)
       { Prof prof_("copy_user_dirs_kernel", s); copy_user_dirs_kernel<<<(unsigned)(((int64_t)r * ndir * 3 + 255) / 256), 256, 0, s>>>(
