@@ -119,8 +119,8 @@ def touching_flops(n_tri: int, n_touch: int, ns: int, q: int) -> float:
     """FP64 flops of one touching_kernel launch (all touching pairs).
 
     The Sauter-Schwab points are processed in groups of ns that share one
-    side.  A point geometry (P2 map, derivatives, interpolated frame,
-    projection, Gram-Schmidt) costs ~300 flops; per point, R and its
+    side.  A point geometry (P2 map, derivatives and interpolated frame from
+    monomial coefficients, projection, Gram-Schmidt) costs ~230 flops; per point, R and its
     direction (13), the 8 singular geometric kernels (~137) and the 48
     weighted multiply-adds (96) cost 246; per group the 6 x 48 contraction
     costs 576.  Coincident and common-edge groups evaluate 1 + ns geometries;
@@ -135,7 +135,7 @@ def touching_flops(n_tri: int, n_touch: int, ns: int, q: int) -> float:
     geo = g_ce * (1 + ns) + (n_vert * 2 * (ns ** 2 + ns ** 3) if ns <= 5 else g_v * (1 + ns))
     points = (g_ce + g_v) * ns
     per_pair = q * q * 900 + 2 * 432 * q * 2
-    return geo * 300.0 + points * 246.0 + (g_ce + g_v) * 576.0 + n_touch * per_pair
+    return geo * 230.0 + points * 246.0 + (g_ce + g_v) * 576.0 + n_touch * per_pair
 
 
 def regular_flops(n_tri: int, n_touch: int, q: int) -> float:
@@ -249,7 +249,7 @@ def run_ours(args):
             ach = fl / (top_ms / top_n / 1e3) / 1e12
             # DRAM bytes per launch, scaled per touching pair from an ncu capture of this kernel
             # on the level-2 sphere (9.507 MB read + written for 4100 touching pairs)
-            traffic = int(round(9.507e6 / 4100 * info["n_touching"]))
+            traffic = None  # set from a capture of the current kernel
             roofline = {"kernel": top_name, "bound": "alu", "pipe": "fp64", "achieved": round(ach, 4),
                         "peak": round(PEAK_FP64 / 1e12, 4), "unit": "TFLOP/s",
                         "frac": round(ach / (PEAK_FP64 / 1e12), 4), "traffic": traffic,

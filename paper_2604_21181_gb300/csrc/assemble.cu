@@ -306,7 +306,8 @@ __device__ __forceinline__ void geo_load(const double* t, PointGeo& g) {
 // One Sauter-Schwab group: the ns points of region 'reg' at Gauss indices
 // (a, b, c, 0..ns-1).  The side that does not depend on eta3 (x if SHX) is
 // evaluated once; U receives its 6 shape values and V the 6 x 8 sums over the
-// group of  W N_k(other) g_c  (g: the 8 singular geometric kernels).  With
+// group of  W N_k(other) g_c  (g: the 8 singular geometric kernels).  Xn,
+// T1, T2 hold the monomial coefficients of position and nodal frame.  With
 // TAB the geometry of both sides is read from shared-memory records (tab_s:
 // the shared side, tab_o: the other side, one record per eta3 index) instead
 // of being evaluated.
@@ -325,7 +326,7 @@ __device__ __forceinline__ void ssq_group(int cls, int reg, int a, int b, int c,
       to_canonical(px, xu, xv, xi, eta);
     else
       to_canonical(py, yu, yv, xi, eta);
-    point_geo(Xn[SHX ? 0 : 1], T1[SHX ? 0 : 1], T2[SHX ? 0 : 1], xi, eta, gs);
+    point_geo_c(Xn[SHX ? 0 : 1], T1[SHX ? 0 : 1], T2[SHX ? 0 : 1], xi, eta, gs);
   }
 #pragma unroll
   for (int i = 0; i < 6; ++i) U[i] = gs.N[i];
@@ -341,7 +342,7 @@ __device__ __forceinline__ void ssq_group(int cls, int reg, int a, int b, int c,
         to_canonical(py, yu, yv, xi, eta);
       else
         to_canonical(px, xu, xv, xi, eta);
-      point_geo(Xn[SHX ? 1 : 0], T1[SHX ? 1 : 0], T2[SHX ? 1 : 0], xi, eta, go);
+      point_geo_c(Xn[SHX ? 1 : 0], T1[SHX ? 1 : 0], T2[SHX ? 1 : 0], xi, eta, go);
     }
     const PointGeo& gx = SHX ? gs : go;
     const PointGeo& gy = SHX ? go : gs;
@@ -400,6 +401,18 @@ __device__ __forceinline__ void touching_pair(
     sT2[side][k] = mk(f[6], f[7], f[8]);
   }
   __syncthreads();
+  // nodal values -> monomial coefficients (in place; point_geo_c reads them)
+  if (tid < 6) {
+    const int side = tid / 3, fld = tid % 3;
+    d3* a = fld == 0 ? sXn[side] : (fld == 1 ? sT1[side] : sT2[side]);
+    d3 v[6], c[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v[k] = a[k];
+    p2_coef(v, c);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) a[k] = c[k];
+  }
+  __syncthreads();
   const int px = P.perm & 0x3f, py = (P.perm >> 8) & 0x3f;
   const int nreg = P.cls == 3 ? 6 : (P.cls == 2 ? 5 : 2);
   // In both common-vertex regions one side depends on (xi, eta1) only and the
@@ -430,7 +443,7 @@ __device__ __forceinline__ void touching_pair(
       else
         to_canonical(py, yu, yv, xi, eta);
       PointGeo g;
-      point_geo(sXn[side], sT1[side], sT2[side], xi, eta, g);
+      point_geo_c(sXn[side], sT1[side], sT2[side], xi, eta, g);
       geo_store(sTab + (size_t)e * GT, g);
     }
     __syncthreads();

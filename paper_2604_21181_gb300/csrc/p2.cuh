@@ -63,19 +63,9 @@ struct PointGeo {
   double N[6];
 };
 
-__host__ __device__ __forceinline__ void point_geo(const d3* X, const d3* T1, const d3* T2, double xi,
-                                          double eta, PointGeo& g) {
-  double dxi[6], deta[6];
-  p2_eval(xi, eta, g.N, dxi, deta);
-  d3 x = mk(0, 0, 0), a1 = mk(0, 0, 0), a2 = mk(0, 0, 0), u1 = mk(0, 0, 0), u2 = mk(0, 0, 0);
-#pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    x = fma3(g.N[k], X[k], x);
-    a1 = fma3(dxi[k], X[k], a1);
-    a2 = fma3(deta[k], X[k], a2);
-    u1 = fma3(g.N[k], T1[k], u1);
-    u2 = fma3(g.N[k], T2[k], u2);
-  }
+// normal, continuous frame and Jacobian from x, the covariant vectors a1, a2
+// and the interpolated nodal frame vectors u1, u2 (Sec. 3.3)
+__host__ __device__ __forceinline__ void frame_from(d3 x, d3 a1, d3 a2, d3 u1, d3 u2, PointGeo& g) {
   d3 c = cross(a1, a2);
   const double cc = dot(c, c);
   const double iJ = inv_sqrt(cc);
@@ -98,6 +88,56 @@ __host__ __device__ __forceinline__ void point_geo(const d3* X, const d3* T1, co
   g.s2 = cross(t2, n);
   g.J = J;
   g.gs = fmin(n1, n2);
+}
+
+__host__ __device__ __forceinline__ void point_geo(const d3* X, const d3* T1, const d3* T2, double xi,
+                                          double eta, PointGeo& g) {
+  double dxi[6], deta[6];
+  p2_eval(xi, eta, g.N, dxi, deta);
+  d3 x = mk(0, 0, 0), a1 = mk(0, 0, 0), a2 = mk(0, 0, 0), u1 = mk(0, 0, 0), u2 = mk(0, 0, 0);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    x = fma3(g.N[k], X[k], x);
+    a1 = fma3(dxi[k], X[k], a1);
+    a2 = fma3(deta[k], X[k], a2);
+    u1 = fma3(g.N[k], T1[k], u1);
+    u2 = fma3(g.N[k], T2[k], u2);
+  }
+  frame_from(x, a1, a2, u1, u2, g);
+}
+
+// Monomial coefficients of a P2 field with nodal values v (node order v0 v1
+// v2 m01 m12 m20): f = c0 + c1 xi + c2 eta + c3 xi^2 + c4 xi eta + c5 eta^2.
+__host__ __device__ __forceinline__ void p2_coef(const d3* v, d3* c) {
+  c[0] = v[0];
+  c[1] = add(add(scl(-3.0, v[0]), scl(-1.0, v[1])), scl(4.0, v[3]));
+  c[2] = add(add(scl(-3.0, v[0]), scl(-1.0, v[2])), scl(4.0, v[5]));
+  c[3] = add(add(scl(2.0, v[0]), scl(2.0, v[1])), scl(-4.0, v[3]));
+  c[4] = scl(4.0, add(sub(v[0], v[3]), sub(v[4], v[5])));
+  c[5] = add(add(scl(2.0, v[0]), scl(2.0, v[2])), scl(-4.0, v[5]));
+}
+
+__host__ __device__ __forceinline__ d3 p2_val(const d3* c, double xi, double eta) {
+  const d3 a = fma3(xi, c[3], fma3(eta, c[4], c[1]));
+  const d3 b = fma3(eta, c[5], c[2]);
+  return fma3(xi, a, fma3(eta, b, c[0]));
+}
+
+// point_geo from monomial coefficients of the position (CX) and of the
+// nodal frame fields (CU1, CU2): the same quantities, fewer operations
+__host__ __device__ __forceinline__ void point_geo_c(const d3* CX, const d3* CU1, const d3* CU2,
+                                            double xi, double eta, PointGeo& g) {
+  const double l0 = 1.0 - xi - eta;
+  g.N[0] = l0 * (2.0 * l0 - 1.0);
+  g.N[1] = xi * (2.0 * xi - 1.0);
+  g.N[2] = eta * (2.0 * eta - 1.0);
+  g.N[3] = 4.0 * l0 * xi;
+  g.N[4] = 4.0 * xi * eta;
+  g.N[5] = 4.0 * eta * l0;
+  const d3 x = p2_val(CX, xi, eta);
+  const d3 a1 = fma3(2.0 * xi, CX[3], fma3(eta, CX[4], CX[1]));
+  const d3 a2 = fma3(xi, CX[4], fma3(2.0 * eta, CX[5], CX[2]));
+  frame_from(x, a1, a2, p2_val(CU1, xi, eta), p2_val(CU2, xi, eta), g);
 }
 
 }  // namespace mu
