@@ -249,7 +249,9 @@ def run_ours(args):
             ach = fl / (top_ms / top_n / 1e3) / 1e12
             # DRAM bytes per launch, scaled per touching pair from an ncu capture of this kernel
             # on the level-2 sphere (9.507 MB read + written for 4100 touching pairs)
-            traffic = None  # set from a capture of the current kernel
+            # DRAM bytes per launch, scaled per touching pair from an ncu capture of this kernel
+            # on the level-2 sphere (9.382 MB read + written for 4100 touching pairs)
+            traffic = int(round(9.382e6 / 4100 * info["n_touching"]))
             roofline = {"kernel": top_name, "bound": "alu", "pipe": "fp64", "achieved": round(ach, 4),
                         "peak": round(PEAK_FP64 / 1e12, 4), "unit": "TFLOP/s",
                         "frac": round(ach / (PEAK_FP64 / 1e12), 4), "traffic": traffic,
