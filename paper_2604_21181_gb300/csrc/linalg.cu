@@ -1305,7 +1305,9 @@ static mueller_status batched_lu_inverse(CT* A, int64_t d, int nb, const int32_t
     // panel rows k0..d-1 in shared memory when they fit, else in place
     const size_t panel_bytes = (size_t)(d - k0) * (LUW + 1) * sizeof(CT);
     if (d - k0 <= 1024 && panel_bytes <= kPanelSmem) {
-      { Prof prof_("lu_panel_smem_kernel", s); lu_panel_smem_kernel<CT, LUW><<<nb, 1024, panel_bytes, s>>>(A, d, sz_dev, k0, piv, status); }
+      // one thread per remaining row: no idle warps in the per-column reductions
+      const unsigned threads = (unsigned)std::max<int64_t>(32, ((d - k0) + 31) / 32 * 32);
+      { Prof prof_("lu_panel_smem_kernel", s); lu_panel_smem_kernel<CT, LUW><<<nb, threads, panel_bytes, s>>>(A, d, sz_dev, k0, piv, status); }
       MU_CHECK_LAUNCH("lu_panel_smem_kernel");
     } else {
       { Prof prof_("lu_panel_kernel", s); lu_panel_kernel<CT, LUW><<<nb, 256, 0, s>>>(A, d, sz_dev, k0, piv, status); }
