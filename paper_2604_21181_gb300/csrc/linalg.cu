@@ -1099,11 +1099,25 @@ __global__ void __launch_bounds__(256) mbj_apply_b_kernel(const float2* __restri
   const float2* row = inv + (int64_t)b * d * d + i * d;
   const float2* vs = v + (int64_t)s * N;
   float ar = 0, ai = 0;
-  for (int j = lane; j < n; j += 32) {
-    const int64_t gj = j < half ? o + j : H + o + (j - half);
-    const float2 x = vs[gj], m = row[j];
-    ar = fmaf(m.x, x.x, fmaf(-m.y, x.y, ar));
-    ai = fmaf(m.x, x.y, fmaf(m.y, x.x, ai));
+  for (int j0 = lane; j0 < n; j0 += 128) {
+    float2 mm[4], xx[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {  // four independent loads in flight per lane
+      const int j = j0 + 32 * u;
+      if (j < n) {
+        const int64_t gj = j < half ? o + j : H + o + (j - half);
+        mm[u] = row[j];
+        xx[u] = vs[gj];
+      } else {
+        mm[u] = make_float2(0.f, 0.f);
+        xx[u] = make_float2(0.f, 0.f);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      ar = fmaf(mm[u].x, xx[u].x, fmaf(-mm[u].y, xx[u].y, ar));
+      ai = fmaf(mm[u].x, xx[u].y, fmaf(mm[u].y, xx[u].x, ai));
+    }
   }
 #pragma unroll
   for (int q = 16; q > 0; q >>= 1) {
@@ -1186,10 +1200,10 @@ mueller_status op_matvec(const mueller_operator* op, const void* X, void* Y, int
 // The same for several complex64 right-hand sides at once: each near block
 // (complex128, read once and rounded to complex64) is applied to RS vectors,
 // so the blocks are read ceil(r / RS) times instead of r times.
-template <int RS>
+template <int RS, class BT>
 __global__ void __launch_bounds__(256, 2) near_spmv_c64_mrhs_kernel(
     int64_t nn, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-    const double2* __restrict__ blk, const float2* __restrict__ x, float2* __restrict__ y,
+    const BT* __restrict__ blk, const float2* __restrict__ x, float2* __restrict__ y,
     int64_t xs, int64_t ys, int r) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t i = (int64_t)blockIdx.x * 8 + warp;
@@ -1203,11 +1217,11 @@ __global__ void __launch_bounds__(256, 2) near_spmv_c64_mrhs_kernel(
     for (int h = 0; h < 4; ++h) ar[k][h] = ai[k][h] = 0.f;
   for (int32_t q = rowptr[i] + lane; q < rowptr[i + 1]; q += 32) {
     const int64_t j = col[q];
-    const double2* b = blk + (int64_t)q * 16;
+    const BT* b = blk + (int64_t)q * 16;
     float2 m[16];
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
-      const double2 v = b[e];
+      const BT v = b[e];
       m[e] = make_float2((float)v.x, (float)v.y);
     }
 #pragma unroll
@@ -1262,13 +1276,31 @@ mueller_status near_apply_c64(const mueller_mesh* m, const void* near_c128, cons
   if (r >= 2) {
     constexpr int RS = 8;
     dim3 g(nblk(m->nn, 8), (r + RS - 1) / RS);
-    { Prof prof_("near_spmv_c64_mrhs_kernel", s); near_spmv_c64_mrhs_kernel<RS><<<g, 256, 0, s>>>(m->nn, m->near_rowptr, m->near_col, (const double2*)near_c128, (const float2*)X, (float2*)Y, N, N, r); }
+    { Prof prof_("near_spmv_c64_mrhs_kernel", s); near_spmv_c64_mrhs_kernel<RS, double2><<<g, 256, 0, s>>>(m->nn, m->near_rowptr, m->near_col, (const double2*)near_c128, (const float2*)X, (float2*)Y, N, N, r); }
     MU_CHECK_LAUNCH("near_spmv_c64_mrhs_kernel");
     return MUELLER_OK;
   }
   dim3 g(nblk(m->nn, 8), r);
   { Prof prof_("near_spmv_kernel<double2, float2>", s); near_spmv_kernel<double2, float2><<<g, 256, 0, s>>>(m->nn, m->near_rowptr, m->near_col, (const double2*)near_c128, (const float2*)X, (float2*)Y, N, N, r); }
   MU_CHECK_LAUNCH("near_spmv_kernel<double2, float2>");
+  return MUELLER_OK;
+}
+
+// y += near x for r complex64 vectors with complex64 near blocks (the inner
+// solver's copy of the FP64 blocks, rounded once per solve)
+static mueller_status near_apply_c64_b32(const mueller_mesh* m, const float2* near32,
+                                         const float2* X, float2* Y, int r, cudaStream_t s) {
+  const int64_t N = 4 * m->nn;
+  if (r >= 2) {
+    constexpr int RS = 8;
+    dim3 g(nblk(m->nn, 8), (r + RS - 1) / RS);
+    { Prof prof_("near_spmv_c64_mrhs_kernel", s); near_spmv_c64_mrhs_kernel<RS, float2><<<g, 256, 0, s>>>(m->nn, m->near_rowptr, m->near_col, near32, X, Y, N, N, r); }
+    MU_CHECK_LAUNCH("near_spmv_c64_mrhs_kernel");
+    return MUELLER_OK;
+  }
+  dim3 g(nblk(m->nn, 8), 1);
+  { Prof prof_("near_spmv_kernel<float2, float2>", s); near_spmv_kernel<float2, float2><<<g, 256, 0, s>>>(m->nn, m->near_rowptr, m->near_col, near32, X, Y, N, N, 1); }
+  MU_CHECK_LAUNCH("near_spmv_kernel<float2, float2>");
   return MUELLER_OK;
 }
 
@@ -1643,9 +1675,10 @@ struct LockWork {
   double *npart, *cs, *bn, *beta, *hn, *res, *rn, *alpha;
   int *mask, *kk;
   void* mwork;
+  float2* near32;  // complex64 copy of the near blocks (nnzb x 16), or null
 };
 
-static size_t lock_bytes(int64_t N, int r, int m) {
+static size_t lock_bytes(int64_t N, int r, int m, int64_t nnzb) {
   const int G = 16;
   size_t b = 0;
   auto add = [&](size_t x) { b += (x + 255) & ~size_t(255); };
@@ -1663,10 +1696,11 @@ static size_t lock_bytes(int64_t N, int r, int m) {
   add((size_t)r * 4);
   add((size_t)r * 4);
   if (r >= 2) add(mrhs_work_bytes(N, r));
+  if (nnzb > 0) add((size_t)nnzb * 16 * 8);
   return b + 1024;
 }
 
-static LockWork carve_lock(char* p, int64_t N, int r, int m) {
+static LockWork carve_lock(char* p, int64_t N, int r, int m, int64_t nnzb) {
   LockWork W;
   W.N = N;
   W.r = r;
@@ -1703,6 +1737,7 @@ static LockWork carve_lock(char* p, int64_t N, int r, int m) {
   W.mask = (int*)take((size_t)r * 4);
   W.kk = (int*)take((size_t)r * 4);
   W.mwork = r >= 2 ? take(mrhs_work_bytes(N, r)) : nullptr;
+  W.near32 = nnzb > 0 ? (float2*)take((size_t)nnzb * 16 * 8) : nullptr;
   return W;
 }
 
@@ -1718,6 +1753,7 @@ static mueller_status lock_matvec(const InnerOp& I, const LockWork& W, const flo
     { Prof prof_("gemv_c64_kernel<float>", s); gemv_c64_kernel<float><<<dim3(nblk(N, 16), 1), 256, 0, s>>>(N, (const float4*)I.op->Z_dev, I.op->ldz, X, Y, N, N, 1); }
     MU_CHECK_LAUNCH("gemv_c64_kernel<float>");
   }
+  if (I.near32) return near_apply_c64_b32(m, I.near32, X, Y, W.r, s);
   return near_apply_c64(m, I.op->near_dev, X, Y, W.r, s);
 }
 
@@ -1833,7 +1869,14 @@ static mueller_status solve_lockstep(const mueller_operator* op, const double2* 
     I.L = layout(N, op->block);
     I.sz_dev = precond_sizes(op, I.L);
   }
-  LockWork W = carve_lock(p, N, r, mres);
+  LockWork W = carve_lock(p, N, r, mres, op->near_dev ? m->nnzb : 0);
+  if (op->near_dev && m->nnzb > 0) {
+    // the inner products read the near blocks rounded to complex64 once
+    const int64_t cnt = m->nnzb * 16;
+    { Prof prof_("c128_to_c64_kernel", s); c128_to_c64_kernel<<<nblk(cnt, 256), 256, 0, s>>>((const double2*)op->near_dev, W.near32, cnt); }
+    MU_CHECK_LAUNCH("near blocks to complex64");
+    I.near32 = W.near32;
+  }
   double* hbuf = nullptr;
   MU_CUDA(cudaMallocHost((void**)&hbuf, (size_t)std::max(8, 2 * r) * sizeof(double)));
   mueller_status st = MUELLER_OK;
@@ -1904,7 +1947,7 @@ size_t solve_work(const mueller_operator* op, int r, const mueller_solver_opts* 
   if (o->mode == MUELLER_SOLVE_GMRES && op->dtype == MUELLER_C128) {
     b = gmres_bytes(N, m, 16);
   } else {
-    b = lock_bytes(N, r, std::min(120, m));
+    b = lock_bytes(N, r, std::min(120, m), op->near_dev ? op->mesh->nnzb : 0);
   }
   return b + 4096;
 }
