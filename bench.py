@@ -51,7 +51,7 @@ PEAK_FP64 = SMS * 2 * 2 * SM_MAX_HZ
 PEAK_FP32 = SMS * 128 * 2 * SM_MAX_HZ
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-extras", action="store_true", help="skip the untimed extra measurements")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 # --------------------------------------------------------------- clocks
@@ -147,6 +147,24 @@ def regular_flops(n_tri: int, n_touch: int, q: int) -> float:
     return pairs * (q * q * 300.0 + 2 * 432 * q * 2)
 
 
+# ---------------------------------------------------------------- ranks
+def job_timing(ms_local: float, units_per_rank: float, world: int, device=None):
+    """Whole-job timing of N replicas (weak scaling, one process per GPU, no
+    collective on the data path): the step time is the slowest rank's, the
+    value the units all ranks processed in that time.  Returns
+    (ms_max, units per second)."""
+    ms_max = float(ms_local)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        t = torch.tensor([ms_local], dtype=torch.float64,
+                         device=device if device is not None else "cpu")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    return ms_max, units_per_rank * world / (ms_max / 1e3)
+
+
 # ---------------------------------------------------------------- ours
 def run_ours(args):
     import torch
@@ -220,11 +238,7 @@ def run_ours(args):
     clk = clocks.stop()
     launches = (mu.launch_count() - l0) // max(1, args.steps)
     ms = ev0.elapsed_time(ev1) / args.steps
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = pairs * world / (ms_max / 1e3)
+    ms_max, value = job_timing(ms, pairs, world, dev)
     sinfo, xs = infos[-1]
 
     extras = {}
