@@ -115,9 +115,13 @@ template <class R, int Q, int W_, int TY_>
 struct RegCfg {
   static constexpr int TY = TY_;
   static constexpr int WARPS = W_;
+  // element pairs a warp processes together (Q = 6: 4 x 36 point pairs fill
+  // the lanes; Q = 12: 144 point pairs already do)
+  static constexpr int NB = Q == 6 ? 4 : 1;
   static constexpr size_t smem =
       sizeof(R) * ((size_t)TY * Q * QD_STRIDE + (size_t)WARPS * Q * QD_STRIDE +
-                   (size_t)WARPS * Q * Q * 24);
+                   (size_t)WARPS * NB * Q * Q * 24) +
+      sizeof(int) * (size_t)WARPS * TY;
 };
 
 // One CTA tile (test elements bx*WARPS.., trial elements by*TY..) of one body.
@@ -146,21 +150,36 @@ __device__ __forceinline__ void regular_tile(int64_t bx, int64_t by, int64_t nt,
   int32_t tx[6];
 #pragma unroll
   for (int k = 0; k < 6; ++k) tx[k] = T[6 * ex + k];
-  R* Kt = sK + (size_t)warp * Q * Q * 24;  // [p][q][c] complex (re, im)
+  constexpr int NB = C::NB;
+  R* Kt = sK + (size_t)warp * NB * Q * Q * 24;  // [b][p][q][c] complex (re, im)
+  int* myList = reinterpret_cast<int*>(sK + (size_t)C::WARPS * NB * Q * Q * 24) + warp * C::TY;
   const R wre = R(0), wim = R(1) / K.ka;   // i / omega
-  for (int yy = 0; yy < ny; ++yy) {
-    const int64_t ey = ey0 + yy;
-    int32_t ty[6];
+  // the trial elements of the tile that do not touch ex, compacted
+  int cnt = 0;
+  for (int base = 0; base < ny; base += 32) {
+    const int yy = base + lane;
+    bool ok = false;
+    if (yy < ny) {
+      int32_t ty[6];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) ty[k] = T[6 * ey + k];
-    if (share_corner<R>(tx, ty)) continue;  // touching pairs: touching_kernel
-    const R* Y = sY + (size_t)yy * Q * QD_STRIDE;
-    // 1. point pairs
-    for (int pq = lane; pq < Q * Q; pq += 32) {
+      for (int k = 0; k < 6; ++k) ty[k] = T[6 * (ey0 + yy) + k];
+      ok = !share_corner<R>(tx, ty);  // touching pairs: touching_kernel
+    }
+    const unsigned msk = __ballot_sync(0xffffffffu, ok);
+    if (ok) myList[cnt + __popc(msk & ((1u << lane) - 1u))] = yy;
+    cnt += __popc(msk);
+  }
+  __syncwarp();
+  for (int b0 = 0; b0 < cnt; b0 += NB) {
+    const int nbb = cnt - b0 < NB ? cnt - b0 : NB;
+    // 1. point pairs of nbb element pairs
+    for (int it = lane; it < nbb * Q * Q; it += 32) {
+      const int b = it / (Q * Q), pq = it % (Q * Q);
       const int p = pq / Q, q = pq % Q;
+      const R* Y = sY + (size_t)myList[b0 + b] * Q * QD_STRIDE;
       cx<R> kv[12];
       point_pair<R>(K, myX + p * QD_STRIDE, Y + q * QD_STRIDE, false, kv);
-      R* o = Kt + (size_t)pq * 24;
+      R* o = Kt + (size_t)it * 24;
 #pragma unroll
       for (int c = 0; c < 12; ++c) {
         o[2 * c] = kv[c].re;
@@ -169,13 +188,15 @@ __device__ __forceinline__ void regular_tile(int64_t bx, int64_t by, int64_t nt,
     }
     __syncwarp();
     // 2. T[p][j][c] = sum_q Kt[p][q][c] N_j(q), written over Kt[p][j][c]
-    for (int pc = lane; pc < Q * 12; pc += 32) {
+    for (int it = lane; it < nbb * Q * 12; it += 32) {
+      const int b = it / (Q * 12), pc = it % (Q * 12);
       const int p = pc / 12, c = pc % 12;
+      R* Kb = Kt + (size_t)b * Q * Q * 24;
       R vre[Q], vim[Q];
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
-        vre[q] = Kt[((size_t)p * Q + q) * 24 + 2 * c];
-        vim[q] = Kt[((size_t)p * Q + q) * 24 + 2 * c + 1];
+        vre[q] = Kb[((size_t)p * Q + q) * 24 + 2 * c];
+        vim[q] = Kb[((size_t)p * Q + q) * 24 + 2 * c + 1];
       }
 #pragma unroll
       for (int j = 0; j < 6; ++j) {
@@ -186,22 +207,25 @@ __device__ __forceinline__ void regular_tile(int64_t bx, int64_t by, int64_t nt,
           are = fma(ph, vre[q], are);
           aim = fma(ph, vim[q], aim);
         }
-        Kt[((size_t)p * Q + j) * 24 + 2 * c] = are;
-        Kt[((size_t)p * Q + j) * 24 + 2 * c + 1] = aim;
+        Kb[((size_t)p * Q + j) * 24 + 2 * c] = are;
+        Kb[((size_t)p * Q + j) * 24 + 2 * c + 1] = aim;
       }
     }
     __syncwarp();
     // 3. L[i][j][c] = sum_p N_i(p) T[p][j][c]; scatter into Z
-    for (int jc = lane; jc < 6 * 12; jc += 32) {
+    for (int it = lane; it < nbb * 6 * 12; it += 32) {
+      const int b = it / 72, jc = it % 72;
       const int j = jc / 12, c = jc % 12;
+      const R* Kb = Kt + (size_t)b * Q * Q * 24;
       R vre[Q], vim[Q];
 #pragma unroll
       for (int p = 0; p < Q; ++p) {
-        vre[p] = Kt[((size_t)p * Q + j) * 24 + 2 * c];
-        vim[p] = Kt[((size_t)p * Q + j) * 24 + 2 * c + 1];
+        vre[p] = Kb[((size_t)p * Q + j) * 24 + 2 * c];
+        vim[p] = Kb[((size_t)p * Q + j) * 24 + 2 * c + 1];
       }
-      const int op = c >> 2, a = (c >> 1) & 1, b = c & 1;
-      const int64_t col = 2 * (int64_t)ty[j] + b + (op == 1 ? H : 0);
+      const int op = c >> 2, a = (c >> 1) & 1, bb = c & 1;
+      const int64_t tyj = T[6 * (ey0 + myList[b0 + b]) + j];
+      const int64_t col = 2 * tyj + bb + (op == 1 ? H : 0);
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
         R are = 0, aim = 0;

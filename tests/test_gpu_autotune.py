@@ -1,8 +1,8 @@
 """Pair-tile shapes of the regular-pair kernel (the autotuner's candidates):
 every shape, forced through MUELLER_REGULAR_TILE, gives the oracle's matrix
-(FP64 path, max |Z_gpu - Z_oracle| / max |Z_oracle| <= 1e-11 per quadrant);
-a shape that does not fit in shared memory is refused; the tuned default
-gives the same matrix."""
+(FP64 path, max |Z_gpu - Z_oracle| / max |Z_oracle| <= 1e-11 per quadrant)
+or, where its staging does not fit in shared memory (in FP64), is refused;
+the tuned default gives the same matrix."""
 
 import os
 
@@ -63,9 +63,15 @@ def assemble(q, shape):
 
 
 @pytest.mark.parametrize("shape", range(SHAPES))
-def test_every_tile_shape_matches_oracle_q6(shape):
+def test_every_tile_shape_matches_oracle_or_is_refused_q6(shape):
     Zo = reference(6)[3]
-    assert quadrant_err(assemble(6, shape), Zo) <= 1e-11
+    try:
+        Z = assemble(6, shape)
+    except mu.MuellerError as e:  # an FP64 shape whose staging exceeds shared memory
+        assert e.status == 1 and "shared memory" in str(e)
+        assert shape == 1
+        return
+    assert quadrant_err(Z, Zo) <= 1e-11
 
 
 def test_tile_shapes_at_q12_fit_or_are_refused():
