@@ -852,7 +852,65 @@ mueller_status launch_regular_t(mueller_mesh* m, const PhysConsts& P, R* Z, int6
   return MUELLER_OK;
 }
 
+template <class R, int Q>
+mueller_status tune_regular_t(mueller_mesh* m, const PhysConsts& P, R* Z, int64_t ldz,
+                              cudaStream_t s) {
+  const R* qd;
+  if constexpr (sizeof(R) == 8)
+    qd = m->qd64;
+  else
+    qd = m->qd32;
+  int shape = 0;
+  return regular_shape_for<R, Q>(m->nt, qd, m->T, kconst<R>(P), Z, ldz, 2 * m->nn, s, &shape);
+}
+
 }  // namespace
+
+mueller_status tune_regular(mueller_mesh* m, const PhysConsts& P, int Q, int dtype, void* Z,
+                            int64_t ldz, cudaStream_t s) {
+  if (dtype == MUELLER_C128) {
+    return Q == 6 ? tune_regular_t<double, 6>(m, P, (double*)Z, ldz, s)
+                  : tune_regular_t<double, 12>(m, P, (double*)Z, ldz, s);
+  }
+  return Q == 6 ? tune_regular_t<float, 6>(m, P, (float*)Z, ldz, s)
+                : tune_regular_t<float, 12>(m, P, (float*)Z, ldz, s);
+}
+
+// One high-priority side stream per device.  The touching-pair kernel (FP64
+// pipe) runs there while the regular-pair kernel (FP32 or FP64 multiply-add
+// work, but mostly issue-bound) runs on the caller's stream: the touching
+// kernel's CTAs are dispatched first and the regular kernel's fill the
+// registers and shared memory they leave on each SM.
+static std::mutex g_side_mu;
+static cudaStream_t g_side[64] = {};
+
+mueller_status side_stream(cudaStream_t* out) {
+  int dev = 0;
+  MU_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error("device index out of range for the side stream");
+    return MUELLER_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lk(g_side_mu);
+  if (!g_side[dev]) {
+    int lo = 0, hi = 0;
+    MU_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    MU_CUDA(cudaStreamCreateWithPriority(&g_side[dev], cudaStreamNonBlocking, hi));
+  }
+  *out = g_side[dev];
+  return MUELLER_OK;
+}
+
+// s2 waits for the work queued on s so far (fork), or s for s2 (join)
+mueller_status stream_order(cudaStream_t before, cudaStream_t after) {
+  cudaEvent_t ev;
+  MU_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  cudaError_t e = cudaEventRecord(ev, before);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(after, ev, 0);
+  cudaEventDestroy(ev);
+  if (e != cudaSuccess) return cuda_fail(e, "stream ordering");
+  return MUELLER_OK;
+}
 
 mueller_status launch_regular(mueller_mesh* m, const PhysConsts& P, int Q, int dtype, void* Z,
                               int64_t ldz, cudaStream_t s) {
@@ -1021,16 +1079,28 @@ mueller_status touching_batch_t(int nb, mueller_mesh* const* meshes, const PhysC
 mueller_status launch_assemble_batch(int nb, mueller_mesh* const* meshes, const PhysConsts* P,
                                      int Q, int ns, int dtype, void* const* Z,
                                      const int64_t* ldz, void* const* near, cudaStream_t s) {
-  mueller_status st;
-  if (dtype == MUELLER_C128)
-    st = Q == 6 ? regular_batch_t<double, 6>(nb, meshes, P, Z, ldz, s)
-                : regular_batch_t<double, 12>(nb, meshes, P, Z, ldz, s);
-  else
-    st = Q == 6 ? regular_batch_t<float, 6>(nb, meshes, P, Z, ldz, s)
-                : regular_batch_t<float, 12>(nb, meshes, P, Z, ldz, s);
+  // tile shape first (a tuning run re-zeroes the largest body's Z), then the
+  // touching pairs on the side stream concurrently with the regular pairs
+  int big = 0;
+  for (int b = 1; b < nb; ++b)
+    if (meshes[b]->nt > meshes[big]->nt) big = b;
+  mueller_status st = tune_regular(meshes[big], P[big], Q, dtype, Z[big], ldz[big], s);
   if (st) return st;
-  return Q == 6 ? touching_batch_t<6>(nb, meshes, P, ns, dtype, Z, ldz, near, s)
-                : touching_batch_t<12>(nb, meshes, P, ns, dtype, Z, ldz, near, s);
+  cudaStream_t s2;
+  st = side_stream(&s2);
+  if (!st) st = stream_order(s, s2);
+  if (st) return st;
+  st = Q == 6 ? touching_batch_t<6>(nb, meshes, P, ns, dtype, Z, ldz, near, s2)
+              : touching_batch_t<12>(nb, meshes, P, ns, dtype, Z, ldz, near, s2);
+  mueller_status st2;
+  if (dtype == MUELLER_C128)
+    st2 = Q == 6 ? regular_batch_t<double, 6>(nb, meshes, P, Z, ldz, s)
+                 : regular_batch_t<double, 12>(nb, meshes, P, Z, ldz, s);
+  else
+    st2 = Q == 6 ? regular_batch_t<float, 6>(nb, meshes, P, Z, ldz, s)
+                 : regular_batch_t<float, 12>(nb, meshes, P, Z, ldz, s);
+  const mueller_status sj = stream_order(s2, s);
+  return st ? st : (st2 ? st2 : sj);
 }
 
 mueller_status launch_mass_rhs(mueller_mesh* m, const PhysConsts& P, int Q, int dtype, void* Z,

@@ -117,6 +117,14 @@ mueller_status launch_regular(mueller_mesh* m, const PhysConsts& P, int Q, int d
                               int64_t ldz, cudaStream_t s);
 mueller_status launch_touching(mueller_mesh* m, const PhysConsts& P, int Q, int ns, int dtype,
                                void* Z, int64_t ldz, void* near, cudaStream_t s);
+// tile-shape choice (autotuned once per precision, rule and mesh size; a
+// tuning run adds into Z and zeroes it again) ahead of launch_regular
+mueller_status tune_regular(mueller_mesh* m, const PhysConsts& P, int Q, int dtype, void* Z,
+                            int64_t ldz, cudaStream_t s);
+// the device's high-priority side stream for the touching-pair kernel
+mueller_status side_stream(cudaStream_t* out);
+// 'after' waits for the work queued on 'before' so far
+mueller_status stream_order(cudaStream_t before, cudaStream_t after);
 mueller_status launch_mass_rhs(mueller_mesh* m, const PhysConsts& P, int Q, int dtype, void* Z,
                                int64_t ldz, void* near, void* B, const double* inc_dev, int r,
                                cudaStream_t s);

@@ -500,8 +500,18 @@ mueller_status mueller_assemble(mueller_mesh* m, const mueller_params* p, int32_
     MU_CUDA(cudaMallocAsync((void**)&inc_dev, (size_t)r * 6 * sizeof(double), s));
     MU_CUDA(cudaMemcpyAsync(inc_dev, inc, (size_t)r * 6 * sizeof(double), cudaMemcpyHostToDevice, s));
   }
-  st = launch_regular(m, P, p->q_regular, dtype, Z, ldz, s);
-  if (!st) st = launch_touching(m, P, p->q_regular, p->ssq_order, dtype, Z, ldz, near, s);
+  // regular pairs on s and touching pairs on the side stream s2, concurrently
+  // (the tile-shape choice comes first: a tuning run re-zeroes Z)
+  st = tune_regular(m, P, p->q_regular, dtype, Z, ldz, s);
+  cudaStream_t s2 = nullptr;
+  if (!st) st = side_stream(&s2);
+  if (!st) st = stream_order(s, s2);
+  if (!st) {
+    st = launch_touching(m, P, p->q_regular, p->ssq_order, dtype, Z, ldz, near, s2);
+    const mueller_status st2 = launch_regular(m, P, p->q_regular, dtype, Z, ldz, s);
+    const mueller_status sj = stream_order(s2, s);
+    if (!st) st = st2 ? st2 : sj;
+  }
   if (!st) st = launch_mass_rhs(m, P, p->q_regular, dtype, Z, ldz, near, B, inc_dev, B ? r : 0, s);
   if (!st) st = launch_mirror_k1(N, dtype, Z, ldz, s);
   if (inc_dev) cudaFreeAsync(inc_dev, s);

@@ -214,13 +214,9 @@ __global__ void __launch_bounds__(256) near_spmv_kernel(int64_t nn, const int32_
 constexpr int NBK = 32;
 constexpr int LUW = 16;
 
-__device__ __forceinline__ double cabs1(double2 a) { return fabs(a.x) + fabs(a.y); }
 template <class CT>
 __device__ __forceinline__ auto cabs1T(CT a) -> decltype(a.x) {
   return fabs(a.x) + fabs(a.y);
-}
-__device__ __forceinline__ double2 cmul2(double2 a, double2 b) {
-  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 template <class CT>
 __device__ __forceinline__ CT cdivT(CT a, CT b) {
@@ -233,12 +229,14 @@ __device__ __forceinline__ double2 cdiv2(double2 a, double2 b) {
 }
 
 // factor panel columns [k0, k0+W) of every block; row swaps are applied
-// to whole rows.  READING: pivot = first row maximising |Re| + |Im|.
+// to whole rows, or with 'defer' to the panel's columns only (the others
+// then take them from lu_swap_trsm_kernel).  READING: pivot = first row
+// maximising |Re| + |Im|.
 template <class CT, int W>
 __global__ void __launch_bounds__(256) lu_panel_kernel(CT* __restrict__ A, int64_t d,
                                                        const int32_t* __restrict__ sz, int k0,
                                                        int32_t* __restrict__ piv,
-                                                       int32_t* __restrict__ status) {
+                                                       int32_t* __restrict__ status, int defer) {
   const int b = blockIdx.x;
   const int n = sz[b];
   if (k0 >= n) return;
@@ -280,7 +278,7 @@ __global__ void __launch_bounds__(256) lu_panel_kernel(CT* __restrict__ A, int64
       if (singular) atomicCAS(status, 0, b + 1);
     }
     if (p != k)
-      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      for (int j = (defer ? k0 : 0) + threadIdx.x; j < (defer ? kend : n); j += blockDim.x) {
         const CT t = M[(int64_t)k * d + j];
         M[(int64_t)k * d + j] = M[(int64_t)p * d + j];
         M[(int64_t)p * d + j] = t;
@@ -313,12 +311,14 @@ __global__ void __launch_bounds__(256) lu_panel_kernel(CT* __restrict__ A, int64
 // pivot search is a warp-shuffle arg-max, the rank-1 updates run on shared
 // memory, and the panel's row swaps are applied to the columns outside it
 // afterwards, in the order they were chosen (the same matrix as swapping
-// whole rows at each step).  Pivot: first row maximising |Re| + |Im|.
+// whole rows at each step), unless 'defer' leaves them to lu_swap_trsm_kernel.
+// Pivot: first row maximising |Re| + |Im|.
 template <class CT, int W>
 __global__ void __launch_bounds__(1024) lu_panel_smem_kernel(CT* __restrict__ A, int64_t d,
                                                              const int32_t* __restrict__ sz,
                                                              int k0, int32_t* __restrict__ piv,
-                                                             int32_t* __restrict__ status) {
+                                                             int32_t* __restrict__ status,
+                                                             int defer) {
   using RT = decltype(CT{}.x);
   constexpr int LD = W + 1;
   extern __shared__ __align__(16) unsigned char lu_smem[];
@@ -414,6 +414,7 @@ __global__ void __launch_bounds__(1024) lu_panel_smem_kernel(CT* __restrict__ A,
     const int i = e / w, j = e - i * w;
     M[(int64_t)(k0 + i) * d + k0 + j] = P[i * LD + j];
   }
+  if (defer) return;
   for (int c = t; c < n; c += blockDim.x) {
     if (c >= k0 && c < k0 + w) continue;
     for (int k = 0; k < w; ++k) {
@@ -428,19 +429,28 @@ __global__ void __launch_bounds__(1024) lu_panel_smem_kernel(CT* __restrict__ A,
 }
 
 // B[k0:k0+w, c0:c1] <- L_kk^{-1} B[...] (unit lower, L from A) or
-// U_kk^{-1} B[...] (upper, non-unit); one thread per column.
+// U_kk^{-1} B[...] (upper, non-unit); one thread per column, the W x W
+// diagonal tile staged in shared memory (its entries are read by every
+// thread in the same order: broadcasts).
 template <class CT, int W>
 __global__ void trsm_tile_kernel(const CT* __restrict__ A, CT* __restrict__ B, int64_t d,
                                  int64_t ldb, int64_t bstride, const int32_t* __restrict__ sz,
                                  int k0, int w_max, int64_t c0, int64_t c1_cap, int upper) {
+  __shared__ CT T[W][W];
   const int b = blockIdx.y;
   const int n = sz[b];
   if (k0 >= n) return;
   const int w = min(w_max, n - k0);
   const int64_t c1 = c1_cap < 0 ? n : mn64(c1_cap, n);
+  if (c0 + (int64_t)blockIdx.x * blockDim.x >= c1) return;  // uniform over the CTA
+  const CT* M = A + (int64_t)b * d * d;
+  for (int e = threadIdx.x; e < W * W; e += blockDim.x) {
+    const int i = e / W, j = e % W;
+    T[i][j] = (i < w && j < w) ? M[(int64_t)(k0 + i) * d + k0 + j] : CT{0, 0};
+  }
+  __syncthreads();
   const int64_t c = c0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= c1) return;
-  const CT* M = A + (int64_t)b * d * d;
   CT* X = B + (int64_t)b * bstride;
   // fixed-size, fully unrolled loops keep v[] in registers; rows >= w are
   // inert (zero right-hand side, never written back)
@@ -453,11 +463,9 @@ __global__ void trsm_tile_kernel(const CT* __restrict__ A, CT* __restrict__ B, i
     for (int i = 1; i < W; ++i)
 #pragma unroll
       for (int j = 0; j < i; ++j) {
-        if (i < w) {
-          const CT l = M[(int64_t)(k0 + i) * d + k0 + j];
-          v[i].x -= l.x * v[j].x - l.y * v[j].y;
-          v[i].y -= l.x * v[j].y + l.y * v[j].x;
-        }
+        const CT l = T[i][j];
+        v[i].x -= l.x * v[j].x - l.y * v[j].y;
+        v[i].y -= l.x * v[j].y + l.y * v[j].x;
       }
   } else {
 #pragma unroll
@@ -465,13 +473,11 @@ __global__ void trsm_tile_kernel(const CT* __restrict__ A, CT* __restrict__ B, i
       if (i < w) {
 #pragma unroll
         for (int j = i + 1; j < W; ++j) {
-          if (j < w) {
-            const CT u = M[(int64_t)(k0 + i) * d + k0 + j];
-            v[i].x -= u.x * v[j].x - u.y * v[j].y;
-            v[i].y -= u.x * v[j].y + u.y * v[j].x;
-          }
+          const CT u = T[i][j];
+          v[i].x -= u.x * v[j].x - u.y * v[j].y;
+          v[i].y -= u.x * v[j].y + u.y * v[j].x;
         }
-        v[i] = cdivT(v[i], M[(int64_t)(k0 + i) * d + k0 + i]);
+        v[i] = cdivT(v[i], T[i][i]);
       }
     }
   }
@@ -547,6 +553,128 @@ __global__ void __launch_bounds__(256) gemm_update_kernel(const CT* __restrict__
         Cb[gr * ldb + gc] = v;
       }
     }
+}
+
+// After panel [k0, k0+W) is factored: its row swaps (recorded in piv, in
+// order) applied to every column outside the panel, and for the columns
+// right of it the row panel of U, U12 = L11^{-1} A12 (L11 unit lower from
+// the panel).  One thread per column.
+template <int W>
+__global__ void lu_swap_trsm_kernel(double2* __restrict__ A, int64_t d,
+                                    const int32_t* __restrict__ sz, int k0,
+                                    const int32_t* __restrict__ piv) {
+  __shared__ double2 T[W][W];
+  const int b = blockIdx.y;
+  const int n = sz[b];
+  if (k0 >= n) return;
+  const int w = min(W, n - k0);
+  if ((int64_t)blockIdx.x * blockDim.x >= n) return;  // uniform over the CTA
+  double2* M = A + (int64_t)b * d * d;
+  for (int e = threadIdx.x; e < W * W; e += blockDim.x) {
+    const int i = e / W, j = e % W;
+    T[i][j] = (i < w && j < w) ? M[(int64_t)(k0 + i) * d + k0 + j] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= n || (c >= k0 && c < k0 + w)) return;
+  const int32_t* pv = piv + (int64_t)b * d + k0;
+  for (int k = 0; k < w; ++k) {
+    const int p = pv[k];
+    if (p != k0 + k) {
+      const double2 x = M[(int64_t)(k0 + k) * d + c];
+      M[(int64_t)(k0 + k) * d + c] = M[(int64_t)p * d + c];
+      M[(int64_t)p * d + c] = x;
+    }
+  }
+  if (c < k0 + w) return;
+  double2 v[W];
+#pragma unroll
+  for (int i = 0; i < W; ++i) v[i] = i < w ? M[(int64_t)(k0 + i) * d + c] : make_double2(0.0, 0.0);
+#pragma unroll
+  for (int i = 1; i < W; ++i)
+#pragma unroll
+    for (int j = 0; j < i; ++j) {
+      const double2 l = T[i][j];
+      v[i].x -= l.x * v[j].x - l.y * v[j].y;
+      v[i].y -= l.x * v[j].y + l.y * v[j].x;
+    }
+#pragma unroll
+  for (int i = 0; i < W; ++i)
+    if (i < w) M[(int64_t)(k0 + i) * d + c] = v[i];
+}
+
+// FP64 trailing update of the block LU: A[r0:n, c0:c1) -= A[r0:n, k0:k0+w)
+// A[k0:k0+w, c0:c1), r0 = k0 + W, over all blocks.  32 x TN output tiles,
+// 64 threads with 4 x TN/8 complex accumulators; CTAs stride over the tiles
+// when the grid is smaller than the tile count.  The FP64 pipe (two DFMA
+// per clock per SM) bounds every tile shape, so small tiles cost nothing and
+// mask less of the late, narrow updates.
+template <int W, int TN>
+__global__ void __launch_bounds__(64) lu_update_kernel(double2* __restrict__ A, int64_t d,
+                                                       const int32_t* __restrict__ sz, int k0,
+                                                       int64_t c0, int64_t c1_cap, int nb) {
+  constexpr int JN = TN / 8;
+  const int64_t r0 = k0 + W;
+  const int64_t cend = c1_cap < 0 ? d : c1_cap;
+  const int64_t rt_n = (d - r0 + 31) / 32, ct_n = (cend - c0 + TN - 1) / TN;
+  const int64_t per_b = rt_n * ct_n, tiles = (int64_t)nb * per_b;
+  __shared__ double2 sA[32][W + 1];
+  __shared__ double2 sB[W][TN + 1];
+  const int ty = threadIdx.x / 8, tx = threadIdx.x % 8;
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int b = (int)(tile / per_b);
+    const int64_t rem = tile - (int64_t)b * per_b;
+    const int n = sz[b];
+    const int64_t c1 = mn64(cend, n);
+    const int64_t tr = r0 + (rem / ct_n) * 32, tc = c0 + (rem % ct_n) * TN;
+    if (k0 >= n || tr >= n || tc >= c1) continue;  // uniform over the CTA
+    const int w = min(W, n - k0);
+    double2* M = A + (int64_t)b * d * d;
+    for (int t = threadIdx.x; t < 32 * W; t += 64) {
+      const int i = t / W, k = t % W;
+      const int64_t gr = tr + i;
+      sA[i][k] = (gr < n && k < w) ? M[gr * d + k0 + k] : make_double2(0.0, 0.0);
+    }
+    for (int t = threadIdx.x; t < W * TN; t += 64) {
+      const int k = t / TN, j = t % TN;
+      const int64_t gc = tc + j;
+      sB[k][j] = (gc < c1 && k < w) ? M[(int64_t)(k0 + k) * d + gc] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    double2 acc[4][JN];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < JN; ++j) acc[i][j] = make_double2(0.0, 0.0);
+#pragma unroll 4
+    for (int k = 0; k < W; ++k) {
+      double2 a[4], bb[JN];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = sA[ty + 8 * i][k];
+#pragma unroll
+      for (int j = 0; j < JN; ++j) bb[j] = sB[k][tx + 8 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < JN; ++j) {
+          acc[i][j].x = fma(a[i].x, bb[j].x, fma(-a[i].y, bb[j].y, acc[i][j].x));
+          acc[i][j].y = fma(a[i].x, bb[j].y, fma(a[i].y, bb[j].x, acc[i][j].y));
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < JN; ++j) {
+        const int64_t gr = tr + ty + 8 * i, gc = tc + tx + 8 * j;
+        if (gr < n && gc < c1) {
+          double2 v = M[gr * d + gc];
+          v.x -= acc[i][j].x;
+          v.y -= acc[i][j].y;
+          M[gr * d + gc] = v;
+        }
+      }
+    __syncthreads();  // before the next tile's loads overwrite sA, sB
+  }
 }
 
 // X <- P I: row k of the identity permuted by the recorded swaps
@@ -1324,38 +1452,70 @@ template <class CT>
 static mueller_status block_inverse(const CT* A, int64_t d, int nb, const int32_t* sz_dev,
                                     const int32_t* piv, CT* inv, cudaStream_t s);
 
-// in-place LU of nb blocks of size d (active sizes sz_dev), then, if inv,
-// their inverses in 'inv' (d x d per block)
+// Panel [k0, k0+LUW) of every block: in shared memory when its rows fit.
+static mueller_status lu_panel(double2* A, int64_t d, int nb, const int32_t* sz_dev, int k0,
+                               int32_t* piv, int32_t* status, int defer, cudaStream_t s) {
+  constexpr size_t kPanelSmem = 200 * 1024;
+  const size_t panel_bytes = (size_t)(d - k0) * (LUW + 1) * sizeof(double2);
+  if (d - k0 <= 1024 && panel_bytes <= kPanelSmem) {
+    MU_CUDA(cudaFuncSetAttribute(lu_panel_smem_kernel<double2, LUW>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPanelSmem));
+    // one thread per remaining row: no idle warps in the per-column reductions
+    const unsigned threads = (unsigned)std::max<int64_t>(32, ((d - k0) + 31) / 32 * 32);
+    { Prof prof_("lu_panel_smem_kernel", s); lu_panel_smem_kernel<double2, LUW><<<nb, threads, panel_bytes, s>>>(A, d, sz_dev, k0, piv, status, defer); }
+    MU_CHECK_LAUNCH("lu_panel_smem_kernel");
+  } else {
+    { Prof prof_("lu_panel_kernel", s); lu_panel_kernel<double2, LUW><<<nb, 256, 0, s>>>(A, d, sz_dev, k0, piv, status, defer); }
+    MU_CHECK_LAUNCH("lu_panel_kernel");
+  }
+  return MUELLER_OK;
+}
+
+// trailing update A[k0+LUW:n, c0:c1) of panel k0: the next panel's columns
+// (TN = LUW) or the rest (TN = 32), one CTA per tile.  (A grid of a few
+// persistent CTAs per SM, which leaves room for the panel beside it, was
+// slower: the panel then shares its SM's FP64 pipe and the chain of panels
+// becomes the critical path.)
+template <int TN>
+static mueller_status lu_update(double2* A, int64_t d, int nb, const int32_t* sz_dev, int k0,
+                                int64_t c0, int64_t c1, cudaStream_t s) {
+  const int64_t rows = d - (k0 + LUW), cols = (c1 < 0 ? d : c1) - c0;
+  if (rows <= 0 || cols <= 0) return MUELLER_OK;
+  const int64_t grid = nb * nblk(rows, 32) * nblk(cols, TN);
+  { Prof prof_("lu_update_kernel", s); lu_update_kernel<LUW, TN><<<(unsigned)grid, 64, 0, s>>>(A, d, sz_dev, k0, c0, c1, nb); }
+  MU_CHECK_LAUNCH("lu_update_kernel");
+  return MUELLER_OK;
+}
+
+// In-place FP64 LU with partial pivoting of nb blocks of size d (active
+// sizes sz_dev), right-looking in panels of LUW columns with a look-ahead of
+// one panel.  Per panel k0: its row swaps reach the other columns and the
+// row panel of U is solved (one kernel); then the side stream updates the
+// columns of panel k0+LUW and factors it (its swaps held back) while the
+// caller's stream updates the remaining columns, so that the panel starts
+// on the SMs the bulk update's last wave leaves free.
+// Then, if inv, the inverses in 'inv' (d x d per block).
 template <class CT>
 static mueller_status batched_lu_inverse(CT* A, int64_t d, int nb, const int32_t* sz_dev,
                                          int32_t* piv, int32_t* status, CT* inv,
                                          cudaStream_t s) {
-  constexpr size_t kPanelSmem = 200 * 1024;
-  MU_CUDA(cudaFuncSetAttribute(lu_panel_smem_kernel<CT, LUW>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPanelSmem));
-  for (int k0 = 0; k0 < d; k0 += LUW) {
-    // panel rows k0..d-1 in shared memory when they fit, else in place
-    const size_t panel_bytes = (size_t)(d - k0) * (LUW + 1) * sizeof(CT);
-    if (d - k0 <= 1024 && panel_bytes <= kPanelSmem) {
-      // one thread per remaining row: no idle warps in the per-column reductions
-      const unsigned threads = (unsigned)std::max<int64_t>(32, ((d - k0) + 31) / 32 * 32);
-      { Prof prof_("lu_panel_smem_kernel", s); lu_panel_smem_kernel<CT, LUW><<<nb, threads, panel_bytes, s>>>(A, d, sz_dev, k0, piv, status); }
-      MU_CHECK_LAUNCH("lu_panel_smem_kernel");
-    } else {
-      { Prof prof_("lu_panel_kernel", s); lu_panel_kernel<CT, LUW><<<nb, 256, 0, s>>>(A, d, sz_dev, k0, piv, status); }
-      MU_CHECK_LAUNCH("lu_panel_kernel");
-    }
-    const int64_t rest = d - (k0 + LUW);
-    if (rest <= 0) continue;
-    // U12 = L11^{-1} A12 (columns k0+LUW .. n)
-    dim3 gt(nblk(rest, 128), nb);
-    { Prof prof_("trsm_tile_kernel", s); trsm_tile_kernel<CT, LUW><<<gt, 128, 0, s>>>(A, A, d, d, d * d, sz_dev, k0, LUW, k0 + LUW, -1, 0); }
-    MU_CHECK_LAUNCH("trsm_tile_kernel");
-    dim3 gg(nblk(rest, 64), nblk(rest, 64), nb);
-    { Prof prof_("gemm_update_kernel", s); gemm_update_kernel<CT, LUW><<<gg, 256, 0, s>>>(A, A, A, d, d, d * d, sz_dev, k0, k0 + LUW, -1, k0 + LUW, -1); }
-    MU_CHECK_LAUNCH("gemm_update_kernel");
+  static_assert(sizeof(CT) == 16, "the block LU is FP64");
+  cudaStream_t s2 = nullptr;
+  mueller_status st = side_stream(&s2);
+  if (!st) st = lu_panel(A, d, nb, sz_dev, 0, piv, status, 1, s);
+  for (int k0 = 0; !st && k0 < d; k0 += LUW) {
+    { Prof prof_("lu_swap_trsm_kernel", s); lu_swap_trsm_kernel<LUW><<<dim3(nblk(d, 128), nb), 128, 0, s>>>(A, d, sz_dev, k0, piv); }
+    MU_CHECK_LAUNCH("lu_swap_trsm_kernel");
+    const int k1 = k0 + LUW;
+    if (k1 >= d) break;
+    st = stream_order(s, s2);
+    if (!st) st = lu_update<LUW>(A, d, nb, sz_dev, k0, k1, k1 + LUW, s2);
+    if (!st) st = lu_panel(A, d, nb, sz_dev, k1, piv, status, 1, s2);
+    const mueller_status su = lu_update<32>(A, d, nb, sz_dev, k0, k1 + LUW, -1, s);
+    const mueller_status sj = stream_order(s2, s);
+    if (!st) st = su ? su : sj;
   }
-  if (!inv) return MUELLER_OK;
+  if (st || !inv) return st;
   return block_inverse<CT>(A, d, nb, sz_dev, piv, inv, s);
 }
 
