@@ -119,13 +119,21 @@ typedef struct {
   double t_ms;         /* wall time of the call                              */
 } mueller_solve_info;
 
+/* Operator flag: Z11 equals -Z00 bit for bit, as mueller_assemble and
+ * mueller_assemble_batch write it (both are +-(i/omega) K1, Eq.
+ * global_system).  The complex64 single-vector products of the inner GMRES
+ * then read Z00 in place of Z11: three quarters of Z per product instead of
+ * all of it.  Leave it clear for a Z that was changed or written by other
+ * means. */
+#define MUELLER_OP_K1_MIRRORED 1
+
 /* The operator handed to the preconditioner and the solver. */
 typedef struct {
   const mueller_mesh* mesh; /* for the near-part layout (C64_NEAR64)         */
   const void* Z_dev;        /* dense Z, dtype below, row-major, ldz          */
   int64_t ldz;
   int32_t dtype;            /* MUELLER_C128 or MUELLER_C64_NEAR64            */
-  int32_t pad;
+  int32_t flags;            /* MUELLER_OP_* bits (0 = none)                  */
   const void* near_dev;     /* complex128 near blocks (C64_NEAR64) or NULL   */
   const void* precond_dev;  /* factors from mueller_precond_build or NULL    */
   int64_t block;            /* cluster size B used to build precond_dev      */

@@ -14,6 +14,7 @@ from .api import (  # noqa: F401
     FRAME_POLAR,
     MUELLER_C128,
     MUELLER_C64_NEAR64,
+    MUELLER_OP_K1_MIRRORED,
     SOLVE_DENSE_LU,
     SOLVE_GMRES,
     SOLVE_GMRES_IR,

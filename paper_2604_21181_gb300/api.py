@@ -18,6 +18,7 @@ from . import buildlib as _build
 
 MUELLER_C128 = 0
 MUELLER_C64_NEAR64 = 1
+MUELLER_OP_K1_MIRRORED = 1
 SOLVE_DENSE_LU = 0
 SOLVE_GMRES = 1
 SOLVE_GMRES_IR = 2
@@ -62,7 +63,7 @@ class CSolveInfo(C.Structure):
 
 class COperator(C.Structure):
     _fields_ = [("mesh", C.c_void_p), ("Z_dev", C.c_void_p), ("ldz", C.c_int64),
-                ("dtype", C.c_int32), ("pad", C.c_int32), ("near_dev", C.c_void_p),
+                ("dtype", C.c_int32), ("flags", C.c_int32), ("near_dev", C.c_void_p),
                 ("precond_dev", C.c_void_p), ("block", C.c_int64)]
 
 
@@ -276,6 +277,7 @@ def assemble(mesh: Mesh, params: Params, dtype: int = MUELLER_C128, inc=None, Z=
     p = params.c()
     _check(mesh._lib.mueller_assemble(mesh.h, C.byref(p), int(dtype), _ptr(Z), Z.stride(0), _ptr(near),
                                       _ptr(B), incp, r, _stream(stream)))
+    Z._mueller_k1_mirrored = Z._version  # Z11 = -Z00 as written; see Operator
     return Z, near, B
 
 
@@ -313,15 +315,36 @@ def assemble_batch(meshes, params, dtype: int = MUELLER_C64_NEAR64, incs=None, s
         rs = (C.c_int32 * nb)(*[a.shape[0] for a in keep])
     _check(lib.mueller_assemble_batch(nb, h, cps, int(dtype), zs, lds, ns, bs, incp, rs,
                                       _stream(stream)))
+    for o in out:
+        o[0]._mueller_k1_mirrored = o[0]._version
     return out
 
 
 class Operator:
-    """The operator struct handed to precond_build / solve / matvec."""
+    """The operator struct handed to precond_build / solve / matvec.
 
-    def __init__(self, mesh: Mesh, Z, near=None, dtype: int = MUELLER_C128, precond=None, block=0):
+    mirrored: Z11 = -Z00 bit for bit (MUELLER_OP_K1_MIRRORED), so that
+    products read three quarters of Z.  By default true exactly while Z was
+    last written by assemble / assemble_batch (returned or passed in as the
+    output) and not changed in place since: the tag holds the tensor's
+    version counter and is read at every call.  A copy, a slice or any other
+    tensor is not tagged.  A Z written behind PyTorch's back
+    (through its raw pointer) keeps its tag: pass False then."""
+
+    def __init__(self, mesh: Mesh, Z, near=None, dtype: int = MUELLER_C128, precond=None, block=0,
+                 mirrored=None):
         self.mesh, self.Z, self.near, self.dtype = mesh, Z, near, dtype
         self.precond, self.block = precond, block
+        self._mirrored = mirrored
+
+    @property
+    def mirrored(self) -> bool:
+        # evaluated at each call, so an Operator made before its Z is
+        # (re)assembled sees the tag
+        if self._mirrored is not None:
+            return bool(self._mirrored)
+        tag = getattr(self.Z, "_mueller_k1_mirrored", None)
+        return tag is not None and tag == self.Z._version
 
     def c(self) -> COperator:
         o = COperator()
@@ -329,6 +352,7 @@ class Operator:
         o.Z_dev = self.Z.data_ptr()
         o.ldz = self.Z.stride(0)
         o.dtype = int(self.dtype)
+        o.flags = MUELLER_OP_K1_MIRRORED if self.mirrored else 0
         o.near_dev = self.near.data_ptr() if self.near is not None else None
         o.precond_dev = self.precond.data_ptr() if self.precond is not None else None
         o.block = int(self.block)

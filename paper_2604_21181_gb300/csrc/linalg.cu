@@ -151,6 +151,61 @@ __global__ void __launch_bounds__(256) gemv_c64_kernel(int64_t N, const float4* 
   }
 }
 
+// y = Z x (complex64, FP32 accumulation) for a Z whose lower-right quadrant
+// is minus the upper-left one (Z11 = -Z00 = -(i/omega) K1, Eq.
+// global_system): with x = [x0; x1] the rows i and H + i come from row i of
+// Z00, Z01 and Z10,
+//   y_i = Z00_i x0 + Z01_i x1,   y_{H+i} = Z10_i x0 - Z00_i x1,
+// so three quarters of Z are read.  One warp per top row i (and its bottom
+// partner), two complex64 entries per lane per quadrant row and step
+// (16-byte loads), two steps in flight.  (The FP64-accumulating products are
+// bound by the FP64 pipe, whose work this does not reduce, and read all of
+// Z.)
+__global__ void __launch_bounds__(256) gemv3_c64_kernel(int64_t H, const float4* __restrict__ Z4,
+                                                        int64_t ldz, const float4* __restrict__ x4,
+                                                        float2* __restrict__ y) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (i >= H) return;
+  float tr = 0.f, ti = 0.f, br = 0.f, bi = 0.f;
+  const int64_t hp = H / 2;  // float4 pairs per quadrant row (H even)
+  const float4* z00 = Z4 + i * (ldz / 2);
+  const float4* z01 = z00 + hp;
+  const float4* z10 = Z4 + (H + i) * (ldz / 2);
+#pragma unroll 2
+  for (int64_t c2 = lane; c2 < hp; c2 += 32) {
+    const float4 xa = __ldg(x4 + c2), xb = __ldg(x4 + hp + c2);
+    const float4 d = __ldg(z00 + c2), e = __ldg(z01 + c2), f = __ldg(z10 + c2);
+    // top: Z00 x0 + Z01 x1
+    tr = fmaf(d.x, xa.x, fmaf(-d.y, xa.y, tr));
+    ti = fmaf(d.x, xa.y, fmaf(d.y, xa.x, ti));
+    tr = fmaf(d.z, xa.z, fmaf(-d.w, xa.w, tr));
+    ti = fmaf(d.z, xa.w, fmaf(d.w, xa.z, ti));
+    tr = fmaf(e.x, xb.x, fmaf(-e.y, xb.y, tr));
+    ti = fmaf(e.x, xb.y, fmaf(e.y, xb.x, ti));
+    tr = fmaf(e.z, xb.z, fmaf(-e.w, xb.w, tr));
+    ti = fmaf(e.z, xb.w, fmaf(e.w, xb.z, ti));
+    // bottom: Z10 x0 - Z00 x1
+    br = fmaf(f.x, xa.x, fmaf(-f.y, xa.y, br));
+    bi = fmaf(f.x, xa.y, fmaf(f.y, xa.x, bi));
+    br = fmaf(f.z, xa.z, fmaf(-f.w, xa.w, br));
+    bi = fmaf(f.z, xa.w, fmaf(f.w, xa.z, bi));
+    br = fmaf(-d.x, xb.x, fmaf(d.y, xb.y, br));
+    bi = fmaf(-d.x, xb.y, fmaf(-d.y, xb.x, bi));
+    br = fmaf(-d.z, xb.z, fmaf(d.w, xb.w, br));
+    bi = fmaf(-d.z, xb.w, fmaf(-d.w, xb.z, bi));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    ti += __shfl_xor_sync(0xffffffffu, ti, o);
+    br += __shfl_xor_sync(0xffffffffu, br, o);
+    bi += __shfl_xor_sync(0xffffffffu, bi, o);
+  }
+  if (lane == 0) y[i] = make_float2(tr, ti);
+  if (lane == 1) y[H + i] = make_float2(br, bi);
+}
+
 // y += near * x for the near blocks (test node rows, 4 x 4 complex blocks
 // [h][alpha][g][beta]).  One warp per test node: lanes take the row's
 // blocks, each block contributes to the node's 4 outputs, then a warp
@@ -1292,6 +1347,21 @@ inline unsigned nblk(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); 
 }  // namespace
 
 // ======================================================= operator products
+// y = Z x of the complex64 dense part for one complex64 vector (FP32
+// accumulation), reading three quarters of Z when Z11 = -Z00
+static mueller_status gemv_c64_f32(const mueller_operator* op, const void* x, void* y,
+                                   cudaStream_t s) {
+  const int64_t N = 4 * op->mesh->nn, H = N / 2;
+  if (op->flags & MUELLER_OP_K1_MIRRORED) {
+    { Prof prof_("gemv3_c64_kernel", s); gemv3_c64_kernel<<<(unsigned)nblk(H, 8), 256, 0, s>>>(H, (const float4*)op->Z_dev, op->ldz, (const float4*)x, (float2*)y); }
+    MU_CHECK_LAUNCH("gemv3_c64_kernel");
+  } else {
+    { Prof prof_("gemv_c64_kernel<float>", s); gemv_c64_kernel<float><<<dim3(nblk(N, 16), 1), 256, 0, s>>>(N, (const float4*)op->Z_dev, op->ldz, x, y, N, N, 1); }
+    MU_CHECK_LAUNCH("gemv_c64_kernel<float>");
+  }
+  return MUELLER_OK;
+}
+
 size_t op_matvec_work(const mueller_operator* op, int r) {
   (void)op;
   (void)r;
@@ -1694,9 +1764,8 @@ mueller_status inner_matvec(const InnerOp& I, const VT* x, VT* y, cudaStream_t s
   if constexpr (sizeof(VT) == 16) {
     return op_matvec(I.op, x, y, 1, nullptr, 0, s);
   } else {
-    { Prof prof_("gemv_c64_kernel<float>", s); gemv_c64_kernel<float><<<dim3(nblk(N, 16), 1), 256, 0, s>>>(N, (const float4*)I.op->Z_dev,
-                                                                I.op->ldz, x, y, N, N, 1); }
-    MU_CHECK_LAUNCH("gemv_c64_kernel<float>");
+    mueller_status st = gemv_c64_f32(I.op, x, y, s);
+    if (st) return st;
     { Prof prof_("near_spmv_kernel<float2, float2>", s); near_spmv_kernel<float2, float2><<<dim3(nblk(m->nn, 8), 1), 256, 0, s>>>(
         m->nn, m->near_rowptr, m->near_col, I.near32, x, y, N, N, 1); }
     MU_CHECK_LAUNCH("near_spmv_kernel<float>");
@@ -1910,8 +1979,8 @@ static mueller_status lock_matvec(const InnerOp& I, const LockWork& W, const flo
     mueller_status st = mrhs_matvec_c64(I.op->Z_dev, N, I.op->ldz, X, Y, W.r, W.mwork, s);
     if (st) return st;
   } else {
-    { Prof prof_("gemv_c64_kernel<float>", s); gemv_c64_kernel<float><<<dim3(nblk(N, 16), 1), 256, 0, s>>>(N, (const float4*)I.op->Z_dev, I.op->ldz, X, Y, N, N, 1); }
-    MU_CHECK_LAUNCH("gemv_c64_kernel<float>");
+    mueller_status st = gemv_c64_f32(I.op, X, Y, s);
+    if (st) return st;
   }
   if (I.near32) return near_apply_c64_b32(m, I.near32, X, Y, W.r, s);
   return near_apply_c64(m, I.op->near_dev, X, Y, W.r, s);

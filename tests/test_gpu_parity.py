@@ -273,3 +273,36 @@ def test_sampled_rows_at_level3_workload():
         sub_o = rows_o[4 * k:4 * k + 4][:, idx[4 * k:4 * k + 4]]
         sub_g = cols_g[4 * k:4 * k + 4][:, idx[4 * k:4 * k + 4]].T
         assert np.abs(sub_g - sub_o).max() <= 5e-6 * scale
+
+
+def test_mirrored_inner_products_match_full_read():
+    """Z11 = -Z00 bit for bit as assembled, so the inner GMRES's complex64
+    product may read three quarters of Z (MUELLER_OP_K1_MIRRORED, set for an
+    assembled Z and void once Z changes in place).  The mixed GMRES-IR solve
+    with it and with the full read differ only in the order of FP32 sums:
+    both reach the FP64 residual 1e-8, with iteration counts within one and
+    solutions within 1e-6 of each other."""
+    xyz, tri6 = workloads.spheroid_p2(2, 1.0, 1.5)
+    m = mu.Mesh(xyz, tri6)
+    m.tangent_frame(0, out=False)
+    p = mu.Params(ka=2.0, eps_r=(3.0, 0.1), ssq_order=3, frame_rule=0)
+    inc = workloads.fibonacci_plane_waves(1)[:1]
+    Z, near, B = mu.assemble(m, p, mu.MUELLER_C64_NEAR64, inc=inc)
+    H = m.N // 2
+    assert torch.equal(Z[H:, H:], -Z[:H, :H])
+    op_m = mu.Operator(m, Z, near, mu.MUELLER_C64_NEAR64)
+    op_f = mu.Operator(m, Z, near, mu.MUELLER_C64_NEAR64, mirrored=False)
+    assert op_m.mirrored and not op_f.mirrored
+    assert not mu.Operator(m, Z.clone(), near, mu.MUELLER_C64_NEAR64).mirrored  # untagged copy
+    opts = mu.SolverOpts(mode=mu.SOLVE_GMRES_IR, restart=30, tol=1e-8)
+    out = []
+    for op in (op_m, op_f):
+        mu.precond_build(op, 64)
+        X, info = mu.solve(op, B, opts)
+        assert info["converged"] == 1 and info["relres"] <= 1e-8
+        out.append((X, info["iters"]))
+    assert abs(out[0][1] - out[1][1]) <= 1
+    e = (torch.linalg.norm(out[0][0] - out[1][0]) / torch.linalg.norm(out[1][0])).item()
+    assert e <= 1e-6, e
+    Z[0, 0] += 1.0  # changed in place: the tag no longer holds
+    assert not op_m.mirrored
