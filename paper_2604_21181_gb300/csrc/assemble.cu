@@ -298,33 +298,33 @@ __global__ void __launch_bounds__(32 * W) regular_batch_kernel(const RegBody* __
 constexpr int TT = 96;  // threads per touching pair (= SSQ points per batch)
 
 // Geometry record of one Sauter-Schwab point side in shared memory:
-// x, n, t1, t2, s1, s2 (3 each), J, N[6].
-constexpr int GT = 25;
-constexpr int MAX_TAB_NS = 5;  // vertex-pair tables: 2 (ns^2 + ns^3) records <= 60 KB
+// x, n, t1, t2 (3 each), J, sig, N[6].
+constexpr int GT = 20;
+constexpr int MAX_TAB_NS = 5;  // vertex-pair tables: 2 (ns^2 + ns^3) records <= 48 KB
 
-__device__ __forceinline__ void geo_store(double* t, const PointGeo& g) {
-  const d3 v[6] = {g.x, g.n, g.t1, g.t2, g.s1, g.s2};
+__device__ __forceinline__ void geo_store(double* t, const SSGeo& g) {
+  const d3 v[4] = {g.x, g.n, g.t1, g.t2};
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
+  for (int k = 0; k < 4; ++k) {
     t[3 * k] = v[k].x;
     t[3 * k + 1] = v[k].y;
     t[3 * k + 2] = v[k].z;
   }
-  t[18] = g.J;
+  t[12] = g.J;
+  t[13] = g.sig;
 #pragma unroll
-  for (int k = 0; k < 6; ++k) t[19 + k] = g.N[k];
+  for (int k = 0; k < 6; ++k) t[14 + k] = g.N[k];
 }
 
-__device__ __forceinline__ void geo_load(const double* t, PointGeo& g) {
+__device__ __forceinline__ void geo_load(const double* t, SSGeo& g) {
   g.x = mk(t[0], t[1], t[2]);
   g.n = mk(t[3], t[4], t[5]);
   g.t1 = mk(t[6], t[7], t[8]);
   g.t2 = mk(t[9], t[10], t[11]);
-  g.s1 = mk(t[12], t[13], t[14]);
-  g.s2 = mk(t[15], t[16], t[17]);
-  g.J = t[18];
+  g.J = t[12];
+  g.sig = t[13];
 #pragma unroll
-  for (int k = 0; k < 6; ++k) g.N[k] = t[19 + k];
+  for (int k = 0; k < 6; ++k) g.N[k] = t[14 + k];
 }
 
 // One Sauter-Schwab group: the ns points of region 'reg' at Gauss indices
@@ -334,56 +334,65 @@ __device__ __forceinline__ void geo_load(const double* t, PointGeo& g) {
 // T1, T2 hold the monomial coefficients of position and nodal frame.  With
 // TAB the geometry of both sides is read from shared-memory records (tab_s:
 // the shared side, tab_o: the other side, one record per eta3 index) instead
-// of being evaluated.
+// of being evaluated.  The map is affine in eta3 (ss_group_affine).
 template <bool SHX, bool TAB>
 __device__ __forceinline__ void ssq_group(int cls, int reg, int a, int b, int c, int ns, int px,
                                           int py, const d3 (*Xn)[6], const d3 (*T1)[6],
                                           const d3 (*T2)[6], const double* tab_s,
                                           const double* tab_o, double* U, double* V) {
-  double xu, xv, yu, yv, w, xi, eta;
-  PointGeo gs;
+  double A[4], B[4], wb, xi, eta;
+  ss_group_affine(cls, reg, a, b, c, c_gl, c_glw, A, B, wb);
+  SSGeo gs;
   if (TAB) {
     geo_load(tab_s, gs);
   } else {
-    ss_point_idx(cls, reg, a, b, c, 0, c_gl, c_glw, xu, xv, yu, yv, w);
     if (SHX)
-      to_canonical(px, xu, xv, xi, eta);
+      to_canonical(px, A[0], A[1], xi, eta);
     else
-      to_canonical(py, yu, yv, xi, eta);
-    point_geo_c(Xn[SHX ? 0 : 1], T1[SHX ? 0 : 1], T2[SHX ? 0 : 1], xi, eta, gs);
+      to_canonical(py, A[2], A[3], xi, eta);
+    ss_geo(Xn[SHX ? 0 : 1], T1[SHX ? 0 : 1], T2[SHX ? 0 : 1], xi, eta, gs);
   }
 #pragma unroll
   for (int i = 0; i < 6; ++i) U[i] = gs.N[i];
 #pragma unroll
   for (int k = 0; k < 48; ++k) V[k] = 0.0;
   for (int d = 0; d < ns; ++d) {
-    ss_point_idx(cls, reg, a, b, c, d, c_gl, c_glw, xu, xv, yu, yv, w);
-    PointGeo go;
+    const double e3 = c_gl[d];
+    const double w = wb * c_glw[d];
+    SSGeo go;
     if (TAB) {
       geo_load(tab_o + d * GT, go);
     } else {
       if (SHX)
-        to_canonical(py, yu, yv, xi, eta);
+        to_canonical(py, fma(B[2], e3, A[2]), fma(B[3], e3, A[3]), xi, eta);
       else
-        to_canonical(px, xu, xv, xi, eta);
-      point_geo_c(Xn[SHX ? 1 : 0], T1[SHX ? 1 : 0], T2[SHX ? 1 : 0], xi, eta, go);
+        to_canonical(px, fma(B[0], e3, A[0]), fma(B[1], e3, A[1]), xi, eta);
+      ss_geo(Xn[SHX ? 1 : 0], T1[SHX ? 1 : 0], T2[SHX ? 1 : 0], xi, eta, go);
     }
-    const PointGeo& gx = SHX ? gs : go;
-    const PointGeo& gy = SHX ? go : gs;
+    const SSGeo& gx = SHX ? gs : go;
+    const SSGeo& gy = SHX ? go : gs;
     const d3 Rv = sub(gx.x, gy.x);
     const double ir = inv_sqrt(dot(Rv, Rv));
     const d3 h = scl(ir, Rv);
     const double W = w * gx.J * gy.J;
+    // kernels of Eqs. kappa_S, kappa2_S from the frame dot products; the
+    // co-normals of x enter as s1 = -sig t2, s2 = sig t1
     const double nR = dot(gx.n, h);
-    const d3 sx[2] = {gx.s1, gx.s2}, tx[2] = {gx.t1, gx.t2}, ty[2] = {gy.t1, gy.t2};
+    const double H0 = dot(h, gy.t1), H1 = dot(h, gy.t2);
+    const double N0 = dot(gx.n, gy.t1), N1 = dot(gx.n, gy.t2);
+    const double Q0 = dot(gx.t1, h), Q1 = dot(gx.t2, h);
+    const double P00 = dot(gx.t1, gy.t1), P01 = dot(gx.t1, gy.t2);
+    const double P10 = dot(gx.t2, gy.t1), P11 = dot(gx.t2, gy.t2);
+    const double sir = gx.sig * ir, ir2 = ir * ir;
     double g[8];
-#pragma unroll
-    for (int al = 0; al < 2; ++al)
-#pragma unroll
-      for (int be = 0; be < 2; ++be) {
-        g[2 * al + be] = (dot(sx[al], ty[be]) + dot(sx[al], h) * dot(h, ty[be])) * ir;
-        g[4 + 2 * al + be] = (dot(tx[al], ty[be]) * nR - dot(tx[al], h) * dot(gx.n, ty[be])) * ir * ir;
-      }
+    g[0] = -sir * fma(Q1, H0, P10);
+    g[1] = -sir * fma(Q1, H1, P11);
+    g[2] = sir * fma(Q0, H0, P00);
+    g[3] = sir * fma(Q0, H1, P01);
+    g[4] = fma(P00, nR, -Q0 * N0) * ir2;
+    g[5] = fma(P01, nR, -Q0 * N1) * ir2;
+    g[6] = fma(P10, nR, -Q1 * N0) * ir2;
+    g[7] = fma(P11, nR, -Q1 * N1) * ir2;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
       const double wn = W * go.N[k];
@@ -425,7 +434,7 @@ __device__ __forceinline__ void touching_pair(
     sT2[side][k] = mk(f[6], f[7], f[8]);
   }
   __syncthreads();
-  // nodal values -> monomial coefficients (in place; point_geo_c reads them)
+  // nodal values -> monomial coefficients (in place; ss_geo reads them)
   if (tid < 6) {
     const int side = tid / 3, fld = tid % 3;
     d3* a = fld == 0 ? sXn[side] : (fld == 1 ? sT1[side] : sT2[side]);
@@ -466,8 +475,8 @@ __device__ __forceinline__ void touching_pair(
         to_canonical(px, xu, xv, xi, eta);
       else
         to_canonical(py, yu, yv, xi, eta);
-      PointGeo g;
-      point_geo_c(sXn[side], sT1[side], sT2[side], xi, eta, g);
+      SSGeo g;
+      ss_geo(sXn[side], sT1[side], sT2[side], xi, eta, g);
       geo_store(sTab + (size_t)e * GT, g);
     }
     __syncthreads();

@@ -140,4 +140,44 @@ __host__ __device__ __forceinline__ void point_geo_c(const d3* CX, const d3* CU1
   frame_from(x, a1, a2, p2_val(CU1, xi, eta), p2_val(CU2, xi, eta), g);
 }
 
+// Point geometry for the Sauter-Schwab points (touching pairs), from
+// monomial coefficients: x, n, t1 as in point_geo_c; t2 = sig (n x t1) with
+// sig = sign((n x t1) . u2).  For orthonormal n, t1 the Gram-Schmidt vector
+// of u2 against n and t1 is the unit vector orthogonal to both on the side
+// of u2, i.e. exactly this one, so the frame is the one of Sec. 3.3 at about
+// two thirds of the operations.  The co-normals need no storage either:
+// s1 = t1 x n = -sig t2 and s2 = t2 x n = sig t1.
+struct SSGeo {
+  d3 x, n, t1, t2;
+  double J, sig;
+  double N[6];
+};
+
+__host__ __device__ __forceinline__ void ss_geo(const d3* CX, const d3* CU1, const d3* CU2,
+                                                double xi, double eta, SSGeo& g) {
+  const double l0 = 1.0 - xi - eta;
+  g.N[0] = l0 * (2.0 * l0 - 1.0);
+  g.N[1] = xi * (2.0 * xi - 1.0);
+  g.N[2] = eta * (2.0 * eta - 1.0);
+  g.N[3] = 4.0 * l0 * xi;
+  g.N[4] = 4.0 * xi * eta;
+  g.N[5] = 4.0 * eta * l0;
+  g.x = p2_val(CX, xi, eta);
+  const d3 a1 = fma3(2.0 * xi, CX[3], fma3(eta, CX[4], CX[1]));
+  const d3 a2 = fma3(xi, CX[4], fma3(2.0 * eta, CX[5], CX[2]));
+  const d3 c = cross(a1, a2);
+  const double cc = dot(c, c);
+  const double iJ = inv_sqrt(cc);
+  g.J = cc * iJ;
+  const d3 n = scl(iJ, c);
+  const d3 u1 = p2_val(CU1, xi, eta);
+  const d3 p1 = sub(u1, scl(dot(n, u1), n));
+  const d3 t1 = scl(inv_sqrt(dot(p1, p1)), p1);
+  const d3 m = cross(n, t1);
+  g.sig = dot(m, p2_val(CU2, xi, eta)) < 0.0 ? -1.0 : 1.0;
+  g.n = n;
+  g.t1 = t1;
+  g.t2 = scl(g.sig, m);
+}
+
 }  // namespace mu

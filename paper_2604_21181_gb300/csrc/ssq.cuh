@@ -12,13 +12,11 @@ namespace mu {
 
 // Point (xu, xv) on the test triangle, (yu, yv) on the trial triangle and
 // weight of region 'reg' of class cls (3 coincident, 2 common edge, 1 common
-// vertex) at the Gauss-Legendre indices (a, b, c, d) of (xi, eta1, eta2, eta3).
-__host__ __device__ __forceinline__ void ss_point_idx(int cls, int reg, int a, int b, int c, int d,
-                                                      const double* gl, const double* glw,
+// vertex) at (xi, eta1, eta2, eta3), W the product of the four Gauss weights.
+__host__ __device__ __forceinline__ void ss_point_val(int cls, int reg, double xi, double e1,
+                                                      double e2, double e3, double W,
                                                       double& xu, double& xv, double& yu,
                                                       double& yv, double& w) {
-  const double xi = gl[a], e1 = gl[b], e2 = gl[c], e3 = gl[d];
-  const double W = glw[a] * glw[b] * glw[c] * glw[d];
   const double x3 = xi * xi * xi;
   if (cls == 3) {  // identical triangles: weight xi^3 e1^2 e2
     w = W * x3 * e1 * e1 * e2;
@@ -50,6 +48,30 @@ __host__ __device__ __forceinline__ void ss_point_idx(int cls, int reg, int a, i
   }
 }
 
+
+// the same at the Gauss-Legendre indices (a, b, c, d)
+__host__ __device__ __forceinline__ void ss_point_idx(int cls, int reg, int a, int b, int c, int d,
+                                                      const double* gl, const double* glw,
+                                                      double& xu, double& xv, double& yu,
+                                                      double& yv, double& w) {
+  ss_point_val(cls, reg, gl[a], gl[b], gl[c], gl[d], glw[a] * glw[b] * glw[c] * glw[d], xu, xv,
+               yu, yv, w);
+}
+
+// In every region the four point coordinates are affine in eta3 and the
+// weight does not depend on it: for the ns points of a group (a, b, c, .)
+// coords(eta3) = A + B eta3 and w = wb * glw[d].  A and B come from the map
+// at eta3 = 0 and 1, wb with the weight product of the indices a, b, c.
+__host__ __device__ __forceinline__ void ss_group_affine(int cls, int reg, int a, int b, int c,
+                                                         const double* gl, const double* glw,
+                                                         double A[4], double B[4], double& wb) {
+  const double W3 = glw[a] * glw[b] * glw[c];
+  double w1;
+  ss_point_val(cls, reg, gl[a], gl[b], gl[c], 0.0, W3, A[0], A[1], A[2], A[3], wb);
+  ss_point_val(cls, reg, gl[a], gl[b], gl[c], 1.0, W3, B[0], B[1], B[2], B[3], w1);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) B[k] -= A[k];
+}
 
 // the same, for the flat index pt = ((((a*ns + b)*ns + c)*ns + d)*nreg + reg)
 __host__ __device__ __forceinline__ void ss_point(int cls, int ns, int64_t pt, const double* gl,
