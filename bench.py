@@ -119,23 +119,28 @@ def touching_flops(n_tri: int, n_touch: int, ns: int, q: int) -> float:
     """FP64 flops of one touching_kernel launch (all touching pairs).
 
     The Sauter-Schwab points are processed in groups of ns that share one
-    side.  A point geometry (P2 map, derivatives and interpolated frame from
-    monomial coefficients, projection, Gram-Schmidt) costs ~230 flops; per point, R and its
-    direction (13), the 8 singular geometric kernels (~137) and the 48
-    weighted multiply-adds (96) cost 246; per group the 6 x 48 contraction
-    costs 576.  Coincident and common-edge groups evaluate 1 + ns geometries;
-    common-vertex pairs (ns <= 5) evaluate the 2 (ns^2 + ns^3) distinct ones
-    once.  Per pair, the remainder kappa - kappa^s on the Q x Q rule (~900
-    flops per point pair) and its 6 x 6 x 12 contraction (2 * 432 * Q * 2)."""
+    side.  A point geometry (P2 map, derivatives and interpolated nodal frame
+    from monomial coefficients, normal, one Gram-Schmidt step for t1, t2 from
+    n x t1 and the sign of u2) costs 189 flops.  Per point: R and its
+    direction 12, the weight product 2, the 11 frame dot products and 8
+    singular kernels 85, the 6 shape weights 6 and the 48 multiply-adds 96,
+    and the eta3-affine map with the weight 5 (206; 202 where the geometry
+    comes from the tables and only the weight is mapped).  Per group the
+    6 x 48 contraction costs 576.  Coincident and
+    common-edge groups evaluate 1 + ns geometries; common-vertex pairs
+    (ns <= 5) evaluate the 2 (ns^2 + ns^3) distinct ones once.  Per pair,
+    the remainder kappa - kappa^s on the Q x Q rule (~900 flops per point
+    pair) and its 6 x 6 x 12 contraction (2 * 432 * Q * 2)."""
     n_coinc = n_tri
     n_edge = 3 * n_tri
     n_vert = n_touch - n_coinc - n_edge
     g_ce = (6 * n_coinc + 5 * n_edge) * ns ** 3
     g_v = 2 * n_vert * ns ** 3
-    geo = g_ce * (1 + ns) + (n_vert * 2 * (ns ** 2 + ns ** 3) if ns <= 5 else g_v * (1 + ns))
-    points = (g_ce + g_v) * ns
+    tab = ns <= 5
+    geo = g_ce * (1 + ns) + (n_vert * 2 * (ns ** 2 + ns ** 3) if tab else g_v * (1 + ns))
+    per_point = g_ce * ns * 206.0 + g_v * ns * (202.0 if tab else 206.0)
     per_pair = q * q * 900 + 2 * 432 * q * 2
-    return geo * 230.0 + points * 246.0 + (g_ce + g_v) * 576.0 + n_touch * per_pair
+    return geo * 189.0 + per_point + (g_ce + g_v) * 576.0 + n_touch * per_pair
 
 
 def regular_flops(n_tri: int, n_touch: int, q: int) -> float:
