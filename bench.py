@@ -115,6 +115,12 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ flop models
+# DRAM bytes (read + written) per touching pair of the touching kernel's
+# launches, from its ncu capture on the level-2 sphere (4100 touching pairs);
+# None while the kernel has changed since that capture.
+TOUCH_DRAM_PER_PAIR = None
+
+
 def touching_flops(n_tri: int, n_touch: int, ns: int, q: int) -> float:
     """FP64 flops of one touching_kernel launch (all touching pairs).
 
@@ -264,14 +270,17 @@ def run_ours(args):
         top_ms, top_name, top_n = kernels[0]
         q, ns = int(w["q_regular"]), int(w["ssq_order"])
         if top_name.startswith("touching_kernel"):
+            # all touching pairs, in top_n launches (coincident and common-edge
+            # pairs, then common-vertex pairs): flops of all of them over
+            # their summed CUDA-event time
             fl = touching_flops(F, info["n_touching"], ns, q)
-            ach = fl / (top_ms / top_n / 1e3) / 1e12
-            # DRAM bytes per launch, scaled per touching pair from an ncu capture of this kernel
-            # on the level-2 sphere (9.507 MB read + written for 4100 touching pairs)
-            # DRAM bytes per launch, scaled per touching pair from an ncu capture of this kernel
-            # on the level-2 sphere (9.382 MB read + written for 4100 touching pairs)
-            traffic = int(round(9.382e6 / 4100 * info["n_touching"]))
-            roofline = {"kernel": top_name, "bound": "alu", "pipe": "fp64", "achieved": round(ach, 4),
+            ach = fl / (top_ms / 1e3) / 1e12
+            # DRAM bytes of the step's launches, scaled per touching pair from
+            # the ncu capture of this kernel on the level-2 sphere
+            traffic = (int(round(TOUCH_DRAM_PER_PAIR * info["n_touching"]))
+                       if TOUCH_DRAM_PER_PAIR else None)
+            roofline = {"kernel": top_name, "launches": top_n, "bound": "alu", "pipe": "fp64",
+                        "achieved": round(ach, 4),
                         "peak": round(PEAK_FP64 / 1e12, 4), "unit": "TFLOP/s",
                         "frac": round(ach / (PEAK_FP64 / 1e12), 4), "traffic": traffic,
                         "peak_source": "152 SMs x 2 DFMA/clk x 2.07 GHz (unit counts, max clock)"}

@@ -885,11 +885,11 @@ mueller_status tune_regular(mueller_mesh* m, const PhysConsts& P, int Q, int dty
                 : tune_regular_t<float, 12>(m, P, (float*)Z, ldz, s);
 }
 
-// One high-priority side stream per device.  The touching-pair kernel (FP64
-// pipe) runs there while the regular-pair kernel (FP32 or FP64 multiply-add
-// work, but mostly issue-bound) runs on the caller's stream: the touching
-// kernel's CTAs are dispatched first and the regular kernel's fill the
-// registers and shared memory they leave on each SM.
+// One high-priority side stream per device, for work that runs beside the
+// caller's stream: the touching-pair kernel next to the regular-pair kernel,
+// the panel chain of the block LU next to its trailing updates.  (Two grids
+// share SMs mainly where one grid's last CTAs leave room: CTAs of a grid
+// that still has CTAs waiting for dispatch keep the other grid's CTAs out.)
 static std::mutex g_side_mu;
 static cudaStream_t g_side[64] = {};
 

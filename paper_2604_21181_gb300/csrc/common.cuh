@@ -121,7 +121,8 @@ mueller_status launch_touching(mueller_mesh* m, const PhysConsts& P, int Q, int 
 // tuning run adds into Z and zeroes it again) ahead of launch_regular
 mueller_status tune_regular(mueller_mesh* m, const PhysConsts& P, int Q, int dtype, void* Z,
                             int64_t ldz, cudaStream_t s);
-// the device's high-priority side stream for the touching-pair kernel
+// the device's high-priority side stream (touching pairs beside the regular
+// pairs, panel chain of the block LU beside its trailing updates)
 mueller_status side_stream(cudaStream_t* out);
 // 'after' waits for the work queued on 'before' so far
 mueller_status stream_order(cudaStream_t before, cudaStream_t after);
