@@ -202,6 +202,89 @@ __global__ void __launch_bounds__(256) far_kernel(int64_t np, const double* __re
 
 inline unsigned far_grid(int64_t nd_eval) { return (unsigned)((nd_eval + kFarDT - 1) / kFarDT); }
 
+// Antipodal pair p of the sphere rule (n_phi even): direction k2 = -k1, the
+// ring n_theta-1-it against ring it, or for odd n_theta the middle ring
+// against itself turned by pi.
+__host__ __device__ __forceinline__ void sphere_pair(int64_t p, int n_theta, int n_phi,
+                                                     int64_t& k1, int64_t& k2) {
+  const int64_t full = (int64_t)(n_theta / 2) * n_phi;
+  if (p < full) {
+    const int64_t it = p / n_phi, ip = p % n_phi;
+    k1 = it * n_phi + ip;
+    k2 = (n_theta - 1 - it) * n_phi + (ip + n_phi / 2) % n_phi;
+  } else {
+    const int64_t mid = n_theta / 2, ip = p - full;
+    k1 = mid * n_phi + ip;
+    k2 = mid * n_phi + ip + n_phi / 2;
+  }
+}
+
+// F at the sphere-rule directions, which come in antipodal pairs
+// (d_k2 = -d_k1 exactly): exp(-i k d_k2.y) = conj(exp(-i k d_k1.y)), so one
+// phase serves both directions of a pair.  DP pairs per CTA; dirs and F
+// point at the sphere block (index k).
+constexpr int kFarDP = 2;
+template <int DP>
+__global__ void __launch_bounds__(256) far_pair_kernel(int64_t np, const double* __restrict__ qd,
+                                                       const double2* __restrict__ rec,
+                                                       const double* __restrict__ dirs,
+                                                       int n_theta, int n_phi, double ka,
+                                                       double2* __restrict__ F) {
+  __shared__ double2 tab[kCisN];
+  __shared__ double red[12][256];
+  cis_fill(tab);
+  __syncthreads();
+  const int64_t npairs = (int64_t)n_theta * n_phi / 2;
+  const int64_t p0 = (int64_t)blockIdx.x * DP;
+  double rk[DP][3];
+#pragma unroll
+  for (int q = 0; q < DP; ++q) {
+    int64_t k1, k2;
+    sphere_pair(p0 + q < npairs ? p0 + q : npairs - 1, n_theta, n_phi, k1, k2);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) rk[q][a] = -ka * dirs[3 * k1 + a];
+  }
+  double acc[DP][2][12];
+#pragma unroll
+  for (int q = 0; q < DP; ++q)
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int c = 0; c < 12; ++c) acc[q][h][c] = 0.0;
+  for (int64_t t = threadIdx.x; t < np; t += blockDim.x) {
+    const double* qp = qd + t * QD_STRIDE;
+    const double y0 = qp[0], y1 = qp[1], y2 = qp[2];
+    const double2* o = rec + t * 6;
+    double2 v[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) v[c] = o[c];
+#pragma unroll
+    for (int q = 0; q < DP; ++q) {
+      const double2 e = cis_tab(fma(rk[q][0], y0, fma(rk[q][1], y1, rk[q][2] * y2)), tab);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        acc[q][0][2 * c] = fma(v[c].x, e.x, fma(-v[c].y, e.y, acc[q][0][2 * c]));
+        acc[q][0][2 * c + 1] = fma(v[c].x, e.y, fma(v[c].y, e.x, acc[q][0][2 * c + 1]));
+        acc[q][1][2 * c] = fma(v[c].x, e.x, fma(v[c].y, e.y, acc[q][1][2 * c]));
+        acc[q][1][2 * c + 1] = fma(-v[c].x, e.y, fma(v[c].y, e.x, acc[q][1][2 * c + 1]));
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < DP; ++q) {
+    if (p0 + q < npairs) {
+      int64_t kk[2];
+      sphere_pair(p0 + q, n_theta, n_phi, kk[0], kk[1]);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const double* dd = dirs + 3 * kk[h];
+        far_finish(red, acc[q][h], dd[0], dd[1], dd[2], ka, F + kk[h] * 3);
+        __syncthreads();
+      }
+    }
+  }
+}
+
 // The directions shared by all right-hand sides (sphere rule, user list:
 // indices 1 .. nd-1) for RS right-hand sides per CTA: each phase
 // exp(-i k r.y) is computed once and applied to the RS current records.
@@ -300,19 +383,15 @@ __global__ void copy_user_dirs_kernel(const double2* __restrict__ Fall, int64_t 
   Fout[t] = Fall[((s * nd_all) + off + d) * 3 + a];
 }
 
-}  // namespace
-
-mueller_status far_field(mueller_mesh* m, const PhysConsts& P, int Q, const void* X, int r,
-                         const double* inc, const double* dirs, int64_t ndir, void* F, double* xs,
-                         int n_theta, int n_phi, cudaStream_t s) {
-  TriangleRule rule;
-  if (!triangle_rule(Q, rule)) return MUELLER_ERR_INVALID_ARG;
-  const int64_t np = m->nt * Q, N = 4 * m->nn;
-  // direction list per RHS: forward k, sphere rule (theta-major), user dirs
-  std::vector<double> gth, wth;
-  gauss_legendre_unit(n_theta, gth, wth);
-  const int64_t nsph = (int64_t)n_theta * n_phi;
-  const int64_t nd = 1 + nsph + ndir;
+// Direction list of every RHS: forward k (index 0), the sphere rule
+// (1 + it n_phi + ip: cos(theta) on Gauss-Legendre nodes, phi on n_phi
+// equal steps), the user directions.  With n_phi even the sphere rule is
+// written in exact antipodal pairs (sphere_pair), the second direction of
+// each pair the negated first (Gauss-Legendre nodes are symmetric, up to
+// the rounding of their computation).
+std::vector<double> far_dirs(int r, const double* inc, int n_theta, int n_phi,
+                             const std::vector<double>& gth, const double* dirs, int64_t ndir) {
+  const int64_t nsph = (int64_t)n_theta * n_phi, nd = 1 + nsph + ndir;
   std::vector<double> hd((size_t)r * nd * 3);
   for (int sidx = 0; sidx < r; ++sidx) {
     double* o = hd.data() + (size_t)sidx * nd * 3;
@@ -329,9 +408,55 @@ mueller_status far_field(mueller_mesh* m, const PhysConsts& P, int Q, const void
         dd[2] = ct;
       }
     }
+    if (n_phi % 2 == 0)
+      for (int64_t p = 0; p < nsph / 2; ++p) {
+        int64_t k1, k2;
+        sphere_pair(p, n_theta, n_phi, k1, k2);
+        for (int a = 0; a < 3; ++a) o[3 * (1 + k2) + a] = -o[3 * (1 + k1) + a];
+      }
     for (int64_t d = 0; d < ndir; ++d)
       for (int a = 0; a < 3; ++a) o[3 * (1 + nsph + d) + a] = dirs[3 * d + a];
   }
+  return hd;
+}
+
+// F of one RHS at all its directions: forward and user directions by
+// far_kernel, the sphere rule by antipodal pairs (far_pair_kernel) when
+// n_phi is even.
+mueller_status far_one_rhs(int64_t np, const double* qd, const double2* rec, const double* dirs,
+                           int64_t nd, int n_theta, int n_phi, int64_t ndir, double ka,
+                           double2* F, cudaStream_t s) {
+  const int64_t nsph = (int64_t)n_theta * n_phi;
+  if (n_phi % 2 != 0) {
+    { Prof prof_("far_kernel", s); far_kernel<kFarDT><<<far_grid(nd), 256, 0, s>>>(np, qd, rec, dirs, nd, ka, F); }
+    MU_CHECK_LAUNCH("far_kernel");
+    return MUELLER_OK;
+  }
+  { Prof prof_("far_kernel", s); far_kernel<kFarDT><<<far_grid(1), 256, 0, s>>>(np, qd, rec, dirs, 1, ka, F); }
+  const int64_t npairs = nsph / 2;
+  { Prof prof_("far_pair_kernel", s); far_pair_kernel<kFarDP><<<(unsigned)((npairs + kFarDP - 1) / kFarDP), 256, 0, s>>>(
+      np, qd, rec, dirs + 3, n_theta, n_phi, ka, F + 3); }
+  if (ndir > 0)
+    { Prof prof_("far_kernel", s); far_kernel<kFarDT><<<far_grid(ndir), 256, 0, s>>>(np, qd, rec, dirs + 3 * (1 + nsph), ndir, ka,
+                                                                                     F + 3 * (1 + nsph)); }
+  MU_CHECK_LAUNCH("far_kernel");
+  return MUELLER_OK;
+}
+
+}  // namespace
+
+mueller_status far_field(mueller_mesh* m, const PhysConsts& P, int Q, const void* X, int r,
+                         const double* inc, const double* dirs, int64_t ndir, void* F, double* xs,
+                         int n_theta, int n_phi, cudaStream_t s) {
+  TriangleRule rule;
+  if (!triangle_rule(Q, rule)) return MUELLER_ERR_INVALID_ARG;
+  const int64_t np = m->nt * Q, N = 4 * m->nn;
+  // direction list per RHS: forward k, sphere rule (theta-major), user dirs
+  std::vector<double> gth, wth;
+  gauss_legendre_unit(n_theta, gth, wth);
+  const int64_t nsph = (int64_t)n_theta * n_phi;
+  const int64_t nd = 1 + nsph + ndir;
+  const std::vector<double> hd = far_dirs(r, inc, n_theta, n_phi, gth, dirs, ndir);
   double phi[MAX_Q * 6];
   for (int p = 0; p < Q; ++p) {
     const double l0 = 1.0 - rule.xi[p] - rule.eta[p], l1 = rule.xi[p], l2 = rule.eta[p];
@@ -375,7 +500,7 @@ mueller_status far_field(mueller_mesh* m, const PhysConsts& P, int Q, const void
     { Prof prof_("currents_kernel", s); currents_kernel<<<dim3(nblk_pts, r), 256, 0, s>>>(m->nt, Q, m->qd64, m->T, (const double2*)X, r,
                                                        N, dphi, rec, cab); }
     if (r == 1) {
-      { Prof prof_("far_kernel", s); far_kernel<kFarDT><<<far_grid(nd), 256, 0, s>>>(np, m->qd64, rec, ddirs, nd, P.ka, Fall); }
+      st = far_one_rhs(np, m->qd64, rec, ddirs, nd, n_theta, n_phi, ndir, P.ka, Fall, s);
     } else {
       // forward direction (one per right-hand side), then the shared
       // directions for 4 right-hand sides per CTA
@@ -386,14 +511,16 @@ mueller_status far_field(mueller_mesh* m, const PhysConsts& P, int Q, const void
       { Prof prof_("far_multi_kernel", s); far_multi_kernel<4><<<dim3((unsigned)(nd - 1), (unsigned)((r + 3) / 4)), 256, 0, s>>>(
           np, m->qd64, rec, r, ddirs, nd, P.ka, Fall); }
     }
-    { Prof prof_("xs_kernel", s); xs_kernel<<<r, 256, 0, s>>>(Fall, nd, n_theta, n_phi, dwth, dinc, P.ka, cab, (int)nblk_pts, dxs); }
-    if (ndir > 0)
-      { Prof prof_("copy_user_dirs_kernel", s); copy_user_dirs_kernel<<<(unsigned)(((int64_t)r * ndir * 3 + 255) / 256), 256, 0, s>>>(
-          Fall, nd, 1 + nsph, ndir, r, (double2*)F); }
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMemcpyAsync(xs, dxs, (size_t)r * 3 * 8, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) st = cuda_fail(e, "far field");
+    if (!st) {
+      { Prof prof_("xs_kernel", s); xs_kernel<<<r, 256, 0, s>>>(Fall, nd, n_theta, n_phi, dwth, dinc, P.ka, cab, (int)nblk_pts, dxs); }
+      if (ndir > 0)
+        { Prof prof_("copy_user_dirs_kernel", s); copy_user_dirs_kernel<<<(unsigned)(((int64_t)r * ndir * 3 + 255) / 256), 256, 0, s>>>(
+            Fall, nd, 1 + nsph, ndir, r, (double2*)F); }
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaMemcpyAsync(xs, dxs, (size_t)r * 3 * 8, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) st = cuda_fail(e, "far field");
+    }
   }
   cudaFreeAsync(buf, s);
   return st;
@@ -479,25 +606,7 @@ mueller_status far_field_noalloc(mueller_mesh* m, const PhysConsts& P, int Q, co
   char* buf = nullptr;
   mueller_status st = far_scratch_address((void**)&buf);
   if (st) return st;
-  std::vector<double> hd((size_t)r * nd * 3);
-  for (int sidx = 0; sidx < r; ++sidx) {
-    double* o = hd.data() + (size_t)sidx * nd * 3;
-    o[0] = inc[6 * sidx];
-    o[1] = inc[6 * sidx + 1];
-    o[2] = inc[6 * sidx + 2];
-    for (int it = 0; it < n_theta; ++it) {
-      const double ct = 2.0 * gth[it] - 1.0, st2 = sqrt(fmax(0.0, 1.0 - ct * ct));
-      for (int ip = 0; ip < n_phi; ++ip) {
-        const double ph = 2.0 * 3.14159265358979323846 * ip / n_phi;
-        double* dd = o + 3 * (1 + (int64_t)it * n_phi + ip);
-        dd[0] = st2 * cos(ph);
-        dd[1] = st2 * sin(ph);
-        dd[2] = ct;
-      }
-    }
-    for (int64_t d = 0; d < ndir; ++d)
-      for (int a = 0; a < 3; ++a) o[3 * (1 + nsph + d) + a] = dirs[3 * d + a];
-  }
+  const std::vector<double> hd = far_dirs(r, inc, n_theta, n_phi, gth, dirs, ndir);
   double phi[MAX_Q * 6];
   for (int p = 0; p < Q; ++p) {
     const double l0 = 1.0 - rule.xi[p] - rule.eta[p], l1 = rule.xi[p], l2 = rule.eta[p];
@@ -522,10 +631,9 @@ mueller_status far_field_noalloc(mueller_mesh* m, const PhysConsts& P, int Q, co
   if (e != cudaSuccess) return cuda_fail(e, "far-field (allocation-free) setup");
   { Prof prof_("currents_kernel", s); currents_kernel<<<dim3(nblk_pts, r), 256, 0, s>>>(m->nt, Q, m->qd64, m->T, (const double2*)X, r, N, dphi, rec, cab); }
   for (int sidx = 0; sidx < r; ++sidx) {
-    Prof prof_("far_kernel", s);
-    far_kernel<kFarDT><<<far_grid(nd), 256, 0, s>>>(np, m->qd64, rec + (size_t)sidx * np * 6,
-                                                    ddirs + (size_t)sidx * nd * 3, nd, P.ka,
-                                                    Fall + (size_t)sidx * nd * 3);
+    st = far_one_rhs(np, m->qd64, rec + (size_t)sidx * np * 6, ddirs + (size_t)sidx * nd * 3, nd,
+                     n_theta, n_phi, ndir, P.ka, Fall + (size_t)sidx * nd * 3, s);
+    if (st) return st;
   }
   { Prof prof_("xs_kernel", s); xs_kernel<<<r, 256, 0, s>>>(Fall, nd, n_theta, n_phi, dwth, dinc, P.ka, cab, (int)nblk_pts, dxs); }
   if (ndir > 0) {

@@ -946,17 +946,17 @@ __global__ void givens_kernel(int j, int m, double2* __restrict__ hacc, const do
                               double* __restrict__ res) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double2* col = Hm + (int64_t)j * (m + 1);
-  for (int l = 0; l <= j; ++l) col[l] = hacc[l];
-  col[j + 1] = make_double2(*hn, 0.0);
+  // earlier rotations [c s; -conj(s) c] down the new column, the entry
+  // rotated into position l + 1 carried in a register
+  double2 a = hacc[0];
   for (int l = 0; l < j; ++l) {
-    const double2 a = col[l], b = col[l + 1];
+    const double2 b = hacc[l + 1];
     const double c = cs[l];
     const double2 s = sn[l];
-    // [c s; -conj(s) c]
     col[l] = make_double2(c * a.x + s.x * b.x - s.y * b.y, c * a.y + s.x * b.y + s.y * b.x);
-    col[l + 1] = make_double2(-(s.x * a.x + s.y * a.y) + c * b.x, -(s.x * a.y - s.y * a.x) + c * b.y);
+    a = make_double2(-(s.x * a.x + s.y * a.y) + c * b.x, -(s.x * a.y - s.y * a.x) + c * b.y);
   }
-  const double2 a = col[j], b = col[j + 1];
+  const double2 b = make_double2(*hn, 0.0);
   const double aa = hypot(a.x, a.y), bb = hypot(b.x, b.y);
   const double rho = hypot(aa, bb);
   double c;
@@ -1167,16 +1167,18 @@ __global__ void givens_b_kernel(int j, int m, int r, double2* __restrict__ hacc,
   double* c_ = cs + (int64_t)s * (m + 1);
   double2* s_ = sn + (int64_t)s * (m + 1);
   double2* gg = g + (int64_t)s * (m + 1);
-  for (int l = 0; l <= j; ++l) col[l] = ha[l];
-  col[j + 1] = make_double2(hn[s], 0.0);
+  // the earlier rotations, applied down the new column; the entry being
+  // rotated into position l + 1 is carried in a register (a), so only the
+  // loads of ha, c_ and s_ (independent of the chain) touch memory
+  double2 a = ha[0];
   for (int l = 0; l < j; ++l) {
-    const double2 a = col[l], b = col[l + 1];
+    const double2 b = ha[l + 1];
     const double c = c_[l];
     const double2 sv = s_[l];
     col[l] = make_double2(c * a.x + sv.x * b.x - sv.y * b.y, c * a.y + sv.x * b.y + sv.y * b.x);
-    col[l + 1] = make_double2(-(sv.x * a.x + sv.y * a.y) + c * b.x, -(sv.x * a.y - sv.y * a.x) + c * b.y);
+    a = make_double2(-(sv.x * a.x + sv.y * a.y) + c * b.x, -(sv.x * a.y - sv.y * a.x) + c * b.y);
   }
-  const double2 a = col[j], b = col[j + 1];
+  const double2 b = make_double2(hn[s], 0.0);
   const double aa = hypot(a.x, a.y), bb = hypot(b.x, b.y);
   const double rho = hypot(aa, bb);
   double c;

@@ -210,27 +210,29 @@ def test_far_field_matches_oracle():
 
 
 @pytest.mark.parametrize("ka", [0.5, 60.0, 4.0e4])
-def test_far_field_phase_range_matches_oracle(ka):
+@pytest.mark.parametrize("r,n_phi", [(1, 16), (1, 15), (2, 16)])
+def test_far_field_phase_range_matches_oracle(ka, r, n_phi):
     """Random currents, so that every phase exp(-i k r.y) counts: k a = 60
     spans many periods of the table-driven exp(i th), 4e4 (|th| beyond
-    2^20 pi/128) the sincos branch.  Both sides form th = k r.y in FP64 with
-    its rounding of a few ulp(|th|), so the bound is 1e-12 of max |F| or
-    50 k a eps, whichever is larger."""
+    2^20 pi/128) the sincos branch.  One RHS with an even n_phi takes the
+    antipodal-pair kernel, an odd n_phi the per-direction one, two RHS the
+    multi-RHS kernel.  Both sides form th = k r.y in FP64 with its rounding
+    of a few ulp(|th|), so the bound is 1e-12 of max |F| or 50 k a eps,
+    whichever is larger."""
     xyz, tri6 = workloads.icosphere_p2(1)
     m = mu.Mesh(xyz, tri6)
     m.tangent_frame(0, out=False)
     mu.assemble(m, mu.Params(ka=1.0, eps_r=(2.0, 0.0), ssq_order=2, frame_rule=0),
                 mu.MUELLER_C128)  # point geometry of the rule
     p = mu.Params(ka=ka, eps_r=(2.0, 0.0), ssq_order=2, frame_rule=0)
-    inc = workloads.fibonacci_plane_waves(1)
+    inc = workloads.fibonacci_plane_waves(1)[:r]
     rng = np.random.default_rng(11)
-    r = inc.shape[0]
     X = rng.standard_normal((r, m.N)) + 1j * rng.standard_normal((r, m.N))
     dirs = workloads.fibonacci_directions(9)
-    F, xs = mu.far_field(m, p, torch.from_numpy(X).cuda(), inc, dirs=dirs, n_theta=8, n_phi=16)
+    F, xs = mu.far_field(m, p, torch.from_numpy(X).cuda(), inc, dirs=dirs, n_theta=9, n_phi=n_phi)
     om = oracle.Mesh(xyz, tri6, frame_rule=0)
     pw = dict(ka=ka, eps_r=(2.0, 0.0), mu_r=(1.0, 0.0), q_regular=6, ssq_order=2)
-    Fo, xso = om.far_field(pw, X, inc, dirs=dirs, n_theta=8, n_phi=16)
+    Fo, xso = om.far_field(pw, X, inc, dirs=dirs, n_theta=9, n_phi=n_phi)
     tol = max(1e-12, 50.0 * ka * np.finfo(float).eps)
     np.testing.assert_allclose(F.cpu().numpy(), Fo, rtol=0, atol=tol * np.abs(Fo).max())
     np.testing.assert_allclose(xs[:, :2], xso[:, :2], rtol=tol, atol=0)
