@@ -296,6 +296,7 @@ __global__ void __launch_bounds__(32 * W) regular_batch_kernel(const RegBody* __
 
 // ------------------------------------------------------- touching pairs
 constexpr int TT = 96;  // threads per touching pair (= SSQ points per batch)
+constexpr int kTouchMinBlocksCE = 3;  // CTAs per SM of the table-free launch
 
 // Geometry record of one Sauter-Schwab point side in shared memory:
 // x, n, t1, t2 (3 each), J, sig, N[6].
@@ -649,16 +650,20 @@ __device__ __forceinline__ void touching_pair(
   }
 }
 
-template <int Q>
-__global__ void __launch_bounds__(TT) touching_kernel(
-    int64_t n_touch, const TouchPair* __restrict__ tp, const double* __restrict__ X,
-    const int32_t* __restrict__ T, const double* __restrict__ frame,
+// CTA b takes pair order[off + b] (n pairs in this launch).  MINB CTAs per
+// SM: 3 for the coincident and common-edge pairs (no tables: the static
+// shared memory allows it, the register cap costs some spills), 2 with the
+// common-vertex tables.
+template <int Q, int MINB>
+__global__ void __launch_bounds__(TT, MINB) touching_kernel(
+    int64_t n, const int32_t* __restrict__ order, int64_t off, const TouchPair* __restrict__ tp,
+    const double* __restrict__ X, const int32_t* __restrict__ T, const double* __restrict__ frame,
     const double* __restrict__ qd, int ns, KConst<double> K, double ae_re, double ae_im,
     double am_re, double am_im, int dtype, void* __restrict__ Zv, int64_t ldz, int64_t H,
     double* __restrict__ near, const int32_t* __restrict__ tp_slot, int use_tables) {
-  if ((int64_t)blockIdx.x >= n_touch) return;
-  touching_pair<Q>(blockIdx.x, tp, X, T, frame, qd, ns, K, ae_re, ae_im, am_re, am_im, dtype, Zv,
-                   ldz, H, near, tp_slot, use_tables);
+  if ((int64_t)blockIdx.x >= n) return;
+  touching_pair<Q>(order[off + blockIdx.x], tp, X, T, frame, qd, ns, K, ae_re, ae_im, am_re,
+                   am_im, dtype, Zv, ldz, H, near, tp_slot, use_tables);
 }
 
 struct TouchBody {
@@ -936,11 +941,21 @@ mueller_status launch_touching(mueller_mesh* m, const PhysConsts& P, int Q, int 
   if (m->n_touch == 0) return MUELLER_OK;
   const double ae_re = 0.5 * (P.eps_re + 1.0), ae_im = 0.5 * P.eps_im;
   const double am_re = 0.5 * (P.mu_re + 1.0), am_im = 0.5 * P.mu_im;
-  auto kern = Q == 6 ? touching_kernel<6> : touching_kernel<12>;
+  auto kern_ce = Q == 6 ? touching_kernel<6, kTouchMinBlocksCE> : touching_kernel<12, kTouchMinBlocksCE>;
+  auto kern_v = Q == 6 ? touching_kernel<6, 2> : touching_kernel<12, 2>;
   const int use_tables = ns <= MAX_TAB_NS ? 1 : 0;
   const size_t tab_bytes = use_tables ? (size_t)2 * (ns * ns + ns * ns * ns) * GT * sizeof(double) : 0;
-  MU_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tab_bytes));
-  { Prof prof_("touching_kernel<Q>", s); kern<<<(unsigned)m->n_touch, TT, tab_bytes, s>>>(m->n_touch, m->tp, m->X, m->T, m->frame, m->qd64, ns,
+  MU_CUDA(cudaFuncSetAttribute(kern_v, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tab_bytes));
+  MU_CUDA(cudaFuncSetAttribute(kern_ce, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared));
+  // coincident and common-edge pairs (no tables), then common-vertex pairs
+  const int64_t n_ce = m->n_touch_ce, n_v = m->n_touch - m->n_touch_ce;
+  if (n_ce > 0)
+    { Prof prof_("touching_kernel<Q>", s); kern_ce<<<(unsigned)n_ce, TT, 0, s>>>(n_ce, m->tp_order, 0, m->tp, m->X, m->T, m->frame, m->qd64, ns,
+                                            kconst<double>(P), ae_re, ae_im, am_re, am_im, dtype,
+                                            Z, ldz, 2 * m->nn, (double*)near, m->tp_slot, 0); }
+  if (n_v > 0)
+    { Prof prof_("touching_kernel<Q>", s); kern_v<<<(unsigned)n_v, TT, tab_bytes, s>>>(n_v, m->tp_order, n_ce, m->tp, m->X, m->T, m->frame, m->qd64, ns,
                                             kconst<double>(P), ae_re, ae_im, am_re, am_im, dtype,
                                             Z, ldz, 2 * m->nn, (double*)near, m->tp_slot, use_tables); }
   MU_CHECK_LAUNCH("touching_kernel");

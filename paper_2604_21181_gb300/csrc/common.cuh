@@ -94,6 +94,8 @@ struct mueller_mesh {
   int32_t* near_rowptr = nullptr;  // nn + 1
   int32_t* near_col = nullptr;     // nnzb
   int32_t* tp_slot = nullptr;      // n_touch x 36 near slots of the pair's node pairs
+  int32_t* tp_order = nullptr;     // pair indices: coincident and common-edge first
+  int64_t n_touch_ce = 0;          // how many of them come before the common-vertex pairs
   std::vector<int32_t> near_rowptr_h, near_col_h;
   // small device scratch
   int32_t* d_flags = nullptr;      // status words

@@ -241,7 +241,7 @@ const char* mueller_status_string(mueller_status s) {
 void mueller_mesh_free(mueller_mesh* m) {
   if (!m) return;
   void* ptrs[] = {m->X, m->T, m->n2e_ptr, m->n2e, m->frame, m->qd64, m->qd32, m->tp,
-                  m->near_rowptr, m->near_col, m->tp_slot, m->d_flags, m->d_scal};
+                  m->near_rowptr, m->near_col, m->tp_slot, m->tp_order, m->d_flags, m->d_scal};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete m;
@@ -327,6 +327,15 @@ mueller_status mueller_mesh_load(const double* xyz, int64_t nn, const int32_t* t
     }
   }
   m->n_touch = (int64_t)tp.size();
+  // launch order of the touching kernel: coincident and common-edge pairs,
+  // then the common-vertex pairs (which use shared-memory tables)
+  std::vector<int32_t> order;
+  order.reserve(tp.size());
+  for (int pass = 0; pass < 2; ++pass)
+    for (size_t q = 0; q < tp.size(); ++q)
+      if ((tp[q].cls == 1) == (pass == 1)) order.push_back((int32_t)q);
+  m->n_touch_ce = 0;
+  for (const TouchPair& q : tp) m->n_touch_ce += q.cls != 1;
   // ---- near-part block layout: node pairs of the touching element pairs.
   // Row by row: the columns of test node ni are the nodes of every trial
   // element touching an element that holds ni (deduplicated with a stamp
@@ -375,6 +384,7 @@ mueller_status mueller_mesh_load(const double* xyz, int64_t nn, const int32_t* t
   if (!st) st = upload(&m->near_rowptr, m->near_rowptr_h.data(), m->near_rowptr_h.size(), s);
   if (!st) st = upload(&m->near_col, m->near_col_h.data(), m->near_col_h.size(), s);
   if (!st) st = upload(&m->tp_slot, slot.data(), slot.size(), s);
+  if (!st) st = upload(&m->tp_order, order.data(), order.size(), s);
   if (!st) {
     cudaError_t e = cudaMalloc((void**)&m->d_flags, 64 * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc((void**)&m->d_scal, 64 * sizeof(double));
