@@ -305,3 +305,34 @@ def mbj_apply(Z, block, v):
     if st:
         raise np.linalg.LinAlgError("singular preconditioner block")
     return out
+
+
+def cross_sections(mesh: Mesh, p, inc):
+    """C_ext, C_sca, C_abs (one row per incident wave) of the oracle's
+    pipeline: assembly (Sec. 4), dense LU solve, far field and cross
+    sections (the formulas of the far-field step)."""
+    Z = mesh.assemble(p)
+    B = mesh.rhs(p, inc)
+    X = lu_solve(Z, B)
+    return np.asarray(mesh.far_field(p, X, inc)[1])
+
+
+def cross_section_gradient(mesh: Mesh, p, inc, h: float = 1e-4):
+    """Jacobian of (C_ext, C_sca, C_abs) of the first incident wave with
+    respect to (Re eps_r, Im eps_r, Re mu_r, Im mu_r), by central differences
+    of cross_sections with step h on each real parameter (truncation
+    O(h^2)).  The paper defines no gradient; this is the plain derivative of
+    the oracle's own results, a 3 x 4 array."""
+    J = np.zeros((3, 4))
+    for k in range(4):
+        key, part = ("eps_r", "mu_r")[k // 2], k % 2
+        val = list(p[key])
+        xs = []
+        for sgn in (1.0, -1.0):
+            q = dict(p)
+            v = list(val)
+            v[part] += sgn * h
+            q[key] = tuple(v)
+            xs.append(cross_sections(mesh, q, inc)[0])
+        J[:, k] = (xs[0] - xs[1]) / (2.0 * h)
+    return J

@@ -40,4 +40,4 @@ from .api import (  # noqa: F401
     sync,
 )
 from .buildlib import build  # noqa: F401
-from . import sweep  # noqa: F401
+from . import grad, sweep  # noqa: F401

@@ -1,0 +1,122 @@
+"""Gradients of the cross sections with respect to the material parameters.
+
+For the scatterer's relative permittivity eps_r and permeability mu_r (each
+complex, i.e. two real parameters) this returns the Jacobian of
+(C_ext, C_sca, C_abs) of one incident wave, and a torch.autograd.Function
+around it.
+
+Method (the tangent-linear form of the adjoint relation: for four real
+parameters and three outputs both need the same number of solves, and this
+one reuses the forward operator and its preconditioner):
+
+* Z(theta) x = b with b independent of eps_r, mu_r; Z is holomorphic in
+  eps_r and mu_r (through k_i = k_a sqrt(eps_r mu_r), principal branch, and
+  the explicit eps_r, mu_r factors of Eq. global_system), so for the real
+  part of a parameter  Z x_theta = -(dZ/dtheta) x  and for the imaginary part
+  the direction is i x_theta.
+* (dZ/dtheta) x is the central difference of two assembled operators,
+  (Z(theta + h) x - Z(theta - h) x) / 2h, each product taken right after
+  its assembly into one scratch matrix (no dZ is stored).
+* C_ext is linear in x and C_sca, C_abs are Hermitian quadratic forms, so
+  dC_ext = C_ext(x_theta) and dC_q = C_q(x + x_theta) - C_q(x) - C_q(x_theta),
+  all from one far-field call over the combined currents.
+Every step runs in the library's CUDA kernels (FP64 assembly, FP64 GMRES
+with the block-Jacobi preconditioner, FP64 far field).
+"""
+
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+from . import api
+
+
+def _fp64_solve(op, B, tol):
+    return api.solve(op, B, api.SolverOpts(mode=api.SOLVE_GMRES, restart=50, tol=tol))[0]
+
+
+def forward_state(mesh, params, inc, block=None, tol=1e-12):
+    """Assembly (FP64), block-Jacobi, FP64 GMRES and far field of one incident
+    wave.  Returns (xs numpy (3,), state) with state holding Z, the operator
+    and the solution for material_jacobian."""
+    inc = np.ascontiguousarray(inc, dtype=np.float64).reshape(-1, 6)[:1]
+    Z, _, B = api.assemble(mesh, params, api.MUELLER_C128, inc=inc)
+    op = api.Operator(mesh, Z, dtype=api.MUELLER_C128)
+    api.precond_build(op, block or min(256, mesh.N // 2))
+    X = _fp64_solve(op, B, tol)
+    _, xs = api.far_field(mesh, params, X, inc)
+    return xs[0], dict(mesh=mesh, params=params, inc=inc, op=op, X=X, xs=xs[0], tol=tol)
+
+
+def material_jacobian(state, h_rel=1e-5):
+    """3 x 4 Jacobian of (C_ext, C_sca, C_abs) with respect to
+    (Re eps_r, Im eps_r, Re mu_r, Im mu_r) at the forward state."""
+    torch = api._torch()
+    mesh, params, inc, op, X = (state[k] for k in ("mesh", "params", "inc", "op", "X"))
+    Zs = torch.empty_like(op.Z)
+    tangents = []
+    for key in ("eps_r", "mu_r"):
+        val = complex(*getattr(params, key))
+        h = h_rel * max(1.0, abs(val))
+        y = []
+        for sgn in (1.0, -1.0):
+            v = val + sgn * h
+            q = dataclasses.replace(params, **{key: (v.real, v.imag)})
+            api.assemble(mesh, q, api.MUELLER_C128, Z=Zs)
+            y.append(api.matvec(api.Operator(mesh, Zs, dtype=api.MUELLER_C128), X))
+        tangents.append(_fp64_solve(op, -(y[0] - y[1]) / (2.0 * h), state["tol"]))
+    del Zs
+    comb = []
+    for Xt in tangents:
+        comb += [Xt, 1j * Xt, X + Xt, X + 1j * Xt]
+    Xall = torch.cat(comb).contiguous()
+    _, xs = api.far_field(mesh, params, Xall, np.repeat(inc, Xall.shape[0], axis=0))
+    x0 = state["xs"]
+    J = np.zeros((3, 4))
+    for c in range(2):
+        lin_re, lin_im, sum_re, sum_im = xs[4 * c:4 * c + 4]
+        J[0, 2 * c] = lin_re[0]
+        J[0, 2 * c + 1] = lin_im[0]
+        for o in (1, 2):
+            J[o, 2 * c] = sum_re[o] - x0[o] - lin_re[o]
+            J[o, 2 * c + 1] = sum_im[o] - x0[o] - lin_im[o]
+    return J
+
+
+def _autograd_function():
+    torch = api._torch()
+
+    class CrossSections(torch.autograd.Function):
+        """(C_ext, C_sca, C_abs) of one incident wave as a function of
+        eps = (Re eps_r, Im eps_r) and mu = (Re mu_r, Im mu_r), float64
+        tensors of shape (2,); the Jacobian is formed in backward."""
+
+        @staticmethod
+        def forward(ctx, eps, mu, mesh, params, inc):
+            p = dataclasses.replace(params, eps_r=tuple(float(v) for v in eps.tolist()),
+                                    mu_r=tuple(float(v) for v in mu.tolist()))
+            xs, state = forward_state(mesh, p, inc)
+            ctx.state = state
+            return torch.tensor(xs, dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, g):
+            J = torch.from_numpy(material_jacobian(ctx.state))
+            ctx.state = None
+            gp = g.to(torch.float64) @ J
+            return gp[:2], gp[2:], None, None, None
+
+    return CrossSections
+
+
+_cs = None
+
+
+def cross_sections(eps, mu, mesh, params, inc):
+    """Differentiable (C_ext, C_sca, C_abs); see CrossSections."""
+    global _cs
+    if _cs is None:
+        _cs = _autograd_function()
+    return _cs.apply(eps, mu, mesh, params, inc)
