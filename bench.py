@@ -369,6 +369,7 @@ def run_ours(args):
         extras["level4_16rhs"] = level4_16rhs(mu, torch, dev)
         extras["multibody64"] = multibody64(mu, torch, dev)
         extras["lspr_sweep"] = lspr_sweep(mu, torch, dev)
+        extras["gradients_L3"] = gradients_l3(mu, torch, dev)
         cpu = cpu_baseline(args.workload, budget_s=15.0)
 
     if rank == 0:
@@ -510,6 +511,36 @@ def multibody64(mu, torch, dev):
             "precond_total_s": round(t_pre, 3), "solve_total_s": round(t_sol, 3),
             "solve_and_far_field_wall_s": round(t_all, 3), "lockstep_iters_total": iters,
             "worst_relres": worst, "worst_energy_balance_by_level": bal}
+
+
+def gradients_l3(mu, torch, dev):
+    """Material gradients on the level-3 spheroid of axis ratio 1.5 (eps_r =
+    3 + 0.2i, mu_r = 1, k_a = 3, incidence +z, x polarised): the FP64
+    forward state (assembly, block-Jacobi, GMRES to 1e-12, far field) and
+    the 3 x 4 Jacobian of (C_ext, C_sca, C_abs) with respect to (Re, Im) of
+    eps_r and mu_r (four more assemblies, two tangent solves, one far-field
+    call), wall time with the device synchronised."""
+    import time as _t
+
+    xyz, tri6 = workloads.spheroid_p2(3, 1.0, 1.5)
+    m = mu.Mesh(xyz, tri6)
+    m.tangent_frame(0, out=False)
+    p = mu.Params(ka=3.0, eps_r=(3.0, 0.2), mu_r=(1.0, 0.0), q_regular=6, ssq_order=5, frame_rule=0)
+    inc = workloads.plane_wave((0.0, 0.0, 1.0), (1.0, 0.0, 0.0))
+    mu.grad.forward_state(m, p, inc)  # warm-up (tuning, rules)
+    torch.cuda.synchronize()
+    t0 = _t.perf_counter()
+    xs, state = mu.grad.forward_state(m, p, inc)
+    torch.cuda.synchronize()
+    t1 = _t.perf_counter()
+    J = mu.grad.material_jacobian(state)
+    torch.cuda.synchronize()
+    t2 = _t.perf_counter()
+    m.free()
+    return {"n_dof": int(m.N), "forward_ms": round((t1 - t0) * 1e3, 1),
+            "jacobian_ms": round((t2 - t1) * 1e3, 1),
+            "cross_sections": [float(v) for v in xs],
+            "jacobian_rows_ext_sca_abs_cols_re_eps_im_eps_re_mu_im_mu": J.round(6).tolist()}
 
 
 def lspr_sweep(mu, torch, dev):
