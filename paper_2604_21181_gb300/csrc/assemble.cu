@@ -668,6 +668,7 @@ __global__ void __launch_bounds__(TT, MINB) touching_kernel(
 
 struct TouchBody {
   int64_t n_touch, pair0, H, ldz;
+  const int32_t* order;  // the body's pairs of this launch: order[0 .. n_touch)
   const TouchPair* tp;
   const double* X;
   const int32_t* T;
@@ -680,16 +681,18 @@ struct TouchBody {
   double* near;
 };
 
-// Many bodies in one launch: CTA t takes pair t - pair0 of its body.
-template <int Q>
-__global__ void __launch_bounds__(TT) touching_batch_kernel(const TouchBody* __restrict__ bodies,
-                                                            const int64_t* __restrict__ first,
-                                                            int nb, int ns, int dtype,
-                                                            int use_tables) {
+// Many bodies in one launch: CTA t takes pair order[t - pair0] of its body
+// (one launch per pair class, as for one body).
+template <int Q, int MINB>
+__global__ void __launch_bounds__(TT, MINB) touching_batch_kernel(const TouchBody* __restrict__ bodies,
+                                                                  const int64_t* __restrict__ first,
+                                                                  int nb, int ns, int dtype,
+                                                                  int use_tables) {
   const int64_t t = blockIdx.x;
   const TouchBody& B = bodies[find_body(first, nb, t)];
-  touching_pair<Q>(t - B.pair0, B.tp, B.X, B.T, B.frame, B.qd, ns, B.K, B.ae_re, B.ae_im, B.am_re,
-                   B.am_im, dtype, B.Z, B.ldz, B.H, B.near, B.tp_slot, use_tables);
+  touching_pair<Q>(B.order[t - B.pair0], B.tp, B.X, B.T, B.frame, B.qd, ns, B.K, B.ae_re,
+                   B.ae_im, B.am_re, B.am_im, dtype, B.Z, B.ldz, B.H, B.near, B.tp_slot,
+                   use_tables);
 }
 
 // Eqs. (rhs_E), (rhs_H): one thread per (RHS, element, local node).
@@ -1047,22 +1050,27 @@ mueller_status regular_batch_t(int nb, mueller_mesh* const* meshes, const PhysCo
   }
 }
 
-template <int Q>
-mueller_status touching_batch_t(int nb, mueller_mesh* const* meshes, const PhysConsts* P, int ns,
-                                int dtype, void* const* Z, const int64_t* ldz,
-                                void* const* near, cudaStream_t s) {
-  std::vector<int> order = by_decreasing(nb, [&](int b) { return meshes[b]->n_touch; });
+template <int Q, int MINB>
+mueller_status touching_batch_class(int nb, mueller_mesh* const* meshes, const PhysConsts* P,
+                                    int ns, int dtype, void* const* Z, const int64_t* ldz,
+                                    void* const* near, bool vertex, cudaStream_t s) {
+  auto count = [&](const mueller_mesh* m) {
+    return vertex ? m->n_touch - m->n_touch_ce : m->n_touch_ce;
+  };
+  std::vector<int> order = by_decreasing(nb, [&](int b) { return count(meshes[b]); });
   std::vector<TouchBody> bodies;
   std::vector<int64_t> first;
   int64_t pairs = 0;
   for (int b : order) {
     const mueller_mesh* m = meshes[b];
-    if (m->n_touch == 0) continue;
+    const int64_t n = count(m);
+    if (n == 0) continue;
     TouchBody B;
-    B.n_touch = m->n_touch;
+    B.n_touch = n;
     B.pair0 = pairs;
     B.H = 2 * m->nn;
     B.ldz = ldz[b];
+    B.order = m->tp_order + (vertex ? m->n_touch_ce : 0);
     B.tp = m->tp;
     B.X = m->X;
     B.T = m->T;
@@ -1078,7 +1086,7 @@ mueller_status touching_batch_t(int nb, mueller_mesh* const* meshes, const PhysC
     B.near = near ? (double*)near[b] : nullptr;
     bodies.push_back(B);
     first.push_back(pairs);
-    pairs += m->n_touch;
+    pairs += n;
   }
   if (pairs == 0) return MUELLER_OK;
   void* buf = nullptr;
@@ -1086,14 +1094,26 @@ mueller_status touching_batch_t(int nb, mueller_mesh* const* meshes, const PhysC
   int64_t* d_first = nullptr;
   mueller_status st = upload_bodies(bodies, first, &buf, &d_bodies, &d_first, s);
   if (st) return st;
-  auto kern = touching_batch_kernel<Q>;
-  const int use_tables = ns <= MAX_TAB_NS ? 1 : 0;
+  auto kern = touching_batch_kernel<Q, MINB>;
+  const int use_tables = vertex && ns <= MAX_TAB_NS ? 1 : 0;
   const size_t tab_bytes = use_tables ? (size_t)2 * (ns * ns + ns * ns * ns) * GT * sizeof(double) : 0;
   MU_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tab_bytes));
   { Prof prof_("touching_batch_kernel<Q>", s); kern<<<(unsigned)pairs, TT, tab_bytes, s>>>(d_bodies, d_first, (int)bodies.size(), ns, dtype, use_tables); }
   MU_CHECK_LAUNCH("touching_batch_kernel");
   cudaFreeAsync(buf, s);
   return MUELLER_OK;
+}
+
+// the coincident and common-edge pairs of all bodies, then their
+// common-vertex pairs
+template <int Q>
+mueller_status touching_batch_t(int nb, mueller_mesh* const* meshes, const PhysConsts* P, int ns,
+                                int dtype, void* const* Z, const int64_t* ldz,
+                                void* const* near, cudaStream_t s) {
+  mueller_status st = touching_batch_class<Q, kTouchMinBlocksCE>(nb, meshes, P, ns, dtype, Z, ldz,
+                                                                 near, false, s);
+  if (st) return st;
+  return touching_batch_class<Q, 2>(nb, meshes, P, ns, dtype, Z, ldz, near, true, s);
 }
 
 }  // namespace
