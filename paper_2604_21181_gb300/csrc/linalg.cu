@@ -777,27 +777,32 @@ __global__ void gather_blocks_kernel(const void* __restrict__ Zv, int64_t ldz, i
 }
 
 // add the near blocks that fall inside MBJ block b (C64_NEAR64 operator)
-__global__ void gather_near_kernel(int64_t nn, const int32_t* __restrict__ rowptr,
-                                   const int32_t* __restrict__ col,
-                                   const double2* __restrict__ nearb, int64_t B, int64_t d,
-                                   const int32_t* __restrict__ sz, double2* __restrict__ out) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;  // test node
+__global__ void __launch_bounds__(256) gather_near_kernel(int64_t nn, const int32_t* __restrict__ rowptr,
+                                                          const int32_t* __restrict__ col,
+                                                          const double2* __restrict__ nearb, int64_t B,
+                                                          int64_t d, const int32_t* __restrict__ sz,
+                                                          double2* __restrict__ out) {
+  // one warp per test node; lanes over its near blocks' 16 entries.  Every
+  // (node pair, h, alpha, g, beta) is one entry of one block, so no two lanes
+  // write the same place.
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;  // test node
+  const int lane = threadIdx.x & 31;
   if (i >= nn) return;
-  for (int32_t q = rowptr[i]; q < rowptr[i + 1]; ++q) {
+  const int32_t q0 = rowptr[i], q1 = rowptr[i + 1];
+  for (int64_t e = (int64_t)q0 * 16 + lane; e < (int64_t)q1 * 16; e += 32) {
+    const int64_t q = e >> 4;
+    const int ha = (int)(e >> 2) & 3, gb = (int)e & 3;
     const int64_t j = col[q];
-    for (int ha = 0; ha < 4; ++ha)
-      for (int gb = 0; gb < 4; ++gb) {
-        const int h = ha >> 1, a = ha & 1, g = gb >> 1, be = gb & 1;
-        const int64_t ri = 2 * i + a, cj = 2 * j + be;  // per-current indices
-        const int64_t bi = ri / B, bj = cj / B;
-        if (bi != bj) continue;
-        const int s = sz[bi] / 2;
-        const int64_t li = (ri - bi * B) + (h ? s : 0), lj = (cj - bj * B) + (g ? s : 0);
-        const double2 v = nearb[(int64_t)q * 16 + ha * 4 + gb];
-        double2* t = out + bi * d * d + li * d + lj;
-        t->x += v.x;
-        t->y += v.y;
-      }
+    const int h = ha >> 1, a = ha & 1, g = gb >> 1, be = gb & 1;
+    const int64_t ri = 2 * i + a, cj = 2 * j + be;  // per-current indices
+    const int64_t bi = ri / B, bj = cj / B;
+    if (bi != bj) continue;
+    const int s = sz[bi] / 2;
+    const int64_t li = (ri - bi * B) + (h ? s : 0), lj = (cj - bj * B) + (g ? s : 0);
+    const double2 v = nearb[e];
+    double2* t = out + bi * d * d + li * d + lj;
+    t->x += v.x;
+    t->y += v.y;
   }
 }
 
@@ -1650,7 +1655,7 @@ mueller_status precond_build(const mueller_operator* op, int64_t block, void* P,
   } else {
     { Prof prof_("gather_blocks_kernel", s); gather_blocks_kernel<MUELLER_C64_NEAR64><<<g, 128, 0, s>>>(op->Z_dev, op->ldz, L.H, L.B, L.d, sz_dev, A); }
     MU_CHECK_LAUNCH("gather_blocks_kernel");
-    { Prof prof_("gather_near_kernel", s); gather_near_kernel<<<nblk(m->nn, 128), 128, 0, s>>>(m->nn, m->near_rowptr, m->near_col,
+    { Prof prof_("gather_near_kernel", s); gather_near_kernel<<<nblk(m->nn, 8), 256, 0, s>>>(m->nn, m->near_rowptr, m->near_col,
                                                         (const double2*)op->near_dev, L.B, L.d,
                                                         sz_dev, A); }
   }
