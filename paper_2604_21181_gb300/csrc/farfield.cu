@@ -117,9 +117,8 @@ __global__ void currents_kernel(int64_t nt, int Q, const double* __restrict__ qd
 
 // Block reduction of the 12 partial sums (N~ and L~, complex) and
 // F = (i k / 4 pi)[(N~ - r (r.N~)) - r x L~] into F_out[0..2] (thread 0).
-__device__ __forceinline__ void far_finish(double (*red)[256], const double* acc, double rx,
-                                           double ry, double rz, double ka,
-                                           double2* __restrict__ F_out) {
+// Block sums of the 12 partials (256 threads); the sums end in red[c][0].
+__device__ __forceinline__ void block_sum12(double (*red)[256], const double* acc) {
   for (int c = 0; c < 12; ++c) red[c][threadIdx.x] = acc[c];
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
@@ -127,6 +126,12 @@ __device__ __forceinline__ void far_finish(double (*red)[256], const double* acc
       for (int c = 0; c < 12; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + o];
     __syncthreads();
   }
+}
+
+__device__ __forceinline__ void far_finish(double (*red)[256], const double* acc, double rx,
+                                           double ry, double rz, double ka,
+                                           double2* __restrict__ F_out) {
+  block_sum12(red, acc);
   if (threadIdx.x == 0) {
     double Nr[3], Ni[3], Lr[3], Li[3];
     for (int a = 0; a < 3; ++a) {
@@ -202,6 +207,57 @@ __global__ void __launch_bounds__(256) far_kernel(int64_t np, const double* __re
 
 inline unsigned far_grid(int64_t nd_eval) { return (unsigned)((nd_eval + kFarDT - 1) / kFarDT); }
 
+// The forward direction (index 0 of each RHS's direction list) of every RHS:
+// one direction has too little work for one CTA, so CTA (g, s) sums the
+// partials of point chunk g of RHS s and far_fwd_finish_kernel adds the
+// chunks up and forms F.
+constexpr int kFwdChunks = 64;
+__global__ void __launch_bounds__(256) far_fwd_part_kernel(int64_t np, const double* __restrict__ qd,
+                                                           const double2* __restrict__ rec,
+                                                           const double* __restrict__ dirs,
+                                                           int64_t nd, double ka,
+                                                           double* __restrict__ part) {
+  __shared__ double2 tab[kCisN];
+  __shared__ double red[12][256];
+  cis_fill(tab);
+  __syncthreads();
+  const int s = blockIdx.y, g = blockIdx.x, G = gridDim.x;
+  const double* dd = dirs + (int64_t)s * nd * 3;
+  const double rk0 = -ka * dd[0], rk1 = -ka * dd[1], rk2 = -ka * dd[2];
+  const int64_t chunk = (np + G - 1) / G, t0 = (int64_t)g * chunk;
+  const int64_t t1 = t0 + chunk < np ? t0 + chunk : np;
+  double acc[12];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) acc[c] = 0.0;
+  for (int64_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+    const double* q = qd + t * QD_STRIDE;
+    const double2 e = cis_tab(fma(rk0, q[0], fma(rk1, q[1], rk2 * q[2])), tab);
+    const double2* o = rec + ((int64_t)s * np + t) * 6;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const double2 v = o[c];
+      acc[2 * c] = fma(v.x, e.x, fma(-v.y, e.y, acc[2 * c]));
+      acc[2 * c + 1] = fma(v.x, e.y, fma(v.y, e.x, acc[2 * c + 1]));
+    }
+  }
+  block_sum12(red, acc);
+  if (threadIdx.x < 12) part[((int64_t)s * G + g) * 12 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void __launch_bounds__(256) far_fwd_finish_kernel(const double* __restrict__ part, int G,
+                                                             const double* __restrict__ dirs,
+                                                             int64_t nd, double ka,
+                                                             double2* __restrict__ F) {
+  __shared__ double red[12][256];
+  const int s = blockIdx.x;
+  double acc[12];
+#pragma unroll
+  for (int c = 0; c < 12; ++c)
+    acc[c] = (int)threadIdx.x < G ? part[((int64_t)s * G + threadIdx.x) * 12 + c] : 0.0;
+  const double* dd = dirs + (int64_t)s * nd * 3;
+  far_finish(red, acc, dd[0], dd[1], dd[2], ka, F + (int64_t)s * nd * 3);
+}
+
 // Antipodal pair p of the sphere rule (n_phi even): direction k2 = -k1, the
 // ring n_theta-1-it against ring it, or for odd n_theta the middle ring
 // against itself turned by pi.
@@ -225,7 +281,7 @@ __host__ __device__ __forceinline__ void sphere_pair(int64_t p, int n_theta, int
 // point at the sphere block (index k).
 constexpr int kFarDP = 2;
 template <int DP>
-__global__ void __launch_bounds__(256) far_pair_kernel(int64_t np, const double* __restrict__ qd,
+__global__ void __launch_bounds__(256, 2) far_pair_kernel(int64_t np, const double* __restrict__ qd,
                                                        const double2* __restrict__ rec,
                                                        const double* __restrict__ dirs,
                                                        int n_theta, int n_phi, double ka,
@@ -420,19 +476,18 @@ std::vector<double> far_dirs(int r, const double* inc, int n_theta, int n_phi,
   return hd;
 }
 
-// F of one RHS at all its directions: forward and user directions by
-// far_kernel, the sphere rule by antipodal pairs (far_pair_kernel) when
-// n_phi is even.
+// F of one RHS at its sphere-rule and user directions (the forward direction
+// is far_fwd's): the sphere rule by antipodal pairs (far_pair_kernel) when
+// n_phi is even, else with the user directions by far_kernel.
 mueller_status far_one_rhs(int64_t np, const double* qd, const double2* rec, const double* dirs,
                            int64_t nd, int n_theta, int n_phi, int64_t ndir, double ka,
                            double2* F, cudaStream_t s) {
   const int64_t nsph = (int64_t)n_theta * n_phi;
   if (n_phi % 2 != 0) {
-    { Prof prof_("far_kernel", s); far_kernel<kFarDT><<<far_grid(nd), 256, 0, s>>>(np, qd, rec, dirs, nd, ka, F); }
+    { Prof prof_("far_kernel", s); far_kernel<kFarDT><<<far_grid(nd - 1), 256, 0, s>>>(np, qd, rec, dirs + 3, nd - 1, ka, F + 3); }
     MU_CHECK_LAUNCH("far_kernel");
     return MUELLER_OK;
   }
-  { Prof prof_("far_kernel", s); far_kernel<kFarDT><<<far_grid(1), 256, 0, s>>>(np, qd, rec, dirs, 1, ka, F); }
   const int64_t npairs = nsph / 2;
   { Prof prof_("far_pair_kernel", s); far_pair_kernel<kFarDP><<<(unsigned)((npairs + kFarDP - 1) / kFarDP), 256, 0, s>>>(
       np, qd, rec, dirs + 3, n_theta, n_phi, ka, F + 3); }
@@ -440,6 +495,15 @@ mueller_status far_one_rhs(int64_t np, const double* qd, const double2* rec, con
     { Prof prof_("far_kernel", s); far_kernel<kFarDT><<<far_grid(ndir), 256, 0, s>>>(np, qd, rec, dirs + 3 * (1 + nsph), ndir, ka,
                                                                                      F + 3 * (1 + nsph)); }
   MU_CHECK_LAUNCH("far_kernel");
+  return MUELLER_OK;
+}
+
+// the forward direction of all r right-hand sides (part: r x kFwdChunks x 12)
+mueller_status far_fwd(int64_t np, const double* qd, const double2* rec, const double* dirs,
+                       int64_t nd, int r, double ka, double* part, double2* F, cudaStream_t s) {
+  { Prof prof_("far_fwd_part_kernel", s); far_fwd_part_kernel<<<dim3(kFwdChunks, (unsigned)r), 256, 0, s>>>(np, qd, rec, dirs, nd, ka, part); }
+  { Prof prof_("far_fwd_finish_kernel", s); far_fwd_finish_kernel<<<(unsigned)r, 256, 0, s>>>(part, kFwdChunks, dirs, nd, ka, F); }
+  MU_CHECK_LAUNCH("far_fwd");
   return MUELLER_OK;
 }
 
@@ -480,6 +544,7 @@ mueller_status far_field(mueller_mesh* m, const PhysConsts& P, int Q, const void
   const size_t o_phi = al(sizeof(phi));
   const size_t o_cab = al((size_t)r * nblk_pts * 8);
   const size_t o_xs = al((size_t)r * 3 * 8);
+  const size_t o_part = al((size_t)r * kFwdChunks * 12 * 8);
   char* buf = nullptr;
   MU_CUDA(cudaMallocAsync((void**)&buf, off, s));
   double2* rec = (double2*)(buf + o_rec);
@@ -499,15 +564,11 @@ mueller_status far_field(mueller_mesh* m, const PhysConsts& P, int Q, const void
   if (!st) {
     { Prof prof_("currents_kernel", s); currents_kernel<<<dim3(nblk_pts, r), 256, 0, s>>>(m->nt, Q, m->qd64, m->T, (const double2*)X, r,
                                                        N, dphi, rec, cab); }
-    if (r == 1) {
+    st = far_fwd(np, m->qd64, rec, ddirs, nd, r, P.ka, (double*)(buf + o_part), Fall, s);
+    if (!st && r == 1) {
       st = far_one_rhs(np, m->qd64, rec, ddirs, nd, n_theta, n_phi, ndir, P.ka, Fall, s);
-    } else {
-      // forward direction (one per right-hand side), then the shared
-      // directions for 4 right-hand sides per CTA
-      for (int sidx = 0; sidx < r; ++sidx)
-        { Prof prof_("far_kernel", s); far_kernel<kFarDT><<<far_grid(1), 256, 0, s>>>(np, m->qd64, rec + (size_t)sidx * np * 6,
-                                                         ddirs + (size_t)sidx * nd * 3, 1, P.ka,
-                                                         Fall + (size_t)sidx * nd * 3); }
+    } else if (!st) {
+      // the shared directions, 4 right-hand sides per CTA
       { Prof prof_("far_multi_kernel", s); far_multi_kernel<4><<<dim3((unsigned)(nd - 1), (unsigned)((r + 3) / 4)), 256, 0, s>>>(
           np, m->qd64, rec, r, ddirs, nd, P.ka, Fall); }
     }
@@ -596,6 +657,7 @@ mueller_status far_field_noalloc(mueller_mesh* m, const PhysConsts& P, int Q, co
   const size_t o_phi = al(sizeof(double) * MAX_Q * 6);
   const size_t o_cab = al((size_t)r * nblk_pts * 8);
   const size_t o_xs = al((size_t)r * 3 * 8);
+  const size_t o_part = al((size_t)r * kFwdChunks * 12 * 8);
   if (off > kFarFieldScratchBytes) {
     set_error("far field needs " + std::to_string(off) + " bytes of scratch, more than the " +
               std::to_string(kFarFieldScratchBytes) +
@@ -630,6 +692,8 @@ mueller_status far_field_noalloc(mueller_mesh* m, const PhysConsts& P, int Q, co
   if (e == cudaSuccess) e = cudaMemcpyAsync(dphi, phi, sizeof(double) * Q * 6, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_fail(e, "far-field (allocation-free) setup");
   { Prof prof_("currents_kernel", s); currents_kernel<<<dim3(nblk_pts, r), 256, 0, s>>>(m->nt, Q, m->qd64, m->T, (const double2*)X, r, N, dphi, rec, cab); }
+  st = far_fwd(np, m->qd64, rec, ddirs, nd, r, P.ka, (double*)(buf + o_part), Fall, s);
+  if (st) return st;
   for (int sidx = 0; sidx < r; ++sidx) {
     st = far_one_rhs(np, m->qd64, rec + (size_t)sidx * np * 6, ddirs + (size_t)sidx * nd * 3, nd,
                      n_theta, n_phi, ndir, P.ka, Fall + (size_t)sidx * nd * 3, s);
