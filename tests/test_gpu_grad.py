@@ -3,7 +3,8 @@ FP64 path (grad.material_jacobian):
 
 * against the oracle's gradient (central differences of its own FP64
   pipeline) on the level-1 spheroid of axis ratio 1.5, eps_r = 3 + 0.2i,
-  k_a = 3: within 1e-5 of each column's largest entry (the two assemblies
+  k_a = 3, and a magnetic case (mu_r = 1.5 + 0.1i): within 1e-5 of each
+  column's largest entry (the two assemblies
   agree to 1e-11, both solves are direct or converged to 1e-12, and the
   oracle's central differences carry an O(h^2) error of about 1e-8);
 * against central differences of the GPU's own cross sections (full solves
@@ -43,12 +44,14 @@ def _colmax_err(A, B):
     return max(np.abs(A[:, k] - B[:, k]).max() / np.abs(B[:, k]).max() for k in range(A.shape[1]))
 
 
-def test_material_jacobian_matches_oracle_gradient():
+@pytest.mark.parametrize("phys", [PHYS, dict(ka=2.0, eps_r=(2.0, 0.1), mu_r=(1.5, 0.1))])
+def test_material_jacobian_matches_oracle_gradient(phys):
     xyz, tri6, m, p, inc = _setup(1)
+    p = dataclasses.replace(p, ka=phys["ka"], eps_r=phys["eps_r"], mu_r=phys["mu_r"])
     xs, state = mu.grad.forward_state(m, p, inc)
     J = mu.grad.material_jacobian(state)
     om = oracle.Mesh(xyz, tri6, frame_rule=0)
-    pw = dict(PHYS, q_regular=6, ssq_order=4)
+    pw = dict(phys, q_regular=6, ssq_order=4)
     xso = oracle.cross_sections(om, pw, inc)[0]
     np.testing.assert_allclose(xs, xso, rtol=1e-10)
     Jo = oracle.cross_section_gradient(om, pw, inc)
