@@ -344,7 +344,8 @@ __global__ void __launch_bounds__(256, 2) far_pair_kernel(int64_t np, const doub
 // The directions shared by all right-hand sides (sphere rule, user list:
 // indices 1 .. nd-1) for RS right-hand sides per CTA: each phase
 // exp(-i k r.y) is computed once and applied to the RS current records.
-// Per right-hand side the sums run in the same order as in far_kernel.
+// Per right-hand side the sums run in the same order as in far_kernel (a
+// single right-hand side uses far_pair_kernel, which agrees to rounding).
 template <int RS>
 __global__ void __launch_bounds__(256) far_multi_kernel(int64_t np, const double* __restrict__ qd,
                                                         const double2* __restrict__ rec, int r,
