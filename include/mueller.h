@@ -228,6 +228,23 @@ mueller_status mueller_assemble_batch(int32_t n_bodies, mueller_mesh* const* mes
                                       void* const* near_dev, void* const* B_dev,
                                       const double* const* inc, const int32_t* r, void* stream);
 
+/*
+ * mueller_dz_matvec -- Y = (dZ/dtheta) X for theta = eps_r (which = 1) or
+ * mu_r (which = 2): the complex derivative of the operator of Eq.
+ * global_system (Z is holomorphic in eps_r and mu_r through
+ * k_i = k_a sqrt(eps_r mu_r) and the explicit eps_r, mu_r factors of the
+ * kernels of Eqs. kappa_S, kappa2_S and of the mass terms), applied to one
+ * vector without forming dZ: every element pair's block of dZ is recomputed
+ * from the derivatives of the radial functions (FP64) and multiplied into Y.
+ * Used for the gradients of the cross sections with respect to the material.
+ *   X_dev    complex128, length N = 4 * n_nodes, read only.
+ *   Y_dev    complex128, length N, overwritten.
+ * Needs mueller_tangent_frame with params->frame_rule (else STATE).
+ * Errors: INVALID_ARG (NULL, which not 1 or 2, bad params), STATE, CUDA.
+ */
+mueller_status mueller_dz_matvec(mueller_mesh* mesh, const mueller_params* params, int32_t which,
+                                 const void* X_dev, void* Y_dev, void* stream);
+
 /* bytes of the complex128 near-part buffer of a loaded mesh */
 size_t mueller_near_bytes(const mueller_mesh* mesh);
 

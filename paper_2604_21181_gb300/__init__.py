@@ -26,6 +26,7 @@ from .api import (  # noqa: F401
     SolverOpts,
     assemble,
     assemble_batch,
+    dz_matvec,
     far_field,
     launch_count,
     load_library,

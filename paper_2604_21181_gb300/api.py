@@ -70,7 +70,8 @@ class COperator(C.Structure):
 EXPORTS = [
     "mueller_version", "mueller_last_error", "mueller_status_string", "mueller_mesh_load",
     "mueller_mesh_free", "mueller_mesh_get_info", "mueller_mesh_perm", "mueller_tangent_frame",
-    "mueller_assemble", "mueller_near_bytes", "mueller_precond_build", "mueller_precond_bytes",
+    "mueller_assemble", "mueller_dz_matvec", "mueller_near_bytes", "mueller_precond_build",
+    "mueller_precond_bytes",
     "mueller_solve", "mueller_solve_workspace_bytes", "mueller_matvec",
     "mueller_matvec_workspace_bytes", "mueller_far_field", "mueller_sync",
     "mueller_profile_enable", "mueller_profile_reset", "mueller_launch_count",
@@ -103,6 +104,7 @@ def load_library(build_if_missing: bool = True):
         "mueller_mesh_perm": (C.c_int, [vp, ip, ip]),
         "mueller_tangent_frame": (C.c_int, [vp, i32, vp, vp]),
         "mueller_assemble": (C.c_int, [vp, C.POINTER(CParams), i32, vp, i64, vp, vp, dp, i32, vp]),
+        "mueller_dz_matvec": (C.c_int, [vp, C.POINTER(CParams), i32, vp, vp, vp]),
         "mueller_near_bytes": (C.c_size_t, [vp]),
         "mueller_precond_build": (C.c_int, [C.POINTER(COperator), i64, vp, vp]),
         "mueller_precond_bytes": (C.c_size_t, [i64, i64]),
@@ -279,6 +281,18 @@ def assemble(mesh: Mesh, params: Params, dtype: int = MUELLER_C128, inc=None, Z=
                                       _ptr(B), incp, r, _stream(stream)))
     Z._mueller_k1_mirrored = Z._version  # Z11 = -Z00 as written; see Operator
     return Z, near, B
+
+
+def dz_matvec(mesh: Mesh, params: Params, which: int, X, stream=None):
+    """mueller_dz_matvec: (dZ/d eps_r) X for which = 1, (dZ/d mu_r) X for 2
+    (complex derivatives; X, result complex128 of length N)."""
+    torch = _torch()
+    X = _dev(X, torch.complex128, "X")
+    Y = torch.empty_like(X)
+    p = params.c()
+    _check(mesh._lib.mueller_dz_matvec(mesh.h, C.byref(p), int(which), _ptr(X), _ptr(Y),
+                                       _stream(stream)))
+    return Y
 
 
 def assemble_batch(meshes, params, dtype: int = MUELLER_C64_NEAR64, incs=None, stream=None):

@@ -125,11 +125,17 @@ struct RegCfg {
 };
 
 // One CTA tile (test elements bx*WARPS.., trial elements by*TY..) of one body.
-template <class R, int Q, int W, int TYT>
+// WHICH = 0 adds the blocks into Z; WHICH = 1, 2 forms the blocks of dZ/deps_r,
+// dZ/dmu_r instead and adds their product with x into y (complex128, length
+// 2H; the blocks are not stored): per warp the 24 rows of its test element
+// are summed in shared memory, then added to y once per tile.
+template <class R, int Q, int W, int TYT, int WHICH = 0>
 __device__ __forceinline__ void regular_tile(int64_t bx, int64_t by, int64_t nt,
                                              const R* __restrict__ qd,
                                              const int32_t* __restrict__ T, const KConst<R>& K,
-                                             R* __restrict__ Z, int64_t ldz, int64_t H) {
+                                             R* __restrict__ Z, int64_t ldz, int64_t H,
+                                             const double2* __restrict__ xd = nullptr,
+                                             double2* __restrict__ yd = nullptr) {
   using C = RegCfg<R, Q, W, TYT>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* sY = reinterpret_cast<R*>(smem_raw);               // TY*Q*QD_STRIDE
@@ -152,6 +158,13 @@ __device__ __forceinline__ void regular_tile(int64_t bx, int64_t by, int64_t nt,
   for (int k = 0; k < 6; ++k) tx[k] = T[6 * ex + k];
   constexpr int NB = C::NB;
   R* Kt = sK + (size_t)warp * NB * Q * Q * 24;  // [b][p][q][c] complex (re, im)
+  double* yacc = nullptr;  // [24][2]: rows 2 tx[i] + a (0..11), then H + 2 tx[i] + a
+  if constexpr (WHICH != 0) {
+    __shared__ double s_yacc[W][48];
+    yacc = s_yacc[warp];
+    for (int k = lane; k < 48; k += 32) yacc[k] = 0.0;
+    __syncwarp();
+  }
   int* myList = reinterpret_cast<int*>(sK + (size_t)C::WARPS * NB * Q * Q * 24) + warp * C::TY;
   const R wre = R(0), wim = R(1) / K.ka;   // i / omega
   // the trial elements of the tile that do not touch ex, compacted
@@ -178,7 +191,7 @@ __device__ __forceinline__ void regular_tile(int64_t bx, int64_t by, int64_t nt,
       const int p = pq / Q, q = pq % Q;
       const R* Y = sY + (size_t)myList[b0 + b] * Q * QD_STRIDE;
       cx<R> kv[12];
-      point_pair<R>(K, myX + p * QD_STRIDE, Y + q * QD_STRIDE, false, kv);
+      point_pair<R, WHICH>(K, myX + p * QD_STRIDE, Y + q * QD_STRIDE, false, kv);
       R* o = Kt + (size_t)it * 24;
 #pragma unroll
       for (int c = 0; c < 12; ++c) {
@@ -235,16 +248,41 @@ __device__ __forceinline__ void regular_tile(int64_t bx, int64_t by, int64_t nt,
           are = fma(ph, vre[p], are);
           aim = fma(ph, vim[p], aim);
         }
-        const int64_t row = 2 * (int64_t)tx[i] + a + (op == 2 ? H : 0);
-        if (op == 0) {  // (i/omega) K1
-          const R zr = wre * are - wim * aim, zi = wre * aim + wim * are;
-          zadd(Z, row * ldz + col, zr, zi);
+        if constexpr (WHICH == 0) {
+          const int64_t row = 2 * (int64_t)tx[i] + a + (op == 2 ? H : 0);
+          if (op == 0) {  // (i/omega) K1
+            const R zr = wre * are - wim * aim, zi = wre * aim + wim * are;
+            zadd(Z, row * ldz + col, zr, zi);
+          } else {
+            zadd(Z, row * ldz + col, are, aim);
+          }
         } else {
-          zadd(Z, row * ldz + col, are, aim);
+          double vr = are, vi = aim;
+          if (op == 0) {
+            vr = -(double)wim * aim;
+            vi = (double)wim * are;
+          }
+          const double2 xv = xd[col];
+          const int lr = (op == 2 ? 12 : 0) + 2 * i + a;
+          atomicAdd(&yacc[2 * lr], vr * xv.x - vi * xv.y);
+          atomicAdd(&yacc[2 * lr + 1], vr * xv.y + vi * xv.x);
+          if (op == 0) {  // Z11 = -Z00: the bottom rows against the bottom half of x
+            const double2 xb = xd[col + H];
+            atomicAdd(&yacc[2 * (12 + 2 * i + a)], -(vr * xb.x - vi * xb.y));
+            atomicAdd(&yacc[2 * (12 + 2 * i + a) + 1], -(vr * xb.y + vi * xb.x));
+          }
         }
       }
     }
     __syncwarp();
+  }
+  if constexpr (WHICH != 0) {
+    for (int k = lane; k < 24; k += 32) {
+      const int h = k / 12, ia = k % 12;
+      const int64_t row = (h ? H : 0) + 2 * (int64_t)tx[ia >> 1] + (ia & 1);
+      atomicAdd(&yd[row].x, yacc[2 * k]);
+      atomicAdd(&yd[row].y, yacc[2 * k + 1]);
+    }
   }
 }
 
@@ -253,6 +291,16 @@ __global__ void __launch_bounds__(32 * W) regular_kernel(int64_t nt, const R* __
                                                          const int32_t* __restrict__ T, KConst<R> K,
                                                          R* __restrict__ Z, int64_t ldz, int64_t H) {
   regular_tile<R, Q, W, TYT>(blockIdx.x, blockIdx.y, nt, qd, T, K, Z, ldz, H);
+}
+
+// y += (dZ/dtheta)_regular x (theta = eps_r for WHICH 1, mu_r for 2), FP64
+template <int Q, int W, int TYT, int WHICH>
+__global__ void __launch_bounds__(32 * W) regular_deriv_kernel(int64_t nt, const double* __restrict__ qd,
+                                                               const int32_t* __restrict__ T,
+                                                               KConst<double> K,
+                                                               const double2* __restrict__ x,
+                                                               double2* __restrict__ y, int64_t H) {
+  regular_tile<double, Q, W, TYT, WHICH>(blockIdx.x, blockIdx.y, nt, qd, T, K, nullptr, 0, H, x, y);
 }
 
 // Many bodies in one launch: CTA t takes tile t - tile0 of the body whose
@@ -404,13 +452,17 @@ __device__ __forceinline__ void ssq_group(int cls, int reg, int a, int b, int c,
 }
 
 // One touching element pair (index pid of the body's pair list) per CTA.
-template <int Q>
+// WHICH = 1, 2: the pair's block of dZ/deps_r, dZ/dmu_r times x added into y
+// (the Sauter-Schwab integrals do not depend on the material; only their
+// constants, the remainder and the mass coefficient do).
+template <int Q, int WHICH = 0>
 __device__ __forceinline__ void touching_pair(
     int64_t pid, const TouchPair* __restrict__ tp, const double* __restrict__ X,
     const int32_t* __restrict__ T, const double* __restrict__ frame,
     const double* __restrict__ qd, int ns, const KConst<double>& K, double ae_re, double ae_im,
     double am_re, double am_im, int dtype, void* __restrict__ Zv, int64_t ldz, int64_t H,
-    double* __restrict__ near, const int32_t* __restrict__ tp_slot, int use_tables) {
+    double* __restrict__ near, const int32_t* __restrict__ tp_slot, int use_tables,
+    const double2* __restrict__ xd = nullptr, double2* __restrict__ yd = nullptr) {
   __shared__ d3 sXn[2][6], sT1[2][6], sT2[2][6];
   // common-vertex pairs: geometry records of the two sides (dynamic)
   extern __shared__ double sTab[];
@@ -553,7 +605,7 @@ __device__ __forceinline__ void touching_pair(
       qy_[c] = QY[q * QD_STRIDE + c];
     }
     cx<double> kv[12];
-    point_pair<double>(K, px_, qy_, true, kv);
+    point_pair<double, WHICH>(K, px_, qy_, true, kv);
     for (int c = 0; c < 12; ++c) {
       sK[(size_t)pq * 24 + 2 * c] = kv[c].re;
       sK[(size_t)pq * 24 + 2 * c + 1] = kv[c].im;
@@ -582,12 +634,27 @@ __device__ __forceinline__ void touching_pair(
   }
   __syncthreads();
   // ---- L = remainder + singular (+ mass on coincident pairs), scatter
-  const double C1re = (K.ka * K.ka - (K.ki_re * K.ki_re - K.ki_im * K.ki_im)) * 0.0397887357729738339422209408431285943;
-  const double C1im = -(2.0 * K.ki_re * K.ki_im) * 0.0397887357729738339422209408431285943;  // /(8 pi)
-  const double Cere = -(1.0 - K.eps_re) * 0.0795774715459476678844418816862571885;
-  const double Ceim = K.eps_im * 0.0795774715459476678844418816862571885;
-  const double Cmre = -(1.0 - K.mu_re) * 0.0795774715459476678844418816862571885;
-  const double Cmim = K.mu_im * 0.0795774715459476678844418816862571885;
+  double C1re = (K.ka * K.ka - (K.ki_re * K.ki_re - K.ki_im * K.ki_im)) * 0.0397887357729738339422209408431285943;
+  double C1im = -(2.0 * K.ki_re * K.ki_im) * 0.0397887357729738339422209408431285943;  // /(8 pi)
+  double Cere = -(1.0 - K.eps_re) * 0.0795774715459476678844418816862571885;
+  double Ceim = K.eps_im * 0.0795774715459476678844418816862571885;
+  double Cmre = -(1.0 - K.mu_re) * 0.0795774715459476678844418816862571885;
+  double Cmim = K.mu_im * 0.0795774715459476678844418816862571885;
+  if constexpr (WHICH != 0) {
+    // d/dtheta: C1 -> -ki dki / (4 pi), dki = ki / (2 theta); C_chi -> 1/(4 pi)
+    // for chi = theta, else 0; the mass coefficient a_chi -> 1/2, else 0
+    const cx<double> ki = cmk(K.ki_re, K.ki_im);
+    const cx<double> th = WHICH == 1 ? cmk(K.eps_re, K.eps_im) : cmk(K.mu_re, K.mu_im);
+    const cx<double> kdk = cmul(ki, crs(0.5, cdivc(ki, th)));
+    C1re = -kdk.re * 0.0795774715459476678844418816862571885;
+    C1im = -kdk.im * 0.0795774715459476678844418816862571885;
+    Cere = WHICH == 1 ? 0.0795774715459476678844418816862571885 : 0.0;
+    Cmre = WHICH == 2 ? 0.0795774715459476678844418816862571885 : 0.0;
+    Ceim = Cmim = 0.0;
+    ae_re = WHICH == 1 ? 0.5 : 0.0;
+    am_re = WHICH == 2 ? 0.5 : 0.0;
+    ae_im = am_im = 0.0;
+  }
   const double wim = 1.0 / K.ka;  // i / omega
   for (int jc = tid; jc < 6 * 12; jc += TT) {
     const int j = jc / 12, c = jc % 12;
@@ -628,7 +695,18 @@ __device__ __forceinline__ void touching_pair(
         are = -wim * aim;
         aim = wim * t;
       }
-      if (dtype == MUELLER_C128) {
+      if constexpr (WHICH != 0) {
+        const int64_t row = 2 * (int64_t)T[6 * P.ex + i] + a + (op == 2 ? H : 0);
+        const int64_t col = 2 * (int64_t)T[6 * P.ey + j] + b + (op == 1 ? H : 0);
+        const double2 xv = xd[col];
+        atomicAdd(&yd[row].x, are * xv.x - aim * xv.y);
+        atomicAdd(&yd[row].y, are * xv.y + aim * xv.x);
+        if (op == 0) {  // Z11 = -Z00
+          const double2 xb = xd[col + H];
+          atomicAdd(&yd[row + H].x, -(are * xb.x - aim * xb.y));
+          atomicAdd(&yd[row + H].y, -(are * xb.y + aim * xb.x));
+        }
+      } else if (dtype == MUELLER_C128) {
         double* Z = (double*)Zv;
         const int64_t row = 2 * (int64_t)T[6 * P.ex + i] + a + (op == 2 ? H : 0);
         const int64_t col = 2 * (int64_t)T[6 * P.ey + j] + b + (op == 1 ? H : 0);
@@ -693,6 +771,18 @@ __global__ void __launch_bounds__(TT, MINB) touching_batch_kernel(const TouchBod
   touching_pair<Q>(B.order[t - B.pair0], B.tp, B.X, B.T, B.frame, B.qd, ns, B.K, B.ae_re,
                    B.ae_im, B.am_re, B.am_im, dtype, B.Z, B.ldz, B.H, B.near, B.tp_slot,
                    use_tables);
+}
+
+// y += (dZ/dtheta)_touching x over all touching pairs (CTA per pair)
+template <int Q, int WHICH>
+__global__ void __launch_bounds__(TT, 2) touching_deriv_kernel(
+    int64_t n_touch, const TouchPair* __restrict__ tp, const double* __restrict__ X,
+    const int32_t* __restrict__ T, const double* __restrict__ frame,
+    const double* __restrict__ qd, int ns, KConst<double> K, int64_t H, int use_tables,
+    const double2* __restrict__ x, double2* __restrict__ y) {
+  if ((int64_t)blockIdx.x >= n_touch) return;
+  touching_pair<Q, WHICH>(blockIdx.x, tp, X, T, frame, qd, ns, K, 0.0, 0.0, 0.0, 0.0,
+                          MUELLER_C128, nullptr, 0, H, nullptr, nullptr, use_tables, x, y);
 }
 
 // Eqs. (rhs_E), (rhs_H): one thread per (RHS, element, local node).
@@ -1160,6 +1250,45 @@ mueller_status launch_mass_rhs(mueller_mesh* m, const PhysConsts& P, int Q, int 
                                                          P.ka, 4 * m->nn, (double*)B); }
   MU_CHECK_LAUNCH("rhs_kernel");
   return MUELLER_OK;
+}
+
+namespace {
+
+template <int Q, int WHICH>
+mueller_status dz_matvec_t(mueller_mesh* m, const PhysConsts& P, int ns, const double2* x,
+                           double2* y, cudaStream_t s) {
+  constexpr int W = 4, TYT = 32;
+  using C = RegCfg<double, Q, W, TYT>;
+  const KConst<double> K = kconst<double>(P);
+  const int64_t H = 2 * m->nn;
+  auto kr = regular_deriv_kernel<Q, W, TYT, WHICH>;
+  MU_CUDA(cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
+  dim3 grid((unsigned)((m->nt + W - 1) / W), (unsigned)((m->nt + TYT - 1) / TYT));
+  { Prof prof_("regular_deriv_kernel", s); kr<<<grid, 32 * W, C::smem, s>>>(m->nt, m->qd64, m->T, K, x, y, H); }
+  MU_CHECK_LAUNCH("regular_deriv_kernel");
+  if (m->n_touch > 0) {
+    auto kt = touching_deriv_kernel<Q, WHICH>;
+    const int use_tables = ns <= MAX_TAB_NS ? 1 : 0;
+    const size_t tab_bytes = use_tables ? (size_t)2 * (ns * ns + ns * ns * ns) * GT * sizeof(double) : 0;
+    MU_CUDA(cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tab_bytes));
+    { Prof prof_("touching_deriv_kernel", s); kt<<<(unsigned)m->n_touch, TT, tab_bytes, s>>>(m->n_touch, m->tp, m->X, m->T, m->frame, m->qd64,
+                                                                   ns, K, H, use_tables, x, y); }
+    MU_CHECK_LAUNCH("touching_deriv_kernel");
+  }
+  return MUELLER_OK;
+}
+
+}  // namespace
+
+// y = (dZ/dtheta) x, theta = eps_r (which 1) or mu_r (which 2), complex128
+mueller_status launch_dz_matvec(mueller_mesh* m, const PhysConsts& P, int Q, int ns, int which,
+                                const void* x, void* y, cudaStream_t s) {
+  MU_CUDA(cudaMemsetAsync(y, 0, (size_t)4 * m->nn * sizeof(double2), s));
+  const double2* xd = (const double2*)x;
+  double2* yd = (double2*)y;
+  if (Q == 6)
+    return which == 1 ? dz_matvec_t<6, 1>(m, P, ns, xd, yd, s) : dz_matvec_t<6, 2>(m, P, ns, xd, yd, s);
+  return which == 1 ? dz_matvec_t<12, 1>(m, P, ns, xd, yd, s) : dz_matvec_t<12, 2>(m, P, ns, xd, yd, s);
 }
 
 mueller_status launch_mirror_k1(int64_t N, int dtype, void* Z, int64_t ldz, cudaStream_t s) {

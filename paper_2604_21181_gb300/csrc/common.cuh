@@ -132,6 +132,8 @@ mueller_status launch_mass_rhs(mueller_mesh* m, const PhysConsts& P, int Q, int 
                                int64_t ldz, void* near, void* B, const double* inc_dev, int r,
                                cudaStream_t s);
 mueller_status launch_mirror_k1(int64_t N, int dtype, void* Z, int64_t ldz, cudaStream_t s);
+mueller_status launch_dz_matvec(mueller_mesh* m, const PhysConsts& P, int Q, int ns, int which,
+                                const void* x, void* y, cudaStream_t s);
 mueller_status launch_assemble_batch(int nb, mueller_mesh* const* meshes, const PhysConsts* P,
                                      int Q, int ns, int dtype, void* const* Z,
                                      const int64_t* ldz, void* const* near, cudaStream_t s);

@@ -528,6 +528,24 @@ mueller_status mueller_assemble(mueller_mesh* m, const mueller_params* p, int32_
   return st;
 }
 
+mueller_status mueller_dz_matvec(mueller_mesh* m, const mueller_params* p, int32_t which,
+                                 const void* X, void* Y, void* stream) {
+  if (!m || !X || !Y) return fail(MUELLER_ERR_INVALID_ARG, "NULL argument");
+  mueller_status st = check_params(p);
+  if (st) return st;
+  if (which != 1 && which != 2) return fail(MUELLER_ERR_INVALID_ARG, "which must be 1 (eps_r) or 2 (mu_r)");
+  if (p->frame_rule != m->frame_rule || !m->has_frame)
+    return fail(MUELLER_ERR_STATE, "call mueller_tangent_frame with params->frame_rule first");
+  cudaStream_t s = (cudaStream_t)stream;
+  st = ensure_geometry(m, p->q_regular, s);
+  if (st) return st;
+  TriangleRule rule;
+  triangle_rule(p->q_regular, rule);
+  st = upload_rules(rule, p->ssq_order);
+  if (st) return st;
+  return launch_dz_matvec(m, make_phys(p), p->q_regular, p->ssq_order, which, X, Y, s);
+}
+
 mueller_status mueller_assemble_batch(int32_t n_bodies, mueller_mesh* const* meshes,
                                       const mueller_params* params, int32_t dtype,
                                       void* const* Z, const int64_t* ldz, void* const* near,

@@ -102,6 +102,52 @@ __host__ __device__ __forceinline__ void qfuncs(cx<R> z, cx<R>& q1, cx<R>& q2, c
   }
 }
 
+// The derivatives Q1'(z), Q2'(z), Q3'(z) and Q3(z) itself, split the same
+// way: power series (term by term: sum c_m z^(m-1)/(m-1)!) for |z| < 1, else
+// the closed forms Q1' = (z^2 + z) e^z - z, Q2' = (z^2 - z) e^z + z,
+// Q3' = z e^z (derivatives of the closed forms above).
+template <class R>
+__host__ __device__ __forceinline__ void qfuncs_d(cx<R> z, cx<R>& p1, cx<R>& p2, cx<R>& p3,
+                                                  cx<R>& q3) {
+  const R az2 = z.re * z.re + z.im * z.im;
+  if (az2 < R(1)) {
+    cx<R> t = cmk<R>(1, 0);  // z^(m-1)/(m-1)! at m = 1
+    cx<R> u = z;             // z^m/m! at m = 1
+    p1 = p2 = p3 = q3 = cmk<R>(0, 0);
+#pragma unroll
+    for (int m = 2; m <= SeriesLen<R>::n; ++m) {
+      t = crs(R(1) / R(m - 1), cmul(t, z));
+      u = crs(R(1) / R(m), cmul(u, z));
+      const R c1 = R((m - 1) * (m - 1)) * R(m >= 3);
+      const R c2 = R((m - 1) * (m - 3)) * R(m >= 4);
+      const R c3 = R(m - 1);
+      p1.re = fma(c1, t.re, p1.re);
+      p1.im = fma(c1, t.im, p1.im);
+      p2.re = fma(c2, t.re, p2.re);
+      p2.im = fma(c2, t.im, p2.im);
+      p3.re = fma(c3, t.re, p3.re);
+      p3.im = fma(c3, t.im, p3.im);
+      q3.re = fma(c3, u.re, q3.re);
+      q3.im = fma(c3, u.im, q3.im);
+    }
+  } else {
+    R s, c;
+    if constexpr (sizeof(R) == 8) {
+      sincos(z.im, &s, &c);
+    } else {
+      sincosf(z.im, &s, &c);
+    }
+    const R ex = (sizeof(R) == 8) ? R(exp((double)z.re)) : R(expf((float)z.re));
+    const cx<R> ez = cmk<R>(ex * c, ex * s);
+    const cx<R> z2 = cmul(z, z);
+    p1 = csub(cmul(cadd(z2, z), ez), z);
+    p2 = cadd(cmul(csub(z2, z), ez), z);
+    p3 = cmul(z, ez);
+    q3 = cmul(cmk<R>(z.re - R(1), z.im), ez);
+    q3.re += R(1);
+  }
+}
+
 template <class R>
 struct KConst {
   R ka, ki_re, ki_im;
@@ -137,9 +183,53 @@ __host__ __device__ __forceinline__ void kernel_scalars(const KConst<R>& K, R r,
   }
 }
 
-// 12 kernel components of one point pair, times the weights:
-// out[4*op + 2*alpha + beta], op = 0 K1, 1 K2^eps, 2 K2^mu.
 template <class R>
+__host__ __device__ __forceinline__ cx<R> cdivc(cx<R> a, cx<R> b) {
+  const R den = b.re * b.re + b.im * b.im;
+  return cmk<R>((a.re * b.re + a.im * b.im) / den, (a.im * b.re - a.re * b.im) / den);
+}
+
+// d/dtheta of S1, S2, De, Dm for theta = eps_r (which = 1) or mu_r (which = 2),
+// complex derivatives (the scalars are holomorphic in eps_r, mu_r):
+// k_i = k_a sqrt(eps_r mu_r) gives dk_i/dtheta = k_i / (2 theta) and
+// dz_i = i R dk_i; the exterior terms do not depend on theta.
+template <class R>
+__host__ __device__ __forceinline__ void kernel_scalars_d(const KConst<R>& K, R r, bool remainder,
+                                                          int which, cx<R>& S1, cx<R>& S2,
+                                                          cx<R>& De, cx<R>& Dm) {
+  const R c = R(0.0795774715459476678844418816862571885);  // 1/(4 pi)
+  const cx<R> ki = cmk(K.ki_re, K.ki_im);
+  const cx<R> ei = cmk(K.eps_re, K.eps_im), mi = cmk(K.mu_re, K.mu_im);
+  const cx<R> dki = crs(R(0.5), cdivc(ki, which == 1 ? ei : mi));
+  const cx<R> zi = cmk<R>(-K.ki_im * r, K.ki_re * r);
+  const cx<R> dzi = cmk<R>(-r * dki.im, r * dki.re);
+  cx<R> p1, p2, p3, q3i;
+  qfuncs_d(zi, p1, p2, p3, q3i);
+  const cx<R> dq1 = cmul(p1, dzi), dq2 = cmul(p2, dzi), dq3 = cmul(p3, dzi);
+  const R ir = R(1) / r;
+  const R ir2 = ir * ir, ir3 = ir2 * ir;
+  S1 = crs(c * ir3, dq1);
+  S2 = crs(-c * ir3, dq2);
+  // De = (c/R^2)(Q3(za) - eps Q3(zi)), Dm likewise with mu
+  De = crs(-c * ir2, cmul(ei, dq3));
+  Dm = crs(-c * ir2, cmul(mi, dq3));
+  if (which == 1) De = csub(De, crs(c * ir2, q3i));
+  else Dm = csub(Dm, crs(c * ir2, q3i));
+  if (!remainder) {
+    // d[(ka^2 - ki^2)/(8 pi R)] = -(c/R) ki dki;  d[-(1 - chi)/(4 pi R^2)] = c/R^2
+    const cx<R> s = crs(-c * ir, cmul(ki, dki));
+    S1 = cadd(S1, s);
+    S2 = cadd(S2, s);
+    if (which == 1) De.re += c * ir2;
+    else Dm.re += c * ir2;
+  }
+}
+
+// 12 kernel components of one point pair, times the weights:// 12 kernel components of one point pair, times the weights:
+// out[4*op + 2*alpha + beta], op = 0 K1, 1 K2^eps, 2 K2^mu.
+// WHICH = 0: the components; 1, 2: their derivatives with respect to eps_r,
+// mu_r (kernel_scalars_d; the geometry factors do not depend on them).
+template <class R, int WHICH = 0>
 __host__ __device__ __forceinline__ void point_pair(const KConst<R>& K, const R* __restrict__ px,
                                            const R* __restrict__ qy, bool remainder,
                                            cx<R> out[12]) {
@@ -154,7 +244,15 @@ __host__ __device__ __forceinline__ void point_pair(const KConst<R>& K, const R*
     const cx<R> ki2 = cmk(K.ki_re * K.ki_re - K.ki_im * K.ki_im, R(2) * K.ki_re * K.ki_im);
     const cx<R> ki3 = cmul(ki2, cmk(K.ki_re, K.ki_im));
     const R inv6pi = R(0.0530516476972984452562945877908381257);
-    const cx<R> lim = cmk(ki3.im * inv6pi, (ka3 - ki3.re) * inv6pi);  // i (ka^3 - ki^3)/(6 pi)
+    cx<R> lim = cmk(ki3.im * inv6pi, (ka3 - ki3.re) * inv6pi);  // i (ka^3 - ki^3)/(6 pi)
+    if constexpr (WHICH != 0) {
+      // d lim = -i ki^2 dki / (2 pi),  dki = ki / (2 chi)
+      const cx<R> dki = crs(R(0.5), cdivc(cmk(K.ki_re, K.ki_im),
+                                          WHICH == 1 ? cmk(K.eps_re, K.eps_im) : cmk(K.mu_re, K.mu_im)));
+      const cx<R> t = cmul(ki2, dki);
+      const R inv2pi = R(0.159154943091895335768883763372514362);
+      lim = cmk(t.im * inv2pi, -t.re * inv2pi);
+    }
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
@@ -172,7 +270,10 @@ __host__ __device__ __forceinline__ void point_pair(const KConst<R>& K, const R*
   const R ir = R(1) / r;
   const R hx = rx * ir, hy = ry * ir, hz = rz * ir;
   cx<R> S1, S2, De, Dm;
-  kernel_scalars<R>(K, r, remainder, S1, S2, De, Dm);
+  if constexpr (WHICH == 0)
+    kernel_scalars<R>(K, r, remainder, S1, S2, De, Dm);
+  else
+    kernel_scalars_d<R>(K, r, remainder, WHICH, S1, S2, De, Dm);
   const R nR = px[3] * hx + px[4] * hy + px[5] * hz;
   R tR[2], sR[2], Rt[2], nt[2];
 #pragma unroll

@@ -14,9 +14,9 @@ one reuses the forward operator and its preconditioner):
   the explicit eps_r, mu_r factors of Eq. global_system), so for the real
   part of a parameter  Z x_theta = -(dZ/dtheta) x  and for the imaginary part
   the direction is i x_theta.
-* (dZ/dtheta) x is the central difference of two assembled operators,
-  (Z(theta + h) x - Z(theta - h) x) / 2h, each product taken right after
-  its assembly into one scratch matrix (no dZ is stored).
+* (dZ/dtheta) x comes from mueller_dz_matvec: every element pair's block of
+  dZ/dtheta is recomputed from the derivatives of the radial functions and
+  multiplied into the result (no dZ is stored).
 * C_ext is linear in x and C_sca, C_abs are Hermitian quadratic forms, so
   dC_ext = C_ext(x_theta) and dC_q = C_q(x + x_theta) - C_q(x) - C_q(x_theta),
   all from one far-field call over the combined currents.
@@ -50,24 +50,31 @@ def forward_state(mesh, params, inc, block=None, tol=1e-12):
     return xs[0], dict(mesh=mesh, params=params, inc=inc, op=op, X=X, xs=xs[0], tol=tol)
 
 
-def material_jacobian(state, h_rel=1e-5):
+def dz_matvec_fd(mesh, params, key, X, h_rel=1e-5):
+    """(dZ/dtheta) X by the central difference of two assembled operators
+    (theta = 'eps_r' or 'mu_r'), for checking mueller_dz_matvec."""
+    torch = api._torch()
+    val = complex(*getattr(params, key))
+    h = h_rel * max(1.0, abs(val))
+    Zs = torch.empty((mesh.N, mesh.N), dtype=torch.complex128, device="cuda")
+    y = []
+    for sgn in (1.0, -1.0):
+        v = val + sgn * h
+        api.assemble(mesh, dataclasses.replace(params, **{key: (v.real, v.imag)}),
+                     api.MUELLER_C128, Z=Zs)
+        y.append(api.matvec(api.Operator(mesh, Zs, dtype=api.MUELLER_C128), X))
+    return (y[0] - y[1]) / (2.0 * h)
+
+
+def material_jacobian(state):
     """3 x 4 Jacobian of (C_ext, C_sca, C_abs) with respect to
     (Re eps_r, Im eps_r, Re mu_r, Im mu_r) at the forward state."""
     torch = api._torch()
     mesh, params, inc, op, X = (state[k] for k in ("mesh", "params", "inc", "op", "X"))
-    Zs = torch.empty_like(op.Z)
     tangents = []
-    for key in ("eps_r", "mu_r"):
-        val = complex(*getattr(params, key))
-        h = h_rel * max(1.0, abs(val))
-        y = []
-        for sgn in (1.0, -1.0):
-            v = val + sgn * h
-            q = dataclasses.replace(params, **{key: (v.real, v.imag)})
-            api.assemble(mesh, q, api.MUELLER_C128, Z=Zs)
-            y.append(api.matvec(api.Operator(mesh, Zs, dtype=api.MUELLER_C128), X))
-        tangents.append(_fp64_solve(op, -(y[0] - y[1]) / (2.0 * h), state["tol"]))
-    del Zs
+    for which in (1, 2):
+        ZtX = api.dz_matvec(mesh, params, which, X[0]).reshape(1, -1)
+        tangents.append(_fp64_solve(op, -ZtX, state["tol"]))
     comb = []
     for Xt in tangents:
         comb += [Xt, 1j * Xt, X + Xt, X + 1j * Xt]
