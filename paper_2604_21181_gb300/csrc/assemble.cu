@@ -126,9 +126,10 @@ struct RegCfg {
 
 // One CTA tile (test elements bx*WARPS.., trial elements by*TY..) of one body.
 // WHICH = 0 adds the blocks into Z; WHICH = 1, 2 forms the blocks of dZ/deps_r,
-// dZ/dmu_r instead and adds their product with x into y (complex128, length
-// 2H; the blocks are not stored): per warp the 24 rows of its test element
-// are summed in shared memory, then added to y once per tile.
+// dZ/dmu_r and adds their product with x into y (complex128, length 2H)
+// without forming the blocks: x is interpolated at the trial points, each
+// lane sums one (test point, a, half) output in registers over the tile, and
+// the 24 rows of the test element are added to y once per tile.
 template <class R, int Q, int W, int TYT, int WHICH = 0>
 __device__ __forceinline__ void regular_tile(int64_t bx, int64_t by, int64_t nt,
                                              const R* __restrict__ qd,
@@ -158,12 +159,18 @@ __device__ __forceinline__ void regular_tile(int64_t bx, int64_t by, int64_t nt,
   for (int k = 0; k < 6; ++k) tx[k] = T[6 * ex + k];
   constexpr int NB = C::NB;
   R* Kt = sK + (size_t)warp * NB * Q * Q * 24;  // [b][p][q][c] complex (re, im)
-  double* yacc = nullptr;  // [24][2]: rows 2 tx[i] + a (0..11), then H + 2 tx[i] + a
+  // Derivative mode contracts with x at the quadrature points instead of
+  // forming the 6 x 6 x 12 blocks: per trial element u[q][bb][hx] =
+  // sum_j N_j(q) x[2 ty_j + bb + hx H], and lane o = (p, a, h) of the test
+  // element keeps A0 = sum K0[p][q][a bb] u[q][bb][h] and
+  // A1 = sum K_{1+h}[p][q][a bb] u[q][bb][1-h] over the tile's trial elements.
+  constexpr int NO = Q * 4;            // outputs (p, a, h)
+  constexpr int NOL = (NO + 31) / 32;  // outputs per lane
+  double dacc[NOL][4] = {};            // A0 re, im, A1 re, im
+  double* su = nullptr;                // [b][q][bb][hx] complex
   if constexpr (WHICH != 0) {
-    __shared__ double s_yacc[W][48];
-    yacc = s_yacc[warp];
-    for (int k = lane; k < 48; k += 32) yacc[k] = 0.0;
-    __syncwarp();
+    __shared__ double s_u[W][C::NB * Q * 8];
+    su = s_u[warp];
   }
   int* myList = reinterpret_cast<int*>(sK + (size_t)C::WARPS * NB * Q * Q * 24) + warp * C::TY;
   const R wre = R(0), wim = R(1) / K.ka;   // i / omega
@@ -200,6 +207,52 @@ __device__ __forceinline__ void regular_tile(int64_t bx, int64_t by, int64_t nt,
       }
     }
     __syncwarp();
+    if constexpr (WHICH != 0) {
+      for (int it = lane; it < nbb * Q * 4; it += 32) {
+        const int b = it / (Q * 4), r = it % (Q * 4);
+        const int q = r >> 2, bb = (r >> 1) & 1, hx = r & 1;
+        const int32_t* ty = T + 6 * (ey0 + myList[b0 + b]);
+        double ur = 0, ui = 0;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+          const double ph = phi_at<double>(q, j);
+          const double2 xv = xd[2 * (int64_t)ty[j] + bb + (hx ? H : 0)];
+          ur = fma(ph, xv.x, ur);
+          ui = fma(ph, xv.y, ui);
+        }
+        su[2 * it] = ur;
+        su[2 * it + 1] = ui;
+      }
+      __syncwarp();
+#pragma unroll
+      for (int k = 0; k < NOL; ++k) {
+        const int o = lane + 32 * k;
+        if (o < NO) {
+          const int p = o >> 2, a = (o >> 1) & 1, h = o & 1;
+          for (int b = 0; b < nbb; ++b) {
+            const R* Kb = Kt + ((size_t)b * Q * Q + (size_t)p * Q) * 24;
+            const double* ub = su + (size_t)b * Q * 8;
+            for (int q = 0; q < Q; ++q) {
+#pragma unroll
+              for (int bb = 0; bb < 2; ++bb) {
+                const int c0 = 2 * a + bb, c1 = 4 * (1 + h) + 2 * a + bb;
+                const double k0r = Kb[q * 24 + 2 * c0], k0i = Kb[q * 24 + 2 * c0 + 1];
+                const double k1r = Kb[q * 24 + 2 * c1], k1i = Kb[q * 24 + 2 * c1 + 1];
+                const double* u = ub + 2 * (q * 4 + 2 * bb);
+                const double uhr = u[2 * h], uhi = u[2 * h + 1];
+                const double uor = u[2 - 2 * h], uoi = u[3 - 2 * h];
+                dacc[k][0] += k0r * uhr - k0i * uhi;
+                dacc[k][1] += k0r * uhi + k0i * uhr;
+                dacc[k][2] += k1r * uor - k1i * uoi;
+                dacc[k][3] += k1r * uoi + k1i * uor;
+              }
+            }
+          }
+        }
+      }
+      __syncwarp();
+      continue;
+    }
     // 2. T[p][j][c] = sum_q Kt[p][q][c] N_j(q), written over Kt[p][j][c]
     for (int it = lane; it < nbb * Q * 12; it += 32) {
       const int b = it / (Q * 12), pc = it % (Q * 12);
@@ -248,40 +301,44 @@ __device__ __forceinline__ void regular_tile(int64_t bx, int64_t by, int64_t nt,
           are = fma(ph, vre[p], are);
           aim = fma(ph, vim[p], aim);
         }
-        if constexpr (WHICH == 0) {
-          const int64_t row = 2 * (int64_t)tx[i] + a + (op == 2 ? H : 0);
-          if (op == 0) {  // (i/omega) K1
-            const R zr = wre * are - wim * aim, zi = wre * aim + wim * are;
-            zadd(Z, row * ldz + col, zr, zi);
-          } else {
-            zadd(Z, row * ldz + col, are, aim);
-          }
+        const int64_t row = 2 * (int64_t)tx[i] + a + (op == 2 ? H : 0);
+        if (op == 0) {  // (i/omega) K1
+          const R zr = wre * are - wim * aim, zi = wre * aim + wim * are;
+          zadd(Z, row * ldz + col, zr, zi);
         } else {
-          double vr = are, vi = aim;
-          if (op == 0) {
-            vr = -(double)wim * aim;
-            vi = (double)wim * are;
-          }
-          const double2 xv = xd[col];
-          const int lr = (op == 2 ? 12 : 0) + 2 * i + a;
-          atomicAdd(&yacc[2 * lr], vr * xv.x - vi * xv.y);
-          atomicAdd(&yacc[2 * lr + 1], vr * xv.y + vi * xv.x);
-          if (op == 0) {  // Z11 = -Z00: the bottom rows against the bottom half of x
-            const double2 xb = xd[col + H];
-            atomicAdd(&yacc[2 * (12 + 2 * i + a)], -(vr * xb.x - vi * xb.y));
-            atomicAdd(&yacc[2 * (12 + 2 * i + a) + 1], -(vr * xb.y + vi * xb.x));
-          }
+          zadd(Z, row * ldz + col, are, aim);
         }
       }
     }
     __syncwarp();
   }
   if constexpr (WHICH != 0) {
-    for (int k = lane; k < 24; k += 32) {
-      const int h = k / 12, ia = k % 12;
-      const int64_t row = (h ? H : 0) + 2 * (int64_t)tx[ia >> 1] + (ia & 1);
-      atomicAdd(&yd[row].x, yacc[2 * k]);
-      atomicAdd(&yd[row].y, yacc[2 * k + 1]);
+    // top rows: (i/omega) A0 + A1; bottom rows (Z11 = -Z00): -(i/omega) A0 + A1;
+    // then y[row(i, a, h)] += sum_p N_i(p) acc[p][a][h]
+    __shared__ double s_acc[W][NO * 2];
+    double* acc = s_acc[warp];
+#pragma unroll
+    for (int k = 0; k < NOL; ++k) {
+      const int o = lane + 32 * k;
+      if (o < NO) {
+        const double sg = (o & 1) ? -1.0 : 1.0, w = (double)wim;
+        acc[2 * o] = dacc[k][2] - sg * w * dacc[k][1];
+        acc[2 * o + 1] = dacc[k][3] + sg * w * dacc[k][0];
+      }
+    }
+    __syncwarp();
+    if (lane < 24) {
+      const int i = lane >> 2, a = (lane >> 1) & 1, h = lane & 1;
+      double vr = 0, vi = 0;
+#pragma unroll
+      for (int p = 0; p < Q; ++p) {
+        const double ph = phi_at<double>(p, i);
+        vr = fma(ph, acc[2 * (p * 4 + 2 * a + h)], vr);
+        vi = fma(ph, acc[2 * (p * 4 + 2 * a + h) + 1], vi);
+      }
+      const int64_t row = (h ? H : 0) + 2 * (int64_t)tx[i] + a;
+      atomicAdd(&yd[row].x, vr);
+      atomicAdd(&yd[row].y, vi);
     }
   }
 }
