@@ -518,7 +518,7 @@ def gradients_l3(mu, torch, dev):
     3 + 0.2i, mu_r = 1, k_a = 3, incidence +z, x polarised): the FP64
     forward state (assembly, block-Jacobi, GMRES to 1e-12, far field) and
     the 3 x 4 Jacobian of (C_ext, C_sca, C_abs) with respect to (Re, Im) of
-    eps_r and mu_r (four more assemblies, two tangent solves, one far-field
+    eps_r and mu_r (two operator-derivative products, two tangent solves, one far-field
     call), wall time with the device synchronised."""
     import time as _t
 
@@ -527,7 +527,8 @@ def gradients_l3(mu, torch, dev):
     m.tangent_frame(0, out=False)
     p = mu.Params(ka=3.0, eps_r=(3.0, 0.2), mu_r=(1.0, 0.0), q_regular=6, ssq_order=5, frame_rule=0)
     inc = workloads.plane_wave((0.0, 0.0, 1.0), (1.0, 0.0, 0.0))
-    mu.grad.forward_state(m, p, inc)  # warm-up (tuning, rules)
+    # warm-up (tuning, rules, first launches of the derivative kernels, workspace)
+    mu.grad.material_jacobian(mu.grad.forward_state(m, p, inc)[1])
     torch.cuda.synchronize()
     t0 = _t.perf_counter()
     xs, state = mu.grad.forward_state(m, p, inc)

@@ -277,21 +277,30 @@ __host__ __device__ __forceinline__ void sphere_pair(int64_t p, int n_theta, int
 
 // F at the sphere-rule directions, which come in antipodal pairs
 // (d_k2 = -d_k1 exactly): exp(-i k d_k2.y) = conj(exp(-i k d_k1.y)), so one
-// phase serves both directions of a pair.  DP pairs per CTA; dirs and F
-// point at the sphere block (index k).
-constexpr int kFarDP = 2;
-template <int DP>
+// phase serves both directions of a pair, and so do the four real products
+// of a current component v with it:
+//   F(d_k1) += (v.x e.x - v.y e.y, v.x e.y + v.y e.x),
+//   F(d_k2) += (v.x e.x + v.y e.y, v.y e.x - v.x e.y),
+// summed as the four sums of v.x e.x, v.y e.y, v.x e.y, v.y e.x (4 FMAs per
+// component for both directions).  A CTA takes DP pairs and RS right-hand
+// sides (blockIdx.y: right-hand sides RS*y ..).  dirs and F point at the
+// sphere block (index k) of right-hand side 0; F of right-hand side s is
+// F + s * f_stride, its currents rec + s * np * 6.
+constexpr int kFarDP = 2;   // one right-hand side: pairs per CTA
+constexpr int kFarMRS = 2;  // several: right-hand sides per CTA (one pair)
+template <int DP, int RS>
 __global__ void __launch_bounds__(256, 2) far_pair_kernel(int64_t np, const double* __restrict__ qd,
-                                                       const double2* __restrict__ rec,
+                                                       const double2* __restrict__ rec, int r,
                                                        const double* __restrict__ dirs,
                                                        int n_theta, int n_phi, double ka,
-                                                       double2* __restrict__ F) {
+                                                       double2* __restrict__ F, int64_t f_stride) {
   __shared__ double2 tab[kCisN];
   __shared__ double red[12][256];
   cis_fill(tab);
   __syncthreads();
   const int64_t npairs = (int64_t)n_theta * n_phi / 2;
   const int64_t p0 = (int64_t)blockIdx.x * DP;
+  const int s0 = blockIdx.y * RS;
   double rk[DP][3];
 #pragma unroll
   for (int q = 0; q < DP; ++q) {
@@ -300,29 +309,37 @@ __global__ void __launch_bounds__(256, 2) far_pair_kernel(int64_t np, const doub
 #pragma unroll
     for (int a = 0; a < 3; ++a) rk[q][a] = -ka * dirs[3 * k1 + a];
   }
-  double acc[DP][2][12];
+  double acc[DP][RS][4][6];  // sums of v.x e.x, v.y e.y, v.x e.y, v.y e.x
 #pragma unroll
   for (int q = 0; q < DP; ++q)
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
+    for (int k = 0; k < RS; ++k)
 #pragma unroll
-      for (int c = 0; c < 12; ++c) acc[q][h][c] = 0.0;
+      for (int h = 0; h < 4; ++h)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) acc[q][k][h][c] = 0.0;
   for (int64_t t = threadIdx.x; t < np; t += blockDim.x) {
     const double* qp = qd + t * QD_STRIDE;
     const double y0 = qp[0], y1 = qp[1], y2 = qp[2];
-    const double2* o = rec + t * 6;
-    double2 v[6];
+    double2 e[DP];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) v[c] = o[c];
+    for (int q = 0; q < DP; ++q) e[q] = cis_tab(fma(rk[q][0], y0, fma(rk[q][1], y1, rk[q][2] * y2)), tab);
 #pragma unroll
-    for (int q = 0; q < DP; ++q) {
-      const double2 e = cis_tab(fma(rk[q][0], y0, fma(rk[q][1], y1, rk[q][2] * y2)), tab);
+    for (int k = 0; k < RS; ++k) {
+      if (s0 + k < r) {
+        const double2* o = rec + ((int64_t)(s0 + k) * np + t) * 6;
+        double2 v[6];
 #pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        acc[q][0][2 * c] = fma(v[c].x, e.x, fma(-v[c].y, e.y, acc[q][0][2 * c]));
-        acc[q][0][2 * c + 1] = fma(v[c].x, e.y, fma(v[c].y, e.x, acc[q][0][2 * c + 1]));
-        acc[q][1][2 * c] = fma(v[c].x, e.x, fma(v[c].y, e.y, acc[q][1][2 * c]));
-        acc[q][1][2 * c + 1] = fma(-v[c].x, e.y, fma(v[c].y, e.x, acc[q][1][2 * c + 1]));
+        for (int c = 0; c < 6; ++c) v[c] = o[c];
+#pragma unroll
+        for (int q = 0; q < DP; ++q)
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            acc[q][k][0][c] = fma(v[c].x, e[q].x, acc[q][k][0][c]);
+            acc[q][k][1][c] = fma(v[c].y, e[q].y, acc[q][k][1][c]);
+            acc[q][k][2][c] = fma(v[c].x, e[q].y, acc[q][k][2][c]);
+            acc[q][k][3][c] = fma(v[c].y, e[q].x, acc[q][k][3][c]);
+          }
       }
     }
   }
@@ -332,27 +349,40 @@ __global__ void __launch_bounds__(256, 2) far_pair_kernel(int64_t np, const doub
       int64_t kk[2];
       sphere_pair(p0 + q, n_theta, n_phi, kk[0], kk[1]);
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const double* dd = dirs + 3 * kk[h];
-        far_finish(red, acc[q][h], dd[0], dd[1], dd[2], ka, F + kk[h] * 3);
-        __syncthreads();
+      for (int k = 0; k < RS; ++k) {
+        if (s0 + k < r) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            double a[12];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+              const double xx = acc[q][k][0][c], yy = acc[q][k][1][c];
+              const double xy = acc[q][k][2][c], yx = acc[q][k][3][c];
+              a[2 * c] = h ? xx + yy : xx - yy;
+              a[2 * c + 1] = h ? yx - xy : xy + yx;
+            }
+            const double* dd = dirs + 3 * kk[h];
+            far_finish(red, a, dd[0], dd[1], dd[2], ka, F + (s0 + k) * f_stride + kk[h] * 3);
+            __syncthreads();
+          }
+        }
       }
     }
   }
 }
 
-// The directions shared by all right-hand sides (sphere rule, user list:
-// indices 1 .. nd-1) for RS right-hand sides per CTA: each phase
-// exp(-i k r.y) is computed once and applied to the RS current records.
-// Per right-hand side the sums run in the same order as in far_kernel (a
-// single right-hand side uses far_pair_kernel, which agrees to rounding).
+// Directions shared by all right-hand sides (indices d0, d0 + 1, .. of the
+// list: the user directions, or with an odd n_phi the whole sphere rule too)
+// for RS right-hand sides per CTA: each phase exp(-i k r.y) is computed once
+// and applied to the RS current records.  Per right-hand side the sums run in
+// the same order as in far_kernel.
 template <int RS>
 __global__ void __launch_bounds__(256) far_multi_kernel(int64_t np, const double* __restrict__ qd,
                                                         const double2* __restrict__ rec, int r,
                                                         const double* __restrict__ dirs,
-                                                        int64_t nd, double ka,
+                                                        int64_t nd, int64_t d0, double ka,
                                                         double2* __restrict__ F) {
-  const int64_t d = 1 + blockIdx.x;
+  const int64_t d = d0 + blockIdx.x;
   const int s0 = blockIdx.y * RS;
   const double rx = dirs[3 * d], ry = dirs[3 * d + 1], rz = dirs[3 * d + 2];
   __shared__ double2 tab[kCisN];
@@ -490,12 +520,38 @@ mueller_status far_one_rhs(int64_t np, const double* qd, const double2* rec, con
     return MUELLER_OK;
   }
   const int64_t npairs = nsph / 2;
-  { Prof prof_("far_pair_kernel", s); far_pair_kernel<kFarDP><<<(unsigned)((npairs + kFarDP - 1) / kFarDP), 256, 0, s>>>(
-      np, qd, rec, dirs + 3, n_theta, n_phi, ka, F + 3); }
+  { Prof prof_("far_pair_kernel", s); far_pair_kernel<kFarDP, 1><<<(unsigned)((npairs + kFarDP - 1) / kFarDP), 256, 0, s>>>(
+      np, qd, rec, 1, dirs + 3, n_theta, n_phi, ka, F + 3, 0); }
   if (ndir > 0)
     { Prof prof_("far_kernel", s); far_kernel<kFarDT><<<far_grid(ndir), 256, 0, s>>>(np, qd, rec, dirs + 3 * (1 + nsph), ndir, ka,
                                                                                      F + 3 * (1 + nsph)); }
   MU_CHECK_LAUNCH("far_kernel");
+  return MUELLER_OK;
+}
+
+// F of all r right-hand sides at the directions they share (sphere rule and
+// user list, indices 1 .. nd-1 of each list; rec, dirs and F hold r blocks).
+// One right-hand side: far_one_rhs.  Several: the sphere rule by antipodal
+// pairs (even n_phi), kFarMRS right-hand sides per CTA, and the remaining
+// directions 4 right-hand sides per CTA.
+mueller_status far_shared(int64_t np, const double* qd, const double2* rec, int r,
+                          const double* dirs, int64_t nd, int n_theta, int n_phi, int64_t ndir,
+                          double ka, double2* F, cudaStream_t s) {
+  if (r == 1) return far_one_rhs(np, qd, rec, dirs, nd, n_theta, n_phi, ndir, ka, F, s);
+  const int64_t nsph = (int64_t)n_theta * n_phi;
+  int64_t d0 = 1;
+  if (n_phi % 2 == 0) {
+    Prof prof_("far_pair_kernel", s);
+    far_pair_kernel<1, kFarMRS><<<dim3((unsigned)(nsph / 2), (unsigned)((r + kFarMRS - 1) / kFarMRS)), 256, 0, s>>>(
+        np, qd, rec, r, dirs + 3, n_theta, n_phi, ka, F + 3, nd * 3);
+    d0 = 1 + nsph;
+  }
+  if (nd > d0) {
+    Prof prof_("far_multi_kernel", s);
+    far_multi_kernel<4><<<dim3((unsigned)(nd - d0), (unsigned)((r + 3) / 4)), 256, 0, s>>>(
+        np, qd, rec, r, dirs, nd, d0, ka, F);
+  }
+  MU_CHECK_LAUNCH("far_shared");
   return MUELLER_OK;
 }
 
@@ -566,13 +622,7 @@ mueller_status far_field(mueller_mesh* m, const PhysConsts& P, int Q, const void
     { Prof prof_("currents_kernel", s); currents_kernel<<<dim3(nblk_pts, r), 256, 0, s>>>(m->nt, Q, m->qd64, m->T, (const double2*)X, r,
                                                        N, dphi, rec, cab); }
     st = far_fwd(np, m->qd64, rec, ddirs, nd, r, P.ka, (double*)(buf + o_part), Fall, s);
-    if (!st && r == 1) {
-      st = far_one_rhs(np, m->qd64, rec, ddirs, nd, n_theta, n_phi, ndir, P.ka, Fall, s);
-    } else if (!st) {
-      // the shared directions, 4 right-hand sides per CTA
-      { Prof prof_("far_multi_kernel", s); far_multi_kernel<4><<<dim3((unsigned)(nd - 1), (unsigned)((r + 3) / 4)), 256, 0, s>>>(
-          np, m->qd64, rec, r, ddirs, nd, P.ka, Fall); }
-    }
+    if (!st) st = far_shared(np, m->qd64, rec, r, ddirs, nd, n_theta, n_phi, ndir, P.ka, Fall, s);
     if (!st) {
       { Prof prof_("xs_kernel", s); xs_kernel<<<r, 256, 0, s>>>(Fall, nd, n_theta, n_phi, dwth, dinc, P.ka, cab, (int)nblk_pts, dxs); }
       if (ndir > 0)
@@ -695,11 +745,8 @@ mueller_status far_field_noalloc(mueller_mesh* m, const PhysConsts& P, int Q, co
   { Prof prof_("currents_kernel", s); currents_kernel<<<dim3(nblk_pts, r), 256, 0, s>>>(m->nt, Q, m->qd64, m->T, (const double2*)X, r, N, dphi, rec, cab); }
   st = far_fwd(np, m->qd64, rec, ddirs, nd, r, P.ka, (double*)(buf + o_part), Fall, s);
   if (st) return st;
-  for (int sidx = 0; sidx < r; ++sidx) {
-    st = far_one_rhs(np, m->qd64, rec + (size_t)sidx * np * 6, ddirs + (size_t)sidx * nd * 3, nd,
-                     n_theta, n_phi, ndir, P.ka, Fall + (size_t)sidx * nd * 3, s);
-    if (st) return st;
-  }
+  st = far_shared(np, m->qd64, rec, r, ddirs, nd, n_theta, n_phi, ndir, P.ka, Fall, s);
+  if (st) return st;
   { Prof prof_("xs_kernel", s); xs_kernel<<<r, 256, 0, s>>>(Fall, nd, n_theta, n_phi, dwth, dinc, P.ka, cab, (int)nblk_pts, dxs); }
   if (ndir > 0) {
     Prof prof_("copy_user_dirs_kernel", s);

@@ -210,13 +210,14 @@ def test_far_field_matches_oracle():
 
 
 @pytest.mark.parametrize("ka", [0.5, 60.0, 4.0e4])
-@pytest.mark.parametrize("r,n_phi", [(1, 16), (1, 15), (2, 16)])
+@pytest.mark.parametrize("r,n_phi", [(1, 16), (1, 15), (3, 16), (3, 15)])
 def test_far_field_phase_range_matches_oracle(ka, r, n_phi):
     """Random currents, so that every phase exp(-i k r.y) counts: k a = 60
     spans many periods of the table-driven exp(i th), 4e4 (|th| beyond
     2^20 pi/128) the sincos branch.  One RHS with an even n_phi takes the
-    antipodal-pair kernel, an odd n_phi the per-direction one, two RHS the
-    multi-RHS kernel.  Both sides form th = k r.y in FP64 with its rounding
+    antipodal-pair kernel, an odd n_phi the per-direction one; three RHS
+    take the pair kernel two RHS per CTA (a partial group) with an even
+    n_phi, the multi-RHS kernel four per CTA with an odd one.  Both sides form th = k r.y in FP64 with its rounding
     of a few ulp(|th|), so the bound is 1e-12 of max |F| or 50 k a eps,
     whichever is larger."""
     xyz, tri6 = workloads.icosphere_p2(1)
@@ -225,7 +226,7 @@ def test_far_field_phase_range_matches_oracle(ka, r, n_phi):
     mu.assemble(m, mu.Params(ka=1.0, eps_r=(2.0, 0.0), ssq_order=2, frame_rule=0),
                 mu.MUELLER_C128)  # point geometry of the rule
     p = mu.Params(ka=ka, eps_r=(2.0, 0.0), ssq_order=2, frame_rule=0)
-    inc = workloads.fibonacci_plane_waves(1)[:r]
+    inc = workloads.fibonacci_plane_waves(2)[:r]
     rng = np.random.default_rng(11)
     X = rng.standard_normal((r, m.N)) + 1j * rng.standard_normal((r, m.N))
     dirs = workloads.fibonacci_directions(9)
