@@ -205,6 +205,34 @@ static int classify_pair(const int32_t* a, const int32_t* b, int32_t& packed) {
   return ns;
 }
 
+// Sorts v[0 .. len) of distinct ids ascending.  Ids of neighbouring nodes or
+// elements in Morton order fall in a narrow range, so they are marked in the
+// bitmap (all zero on entry and on return) and read back in order when the
+// range spans at most 4 words per id; otherwise std::sort.
+static void sort_ids(int32_t* v, size_t len, uint64_t* bits) {
+  if (len < 2) return;
+  int32_t lo = v[0], hi = v[0];
+  for (size_t k = 1; k < len; ++k) {
+    lo = std::min(lo, v[k]);
+    hi = std::max(hi, v[k]);
+  }
+  const int64_t w0 = lo >> 6, w1 = hi >> 6;
+  if (w1 - w0 + 1 > (int64_t)(4 * len)) {
+    std::sort(v, v + len);
+    return;
+  }
+  for (size_t k = 0; k < len; ++k) bits[v[k] >> 6] |= 1ull << (v[k] & 63);
+  size_t o = 0;
+  for (int64_t w = w0; w <= w1; ++w) {
+    uint64_t b = bits[w];
+    bits[w] = 0;
+    while (b) {
+      v[o++] = (int32_t)((w << 6) + __builtin_ctzll(b));
+      b &= b - 1;
+    }
+  }
+}
+
 template <class Tp>
 static mueller_status upload(Tp** dst, const Tp* src, size_t n, cudaStream_t s) {
   MU_CUDA(cudaMalloc((void**)dst, std::max<size_t>(1, n) * sizeof(Tp)));
@@ -311,14 +339,21 @@ mueller_status mueller_mesh_load(const double* xyz, int64_t nn, const int32_t* t
   std::vector<TouchPair> tp;
   {
     std::vector<int32_t> cand;
+    std::vector<int32_t> seen(nt, -1);
+    std::vector<uint64_t> bits((nt + 63) / 64 + 1, 0);
     for (int64_t ex = 0; ex < nt; ++ex) {
       cand.clear();
       for (int k = 0; k < 3; ++k) {
         int32_t v = T[6 * ex + k];
-        for (int32_t q = ptr[v]; q < ptr[v + 1]; ++q) cand.push_back(n2e[q] >> 3);
+        for (int32_t q = ptr[v]; q < ptr[v + 1]; ++q) {
+          const int32_t ey = n2e[q] >> 3;
+          if (seen[ey] != (int32_t)ex) {
+            seen[ey] = (int32_t)ex;
+            cand.push_back(ey);
+          }
+        }
       }
-      std::sort(cand.begin(), cand.end());
-      cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+      sort_ids(cand.data(), cand.size(), bits.data());
       for (int32_t ey : cand) {
         int32_t packed;
         int cls = classify_pair(T + 6 * ex, T + 6 * ey, packed);
@@ -339,31 +374,43 @@ mueller_status mueller_mesh_load(const double* xyz, int64_t nn, const int32_t* t
   // ---- near-part block layout: node pairs of the touching element pairs.
   // Row by row: the columns of test node ni are the nodes of every trial
   // element touching an element that holds ni (deduplicated with a stamp
-  // array, then sorted), and the slot of (pair, i, j) is found through a
-  // column -> position array valid for the current row.
+  // array, without branches, then sorted), and the slot of (pair, i, j) is
+  // found through a column -> position array valid for the current row.
   std::vector<int64_t> pfirst(nt + 1, 0);  // tp is sorted by ex
   for (const TouchPair& q : tp) pfirst[q.ex + 1]++;
   for (int64_t e = 0; e < nt; ++e) pfirst[e + 1] += pfirst[e];
   std::vector<int32_t> slot((size_t)m->n_touch * 36);
   {
     std::vector<int32_t> stamp(nn, -1), pos(nn, 0);
+    std::vector<uint64_t> bits((nn + 63) / 64 + 1, 0);
+    int64_t row_max = 0;  // candidate columns of the longest row
+    for (int64_t ni = 0; ni < nn; ++ni) {
+      int64_t c = 0;
+      for (int32_t q = ptr[ni]; q < ptr[ni + 1]; ++q) {
+        const int64_t ex = n2e[q] >> 3;
+        c += 6 * (pfirst[ex + 1] - pfirst[ex]);
+      }
+      row_max = std::max(row_max, c);
+    }
+    std::vector<int32_t> row((size_t)row_max + 1);
     m->near_rowptr_h.assign(nn + 1, 0);
     m->near_col_h.clear();
     m->near_col_h.reserve((size_t)nn * 64);
     for (int64_t ni = 0; ni < nn; ++ni) {
       const size_t start = m->near_col_h.size();
+      size_t len = 0;
       for (int32_t q = ptr[ni]; q < ptr[ni + 1]; ++q) {
         const int64_t ex = n2e[q] >> 3;
         for (int64_t p = pfirst[ex]; p < pfirst[ex + 1]; ++p)
           for (int j = 0; j < 6; ++j) {
             const int32_t nj = T[6 * tp[p].ey + j];
-            if (stamp[nj] != (int32_t)ni) {
-              stamp[nj] = (int32_t)ni;
-              m->near_col_h.push_back(nj);
-            }
+            row[len] = nj;
+            len += stamp[nj] != (int32_t)ni;
+            stamp[nj] = (int32_t)ni;
           }
       }
-      std::sort(m->near_col_h.begin() + start, m->near_col_h.end());
+      sort_ids(row.data(), len, bits.data());
+      m->near_col_h.insert(m->near_col_h.end(), row.begin(), row.begin() + len);
       m->near_rowptr_h[ni + 1] = (int32_t)m->near_col_h.size();
       for (size_t k = start; k < m->near_col_h.size(); ++k) pos[m->near_col_h[k]] = (int32_t)k;
       for (int32_t q = ptr[ni]; q < ptr[ni + 1]; ++q) {
