@@ -317,6 +317,40 @@ def cross_sections(mesh: Mesh, p, inc):
     return np.asarray(mesh.far_field(p, X, inc)[1])
 
 
+def cross_section_shape_derivative(xyz, tri6, p, inc, V, h: float = 1e-6, frame_rule: int = 0):
+    """Derivative of (C_ext, C_sca, C_abs), one row per incident wave, along
+    the node displacement field V (n_nodes x 3): d/dt C(xyz + t V) at t = 0,
+    by central differences of cross_sections on the meshes with nodes
+    xyz +- h V and the same connectivity (truncation O(h^2)).  The paper
+    defines no shape derivative; this is the plain derivative of the
+    oracle's own results."""
+    xyz = np.asarray(xyz, dtype=np.float64)
+    V = np.asarray(V, dtype=np.float64)
+    xs = []
+    for sgn in (1.0, -1.0):
+        m = Mesh(xyz + sgn * h * V, tri6, frame_rule=frame_rule)
+        xs.append(cross_sections(m, p, inc))
+    return (xs[0] - xs[1]) / (2.0 * h)
+
+
+def cross_section_coordinate_gradient(xyz, tri6, p, inc, nodes=None, h: float = 1e-6,
+                                      frame_rule: int = 0):
+    """Gradient of (C_ext, C_sca, C_abs) of the first incident wave with
+    respect to the coordinates of the listed nodes (all nodes by default;
+    node ids of the caller's xyz): array (len(nodes), 3 coordinates,
+    3 cross sections), each entry cross_section_shape_derivative along one
+    unit coordinate displacement."""
+    xyz = np.asarray(xyz, dtype=np.float64)
+    nodes = range(xyz.shape[0]) if nodes is None else nodes
+    G = np.zeros((len(nodes), 3, 3))
+    for a, k in enumerate(nodes):
+        for d in range(3):
+            V = np.zeros_like(xyz)
+            V[k, d] = 1.0
+            G[a, d] = cross_section_shape_derivative(xyz, tri6, p, inc, V, h, frame_rule)[0]
+    return G
+
+
 def cross_section_gradient(mesh: Mesh, p, inc, h: float = 1e-4):
     """Jacobian of (C_ext, C_sca, C_abs) of the first incident wave with
     respect to (Re eps_r, Im eps_r, Re mu_r, Im mu_r), by central differences
