@@ -80,6 +80,12 @@ enum {
   MUELLER_FRAME_POLAR = 1  /* v_ref = z except within 1e-8 of the poles      */
 };
 
+/* mueller_mesh_load flags (bits) */
+enum {
+  MUELLER_MESH_KEEP_ORDER = 1, /* keep the input node and element order      */
+  MUELLER_MESH_HOST_ONLY = 2   /* build the host tables only: no device data */
+};
+
 typedef struct mueller_mesh mueller_mesh;
 
 typedef struct {
@@ -156,7 +162,12 @@ const char* mueller_status_string(mueller_status s);
  * everything to the device on 'stream'.
  *   xyz   host, n_nodes x 3 float64, read only, copied.
  *   tri6  host, n_tri x 6 int32 node ids, read only, copied.
- *   flags bit 0: keep the input order (no Morton permutation).
+ *   flags MUELLER_MESH_KEEP_ORDER: keep the input order (no Morton
+ *         permutation).  MUELLER_MESH_HOST_ONLY: validate and build the
+ *         host tables (orders, touching pairs, near-block layout) but touch
+ *         no device: the handle serves mueller_mesh_get_info,
+ *         mueller_mesh_perm, mueller_mesh_touching, mueller_mesh_near_layout
+ *         and mueller_near_bytes; calls that need device data return STATE.
  *   out   receives the handle (owned by the library; free with
  *         mueller_mesh_free).
  * Errors: INVALID_ARG (null/sizes), MESH (validation), OOM, CUDA.
@@ -169,6 +180,38 @@ mueller_status mueller_mesh_get_info(const mueller_mesh* mesh, mueller_mesh_info
 /* host outputs: node_perm[n_nodes], elem_perm[n_tri] (new -> old); either may be NULL */
 mueller_status mueller_mesh_perm(const mueller_mesh* mesh, int32_t* node_perm,
                                  int32_t* elem_perm);
+
+/*
+ * mueller_mesh_touching -- Sec. 4.2: the touching element pairs the
+ * Sauter-Schwab quadrature takes, in the order the library keeps them
+ * (test element ascending, then trial element), n_touching entries per
+ * output (host arrays, any may be NULL; element ids in the mesh's order):
+ *   ex, ey   test and trial element;
+ *   cls      shared corners: 3 coincident, 2 common edge, 1 common vertex;
+ *   relabel  the corner relabellings of the two elements, packed: bits
+ *            2k..2k+1 hold the test element's local corner that becomes
+ *            corner k of the relabelled triangle, bits 8+2k..9+2k the trial
+ *            element's (k = 0, 1, 2).  Common edge: the shared edge is
+ *            corners 0 -> 1 as it runs in the test element; common vertex:
+ *            the shared corner is corner 0 of both, the others follow
+ *            cyclically; coincident: identity.
+ * Errors: INVALID_ARG (mesh NULL).
+ */
+mueller_status mueller_mesh_touching(const mueller_mesh* mesh, int32_t* ex, int32_t* ey,
+                                     int32_t* cls, int32_t* relabel);
+
+/*
+ * mueller_mesh_near_layout -- the block layout of the near part (the node
+ * pairs of the touching element pairs, Eq. global_system split into the
+ * far part in Z and the near blocks): host outputs, any may be NULL,
+ *   rowptr  n_nodes + 1: blocks of test node i are rowptr[i] .. rowptr[i+1]-1;
+ *   col     n_near_blocks: their trial nodes, ascending within a row;
+ *   slot    36 n_touching: slot[(p*6 + i)*6 + j] is the block of the node
+ *           pair (node i of ex_p, node j of ey_p) of touching pair p.
+ * Errors: INVALID_ARG (mesh NULL).
+ */
+mueller_status mueller_mesh_near_layout(const mueller_mesh* mesh, int32_t* rowptr, int32_t* col,
+                                        int32_t* slot);
 
 /*
  * mueller_tangent_frame -- Sec. 3.1 Eq. (U_contribution) and Sec. 3.2

@@ -22,6 +22,8 @@ MUELLER_OP_K1_MIRRORED = 1
 SOLVE_DENSE_LU = 0
 SOLVE_GMRES = 1
 SOLVE_GMRES_IR = 2
+MESH_KEEP_ORDER = 1
+MESH_HOST_ONLY = 2
 FRAME_PAPER = 0
 FRAME_POLAR = 1
 
@@ -69,7 +71,8 @@ class COperator(C.Structure):
 
 EXPORTS = [
     "mueller_version", "mueller_last_error", "mueller_status_string", "mueller_mesh_load",
-    "mueller_mesh_free", "mueller_mesh_get_info", "mueller_mesh_perm", "mueller_tangent_frame",
+    "mueller_mesh_free", "mueller_mesh_get_info", "mueller_mesh_perm", "mueller_mesh_touching",
+    "mueller_mesh_near_layout", "mueller_tangent_frame",
     "mueller_assemble", "mueller_dz_matvec", "mueller_near_bytes", "mueller_precond_build",
     "mueller_precond_bytes",
     "mueller_solve", "mueller_solve_workspace_bytes", "mueller_matvec",
@@ -102,6 +105,8 @@ def load_library(build_if_missing: bool = True):
         "mueller_mesh_free": (None, [vp]),
         "mueller_mesh_get_info": (C.c_int, [vp, C.POINTER(CMeshInfo)]),
         "mueller_mesh_perm": (C.c_int, [vp, ip, ip]),
+        "mueller_mesh_touching": (C.c_int, [vp, ip, ip, ip, ip]),
+        "mueller_mesh_near_layout": (C.c_int, [vp, ip, ip, ip]),
         "mueller_tangent_frame": (C.c_int, [vp, i32, vp, vp]),
         "mueller_assemble": (C.c_int, [vp, C.POINTER(CParams), i32, vp, i64, vp, vp, dp, i32, vp]),
         "mueller_dz_matvec": (C.c_int, [vp, C.POINTER(CParams), i32, vp, vp, vp]),
@@ -165,6 +170,10 @@ def _dp(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
+def _ip(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
 def _dev(t, dtype, name):
     """A CUDA tensor of the given dtype, row-major contiguous (the C ABI takes
     plain pointers and assumes dense rows)."""
@@ -207,15 +216,17 @@ class Params:
 class Mesh:
     """mueller_mesh_load + mueller_tangent_frame."""
 
-    def __init__(self, xyz, tri6, morton: bool = True, stream=None):
+    def __init__(self, xyz, tri6, morton: bool = True, stream=None, host_only: bool = False):
         lib = load_library()
-        _torch()
+        if not host_only:
+            _torch()
         self.xyz = np.ascontiguousarray(xyz, dtype=np.float64)
         self.tri6 = np.ascontiguousarray(tri6, dtype=np.int32)
         h = C.c_void_p()
+        flags = (0 if morton else MESH_KEEP_ORDER) | (MESH_HOST_ONLY if host_only else 0)
         st = lib.mueller_mesh_load(_dp(self.xyz), self.xyz.shape[0],
                                    self.tri6.ctypes.data_as(C.POINTER(C.c_int32)),
-                                   self.tri6.shape[0], 0 if morton else 1, _stream(stream),
+                                   self.tri6.shape[0], flags, None if host_only else _stream(stream),
                                    C.byref(h))
         _check(st)
         self.h = h
@@ -235,6 +246,24 @@ class Mesh:
         _check(self._lib.mueller_mesh_perm(self.h, npm.ctypes.data_as(C.POINTER(C.c_int32)),
                                            epm.ctypes.data_as(C.POINTER(C.c_int32))))
         return npm, epm
+
+    def touching(self) -> dict:
+        """The touching element pairs (mueller_mesh_touching): ex, ey, cls,
+        relabel, one entry per pair, element ids in the mesh's order."""
+        n = int(self.info()["n_touching"])
+        out = {k: np.zeros(n, np.int32) for k in ("ex", "ey", "cls", "relabel")}
+        _check(self._lib.mueller_mesh_touching(self.h, *(_ip(out[k]) for k in
+                                                          ("ex", "ey", "cls", "relabel"))))
+        return out
+
+    def near_layout(self):
+        """(rowptr, col, slot) of the near-block layout (mueller_mesh_near_layout)."""
+        i = self.info()
+        rowptr = np.zeros(int(i["n_nodes"]) + 1, np.int32)
+        col = np.zeros(int(i["n_near_blocks"]), np.int32)
+        slot = np.zeros(36 * int(i["n_touching"]), np.int32)
+        _check(self._lib.mueller_mesh_near_layout(self.h, _ip(rowptr), _ip(col), _ip(slot)))
+        return rowptr, col, slot.reshape(-1, 6, 6)
 
     def tangent_frame(self, frame_rule: int = FRAME_PAPER, stream=None, out=True):
         torch = _torch()

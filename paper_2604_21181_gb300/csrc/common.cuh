@@ -97,6 +97,9 @@ struct mueller_mesh {
   int32_t* tp_order = nullptr;     // pair indices: coincident and common-edge first
   int64_t n_touch_ce = 0;          // how many of them come before the common-vertex pairs
   std::vector<int32_t> near_rowptr_h, near_col_h;
+  std::vector<mu::TouchPair> tp_h;  // host copies of tp and tp_slot
+  std::vector<int32_t> tp_slot_h;
+  bool host_only = false;           // loaded with MUELLER_MESH_HOST_ONLY: no device data
   // small device scratch
   int32_t* d_flags = nullptr;      // status words
   double* d_scal = nullptr;        // 64 doubles

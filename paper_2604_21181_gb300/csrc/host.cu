@@ -60,6 +60,9 @@ Prof::~Prof() {
   e.second += 1;
 }
 
+static const char* const kHostOnlyMsg =
+    "the mesh was loaded with MUELLER_MESH_HOST_ONLY and has no device data";
+
 static mueller_status fail(mueller_status s, const std::string& msg) {
   set_error(msg);
   return s;
@@ -289,7 +292,7 @@ mueller_status mueller_mesh_load(const double* xyz, int64_t nn, const int32_t* t
   m->nn = nn;
   m->nt = nt;
   // ---- double Morton permutation (Sec. 5)
-  if (flags & 1) {
+  if (flags & MUELLER_MESH_KEEP_ORDER) {
     m->node_perm.resize(nn);
     m->elem_perm.resize(nt);
     std::iota(m->node_perm.begin(), m->node_perm.end(), 0);
@@ -422,6 +425,13 @@ mueller_status mueller_mesh_load(const double* xyz, int64_t nn, const int32_t* t
     }
     m->nnzb = m->near_rowptr_h[nn];
   }
+  if (flags & MUELLER_MESH_HOST_ONLY) {
+    m->host_only = true;
+    m->tp_h = std::move(tp);
+    m->tp_slot_h = std::move(slot);
+    *out = m;
+    return MUELLER_OK;
+  }
   // ---- upload
   st = upload(&m->X, m->X_h.data(), m->X_h.size(), s);
   if (!st) st = upload(&m->T, m->T_h.data(), m->T_h.size(), s);
@@ -443,6 +453,8 @@ mueller_status mueller_mesh_load(const double* xyz, int64_t nn, const int32_t* t
     mueller_mesh_free(m);
     return st;
   }
+  m->tp_h = std::move(tp);
+  m->tp_slot_h = std::move(slot);
   *out = m;
   return MUELLER_OK;
 }
@@ -465,11 +477,34 @@ mueller_status mueller_mesh_perm(const mueller_mesh* m, int32_t* node_perm, int3
   return MUELLER_OK;
 }
 
+mueller_status mueller_mesh_touching(const mueller_mesh* m, int32_t* ex, int32_t* ey, int32_t* cls,
+                                     int32_t* relabel) {
+  if (!m) return fail(MUELLER_ERR_INVALID_ARG, "mesh is NULL");
+  for (size_t q = 0; q < m->tp_h.size(); ++q) {
+    const TouchPair& t = m->tp_h[q];
+    if (ex) ex[q] = t.ex;
+    if (ey) ey[q] = t.ey;
+    if (cls) cls[q] = t.cls;
+    if (relabel) relabel[q] = t.perm;
+  }
+  return MUELLER_OK;
+}
+
+mueller_status mueller_mesh_near_layout(const mueller_mesh* m, int32_t* rowptr, int32_t* col,
+                                        int32_t* slot) {
+  if (!m) return fail(MUELLER_ERR_INVALID_ARG, "mesh is NULL");
+  if (rowptr) std::copy(m->near_rowptr_h.begin(), m->near_rowptr_h.end(), rowptr);
+  if (col) std::copy(m->near_col_h.begin(), m->near_col_h.end(), col);
+  if (slot) std::copy(m->tp_slot_h.begin(), m->tp_slot_h.end(), slot);
+  return MUELLER_OK;
+}
+
 mueller_status mueller_tangent_frame(mueller_mesh* m, int32_t frame_rule, double* frame_dev,
                                      void* stream) {
   if (!m) return fail(MUELLER_ERR_INVALID_ARG, "mesh is NULL");
   if (frame_rule != MUELLER_FRAME_PAPER && frame_rule != MUELLER_FRAME_POLAR)
     return fail(MUELLER_ERR_INVALID_ARG, "unknown frame_rule");
+  if (m->host_only) return fail(MUELLER_ERR_STATE, kHostOnlyMsg);
   cudaStream_t s = (cudaStream_t)stream;
   if (!m->frame) MU_CUDA(cudaMalloc((void**)&m->frame, 9 * m->nn * sizeof(double)));
   mueller_status st = launch_frame(m, frame_rule, s);
@@ -666,6 +701,7 @@ mueller_status mueller_precond_build(const mueller_operator* op, int64_t block, 
   if (block < 1) return fail(MUELLER_ERR_INVALID_ARG, "block must be >= 1");
   if (op->dtype == MUELLER_C64_NEAR64 && !op->near_dev)
     return fail(MUELLER_ERR_INVALID_ARG, "operator lacks its near part");
+  if (op->mesh->host_only) return fail(MUELLER_ERR_STATE, kHostOnlyMsg);
   return precond_build(op, block, P, (cudaStream_t)stream);
 }
 
@@ -690,6 +726,7 @@ mueller_status mueller_solve(const mueller_operator* op, const void* B, void* X,
     return fail(MUELLER_ERR_INVALID_ARG, "GMRES_IR needs a C64_NEAR64 operator");
   if (o->use_precond && !op->precond_dev)
     return fail(MUELLER_ERR_INVALID_ARG, "use_precond set but operator has no precond_dev");
+  if (op->mesh->host_only) return fail(MUELLER_ERR_STATE, kHostOnlyMsg);
   size_t need = solve_work(op, r, o);
   if (work && work_bytes < need) return fail(MUELLER_ERR_INVALID_ARG, "workspace too small");
   auto t0 = std::chrono::steady_clock::now();
@@ -709,6 +746,7 @@ mueller_status mueller_matvec(const mueller_operator* op, const void* X, void* Y
   if (r < 1) return fail(MUELLER_ERR_INVALID_ARG, "r must be >= 1");
   if (op->dtype == MUELLER_C64_NEAR64 && !op->near_dev)
     return fail(MUELLER_ERR_INVALID_ARG, "operator lacks its near part");
+  if (op->mesh->host_only) return fail(MUELLER_ERR_STATE, kHostOnlyMsg);
   if (work && work_bytes < op_matvec_work(op, r)) return fail(MUELLER_ERR_INVALID_ARG, "workspace too small");
   return op_matvec(op, X, Y, r, work, work_bytes, (cudaStream_t)stream);
 }
@@ -723,6 +761,7 @@ mueller_status mueller_matvec_mrhs(const mueller_operator* op, const void* X, vo
   if (!op || !op->mesh || !op->Z_dev || !X || !Y) return fail(MUELLER_ERR_INVALID_ARG, "NULL argument");
   if (op->dtype != MUELLER_C64_NEAR64 || !op->near_dev)
     return fail(MUELLER_ERR_INVALID_ARG, "the tensor-core product needs a C64_NEAR64 operator");
+  if (op->mesh->host_only) return fail(MUELLER_ERR_STATE, kHostOnlyMsg);
   const int64_t N = 4 * op->mesh->nn;
   if (r < 1 || r > 128) return fail(MUELLER_ERR_INVALID_ARG, "r must be in 1..128");
   if (!work || work_bytes < mrhs_work_bytes(N, r))
