@@ -241,7 +241,8 @@ mueller_status mueller_tangent_frame(mueller_mesh* mesh, int32_t frame_rule, dou
  *   Z_dev, near_dev are overwritten (zeroed first).
  *   B_dev    optional complex128 r x N right-hand sides (Eqs. rhs_E, rhs_H)
  *            for the plane waves inc (host, r x 6: k-hat, real p-hat with
- *            p.k = 0; E_inc = p exp(i k_a k.x), H_inc = k x E_inc).
+ *            p.k = 0; E_inc = p exp(i k_a k.x), H_inc = k x E_inc; rows not
+ *            orthonormal to 1e-10 are refused with INVALID_ARG).
  * Requires mueller_tangent_frame first (else STATE).
  * Errors: INVALID_ARG, STATE, DEGENERATE_FRAME, CUDA.
  */
@@ -262,7 +263,8 @@ mueller_status mueller_assemble(mueller_mesh* mesh, const mueller_params* params
  *   Z[b], ldz[b], near[b]   per-body outputs as in mueller_assemble (near may
  *            be NULL for MUELLER_C128).
  *   B, inc, r   optional (all NULL, or all given): B[b] may be NULL for a
- *            body without right-hand sides; else inc[b] (host, r[b] x 6).
+ *            body without right-hand sides; else inc[b] (host, r[b] x 6,
+ *            orthonormal rows as for mueller_assemble).
  * Errors: INVALID_ARG (naming the body), STATE, DEGENERATE_FRAME, CUDA.
  */
 mueller_status mueller_assemble_batch(int32_t n_bodies, mueller_mesh* const* meshes,
@@ -361,8 +363,10 @@ size_t mueller_matvec_mrhs_workspace_bytes(const mueller_operator* op, int32_t r
  *   (Gauss-Legendre n_theta in cos(theta) x n_phi trapezoid in phi),
  *   C_abs = Re int j_m . (conj(j) x n).
  *   X_dev    complex128 r x N solutions.
- *   inc      host r x 6 incident waves (for C_ext).
- *   dirs     host n_dir x 3 unit directions (may be NULL if n_dir == 0).
+ *   inc      host r x 6 incident waves (for C_ext), orthonormal rows
+ *            (k-hat, p-hat) as for mueller_assemble.
+ *   dirs     host n_dir x 3 unit directions (may be NULL if n_dir == 0;
+ *            squared norms off 1 by more than 1e-10 give INVALID_ARG).
  *   F_dev    optional complex128 r x n_dir x 3 output.
  *   xs       host r x 3 output (C_ext, C_sca, C_abs).  Synchronising.
  * Errors: INVALID_ARG, STATE, CUDA.

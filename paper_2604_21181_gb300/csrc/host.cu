@@ -522,6 +522,34 @@ size_t mueller_near_bytes(const mueller_mesh* m) {
   return m ? (size_t)m->nnzb * 16 * 2 * sizeof(double) : 0;
 }
 
+// Incident waves: rows (k-hat, p-hat) of orthonormal real vectors; far-field
+// directions: unit vectors (both to 1e-10 in the squared norms and k.p).
+static mueller_status check_inc(const double* inc, int64_t r) {
+  for (int64_t q = 0; q < r; ++q) {
+    const double* k = inc + 6 * q;
+    const double* e = k + 3;
+    for (int a = 0; a < 6; ++a)
+      if (!std::isfinite(k[a]))
+        return fail(MUELLER_ERR_INVALID_ARG, "incident wave " + std::to_string(q) + " is not finite");
+    const double kk = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+    const double ee = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
+    const double ke = k[0] * e[0] + k[1] * e[1] + k[2] * e[2];
+    if (!(std::fabs(kk - 1.0) <= 1e-10 && std::fabs(ee - 1.0) <= 1e-10 && std::fabs(ke) <= 1e-10))
+      return fail(MUELLER_ERR_INVALID_ARG, "incident wave " + std::to_string(q) +
+                                               ": k-hat and p-hat must be orthonormal");
+  }
+  return MUELLER_OK;
+}
+
+static mueller_status check_dirs(const double* d, int64_t n) {
+  for (int64_t q = 0; q < n; ++q) {
+    const double dd = d[3 * q] * d[3 * q] + d[3 * q + 1] * d[3 * q + 1] + d[3 * q + 2] * d[3 * q + 2];
+    if (!(std::fabs(dd - 1.0) <= 1e-10))
+      return fail(MUELLER_ERR_INVALID_ARG, "direction " + std::to_string(q) + " is not a unit vector");
+  }
+  return MUELLER_OK;
+}
+
 static mueller_status check_params(const mueller_params* p) {
   if (!p) return fail(MUELLER_ERR_INVALID_ARG, "params is NULL");
   if (!(p->ka > 0.0) || !std::isfinite(p->ka)) return fail(MUELLER_ERR_INVALID_ARG, "ka must be positive");
@@ -573,6 +601,7 @@ mueller_status mueller_assemble(mueller_mesh* m, const mueller_params* p, int32_
   if (!Z || ldz < N) return fail(MUELLER_ERR_INVALID_ARG, "Z is NULL or ldz < N");
   if (dtype == MUELLER_C64_NEAR64 && !near) return fail(MUELLER_ERR_INVALID_ARG, "near buffer required");
   if (B && (r < 1 || !inc)) return fail(MUELLER_ERR_INVALID_ARG, "B given without r >= 1 and inc");
+  if (B && (st = check_inc(inc, r))) return st;
   if (p->frame_rule != m->frame_rule || !m->has_frame)
     return fail(MUELLER_ERR_STATE, "call mueller_tangent_frame with params->frame_rule first");
   cudaStream_t s = (cudaStream_t)stream;
@@ -655,6 +684,7 @@ mueller_status mueller_assemble_batch(int32_t n_bodies, mueller_mesh* const* mes
     if (!Z[b] || ldz[b] < N) return fail(MUELLER_ERR_INVALID_ARG, who + "Z is NULL or ldz < N");
     if (dtype == MUELLER_C64_NEAR64 && !near[b]) return fail(MUELLER_ERR_INVALID_ARG, who + "near is NULL");
     if (B && B[b] && (r[b] < 1 || !inc[b])) return fail(MUELLER_ERR_INVALID_ARG, who + "B without r >= 1 and inc");
+    if (B && B[b] && (st = check_inc(inc[b], r[b]))) return st;
     if (p->frame_rule != m->frame_rule || !m->has_frame)
       return fail(MUELLER_ERR_STATE, who + "call mueller_tangent_frame with params->frame_rule first");
     st = ensure_geometry(m, q, s);
@@ -783,6 +813,7 @@ mueller_status mueller_far_field(mueller_mesh* m, const mueller_params* p, const
   if (r < 1 || ndir < 0 || (ndir > 0 && (!dirs || !F))) return fail(MUELLER_ERR_INVALID_ARG, "bad r/n_dir");
   if (n_theta < 2 || n_phi < 3 || n_theta > 512 || n_phi > 1024)
     return fail(MUELLER_ERR_INVALID_ARG, "n_theta in 2..512, n_phi in 3..1024");
+  if ((st = check_inc(inc, r)) || (st = check_dirs(dirs, ndir))) return st;
   cudaStream_t s = (cudaStream_t)stream;
   st = ensure_geometry(m, p->q_regular, s);
   if (st) return st;
@@ -841,6 +872,7 @@ mueller_status mueller_far_field_noalloc(mueller_mesh* m, const mueller_params* 
   if (r < 1 || ndir < 0 || (ndir > 0 && (!dirs || !F))) return fail(MUELLER_ERR_INVALID_ARG, "bad r/n_dir");
   if (n_theta < 2 || n_phi < 3 || n_theta > 512 || n_phi > 1024)
     return fail(MUELLER_ERR_INVALID_ARG, "n_theta in 2..512, n_phi in 3..1024");
+  if ((st = check_inc(inc, r)) || (st = check_dirs(dirs, ndir))) return st;
   // the point geometry is allocated by mueller_assemble / mueller_far_field;
   // this variant never allocates, so it must already exist for the rule
   if (!m->has_frame || p->frame_rule != m->frame_rule || m->qd_q != p->q_regular)

@@ -131,7 +131,7 @@ def test_host_only_handle_refuses_device_work():
     assert lib.mueller_assemble(h, C.byref(p), api.MUELLER_C128, fake, 1 << 20, None, None, None,
                                 0, None) == STATE
     assert lib.mueller_dz_matvec(h, C.byref(p), 1, fake, fake, None) == STATE
-    inc = np.zeros((1, 6))
+    inc = np.ascontiguousarray(workloads.plane_wave().reshape(1, 6))
     xs = np.zeros((1, 3))
     dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))  # noqa: E731
     assert lib.mueller_far_field(h, C.byref(p), fake, 1, dp(inc), None, 0, None, dp(xs), 8, 16,
@@ -147,4 +147,51 @@ def test_host_only_handle_refuses_device_work():
     assert lib.mueller_solve(C.byref(op), fake, fake, 1, C.byref(o), C.byref(info), None, 0,
                              None) == STATE
     assert m.near_bytes() == 32 * 8 * m.info()["n_near_blocks"]
+    m.free()
+
+
+def test_incident_waves_and_directions_are_checked():
+    """Rows (k-hat, p-hat) must be orthonormal and far-field directions unit
+    vectors: INVALID_ARG before any device work (here before the missing
+    frame of a host-only mesh would give STATE)."""
+    lib = api.load_library()
+    xyz, tri6 = MESHES["sphere_L0"]
+    m = api.Mesh(xyz, tri6, host_only=True)
+    p = api.CParams(ka=1.0, q_regular=6, ssq_order=4, frame_rule=0)
+    p.eps_r[0], p.mu_r[0] = 2.0, 1.0
+    buf = C.create_string_buffer(64)
+    fake = C.cast(buf, C.c_void_p)
+    dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))  # noqa: E731
+    good = np.ascontiguousarray(workloads.fibonacci_plane_waves(2))
+    xs = np.zeros((4, 3))
+    bad_rows = []
+    b = good.copy()
+    b[0, 3:] = good[0, :3]  # p parallel to k
+    bad_rows.append((0, b))
+    b = good.copy()
+    b[1, :3] *= 1.001  # k not a unit vector
+    bad_rows.append((1, b))
+    b = good.copy()
+    b[2, 3:] = (good[2, 3:] + 0.1 * good[2, :3]) / np.linalg.norm(good[2, 3:] + 0.1 * good[2, :3])
+    bad_rows.append((2, b))  # unit p, not orthogonal to k
+    b = good.copy()
+    b[3, 5] = np.nan
+    bad_rows.append((3, b))
+    for row, b in bad_rows:
+        assert lib.mueller_assemble(m.h, C.byref(p), api.MUELLER_C128, fake, 1 << 20, None, fake,
+                                    dp(b), 4, None) == 1
+        assert ("incident wave %d" % row) in lib.mueller_last_error().decode()
+        for fn in (lib.mueller_far_field, lib.mueller_far_field_noalloc):
+            assert fn(m.h, C.byref(p), fake, 4, dp(b), None, 0, None, dp(xs), 8, 16, None) == 1
+    # the well-formed waves pass the checks and meet the missing frame
+    assert lib.mueller_assemble(m.h, C.byref(p), api.MUELLER_C128, fake, 1 << 20, None, fake,
+                                dp(good), 4, None) == STATE
+    dirs = np.ascontiguousarray(workloads.fibonacci_directions(5))
+    F = fake
+    assert lib.mueller_far_field(m.h, C.byref(p), fake, 4, dp(good), dp(dirs), 5, F, dp(xs), 8, 16,
+                                 None) == STATE
+    dirs[2] *= 1.01
+    for fn in (lib.mueller_far_field, lib.mueller_far_field_noalloc):
+        assert fn(m.h, C.byref(p), fake, 4, dp(good), dp(dirs), 5, F, dp(xs), 8, 16, None) == 1
+        assert "direction 2" in lib.mueller_last_error().decode()
     m.free()
