@@ -86,6 +86,12 @@ enum {
   MUELLER_MESH_HOST_ONLY = 2   /* build the host tables only: no device data */
 };
 
+/* Quadrature tables (mueller_quadrature_rule) */
+enum {
+  MUELLER_RULE_TRIANGLE = 0,       /* symmetric rule on the reference triangle */
+  MUELLER_RULE_GAUSS_LEGENDRE = 1  /* Gauss-Legendre on [0, 1]                 */
+};
+
 typedef struct mueller_mesh mueller_mesh;
 
 typedef struct {
@@ -144,6 +150,21 @@ typedef struct {
   const void* precond_dev;  /* factors from mueller_precond_build or NULL    */
   int64_t block;            /* cluster size B used to build precond_dev      */
 } mueller_operator;
+
+/*
+ * mueller_quadrature_rule -- the quadrature tables the library derives on the
+ * host and uses: the regular-pair triangle rules (Sec. 5.1; 6 points of
+ * degree 4, 12 points of degree 6, from their moment equations) and
+ * Gauss-Legendre (the Sauter-Schwab tensor rules of Sec. 4.2, the far-field
+ * sphere rule in cos(theta)).  Host outputs of n entries:
+ *   MUELLER_RULE_TRIANGLE        n = 6 or 12; a = xi, b = eta on the
+ *                                reference triangle {xi, eta >= 0,
+ *                                xi + eta <= 1}; w sums to its area 1/2.
+ *   MUELLER_RULE_GAUSS_LEGENDRE  n in 1..512; a = nodes on [0, 1] ascending,
+ *                                w sums to 1; b unused (may be NULL).
+ * Errors: INVALID_ARG (kind, n, NULL outputs).
+ */
+mueller_status mueller_quadrature_rule(int32_t kind, int32_t n, double* a, double* b, double* w);
 
 /* Library version; text of the calling thread's last error. */
 int32_t mueller_version(void);

@@ -22,6 +22,8 @@ MUELLER_OP_K1_MIRRORED = 1
 SOLVE_DENSE_LU = 0
 SOLVE_GMRES = 1
 SOLVE_GMRES_IR = 2
+RULE_TRIANGLE = 0
+RULE_GAUSS_LEGENDRE = 1
 MESH_KEEP_ORDER = 1
 MESH_HOST_ONLY = 2
 FRAME_PAPER = 0
@@ -72,7 +74,7 @@ class COperator(C.Structure):
 EXPORTS = [
     "mueller_version", "mueller_last_error", "mueller_status_string", "mueller_mesh_load",
     "mueller_mesh_free", "mueller_mesh_get_info", "mueller_mesh_perm", "mueller_mesh_touching",
-    "mueller_mesh_near_layout", "mueller_tangent_frame",
+    "mueller_mesh_near_layout", "mueller_quadrature_rule", "mueller_tangent_frame",
     "mueller_assemble", "mueller_dz_matvec", "mueller_near_bytes", "mueller_precond_build",
     "mueller_precond_bytes",
     "mueller_solve", "mueller_solve_workspace_bytes", "mueller_matvec",
@@ -106,6 +108,7 @@ def load_library(build_if_missing: bool = True):
         "mueller_mesh_get_info": (C.c_int, [vp, C.POINTER(CMeshInfo)]),
         "mueller_mesh_perm": (C.c_int, [vp, ip, ip]),
         "mueller_mesh_touching": (C.c_int, [vp, ip, ip, ip, ip]),
+        "mueller_quadrature_rule": (C.c_int, [i32, i32, dp, dp, dp]),
         "mueller_mesh_near_layout": (C.c_int, [vp, ip, ip, ip]),
         "mueller_tangent_frame": (C.c_int, [vp, i32, vp, vp]),
         "mueller_assemble": (C.c_int, [vp, C.POINTER(CParams), i32, vp, i64, vp, vp, dp, i32, vp]),
@@ -140,6 +143,16 @@ def load_library(build_if_missing: bool = True):
         f.argtypes = args
     _lib = lib
     return lib
+
+
+def quadrature_rule(kind: int, n: int):
+    """(a, b, w) of mueller_quadrature_rule: (xi, eta, w) of a triangle rule,
+    (x, None, w) of Gauss-Legendre on [0, 1]."""
+    lib = load_library()
+    a, b, w = np.zeros(n), np.zeros(n), np.zeros(n)
+    _check(lib.mueller_quadrature_rule(int(kind), int(n), _dp(a),
+                                       _dp(b) if kind == RULE_TRIANGLE else None, _dp(w)))
+    return a, (b if kind == RULE_TRIANGLE else None), w
 
 
 def _check(status: int):

@@ -477,6 +477,28 @@ mueller_status mueller_mesh_perm(const mueller_mesh* m, int32_t* node_perm, int3
   return MUELLER_OK;
 }
 
+mueller_status mueller_quadrature_rule(int32_t kind, int32_t n, double* a, double* b, double* w) {
+  if (!a || !w) return fail(MUELLER_ERR_INVALID_ARG, "a or w is NULL");
+  if (kind == MUELLER_RULE_TRIANGLE) {
+    TriangleRule r;
+    if (!b) return fail(MUELLER_ERR_INVALID_ARG, "b is NULL");
+    if ((n != 6 && n != 12) || !triangle_rule(n, r))
+      return fail(MUELLER_ERR_INVALID_ARG, "triangle rules have 6 or 12 points");
+    std::copy(r.xi.begin(), r.xi.end(), a);
+    std::copy(r.eta.begin(), r.eta.end(), b);
+    std::copy(r.w.begin(), r.w.end(), w);
+  } else if (kind == MUELLER_RULE_GAUSS_LEGENDRE) {
+    if (n < 1 || n > 512) return fail(MUELLER_ERR_INVALID_ARG, "Gauss-Legendre n in 1..512");
+    std::vector<double> x, ww;
+    gauss_legendre_unit(n, x, ww);
+    std::copy(x.begin(), x.end(), a);
+    std::copy(ww.begin(), ww.end(), w);
+  } else {
+    return fail(MUELLER_ERR_INVALID_ARG, "unknown rule kind");
+  }
+  return MUELLER_OK;
+}
+
 mueller_status mueller_mesh_touching(const mueller_mesh* m, int32_t* ex, int32_t* ey, int32_t* cls,
                                      int32_t* relabel) {
   if (!m) return fail(MUELLER_ERR_INVALID_ARG, "mesh is NULL");
