@@ -71,6 +71,7 @@ def _load():
                 "oracle_classify": (I, [P, I64, I64, I, ip, ip]),
                 "oracle_ssq_singular": (I, [P, I64, I64, I, I, dp]),
                 "oracle_ssq_test": (D, [P, I64, I64, I, I, I]),
+                "oracle_brute_singular": (I, [P, I64, I64, I, dp]),
                 "oracle_pair_block": (I, [P, D, D, D, D, D, I, I, I64, I64, dp]),
                 "oracle_ssq_full": (I, [P, D, D, D, D, D, I64, I64, I, dp]),
                 "oracle_assemble": (None, [P, D, D, D, D, D, I, I, I, dp, ip, I64]),
@@ -206,6 +207,14 @@ class Mesh:
     def ssq_singular(self, ex, ey, ns, alt=False):
         out = np.zeros((6, 6, 8))
         c = self._lib.oracle_ssq_singular(self.h, ex, ey, ns, int(alt), _d(out))
+        return c, out
+
+    def brute_singular(self, ex, ey, n):
+        """G1, G2 of a touching pair by the brute-force route (relative polar
+        coordinates over the unfolded pair, no Sauter-Schwab map): (class,
+        array 6 x 6 x 8) like ssq_singular."""
+        out = np.zeros((6, 6, 8))
+        c = self._lib.oracle_brute_singular(self.h, ex, ey, n, _d(out))
         return c, out
 
     def ssq_test(self, ex, ey, ns, which, alt=False):

@@ -1038,6 +1038,243 @@ static C3 far_amp(const Mesh& m, const std::vector<std::vector<Geo>>& G, const T
   return C3{pre * (tN.x - rL.x), pre * (tN.y - rL.y), pre * (tN.z - rL.z)};
 }
 
+// ============================================ brute-force singular integrals
+// A second, independent route to the singular integrals G1, G2 of a touching
+// pair (Eqs. kappa_S, kappa2_S, the integrals that ssq_singular takes by
+// Sauter-Schwab), used only to pin ssq_singular: no Sauter-Schwab map, no
+// relabelling table.  The test element's parametric triangle T and the trial
+// element's triangle T' placed in the same plane by an affine map A --
+// coincident: A = identity; common edge: T' folded across the shared edge so
+// that the two parametrisations of that edge coincide; common vertex: T'
+// reflected through the shared corner -- turn the pair integral into one over
+// p in T and q in A(T'), singular only at q = p.  In relative polar
+// coordinates q = p + rho e(theta),
+//   int_T int_A(T') F dq dp = int dtheta int rho drho
+//                              int_{T cap (A(T') - rho e)} F(p, p + rho e) dp,
+// and the factor rho cancels the 1/R of the kernels (R >= c rho on these
+// placements), so every integrand below is bounded and analytic on its
+// piece.  The polygon T cap (A(T') - rho e) is cut from the six edge
+// half-planes; theta is split at the directions where the polygon's shape
+// changes (edge directions and corner-to-corner vectors), rho at the values
+// where three edge lines meet.  Tensor Gauss-Legendre on every piece then
+// converges exponentially in the order n (checked in the tests by raising n).
+struct P2d {
+  double x, y;
+};
+
+static double cross2(P2d a, P2d b) { return a.x * b.y - a.y * b.x; }
+
+// half-plane a.p <= b
+struct HalfPlane {
+  double ax, ay, b;
+};
+
+// the three half-planes of a triangle (either orientation)
+static void tri_halfplanes(const P2d v[3], HalfPlane h[3]) {
+  const double s = cross2(P2d{v[1].x - v[0].x, v[1].y - v[0].y},
+                          P2d{v[2].x - v[0].x, v[2].y - v[0].y}) > 0 ? 1.0 : -1.0;
+  for (int k = 0; k < 3; ++k) {
+    const P2d a = v[k], b = v[(k + 1) % 3];
+    // outward normal of edge a -> b for a counter-clockwise triangle
+    const double nx = s * (b.y - a.y), ny = -s * (b.x - a.x);
+    h[k] = HalfPlane{nx, ny, nx * a.x + ny * a.y};
+  }
+}
+
+// Sutherland-Hodgman: clip polygon P by a.p <= b
+static std::vector<P2d> clip(const std::vector<P2d>& P, double ax, double ay, double b) {
+  std::vector<P2d> out;
+  const size_t n = P.size();
+  for (size_t i = 0; i < n; ++i) {
+    const P2d c = P[i], d = P[(i + 1) % n];
+    const double fc = ax * c.x + ay * c.y - b, fd = ax * d.x + ay * d.y - b;
+    if (fc <= 0) out.push_back(c);
+    if ((fc < 0 && fd > 0) || (fc > 0 && fd < 0)) {
+      const double t = fc / (fc - fd);
+      out.push_back(P2d{c.x + t * (d.x - c.x), c.y + t * (d.y - c.y)});
+    }
+  }
+  return out;
+}
+
+static double poly_area(const std::vector<P2d>& P) {
+  double a = 0;
+  for (size_t i = 0; i < P.size(); ++i) a += cross2(P[i], P[(i + 1) % P.size()]);
+  return 0.5 * a;
+}
+
+// G[i][j][0..3] = G1, G[i][j][4..7] = G2 (node i of ex, node j of ey, the
+// elements' own node order; component 2a + b for s_a or t_a at x, t_b at y)
+static int brute_singular(const Mesh& m, int64_t ex, int64_t ey, int n, double G[6][6][8]) {
+  const int32_t* tx = &m.T[6 * ex];
+  const int32_t* ty = &m.T[6 * ey];
+  int sx[3], sy[3], nsh = 0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      if (tx[i] == ty[j]) {
+        sx[nsh] = i;
+        sy[nsh] = j;
+        ++nsh;
+      }
+  if (nsh == 0) return 0;
+  const P2d C[3] = {{0.0, 0.0}, {1.0, 0.0}, {0.0, 1.0}};  // canonical corners
+  // images of the trial element's corners in the test element's plane
+  P2d img[3];
+  if (nsh == 3) {
+    for (int j = 0; j < 3; ++j)
+      for (int k = 0; k < 3; ++k)
+        if (sy[k] == j) img[j] = C[sx[k]];
+  } else if (nsh == 2) {
+    const P2d a = C[sx[0]], b = C[sx[1]], c = C[3 - sx[0] - sx[1]];
+    // reflection of the test element's third corner across the shared edge
+    const double dx = b.x - a.x, dy = b.y - a.y, t = ((c.x - a.x) * dx + (c.y - a.y) * dy) /
+                                                     (dx * dx + dy * dy);
+    const P2d foot{a.x + t * dx, a.y + t * dy};
+    img[sy[0]] = a;
+    img[sy[1]] = b;
+    img[3 - sy[0] - sy[1]] = P2d{2 * foot.x - c.x, 2 * foot.y - c.y};
+  } else {
+    const P2d a = C[sx[0]];
+    const int i1 = (sx[0] + 1) % 3, i2 = (sx[0] + 2) % 3;
+    img[sy[0]] = a;
+    img[(sy[0] + 1) % 3] = P2d{2 * a.x - C[i1].x, 2 * a.y - C[i1].y};
+    img[(sy[0] + 2) % 3] = P2d{2 * a.x - C[i2].x, 2 * a.y - C[i2].y};
+  }
+  // A maps the trial element's parametric point (xi, eta) to
+  // img0 + xi (img1 - img0) + eta (img2 - img0); its inverse takes q back
+  const P2d e1{img[1].x - img[0].x, img[1].y - img[0].y};
+  const P2d e2{img[2].x - img[0].x, img[2].y - img[0].y};
+  const double detA = cross2(e1, e2);
+  auto to_trial = [&](P2d q, double& xi, double& eta) {
+    const P2d d{q.x - img[0].x, q.y - img[0].y};
+    xi = cross2(d, e2) / detA;
+    eta = cross2(e1, d) / detA;
+  };
+  HalfPlane hx[3], hy[3];
+  tri_halfplanes(C, hx);
+  tri_halfplanes(img, hy);
+  // critical directions: edges of both triangles and corner-to-corner vectors
+  std::vector<double> crit;
+  auto add_dir = [&](double x, double y) {
+    if (std::hypot(x, y) < 1e-14) return;
+    double a = std::atan2(y, x);
+    if (a < 0) a += 2 * PI;
+    crit.push_back(a);
+    double b = a + PI;
+    if (b >= 2 * PI) b -= 2 * PI;
+    crit.push_back(b);
+  };
+  for (int k = 0; k < 3; ++k) {
+    add_dir(C[(k + 1) % 3].x - C[k].x, C[(k + 1) % 3].y - C[k].y);
+    add_dir(img[(k + 1) % 3].x - img[k].x, img[(k + 1) % 3].y - img[k].y);
+    for (int j = 0; j < 3; ++j) add_dir(img[j].x - C[k].x, img[j].y - C[k].y);
+  }
+  crit.push_back(0.0);
+  crit.push_back(2 * PI);
+  std::sort(crit.begin(), crit.end());
+  std::vector<double> th;
+  for (double a : crit)
+    if (th.empty() || a - th.back() > 1e-12) th.push_back(a);
+  std::vector<double> g, gw;
+  gauss_legendre01(n, g, gw);
+  // one work item per (theta piece, theta node)
+  const int npiece = (int)th.size() - 1;
+  std::vector<double> acc((size_t)npiece * n * 288, 0.0);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int item = 0; item < npiece * n; ++item) {
+    const int ip = item / n, it = item % n;
+    const double t0 = th[ip], t1 = th[ip + 1];
+    const double theta = t0 + (t1 - t0) * g[it];
+    const double wth = (t1 - t0) * gw[it];
+    const P2d e{std::cos(theta), std::sin(theta)};
+    // lines a.p = b + rho c: test triangle (c = 0), shifted trial triangle
+    double la[6][2], lb[6], lc[6];
+    for (int k = 0; k < 3; ++k) {
+      la[k][0] = hx[k].ax;
+      la[k][1] = hx[k].ay;
+      lb[k] = hx[k].b;
+      lc[k] = 0.0;
+      la[3 + k][0] = hy[k].ax;
+      la[3 + k][1] = hy[k].ay;
+      lb[3 + k] = hy[k].b;
+      lc[3 + k] = -(hy[k].ax * e.x + hy[k].ay * e.y);
+    }
+    std::vector<double> br{0.0};
+    for (int a = 0; a < 6; ++a)
+      for (int b = a + 1; b < 6; ++b)
+        for (int c = b + 1; c < 6; ++c) {
+          auto det3 = [&](const double* col) {
+            return la[a][0] * (la[b][1] * col[c] - la[c][1] * col[b]) -
+                   la[a][1] * (la[b][0] * col[c] - la[c][0] * col[b]) +
+                   col[a] * (la[b][0] * la[c][1] - la[c][0] * la[b][1]);
+          };
+          const double D0 = det3(lb), D1 = det3(lc);
+          if (std::fabs(D1) < 1e-14) continue;
+          const double r = -D0 / D1;
+          if (r > 1e-13 && r < 10.0) br.push_back(r);
+        }
+    std::sort(br.begin(), br.end());
+    double* out = &acc[(size_t)item * 288];
+    for (size_t k = 0; k + 1 < br.size(); ++k) {
+      const double r0 = br[k], r1 = br[k + 1];
+      if (r1 - r0 < 1e-13) continue;
+      for (int ir = 0; ir < n; ++ir) {
+        const double rho = r0 + (r1 - r0) * g[ir];
+        const double wr = (r1 - r0) * gw[ir] * rho * wth;
+        std::vector<P2d> P(C, C + 3);
+        for (int j = 0; j < 3 && !P.empty(); ++j)
+          P = clip(P, hy[j].ax, hy[j].ay, hy[j].b - rho * (hy[j].ax * e.x + hy[j].ay * e.y));
+        if (P.size() < 3 || std::fabs(poly_area(P)) < 1e-300) continue;
+        for (size_t f = 1; f + 1 < P.size(); ++f) {
+          const P2d A0 = P[0], B0 = P[f], C0 = P[f + 1];
+          const double jac = std::fabs(cross2(P2d{B0.x - A0.x, B0.y - A0.y},
+                                              P2d{C0.x - A0.x, C0.y - A0.y}));
+          for (int is = 0; is < n; ++is)
+            for (int jt = 0; jt < n; ++jt) {
+              const double s = g[is], t = g[jt];
+              const P2d p{A0.x + s * ((1 - t) * (B0.x - A0.x) + t * (C0.x - A0.x)),
+                          A0.y + s * ((1 - t) * (B0.y - A0.y) + t * (C0.y - A0.y))};
+              const double wp = gw[is] * gw[jt] * s * jac;
+              double yxi, yeta;
+              to_trial(P2d{p.x + rho * e.x, p.y + rho * e.y}, yxi, yeta);
+              const Geo gx = geo_at(m, ex, p.x, p.y);
+              const Geo gy = geo_at(m, ey, yxi, yeta);
+              const V3 d = gx.x - gy.x;
+              const double R = norm(d);
+              const V3 u = (1.0 / R) * d;
+              const double w = wr * wp * gx.J * gy.J / std::fabs(detA);
+              const double nu = dot(gx.n, u);
+              double k1[4], k2[4];
+              for (int a = 0; a < 2; ++a)
+                for (int b = 0; b < 2; ++b) {
+                  const double ty_b_u = dot(gy.t[b], u);
+                  k1[2 * a + b] = (dot(gx.s[a], gy.t[b]) + dot(gx.s[a], u) * ty_b_u) / R;
+                  k2[2 * a + b] =
+                      (dot(gx.t[a], gy.t[b]) * nu - dot(gx.t[a], u) * dot(gx.n, gy.t[b])) / (R * R);
+                }
+              for (int i = 0; i < 6; ++i)
+                for (int j = 0; j < 6; ++j) {
+                  const double nn = w * gx.N[i] * gy.N[j];
+                  for (int c = 0; c < 4; ++c) {
+                    out[(i * 6 + j) * 8 + c] += nn * k1[c];
+                    out[(i * 6 + j) * 8 + 4 + c] += nn * k2[c];
+                  }
+                }
+            }
+        }
+      }
+    }
+  }
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j)
+      for (int c = 0; c < 8; ++c) {
+        double s = 0;
+        for (int item = 0; item < npiece * n; ++item) s += acc[(size_t)item * 288 + (i * 6 + j) * 8 + c];
+        G[i][j][c] = s;
+      }
+  return nsh;
+}
+
 // ================================================================ C API
 struct OracleMesh {
   Mesh m;
@@ -1323,6 +1560,21 @@ void oracle_rhs(void* h, double ka, double er_re, double er_im, double mr_re, do
   Mesh& m = ((OracleMesh*)h)->m;
   Params pr{ka, er_re, er_im, mr_re, mr_im, q_regular, 5};
   rhs(m, pr, inc, r, (cd*)B);
+}
+
+// singular integrals of a touching pair by the brute-force route (pin of
+// ssq_singular): out[6][6][8] = (G1[4], G2[4]), the elements' own node
+// order; n = Gauss order of every direction of every piece.  Returns the
+// number of shared corners (0: not a touching pair, nothing written).
+int oracle_brute_singular(void* h, int64_t ex, int64_t ey, int n, double* out) {
+  Mesh& m = ((OracleMesh*)h)->m;
+  double G[6][6][8];
+  int c = brute_singular(m, ex, ey, n, G);
+  if (c == 0) return 0;
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j)
+      for (int k = 0; k < 8; ++k) out[(i * 6 + j) * 8 + k] = G[i][j][k];
+  return c;
 }
 
 // Mass matrix of the scalar P2 Gram (Eq. mass_matrix), dense nn x nn, real.
