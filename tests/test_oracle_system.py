@@ -48,16 +48,23 @@ def _solve(level, p, inc=INC, frame_rule=1):
 
 
 def test_cross_sections_converge_to_mie():
+    """Config-1 physics (eps_r = 4, k_a = 1), polar frame rule, Q = 6,
+    Ns = 5: the errors of C_ext, C_sca and C_abs (exactly 0 for this
+    lossless sphere) against Mie fall at least as h^1.9 from level 1 to 2
+    (measured slopes 2.0, 2.3, 2.2; the GPU table to level 4 gives 2.0-2.4:
+    the frame turns by O(1) inside the elements around the poles, so the
+    current components there are represented only to O(1) on an O(h^2)
+    area), and the energy balance holds to discretisation accuracy."""
     ref = mie.mie_bh(P1["ka"], P1["eps_r"][0])
     errs = []
     for L in (1, 2):
         m, Z, B, X = _solve(L, P1)
         _, xs = m.far_field(P1, X, INC)
-        errs.append(abs(xs[0, 0] - ref[0]) / ref[0])
-        # energy balance to discretisation accuracy; C_abs -> 0 (lossless)
+        errs.append(np.abs(xs[0] - ref) / ref[0])
         assert abs(xs[0, 0] - xs[0, 1] - xs[0, 2]) / xs[0, 0] < 0.05
-    assert errs[1] < 3e-3, errs
-    assert errs[1] < errs[0] / 3, errs
+    slopes = np.log2(errs[0] / errs[1])  # h halves per level
+    assert np.all(slopes >= 1.9), (errs, slopes)
+    assert errs[1][0] < 2e-3, errs
 
 
 def test_zero_contrast_scatters_nothing():
