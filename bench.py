@@ -59,6 +59,13 @@ def parse(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-extras", action="store_true", help="skip the untimed extra measurements")
+    # one untimed invocation of part of the path on a sphere, for profiler
+    # captures (ncu -k <kernel> ... python bench.py --profile-case assemble)
+    ap.add_argument("--profile-case", default=None,
+                    choices=["assemble", "assemble64", "precond", "solve", "mrhs"])
+    ap.add_argument("--level", type=int, default=2, help="--profile-case: icosphere level")
+    ap.add_argument("--rhs", type=int, default=16, help="--profile-case mrhs: right-hand sides")
+    ap.add_argument("--block", type=int, default=256, help="--profile-case: cluster size B")
     return ap.parse_args(argv)
 
 
@@ -370,7 +377,7 @@ def run_ours(args):
         extras["multibody64"] = multibody64(mu, torch, dev)
         extras["lspr_sweep"] = lspr_sweep(mu, torch, dev)
         extras["gradients_L3"] = gradients_l3(mu, torch, dev)
-        cpu = cpu_baseline(args.workload, budget_s=15.0)
+        cpu = cpu_baseline(args.workload)
 
     if rank == 0:
         line = {
@@ -600,19 +607,70 @@ def oracle_sample(workload: str, n_test_elems: int):
     return n_ex * om.nt, dt, oracle.num_threads()
 
 
-def cpu_baseline(workload: str, budget_s: float = 15.0):
+def oracle_step(workload: str) -> dict:
+    """The oracle's whole step on the workload, the same scope as one GPU
+    step: mesh (Morton, frame), FP64 assembly, right-hand side, Morton
+    block-Jacobi build + GMRES(m) to the workload's tolerance (complex128
+    throughout), far field and cross sections.  Seconds per part."""
+    import oracle
+
     xyz, tri6, inc, w = workloads.workload(workload)
-    F = tri6.shape[0]
-    n = max(1, F // 64)
-    pairs, dt, th = oracle_sample(workload, n)
-    # grow the sample towards the time budget (10-30 s of CPU work)
-    if dt < budget_s / 4 and n < F:
-        n2 = min(F, int(n * budget_s / max(dt, 1e-3)))
-        pairs, dt, th = oracle_sample(workload, n2)
-        n = n2
-    return {"value": pairs / dt, "unit": UNIT, "cores": th, "kind": "oracle",
-            "sample": f"oracle FP64 assembly of the Z rows of the nodes of {n} of {F} test "
-                      f"elements ({pairs} element pairs incl. Sauter-Schwab), {dt:.1f} s"}
+    pw = dict(ka=w["ka"], eps_r=w["eps_r"], mu_r=w["mu_r"], q_regular=w["q_regular"],
+              ssq_order=w["ssq_order"])
+    t = [time.perf_counter()]
+    om = oracle.Mesh(xyz, tri6)
+    om.frame()
+    t.append(time.perf_counter())
+    Z = om.assemble(pw)
+    t.append(time.perf_counter())
+    B = om.rhs(pw, inc)
+    X = np.zeros_like(B)
+    for s in range(B.shape[0]):
+        X[s], _ = oracle.gmres(Z, B[s], block=int(w["block"]), restart=int(w["restart"]),
+                               tol=float(w["tol"]))
+    t.append(time.perf_counter())
+    om.far_field(pw, X, inc)
+    t.append(time.perf_counter())
+    return {"mesh_s": t[1] - t[0], "assembly_s": t[2] - t[1], "solve_s": t[3] - t[2],
+            "far_field_s": t[4] - t[3], "total_s": t[4] - t[0], "threads": oracle.num_threads(),
+            "element_pairs": float(tri6.shape[0]) ** 2}
+
+
+def oracle_single_thread(workload: str, n_test_elems: int):
+    """oracle_sample in a child process limited to one OpenMP thread (the
+    plain-loop baseline).  Returns (pairs, seconds, threads) or None."""
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.oracle_sample(%r, %d)))" % (ROOT, workload, n_test_elems))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                           timeout=300)
+        return tuple(json.loads(r.stdout.strip().splitlines()[-1]))
+    except Exception:
+        return None
+
+
+def cpu_baseline(workload: str):
+    """The oracle timed on the host cores: its whole step once (value, in
+    the metric's unit), its assembly alone, and an assembly sample on one
+    thread."""
+    st = oracle_step(workload)
+    F = int(round(st["element_pairs"] ** 0.5))
+    n1 = max(1, F // 64)
+    one = oracle_single_thread(workload, n1)
+    out = {"value": st["element_pairs"] / st["total_s"], "unit": UNIT, "cores": st["threads"],
+           "kind": "oracle",
+           "sample": (f"one whole oracle step of the workload (mesh + frame, FP64 assembly of all "
+                      f"{F * F} element pairs, RHS, block-Jacobi + GMRES to tol, far field): "
+                      f"{st['total_s']:.2f} s on {st['threads']} threads"),
+           "parts_s": {k: round(v, 3) for k, v in st.items() if k.endswith("_s")},
+           "assembly_only_pairs_per_s": st["element_pairs"] / st["assembly_s"]}
+    if one is not None:
+        out["single_thread"] = {"value": one[0] / one[1], "unit": UNIT, "cores": 1,
+                                "sample": f"FP64 assembly of the Z rows of the nodes of {n1} of "
+                                          f"{F} test elements ({one[0]} element pairs), "
+                                          f"{one[1]:.2f} s, OMP_NUM_THREADS=1"}
+    return out
 
 
 def run_reference(args):
@@ -622,14 +680,13 @@ def run_reference(args):
         return
     xyz, tri6, inc, w = workloads.workload(args.workload)
     F = tri6.shape[0]
-    n = max(1, F // 64)
+    # warm-up: page the oracle in on a small assembly sample
     for _ in range(args.warmup):
-        oracle_sample(args.workload, max(1, n // 4))
-    tot_pairs, tot_s, th = 0, 0.0, 1
-    for _ in range(args.steps):
-        pairs, dt, th = oracle_sample(args.workload, n)
-        tot_pairs += pairs
-        tot_s += dt
+        oracle_sample(args.workload, max(1, F // 256))
+    steps = [oracle_step(args.workload) for _ in range(args.steps)]
+    tot_s = sum(s["total_s"] for s in steps)
+    tot_pairs = sum(s["element_pairs"] for s in steps)
+    th = steps[-1]["threads"]
     value = tot_pairs / tot_s
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(1e3 * tot_s / args.steps, 3),
@@ -637,14 +694,53 @@ def run_reference(args):
             "data": "synthetic", "impl": "reference",
             "config": {"workload": args.workload, "n_tri": F, "parallelism": "host cores"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": th, "kind": "oracle",
-                             "sample": f"per step: oracle FP64 assembly of the Z rows of the nodes "
-                                       f"of {n} of {F} test elements"},
+                             "sample": "per step: the oracle's whole step (mesh + frame, FP64 "
+                                       "assembly of all element pairs, RHS, block-Jacobi + "
+                                       "GMRES to tol, far field), the scope of one GPU step",
+                             "assembly_s_per_step": round(sum(s["assembly_s"] for s in steps)
+                                                          / args.steps, 3)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
+def profile_case(args):
+    """One untimed run of part of the hot path on the level-L sphere (eps_r =
+    2.25, k_a = 5, Q = 6, Ns = 5), for profiler captures, then exit:
+      assemble    tangent frame + mixed assembly (regular pairs FP32)
+      assemble64  tangent frame + FP64 assembly
+      precond     mixed assembly + block-Jacobi build (FP64 LU, FP32 inverse)
+      solve       mixed assembly + block-Jacobi + one GMRES-IR solve
+      mrhs        mixed assembly + one tensor-core product of --rhs vectors
+    """
+    import torch
+
+    import paper_2604_21181_gb300 as mu
+
+    xyz, tri6 = workloads.icosphere_p2(args.level)
+    p = mu.Params(ka=5.0, eps_r=(2.25, 0.0), q_regular=6, ssq_order=5)
+    mesh = mu.Mesh(xyz, tri6)
+    mesh.tangent_frame(p.frame_rule, out=False)
+    inc = workloads.plane_wave()
+    dtype = mu.MUELLER_C128 if args.profile_case == "assemble64" else mu.MUELLER_C64_NEAR64
+    Z, near, B = mu.assemble(mesh, p, dtype, inc=inc)
+    op = mu.Operator(mesh, Z, near, dtype)
+    if args.profile_case in ("precond", "solve"):
+        mu.precond_build(op, args.block)
+    if args.profile_case == "solve":
+        mu.solve(op, B, mu.SolverOpts(mode=mu.SOLVE_GMRES_IR, restart=50, tol=1e-8))
+    if args.profile_case == "mrhs":
+        g = torch.Generator().manual_seed(1)
+        X = torch.randn((args.rhs, mesh.N), dtype=torch.complex64, generator=g).cuda()
+        mu.matvec_mrhs(op, X)
+    torch.cuda.synchronize()
+    print("ok", args.profile_case, "level", args.level, "N", mesh.N)
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        profile_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -69,3 +69,27 @@ def test_reference_arm_prints_from_rank_zero_only(monkeypatch):
     with redirect_stdout(buf):
         bench.run_reference(bench.parse(["--impl", "reference"]))
     assert buf.getvalue() == ""
+
+
+def test_reference_arm_times_the_whole_oracle_step(monkeypatch):
+    """The reference arm (rank 0, N = 1) prints one JSON line whose value is
+    element pairs per second of the oracle's whole step (the scope of one
+    GPU step), on the small level-1 workload here."""
+    import json
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    monkeypatch.setenv("RANK", "0")
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        bench.run_reference(bench.parse(["--impl", "reference", "--steps", "2", "--warmup", "1",
+                                         "--workload", "sphere_L1_eps4_ka1"]))
+    line = json.loads(buf.getvalue().strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["steps"] == 2
+    assert line["value"] > 0 and line["unit"] == bench.UNIT
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["value"] == line["value"]
+    # value = element pairs of the steps over their summed time
+    assert line["value"] == pytest.approx(2 * 80 * 80 / (2 * line["ms_per_step"] / 1e3), rel=1e-3)
