@@ -740,13 +740,20 @@ mueller_status far_field_noalloc(mueller_mesh* m, const PhysConsts& P, int Q, co
   cudaError_t e = cudaMemcpyAsync(ddirs, hd.data(), hd.size() * 8, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dwth, wth.data(), wth.size() * 8, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dinc, inc, (size_t)r * 6 * 8, cudaMemcpyHostToDevice, s);
+  // From the first copy on, work sits on the stream that uses the shared
+  // scratch: every return below waits for the stream first (keeping the
+  // first error), so that a later call on another stream cannot overlap it.
+  auto drain = [&](mueller_status status) {
+    cudaStreamSynchronize(s);
+    return status;
+  };
   if (e == cudaSuccess) e = cudaMemcpyAsync(dphi, phi, sizeof(double) * Q * 6, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return cuda_fail(e, "far-field (allocation-free) setup");
+  if (e != cudaSuccess) return drain(cuda_fail(e, "far-field (allocation-free) setup"));
   { Prof prof_("currents_kernel", s); currents_kernel<<<dim3(nblk_pts, r), 256, 0, s>>>(m->nt, Q, m->qd64, m->T, (const double2*)X, r, N, dphi, rec, cab); }
   st = far_fwd(np, m->qd64, rec, ddirs, nd, r, P.ka, (double*)(buf + o_part), Fall, s);
-  if (st) return st;
+  if (st) return drain(st);
   st = far_shared(np, m->qd64, rec, r, ddirs, nd, n_theta, n_phi, ndir, P.ka, Fall, s);
-  if (st) return st;
+  if (st) return drain(st);
   { Prof prof_("xs_kernel", s); xs_kernel<<<r, 256, 0, s>>>(Fall, nd, n_theta, n_phi, dwth, dinc, P.ka, cab, (int)nblk_pts, dxs); }
   if (ndir > 0) {
     Prof prof_("copy_user_dirs_kernel", s);
@@ -756,7 +763,7 @@ mueller_status far_field_noalloc(mueller_mesh* m, const PhysConsts& P, int Q, co
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(xs, dxs, (size_t)r * 3 * 8, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_fail(e, "far field (allocation-free)");
+  if (e != cudaSuccess) return drain(cuda_fail(e, "far field (allocation-free)"));
   return MUELLER_OK;
 }
 
