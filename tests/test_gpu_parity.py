@@ -261,21 +261,33 @@ def test_sampled_rows_at_level3_workload():
     del Z
     scale = np.abs(rows_o).max()
     assert np.abs(rows_g - rows_o).max() <= 1e-11 * scale
+    # whole rows of the mixed operator: the complex64 far part read from Z
+    # plus the FP64 near blocks of those test nodes (near-block layout)
     Z32, near, _ = mu.assemble(m, p, mu.MUELLER_C64_NEAR64)
-    op = mu.Operator(m, Z32, near, mu.MUELLER_C64_NEAR64)
-    # rows of the mixed operator through Z^T e_i = matvec of the transpose is
-    # not available; use columns instead: Z e_j for sampled trial nodes
-    cols_idx = idx
-    E = torch.zeros((len(cols_idx), m.N), dtype=torch.complex128, device="cuda")
-    E[torch.arange(len(cols_idx)), torch.from_numpy(cols_idx).cuda()] = 1.0
-    cols_g = mu.matvec(op, E).cpu().numpy()  # column j of Z in row k
+    far_rows = Z32[torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.complex128)
+    rowptr, col, _ = m.near_layout()
+    blocks = near.cpu().numpy().reshape(-1, 2, 2, 2, 2)
     del Z32, near
-    # oracle columns: assemble rows of the transposed problem is not
-    # available either, so compare the diagonal 4x4 node blocks in both
+    near_rows = np.zeros_like(far_rows)
     for k, n in enumerate(nodes):
-        sub_o = rows_o[4 * k:4 * k + 4][:, idx[4 * k:4 * k + 4]]
-        sub_g = cols_g[4 * k:4 * k + 4][:, idx[4 * k:4 * k + 4]].T
-        assert np.abs(sub_g - sub_o).max() <= 5e-6 * scale
+        for q in range(rowptr[n], rowptr[n + 1]):
+            j = col[q]
+            for h in (0, 1):
+                for a in (0, 1):
+                    for g in (0, 1):
+                        for b in (0, 1):
+                            near_rows[4 * k + 2 * h + a, g * H + 2 * j + b] = blocks[q, h, a, g, b]
+    mixed_rows = far_rows + near_rows
+    # the only difference from the oracle is the FP32 rounding of the far
+    # part (regular element pairs): within 5e-6 of the largest entry
+    # overall, and entry by entry within a few FP32 roundings of the entry
+    # (plus 1e-7 of the largest, for entries that cancel)
+    d = np.abs(mixed_rows - rows_o)
+    assert d.max() <= 5e-6 * scale, d.max() / scale
+    assert np.all(d <= 4e-6 * np.abs(rows_o) + 1e-7 * scale)
+    # the near blocks carry the singular and mass parts: leaving them out is
+    # far outside that bound
+    assert np.abs(far_rows - rows_o).max() > 1e-3 * scale
 
 
 def test_mirrored_inner_products_match_full_read():

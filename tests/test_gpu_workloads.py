@@ -63,17 +63,33 @@ def test_level4_plasmonic_sphere_16_rhs():
     assert abs(xs[:, 0].mean() - ref[0]) <= 0.05 * ref[0], (xs[:, 0].mean(), ref)
 
 
-def test_small_sphere_matches_mie_with_polar_frames():
-    xyz, tri6 = workloads.icosphere_p2(3)
-    p = mu.Params(ka=1.0, eps_r=(4.0, 0.0), q_regular=6, ssq_order=5, frame_rule=mu.FRAME_POLAR)
+def _mie_errors(level, q=6, ns=5, frame_rule=mu.FRAME_POLAR):
+    xyz, tri6 = workloads.icosphere_p2(level)
+    p = mu.Params(ka=1.0, eps_r=(4.0, 0.0), q_regular=q, ssq_order=ns, frame_rule=frame_rule)
     m = mu.Mesh(xyz, tri6)
     m.tangent_frame(p.frame_rule, out=False)
     inc = workloads.plane_wave()
     Z, near, B = mu.assemble(m, p, mu.MUELLER_C64_NEAR64, inc=inc)
     op = mu.Operator(m, Z, near, mu.MUELLER_C64_NEAR64)
     mu.precond_build(op, 256)
-    X, info = mu.solve(op, B, mu.SolverOpts(mode=mu.SOLVE_GMRES_IR, tol=1e-8))
+    X, info = mu.solve(op, B, mu.SolverOpts(mode=mu.SOLVE_GMRES_IR, tol=1e-10))
     _, xs = mu.far_field(m, p, X, inc)
+    del Z, near, op
+    m.free()
+    torch.cuda.empty_cache()
     ref = mie.mie_bh(1.0, 4.0)
-    assert abs(xs[0, 0] - ref[0]) <= 2e-3 * ref[0], (xs, ref)
-    assert abs(xs[0, 2]) <= 1e-2 * ref[0]  # lossless: C_abs -> 0
+    return np.abs(xs[0] - ref) / ref[0]  # C_ext, C_sca, C_abs (Mie: 0) errors
+
+
+def test_small_sphere_converges_to_mie_with_polar_frames():
+    """Config-1 physics (eps_r = 4, k_a = 1) on the level-2, 3 and 4 spheres
+    (N = 2568, 10248, 40968), polar frame rule, Q = 6, Ns = 5, mixed path to
+    a 1e-10 FP64 residual.  Measured errors of C_ext: 1.4e-3, 2.7e-4,
+    5.2e-5 (h^2.4 per level); an error of 1e-4 is met at level 4, not
+    at level 3 (Q = 12 gives 1.7e-4 there; Ns = 8 changes nothing, so the
+    Sauter-Schwab error is not what limits it).  Every error falls at least
+    as h^1.9 (C_sca and C_abs measured at h^2.0 .. h^2.3)."""
+    errs = [_mie_errors(L) for L in (2, 3, 4)]
+    slopes = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(slopes >= 1.9), (errs, slopes)
+    assert errs[1][0] <= 4e-4 and errs[2][0] <= 1e-4, errs
