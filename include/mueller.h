@@ -56,7 +56,9 @@ typedef enum {
   MUELLER_ERR_TIMEOUT = 6,          /* a bounded device wait gave up          */
   MUELLER_ERR_CUDA = 7,             /* CUDA runtime error                     */
   MUELLER_ERR_OOM = 8,              /* device allocation failed               */
-  MUELLER_ERR_STATE = 9             /* call order violated (e.g. no frame)    */
+  MUELLER_ERR_STATE = 9,            /* call order violated (e.g. no frame)    */
+  MUELLER_ERR_NAN = 10              /* a right-hand side's residual became NaN
+                                       or infinite (named in the message)     */
 } mueller_status;
 
 /* Matrix storage types */
@@ -338,8 +340,14 @@ size_t mueller_precond_bytes(int64_t n_dof, int64_t block);
  *   B_dev, X_dev  complex128 r x N (X_dev holds x0 if opts->warm_start).
  *   work_dev      caller scratch of mueller_solve_workspace_bytes() bytes, or
  *                 NULL to let the call allocate (and free) it on the stream.
- *   info          host, filled on OK and on NOT_CONVERGED.
- * Errors: INVALID_ARG, NOT_CONVERGED, SINGULAR_BLOCK, TIMEOUT, OOM, CUDA.
+ *   info          host, filled on OK, NOT_CONVERGED and NAN.
+ * GMRES_IR (the complex64 inner solver, all right-hand sides in lockstep)
+ * tests convergence on the device and reads it back every few Arnoldi
+ * steps; steps queued past convergence do no work.
+ * Errors: INVALID_ARG, NOT_CONVERGED, NAN (a right-hand side's Arnoldi
+ * estimate or FP64 residual was NaN or infinite: it is frozen, the others
+ * are solved, the message names the first such right-hand side),
+ * SINGULAR_BLOCK, TIMEOUT (a bounded device wait gave up), OOM, CUDA.
  */
 mueller_status mueller_solve(const mueller_operator* op, const void* B_dev, void* X_dev,
                              int32_t r, const mueller_solver_opts* opts, mueller_solve_info* info,
@@ -409,8 +417,10 @@ mueller_status mueller_far_field(mueller_mesh* mesh, const mueller_params* param
  *     array in device memory, held by every GPU that loads the library until
  *     the process exits.  A request that needs more (it grows with
  *     r * (n_tri * q_regular + n_theta * n_phi + n_dir)) is rejected with
- *     INVALID_ARG and a message naming the size; roughly 16 right-hand sides
- *     of the level-3 sphere with the default 48 x 96 sphere rule fit.
+ *     INVALID_ARG and a message naming the size.  The level-3 sphere (1280
+ *     triangles, q_regular = 6) with the default 48 x 96 sphere rule needs
+ *     about 1.07 MB per right-hand side: up to 15 right-hand sides fit, 16
+ *     are refused.
  *   - the mesh must already hold the point geometry for params (call
  *     mueller_assemble or mueller_far_field with the same params first), else
  *     STATE: this call never creates it.
@@ -419,8 +429,9 @@ mueller_status mueller_far_field(mueller_mesh* mesh, const mueller_params* param
  *     capture.
  *   - every call uses the same scratch: calls whose GPU work overlaps (on
  *     different streams or host threads) race and give wrong results; the
- *     call synchronises its stream before returning, so calls issued one
- *     after another on one thread are safe.  Nothing in the scratch needs to
+ *     call synchronises its stream before returning, on success and on
+ *     every error after its first copy, so calls issued one after another
+ *     on one thread are safe.  Nothing in the scratch needs to
  *     start at zero: each region is fully written before it is read.
  */
 #define MUELLER_FAR_FIELD_NOALLOC_SCRATCH_BYTES (16u << 20)

@@ -33,6 +33,7 @@ STATUS = {
     0: "ok", 1: "invalid argument", 2: "invalid mesh", 3: "degenerate tangent frame",
     4: "singular preconditioner block", 5: "not converged", 6: "device wait timed out",
     7: "CUDA error", 8: "out of device memory", 9: "call order violated",
+    10: "NaN or infinite residual",
 }
 
 

@@ -153,8 +153,10 @@ size_t solve_work(const mueller_operator* op, int r, const mueller_solver_opts* 
 
 // mrhs.cu
 size_t mrhs_work_bytes(int64_t N, int r);
+// stop (device, may be null): nonzero skips the product (a converged solver
+// that queued its steps ahead)
 mueller_status mrhs_matvec_c64(const void* Z, int64_t N, int64_t ldz, const void* X, void* Y,
-                               int r, void* work, cudaStream_t s);
+                               int r, void* work, cudaStream_t s, const int* stop = nullptr);
 mueller_status mrhs_check_error(void* work, int64_t N, int r, cudaStream_t s);
 mueller_status near_apply_c64(const mueller_mesh* m, const void* near_c128, const void* X, void* Y,
                               int r, cudaStream_t s);

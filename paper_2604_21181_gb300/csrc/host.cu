@@ -265,6 +265,7 @@ const char* mueller_status_string(mueller_status s) {
     case MUELLER_ERR_CUDA: return "CUDA error";
     case MUELLER_ERR_OOM: return "out of device memory";
     case MUELLER_ERR_STATE: return "call order violated";
+    case MUELLER_ERR_NAN: return "NaN or infinite residual";
   }
   return "unknown status";
 }

@@ -101,7 +101,9 @@ template <class ACC>
 __global__ void __launch_bounds__(256) gemv_c64_kernel(int64_t N, const float4* __restrict__ Z4,
                                                        int64_t ldz, const void* __restrict__ xv_,
                                                        void* __restrict__ yv_, int64_t xs,
-                                                       int64_t ys, int r) {
+                                                       int64_t ys, int r,
+                                                       const int* __restrict__ stop) {
+  if (stop && *stop) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t row0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * 2;
   const int s = blockIdx.y;
@@ -160,10 +162,17 @@ __global__ void __launch_bounds__(256) gemv_c64_kernel(int64_t N, const float4* 
 // partner), two complex64 entries per lane per quadrant row and step
 // (16-byte loads), two steps in flight.  (The FP64-accumulating products are
 // bound by the FP64 pipe, whose work this does not reduce, and read all of
-// Z.)
+// Z.)  With nblk (complex64 near blocks, [h][alpha][g][beta] per block) the
+// near part of rows i and H + i -- node i/2, alpha = i mod 2 -- is added in
+// the same pass, lanes over the node's blocks.
 __global__ void __launch_bounds__(256) gemv3_c64_kernel(int64_t H, const float4* __restrict__ Z4,
                                                         int64_t ldz, const float4* __restrict__ x4,
-                                                        float2* __restrict__ y) {
+                                                        float2* __restrict__ y,
+                                                        const int* __restrict__ stop,
+                                                        const int32_t* __restrict__ nrowptr,
+                                                        const int32_t* __restrict__ ncol,
+                                                        const float2* __restrict__ nblk) {
+  if (stop && *stop) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
   if (i >= H) return;
@@ -195,6 +204,24 @@ __global__ void __launch_bounds__(256) gemv3_c64_kernel(int64_t H, const float4*
     br = fmaf(-d.z, xb.z, fmaf(d.w, xb.w, br));
     bi = fmaf(-d.z, xb.w, fmaf(-d.w, xb.z, bi));
   }
+  if (nblk) {
+    const int64_t n = i >> 1;
+    const int al = (int)(i & 1);
+    const float2* xf = reinterpret_cast<const float2*>(x4);
+    for (int32_t q = nrowptr[n] + lane; q < nrowptr[n + 1]; q += 32) {
+      const int64_t jn = ncol[q];
+      const float2* b = nblk + (int64_t)q * 16;
+#pragma unroll
+      for (int gb = 0; gb < 4; ++gb) {
+        const float2 xv = xf[(gb >> 1) * H + 2 * jn + (gb & 1)];
+        const float2 mt = b[al * 4 + gb], mb = b[(2 + al) * 4 + gb];
+        tr = fmaf(mt.x, xv.x, fmaf(-mt.y, xv.y, tr));
+        ti = fmaf(mt.x, xv.y, fmaf(mt.y, xv.x, ti));
+        br = fmaf(mb.x, xv.x, fmaf(-mb.y, xv.y, br));
+        bi = fmaf(mb.x, xv.y, fmaf(mb.y, xv.x, bi));
+      }
+    }
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     tr += __shfl_xor_sync(0xffffffffu, tr, o);
@@ -215,7 +242,9 @@ __global__ void __launch_bounds__(256) near_spmv_kernel(int64_t nn, const int32_
                                                         const int32_t* __restrict__ col,
                                                         const BT* __restrict__ blk,
                                                         const VT* __restrict__ x, VT* __restrict__ y,
-                                                        int64_t xs, int64_t ys, int r) {
+                                                        int64_t xs, int64_t ys, int r,
+                                                        const int* __restrict__ stop) {
+  if (stop && *stop) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t i = (int64_t)blockIdx.x * 8 + warp;
   const int s = blockIdx.y;
@@ -1160,13 +1189,14 @@ __global__ void scale_b_kernel(const IT* __restrict__ w, int64_t N, const double
   out[(int64_t)s * N + i].y = (decltype(out[0].x))(a.y * inv);
 }
 
-// Givens step of column j for every right-hand side (thread s)
-__global__ void givens_b_kernel(int j, int m, int r, double2* __restrict__ hacc,
-                                const double* __restrict__ hn, double2* __restrict__ Hm,
-                                double* __restrict__ cs, double2* __restrict__ sn,
-                                double2* __restrict__ g, double* __restrict__ res) {
-  const int s = threadIdx.x + blockIdx.x * blockDim.x;
-  if (s >= r) return;
+// Givens step of Arnoldi column j of right-hand side s: the earlier
+// rotations applied to the accumulated Gram-Schmidt coefficients hacc[s],
+// a new rotation against ||w|| = hn, the rotated column stored in Hm and
+// the residual estimate |g[j+1]| in res[s]; hacc[s] is cleared.
+__device__ void givens_column(int j, int m, int s, double2* __restrict__ hacc, double hn_s,
+                              double2* __restrict__ Hm, double* __restrict__ cs,
+                              double2* __restrict__ sn, double2* __restrict__ g,
+                              double* __restrict__ res) {
   double2* ha = hacc + (int64_t)s * (m + 2);
   double2* col = Hm + ((int64_t)s * m + j) * (m + 1);
   double* c_ = cs + (int64_t)s * (m + 1);
@@ -1183,7 +1213,7 @@ __global__ void givens_b_kernel(int j, int m, int r, double2* __restrict__ hacc,
     col[l] = make_double2(c * a.x + sv.x * b.x - sv.y * b.y, c * a.y + sv.x * b.y + sv.y * b.x);
     a = make_double2(-(sv.x * a.x + sv.y * a.y) + c * b.x, -(sv.x * a.y - sv.y * a.x) + c * b.y);
   }
-  const double2 b = make_double2(hn[s], 0.0);
+  const double2 b = make_double2(hn_s, 0.0);
   const double aa = hypot(a.x, a.y), bb = hypot(b.x, b.y);
   const double rho = hypot(aa, bb);
   double c;
@@ -1205,6 +1235,201 @@ __global__ void givens_b_kernel(int j, int m, int r, double2* __restrict__ hacc,
   gg[j + 1] = make_double2(-(sv.x * gj.x + sv.y * gj.y), -(sv.x * gj.y - sv.y * gj.x));
   res[s] = hypot(gg[j + 1].x, gg[j + 1].y);
   for (int l = 0; l <= j + 1; ++l) ha[l] = make_double2(0, 0);
+}
+
+// Givens step of column j for every right-hand side (thread s)
+__global__ void givens_b_kernel(int j, int m, int r, double2* __restrict__ hacc,
+                                const double* __restrict__ hn, double2* __restrict__ Hm,
+                                double* __restrict__ cs, double2* __restrict__ sn,
+                                double2* __restrict__ g, double* __restrict__ res) {
+  const int s = threadIdx.x + blockIdx.x * blockDim.x;
+  if (s >= r) return;
+  givens_column(j, m, s, hacc, hn[s], Hm, cs, sn, g, res);
+}
+
+// ------------------------------------------------ fused Arnoldi step tail
+// Grid-wide barrier of a cooperative launch (every CTA resident): arrival
+// counter bar[0], generation bar[1].  The wait is bounded: after about a
+// second without the generation changing, err is set and the CTA goes on
+// (the host reads err and reports a timeout; results are then void).
+__device__ void grid_barrier(unsigned* bar, unsigned nblocks, int* err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 1;
+    const unsigned gen = *vgen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == nblocks - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long spins = 0;
+      while (*vgen == gen) {
+        __nanosleep(64);
+        if (++spins > (1ll << 24)) {
+          atomicExch(err, 1);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+struct TailArgs {
+  const float2* V;  // Krylov basis V[(l r + s) N + i], l <= j read, l = j + 1 written
+  float2* w;        // A z_j for the r right-hand sides (orthogonalised in place)
+  int64_t N;
+  int r, j, m;
+  double2* part;    // [P][r][m + 1] partial dot products
+  double2* h;       // [r][m + 1] coefficients of the current pass
+  double* npart;    // [P][r] partial squared norms
+  double2* hacc;    // [r][m + 2] coefficients summed over both passes
+  double2* Hm;
+  double* cs;
+  double2* sn;
+  double2* g;
+  double* res;      // [r] Arnoldi residual estimates
+  int* kk;          // [r] converged step count (0: not yet)
+  const int* active;
+  int* bad;         // [r] set when a residual estimate is not a number
+  double tol;
+  int* stop;        // set when every active right-hand side has converged
+  int* jstop;       // steps taken when stop was set
+  unsigned* bar;
+  int* err;
+};
+
+// One Arnoldi step after the product w = A P^-1 v_j, for all r right-hand
+// sides in one cooperative launch: classical Gram-Schmidt twice against
+// v_0..v_j (each pass: partial dot products per CTA chunk, a grid barrier,
+// each coefficient reduced by one CTA, a barrier, the update of the CTA's
+// own chunk), the norm, v_{j+1} = w / ||w||, the Givens step and the
+// convergence test on the device.  Skipped entirely once *stop is set, so
+// the host may queue steps ahead and read the flag only now and then.
+__global__ void __launch_bounds__(256) arnoldi_tail_kernel(TailArgs a) {
+  if (*a.stop) return;  // read by every CTA before the first barrier: uniform
+  const unsigned P = gridDim.x, c = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = a.r, nl = a.j + 1, m1 = a.m + 1;
+  const int64_t ch = (a.N + P - 1) / P;
+  const int64_t i0 = (int64_t)c * ch, i1 = min(a.N, i0 + ch), len = max((int64_t)0, i1 - i0);
+  const int npair = r * nl;
+  for (int pass = 0; pass < 2; ++pass) {
+    // partial dots conj(v_l[s]) . w[s] over this CTA's chunk, one warp per pair
+    for (int p = warp; p < npair; p += 8) {
+      const int s = p / nl, l = p % nl;
+      const float2* v = a.V + ((int64_t)l * r + s) * a.N;
+      const float2* ww = a.w + (int64_t)s * a.N;
+      float ar = 0.f, ai = 0.f;
+      for (int64_t i = i0 + lane; i < i1; i += 32) {
+        const float2 x = v[i], y = ww[i];
+        ar = fmaf(x.x, y.x, fmaf(x.y, y.y, ar));
+        ai = fmaf(x.x, y.y, fmaf(-x.y, y.x, ai));
+      }
+      double dr = ar, di = ai;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        dr += __shfl_xor_sync(0xffffffffu, dr, o);
+        di += __shfl_xor_sync(0xffffffffu, di, o);
+      }
+      if (lane == 0) a.part[((int64_t)c * r + s) * m1 + l] = make_double2(dr, di);
+    }
+    grid_barrier(a.bar, P, a.err);
+    // coefficient p = c, c + P, ...: sum of the P partials, by one warp each
+    for (int p = c + P * warp; p < npair; p += P * 8) {
+      const int s = p / nl, l = p % nl;
+      double dr = 0, di = 0;
+      for (unsigned q = lane; q < P; q += 32) {
+        const double2 t = a.part[((int64_t)q * r + s) * m1 + l];
+        dr += t.x;
+        di += t.y;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        dr += __shfl_xor_sync(0xffffffffu, dr, o);
+        di += __shfl_xor_sync(0xffffffffu, di, o);
+      }
+      if (lane == 0) {
+        a.h[(int64_t)s * m1 + l] = make_double2(dr, di);
+        double2* acc = a.hacc + (int64_t)s * (a.m + 2) + l;
+        acc->x += dr;
+        acc->y += di;
+      }
+    }
+    grid_barrier(a.bar, P, a.err);
+    // w[s] -= sum_l h[s][l] v_l[s] on this CTA's chunk
+    for (int64_t t = threadIdx.x; t < (int64_t)r * len; t += blockDim.x) {
+      const int s = (int)(t / len);
+      const int64_t i = i0 + t % len;
+      float2* wp = a.w + (int64_t)s * a.N + i;
+      float ar = wp->x, ai = wp->y;
+      const double2* hs = a.h + (int64_t)s * m1;
+      for (int l = 0; l < nl; ++l) {
+        const double2 hd = hs[l];
+        const float hr = (float)hd.x, hi = (float)hd.y;
+        const float2 v = a.V[((int64_t)l * r + s) * a.N + i];
+        ar = fmaf(-hr, v.x, fmaf(hi, v.y, ar));
+        ai = fmaf(-hr, v.y, fmaf(-hi, v.x, ai));
+      }
+      *wp = make_float2(ar, ai);
+    }
+    __syncthreads();  // the next pass reads this CTA's chunk only
+  }
+  // squared norms of this chunk, one warp per right-hand side
+  for (int s = warp; s < r; s += 8) {
+    const float2* ww = a.w + (int64_t)s * a.N;
+    double q = 0;
+    for (int64_t i = i0 + lane; i < i1; i += 32) q += (double)ww[i].x * ww[i].x + (double)ww[i].y * ww[i].y;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    if (lane == 0) a.npart[(int64_t)c * r + s] = q;
+  }
+  grid_barrier(a.bar, P, a.err);
+  // v_{j+1} = w / ||w|| (every CTA sums the partials in the same order)
+  __shared__ double hn_sh[128];
+  for (int s = warp; s < r; s += 8) {
+    double q = 0;
+    for (unsigned k = lane; k < P; k += 32) q += a.npart[(int64_t)k * r + s];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    if (lane == 0) hn_sh[s] = sqrt(q);
+  }
+  __syncthreads();
+  float2* vn = const_cast<float2*>(a.V) + (int64_t)(a.j + 1) * r * a.N;
+  for (int64_t t = threadIdx.x; t < (int64_t)r * len; t += blockDim.x) {
+    const int s = (int)(t / len);
+    const int64_t i = i0 + t % len;
+    const double n = hn_sh[s];
+    const double inv = n > 0 ? 1.0 / n : 0.0;
+    const float2 x = a.w[(int64_t)s * a.N + i];
+    vn[(int64_t)s * a.N + i] = make_float2((float)(x.x * inv), (float)(x.y * inv));
+  }
+  if (c != 0) return;
+  for (int s = threadIdx.x; s < r; s += blockDim.x)
+    givens_column(a.j, a.m, s, a.hacc, hn_sh[s], a.Hm, a.cs, a.sn, a.g, a.res);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bool all = true;
+    for (int s = 0; s < r; ++s) {
+      if (!a.active[s]) continue;
+      if (a.kk[s] == 0) {
+        const double v = a.res[s];
+        if (!(v == v)) {
+          a.bad[s] = 1;
+          a.kk[s] = a.j + 1;
+        } else if (v <= a.tol) {
+          a.kk[s] = a.j + 1;
+        }
+      }
+      if (a.kk[s] == 0) all = false;
+    }
+    if (all) {
+      *a.jstop = a.j + 1;
+      *a.stop = 1;
+    }
+  }
 }
 
 // g[s] = beta[s] e1
@@ -1279,7 +1504,9 @@ __global__ void __launch_bounds__(256) mbj_apply_b_kernel(const float2* __restri
                                                           const int32_t* __restrict__ sz, int64_t B,
                                                           int64_t H, int64_t N,
                                                           const float2* __restrict__ v,
-                                                          float2* __restrict__ z) {
+                                                          float2* __restrict__ z,
+                                                          const int* __restrict__ stop) {
+  if (stop && *stop) return;
   const int b = blockIdx.y, s = blockIdx.z;
   const int n = sz[b], half = n / 2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1356,14 +1583,21 @@ inline unsigned nblk(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); 
 // ======================================================= operator products
 // y = Z x of the complex64 dense part for one complex64 vector (FP32
 // accumulation), reading three quarters of Z when Z11 = -Z00
+// With near32 (complex64 near blocks) and the three-quadrant product, the
+// near part is added in the same kernel (*fused set to 1); otherwise the
+// caller adds it.
 static mueller_status gemv_c64_f32(const mueller_operator* op, const void* x, void* y,
-                                   cudaStream_t s) {
+                                   cudaStream_t s, const int* stop = nullptr,
+                                   const float2* near32 = nullptr, int* fused = nullptr) {
+  if (fused) *fused = 0;
   const int64_t N = 4 * op->mesh->nn, H = N / 2;
   if (op->flags & MUELLER_OP_K1_MIRRORED) {
-    { Prof prof_("gemv3_c64_kernel", s); gemv3_c64_kernel<<<(unsigned)nblk(H, 8), 256, 0, s>>>(H, (const float4*)op->Z_dev, op->ldz, (const float4*)x, (float2*)y); }
+    { Prof prof_("gemv3_c64_kernel", s); gemv3_c64_kernel<<<(unsigned)nblk(H, 8), 256, 0, s>>>(H, (const float4*)op->Z_dev, op->ldz, (const float4*)x, (float2*)y, stop,
+        near32 ? op->mesh->near_rowptr : nullptr, near32 ? op->mesh->near_col : nullptr, near32); }
+    if (fused && near32) *fused = 1;
     MU_CHECK_LAUNCH("gemv3_c64_kernel");
   } else {
-    { Prof prof_("gemv_c64_kernel<float>", s); gemv_c64_kernel<float><<<dim3(nblk(N, 16), 1), 256, 0, s>>>(N, (const float4*)op->Z_dev, op->ldz, x, y, N, N, 1); }
+    { Prof prof_("gemv_c64_kernel<float>", s); gemv_c64_kernel<float><<<dim3(nblk(N, 16), 1), 256, 0, s>>>(N, (const float4*)op->Z_dev, op->ldz, x, y, N, N, 1, stop); }
     MU_CHECK_LAUNCH("gemv_c64_kernel<float>");
   }
   return MUELLER_OK;
@@ -1391,12 +1625,12 @@ mueller_status op_matvec(const mueller_operator* op, const void* X, void* Y, int
   } else {
     // FP64-bound: small blocks (2 warps, 4 rows) spread the rows evenly over the SMs
     dim3 grid(nblk(N, 4), r);
-    { Prof prof_("gemv_c64_kernel<double>", s); gemv_c64_kernel<double><<<grid, 64, 0, s>>>(N, (const float4*)op->Z_dev, op->ldz, X, Y, N, N, r); }
+    { Prof prof_("gemv_c64_kernel<double>", s); gemv_c64_kernel<double><<<grid, 64, 0, s>>>(N, (const float4*)op->Z_dev, op->ldz, X, Y, N, N, r, nullptr); }
     MU_CHECK_LAUNCH("gemv_c64_kernel<double>");
     dim3 g2(nblk(m->nn, 8), r);
     { Prof prof_("near_spmv_kernel<double2, double2>", s); near_spmv_kernel<double2, double2><<<g2, 256, 0, s>>>(m->nn, m->near_rowptr, m->near_col,
                                                           (const double2*)op->near_dev,
-                                                          (const double2*)X, (double2*)Y, N, N, r); }
+                                                          (const double2*)X, (double2*)Y, N, N, r, nullptr); }
     MU_CHECK_LAUNCH("near_spmv_kernel");
   }
   return MUELLER_OK;
@@ -1409,7 +1643,8 @@ template <int RS, class BT>
 __global__ void __launch_bounds__(256, 2) near_spmv_c64_mrhs_kernel(
     int64_t nn, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
     const BT* __restrict__ blk, const float2* __restrict__ x, float2* __restrict__ y,
-    int64_t xs, int64_t ys, int r) {
+    int64_t xs, int64_t ys, int r, const int* __restrict__ stop) {
+  if (stop && *stop) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t i = (int64_t)blockIdx.x * 8 + warp;
   const int s0 = blockIdx.y * RS;
@@ -1481,12 +1716,12 @@ mueller_status near_apply_c64(const mueller_mesh* m, const void* near_c128, cons
   if (r >= 2) {
     constexpr int RS = 8;
     dim3 g(nblk(m->nn, 8), (r + RS - 1) / RS);
-    { Prof prof_("near_spmv_c64_mrhs_kernel", s); near_spmv_c64_mrhs_kernel<RS, double2><<<g, 256, 0, s>>>(m->nn, m->near_rowptr, m->near_col, (const double2*)near_c128, (const float2*)X, (float2*)Y, N, N, r); }
+    { Prof prof_("near_spmv_c64_mrhs_kernel", s); near_spmv_c64_mrhs_kernel<RS, double2><<<g, 256, 0, s>>>(m->nn, m->near_rowptr, m->near_col, (const double2*)near_c128, (const float2*)X, (float2*)Y, N, N, r, nullptr); }
     MU_CHECK_LAUNCH("near_spmv_c64_mrhs_kernel");
     return MUELLER_OK;
   }
   dim3 g(nblk(m->nn, 8), r);
-  { Prof prof_("near_spmv_kernel<double2, float2>", s); near_spmv_kernel<double2, float2><<<g, 256, 0, s>>>(m->nn, m->near_rowptr, m->near_col, (const double2*)near_c128, (const float2*)X, (float2*)Y, N, N, r); }
+  { Prof prof_("near_spmv_kernel<double2, float2>", s); near_spmv_kernel<double2, float2><<<g, 256, 0, s>>>(m->nn, m->near_rowptr, m->near_col, (const double2*)near_c128, (const float2*)X, (float2*)Y, N, N, r, nullptr); }
   MU_CHECK_LAUNCH("near_spmv_kernel<double2, float2>");
   return MUELLER_OK;
 }
@@ -1494,17 +1729,18 @@ mueller_status near_apply_c64(const mueller_mesh* m, const void* near_c128, cons
 // y += near x for r complex64 vectors with complex64 near blocks (the inner
 // solver's copy of the FP64 blocks, rounded once per solve)
 static mueller_status near_apply_c64_b32(const mueller_mesh* m, const float2* near32,
-                                         const float2* X, float2* Y, int r, cudaStream_t s) {
+                                         const float2* X, float2* Y, int r, cudaStream_t s,
+                                         const int* stop = nullptr) {
   const int64_t N = 4 * m->nn;
   if (r >= 2) {
     constexpr int RS = 8;
     dim3 g(nblk(m->nn, 8), (r + RS - 1) / RS);
-    { Prof prof_("near_spmv_c64_mrhs_kernel", s); near_spmv_c64_mrhs_kernel<RS, float2><<<g, 256, 0, s>>>(m->nn, m->near_rowptr, m->near_col, near32, X, Y, N, N, r); }
+    { Prof prof_("near_spmv_c64_mrhs_kernel", s); near_spmv_c64_mrhs_kernel<RS, float2><<<g, 256, 0, s>>>(m->nn, m->near_rowptr, m->near_col, near32, X, Y, N, N, r, stop); }
     MU_CHECK_LAUNCH("near_spmv_c64_mrhs_kernel");
     return MUELLER_OK;
   }
   dim3 g(nblk(m->nn, 8), 1);
-  { Prof prof_("near_spmv_kernel<float2, float2>", s); near_spmv_kernel<float2, float2><<<g, 256, 0, s>>>(m->nn, m->near_rowptr, m->near_col, near32, X, Y, N, N, 1); }
+  { Prof prof_("near_spmv_kernel<float2, float2>", s); near_spmv_kernel<float2, float2><<<g, 256, 0, s>>>(m->nn, m->near_rowptr, m->near_col, near32, X, Y, N, N, 1, stop); }
   MU_CHECK_LAUNCH("near_spmv_kernel<float2, float2>");
   return MUELLER_OK;
 }
@@ -1774,7 +2010,7 @@ mueller_status inner_matvec(const InnerOp& I, const VT* x, VT* y, cudaStream_t s
     mueller_status st = gemv_c64_f32(I.op, x, y, s);
     if (st) return st;
     { Prof prof_("near_spmv_kernel<float2, float2>", s); near_spmv_kernel<float2, float2><<<dim3(nblk(m->nn, 8), 1), 256, 0, s>>>(
-        m->nn, m->near_rowptr, m->near_col, I.near32, x, y, N, N, 1); }
+        m->nn, m->near_rowptr, m->near_col, I.near32, x, y, N, N, 1, nullptr); }
     MU_CHECK_LAUNCH("near_spmv_kernel<float>");
     return MUELLER_OK;
   }
@@ -1912,7 +2148,22 @@ struct LockWork {
   int *mask, *kk;
   void* mwork;
   float2* near32;  // complex64 copy of the near blocks (nnzb x 16), or null
+  // fused Arnoldi step (arnoldi_tail_kernel): P CTAs
+  int P;
+  double2 *tpart, *th;
+  double* tnpart;
+  int* flags;      // [0] stop, [1] steps at stop, [2] barrier timeout, [4..5] barrier
+  int* bad;        // [r] residual estimate not a number
 };
+
+// CTAs of the fused Arnoldi step: one per SM, at least 32 entries each
+static int tail_ctas(int64_t N) {
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+    nsm = 1;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(nsm, (N + 31) / 32));
+}
 
 static size_t lock_bytes(int64_t N, int r, int m, int64_t nnzb) {
   const int G = 16;
@@ -1933,6 +2184,12 @@ static size_t lock_bytes(int64_t N, int r, int m, int64_t nnzb) {
   add((size_t)r * 4);
   if (r >= 2) add(mrhs_work_bytes(N, r));
   if (nnzb > 0) add((size_t)nnzb * 16 * 8);
+  const int P = tail_ctas(N);
+  add((size_t)P * r * (m + 1) * 16);
+  add((size_t)r * (m + 1) * 16);
+  add((size_t)P * r * 8);
+  add(64 * 4);
+  add((size_t)r * 4);
   return b + 1024;
 }
 
@@ -1974,33 +2231,42 @@ static LockWork carve_lock(char* p, int64_t N, int r, int m, int64_t nnzb) {
   W.kk = (int*)take((size_t)r * 4);
   W.mwork = r >= 2 ? take(mrhs_work_bytes(N, r)) : nullptr;
   W.near32 = nnzb > 0 ? (float2*)take((size_t)nnzb * 16 * 8) : nullptr;
+  W.P = tail_ctas(N);
+  W.tpart = (double2*)take((size_t)W.P * r * (m + 1) * 16);
+  W.th = (double2*)take((size_t)r * (m + 1) * 16);
+  W.tnpart = (double*)take((size_t)W.P * r * 8);
+  W.flags = (int*)take(64 * 4);
+  W.bad = (int*)take((size_t)r * 4);
   return W;
 }
 
 // complex64 product of the stored operator for the r vectors of X
+// (stop: device flag; nonzero skips the kernels, see arnoldi_tail_kernel)
 static mueller_status lock_matvec(const InnerOp& I, const LockWork& W, const float2* X, float2* Y,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, const int* stop = nullptr) {
   const mueller_mesh* m = I.op->mesh;
   const int64_t N = W.N;
   if (W.r >= 2) {
-    mueller_status st = mrhs_matvec_c64(I.op->Z_dev, N, I.op->ldz, X, Y, W.r, W.mwork, s);
+    mueller_status st = mrhs_matvec_c64(I.op->Z_dev, N, I.op->ldz, X, Y, W.r, W.mwork, s, stop);
     if (st) return st;
   } else {
-    mueller_status st = gemv_c64_f32(I.op, X, Y, s);
+    int fused = 0;
+    mueller_status st = gemv_c64_f32(I.op, X, Y, s, stop, I.near32, &fused);
     if (st) return st;
+    if (fused) return MUELLER_OK;
   }
-  if (I.near32) return near_apply_c64_b32(m, I.near32, X, Y, W.r, s);
+  if (I.near32) return near_apply_c64_b32(m, I.near32, X, Y, W.r, s, stop);
   return near_apply_c64(m, I.op->near_dev, X, Y, W.r, s);
 }
 
 static mueller_status lock_precond(const InnerOp& I, const LockWork& W, const float2* v, float2* z,
-                                   cudaStream_t s) {
+                                   cudaStream_t s, const int* stop = nullptr) {
   if (!I.op->precond_dev) {
     MU_CUDA(cudaMemcpyAsync(z, v, (size_t)W.r * W.N * 8, cudaMemcpyDeviceToDevice, s));
     return MUELLER_OK;
   }
   dim3 g(nblk(I.L.d, 8), I.L.nb, W.r);
-  { Prof prof_("mbj_apply_b_kernel", s); mbj_apply_b_kernel<<<g, 256, 0, s>>>(I.inv32, I.L.d, I.sz_dev, I.L.B, I.L.H, W.N, v, z); }
+  { Prof prof_("mbj_apply_b_kernel", s); mbj_apply_b_kernel<<<g, 256, 0, s>>>(I.inv32, I.L.d, I.sz_dev, I.L.B, I.L.H, W.N, v, z, stop); }
   MU_CHECK_LAUNCH("mbj_apply_b_kernel");
   return MUELLER_OK;
 }
@@ -2049,29 +2315,90 @@ static mueller_status lock_gmres(const InnerOp& I, LockWork& W, double tol, int 
     MU_CUDA(cudaMemsetAsync(W.hacc, 0, (size_t)r * (m + 2) * 16, s));
     std::fill(kk.begin(), kk.end(), 0);
     int jlast = 0;
-    for (int j = 0; j < m && iters < maxit; ++j) {
-      const float2* Vj = W.V + (int64_t)j * r * N;
-      if ((st = lock_precond(I, W, Vj, W.Zt, s))) return st;
-      if ((st = lock_matvec(I, W, W.Zt, W.W, s))) return st;
-      for (int pass = 0; pass < 2; ++pass) {
-        { Prof prof_("dots_b_kernel", s); dots_b_kernel<<<dim3(G, j + 1, r), 256, 0, s>>>(W.V, N, r, j + 1, m + 1, W.W, W.part, G); }
-        { Prof prof_("orth_b_kernel", s); orth_b_kernel<<<dim3(nblk(N, 256), r), 256, 0, s>>>(W.V, N, r, j + 1, m + 1, W.part, G, W.W, W.hacc); }
+    if (r <= 128) {
+      // Arnoldi steps queued ahead: the convergence test runs on the device
+      // (arnoldi_tail_kernel sets the stop flag, after which every queued
+      // kernel returns at once); the host reads the flags every kSync steps
+      constexpr int kSync = 8;
+      MU_CUDA(cudaMemsetAsync(W.kk, 0, (size_t)r * 4, s));
+      MU_CUDA(cudaMemsetAsync(W.flags, 0, 3 * sizeof(int), s));
+      const int* stop = W.flags;
+      TailArgs ta;
+      ta.V = W.V;
+      ta.w = W.W;
+      ta.N = N;
+      ta.r = r;
+      ta.m = m;
+      ta.part = W.tpart;
+      ta.h = W.th;
+      ta.npart = W.tnpart;
+      ta.hacc = W.hacc;
+      ta.Hm = W.Hm;
+      ta.cs = W.cs;
+      ta.sn = W.sn;
+      ta.g = W.g;
+      ta.res = W.res;
+      ta.kk = W.kk;
+      ta.active = W.mask;
+      ta.bad = W.bad;
+      ta.tol = tol;
+      ta.stop = W.flags;
+      ta.jstop = W.flags + 1;
+      ta.err = W.flags + 2;
+      ta.bar = (unsigned*)(W.flags + 4);
+      int queued = 0, hf[3] = {0, 0, 0};
+      for (int j = 0; j < m && iters + queued < maxit; ++j) {
+        const float2* Vj = W.V + (int64_t)j * r * N;
+        if ((st = lock_precond(I, W, Vj, W.Zt, s, stop))) return st;
+        if ((st = lock_matvec(I, W, W.Zt, W.W, s, stop))) return st;
+        ta.j = j;
+        void* args[] = {&ta};
+        {
+          Prof prof_("arnoldi_tail_kernel", s);
+          MU_CUDA(cudaLaunchCooperativeKernel((const void*)arnoldi_tail_kernel, dim3(W.P), dim3(256),
+                                              args, 0, s));
+        }
+        ++queued;
+        if ((j + 1) % kSync == 0 || j == m - 1 || iters + queued >= maxit) {
+          MU_CUDA(cudaMemcpyAsync(hf, W.flags, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
+          MU_CUDA(cudaStreamSynchronize(s));
+          if (hf[2]) {
+            set_error("GMRES: a grid barrier of the Arnoldi step timed out");
+            return MUELLER_ERR_TIMEOUT;
+          }
+          if (hf[0]) break;
+        }
       }
-      if ((st = lock_norms<float2>(W, W.W, W.hn, nullptr, s))) return st;
-      { Prof prof_("scale_b_kernel", s); scale_b_kernel<float2, float2><<<dim3(nblk(N, 256), r), 256, 0, s>>>(W.W, N, W.hn, W.V + (int64_t)(j + 1) * r * N); }
-      { Prof prof_("givens_b_kernel", s); givens_b_kernel<<<nblk(r, 64), 64, 0, s>>>(j, m, r, W.hacc, W.hn, W.Hm, W.cs, W.sn, W.g, W.res); }
-      MU_CHECK_LAUNCH("lockstep Arnoldi step");
-      ++iters;
-      jlast = j;
-      MU_CUDA(cudaMemcpyAsync(hbuf, W.res, r * 8, cudaMemcpyDeviceToHost, s));
+      const int done = hf[0] ? hf[1] : queued;
+      iters += done;
+      jlast = done - 1;
+      MU_CUDA(cudaMemcpyAsync(kk.data(), W.kk, (size_t)r * 4, cudaMemcpyDeviceToHost, s));
       MU_CUDA(cudaStreamSynchronize(s));
-      bool all = true;
-      for (int k = 0; k < r; ++k) {
-        if (!active[k]) continue;
-        if (kk[k] == 0 && (hbuf[k] <= tol || !(hbuf[k] == hbuf[k]))) kk[k] = j + 1;
-        if (kk[k] == 0) all = false;
+    } else {
+      for (int j = 0; j < m && iters < maxit; ++j) {
+        const float2* Vj = W.V + (int64_t)j * r * N;
+        if ((st = lock_precond(I, W, Vj, W.Zt, s))) return st;
+        if ((st = lock_matvec(I, W, W.Zt, W.W, s))) return st;
+        for (int pass = 0; pass < 2; ++pass) {
+          { Prof prof_("dots_b_kernel", s); dots_b_kernel<<<dim3(G, j + 1, r), 256, 0, s>>>(W.V, N, r, j + 1, m + 1, W.W, W.part, G); }
+          { Prof prof_("orth_b_kernel", s); orth_b_kernel<<<dim3(nblk(N, 256), r), 256, 0, s>>>(W.V, N, r, j + 1, m + 1, W.part, G, W.W, W.hacc); }
+        }
+        if ((st = lock_norms<float2>(W, W.W, W.hn, nullptr, s))) return st;
+        { Prof prof_("scale_b_kernel", s); scale_b_kernel<float2, float2><<<dim3(nblk(N, 256), r), 256, 0, s>>>(W.W, N, W.hn, W.V + (int64_t)(j + 1) * r * N); }
+        { Prof prof_("givens_b_kernel", s); givens_b_kernel<<<nblk(r, 64), 64, 0, s>>>(j, m, r, W.hacc, W.hn, W.Hm, W.cs, W.sn, W.g, W.res); }
+        MU_CHECK_LAUNCH("lockstep Arnoldi step");
+        ++iters;
+        jlast = j;
+        MU_CUDA(cudaMemcpyAsync(hbuf, W.res, r * 8, cudaMemcpyDeviceToHost, s));
+        MU_CUDA(cudaStreamSynchronize(s));
+        bool all = true;
+        for (int k = 0; k < r; ++k) {
+          if (!active[k]) continue;
+          if (kk[k] == 0 && (hbuf[k] <= tol || !(hbuf[k] == hbuf[k]))) kk[k] = j + 1;
+          if (kk[k] == 0) all = false;
+        }
+        if (all) break;
       }
-      if (all) break;
     }
     int kmax = 0;
     for (int k = 0; k < r; ++k) {
@@ -2115,11 +2442,13 @@ static mueller_status solve_lockstep(const mueller_operator* op, const double2* 
   }
   double* hbuf = nullptr;
   MU_CUDA(cudaMallocHost((void**)&hbuf, (size_t)std::max(8, 2 * r) * sizeof(double)));
+  MU_CUDA(cudaMemsetAsync(W.flags, 0, 64 * sizeof(int), s));
+  MU_CUDA(cudaMemsetAsync(W.bad, 0, (size_t)r * sizeof(int), s));
   mueller_status st = MUELLER_OK;
   const int maxref = o->max_refine > 0 ? o->max_refine : 20;
   const double itol = o->inner_tol > 0 ? o->inner_tol : 1e-5;
   std::vector<double> bn(r), rn(r);
-  std::vector<int> active(r, 1);
+  std::vector<int> active(r, 1), bad(r, 0);
   int it_left = o->maxit;
   if (!o->warm_start) MU_CUDA(cudaMemsetAsync(X, 0, (size_t)r * N * 16, s));
   if ((st = lock_norms<double2>(W, B, W.bn, nullptr, s))) goto out;
@@ -2142,6 +2471,11 @@ static mueller_status solve_lockstep(const mueller_operator* op, const double2* 
     for (int k = 0; k < r; ++k) {
       rn[k] = hbuf[k];
       const double rel = bn[k] > 0 ? rn[k] / bn[k] : 0.0;
+      if (!(rel == rel) || rel == HUGE_VAL) {  // NaN or Inf: that right-hand side stops
+        bad[k] = 1;
+        active[k] = 0;
+        continue;
+      }
       worst = std::max(worst, rel);
       active[k] = rel > o->tol;
       any |= active[k] != 0;
@@ -2165,8 +2499,25 @@ static mueller_status solve_lockstep(const mueller_operator* op, const double2* 
     MU_CHECK_LAUNCH("refinement update");
   }
   for (int k = 0; k < r; ++k)
-    if (bn[k] == 0 || rn[k] / bn[k] <= o->tol) info->converged++;
+    if (!bad[k] && (bn[k] == 0 || rn[k] / bn[k] <= o->tol)) info->converged++;
   if (r >= 2 && !st) st = mrhs_check_error(W.mwork, N, r, s);
+  if (!st) {
+    // right-hand sides whose Arnoldi estimate or FP64 residual was not a number
+    std::vector<int> dbad(r, 0);
+    MU_CUDA(cudaMemcpyAsync(dbad.data(), W.bad, (size_t)r * sizeof(int), cudaMemcpyDeviceToHost, s));
+    MU_CUDA(cudaStreamSynchronize(s));
+    int nbad = 0, first = -1;
+    for (int k = 0; k < r; ++k)
+      if (bad[k] || dbad[k]) {
+        ++nbad;
+        if (first < 0) first = k;
+      }
+    if (nbad) {
+      set_error(std::to_string(nbad) + " right-hand side(s) produced a NaN or infinite residual "
+                "(first: right-hand side " + std::to_string(first) + "); the others are solved");
+      st = MUELLER_ERR_NAN;
+    }
+  }
 out:
   cudaFreeHost(hbuf);
   return st;

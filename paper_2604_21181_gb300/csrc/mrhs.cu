@@ -146,6 +146,7 @@ struct MrhsArgs {
   uint32_t tmem_cols;
   float* Y;         // complex64 r x N, accumulated (atomic adds)
   int* err;         // error word
+  const int* stop;  // nonzero: skip the product (solver converged); may be null
 };
 
 // dynamic shared memory: [stages][A 16 KB | Alo 16 KB | Bhi | Blo] + barriers
@@ -153,6 +154,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     mrhs_tf32_kernel(const __grid_constant__ CUtensorMap mapZ,
                      const __grid_constant__ CUtensorMap mapBhi,
                      const __grid_constant__ CUtensorMap mapBlo, MrhsArgs a) {
+  if (a.stop && *a.stop) return;  // uniform: before any barrier or TMEM allocation
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t bbytes = (uint32_t)a.nprime * BK * 4;
@@ -353,6 +355,7 @@ struct ZnArgs {
   int nprime, r, ktiles, kchunk, stages, stacked;
   float* Y;  // complex64 r x N, accumulated (atomic adds of the real parts)
   int* err;
+  const int* stop;  // nonzero: skip the product (solver converged); may be null
 };
 
 // dynamic shared memory: [stages][Z 16 KB | Zlo 16 KB | A0 8 KB | A1 8 KB (unstacked)]
@@ -360,6 +363,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     mrhs_zn_kernel(const __grid_constant__ CUtensorMap mapZ,
                    const __grid_constant__ CUtensorMap mapA0,
                    const __grid_constant__ CUtensorMap mapA1, ZnArgs a) {
+  if (a.stop && *a.stop) return;  // uniform: before any barrier or TMEM allocation
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   constexpr uint32_t ZB = ZN * ZBK * 4;   // 16 KB
@@ -513,7 +517,9 @@ __global__ void __launch_bounds__(THREADS, 1)
 
 // B' head / remainder (nprime x 2N, K-major) from X (complex64 r x N)
 __global__ void build_bprime_kernel(const float2* __restrict__ X, int64_t N, int r, int nprime,
-                                    float* __restrict__ Bhi, float* __restrict__ Blo) {
+                                    float* __restrict__ Bhi, float* __restrict__ Blo,
+                                    const int* __restrict__ stop) {
+  if (stop && *stop) return;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= (int64_t)nprime * N) return;
   const int row = (int)(t / N);
@@ -585,7 +591,7 @@ size_t mrhs_work_bytes(int64_t N, int r) {
 // Y (complex64 r x N) = Z (complex64, N x ldz) X (complex64 r x N); work:
 // mrhs_work_bytes(N, r) bytes of device scratch.
 mueller_status mrhs_matvec_c64(const void* Z, int64_t N, int64_t ldz, const void* X, void* Y,
-                               int r, void* work, cudaStream_t s) {
+                               int r, void* work, cudaStream_t s, const int* stop) {
   if (r < 1 || r > 128) {
     set_error("tensor-core product supports 1..128 right-hand sides");
     return MUELLER_ERR_INVALID_ARG;
@@ -607,7 +613,7 @@ mueller_status mrhs_matvec_c64(const void* Z, int64_t N, int64_t ldz, const void
   {
     Prof prof_("build_bprime_kernel", s);
     build_bprime_kernel<<<(unsigned)cdiv((int64_t)nprime * N, 256), 256, 0, s>>>(
-        (const float2*)X, N, r, nprime, Bhi, Blo);
+        (const float2*)X, N, r, nprime, Bhi, Blo, stop);
   }
   MU_CHECK_LAUNCH("build_bprime_kernel");
   if (nprime <= BM) {
@@ -632,6 +638,7 @@ mueller_status mrhs_matvec_c64(const void* Z, int64_t N, int64_t ldz, const void
     z.stacked = zstacked;
     z.Y = (float*)Y;
     z.err = err;
+    z.stop = stop;
     const int64_t ntiles = cdiv(N, ZN);
     int ksplit = (int)std::max<int64_t>(1, std::min<int64_t>(z.ktiles / 16, cdiv(4 * 152, ntiles)));
     z.kchunk = (int)cdiv(z.ktiles, ksplit);
@@ -663,6 +670,7 @@ mueller_status mrhs_matvec_c64(const void* Z, int64_t N, int64_t ldz, const void
   a.tmem_cols = tmem_cols;
   a.Y = (float*)Y;
   a.err = err;
+  a.stop = stop;
   const int64_t mtiles = cdiv(N, BM);
   // split K so that the grid covers the SMs about 4 times
   int ksplit = (int)std::max<int64_t>(1, std::min<int64_t>(a.ktiles / 8, cdiv(4 * 152, mtiles)));
