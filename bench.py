@@ -51,6 +51,16 @@ PEAK_FP64 = SMS * 2 * 2 * SM_MAX_HZ
 PEAK_FP32 = SMS * 128 * 2 * SM_MAX_HZ
 
 
+def measured_hbm_gbs() -> tuple:
+    """(GB/s, source): the measured copy bandwidth of the GB300s from
+    MEASURED_PEAKS.json, else the recipe's fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json)"
+    except Exception:
+        return 6800.0, "fallback"
+
+
 def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -125,7 +135,24 @@ class ClockSampler:
 # DRAM bytes (read + written) per touching pair of the touching kernel's
 # launches, from its ncu capture on the level-2 sphere (4100 touching pairs);
 # None while the kernel has changed since that capture.
-TOUCH_DRAM_PER_PAIR = 49.44e6 / 4100
+TOUCH_DRAM_PER_PAIR = None
+
+
+def touching_points(n_tri: int, n_touch: int, ns: int) -> float:
+    """Sauter-Schwab points of all touching pairs: 6, 5 and 2 regions of ns^4
+    points for the coincident, common-edge and common-vertex pairs."""
+    n_vert = n_touch - 4 * n_tri
+    return float(ns ** 4) * (6 * n_tri + 5 * 3 * n_tri + 2 * n_vert)
+
+
+def touching_flops_algorithmic(n_tri: int, n_touch: int, ns: int, q: int) -> float:
+    """The algorithmic count of the touching pairs: per Sauter-Schwab point
+    about 60 flops of singular kernel and 8 real accumulators x 36 node pairs
+    (576), with the point geometry precomputed; per touching pair the
+    remainder kappa - kappa^s on the Q x Q rule (Q^2 540 + Q 1728 flops, the
+    regular-pair count)."""
+    return touching_points(n_tri, n_touch, ns) * (60.0 + 576.0) + \
+        n_touch * (q * q * 540.0 + q * 1728.0)
 
 
 def touching_flops(n_tri: int, n_touch: int, ns: int, q: int) -> float:
@@ -141,7 +168,9 @@ def touching_flops(n_tri: int, n_touch: int, ns: int, q: int) -> float:
     comes from the tables and only the weight is mapped).  Per group the
     6 x 48 contraction costs 576.  Coincident and
     common-edge groups evaluate 1 + ns geometries; common-vertex pairs
-    (ns <= 5) evaluate the 2 (ns^2 + ns^3) distinct ones once.  Per pair,
+    (ns <= 5) evaluate the 2 (ns^2 + ns^3) distinct ones once.  Groups whose
+    shared side depends on (a, b) only are folded by sets of ns before the
+    contraction.  Per pair,
     the remainder kappa - kappa^s on the Q x Q rule (~900 flops per point
     pair) and its 6 x 6 x 12 contraction (2 * 432 * Q * 2)."""
     n_coinc = n_tri
@@ -153,7 +182,13 @@ def touching_flops(n_tri: int, n_touch: int, ns: int, q: int) -> float:
     geo = g_ce * (1 + ns) + (n_vert * 2 * (ns ** 2 + ns ** 3) if tab else g_v * (1 + ns))
     per_point = g_ce * ns * 206.0 + g_v * ns * (202.0 if tab else 206.0)
     per_pair = q * q * 900 + 2 * 432 * q * 2
-    return geo * 189.0 + per_point + (g_ce + g_v) * 576.0 + n_touch * per_pair
+    # contraction 576 per group; where the shared side depends on (a, b)
+    # only (common-edge regions 1 and 3, both common-vertex regions) the ns
+    # groups of a set are folded first (48 (ns - 1) adds) and contracted once
+    sets_shared = (2 * n_edge + 2 * n_vert) * ns ** 2
+    g_plain = (6 * n_coinc + 3 * n_edge) * ns ** 3
+    contraction = g_plain * 576.0 + sets_shared * (576.0 + 48.0 * (ns - 1))
+    return geo * 189.0 + per_point + contraction + n_touch * per_pair
 
 
 def regular_flops(n_tri: int, n_touch: int, q: int) -> float:
@@ -278,10 +313,13 @@ def run_ours(args):
         q, ns = int(w["q_regular"]), int(w["ssq_order"])
         if top_name.startswith("touching_kernel"):
             # all touching pairs, in top_n launches (coincident and common-edge
-            # pairs, then common-vertex pairs): flops of all of them over
-            # their summed CUDA-event time
-            fl = touching_flops(F, info["n_touching"], ns, q)
+            # pairs, then common-vertex pairs): algorithmic flops of all of
+            # them over their summed CUDA-event time; beside it the flops the
+            # kernel executes by its own model
+            fl = touching_flops_algorithmic(F, info["n_touching"], ns, q)
             ach = fl / (top_ms / 1e3) / 1e12
+            fx = touching_flops(F, info["n_touching"], ns, q)
+            ax = fx / (top_ms / 1e3) / 1e12
             # DRAM bytes of the step's launches, scaled per touching pair from
             # the ncu capture of this kernel on the level-2 sphere
             traffic = (int(round(TOUCH_DRAM_PER_PAIR * info["n_touching"]))
@@ -290,6 +328,11 @@ def run_ours(args):
                         "achieved": round(ach, 4),
                         "peak": round(PEAK_FP64 / 1e12, 4), "unit": "TFLOP/s",
                         "frac": round(ach / (PEAK_FP64 / 1e12), 4), "traffic": traffic,
+                        "algorithmic_gflop": round(fl / 1e9, 3),
+                        "definition": "Sauter-Schwab points x (60 + 576) flops + touching pairs "
+                                      "x (Q^2 540 + Q 1728) remainder flops",
+                        "executed_model": {"gflop": round(fx / 1e9, 3), "achieved": round(ax, 4),
+                                           "frac": round(ax / (PEAK_FP64 / 1e12), 4)},
                         "peak_source": "152 SMs x 2 DFMA/clk x 2.07 GHz (unit counts, max clock)"}
         elif top_name.startswith("regular_kernel"):
             fl = regular_flops(F, info["n_touching"], q)
@@ -436,13 +479,19 @@ def level4_16rhs(mu, torch, dev):
     X32 = X.to(torch.complex64)
     t_mm, _ = ev_time(lambda: mu.matvec_mrhs(op, X32), reps=5)
     _, xs = mu.far_field(m, p, X, inc)
-    gbs = m.N * m.N * 8 / (t_mm / 1e3) / 1e9
+    # algorithmic bytes: the three-block form (Z00, Z01, Z10: Z11 = -Z00 is
+    # not read again) for r <= 16, else all of Z, plus X and Y
+    r = int(inc.shape[0])
+    zbytes = (0.75 if r <= 16 else 1.0) * m.N * m.N * 8
+    gbs = (zbytes + 2 * r * m.N * 8) / (t_mm / 1e3) / 1e9
     return {"n_dof": m.N, "rhs": int(inc.shape[0]), "assembly_ms": round(t_asm, 2),
             "assembly_pairs_per_s": F * F / (t_asm / 1e3), "precond_ms": round(t_pre, 2),
             "solve_s": round(t_solve / 1e3, 4), "iters_lockstep": info["iters"] // inc.shape[0],
             "refinements": info["refinements"], "relres": info["relres"],
             "mrhs_product_ms": round(t_mm, 3), "mrhs_product_hbm_gbs": round(gbs, 1),
-            "mrhs_product_hbm_frac": round(gbs / 6783.5, 3),
+            "mrhs_product_hbm_frac": round(gbs / measured_hbm_gbs()[0], 3),
+            "mrhs_product_bytes": "complex64 Z read once per product (three quarters of it "
+                                  "when Z11 = -Z00 and r <= 16) + X, Y",
             "C_ext_mean": float(xs[:, 0].mean())}
 
 
@@ -484,20 +533,22 @@ def multibody64(mu, torch, dev):
     t_loop, _ = ev(lambda: [mu.assemble(m, p, mu.MUELLER_C64_NEAR64, inc=inc, Z=Z, near=nr, B=B)
                             for m, p, (Z, nr, B) in zip(meshes, params, out)])
     opts = mu.SolverOpts(mode=mu.SOLVE_GMRES_IR, restart=50, tol=1e-8)
+    ops = [mu.Operator(m, Z, nr, mu.MUELLER_C64_NEAR64) for m, (Z, nr, B) in zip(meshes, out)]
+    blocks = [min(256, m.N // 2) for m in meshes]
+    # the block-Jacobi builds of all bodies: one batched LU, and per body
+    t_pre_loop, _ = ev(lambda: [mu.precond_build(op, b) for op, b in zip(ops, blocks)], reps=1)
     torch.cuda.synchronize()
     t0 = _t.perf_counter()
-    t_pre = t_sol = 0.0
+    mu.precond_build_batch(ops, blocks)
+    torch.cuda.synchronize()
+    t_pre = _t.perf_counter() - t0
+    t_sol = 0.0
     worst, iters, bal = 0.0, 0, {}
-    for m, p, (Z, nr, B) in zip(meshes, params, out):
-        op = mu.Operator(m, Z, nr, mu.MUELLER_C64_NEAR64)
-        ta = _t.perf_counter()
-        mu.precond_build(op, min(256, m.N // 2))
-        torch.cuda.synchronize()
+    for m, p, op, (Z, nr, B) in zip(meshes, params, ops, out):
         tb = _t.perf_counter()
         X, info = mu.solve(op, B, opts)
         torch.cuda.synchronize()
         tc = _t.perf_counter()
-        t_pre += tb - ta
         t_sol += tc - tb
         worst = max(worst, info["relres"])
         iters += info["iters"] // inc.shape[0]
@@ -515,7 +566,8 @@ def multibody64(mu, torch, dev):
             "assembly_batched_pairs_per_s": pairs / (t_batch / 1e3),
             "assembly_loop_ms": round(t_loop, 2),
             "assembly_loop_pairs_per_s": pairs / (t_loop / 1e3),
-            "precond_total_s": round(t_pre, 3), "solve_total_s": round(t_sol, 3),
+            "precond_batched_s": round(t_pre, 3),
+            "precond_loop_s": round(t_pre_loop / 1e3, 3), "solve_total_s": round(t_sol, 3),
             "solve_and_far_field_wall_s": round(t_all, 3), "lockstep_iters_total": iters,
             "worst_relres": worst, "worst_energy_balance_by_level": bal}
 

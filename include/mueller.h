@@ -313,6 +313,29 @@ mueller_status mueller_assemble_batch(int32_t n_bodies, mueller_mesh* const* mes
 mueller_status mueller_dz_matvec(mueller_mesh* mesh, const mueller_params* params, int32_t which,
                                  const void* X_dev, void* Y_dev, void* stream);
 
+/*
+ * mueller_zshape_vjp -- the gradient of Re lam^H Z(X) x with respect to the
+ * node coordinates X (the operator of Eq. global_system as a function of
+ * the P2 geometry, Sec. 3), for given lam and x: the term of the adjoint
+ * relation dC/dX = dC/dX|_x + 2 Re lam^H (db/dX - (dZ/dX) x) that involves
+ * the operator.  Every element pair's kernel values are recomputed with
+ * their derivatives with respect to the point geometry (regular pairs,
+ * touching-pair remainders, the Sauter-Schwab integrals of the singular
+ * parts, the mass term) and contracted with lam and x; the adjoints are
+ * carried back through the continuous frame (Sec. 3.3), the nodal frame
+ * (Sec. 3.2) and the metric-weighted nodal normal (Sec. 3.1) to the node
+ * positions.  No derivative of Z is stored.  FP64.
+ *   lam_dev, X_dev  complex128, length N = 4 n_nodes, the mesh's unknown
+ *                   order; read only.
+ *   grad            host, n_nodes x 3, the node order of the mesh's input
+ *                   (node_perm applied); overwritten.  Synchronising.
+ * Needs mueller_tangent_frame with params->frame_rule (else STATE).
+ * Errors: INVALID_ARG, STATE, OOM, CUDA.
+ */
+mueller_status mueller_zshape_vjp(mueller_mesh* mesh, const mueller_params* params,
+                                  const void* lam_dev, const void* X_dev, double* grad,
+                                  void* stream);
+
 /* bytes of the complex128 near-part buffer of a loaded mesh */
 size_t mueller_near_bytes(const mueller_mesh* mesh);
 
@@ -332,6 +355,24 @@ size_t mueller_near_bytes(const mueller_mesh* mesh);
 mueller_status mueller_precond_build(const mueller_operator* op, int64_t block,
                                      void* precond_dev, void* stream);
 size_t mueller_precond_bytes(int64_t n_dof, int64_t block);
+
+/*
+ * mueller_precond_build_batch -- what mueller_precond_build computes, for n
+ * operators (bodies) at once: the blocks of every body (Sec. 5, Eq.
+ * precond_block; block dimension 2 min(block[b], N_b / 2)) are gathered
+ * into one batch and factorised by one batched FP64 LU, so that many small
+ * bodies fill the GPU together.  Bodies whose block dimension or dtype
+ * differ from the others' go into batches of their own.  The paper treats
+ * one body; batching many scatterers is an extension of this library.
+ *   ops[b], block[b]  as in mueller_precond_build, one per body.
+ *   precond_dev[b]    caller-owned, mueller_precond_bytes(N_b, block[b])
+ *                     bytes, the same layout as mueller_precond_build.
+ * Synchronising.  Errors: INVALID_ARG (naming the body), STATE,
+ * SINGULAR_BLOCK (naming the body and block), OOM, CUDA.
+ */
+mueller_status mueller_precond_build_batch(int32_t n, const mueller_operator* ops,
+                                           const int64_t* block, void* const* precond_dev,
+                                           void* stream);
 
 /*
  * mueller_solve -- Sec. 5 (GMRES with right block-Jacobi preconditioning)

@@ -27,6 +27,7 @@ from .api import (  # noqa: F401
     assemble,
     assemble_batch,
     dz_matvec,
+    zshape_vjp,
     far_field,
     launch_count,
     load_library,
@@ -36,6 +37,7 @@ from .api import (  # noqa: F401
     matvec,
     matvec_mrhs,
     precond_build,
+    precond_build_batch,
     solve,
     solve_workspace_bytes,
     sync,

@@ -83,6 +83,7 @@ EXPORTS = [
     "mueller_profile_enable", "mueller_profile_reset", "mueller_launch_count",
     "mueller_profile_get", "mueller_profile_names", "mueller_far_field_noalloc",
     "mueller_matvec_mrhs", "mueller_matvec_mrhs_workspace_bytes", "mueller_assemble_batch",
+    "mueller_precond_build_batch", "mueller_zshape_vjp",
 ]
 
 _lib = None
@@ -114,9 +115,12 @@ def load_library(build_if_missing: bool = True):
         "mueller_tangent_frame": (C.c_int, [vp, i32, vp, vp]),
         "mueller_assemble": (C.c_int, [vp, C.POINTER(CParams), i32, vp, i64, vp, vp, dp, i32, vp]),
         "mueller_dz_matvec": (C.c_int, [vp, C.POINTER(CParams), i32, vp, vp, vp]),
+        "mueller_zshape_vjp": (C.c_int, [vp, C.POINTER(CParams), vp, vp, dp, vp]),
         "mueller_near_bytes": (C.c_size_t, [vp]),
         "mueller_precond_build": (C.c_int, [C.POINTER(COperator), i64, vp, vp]),
         "mueller_precond_bytes": (C.c_size_t, [i64, i64]),
+        "mueller_precond_build_batch": (C.c_int, [i32, C.POINTER(COperator), C.POINTER(i64),
+                                                  C.POINTER(vp), vp]),
         "mueller_solve": (C.c_int, [C.POINTER(COperator), vp, vp, i32, C.POINTER(CSolverOpts),
                                     C.POINTER(CSolveInfo), vp, C.c_size_t, vp]),
         "mueller_solve_workspace_bytes": (C.c_size_t, [C.POINTER(COperator), i32, C.POINTER(CSolverOpts)]),
@@ -338,6 +342,21 @@ def dz_matvec(mesh: Mesh, params: Params, which: int, X, stream=None):
     return Y
 
 
+def zshape_vjp(mesh: Mesh, params: Params, lam, X, stream=None):
+    """mueller_zshape_vjp: gradient of Re lam^H Z(X) x with respect to the
+    node coordinates, numpy (n_nodes, 3) in the input node order."""
+    torch = _torch()
+    lam = _dev(lam, torch.complex128, "lam").reshape(-1)
+    X = _dev(X, torch.complex128, "X").reshape(-1)
+    if lam.numel() != mesh.N or X.numel() != mesh.N:
+        raise ValueError("lam and X must have length N")
+    g = np.zeros((mesh.nn, 3))
+    p = params.c()
+    _check(mesh._lib.mueller_zshape_vjp(mesh.h, C.byref(p), _ptr(lam), _ptr(X), _dp(g),
+                                        _stream(stream)))
+    return g
+
+
 def assemble_batch(meshes, params, dtype: int = MUELLER_C64_NEAR64, incs=None, stream=None):
     """mueller_assemble_batch: one launch of each assembly kernel for all bodies.
     Returns a list of (Z, near, B) per body as CUDA tensors."""
@@ -425,6 +444,26 @@ def precond_build(op: Operator, block: int, stream=None):
     _check(lib.mueller_precond_build(C.byref(o), int(block), _ptr(P), _stream(stream)))
     op.precond, op.block = P, int(block)
     return P
+
+
+def precond_build_batch(ops, blocks, stream=None):
+    """mueller_precond_build_batch: the block-Jacobi preconditioners of many
+    operators (bodies) by one batched LU.  Sets and returns each operator's
+    buffer."""
+    torch = _torch()
+    lib = load_library()
+    n = len(ops)
+    if len(blocks) != n:
+        raise ValueError("one block size per operator")
+    bufs = [torch.empty(lib.mueller_precond_bytes(op.mesh.N, int(b)), dtype=torch.uint8,
+                        device="cuda") for op, b in zip(ops, blocks)]
+    cops = (COperator * n)(*[op.c() for op in ops])
+    cblk = (C.c_int64 * n)(*[int(b) for b in blocks])
+    cptr = (C.c_void_p * n)(*[b.data_ptr() for b in bufs])
+    _check(lib.mueller_precond_build_batch(n, cops, cblk, cptr, _stream(stream)))
+    for op, P, b in zip(ops, bufs, blocks):
+        op.precond, op.block = P, int(b)
+    return bufs
 
 
 @dataclass

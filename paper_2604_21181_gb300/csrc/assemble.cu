@@ -598,13 +598,15 @@ __device__ __forceinline__ void touching_pair(
   // before the 6 x 48 contraction (5x fewer multiply-adds).
   const int ngroups = nreg * ns * ns * ns;
   const int ns3 = ns * ns * ns;
+  // batches of whole (region, a, b) sets of ns groups (ns divides ns^3)
+  const int step = (TT / ns) * ns;
   double acc[3] = {0.0, 0.0, 0.0};
-  for (int base = 0; base < ngroups; base += TT) {
+  for (int base = 0; base < ngroups; base += step) {
     // region-major numbering keeps whole warps in one region (one branch)
     const int grp = base + tid;
     double* myV = sV[tid];
     int shx = 1;
-    if (grp < ngroups) {
+    if (tid < step && grp < ngroups) {
       const int reg = grp / ns3;
       int rest = grp % ns3;
       const int ci = rest % ns;
@@ -632,6 +634,22 @@ __device__ __forceinline__ void touching_pair(
     }
     sFlag[tid] = shx;
     __syncthreads();
+    // where the shared side depends on (a, b) only, the ns groups of a set
+    // have the same shape values U: their sums V are added into the first
+    // record (all threads over (set, component)) and the others are skipped
+    // by the contraction
+    for (int e = tid; e < (step / ns) * 48; e += TT) {
+      const int set = e / 48, c = e % 48;
+      const int g0 = base + set * ns;
+      if (g0 < ngroups && ss_shared_ab(P.cls, g0 / ns3)) {
+        double v = sV[set * ns][c];
+        for (int k = 1; k < ns; ++k) v += sV[set * ns + k][c];
+        sV[set * ns][c] = v;
+      }
+    }
+    if (tid < step && grp < ngroups && (grp % ns) != 0 && ss_shared_ab(P.cls, grp / ns3))
+      sFlag[tid] = -1;
+    __syncthreads();
     // G[i][j][c] += N_i(x) V[j][c]  (x shared)  or  V[i][c] N_j(y)  (y shared)
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -639,6 +657,7 @@ __device__ __forceinline__ void touching_pair(
       const int i = o / 48, jc = o % 48, j = jc >> 3, c = jc & 7;
       double s2 = acc[k];
       for (int q = 0; q < TT; ++q) {
+        if (sFlag[q] < 0) continue;
         const bool fx = sFlag[q] != 0;
         const double u = sU[q][fx ? i : j];
         const double v = sV[q][fx ? jc : i * 8 + c];

@@ -146,6 +146,8 @@ mueller_status op_matvec(const mueller_operator* op, const void* X, void* Y, int
                          size_t work_bytes, cudaStream_t s);
 size_t op_matvec_work(const mueller_operator* op, int r);
 mueller_status precond_build(const mueller_operator* op, int64_t block, void* P, cudaStream_t s);
+mueller_status precond_build_batch(int n, const mueller_operator* ops, const int64_t* blocks,
+                                   void* const* P, cudaStream_t s);
 mueller_status solve(const mueller_operator* op, const void* B, void* X, int r,
                      const mueller_solver_opts* o, mueller_solve_info* info, void* work,
                      size_t work_bytes, cudaStream_t s);
@@ -155,8 +157,11 @@ size_t solve_work(const mueller_operator* op, int r, const mueller_solver_opts* 
 size_t mrhs_work_bytes(int64_t N, int r);
 // stop (device, may be null): nonzero skips the product (a converged solver
 // that queued its steps ahead)
+// mirrored: Z11 = -Z00 bit for bit (MUELLER_OP_K1_MIRRORED): Z00 is then read
+// once for both diagonal blocks where r <= 16
 mueller_status mrhs_matvec_c64(const void* Z, int64_t N, int64_t ldz, const void* X, void* Y,
-                               int r, void* work, cudaStream_t s, const int* stop = nullptr);
+                               int r, void* work, cudaStream_t s, const int* stop = nullptr,
+                               int mirrored = 0);
 mueller_status mrhs_check_error(void* work, int64_t N, int r, cudaStream_t s);
 mueller_status near_apply_c64(const mueller_mesh* m, const void* near_c128, const void* X, void* Y,
                               int r, cudaStream_t s);
@@ -170,4 +175,9 @@ mueller_status far_field_noalloc(mueller_mesh* m, const PhysConsts& P, int Q, co
                                  double* xs, int n_theta, int n_phi, cudaStream_t s);
 
 PhysConsts make_phys(const mueller_params* p);
+
+// shape_grad.cu: grad (host, n_nodes x 3, input node order) += the gradient
+// of Re lam^H Z(X) x with respect to the node coordinates
+mueller_status zshape_vjp(mueller_mesh* m, const PhysConsts& P, int Q, int ns, const void* lam,
+                          const void* x, double* grad, cudaStream_t s);
 }  // namespace mu

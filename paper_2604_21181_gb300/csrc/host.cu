@@ -680,6 +680,21 @@ mueller_status mueller_dz_matvec(mueller_mesh* m, const mueller_params* p, int32
   return launch_dz_matvec(m, make_phys(p), p->q_regular, p->ssq_order, which, X, Y, s);
 }
 
+mueller_status mueller_zshape_vjp(mueller_mesh* m, const mueller_params* p, const void* lam,
+                                  const void* X, double* grad, void* stream) {
+  if (!m || !lam || !X || !grad) return fail(MUELLER_ERR_INVALID_ARG, "NULL argument");
+  mueller_status st = check_params(p);
+  if (st) return st;
+  if (m->host_only) return fail(MUELLER_ERR_STATE, kHostOnlyMsg);
+  if (p->frame_rule != m->frame_rule || !m->has_frame)
+    return fail(MUELLER_ERR_STATE, "call mueller_tangent_frame with params->frame_rule first");
+  cudaStream_t s = (cudaStream_t)stream;
+  st = ensure_geometry(m, p->q_regular, s);
+  if (st) return st;
+  std::fill(grad, grad + 3 * m->nn, 0.0);
+  return zshape_vjp(m, make_phys(p), p->q_regular, p->ssq_order, lam, X, grad, s);
+}
+
 mueller_status mueller_assemble_batch(int32_t n_bodies, mueller_mesh* const* meshes,
                                       const mueller_params* params, int32_t dtype,
                                       void* const* Z, const int64_t* ldz, void* const* near,
@@ -758,6 +773,24 @@ mueller_status mueller_precond_build(const mueller_operator* op, int64_t block, 
   return precond_build(op, block, P, (cudaStream_t)stream);
 }
 
+mueller_status mueller_precond_build_batch(int32_t n, const mueller_operator* ops,
+                                           const int64_t* blocks, void* const* precond_dev,
+                                           void* stream) {
+  if (n < 1 || !ops || !blocks || !precond_dev) return fail(MUELLER_ERR_INVALID_ARG, "NULL argument or n < 1");
+  for (int32_t b = 0; b < n; ++b) {
+    const std::string who = "body " + std::to_string(b) + ": ";
+    const mueller_operator* op = &ops[b];
+    if (!op->mesh || !op->Z_dev || !precond_dev[b]) return fail(MUELLER_ERR_INVALID_ARG, who + "NULL argument");
+    if (blocks[b] < 1) return fail(MUELLER_ERR_INVALID_ARG, who + "block must be >= 1");
+    if (op->dtype != MUELLER_C128 && op->dtype != MUELLER_C64_NEAR64)
+      return fail(MUELLER_ERR_INVALID_ARG, who + "unknown operator dtype");
+    if (op->dtype == MUELLER_C64_NEAR64 && !op->near_dev)
+      return fail(MUELLER_ERR_INVALID_ARG, who + "operator lacks its near part");
+    if (op->mesh->host_only) return fail(MUELLER_ERR_STATE, who + kHostOnlyMsg);
+  }
+  return precond_build_batch(n, ops, blocks, precond_dev, (cudaStream_t)stream);
+}
+
 size_t mueller_solve_workspace_bytes(const mueller_operator* op, int32_t r,
                                      const mueller_solver_opts* o) {
   if (!op || !o || r < 1) return 0;
@@ -820,7 +853,8 @@ mueller_status mueller_matvec_mrhs(const mueller_operator* op, const void* X, vo
   if (!work || work_bytes < mrhs_work_bytes(N, r))
     return fail(MUELLER_ERR_INVALID_ARG, "workspace missing or too small");
   cudaStream_t s = (cudaStream_t)stream;
-  mueller_status st = mrhs_matvec_c64(op->Z_dev, N, op->ldz, X, Y, r, work, s);
+  mueller_status st = mrhs_matvec_c64(op->Z_dev, N, op->ldz, X, Y, r, work, s, nullptr,
+                                      (op->flags & MUELLER_OP_K1_MIRRORED) ? 1 : 0);
   if (!st) st = near_apply_c64(op->mesh, op->near_dev, X, Y, r, s);
   if (!st) st = mrhs_check_error(work, N, r, s);
   return st;

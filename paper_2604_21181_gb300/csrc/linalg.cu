@@ -1249,9 +1249,10 @@ __global__ void givens_b_kernel(int j, int m, int r, double2* __restrict__ hacc,
 
 // ------------------------------------------------ fused Arnoldi step tail
 // Grid-wide barrier of a cooperative launch (every CTA resident): arrival
-// counter bar[0], generation bar[1].  The wait is bounded: after about a
-// second without the generation changing, err is set and the CTA goes on
-// (the host reads err and reports a timeout; results are then void).
+// counter bar[0], generation bar[1].  The wait is bounded: after 2^31 clock
+// cycles (about a second) without the generation changing, err is set and
+// the CTA goes on (the host reads err and reports a timeout; the results of
+// that step are then void).
 __device__ void grid_barrier(unsigned* bar, unsigned nblocks, int* err) {
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1263,10 +1264,9 @@ __device__ void grid_barrier(unsigned* bar, unsigned nblocks, int* err) {
       __threadfence();
       atomicAdd(bar + 1, 1u);
     } else {
-      long long spins = 0;
+      const long long t0 = clock64();
       while (*vgen == gen) {
-        __nanosleep(64);
-        if (++spins > (1ll << 24)) {
+        if (clock64() - t0 > (1ll << 31)) {
           atomicExch(err, 1);
           break;
         }
@@ -1277,7 +1277,12 @@ __device__ void grid_barrier(unsigned* bar, unsigned nblocks, int* err) {
   __syncthreads();
 }
 
+// up to this many (right-hand side, basis vector) coefficients, every CTA
+// of the Arnoldi step reduces all partial dot products itself
+constexpr int kTailDirect = 1024;
+
 struct TailArgs {
+  int direct;       // nonzero: r (j + 1) <= kTailDirect and few CTAs
   const float2* V;  // Krylov basis V[(l r + s) N + i], l <= j read, l = j + 1 written
   float2* w;        // A z_j for the r right-hand sides (orthogonalised in place)
   int64_t N;
@@ -1310,6 +1315,7 @@ struct TailArgs {
 // the host may queue steps ahead and read the flag only now and then.
 __global__ void __launch_bounds__(256) arnoldi_tail_kernel(TailArgs a) {
   if (*a.stop) return;  // read by every CTA before the first barrier: uniform
+  __shared__ double sh_h[2 * kTailDirect];
   const unsigned P = gridDim.x, c = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r = a.r, nl = a.j + 1, m1 = a.m + 1;
@@ -1317,18 +1323,29 @@ __global__ void __launch_bounds__(256) arnoldi_tail_kernel(TailArgs a) {
   const int64_t i0 = (int64_t)c * ch, i1 = min(a.N, i0 + ch), len = max((int64_t)0, i1 - i0);
   const int npair = r * nl;
   for (int pass = 0; pass < 2; ++pass) {
-    // partial dots conj(v_l[s]) . w[s] over this CTA's chunk, one warp per pair
+    // partial dots conj(v_l[s]) . w[s] over this CTA's chunk, one warp per
+    // pair, four independent accumulators per lane (loads in flight)
     for (int p = warp; p < npair; p += 8) {
       const int s = p / nl, l = p % nl;
       const float2* v = a.V + ((int64_t)l * r + s) * a.N;
       const float2* ww = a.w + (int64_t)s * a.N;
-      float ar = 0.f, ai = 0.f;
-      for (int64_t i = i0 + lane; i < i1; i += 32) {
-        const float2 x = v[i], y = ww[i];
-        ar = fmaf(x.x, y.x, fmaf(x.y, y.y, ar));
-        ai = fmaf(x.x, y.y, fmaf(-x.y, y.x, ai));
+      float ar[4] = {0.f, 0.f, 0.f, 0.f}, ai[4] = {0.f, 0.f, 0.f, 0.f};
+      int64_t i = i0 + lane;
+      for (; i + 96 < i1; i += 128) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float2 x = v[i + 32 * u], y = ww[i + 32 * u];
+          ar[u] = fmaf(x.x, y.x, fmaf(x.y, y.y, ar[u]));
+          ai[u] = fmaf(x.x, y.y, fmaf(-x.y, y.x, ai[u]));
+        }
       }
-      double dr = ar, di = ai;
+      for (; i < i1; i += 32) {
+        const float2 x = v[i], y = ww[i];
+        ar[0] = fmaf(x.x, y.x, fmaf(x.y, y.y, ar[0]));
+        ai[0] = fmaf(x.x, y.y, fmaf(-x.y, y.x, ai[0]));
+      }
+      double dr = (double)(ar[0] + ar[1]) + (double)(ar[2] + ar[3]);
+      double di = (double)(ai[0] + ai[1]) + (double)(ai[2] + ai[3]);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         dr += __shfl_xor_sync(0xffffffffu, dr, o);
@@ -1337,6 +1354,52 @@ __global__ void __launch_bounds__(256) arnoldi_tail_kernel(TailArgs a) {
       if (lane == 0) a.part[((int64_t)c * r + s) * m1 + l] = make_double2(dr, di);
     }
     grid_barrier(a.bar, P, a.err);
+    if (a.direct) {
+      // few partials: every CTA sums all of them itself (one barrier less);
+      // CTA 0 keeps the running sums for the Givens step
+      double2* hs = reinterpret_cast<double2*>(sh_h);
+      for (int p = warp; p < npair; p += 8) {
+        const int s = p / nl, l = p % nl;
+        double dr = 0, di = 0;
+        for (unsigned q = lane; q < P; q += 32) {
+          const double2 t = a.part[((int64_t)q * r + s) * m1 + l];
+          dr += t.x;
+          di += t.y;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          dr += __shfl_xor_sync(0xffffffffu, dr, o);
+          di += __shfl_xor_sync(0xffffffffu, di, o);
+        }
+        if (lane == 0) {
+          hs[p] = make_double2(dr, di);
+          if (c == 0) {
+            double2* acc = a.hacc + (int64_t)s * (a.m + 2) + l;
+            acc->x += dr;
+            acc->y += di;
+          }
+        }
+      }
+      __syncthreads();
+      // w[s] -= sum_l h[s][l] v_l[s] on this CTA's chunk
+      for (int64_t t = threadIdx.x; t < (int64_t)r * len; t += blockDim.x) {
+        const int s = (int)(t / len);
+        const int64_t i = i0 + t % len;
+        float2* wp = a.w + (int64_t)s * a.N + i;
+        float ar = wp->x, ai = wp->y;
+#pragma unroll 4
+        for (int l = 0; l < nl; ++l) {
+          const double2 hd = hs[s * nl + l];
+          const float hr = (float)hd.x, hi = (float)hd.y;
+          const float2 v = a.V[((int64_t)l * r + s) * a.N + i];
+          ar = fmaf(-hr, v.x, fmaf(hi, v.y, ar));
+          ai = fmaf(-hr, v.y, fmaf(-hi, v.x, ai));
+        }
+        *wp = make_float2(ar, ai);
+      }
+      __syncthreads();
+      continue;
+    }
     // coefficient p = c, c + P, ...: sum of the P partials, by one warp each
     for (int p = c + P * warp; p < npair; p += P * 8) {
       const int s = p / nl, l = p % nl;
@@ -1544,6 +1607,62 @@ __global__ void __launch_bounds__(256) mbj_apply_b_kernel(const float2* __restri
   if (lane == 0) {
     const int64_t gi = i < half ? o + i : H + o + (i - half);
     z[(int64_t)s * N + gi] = make_float2(ar, ai);
+  }
+}
+
+// The same for RS right-hand sides at once (s0 = blockIdx.z * RS): the CTA
+// stages the block's piece of the RS vectors in shared memory (RS x n
+// complex64, dynamic), then each warp multiplies rows of the inverse with
+// all RS of them, so every inverse entry is read once for RS vectors.  Rows
+// kMbjRows per CTA (blockIdx.x).
+constexpr int kMbjRows = 64;
+template <int RS>
+__global__ void __launch_bounds__(256) mbj_apply_rs_kernel(const float2* __restrict__ inv, int64_t d,
+                                                           const int32_t* __restrict__ sz, int64_t B,
+                                                           int64_t H, int64_t N, int r,
+                                                           const float2* __restrict__ v,
+                                                           float2* __restrict__ z,
+                                                           const int* __restrict__ stop) {
+  if (stop && *stop) return;
+  extern __shared__ float2 sv[];  // [RS][n]
+  const int b = blockIdx.y, s0 = blockIdx.z * RS;
+  const int n = sz[b], half = n / 2;
+  const int i0 = blockIdx.x * kMbjRows;
+  if (i0 >= n) return;  // uniform for the CTA
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t o = (int64_t)b * B;
+  for (int t = threadIdx.x; t < RS * n; t += blockDim.x) {
+    const int k = t / n, j = t % n;
+    const int64_t gj = j < half ? o + j : H + o + (j - half);
+    sv[t] = s0 + k < r ? v[(int64_t)(s0 + k) * N + gj] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const int i1 = min(n, i0 + kMbjRows);
+  for (int i = i0 + warp; i < i1; i += 8) {
+    const float2* row = inv + (int64_t)b * d * d + (int64_t)i * d;
+    float ar[RS], ai[RS];
+#pragma unroll
+    for (int k = 0; k < RS; ++k) ar[k] = ai[k] = 0.f;
+    for (int j = lane; j < n; j += 32) {
+      const float2 m = row[j];
+#pragma unroll
+      for (int k = 0; k < RS; ++k) {
+        const float2 x = sv[k * n + j];
+        ar[k] = fmaf(m.x, x.x, fmaf(-m.y, x.y, ar[k]));
+        ai[k] = fmaf(m.x, x.y, fmaf(m.y, x.x, ai[k]));
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < RS; ++k)
+#pragma unroll
+      for (int q = 16; q > 0; q >>= 1) {
+        ar[k] += __shfl_xor_sync(0xffffffffu, ar[k], q);
+        ai[k] += __shfl_xor_sync(0xffffffffu, ai[k], q);
+      }
+    const int64_t gi = i < half ? o + i : H + o + (i - half);
+#pragma unroll
+    for (int k = 0; k < RS; ++k)
+      if (lane == k && s0 + k < r) z[(int64_t)(s0 + k) * N + gi] = make_float2(ar[k], ai[k]);
   }
 }
 
@@ -1932,6 +2051,123 @@ mueller_status precond_build(const mueller_operator* op, int64_t block, void* P,
   return MUELLER_OK;
 }
 
+// Block-Jacobi preconditioners of n operators (bodies) at once: the blocks
+// of every body (same block dimension d = 2 min(B, H)) are gathered into one
+// array and factorised by one batched LU, so that many small bodies fill the
+// GPU together; each body's inverses then go to its own buffer.  Bodies with
+// another d are built in their own batch.
+mueller_status precond_build_batch(int n, const mueller_operator* ops, const int64_t* blocks,
+                                   void* const* P, cudaStream_t s) {
+  std::vector<BlockLayout> Ls(n);
+  for (int b = 0; b < n; ++b) Ls[b] = layout(4 * ops[b].mesh->nn, blocks[b]);
+  std::vector<int> done(n, 0);
+  for (int lead = 0; lead < n; ++lead) {
+    if (done[lead]) continue;
+    const int64_t d = Ls[lead].d;
+    const int dtype = ops[lead].dtype;
+    std::vector<int> grp;
+    for (int b = lead; b < n; ++b)
+      if (!done[b] && Ls[b].d == d && ops[b].dtype == dtype) {
+        grp.push_back(b);
+        done[b] = 1;
+      }
+    // block offsets of the group's bodies in the batch
+    std::vector<int64_t> off(grp.size() + 1, 0);
+    std::vector<int32_t> sz_all;
+    for (size_t g = 0; g < grp.size(); ++g) {
+      off[g + 1] = off[g] + Ls[grp[g]].nb;
+      sz_all.insert(sz_all.end(), Ls[grp[g]].sz.begin(), Ls[grp[g]].sz.end());
+    }
+    const int64_t nbt = off.back();
+    const size_t elem = dtype == MUELLER_C128 ? 16 : 8;
+    double2* A = nullptr;
+    int32_t* piv = nullptr;
+    int32_t* sz_dev = nullptr;
+    void* inv = nullptr;
+    float2* A32 = nullptr;
+    mueller_status st = MUELLER_OK;
+    auto take = [&](void** ptr, size_t bytes) {
+      if (st) return;
+      cudaError_t e = cudaMallocAsync(ptr, bytes, s);
+      if (e != cudaSuccess) st = cuda_fail(e, "batched precond workspace");
+    };
+    take((void**)&A, (size_t)nbt * d * d * sizeof(double2));
+    take((void**)&piv, (size_t)nbt * d * sizeof(int32_t) + 64);
+    take((void**)&sz_dev, (size_t)nbt * sizeof(int32_t));
+    take(&inv, (size_t)nbt * d * d * elem);
+    int32_t* status = piv ? piv + nbt * d : nullptr;
+    if (!st) {
+      cudaError_t e = cudaMemcpyAsync(sz_dev, sz_all.data(), nbt * sizeof(int32_t),
+                                      cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int32_t), s);
+      if (e != cudaSuccess) st = cuda_fail(e, "batched precond setup");
+    }
+    for (size_t g = 0; g < grp.size() && !st; ++g) {
+      const mueller_operator* op = &ops[grp[g]];
+      const BlockLayout& L = Ls[grp[g]];
+      const mueller_mesh* m = op->mesh;
+      double2* Ab = A + off[g] * d * d;
+      const int32_t* szb = sz_dev + off[g];
+      dim3 gg(nblk(d, 128), d, L.nb);
+      if (dtype == MUELLER_C128) {
+        { Prof prof_("gather_blocks_kernel", s); gather_blocks_kernel<MUELLER_C128><<<gg, 128, 0, s>>>(op->Z_dev, op->ldz, L.H, L.B, d, szb, Ab); }
+      } else {
+        { Prof prof_("gather_blocks_kernel", s); gather_blocks_kernel<MUELLER_C64_NEAR64><<<gg, 128, 0, s>>>(op->Z_dev, op->ldz, L.H, L.B, d, szb, Ab); }
+        { Prof prof_("gather_near_kernel", s); gather_near_kernel<<<nblk(m->nn, 8), 256, 0, s>>>(m->nn, m->near_rowptr, m->near_col,
+                                                            (const double2*)op->near_dev, L.B, d, szb, Ab); }
+      }
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) st = cuda_fail(e, "batched precond gather");
+    }
+    if (!st) {
+      if (dtype == MUELLER_C128) {
+        st = batched_lu_inverse<double2>(A, d, (int)nbt, sz_dev, piv, status, (double2*)inv, s);
+      } else {
+        st = batched_lu_inverse<double2>(A, d, (int)nbt, sz_dev, piv, status, nullptr, s);
+        const int64_t cnt = nbt * d * d;
+        take((void**)&A32, cnt * sizeof(float2));
+        if (!st) {
+          { Prof prof_("c128_to_c64_kernel", s); c128_to_c64_kernel<<<nblk(cnt, 256), 256, 0, s>>>(A, A32, cnt); }
+          MU_CHECK_LAUNCH("c128_to_c64_kernel");
+          st = block_inverse<float2>(A32, d, (int)nbt, sz_dev, piv, (float2*)inv, s);
+        }
+      }
+    }
+    // each body's inverses and block sizes into its buffer (layout of precond_build)
+    for (size_t g = 0; g < grp.size() && !st; ++g) {
+      const BlockLayout& L = Ls[grp[g]];
+      char* Pb = (char*)P[grp[g]];
+      const size_t bytes = (size_t)L.nb * d * d * elem;
+      cudaError_t e = cudaMemcpyAsync(Pb, (const char*)inv + (size_t)off[g] * d * d * elem, bytes,
+                                      cudaMemcpyDeviceToDevice, s);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(Pb + bytes, L.sz.data(), L.nb * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) st = cuda_fail(e, "batched precond copy-out");
+    }
+    int32_t hst = 0;
+    if (!st) {
+      cudaError_t e = cudaMemcpyAsync(&hst, status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) st = cuda_fail(e, "batched precond status");
+    }
+    if (A) cudaFreeAsync(A, s);
+    if (piv) cudaFreeAsync(piv, s);
+    if (sz_dev) cudaFreeAsync(sz_dev, s);
+    if (inv) cudaFreeAsync(inv, s);
+    if (A32) cudaFreeAsync(A32, s);
+    if (st) return st;
+    if (hst) {
+      const int64_t k = hst - 1;
+      size_t g = 0;
+      while (g + 1 < off.size() && off[g + 1] <= k) ++g;
+      set_error("zero pivot in block-Jacobi block " + std::to_string(k - off[g]) + " of body " +
+                std::to_string(grp[g]));
+      return MUELLER_ERR_SINGULAR_BLOCK;
+    }
+  }
+  return MUELLER_OK;
+}
+
 // ================================================================= solvers
 namespace {
 
@@ -2156,13 +2392,16 @@ struct LockWork {
   int* bad;        // [r] residual estimate not a number
 };
 
-// CTAs of the fused Arnoldi step: one per SM, at least 32 entries each
-static int tail_ctas(int64_t N) {
+// CTAs of the fused Arnoldi step: about one per 1024 vector entries (the
+// Krylov basis is read from L2 by every CTA's SM), at least 32 and at most
+// one per SM, and at least 32 entries per CTA
+static int tail_ctas(int64_t N, int r) {
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
     nsm = 1;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(nsm, (N + 31) / 32));
+  const int64_t want = std::max<int64_t>(32, (int64_t)r * N / 1024);
+  return (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)nsm, want, (N + 31) / 32}));
 }
 
 static size_t lock_bytes(int64_t N, int r, int m, int64_t nnzb) {
@@ -2184,7 +2423,7 @@ static size_t lock_bytes(int64_t N, int r, int m, int64_t nnzb) {
   add((size_t)r * 4);
   if (r >= 2) add(mrhs_work_bytes(N, r));
   if (nnzb > 0) add((size_t)nnzb * 16 * 8);
-  const int P = tail_ctas(N);
+  const int P = tail_ctas(N, r);
   add((size_t)P * r * (m + 1) * 16);
   add((size_t)r * (m + 1) * 16);
   add((size_t)P * r * 8);
@@ -2231,7 +2470,7 @@ static LockWork carve_lock(char* p, int64_t N, int r, int m, int64_t nnzb) {
   W.kk = (int*)take((size_t)r * 4);
   W.mwork = r >= 2 ? take(mrhs_work_bytes(N, r)) : nullptr;
   W.near32 = nnzb > 0 ? (float2*)take((size_t)nnzb * 16 * 8) : nullptr;
-  W.P = tail_ctas(N);
+  W.P = tail_ctas(N, r);
   W.tpart = (double2*)take((size_t)W.P * r * (m + 1) * 16);
   W.th = (double2*)take((size_t)r * (m + 1) * 16);
   W.tnpart = (double*)take((size_t)W.P * r * 8);
@@ -2247,7 +2486,8 @@ static mueller_status lock_matvec(const InnerOp& I, const LockWork& W, const flo
   const mueller_mesh* m = I.op->mesh;
   const int64_t N = W.N;
   if (W.r >= 2) {
-    mueller_status st = mrhs_matvec_c64(I.op->Z_dev, N, I.op->ldz, X, Y, W.r, W.mwork, s, stop);
+    mueller_status st = mrhs_matvec_c64(I.op->Z_dev, N, I.op->ldz, X, Y, W.r, W.mwork, s, stop,
+                                         (I.op->flags & MUELLER_OP_K1_MIRRORED) ? 1 : 0);
     if (st) return st;
   } else {
     int fused = 0;
@@ -2263,6 +2503,16 @@ static mueller_status lock_precond(const InnerOp& I, const LockWork& W, const fl
                                    cudaStream_t s, const int* stop = nullptr) {
   if (!I.op->precond_dev) {
     MU_CUDA(cudaMemcpyAsync(z, v, (size_t)W.r * W.N * 8, cudaMemcpyDeviceToDevice, s));
+    return MUELLER_OK;
+  }
+  constexpr int RS = 8;
+  const size_t smem = (size_t)RS * I.L.d * sizeof(float2);
+  if (W.r >= 2 && smem <= 200 * 1024) {
+    dim3 g(nblk(I.L.d, kMbjRows), I.L.nb, (W.r + RS - 1) / RS);
+    MU_CUDA(cudaFuncSetAttribute(mbj_apply_rs_kernel<RS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    { Prof prof_("mbj_apply_rs_kernel", s); mbj_apply_rs_kernel<RS><<<g, 256, smem, s>>>(I.inv32, I.L.d, I.sz_dev, I.L.B, I.L.H, W.N, W.r, v, z, stop); }
+    MU_CHECK_LAUNCH("mbj_apply_rs_kernel");
     return MUELLER_OK;
   }
   dim3 g(nblk(I.L.d, 8), I.L.nb, W.r);
@@ -2346,6 +2596,7 @@ static mueller_status lock_gmres(const InnerOp& I, LockWork& W, double tol, int 
       ta.jstop = W.flags + 1;
       ta.err = W.flags + 2;
       ta.bar = (unsigned*)(W.flags + 4);
+      ta.direct = (r * (m + 1) <= kTailDirect && (int64_t)W.P * r * (m + 1) <= 16384) ? 1 : 0;
       int queued = 0, hf[3] = {0, 0, 0};
       for (int j = 0; j < m && iters + queued < maxit; ++j) {
         const float2* Vj = W.V + (int64_t)j * r * N;

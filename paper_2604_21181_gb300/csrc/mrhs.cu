@@ -356,6 +356,16 @@ struct ZnArgs {
   float* Y;  // complex64 r x N, accumulated (atomic adds of the real parts)
   int* err;
   const int* stop;  // nonzero: skip the product (solver converged); may be null
+  // Z11 = -Z00 (three quarters of Z read), stacked with 4 nprime <= 128:
+  // mirror 1: the Z rows of the upper half (Z00 | Z01, K over 2N) against
+  //   A = [X'(k); X'(k + N)] for k < N and [X'(k); 0] beyond, lanes
+  //   [0, 2 nprime) -> rows i, lanes [2 nprime, 4 nprime) -> -(rows H + i);
+  // mirror 2: the Z rows of the lower half (Z10 only, K over N) against
+  //   A = [X'(k); -], lanes [0, 2 nprime) -> rows H + i.
+  // A is then loaded as two boxes of 2 nprime rows (box rows abox).
+  int mirror;
+  int64_t H;
+  int xoob;  // an aligned K coordinate beyond the operand: the box reads zeros
 };
 
 // dynamic shared memory: [stages][Z 16 KB | Zlo 16 KB | A0 8 KB | A1 8 KB (unstacked)]
@@ -375,6 +385,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint64_t* accf = empty + a.stages;
   uint32_t* tmem_slot = (uint32_t*)(accf + 1);
   volatile int* bail = (volatile int*)(tmem_slot + 1);
+  const uint32_t half_box = (uint32_t)(2 * a.nprime) * ZBK * 4;  // bytes of one A half (mirror)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t n0 = (int64_t)blockIdx.x * ZN;
@@ -418,11 +429,22 @@ __global__ void __launch_bounds__(THREADS, 1)
           *bail = 1;
           break;
         }
-        mbar_expect_tx(&full[s], ZB + (a.stacked ? 1 : 2) * AB);
         const int kc = (kt0 + it) * ZBK;
-        tma_load_2d(Z_of(s), &mapZ, &full[s], kc, (int)n0);
-        tma_load_2d(A0_of(s), &mapA0, &full[s], kc, 0);
-        if (!a.stacked) tma_load_2d(A1_of(s), &mapA1, &full[s], kc, 0);
+        if (a.mirror) {
+          // two A boxes of 2 nprime rows: X'(kc) and, upper half only,
+          // X'(kc + N) below it (zeros for the Z01 columns, kc >= N)
+          mbar_expect_tx(&full[s], ZB + (a.mirror == 1 ? 2 : 1) * half_box);
+          tma_load_2d(Z_of(s), &mapZ, &full[s], kc, (int)n0);
+          tma_load_2d(A0_of(s), &mapA1, &full[s], kc, 0);
+          if (a.mirror == 1)
+            tma_load_2d(A0_of(s) + half_box, &mapA1, &full[s],
+                        kc < (int)a.N ? kc + (int)a.N : a.xoob, 0);
+        } else {
+          mbar_expect_tx(&full[s], ZB + (a.stacked ? 1 : 2) * AB);
+          tma_load_2d(Z_of(s), &mapZ, &full[s], kc, (int)n0);
+          tma_load_2d(A0_of(s), &mapA0, &full[s], kc, 0);
+          if (!a.stacked) tma_load_2d(A1_of(s), &mapA1, &full[s], kc, 0);
+        }
         ++issued;
       }
       for (int it = max(0, issued - a.stages); it < issued; ++it)
@@ -490,9 +512,23 @@ __global__ void __launch_bounds__(THREADS, 1)
     asm volatile("tcgen05.fence::after_thread_sync;");
     const int quarter = warp & 3;
     const int l = quarter * 32 + lane;
-    const int comp = a.stacked && l >= a.nprime ? l - a.nprime : l;
-    const bool valid = ok && l < (a.stacked ? 2 * a.nprime : a.nprime) && (comp >> 1) < a.r;
-    float* yb = a.Y + 2 * ((int64_t)(comp >> 1) * a.N) + (comp & 1);
+    int comp, nlanes;
+    float sgn = 1.f;
+    int64_t rows = a.N, roff = 0;  // output rows roff + (n0 + ...), below rows
+    if (a.mirror) {
+      const int np2 = 2 * a.nprime;
+      const int ll = l % np2;
+      comp = ll >= a.nprime ? ll - a.nprime : ll;
+      nlanes = a.mirror == 1 ? 2 * np2 : np2;
+      rows = a.H;
+      if (a.mirror == 2 || l >= np2) roff = a.H;
+      if (a.mirror == 1 && l >= np2) sgn = -1.f;  // Z11 = -Z00
+    } else {
+      comp = a.stacked && l >= a.nprime ? l - a.nprime : l;
+      nlanes = a.stacked ? 2 * a.nprime : a.nprime;
+    }
+    const bool valid = ok && l < nlanes && (comp >> 1) < a.r;
+    float* yb = a.Y + 2 * ((int64_t)(comp >> 1) * a.N + roff) + (comp & 1);
     const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
     for (int c0 = 0; c0 < ZN; c0 += 16) {
       uint32_t v[16];
@@ -502,7 +538,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
           const int64_t row = n0 + c0 + e;
-          if (row < a.N) atomicAdd(yb + 2 * row, __uint_as_float(v[e]));
+          if (row < rows) atomicAdd(yb + 2 * row, sgn * __uint_as_float(v[e]));
         }
       }
     }
@@ -591,7 +627,7 @@ size_t mrhs_work_bytes(int64_t N, int r) {
 // Y (complex64 r x N) = Z (complex64, N x ldz) X (complex64 r x N); work:
 // mrhs_work_bytes(N, r) bytes of device scratch.
 mueller_status mrhs_matvec_c64(const void* Z, int64_t N, int64_t ldz, const void* X, void* Y,
-                               int r, void* work, cudaStream_t s, const int* stop) {
+                               int r, void* work, cudaStream_t s, const int* stop, int mirrored) {
   if (r < 1 || r > 128) {
     set_error("tensor-core product supports 1..128 right-hand sides");
     return MUELLER_ERR_INVALID_ARG;
@@ -616,6 +652,50 @@ mueller_status mrhs_matvec_c64(const void* Z, int64_t N, int64_t ldz, const void
         (const float2*)X, N, r, nprime, Bhi, Blo, stop);
   }
   MU_CHECK_LAUNCH("build_bprime_kernel");
+  if (mirrored && 4 * nprime <= BM && (N & 1) == 0) {
+    // Z11 = -Z00: the upper rows read Z00 once for both diagonal blocks
+    const int64_t H = N / 2;
+    CUtensorMap mZt, mZb, mA;
+    if (!make_map(&mZt, Z, (uint64_t)2 * N, (uint64_t)H, (uint64_t)ldz * 8, ZBK, ZN,
+                  CU_TENSOR_MAP_SWIZZLE_64B) ||
+        // lower rows: Z10 only (N real columns; a K tile across column N
+        // reads zeros there instead of Z11)
+        !make_map(&mZb, (const float*)Z + (size_t)H * ldz * 2, (uint64_t)N, (uint64_t)H,
+                  (uint64_t)ldz * 8, ZBK, ZN, CU_TENSOR_MAP_SWIZZLE_64B) ||
+        !make_map(&mA, Bhi, (uint64_t)2 * N, 2 * (uint64_t)nprime, (uint64_t)2 * N * 4, ZBK,
+                  2 * nprime, CU_TENSOR_MAP_SWIZZLE_64B)) {
+      set_error("cuTensorMapEncodeTiled failed (driver entry point or layout)");
+      return MUELLER_ERR_CUDA;
+    }
+    const size_t stage_bytes = 2 * (size_t)ZN * ZBK * 4 + (size_t)BM * ZBK * 4;
+    const int stages = (int)std::min<size_t>(8, (SMEM_BUDGET - 2048) / stage_bytes);
+    const size_t smem = 1024 + stages * stage_bytes + (3 * stages + 1) * 8 + 16;
+    MU_CUDA(cudaFuncSetAttribute(mrhs_zn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t ntiles = cdiv(H, ZN);
+    for (int half = 1; half <= 2; ++half) {
+      ZnArgs z;
+      z.N = N;
+      z.nprime = nprime;
+      z.r = r;
+      z.ktiles = (int)cdiv(half == 1 ? 2 * N : N, ZBK);
+      z.stacked = 1;
+      z.Y = (float*)Y;
+      z.err = err;
+      z.stop = stop;
+      z.mirror = half;
+      z.H = H;
+      z.xoob = (int)(cdiv(2 * N, ZBK) * ZBK + ZBK);
+      z.stages = stages;
+      int ksplit = (int)std::max<int64_t>(1, std::min<int64_t>(z.ktiles / 16, cdiv(4 * 152, ntiles)));
+      z.kchunk = (int)cdiv(z.ktiles, ksplit);
+      ksplit = (int)cdiv(z.ktiles, z.kchunk);
+      Prof prof_("mrhs_zn_kernel", s);
+      mrhs_zn_kernel<<<dim3((unsigned)ntiles, (unsigned)ksplit), THREADS, smem, s>>>(
+          half == 1 ? mZt : mZb, mA, mA, z);
+    }
+    MU_CHECK_LAUNCH("mrhs_zn_kernel (mirrored)");
+    return MUELLER_OK;
+  }
   if (nprime <= BM) {
     // Z on the N side: 256 Z rows per MMA
     const int zstacked = 2 * nprime <= BM ? 1 : 0;
@@ -639,6 +719,9 @@ mueller_status mrhs_matvec_c64(const void* Z, int64_t N, int64_t ldz, const void
     z.Y = (float*)Y;
     z.err = err;
     z.stop = stop;
+    z.mirror = 0;
+    z.H = N / 2;
+    z.xoob = 0;
     const int64_t ntiles = cdiv(N, ZN);
     int ksplit = (int)std::max<int64_t>(1, std::min<int64_t>(z.ktiles / 16, cdiv(4 * 152, ntiles)));
     z.kchunk = (int)cdiv(z.ktiles, ksplit);

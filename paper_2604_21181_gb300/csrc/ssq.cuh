@@ -98,6 +98,16 @@ __host__ __device__ __forceinline__ int ss_shared_x(int cls, int reg) {
   return reg == 0;
 }
 
+// Regions whose shared side depends on (xi, eta1) only (Gauss indices a, b):
+// common vertex, both regions; common edge, regions 1 and 3.  The ns groups
+// (a, b, 0..ns-1) of such a region share the shared side's shape values, so
+// their trial-side sums can be added before the contraction.
+__host__ __device__ __forceinline__ bool ss_shared_ab(int cls, int reg) {
+  if (cls == 1) return true;
+  if (cls == 2) return reg == 1 || reg == 3;
+  return false;
+}
+
 // relabelled reference point (u, v) -> canonical (xi, eta); perm holds the
 // canonical corner of each relabelled corner in 2-bit fields
 __host__ __device__ __forceinline__ void to_canonical(int perm, double u, double v, double& xi, double& eta) {

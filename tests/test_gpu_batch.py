@@ -145,3 +145,62 @@ def test_batched_bodies_cross_sections_match_oracle_dense_solve(dtype):
         bal = np.abs(xs[:, 0] - xs[:, 1] - xs[:, 2]) / np.abs(xs[:, 0])
         bal_o = np.abs(xso[:, 0] - xso[:, 1] - xso[:, 2]) / np.abs(xso[:, 0])
         np.testing.assert_allclose(bal, bal_o, rtol=0, atol=3 * tol)
+
+
+@pytest.mark.parametrize("dtype", [mu.MUELLER_C128, mu.MUELLER_C64_NEAR64])
+def test_batched_block_jacobi_matches_per_body_builds(dtype):
+    """mueller_precond_build_batch factorises the blocks of uneven bodies in
+    one batched LU: each body's preconditioner equals the one built for it
+    alone (same kernels, block by block: FP64 inverses to 1e-13, complex64
+    inverses to FP32 rounding), and a solve with it takes the same number of
+    iterations."""
+    spec = workloads.multibody_spec()
+    pick = [13, 15, next(i for i, b in enumerate(spec) if b["level"] == 2),
+            next(i for i, b in enumerate(spec) if b["level"] == 3)]
+    ops, Bs, blocks = [], [], []
+    inc = workloads.fibonacci_plane_waves(1)
+    for i in pick:
+        b = spec[i]
+        xyz, tri6 = workloads.multibody_mesh(b)
+        m = mu.Mesh(xyz, tri6)
+        m.tangent_frame(0, out=False)
+        p = mu.Params(ka=b["ka"], eps_r=b["eps_r"], mu_r=b["mu_r"], ssq_order=3, frame_rule=0)
+        Z, near, B = mu.assemble(m, p, dtype, inc=inc)
+        ops.append(mu.Operator(m, Z, near, dtype))
+        Bs.append(B)
+        blocks.append(min(128, m.N // 2))
+    batch = [P.clone() for P in mu.precond_build_batch(ops, blocks)]
+    elem = 16 if dtype == mu.MUELLER_C128 else 8
+    cdt = torch.complex128 if dtype == mu.MUELLER_C128 else torch.complex64
+    tol = 1e-13 if dtype == mu.MUELLER_C128 else 1e-5
+    opts = mu.SolverOpts(mode=mu.SOLVE_GMRES if dtype == mu.MUELLER_C128 else mu.SOLVE_GMRES_IR,
+                         restart=30, tol=1e-8)
+    for op, B, blk, Pb in zip(ops, Bs, blocks, batch):
+        op.precond = Pb
+        Xb, ib = mu.solve(op, B, opts)
+        Ps = mu.precond_build(op, blk)
+        Xs, is_ = mu.solve(op, B, opts)
+        H = op.mesh.N // 2
+        nb, d = (H + blk - 1) // blk, 2 * min(blk, H)
+        n_inv = nb * d * d  # inverses [nb][d][d], then int32 sizes[nb]
+        a = Pb[: n_inv * elem].view(cdt)
+        c = Ps[: n_inv * elem].view(cdt)
+        assert torch.equal(Pb[n_inv * elem: n_inv * elem + 4 * nb],
+                           Ps[n_inv * elem: n_inv * elem + 4 * nb])  # block sizes
+        err = ((a - c).abs().max() / c.abs().max()).item()
+        assert err <= tol, err
+        assert abs(ib["iters"] - is_["iters"]) <= 1 and ib["relres"] <= 1e-8
+        e = (torch.linalg.norm(Xb - Xs) / torch.linalg.norm(Xs)).item()
+        assert e <= 1e-6, e
+
+
+def test_batched_block_jacobi_refuses_bad_arguments():
+    xyz, tri6 = workloads.icosphere_p2(0)
+    m = mu.Mesh(xyz, tri6)
+    m.tangent_frame(0, out=False)
+    Z, near, _ = mu.assemble(m, mu.Params(ka=1.0, eps_r=(2.0, 0.0), ssq_order=2),
+                             mu.MUELLER_C64_NEAR64)
+    ops = [mu.Operator(m, Z, near, mu.MUELLER_C64_NEAR64), mu.Operator(m, Z, None, mu.MUELLER_C64_NEAR64)]
+    with pytest.raises(mu.MuellerError) as e:
+        mu.precond_build_batch(ops, [8, 8])
+    assert e.value.status == 1 and "body 1" in str(e.value)
