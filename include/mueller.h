@@ -141,6 +141,13 @@ typedef struct {
  * means. */
 #define MUELLER_OP_K1_MIRRORED 1
 
+/* Operator flag: the call works with the adjoint Z^H instead of Z (and a
+ * preconditioner built from Z applied as (P^{-1})^H, the block-Jacobi
+ * preconditioner of Z^H).  For the adjoint solves of the gradients (Z^H lam
+ * = g^*).  Complex128 operators only, with mueller_matvec and mueller_solve
+ * in MUELLER_SOLVE_GMRES mode (else INVALID_ARG). */
+#define MUELLER_OP_ADJOINT 2
+
 /* The operator handed to the preconditioner and the solver. */
 typedef struct {
   const mueller_mesh* mesh; /* for the near-part layout (C64_NEAR64)         */
@@ -335,6 +342,47 @@ mueller_status mueller_dz_matvec(mueller_mesh* mesh, const mueller_params* param
 mueller_status mueller_zshape_vjp(mueller_mesh* mesh, const mueller_params* params,
                                   const void* lam_dev, const void* X_dev, double* grad,
                                   void* stream);
+
+/*
+ * mueller_rhs_shape_vjp -- the gradient of Re lam^H b(X) with respect to
+ * the node coordinates X, b the plane-wave right-hand side of Eqs. (rhs_E),
+ * (rhs_H) for the incident wave inc (host, 6: k-hat, p-hat, orthonormal):
+ * the db/dX term of the adjoint relation of mueller_zshape_vjp.  The
+ * derivatives of the rule points, weights and test frames are carried back
+ * to the node positions as there.  FP64.
+ *   lam_dev  complex128, length N = 4 n_nodes, the mesh's unknown order.
+ *   grad     host, n_nodes x 3, input node order; overwritten.  Synchronising.
+ * Needs mueller_tangent_frame with params->frame_rule (else STATE).
+ * Errors: INVALID_ARG, STATE, OOM, CUDA.
+ */
+mueller_status mueller_rhs_shape_vjp(mueller_mesh* mesh, const mueller_params* params,
+                                     const void* lam_dev, const double* inc, double* grad,
+                                     void* stream);
+
+/*
+ * mueller_cross_section_partials -- the partial derivatives of the three
+ * cross sections of mueller_far_field (C_ext, C_sca, C_abs, in that order)
+ * for one solution x and incident wave inc:
+ *   G_dev  device complex128 3 x N output: row o is conj(dC_o/dx), with
+ *          dC_o = 2 Re sum_u (dC_o/dx_u) dx_u for a change dx of x at fixed
+ *          geometry -- the right-hand side of the adjoint system
+ *          Z^H lam_o = G_o (mueller_solve with MUELLER_OP_ADJOINT).
+ *   grad   host 3 x n_nodes x 3 output: dC_o/dX at fixed x (through the
+ *          rule points, weights, normals and current frames), input node
+ *          order; overwritten.
+ *   xs     host 3 output (may be NULL): C_ext, C_sca, C_abs of x, computed
+ *          on the same rules.
+ * C_sca uses the sphere rule of mueller_far_field (n_theta Gauss-Legendre
+ * nodes in cos(theta) x n_phi trapezoid steps in phi).  With
+ * mueller_zshape_vjp and mueller_rhs_shape_vjp this gives the shape
+ * gradient dC_o/dX = grad_o + 2 Re(rhs_vjp(lam_o) - zshape_vjp(lam_o, x)).
+ * Synchronising.  Needs mueller_tangent_frame with params->frame_rule.
+ * Errors: INVALID_ARG, STATE, OOM, CUDA.
+ */
+mueller_status mueller_cross_section_partials(mueller_mesh* mesh, const mueller_params* params,
+                                              const void* X_dev, const double* inc,
+                                              int32_t n_theta, int32_t n_phi, void* G_dev,
+                                              double* grad, double* xs, void* stream);
 
 /* bytes of the complex128 near-part buffer of a loaded mesh */
 size_t mueller_near_bytes(const mueller_mesh* mesh);

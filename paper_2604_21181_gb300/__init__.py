@@ -15,6 +15,7 @@ from .api import (  # noqa: F401
     MUELLER_C128,
     MUELLER_C64_NEAR64,
     MUELLER_OP_K1_MIRRORED,
+    MUELLER_OP_ADJOINT,
     SOLVE_DENSE_LU,
     SOLVE_GMRES,
     SOLVE_GMRES_IR,
@@ -28,6 +29,8 @@ from .api import (  # noqa: F401
     assemble_batch,
     dz_matvec,
     zshape_vjp,
+    rhs_shape_vjp,
+    cross_section_partials,
     far_field,
     launch_count,
     load_library,

@@ -19,6 +19,7 @@ from . import buildlib as _build
 MUELLER_C128 = 0
 MUELLER_C64_NEAR64 = 1
 MUELLER_OP_K1_MIRRORED = 1
+MUELLER_OP_ADJOINT = 2
 SOLVE_DENSE_LU = 0
 SOLVE_GMRES = 1
 SOLVE_GMRES_IR = 2
@@ -83,7 +84,8 @@ EXPORTS = [
     "mueller_profile_enable", "mueller_profile_reset", "mueller_launch_count",
     "mueller_profile_get", "mueller_profile_names", "mueller_far_field_noalloc",
     "mueller_matvec_mrhs", "mueller_matvec_mrhs_workspace_bytes", "mueller_assemble_batch",
-    "mueller_precond_build_batch", "mueller_zshape_vjp",
+    "mueller_precond_build_batch", "mueller_zshape_vjp", "mueller_rhs_shape_vjp",
+    "mueller_cross_section_partials",
 ]
 
 _lib = None
@@ -116,6 +118,9 @@ def load_library(build_if_missing: bool = True):
         "mueller_assemble": (C.c_int, [vp, C.POINTER(CParams), i32, vp, i64, vp, vp, dp, i32, vp]),
         "mueller_dz_matvec": (C.c_int, [vp, C.POINTER(CParams), i32, vp, vp, vp]),
         "mueller_zshape_vjp": (C.c_int, [vp, C.POINTER(CParams), vp, vp, dp, vp]),
+        "mueller_rhs_shape_vjp": (C.c_int, [vp, C.POINTER(CParams), vp, dp, dp, vp]),
+        "mueller_cross_section_partials": (C.c_int, [vp, C.POINTER(CParams), vp, dp, i32, i32, vp,
+                                                     dp, dp, vp]),
         "mueller_near_bytes": (C.c_size_t, [vp]),
         "mueller_precond_build": (C.c_int, [C.POINTER(COperator), i64, vp, vp]),
         "mueller_precond_bytes": (C.c_size_t, [i64, i64]),
@@ -357,6 +362,42 @@ def zshape_vjp(mesh: Mesh, params: Params, lam, X, stream=None):
     return g
 
 
+def rhs_shape_vjp(mesh: Mesh, params: Params, lam, inc, stream=None):
+    """mueller_rhs_shape_vjp: gradient of Re lam^H b(X) with respect to the
+    node coordinates for one incident wave inc (6,), numpy (n_nodes, 3)."""
+    torch = _torch()
+    lam = _dev(lam, torch.complex128, "lam").reshape(-1)
+    if lam.numel() != mesh.N:
+        raise ValueError("lam must have length N")
+    inc = np.ascontiguousarray(inc, dtype=np.float64).reshape(6)
+    g = np.zeros((mesh.nn, 3))
+    p = params.c()
+    _check(mesh._lib.mueller_rhs_shape_vjp(mesh.h, C.byref(p), _ptr(lam), _dp(inc), _dp(g),
+                                           _stream(stream)))
+    return g
+
+
+def cross_section_partials(mesh: Mesh, params: Params, X, inc, n_theta: int = 48,
+                           n_phi: int = 96, stream=None):
+    """mueller_cross_section_partials for one solution X and incident wave inc.
+    Returns (G complex128 (3, N) CUDA tensor, the adjoint right-hand sides of
+    C_ext, C_sca, C_abs; grad numpy (3, n_nodes, 3), dC/dX at fixed X;
+    xs numpy (3,))."""
+    torch = _torch()
+    X = _dev(X, torch.complex128, "X").reshape(-1)
+    if X.numel() != mesh.N:
+        raise ValueError("X must have length N")
+    inc = np.ascontiguousarray(inc, dtype=np.float64).reshape(6)
+    G = torch.empty((3, mesh.N), dtype=torch.complex128, device=X.device)
+    g = np.zeros((3, mesh.nn, 3))
+    xs = np.zeros(3)
+    p = params.c()
+    _check(mesh._lib.mueller_cross_section_partials(mesh.h, C.byref(p), _ptr(X), _dp(inc),
+                                                    int(n_theta), int(n_phi), _ptr(G), _dp(g),
+                                                    _dp(xs), _stream(stream)))
+    return G, g, xs
+
+
 def assemble_batch(meshes, params, dtype: int = MUELLER_C64_NEAR64, incs=None, stream=None):
     """mueller_assemble_batch: one launch of each assembly kernel for all bodies.
     Returns a list of (Z, near, B) per body as CUDA tensors."""
@@ -408,10 +449,11 @@ class Operator:
     (through its raw pointer) keeps its tag: pass False then."""
 
     def __init__(self, mesh: Mesh, Z, near=None, dtype: int = MUELLER_C128, precond=None, block=0,
-                 mirrored=None):
+                 mirrored=None, adjoint: bool = False):
         self.mesh, self.Z, self.near, self.dtype = mesh, Z, near, dtype
         self.precond, self.block = precond, block
         self._mirrored = mirrored
+        self.adjoint = bool(adjoint)  # MUELLER_OP_ADJOINT: Z^H, (P^{-1})^H
 
     @property
     def mirrored(self) -> bool:
@@ -428,7 +470,8 @@ class Operator:
         o.Z_dev = self.Z.data_ptr()
         o.ldz = self.Z.stride(0)
         o.dtype = int(self.dtype)
-        o.flags = MUELLER_OP_K1_MIRRORED if self.mirrored else 0
+        o.flags = (MUELLER_OP_K1_MIRRORED if self.mirrored else 0) | \
+            (MUELLER_OP_ADJOINT if self.adjoint else 0)
         o.near_dev = self.near.data_ptr() if self.near is not None else None
         o.precond_dev = self.precond.data_ptr() if self.precond is not None else None
         o.block = int(self.block)

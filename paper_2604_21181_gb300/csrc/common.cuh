@@ -180,4 +180,12 @@ PhysConsts make_phys(const mueller_params* p);
 // of Re lam^H Z(X) x with respect to the node coordinates
 mueller_status zshape_vjp(mueller_mesh* m, const PhysConsts& P, int Q, int ns, const void* lam,
                           const void* x, double* grad, cudaStream_t s);
+// grad (host, n_nodes x 3) += the gradient of Re lam^H b(X)
+mueller_status rhs_shape_vjp(mueller_mesh* m, const PhysConsts& P, int Q, const void* lam,
+                             const double* inc, double* grad, cudaStream_t s);
+// dC/dx (device G, 3 x N, the right-hand sides of Z^H lam = G) and dC/dX at
+// fixed x (host grad, 3 x n_nodes x 3, added) for C_ext, C_sca, C_abs
+mueller_status cross_section_partials(mueller_mesh* m, const PhysConsts& P, int Q, const void* x,
+                                      const double* inc, int n_theta, int n_phi, void* G,
+                                      double* grad, double* xs, cudaStream_t s);
 }  // namespace mu

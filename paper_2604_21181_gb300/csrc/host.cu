@@ -695,6 +695,43 @@ mueller_status mueller_zshape_vjp(mueller_mesh* m, const mueller_params* p, cons
   return zshape_vjp(m, make_phys(p), p->q_regular, p->ssq_order, lam, X, grad, s);
 }
 
+mueller_status mueller_rhs_shape_vjp(mueller_mesh* m, const mueller_params* p, const void* lam,
+                                     const double* inc, double* grad, void* stream) {
+  if (!m || !lam || !inc || !grad) return fail(MUELLER_ERR_INVALID_ARG, "NULL argument");
+  mueller_status st = check_params(p);
+  if (st) return st;
+  if ((st = check_inc(inc, 1))) return st;
+  if (m->host_only) return fail(MUELLER_ERR_STATE, kHostOnlyMsg);
+  if (p->frame_rule != m->frame_rule || !m->has_frame)
+    return fail(MUELLER_ERR_STATE, "call mueller_tangent_frame with params->frame_rule first");
+  cudaStream_t s = (cudaStream_t)stream;
+  st = ensure_geometry(m, p->q_regular, s);
+  if (st) return st;
+  std::fill(grad, grad + 3 * m->nn, 0.0);
+  return rhs_shape_vjp(m, make_phys(p), p->q_regular, lam, inc, grad, s);
+}
+
+mueller_status mueller_cross_section_partials(mueller_mesh* m, const mueller_params* p,
+                                              const void* X, const double* inc, int32_t n_theta,
+                                              int32_t n_phi, void* G, double* grad, double* xs,
+                                              void* stream) {
+  if (!m || !X || !inc || !G || !grad) return fail(MUELLER_ERR_INVALID_ARG, "NULL argument");
+  mueller_status st = check_params(p);
+  if (st) return st;
+  if ((st = check_inc(inc, 1))) return st;
+  if (n_theta < 2 || n_phi < 3 || n_theta > 512 || n_phi > 1024)
+    return fail(MUELLER_ERR_INVALID_ARG, "n_theta must be in [2, 512] and n_phi in [3, 1024]");
+  if (m->host_only) return fail(MUELLER_ERR_STATE, kHostOnlyMsg);
+  if (p->frame_rule != m->frame_rule || !m->has_frame)
+    return fail(MUELLER_ERR_STATE, "call mueller_tangent_frame with params->frame_rule first");
+  cudaStream_t s = (cudaStream_t)stream;
+  st = ensure_geometry(m, p->q_regular, s);
+  if (st) return st;
+  std::fill(grad, grad + 9 * m->nn, 0.0);
+  return cross_section_partials(m, make_phys(p), p->q_regular, X, inc, n_theta, n_phi, G, grad,
+                                xs, s);
+}
+
 mueller_status mueller_assemble_batch(int32_t n_bodies, mueller_mesh* const* meshes,
                                       const mueller_params* params, int32_t dtype,
                                       void* const* Z, const int64_t* ldz, void* const* near,
@@ -812,6 +849,10 @@ mueller_status mueller_solve(const mueller_operator* op, const void* B, void* X,
     return fail(MUELLER_ERR_INVALID_ARG, "GMRES_IR needs a C64_NEAR64 operator");
   if (o->use_precond && !op->precond_dev)
     return fail(MUELLER_ERR_INVALID_ARG, "use_precond set but operator has no precond_dev");
+  if ((op->flags & MUELLER_OP_ADJOINT) &&
+      (op->dtype != MUELLER_C128 || o->mode != MUELLER_SOLVE_GMRES))
+    return fail(MUELLER_ERR_INVALID_ARG,
+                "the adjoint operator needs a complex128 operator and MUELLER_SOLVE_GMRES");
   if (op->mesh->host_only) return fail(MUELLER_ERR_STATE, kHostOnlyMsg);
   size_t need = solve_work(op, r, o);
   if (work && work_bytes < need) return fail(MUELLER_ERR_INVALID_ARG, "workspace too small");
@@ -832,6 +873,8 @@ mueller_status mueller_matvec(const mueller_operator* op, const void* X, void* Y
   if (r < 1) return fail(MUELLER_ERR_INVALID_ARG, "r must be >= 1");
   if (op->dtype == MUELLER_C64_NEAR64 && !op->near_dev)
     return fail(MUELLER_ERR_INVALID_ARG, "operator lacks its near part");
+  if ((op->flags & MUELLER_OP_ADJOINT) && op->dtype != MUELLER_C128)
+    return fail(MUELLER_ERR_INVALID_ARG, "the adjoint operator needs a complex128 operator");
   if (op->mesh->host_only) return fail(MUELLER_ERR_STATE, kHostOnlyMsg);
   if (work && work_bytes < op_matvec_work(op, r)) return fail(MUELLER_ERR_INVALID_ARG, "workspace too small");
   return op_matvec(op, X, Y, r, work, work_bytes, (cudaStream_t)stream);

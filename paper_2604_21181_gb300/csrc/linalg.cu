@@ -65,6 +65,40 @@ __global__ void __launch_bounds__(256) gemv_c128_kernel(int64_t N, const double2
   }
 }
 
+// y = Z^H x (complex128), the adjoint operator (MUELLER_OP_ADJOINT): 64
+// columns per CTA, 4 row lanes per column, rows split into gridDim.y chunks
+// whose partial sums meet in y by atomic additions (y zeroed by the caller).
+__global__ void __launch_bounds__(256) gemvh_c128_kernel(int64_t N, const double2* __restrict__ Z,
+                                                         int64_t ldz, const double2* __restrict__ x,
+                                                         double2* __restrict__ y, int64_t xs,
+                                                         int64_t ys) {
+  const int cl = threadIdx.x & 63, rl = threadIdx.x >> 6;
+  const int64_t j = (int64_t)blockIdx.x * 64 + cl;
+  const int s = blockIdx.z;
+  const int64_t chunk = (N + gridDim.y - 1) / gridDim.y;
+  const int64_t i0 = (int64_t)blockIdx.y * chunk, i1 = i0 + chunk < N ? i0 + chunk : N;
+  double ar = 0.0, ai = 0.0;
+  if (j < N) {
+    const double2* xv = x + s * xs;
+    for (int64_t i = i0 + rl; i < i1; i += 4) {
+      const double2 z = __ldg(Z + i * ldz + j), xi = __ldg(xv + i);
+      // conj(z) x
+      ar = fma(z.x, xi.x, fma(z.y, xi.y, ar));
+      ai = fma(z.x, xi.y, fma(-z.y, xi.x, ai));
+    }
+  }
+  __shared__ double sr[4][64], si[4][64];
+  sr[rl][cl] = ar;
+  si[rl][cl] = ai;
+  __syncthreads();
+  if (rl == 0 && j < N) {
+    const double vr = sr[0][cl] + sr[1][cl] + sr[2][cl] + sr[3][cl];
+    const double vi = si[0][cl] + si[1][cl] + si[2][cl] + si[3][cl];
+    atomicAdd(&y[s * ys + j].x, vr);
+    atomicAdd(&y[s * ys + j].y, vi);
+  }
+}
+
 // float -> double with integer instructions only (exact for every input:
 // the exponent is rebiased and the mantissa shifted; subnormal floats are
 // normalised through a leading-zero count).  The conversion instruction
@@ -869,6 +903,32 @@ __global__ void __launch_bounds__(256) mbj_apply_kernel(const BT* __restrict__ i
     z[gi].x = ar;
     z[gi].y = ai;
   }
+}
+
+// z = (P^{-1})^H v (complex128): block b's explicit inverse conjugate-
+// transposed, one thread per output entry (column i of the inverse; the
+// threads of a warp read consecutive entries of each row).
+__global__ void __launch_bounds__(128) mbj_apply_h_kernel(const double2* __restrict__ inv,
+                                                          int64_t d, const int32_t* __restrict__ sz,
+                                                          int64_t B, int64_t H,
+                                                          const double2* __restrict__ v,
+                                                          double2* __restrict__ z) {
+  const int b = blockIdx.y;
+  const int n = sz[b], half = n / 2;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t o = (int64_t)b * B;
+  const double2* M = inv + (int64_t)b * d * d;
+  double ar = 0.0, ai = 0.0;
+  for (int j = 0; j < n; ++j) {
+    const double2 m = M[(int64_t)j * d + i];
+    const int64_t gj = j < half ? o + j : H + o + (j - half);
+    const double2 x = v[gj];
+    ar = fma(m.x, x.x, fma(m.y, x.y, ar));
+    ai = fma(m.x, x.y, fma(-m.y, x.x, ai));
+  }
+  const int64_t gi = i < half ? o + i : H + o + (i - half);
+  z[gi] = make_double2(ar, ai);
 }
 
 __global__ void c128_to_c64_kernel(const double2* __restrict__ a, float2* __restrict__ b, int64_t n) {
@@ -1736,7 +1796,13 @@ mueller_status op_matvec(const mueller_operator* op, const void* X, void* Y, int
   (void)work_bytes;
   const mueller_mesh* m = op->mesh;
   const int64_t N = 4 * m->nn;
-  if (op->dtype == MUELLER_C128) {
+  if (op->dtype == MUELLER_C128 && (op->flags & MUELLER_OP_ADJOINT)) {
+    MU_CUDA(cudaMemsetAsync(Y, 0, (size_t)N * r * sizeof(double2), s));
+    dim3 grid(nblk(N, 64), 8, r);
+    { Prof prof_("gemvh_c128_kernel", s); gemvh_c128_kernel<<<grid, 256, 0, s>>>(N, (const double2*)op->Z_dev, op->ldz, (const double2*)X,
+                                           (double2*)Y, N, N); }
+    MU_CHECK_LAUNCH("gemvh_c128_kernel");
+  } else if (op->dtype == MUELLER_C128) {
     dim3 grid(nblk(N, 32), r);
     { Prof prof_("gemv_c128_kernel", s); gemv_c128_kernel<<<grid, 256, 0, s>>>(N, (const double2*)op->Z_dev, op->ldz, (const double2*)X,
                                           (double2*)Y, N, N, r); }
@@ -2261,6 +2327,11 @@ mueller_status inner_precond(const InnerOp& I, const VT* v, VT* z, cudaStream_t 
   }
   dim3 g(nblk(I.L.d, 8), I.L.nb);
   if constexpr (sizeof(VT) == 16) {
+    if (I.op->flags & MUELLER_OP_ADJOINT) {
+      { Prof prof_("mbj_apply_h_kernel", s); mbj_apply_h_kernel<<<dim3(nblk(I.L.d, 128), I.L.nb), 128, 0, s>>>((const double2*)I.op->precond_dev, I.L.d, I.sz_dev, I.L.B, I.L.H, (const double2*)v, (double2*)z); }
+      MU_CHECK_LAUNCH("mbj_apply_h_kernel");
+      return MUELLER_OK;
+    }
     { Prof prof_("mbj_apply_kernel<double2, double2>", s); mbj_apply_kernel<double2, double2><<<g, 256, 0, s>>>((const double2*)I.op->precond_dev, I.L.d,
                                                         I.sz_dev, I.L.B, I.L.H, v, z); }
   } else {

@@ -763,6 +763,291 @@ __global__ void frame_backprop_kernel(int64_t nn, const double* __restrict__ X,
   }
 }
 
+// ------------------------------------------------------- right-hand side
+// Re lam^H b (Eqs. rhs_E, rhs_H): b rows (h = 0, node, a) = sum_p W_p N(p)
+// (-s_a . p) e^{i phi_p}, (h = 1) = sum_p W_p N(p) (s_a . (k x p)) e^{i phi_p},
+// phi_p = k_a k . y_p; the adjoints of s_a, y and W at each rule point.
+__global__ void rhs_vjp_kernel(int64_t n, const double* __restrict__ qd,
+                               const double2* __restrict__ Lp, d3 kh, d3 ph, double ka,
+                               double* __restrict__ radj) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const double* rc = qd + t * QD_STRIDE;
+  const double2* L = Lp + t * 4;
+  const d3 hk = cross(kh, ph);
+  double sn, cs;
+  sincos(ka * dot(kh, ld3(rc)), &sn, &cs);
+  const double W = rc[18];
+  double vr = 0.0, vi = 0.0;
+  for (int a = 0; a < 2; ++a) {
+    // E_a = e^{i phi} (-L0a p + L1a hk): real and imaginary 3-vectors
+    const cx<double> l0 = cmk(L[a].x, L[a].y), l1 = cmk(L[2 + a].x, L[2 + a].y);
+    const cx<double> e = cmk(cs, sn);
+    const cx<double> c0 = cmul(e, l0), c1 = cmul(e, l1);
+    const d3 Er = sub(scl(c1.re, hk), scl(c0.re, ph));
+    const d3 Ei = sub(scl(c1.im, hk), scl(c0.im, ph));
+    const d3 sa = ld3(rc + 12 + 3 * a);
+    vr += dot(sa, Er);
+    vi += dot(sa, Ei);
+    double* g = radj + t * 19 + 12 + 3 * a;
+    g[0] += W * Er.x;
+    g[1] += W * Er.y;
+    g[2] += W * Er.z;
+  }
+  // d/dy of e^{i phi}: i k_a k -> Re(i k_a k W v) = -k_a W Im(v) k
+  double* g = radj + t * 19;
+  g[0] += -ka * W * vi * kh.x;
+  g[1] += -ka * W * vi * kh.y;
+  g[2] += -ka * W * vi * kh.z;
+  g[18] += vr;
+}
+
+// ------------------------------------------------------------ far field
+// Currents at the rule points: cur[p] = (W j, W j_m) (complex 3-vectors),
+// j = sum_b Xi_0b t_b, j_m = sum_b Xi_1b t_b (Sec. 4.1 basis).
+__global__ void far_currents_kernel(int64_t n, const double* __restrict__ qd,
+                                    const double2* __restrict__ Xp, double2* __restrict__ cur) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const double* rc = qd + t * QD_STRIDE;
+  const double2* X = Xp + t * 4;
+  const double W = rc[18];
+  for (int c = 0; c < 3; ++c) {
+    double2 j = make_double2(0, 0), m = make_double2(0, 0);
+    for (int b = 0; b < 2; ++b) {
+      const double tb = rc[6 + 3 * b + c];
+      j.x += X[b].x * tb;
+      j.y += X[b].y * tb;
+      m.x += X[2 + b].x * tb;
+      m.y += X[2 + b].y * tb;
+    }
+    cur[t * 6 + c] = make_double2(W * j.x, W * j.y);
+    cur[t * 6 + 3 + c] = make_double2(W * m.x, W * m.y);
+  }
+}
+
+// F(d) = (i k/4 pi) sum_p e^{-i k d.y_p} [P_d W j - d x W j_m], one CTA per
+// direction (the directions in dirs[nd][3])
+__global__ void __launch_bounds__(256) far_sum_kernel(int64_t np, const double* __restrict__ qd,
+                                                      const double2* __restrict__ cur,
+                                                      const double* __restrict__ dirs, double ka,
+                                                      double2* __restrict__ F) {
+  const int64_t di = blockIdx.x;
+  const d3 d = ld3(dirs + 3 * di);
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t p = threadIdx.x; p < np; p += blockDim.x) {
+    double sn, cs;
+    sincos(-ka * dot(d, ld3(qd + p * QD_STRIDE)), &sn, &cs);
+    const double2* c = cur + p * 6;
+    d3 jr = mk(c[0].x, c[1].x, c[2].x), ji = mk(c[0].y, c[1].y, c[2].y);
+    const d3 mr = mk(c[3].x, c[4].x, c[5].x), mi = mk(c[3].y, c[4].y, c[5].y);
+    jr = sub(sub(jr, scl(dot(d, jr), d)), cross(d, mr));
+    ji = sub(sub(ji, scl(dot(d, ji), d)), cross(d, mi));
+    // (cs + i sn)(jr + i ji)
+    acc[0] += cs * jr.x - sn * ji.x;
+    acc[1] += cs * ji.x + sn * jr.x;
+    acc[2] += cs * jr.y - sn * ji.y;
+    acc[3] += cs * ji.y + sn * jr.y;
+    acc[4] += cs * jr.z - sn * ji.z;
+    acc[5] += cs * ji.z + sn * jr.z;
+  }
+  __shared__ double red[6][256];
+  for (int k = 0; k < 6; ++k) red[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int k = 0; k < 6; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) {
+    // times i k/(4 pi)
+    const double f = ka * kC4pi, re = red[2 * threadIdx.x][0], im = red[2 * threadIdx.x + 1][0];
+    F[di * 3 + threadIdx.x] = make_double2(-f * im, f * re);
+  }
+}
+
+// Per rule point and output o (0 C_ext, 1 C_sca, 2 C_abs): JA, MA with
+// dC = 2 Re(JA . dj + MA . dj_m) at fixed geometry, and the explicit
+// adjoints of y, W, n.  C_sca sums over the sphere rule (directions 1..nsph
+// of dirs with weights wd); one CTA per point.
+struct FarArgs {
+  int64_t np, nsph;
+  const double* qd;
+  const double2* cur;   // W j, W j_m
+  const double* dirs;   // [0] forward, then the sphere rule
+  const double* wd;     // weights of the sphere directions
+  const double2* F;     // far fields of dirs
+  double ka;
+  d3 kh, ph;
+  double2* JA;          // [3][np][3]
+  double2* MA;          // [3][np][3]
+  double* radj;         // [3][np][19]
+  double* cab;          // [np]: W Re j_m . (conj(j) x n)
+};
+
+__global__ void __launch_bounds__(128) far_adjoint_kernel(FarArgs a) {
+  const int64_t p = blockIdx.x;
+  const double* rc = a.qd + p * QD_STRIDE;
+  const d3 y = ld3(rc);
+  const double W = rc[18];
+  const double2* c = a.cur + p * 6;
+  // j and j_m themselves (cur holds W j)
+  const double iW = 1.0 / W;
+  cx<double> j[3], m[3];
+  for (int k = 0; k < 3; ++k) {
+    j[k] = cmk(c[k].x * iW, c[k].y * iW);
+    m[k] = cmk(c[3 + k].x * iW, c[3 + k].y * iW);
+  }
+  // ---- C_sca: sums over the sphere directions
+  double acc[16];
+  for (int k = 0; k < 16; ++k) acc[k] = 0.0;
+  const cx<double> ikf = cmk(0.0, a.ka * kC4pi);  // i k/(4 pi)
+  for (int64_t dd = threadIdx.x; dd < a.nsph; dd += blockDim.x) {
+    const d3 d = ld3(a.dirs + 3 * (1 + dd));
+    double sn, cs;
+    sincos(-a.ka * dot(d, y), &sn, &cs);
+    const cx<double> ph = cmul(cmk(a.wd[dd] * cs, a.wd[dd] * sn), ikf);  // wd (ik/4pi) e^{-ik d.y}
+    const double2* Fd = a.F + (1 + dd) * 3;
+    const cx<double> Fc[3] = {cmk(Fd[0].x, -Fd[0].y), cmk(Fd[1].x, -Fd[1].y), cmk(Fd[2].x, -Fd[2].y)};
+    // P_d conj(F) and conj(F) x d
+    const cx<double> dF = cadd(cadd(crs(d.x, Fc[0]), crs(d.y, Fc[1])), crs(d.z, Fc[2]));
+    const double dv[3] = {d.x, d.y, d.z};
+    cx<double> PF[3], Fxd[3];
+    for (int k = 0; k < 3; ++k) PF[k] = csub(Fc[k], crs(dv[k], dF));
+    Fxd[0] = csub(crs(d.z, Fc[1]), crs(d.y, Fc[2]));
+    Fxd[1] = csub(crs(d.x, Fc[2]), crs(d.z, Fc[0]));
+    Fxd[2] = csub(crs(d.y, Fc[0]), crs(d.x, Fc[1]));
+    // JA += ph W P conj(F);  MA += -ph W (conj(F) x d)
+    for (int k = 0; k < 3; ++k) {
+      const cx<double> u = cmul(ph, PF[k]);
+      const cx<double> v = cmul(ph, Fxd[k]);
+      acc[2 * k] += W * u.re;
+      acc[2 * k + 1] += W * u.im;
+      acc[6 + 2 * k] -= W * v.re;
+      acc[6 + 2 * k + 1] -= W * v.im;
+    }
+    // conj(F) . [P j - d x j_m]  =  PF . j - Fxd . j_m
+    cx<double> q = cmk(0.0, 0.0);
+    for (int k = 0; k < 3; ++k) q = csub(cadd(q, cmul(PF[k], j[k])), cmul(Fxd[k], m[k]));
+    const cx<double> qq = cmul(ph, q);
+    // W: 2 Re(qq);  y: 2 Re(qq (-i k) W) d = 2 k W Im(qq) d
+    acc[12] += 2.0 * qq.re;
+    const double gy = 2.0 * a.ka * W * qq.im;
+    acc[13] += gy * d.x;
+    acc[14] += gy * d.y;
+    acc[15] += gy * d.z;
+  }
+  __shared__ double red[16][128];
+  for (int k = 0; k < 16; ++k) red[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int o = 64; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int k = 0; k < 16; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  const int64_t np = a.np;
+  // C_sca (o = 1)
+  for (int k = 0; k < 3; ++k) {
+    a.JA[(1 * np + p) * 3 + k] = make_double2(red[2 * k][0], red[2 * k + 1][0]);
+    a.MA[(1 * np + p) * 3 + k] = make_double2(red[6 + 2 * k][0], red[6 + 2 * k + 1][0]);
+  }
+  double* g1 = a.radj + (1 * np + p) * 19;
+  g1[0] += red[13][0];
+  g1[1] += red[14][0];
+  g1[2] += red[15][0];
+  g1[18] += red[12][0];
+  // C_ext (o = 0): Re sum W e^{-i psi} [p.j - (p x k).j_m], psi = k kh.y
+  {
+    double sn, cs;
+    sincos(-a.ka * dot(a.kh, y), &sn, &cs);
+    const cx<double> e = cmk(cs, sn);
+    const d3 pk = cross(a.ph, a.kh);
+    const double pv[3] = {a.ph.x, a.ph.y, a.ph.z}, kv[3] = {pk.x, pk.y, pk.z};
+    cx<double> v = cmk(0.0, 0.0);
+    for (int k = 0; k < 3; ++k) {
+      v = csub(cadd(v, crs(pv[k], j[k])), crs(kv[k], m[k]));
+      a.JA[p * 3 + k] = make_double2(0.5 * W * e.re * pv[k], 0.5 * W * e.im * pv[k]);
+      a.MA[p * 3 + k] = make_double2(-0.5 * W * e.re * kv[k], -0.5 * W * e.im * kv[k]);
+    }
+    const cx<double> ev = cmul(e, v);
+    double* g0 = a.radj + p * 19;
+    g0[18] += ev.re;
+    // d/dy e^{-i k kh.y} = -i k kh e: Re(-i k W ev) kh = k W Im(ev) kh
+    g0[0] += a.ka * W * ev.im * a.kh.x;
+    g0[1] += a.ka * W * ev.im * a.kh.y;
+    g0[2] += a.ka * W * ev.im * a.kh.z;
+  }
+  // C_abs (o = 2): Re sum W j_m . (conj(j) x n)
+  {
+    const d3 n = ld3(rc + 3);
+    const double nv[3] = {n.x, n.y, n.z};
+    cx<double> cj[3] = {cmk(j[0].re, -j[0].im), cmk(j[1].re, -j[1].im), cmk(j[2].re, -j[2].im)};
+    cx<double> cjn[3], nm[3], mcj[3];
+    for (int k = 0; k < 3; ++k) {
+      const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+      cjn[k] = csub(crs(nv[k2], cj[k1]), crs(nv[k1], cj[k2]));      // conj(j) x n
+      nm[k] = csub(crs(nv[k1], m[k2]), crs(nv[k2], m[k1]));          // n x j_m
+      mcj[k] = csub(cmul(m[k1], cj[k2]), cmul(m[k2], cj[k1]));       // j_m x conj(j)
+    }
+    double val = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      val += cmul(m[k], cjn[k]).re;
+      a.JA[(2 * np + p) * 3 + k] = make_double2(0.5 * W * nm[k].re, -0.5 * W * nm[k].im);
+      a.MA[(2 * np + p) * 3 + k] = make_double2(0.5 * W * cjn[k].re, 0.5 * W * cjn[k].im);
+    }
+    double* g2 = a.radj + (2 * np + p) * 19;
+    g2[18] += val;
+    a.cab[p] = W * val;
+    g2[3] += W * mcj[0].re;
+    g2[4] += W * mcj[1].re;
+    g2[5] += W * mcj[2].re;
+  }
+}
+
+// From JA, MA of each output: the frame adjoints 2 Re(Xi_0b JA + Xi_1b MA)
+// at the points, and G[o][u] = sum over the points of N_k (JA . t_b) (g = 0)
+// or N_k (MA . t_b) (g = 1) for u = g H + 2 node_k + b, conjugated on output
+// (the right-hand sides of Z^H lam = G).
+__global__ void far_finish_kernel(int64_t nt, RuleC rule, const int32_t* __restrict__ T,
+                                  const double* __restrict__ qd, const double2* __restrict__ Xp,
+                                  const double2* __restrict__ JA, const double2* __restrict__ MA,
+                                  int64_t H, double* __restrict__ radj, double2* __restrict__ G) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t np = nt * rule.Q;
+  if (t >= 3 * np) return;
+  const int o = (int)(t / np);
+  const int64_t pt = t % np;
+  const int64_t e = pt / rule.Q;
+  const int p = (int)(pt % rule.Q);
+  const double* rc = qd + pt * QD_STRIDE;
+  const double2* X = Xp + pt * 4;
+  const double2* ja = JA + (o * np + pt) * 3;
+  const double2* ma = MA + (o * np + pt) * 3;
+  double* g = radj + (o * np + pt) * 19;
+  double N[6];
+  p2N(rule.xi[p], rule.eta[p], N);
+  for (int b = 0; b < 2; ++b) {
+    const cx<double> x0 = cmk(X[b].x, X[b].y), x1 = cmk(X[2 + b].x, X[2 + b].y);
+    cx<double> jt = cmk(0.0, 0.0), mt = cmk(0.0, 0.0);
+    for (int k = 0; k < 3; ++k) {
+      const cx<double> jk = cmk(ja[k].x, ja[k].y), mk_ = cmk(ma[k].x, ma[k].y);
+      g[6 + 3 * b + k] += 2.0 * (cmul(x0, jk).re + cmul(x1, mk_).re);
+      jt = cadd(jt, crs(rc[6 + 3 * b + k], jk));
+      mt = cadd(mt, crs(rc[6 + 3 * b + k], mk_));
+    }
+    for (int i = 0; i < 6; ++i) {
+      const int64_t node = T[6 * e + i];
+      double2* g0 = G + (int64_t)o * 2 * H + 2 * node + b;
+      double2* g1 = G + (int64_t)o * 2 * H + H + 2 * node + b;
+      atomicAdd(&g0->x, N[i] * jt.re);
+      atomicAdd(&g0->y, -N[i] * jt.im);
+      atomicAdd(&g1->x, N[i] * mt.re);
+      atomicAdd(&g1->y, -N[i] * mt.im);
+    }
+  }
+}
+
 inline unsigned nblk(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 }  // namespace
@@ -867,6 +1152,154 @@ mueller_status zshape_vjp(mueller_mesh* m, const PhysConsts& P, int Q, int ns, c
   }
   if (!st) st = shape_finish(m, rc, W, grad, s);
   shape_free(W, s);
+  return st;
+}
+
+mueller_status rhs_shape_vjp(mueller_mesh* m, const PhysConsts& P, int Q, const void* lam,
+                             const double* inc, double* grad, cudaStream_t s) {
+  TriangleRule rule;
+  if (!triangle_rule(Q, rule)) {
+    set_error("q_regular must be 6 or 12");
+    return MUELLER_ERR_INVALID_ARG;
+  }
+  const RuleC rc = rule_c(rule);
+  ShapeWork W;
+  mueller_status st = shape_alloc(m, Q, W, s);
+  const int64_t N = 4 * m->nn, H = N / 2;
+  if (!st) {
+    const d3 kh = mk(inc[0], inc[1], inc[2]), ph = mk(inc[3], inc[4], inc[5]);
+    { Prof prof_("pt_fields_kernel", s); pt_fields_kernel<<<nblk(m->nt * Q, 128), 128, 0, s>>>(m->nt, rc, m->T, (const double2*)lam, (const double2*)lam, H, W.Lp, W.Xp); }
+    { Prof prof_("rhs_vjp_kernel", s); rhs_vjp_kernel<<<nblk(m->nt * Q, 128), 128, 0, s>>>(m->nt * Q, m->qd64, W.Lp, kh, ph, P.ka, W.radj); }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) st = cuda_fail(e, "right-hand-side adjoint kernels");
+  }
+  if (!st) st = shape_finish(m, rc, W, grad, s);
+  shape_free(W, s);
+  return st;
+}
+
+// dC/dx (as the right-hand sides G of Z^H lam = G, device 3 x N complex128)
+// and dC/dX at fixed x (host, 3 x n_nodes x 3, added) for C_ext, C_sca,
+// C_abs of one incident wave; xs (host, 3): the cross sections of x.
+mueller_status cross_section_partials(mueller_mesh* m, const PhysConsts& P, int Q, const void* x,
+                                      const double* inc, int n_theta, int n_phi, void* G,
+                                      double* grad, double* xs, cudaStream_t s) {
+  TriangleRule rule;
+  if (!triangle_rule(Q, rule)) {
+    set_error("q_regular must be 6 or 12");
+    return MUELLER_ERR_INVALID_ARG;
+  }
+  const RuleC rc = rule_c(rule);
+  const int64_t np = m->nt * Q, N = 4 * m->nn, H = N / 2;
+  const int64_t nsph = (int64_t)n_theta * n_phi, nd = 1 + nsph;
+  // directions: forward, then cos(theta) on Gauss-Legendre nodes x phi on
+  // n_phi equal steps, weights 2 w_theta 2 pi / n_phi (the sphere rule of
+  // the cross sections)
+  std::vector<double> gth, wth;
+  gauss_legendre_unit(n_theta, gth, wth);
+  std::vector<double> hd(nd * 3), hw(nsph);
+  hd[0] = inc[0];
+  hd[1] = inc[1];
+  hd[2] = inc[2];
+  for (int it = 0; it < n_theta; ++it) {
+    const double ct = 2.0 * gth[it] - 1.0, st = sqrt(fmax(0.0, 1.0 - ct * ct));
+    for (int ip = 0; ip < n_phi; ++ip) {
+      const double ph = 2.0 * kPi * ip / n_phi;
+      const int64_t k = (int64_t)it * n_phi + ip;
+      hd[3 * (1 + k)] = st * cos(ph);
+      hd[3 * (1 + k) + 1] = st * sin(ph);
+      hd[3 * (1 + k) + 2] = ct;
+      hw[k] = 2.0 * wth[it] * (2.0 * kPi / n_phi);
+    }
+  }
+  // three outputs share the point fields; radj holds 3 x np x 19
+  double2 *Lp = nullptr, *Xp = nullptr, *cur = nullptr, *F = nullptr, *JA = nullptr, *MA = nullptr;
+  double *dirs = nullptr, *wd = nullptr, *radj = nullptr, *eadj = nullptr, *gpos = nullptr;
+  double* cab = nullptr;
+  mueller_status st = MUELLER_OK;
+  auto take = [&](void** ptr, size_t bytes) {
+    if (st) return;
+    cudaError_t e = cudaMallocAsync(ptr, bytes, s);
+    if (e != cudaSuccess) st = cuda_fail(e, "cross-section partials workspace");
+  };
+  take((void**)&Lp, np * 4 * sizeof(double2));
+  take((void**)&Xp, np * 4 * sizeof(double2));
+  take((void**)&cur, np * 6 * sizeof(double2));
+  take((void**)&F, nd * 3 * sizeof(double2));
+  take((void**)&JA, 3 * np * 3 * sizeof(double2));
+  take((void**)&MA, 3 * np * 3 * sizeof(double2));
+  take((void**)&dirs, nd * 3 * sizeof(double));
+  take((void**)&wd, nsph * sizeof(double));
+  take((void**)&radj, 3 * np * 19 * sizeof(double));
+  take((void**)&eadj, m->nt * 54 * sizeof(double));
+  take((void**)&gpos, m->nn * 3 * sizeof(double));
+  take((void**)&cab, np * sizeof(double));
+  std::vector<double> Fh(nd * 6), cabh(np);
+  if (!st) {
+    cudaError_t e = cudaMemcpyAsync(dirs, hd.data(), hd.size() * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(wd, hw.data(), hw.size() * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(radj, 0, 3 * np * 19 * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(G, 0, 3 * N * sizeof(double2), s);
+    if (e != cudaSuccess) st = cuda_fail(e, "cross-section partials setup");
+  }
+  if (!st) {
+    const d3 kh = mk(inc[0], inc[1], inc[2]), ph = mk(inc[3], inc[4], inc[5]);
+    { Prof prof_("pt_fields_kernel", s); pt_fields_kernel<<<nblk(np, 128), 128, 0, s>>>(m->nt, rc, m->T, (const double2*)x, (const double2*)x, H, Lp, Xp); }
+    { Prof prof_("far_currents_kernel", s); far_currents_kernel<<<nblk(np, 128), 128, 0, s>>>(np, m->qd64, Xp, cur); }
+    { Prof prof_("far_sum_kernel", s); far_sum_kernel<<<(unsigned)nd, 256, 0, s>>>(np, m->qd64, cur, dirs, P.ka, F); }
+    FarArgs fa;
+    fa.np = np;
+    fa.nsph = nsph;
+    fa.qd = m->qd64;
+    fa.cur = cur;
+    fa.dirs = dirs;
+    fa.wd = wd;
+    fa.F = F;
+    fa.ka = P.ka;
+    fa.kh = kh;
+    fa.ph = ph;
+    fa.JA = JA;
+    fa.MA = MA;
+    fa.radj = radj;
+    fa.cab = cab;
+    { Prof prof_("far_adjoint_kernel", s); far_adjoint_kernel<<<(unsigned)np, 128, 0, s>>>(fa); }
+    { Prof prof_("far_finish_kernel", s); far_finish_kernel<<<nblk(3 * np, 128), 128, 0, s>>>(m->nt, rc, m->T, m->qd64, Xp, JA, MA, H, radj, (double2*)G); }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Fh.data(), F, nd * 3 * sizeof(double2), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cabh.data(), cab, np * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) st = cuda_fail(e, "cross-section partial kernels");
+  }
+  // geometry adjoints of each output through the records
+  for (int o = 0; o < 3 && !st; ++o) {
+    cudaError_t e = cudaMemsetAsync(eadj, 0, m->nt * 54 * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(gpos, 0, m->nn * 3 * sizeof(double), s);
+    if (e != cudaSuccess) {
+      st = cuda_fail(e, "cross-section partials");
+      break;
+    }
+    ShapeWork W;
+    W.radj = radj + (size_t)o * np * 19;
+    W.eadj = eadj;
+    W.gpos = gpos;
+    st = shape_finish(m, rc, W, grad + (size_t)o * m->nn * 3, s);
+  }
+  if (!st && xs) {
+    // C_ext = (4 pi/k) Im(p . F(k)), C_sca = sum wd |F|^2, C_abs = sum of cab
+    const double pv[3] = {inc[3], inc[4], inc[5]};
+    double im = 0.0;
+    for (int k = 0; k < 3; ++k) im += pv[k] * Fh[2 * k + 1];
+    xs[0] = 4.0 * kPi / P.ka * im;
+    double cs = 0.0;
+    for (int64_t k = 0; k < nsph; ++k)
+      for (int c = 0; c < 6; ++c) cs += hw[k] * Fh[6 * (1 + k) + c] * Fh[6 * (1 + k) + c];
+    xs[1] = cs;
+    double ca = 0.0;
+    for (int64_t k = 0; k < np; ++k) ca += cabh[k];
+    xs[2] = ca;
+  }
+  for (void* q : {(void*)Lp, (void*)Xp, (void*)cur, (void*)F, (void*)JA, (void*)MA, (void*)dirs,
+                  (void*)wd, (void*)radj, (void*)eadj, (void*)gpos, (void*)cab})
+    if (q) cudaFreeAsync(q, s);
   return st;
 }
 

@@ -1,9 +1,12 @@
-"""Gradients of the cross sections with respect to the material parameters.
+"""Gradients of the cross sections with respect to the material parameters
+and to the node coordinates of the P2 mesh.
 
 For the scatterer's relative permittivity eps_r and permeability mu_r (each
 complex, i.e. two real parameters) this returns the Jacobian of
 (C_ext, C_sca, C_abs) of one incident wave, and a torch.autograd.Function
-around it.
+around it.  For the node coordinates X it returns the three gradients
+dC/dX by the adjoint method (shape_gradient, below), and an autograd
+Function of the coordinates.
 
 Method (the tangent-linear form of the adjoint relation: for four real
 parameters and three outputs both need the same number of solves, and this
@@ -127,3 +130,64 @@ def cross_sections(eps, mu, mesh, params, inc):
     if _cs is None:
         _cs = _autograd_function()
     return _cs.apply(eps, mu, mesh, params, inc)
+
+
+def shape_gradient(state, n_theta=48, n_phi=96):
+    """Gradients of (C_ext, C_sca, C_abs) with respect to the node coordinates
+    at the forward state, numpy (3, n_nodes, 3) in the input node order.
+
+    Adjoint method: with G_o = conj(dC_o/dx) at fixed geometry and
+    Z^H lam_o = G_o,
+        dC_o/dX = dC_o/dX|_x + 2 Re lam_o^H (db/dX - (dZ/dX) x).
+    The three adjoint systems are one FP64 GMRES call on Z^H (the
+    conjugate-transposed block-Jacobi inverse as right preconditioner); the
+    terms are mueller_cross_section_partials, mueller_rhs_shape_vjp and
+    mueller_zshape_vjp.  The frame depends on X through the nodal normals and
+    frames (Secs. 3.1-3.3), and the gradient follows it: it is the derivative
+    of the discrete cross sections as the library computes them."""
+    mesh, params, inc, op, X = (state[k] for k in ("mesh", "params", "inc", "op", "X"))
+    G, grad, _ = api.cross_section_partials(mesh, params, X[0], inc[0], n_theta, n_phi)
+    opa = api.Operator(mesh, op.Z, dtype=api.MUELLER_C128, precond=op.precond, block=op.block,
+                       adjoint=True)
+    lam = _fp64_solve(opa, G, state["tol"])
+    for o in range(3):
+        grad[o] += 2.0 * (api.rhs_shape_vjp(mesh, params, lam[o], inc[0])
+                          - api.zshape_vjp(mesh, params, lam[o], X[0]))
+    return grad
+
+
+def _shape_function():
+    torch = api._torch()
+
+    class ShapeCrossSections(torch.autograd.Function):
+        """(C_ext, C_sca, C_abs) of one incident wave as a function of the
+        node coordinates xyz (float64 tensor (n_nodes, 3)) of a P2 mesh with
+        connectivity tri6; the gradient is formed in backward."""
+
+        @staticmethod
+        def forward(ctx, xyz, tri6, params, inc, block):
+            mesh = api.Mesh(xyz.detach().cpu().numpy(), tri6)
+            mesh.tangent_frame(params.frame_rule, out=False)
+            xs, state = forward_state(mesh, params, inc, block)
+            ctx.state = state
+            return torch.tensor(xs, dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, g):
+            G = torch.from_numpy(shape_gradient(ctx.state))
+            ctx.state["mesh"].free()
+            ctx.state = None
+            return torch.einsum("o,onk->nk", g.to(torch.float64), G), None, None, None, None
+
+    return ShapeCrossSections
+
+
+_sc = None
+
+
+def cross_sections_of_nodes(xyz, tri6, params, inc, block=None):
+    """Differentiable (C_ext, C_sca, C_abs) of the node coordinates."""
+    global _sc
+    if _sc is None:
+        _sc = _shape_function()
+    return _sc.apply(xyz, tri6, params, inc, block)
