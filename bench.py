@@ -573,34 +573,59 @@ def multibody64(mu, torch, dev):
 
 
 def gradients_l3(mu, torch, dev):
-    """Material gradients on the level-3 spheroid of axis ratio 1.5 (eps_r =
-    3 + 0.2i, mu_r = 1, k_a = 3, incidence +z, x polarised): the FP64
-    forward state (assembly, block-Jacobi, GMRES to 1e-12, far field) and
-    the 3 x 4 Jacobian of (C_ext, C_sca, C_abs) with respect to (Re, Im) of
-    eps_r and mu_r (two operator-derivative products, two tangent solves, one far-field
-    call), wall time with the device synchronised."""
+    """Adjoint gradients on the level-3 spheroid of axis ratio 1.5 (eps_r =
+    3 + 0.2i, mu_r = 1, k_a = 3, incidence +z, x polarised, the paper's frame
+    rule): the FP64 forward state (assembly, block-Jacobi, GMRES to 1e-12,
+    far field); then (a) the full gradients of (C_ext, C_sca, C_abs) by one
+    adjoint solve with three right-hand sides: the 3 x 4 material Jacobian
+    and the 3 x 2562 x 3 node-coordinate gradient, per stage; (b) one
+    reverse-mode product w^T (gradients) as an autograd backward makes it
+    (one adjoint solve, one pass of each derivative kernel); (c) the
+    tangent-linear material Jacobian for comparison.  Wall times with the
+    device synchronised, after a warm-up of every path."""
     import time as _t
 
     xyz, tri6 = workloads.spheroid_p2(3, 1.0, 1.5)
-    m = mu.Mesh(xyz, tri6)
-    m.tangent_frame(0, out=False)
     p = mu.Params(ka=3.0, eps_r=(3.0, 0.2), mu_r=(1.0, 0.0), q_regular=6, ssq_order=5, frame_rule=0)
     inc = workloads.plane_wave((0.0, 0.0, 1.0), (1.0, 0.0, 0.0))
+
+    def fwd():
+        m = mu.Mesh(xyz, tri6)
+        m.tangent_frame(0, out=False)
+        xs, state = mu.grad.forward_state(m, p, inc)
+        return m, xs, state
+
     # warm-up (tuning, rules, first launches of the derivative kernels, workspace)
-    mu.grad.material_jacobian(mu.grad.forward_state(m, p, inc)[1])
+    m, _, state = fwd()
+    mu.grad.adjoint_gradients(state)
+    mu.grad.vjp(state, np.ones(3))
+    mu.grad.material_jacobian(state)
+    m.free()
     torch.cuda.synchronize()
     t0 = _t.perf_counter()
-    xs, state = mu.grad.forward_state(m, p, inc)
+    m, xs, state = fwd()
     torch.cuda.synchronize()
     t1 = _t.perf_counter()
-    J = mu.grad.material_jacobian(state)
-    torch.cuda.synchronize()
+    stages = {}
+    J, G = mu.grad.adjoint_gradients(state, timings=stages)
     t2 = _t.perf_counter()
+    mu.grad.vjp(state, np.array([1.0, 0.5, 0.25]))
+    torch.cuda.synchronize()
+    t3 = _t.perf_counter()
+    Jt = mu.grad.material_jacobian(state)
+    torch.cuda.synchronize()
+    t4 = _t.perf_counter()
     m.free()
-    return {"n_dof": int(m.N), "forward_ms": round((t1 - t0) * 1e3, 1),
-            "jacobian_ms": round((t2 - t1) * 1e3, 1),
+    return {"n_dof": int(m.N), "n_nodes": int(len(xyz)), "forward_ms": round((t1 - t0) * 1e3, 1),
+            "adjoint_gradients_ms": round((t2 - t1) * 1e3, 1), "adjoint_stages_ms": stages,
+            "vjp_ms": round((t3 - t2) * 1e3, 1),
+            "tangent_jacobian_ms": round((t4 - t3) * 1e3, 1),
+            "jacobian_adjoint_vs_tangent": float(np.abs(J - Jt).max() / np.abs(Jt).max()),
             "cross_sections": [float(v) for v in xs],
-            "jacobian_rows_ext_sca_abs_cols_re_eps_im_eps_re_mu_im_mu": J.round(6).tolist()}
+            "jacobian_rows_ext_sca_abs_cols_re_eps_im_eps_re_mu_im_mu": J.round(6).tolist(),
+            "coordinate_gradient_max_abs": [float(np.abs(G[o]).max()) for o in range(3)],
+            "translation_residual": [float(np.abs(G[o].sum(axis=0)).max() / np.abs(G[o]).max())
+                                     for o in range(3)]}
 
 
 def lspr_sweep(mu, torch, dev):

@@ -65,37 +65,59 @@ __global__ void __launch_bounds__(256) gemv_c128_kernel(int64_t N, const double2
   }
 }
 
-// y = Z^H x (complex128), the adjoint operator (MUELLER_OP_ADJOINT): 64
-// columns per CTA, 4 row lanes per column, rows split into gridDim.y chunks
-// whose partial sums meet in y by atomic additions (y zeroed by the caller).
+// y = Z^H x (complex128), the adjoint operator (MUELLER_OP_ADJOINT).  A CTA
+// owns a block of rows [i0, i1) and a tile of 512 columns: its 256 threads
+// stream the block's row segments (8 KB each, contiguous) two columns per
+// thread, four rows per step, and add their partial sums into y by atomic
+// additions (y zeroed by the caller).
+constexpr int kGemvhCols = 512;
 __global__ void __launch_bounds__(256) gemvh_c128_kernel(int64_t N, const double2* __restrict__ Z,
                                                          int64_t ldz, const double2* __restrict__ x,
                                                          double2* __restrict__ y, int64_t xs,
-                                                         int64_t ys) {
-  const int cl = threadIdx.x & 63, rl = threadIdx.x >> 6;
-  const int64_t j = (int64_t)blockIdx.x * 64 + cl;
+                                                         int64_t ys, int64_t rows) {
+  constexpr int U = 4;
   const int s = blockIdx.z;
-  const int64_t chunk = (N + gridDim.y - 1) / gridDim.y;
-  const int64_t i0 = (int64_t)blockIdx.y * chunk, i1 = i0 + chunk < N ? i0 + chunk : N;
-  double ar = 0.0, ai = 0.0;
-  if (j < N) {
-    const double2* xv = x + s * xs;
-    for (int64_t i = i0 + rl; i < i1; i += 4) {
-      const double2 z = __ldg(Z + i * ldz + j), xi = __ldg(xv + i);
+  const int64_t j0 = (int64_t)blockIdx.x * kGemvhCols + threadIdx.x, j1 = j0 + 256;
+  const int64_t i0 = (int64_t)blockIdx.y * rows, i1 = i0 + rows < N ? i0 + rows : N;
+  const bool v0 = j0 < N, v1 = j1 < N;
+  const double2* xv = x + s * xs;
+  double ar0 = 0.0, ai0 = 0.0, ar1 = 0.0, ai1 = 0.0;
+  const double2 zero = make_double2(0.0, 0.0);
+  int64_t i = i0;
+  for (; i + U <= i1; i += U) {
+    double2 z0[U], z1[U], xi[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const double2* row = Z + (i + u) * ldz;
+      z0[u] = v0 ? __ldg(row + j0) : zero;
+      z1[u] = v1 ? __ldg(row + j1) : zero;
+      xi[u] = __ldg(xv + i + u);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
       // conj(z) x
-      ar = fma(z.x, xi.x, fma(z.y, xi.y, ar));
-      ai = fma(z.x, xi.y, fma(-z.y, xi.x, ai));
+      ar0 = fma(z0[u].x, xi[u].x, fma(z0[u].y, xi[u].y, ar0));
+      ai0 = fma(z0[u].x, xi[u].y, fma(-z0[u].y, xi[u].x, ai0));
+      ar1 = fma(z1[u].x, xi[u].x, fma(z1[u].y, xi[u].y, ar1));
+      ai1 = fma(z1[u].x, xi[u].y, fma(-z1[u].y, xi[u].x, ai1));
     }
   }
-  __shared__ double sr[4][64], si[4][64];
-  sr[rl][cl] = ar;
-  si[rl][cl] = ai;
-  __syncthreads();
-  if (rl == 0 && j < N) {
-    const double vr = sr[0][cl] + sr[1][cl] + sr[2][cl] + sr[3][cl];
-    const double vi = si[0][cl] + si[1][cl] + si[2][cl] + si[3][cl];
-    atomicAdd(&y[s * ys + j].x, vr);
-    atomicAdd(&y[s * ys + j].y, vi);
+  for (; i < i1; ++i) {
+    const double2* row = Z + i * ldz;
+    const double2 xi = __ldg(xv + i);
+    const double2 z0 = v0 ? __ldg(row + j0) : zero, z1 = v1 ? __ldg(row + j1) : zero;
+    ar0 = fma(z0.x, xi.x, fma(z0.y, xi.y, ar0));
+    ai0 = fma(z0.x, xi.y, fma(-z0.y, xi.x, ai0));
+    ar1 = fma(z1.x, xi.x, fma(z1.y, xi.y, ar1));
+    ai1 = fma(z1.x, xi.y, fma(-z1.y, xi.x, ai1));
+  }
+  if (v0) {
+    atomicAdd(&y[s * ys + j0].x, ar0);
+    atomicAdd(&y[s * ys + j0].y, ai0);
+  }
+  if (v1) {
+    atomicAdd(&y[s * ys + j1].x, ar1);
+    atomicAdd(&y[s * ys + j1].y, ai1);
   }
 }
 
@@ -1798,9 +1820,13 @@ mueller_status op_matvec(const mueller_operator* op, const void* X, void* Y, int
   const int64_t N = 4 * m->nn;
   if (op->dtype == MUELLER_C128 && (op->flags & MUELLER_OP_ADJOINT)) {
     MU_CUDA(cudaMemsetAsync(Y, 0, (size_t)N * r * sizeof(double2), s));
-    dim3 grid(nblk(N, 64), 8, r);
+    // row blocks: about four CTAs per SM over the column tiles
+    const int64_t ct = nblk(N, kGemvhCols);
+    const int64_t nrb = std::max<int64_t>(1, std::min<int64_t>(N, (4 * 152 + ct - 1) / ct));
+    const int64_t rows = (N + nrb - 1) / nrb;
+    dim3 grid((unsigned)ct, (unsigned)nblk(N, (int)rows), r);
     { Prof prof_("gemvh_c128_kernel", s); gemvh_c128_kernel<<<grid, 256, 0, s>>>(N, (const double2*)op->Z_dev, op->ldz, (const double2*)X,
-                                           (double2*)Y, N, N); }
+                                           (double2*)Y, N, N, rows); }
     MU_CHECK_LAUNCH("gemvh_c128_kernel");
   } else if (op->dtype == MUELLER_C128) {
     dim3 grid(nblk(N, 32), r);

@@ -8,9 +8,10 @@ around it.  For the node coordinates X it returns the three gradients
 dC/dX by the adjoint method (shape_gradient, below), and an autograd
 Function of the coordinates.
 
-Method (the tangent-linear form of the adjoint relation: for four real
-parameters and three outputs both need the same number of solves, and this
-one reuses the forward operator and its preconditioner):
+Two forms of the material Jacobian are kept: adjoint_gradients (one adjoint
+solve Z^H lam = conj(dC/dx) for the three outputs, then lam^H (dZ/dtheta) x;
+the autograd Functions use it, and it serves the node coordinates too) and
+material_jacobian, the tangent-linear form below, which checks it:
 
 * Z(theta) x = b with b independent of eps_r, mu_r; Z is holomorphic in
   eps_r and mu_r (through k_i = k_a sqrt(eps_r mu_r), principal branch, and
@@ -113,9 +114,8 @@ def _autograd_function():
 
         @staticmethod
         def backward(ctx, g):
-            J = torch.from_numpy(material_jacobian(ctx.state))
+            gp = torch.from_numpy(vjp(ctx.state, g.detach().cpu().numpy(), shape=False)[0])
             ctx.state = None
-            gp = g.to(torch.float64) @ J
             return gp[:2], gp[2:], None, None, None
 
     return CrossSections
@@ -132,28 +132,98 @@ def cross_sections(eps, mu, mesh, params, inc):
     return _cs.apply(eps, mu, mesh, params, inc)
 
 
-def shape_gradient(state, n_theta=48, n_phi=96):
-    """Gradients of (C_ext, C_sca, C_abs) with respect to the node coordinates
-    at the forward state, numpy (3, n_nodes, 3) in the input node order.
+def adjoint_gradients(state, n_theta=48, n_phi=96, material=True, shape=True, timings=None):
+    """Gradients of (C_ext, C_sca, C_abs) at the forward state by one adjoint
+    solve: the 3 x 4 Jacobian with respect to (Re eps_r, Im eps_r, Re mu_r,
+    Im mu_r) and the (3, n_nodes, 3) gradient with respect to the node
+    coordinates (input node order).
 
-    Adjoint method: with G_o = conj(dC_o/dx) at fixed geometry and
-    Z^H lam_o = G_o,
-        dC_o/dX = dC_o/dX|_x + 2 Re lam_o^H (db/dX - (dZ/dX) x).
-    The three adjoint systems are one FP64 GMRES call on Z^H (the
-    conjugate-transposed block-Jacobi inverse as right preconditioner); the
-    terms are mueller_cross_section_partials, mueller_rhs_shape_vjp and
-    mueller_zshape_vjp.  The frame depends on X through the nodal normals and
-    frames (Secs. 3.1-3.3), and the gradient follows it: it is the derivative
-    of the discrete cross sections as the library computes them."""
+    With G_o = conj(dC_o/dx) at fixed geometry and Z^H lam_o = G_o,
+        dC_o/dtheta = 2 Re lam_o^H (db/dtheta - (dZ/dtheta) x) + dC_o/dtheta|_x.
+    * Material parameters: b and C|_x do not depend on them and Z is
+      holomorphic, so with d = lam^H (dZ/dtheta) x (mueller_dz_matvec) the
+      real part of theta gives -2 Re d and the imaginary part 2 Im d.
+    * Node coordinates: dC/dX|_x from mueller_cross_section_partials,
+      2 Re lam^H db/dX from mueller_rhs_shape_vjp, 2 Re lam^H (dZ/dX) x from
+      mueller_zshape_vjp (pair blocks recomputed, no dZ stored).  The frame
+      depends on X through the nodal normals and frames (Secs. 3.1-3.3), and
+      the gradient follows it: it is the derivative of the discrete cross
+      sections as the library computes them.
+    The three adjoint systems are one FP64 GMRES call on Z^H, right-
+    preconditioned by the conjugate transpose of the block-Jacobi inverse.
+    material / shape: which of the two to form (the other is returned as
+    None).  timings: an optional dict that receives the wall time (ms, device
+    synchronised) of each stage."""
+    import time
+
+    torch = api._torch()
     mesh, params, inc, op, X = (state[k] for k in ("mesh", "params", "inc", "op", "X"))
+    clock = [time.perf_counter()]
+
+    def lap(name):
+        if timings is not None:
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            timings[name] = round((t - clock[0]) * 1e3, 2)
+            clock[0] = t
+
     G, grad, _ = api.cross_section_partials(mesh, params, X[0], inc[0], n_theta, n_phi)
+    lap("partials_ms")
     opa = api.Operator(mesh, op.Z, dtype=api.MUELLER_C128, precond=op.precond, block=op.block,
                        adjoint=True)
     lam = _fp64_solve(opa, G, state["tol"])
+    lap("adjoint_solve_ms")
+    J = None
+    if material:
+        J = np.zeros((3, 4))
+        for c, which in enumerate((1, 2)):
+            v = api.dz_matvec(mesh, params, which, X[0])
+            d = (lam.conj() @ v).cpu().numpy()
+            J[:, 2 * c] = -2.0 * d.real
+            J[:, 2 * c + 1] = 2.0 * d.imag
+        lap("material_ms")
+    if not shape:
+        return J, None
     for o in range(3):
         grad[o] += 2.0 * (api.rhs_shape_vjp(mesh, params, lam[o], inc[0])
                           - api.zshape_vjp(mesh, params, lam[o], X[0]))
-    return grad
+    lap("shape_ms")
+    return J, grad
+
+
+def shape_gradient(state, n_theta=48, n_phi=96):
+    """The node-coordinate part of adjoint_gradients, numpy (3, n_nodes, 3)."""
+    return adjoint_gradients(state, n_theta, n_phi, material=False)[1]
+
+
+def vjp(state, w, material=True, shape=True, n_theta=48, n_phi=96):
+    """w^T of the gradients of (C_ext, C_sca, C_abs) for real weights w (3,):
+    (w^T J numpy (4,) or None, w^T dC/dX numpy (n_nodes, 3) or None).
+
+    Everything after the forward solve is real-linear in lam, so the weighted
+    sum needs one adjoint solve Z^H lam = sum_o w_o G_o and one pass of each
+    derivative kernel, a third of adjoint_gradients' work: this is what a
+    reverse-mode backward needs."""
+    torch = api._torch()
+    mesh, params, inc, op, X = (state[k] for k in ("mesh", "params", "inc", "op", "X"))
+    w = np.asarray(w, dtype=np.float64).reshape(3)
+    G, gfix, _ = api.cross_section_partials(mesh, params, X[0], inc[0], n_theta, n_phi)
+    wt = torch.as_tensor(w, dtype=torch.complex128, device=G.device)
+    Gw = (wt @ G).reshape(1, -1)
+    opa = api.Operator(mesh, op.Z, dtype=api.MUELLER_C128, precond=op.precond, block=op.block,
+                       adjoint=True)
+    lam = _fp64_solve(opa, Gw, state["tol"])[0]
+    gJ = gX = None
+    if material:
+        gJ = np.zeros(4)
+        for c, which in enumerate((1, 2)):
+            d = torch.vdot(lam, api.dz_matvec(mesh, params, which, X[0])).item()
+            gJ[2 * c] = -2.0 * d.real
+            gJ[2 * c + 1] = 2.0 * d.imag
+    if shape:
+        gX = np.einsum("o,onk->nk", w, gfix) + 2.0 * (
+            api.rhs_shape_vjp(mesh, params, lam, inc[0]) - api.zshape_vjp(mesh, params, lam, X[0]))
+    return gJ, gX
 
 
 def _shape_function():
@@ -174,10 +244,10 @@ def _shape_function():
 
         @staticmethod
         def backward(ctx, g):
-            G = torch.from_numpy(shape_gradient(ctx.state))
+            gX = torch.from_numpy(vjp(ctx.state, g.detach().cpu().numpy(), material=False)[1])
             ctx.state["mesh"].free()
             ctx.state = None
-            return torch.einsum("o,onk->nk", g.to(torch.float64), G), None, None, None, None
+            return gX, None, None, None, None
 
     return ShapeCrossSections
 

@@ -9,6 +9,9 @@ FP64 path (grad.material_jacobian):
   oracle's central differences carry an O(h^2) error of about 1e-8);
 * against central differences of the GPU's own cross sections (full solves
   at theta +- h) on the level-2 spheroid, within 1e-5;
+* the adjoint form (one solve Z^H lam = conj(dC/dx) for the three outputs,
+  then lam^H (dZ/dtheta) x) against the tangent-linear form, within 1e-8,
+  and against the oracle, within 1e-5;
 * the autograd.Function's backward returns g^T J.
 """
 
@@ -58,6 +61,19 @@ def test_material_jacobian_matches_oracle_gradient(phys):
     assert _colmax_err(J, Jo) <= 1e-5, (J, Jo)
 
 
+@pytest.mark.parametrize("phys", [PHYS, dict(ka=2.0, eps_r=(2.0, 0.1), mu_r=(1.5, 0.1))])
+def test_adjoint_material_jacobian_matches_tangent_and_oracle(phys):
+    xyz, tri6, m, p, inc = _setup(1)
+    p = dataclasses.replace(p, ka=phys["ka"], eps_r=phys["eps_r"], mu_r=phys["mu_r"])
+    _, state = mu.grad.forward_state(m, p, inc)
+    Ja, _ = mu.grad.adjoint_gradients(state, shape=False)
+    Jt = mu.grad.material_jacobian(state)
+    assert _colmax_err(Ja, Jt) <= 1e-8, (Ja, Jt)
+    om = oracle.Mesh(xyz, tri6, frame_rule=0)
+    Jo = oracle.cross_section_gradient(om, dict(phys, q_regular=6, ssq_order=4), inc)
+    assert _colmax_err(Ja, Jo) <= 1e-5, (Ja, Jo)
+
+
 def test_material_jacobian_matches_own_central_differences():
     _, _, m, p, inc = _setup(2, ns=3)
     _, state = mu.grad.forward_state(m, p, inc)
@@ -83,10 +99,10 @@ def test_autograd_backward_is_g_transpose_j():
     g = torch.tensor([1.0, 2.0, -0.5], dtype=torch.float64)
     (C * g).sum().backward()
     _, state = mu.grad.forward_state(m, p, inc)
-    J = mu.grad.material_jacobian(state)
+    J = mu.grad.material_jacobian(state)  # the tangent-linear form; backward uses the adjoint
     want = g.numpy() @ J
-    np.testing.assert_allclose(np.r_[eps.grad.numpy(), mur.grad.numpy()], want, rtol=1e-9,
-                               atol=1e-12 * np.abs(want).max())
+    np.testing.assert_allclose(np.r_[eps.grad.numpy(), mur.grad.numpy()], want, rtol=1e-7,
+                               atol=1e-9 * np.abs(want).max())
 
 
 @pytest.mark.parametrize("which,key", [(1, "eps_r"), (2, "mu_r")])
