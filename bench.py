@@ -542,9 +542,10 @@ def multibody64(mu, torch, dev):
     mu.precond_build_batch(ops, blocks)
     torch.cuda.synchronize()
     t_pre = _t.perf_counter() - t0
-    t_sol = 0.0
-    worst, iters, bal = 0.0, 0, {}
+    t_sol, t_far = 0.0, 0.0
+    worst, iters, bal, by_level = 0.0, 0, {}, {}
     for m, p, op, (Z, nr, B) in zip(meshes, params, ops, out):
+        key = "L%d" % {80: 1, 320: 2, 1280: 3}.get(m.nt, 0)
         tb = _t.perf_counter()
         X, info = mu.solve(op, B, opts)
         torch.cuda.synchronize()
@@ -553,11 +554,19 @@ def multibody64(mu, torch, dev):
         worst = max(worst, info["relres"])
         iters += info["iters"] // inc.shape[0]
         _, xs = mu.far_field(m, p, X, inc)
+        td = _t.perf_counter()
+        t_far += td - tc
+        lv = by_level.setdefault(key, {"bodies": 0, "solve_s": 0.0, "far_field_s": 0.0})
+        lv["bodies"] += 1
+        lv["solve_s"] += tc - tb
+        lv["far_field_s"] += td - tc
         # |C_ext - C_sca - C_abs| / C_ext: the discretisation error of the body's mesh
         e = float(np.max(np.abs(xs[:, 0] - xs[:, 1] - xs[:, 2]) / np.abs(xs[:, 0])))
-        key = "L%d" % {80: 1, 320: 2, 1280: 3}.get(m.nt, 0)
         bal[key] = max(bal.get(key, 0.0), e)
     t_all = _t.perf_counter() - t0
+    for lv in by_level.values():
+        lv["solve_s"] = round(lv["solve_s"], 3)
+        lv["far_field_s"] = round(lv["far_field_s"], 3)
     for m in meshes:
         m.free()
     return {"bodies": len(meshes), "rhs_per_body": int(inc.shape[0]),
@@ -568,6 +577,7 @@ def multibody64(mu, torch, dev):
             "assembly_loop_pairs_per_s": pairs / (t_loop / 1e3),
             "precond_batched_s": round(t_pre, 3),
             "precond_loop_s": round(t_pre_loop / 1e3, 3), "solve_total_s": round(t_sol, 3),
+            "far_field_total_s": round(t_far, 3), "by_level": by_level,
             "solve_and_far_field_wall_s": round(t_all, 3), "lockstep_iters_total": iters,
             "worst_relres": worst, "worst_energy_balance_by_level": bal}
 

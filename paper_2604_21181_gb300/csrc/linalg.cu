@@ -7,6 +7,7 @@
 //   * restarted GMRES with right preconditioning (classical Gram-Schmidt
 //     applied twice, complex Givens rotations) and the mixed-precision
 //     iterative refinement around it.
+#include <cooperative_groups.h>
 #include <math.h>
 #include <stdio.h>
 
@@ -1330,51 +1331,28 @@ __global__ void givens_b_kernel(int j, int m, int r, double2* __restrict__ hacc,
 }
 
 // ------------------------------------------------ fused Arnoldi step tail
-// Grid-wide barrier of a cooperative launch (every CTA resident): arrival
-// counter bar[0], generation bar[1].  The wait is bounded: after 2^31 clock
-// cycles (about a second) without the generation changing, err is set and
-// the CTA goes on (the host reads err and reports a timeout; the results of
-// that step are then void).
-__device__ void grid_barrier(unsigned* bar, unsigned nblocks, int* err) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned* vgen = bar + 1;
-    const unsigned gen = *vgen;
-    __threadfence();
-    if (atomicAdd(bar, 1u) == nblocks - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      const long long t0 = clock64();
-      while (*vgen == gen) {
-        if (clock64() - t0 > (1ll << 31)) {
-          atomicExch(err, 1);
-          break;
-        }
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-}
-
-// up to this many (right-hand side, basis vector) coefficients, every CTA
-// of the Arnoldi step reduces all partial dot products itself
-constexpr int kTailDirect = 1024;
+// One Arnoldi step after the product w = A P^-1 v_j, for all r right-hand
+// sides in one launch: a cluster of CS CTAs per right-hand side, each CTA
+// owning a contiguous chunk of the vector.  Classical Gram-Schmidt twice
+// against v_0..v_j (per pass: the chunk's partial dot products in shared
+// memory, a cluster barrier, every CTA of the cluster sums the CS partials of
+// every coefficient in the same order through distributed shared memory, then
+// updates its chunk), the norm the same way, v_{j+1} = w / ||w||, the Givens
+// step and the convergence test of the right-hand side by the cluster's
+// first CTA.  The clusters never wait on one another: the last one to finish
+// (a ticket counter) decides whether every active right-hand side has
+// converged and sets the stop flag, after which every queued step returns at
+// once, so the host reads the flag only now and then.
+constexpr int kTailMaxM = 128;  // restart length limit of the lockstep solver
 
 struct TailArgs {
-  int direct;       // nonzero: r (j + 1) <= kTailDirect and few CTAs
   const float2* V;  // Krylov basis V[(l r + s) N + i], l <= j read, l = j + 1 written
   float2* w;        // A z_j for the r right-hand sides (orthogonalised in place)
   int64_t N;
-  int r, j, m;
-  double2* part;    // [P][r][m + 1] partial dot products
-  double2* h;       // [r][m + 1] coefficients of the current pass
-  double* npart;    // [P][r] partial squared norms
+  int r, j, m, cs;  // cs: CTAs per right-hand side (the cluster size)
   double2* hacc;    // [r][m + 2] coefficients summed over both passes
   double2* Hm;
-  double* cs;
+  double* cs_;
   double2* sn;
   double2* g;
   double* res;      // [r] Arnoldi residual estimates
@@ -1384,47 +1362,55 @@ struct TailArgs {
   double tol;
   int* stop;        // set when every active right-hand side has converged
   int* jstop;       // steps taken when stop was set
-  unsigned* bar;
-  int* err;
+  unsigned* ticket; // clusters finished in this step (reset by the last one)
 };
 
-// One Arnoldi step after the product w = A P^-1 v_j, for all r right-hand
-// sides in one cooperative launch: classical Gram-Schmidt twice against
-// v_0..v_j (each pass: partial dot products per CTA chunk, a grid barrier,
-// each coefficient reduced by one CTA, a barrier, the update of the CTA's
-// own chunk), the norm, v_{j+1} = w / ||w||, the Givens step and the
-// convergence test on the device.  Skipped entirely once *stop is set, so
-// the host may queue steps ahead and read the flag only now and then.
 __global__ void __launch_bounds__(256) arnoldi_tail_kernel(TailArgs a) {
-  if (*a.stop) return;  // read by every CTA before the first barrier: uniform
-  __shared__ double sh_h[2 * kTailDirect];
-  const unsigned P = gridDim.x, c = blockIdx.x;
+  if (*a.stop) return;  // written only between launches: uniform over the grid
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ double2 part[2][kTailMaxM + 1];  // this CTA's partial dots, per pass
+  __shared__ double2 hsh[kTailMaxM + 1];      // the summed coefficients of the pass
+  __shared__ double npart, hn;
+  const int q = (int)cl.block_rank(), CS = a.cs;
+  const int s = blockIdx.y;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int r = a.r, nl = a.j + 1, m1 = a.m + 1;
-  const int64_t ch = (a.N + P - 1) / P;
-  const int64_t i0 = (int64_t)c * ch, i1 = min(a.N, i0 + ch), len = max((int64_t)0, i1 - i0);
-  const int npair = r * nl;
+  const int nl = a.j + 1;
+  // chunks of whole float4 pairs (N is a multiple of 4, so every chunk
+  // boundary and every pair is 16-byte aligned)
+  const int64_t np2 = a.N / 2, ch = (np2 + CS - 1) / CS;
+  const int64_t p0 = (int64_t)q * ch, p1 = min(np2, p0 + ch);
+  float4* ww = reinterpret_cast<float4*>(a.w + (int64_t)s * a.N);
+  const int64_t vstride = (int64_t)a.r * a.N / 2;  // in float4
+  const float4* V0 = reinterpret_cast<const float4*>(a.V + (int64_t)s * a.N);
   for (int pass = 0; pass < 2; ++pass) {
-    // partial dots conj(v_l[s]) . w[s] over this CTA's chunk, one warp per
-    // pair, four independent accumulators per lane (loads in flight)
-    for (int p = warp; p < npair; p += 8) {
-      const int s = p / nl, l = p % nl;
-      const float2* v = a.V + ((int64_t)l * r + s) * a.N;
-      const float2* ww = a.w + (int64_t)s * a.N;
+    // partial dots conj(v_l) . w over the chunk: a warp per basis vector,
+    // two entries per load, four independent accumulators per lane
+    for (int l = warp; l < nl; l += 8) {
+      const float4* v = V0 + l * vstride;
       float ar[4] = {0.f, 0.f, 0.f, 0.f}, ai[4] = {0.f, 0.f, 0.f, 0.f};
-      int64_t i = i0 + lane;
-      for (; i + 96 < i1; i += 128) {
+      int64_t i = p0 + lane;
+      for (; i + 96 < p1; i += 128) {
+        float4 x[4], y[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const float2 x = v[i + 32 * u], y = ww[i + 32 * u];
-          ar[u] = fmaf(x.x, y.x, fmaf(x.y, y.y, ar[u]));
-          ai[u] = fmaf(x.x, y.y, fmaf(-x.y, y.x, ai[u]));
+          x[u] = v[i + 32 * u];
+          y[u] = ww[i + 32 * u];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          ar[u] = fmaf(x[u].x, y[u].x, fmaf(x[u].y, y[u].y, ar[u]));
+          ai[u] = fmaf(x[u].x, y[u].y, fmaf(-x[u].y, y[u].x, ai[u]));
+          ar[u] = fmaf(x[u].z, y[u].z, fmaf(x[u].w, y[u].w, ar[u]));
+          ai[u] = fmaf(x[u].z, y[u].w, fmaf(-x[u].w, y[u].z, ai[u]));
         }
       }
-      for (; i < i1; i += 32) {
-        const float2 x = v[i], y = ww[i];
+      for (; i < p1; i += 32) {
+        const float4 x = v[i], y = ww[i];
         ar[0] = fmaf(x.x, y.x, fmaf(x.y, y.y, ar[0]));
         ai[0] = fmaf(x.x, y.y, fmaf(-x.y, y.x, ai[0]));
+        ar[1] = fmaf(x.z, y.z, fmaf(x.w, y.w, ar[1]));
+        ai[1] = fmaf(x.z, y.w, fmaf(-x.w, y.z, ai[1]));
       }
       double dr = (double)(ar[0] + ar[1]) + (double)(ar[2] + ar[3]);
       double di = (double)(ai[0] + ai[1]) + (double)(ai[2] + ai[3]);
@@ -1433,148 +1419,116 @@ __global__ void __launch_bounds__(256) arnoldi_tail_kernel(TailArgs a) {
         dr += __shfl_xor_sync(0xffffffffu, dr, o);
         di += __shfl_xor_sync(0xffffffffu, di, o);
       }
-      if (lane == 0) a.part[((int64_t)c * r + s) * m1 + l] = make_double2(dr, di);
+      if (lane == 0) part[pass][l] = make_double2(dr, di);
     }
-    grid_barrier(a.bar, P, a.err);
-    if (a.direct) {
-      // few partials: every CTA sums all of them itself (one barrier less);
-      // CTA 0 keeps the running sums for the Givens step
-      double2* hs = reinterpret_cast<double2*>(sh_h);
-      for (int p = warp; p < npair; p += 8) {
-        const int s = p / nl, l = p % nl;
-        double dr = 0, di = 0;
-        for (unsigned q = lane; q < P; q += 32) {
-          const double2 t = a.part[((int64_t)q * r + s) * m1 + l];
-          dr += t.x;
-          di += t.y;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          dr += __shfl_xor_sync(0xffffffffu, dr, o);
-          di += __shfl_xor_sync(0xffffffffu, di, o);
-        }
-        if (lane == 0) {
-          hs[p] = make_double2(dr, di);
-          if (c == 0) {
-            double2* acc = a.hacc + (int64_t)s * (a.m + 2) + l;
-            acc->x += dr;
-            acc->y += di;
-          }
-        }
-      }
-      __syncthreads();
-      // w[s] -= sum_l h[s][l] v_l[s] on this CTA's chunk
-      for (int64_t t = threadIdx.x; t < (int64_t)r * len; t += blockDim.x) {
-        const int s = (int)(t / len);
-        const int64_t i = i0 + t % len;
-        float2* wp = a.w + (int64_t)s * a.N + i;
-        float ar = wp->x, ai = wp->y;
-#pragma unroll 4
-        for (int l = 0; l < nl; ++l) {
-          const double2 hd = hs[s * nl + l];
-          const float hr = (float)hd.x, hi = (float)hd.y;
-          const float2 v = a.V[((int64_t)l * r + s) * a.N + i];
-          ar = fmaf(-hr, v.x, fmaf(hi, v.y, ar));
-          ai = fmaf(-hr, v.y, fmaf(-hi, v.x, ai));
-        }
-        *wp = make_float2(ar, ai);
-      }
-      __syncthreads();
-      continue;
-    }
-    // coefficient p = c, c + P, ...: sum of the P partials, by one warp each
-    for (int p = c + P * warp; p < npair; p += P * 8) {
-      const int s = p / nl, l = p % nl;
-      double dr = 0, di = 0;
-      for (unsigned q = lane; q < P; q += 32) {
-        const double2 t = a.part[((int64_t)q * r + s) * m1 + l];
+    cl.sync();
+    // every CTA sums the partials of the cluster in rank order
+    for (int l = threadIdx.x; l < nl; l += blockDim.x) {
+      double dr = 0.0, di = 0.0;
+      for (int k = 0; k < CS; ++k) {
+        const double2 t = cl.map_shared_rank(&part[pass][0], k)[l];
         dr += t.x;
         di += t.y;
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        dr += __shfl_xor_sync(0xffffffffu, dr, o);
-        di += __shfl_xor_sync(0xffffffffu, di, o);
-      }
-      if (lane == 0) {
-        a.h[(int64_t)s * m1 + l] = make_double2(dr, di);
+      hsh[l] = make_double2(dr, di);
+      if (q == 0) {
         double2* acc = a.hacc + (int64_t)s * (a.m + 2) + l;
         acc->x += dr;
         acc->y += di;
       }
     }
-    grid_barrier(a.bar, P, a.err);
-    // w[s] -= sum_l h[s][l] v_l[s] on this CTA's chunk
-    for (int64_t t = threadIdx.x; t < (int64_t)r * len; t += blockDim.x) {
-      const int s = (int)(t / len);
-      const int64_t i = i0 + t % len;
-      float2* wp = a.w + (int64_t)s * a.N + i;
-      float ar = wp->x, ai = wp->y;
-      const double2* hs = a.h + (int64_t)s * m1;
-      for (int l = 0; l < nl; ++l) {
-        const double2 hd = hs[l];
-        const float hr = (float)hd.x, hi = (float)hd.y;
-        const float2 v = a.V[((int64_t)l * r + s) * a.N + i];
-        ar = fmaf(-hr, v.x, fmaf(hi, v.y, ar));
-        ai = fmaf(-hr, v.y, fmaf(-hi, v.x, ai));
-      }
-      *wp = make_float2(ar, ai);
-    }
-    __syncthreads();  // the next pass reads this CTA's chunk only
-  }
-  // squared norms of this chunk, one warp per right-hand side
-  for (int s = warp; s < r; s += 8) {
-    const float2* ww = a.w + (int64_t)s * a.N;
-    double q = 0;
-    for (int64_t i = i0 + lane; i < i1; i += 32) q += (double)ww[i].x * ww[i].x + (double)ww[i].y * ww[i].y;
+    __syncthreads();
+    // w -= sum_l h_l v_l on the chunk, eight basis vectors' loads in flight
+    for (int64_t i = p0 + threadIdx.x; i < p1; i += blockDim.x) {
+      float4 acc = ww[i];
+      int l = 0;
+      for (; l + 8 <= nl; l += 8) {
+        float4 v[8];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
-    if (lane == 0) a.npart[(int64_t)c * r + s] = q;
-  }
-  grid_barrier(a.bar, P, a.err);
-  // v_{j+1} = w / ||w|| (every CTA sums the partials in the same order)
-  __shared__ double hn_sh[128];
-  for (int s = warp; s < r; s += 8) {
-    double q = 0;
-    for (unsigned k = lane; k < P; k += 32) q += a.npart[(int64_t)k * r + s];
+        for (int u = 0; u < 8; ++u) v[u] = V0[(l + u) * vstride + i];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
-    if (lane == 0) hn_sh[s] = sqrt(q);
-  }
-  __syncthreads();
-  float2* vn = const_cast<float2*>(a.V) + (int64_t)(a.j + 1) * r * a.N;
-  for (int64_t t = threadIdx.x; t < (int64_t)r * len; t += blockDim.x) {
-    const int s = (int)(t / len);
-    const int64_t i = i0 + t % len;
-    const double n = hn_sh[s];
-    const double inv = n > 0 ? 1.0 / n : 0.0;
-    const float2 x = a.w[(int64_t)s * a.N + i];
-    vn[(int64_t)s * a.N + i] = make_float2((float)(x.x * inv), (float)(x.y * inv));
-  }
-  if (c != 0) return;
-  for (int s = threadIdx.x; s < r; s += blockDim.x)
-    givens_column(a.j, a.m, s, a.hacc, hn_sh[s], a.Hm, a.cs, a.sn, a.g, a.res);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    bool all = true;
-    for (int s = 0; s < r; ++s) {
-      if (!a.active[s]) continue;
-      if (a.kk[s] == 0) {
-        const double v = a.res[s];
-        if (!(v == v)) {
-          a.bad[s] = 1;
-          a.kk[s] = a.j + 1;
-        } else if (v <= a.tol) {
-          a.kk[s] = a.j + 1;
+        for (int u = 0; u < 8; ++u) {
+          const double2 hd = hsh[l + u];
+          const float hr = (float)hd.x, hi = (float)hd.y;
+          acc.x = fmaf(-hr, v[u].x, fmaf(hi, v[u].y, acc.x));
+          acc.y = fmaf(-hr, v[u].y, fmaf(-hi, v[u].x, acc.y));
+          acc.z = fmaf(-hr, v[u].z, fmaf(hi, v[u].w, acc.z));
+          acc.w = fmaf(-hr, v[u].w, fmaf(-hi, v[u].z, acc.w));
         }
       }
-      if (a.kk[s] == 0) all = false;
+      for (; l < nl; ++l) {
+        const float4 v = V0[l * vstride + i];
+        const double2 hd = hsh[l];
+        const float hr = (float)hd.x, hi = (float)hd.y;
+        acc.x = fmaf(-hr, v.x, fmaf(hi, v.y, acc.x));
+        acc.y = fmaf(-hr, v.y, fmaf(-hi, v.x, acc.y));
+        acc.z = fmaf(-hr, v.z, fmaf(hi, v.w, acc.z));
+        acc.w = fmaf(-hr, v.w, fmaf(-hi, v.z, acc.w));
+      }
+      ww[i] = acc;
     }
-    if (all) {
-      *a.jstop = a.j + 1;
-      *a.stop = 1;
+    __syncthreads();  // hsh is rewritten by the next pass; the chunk is this CTA's own
+  }
+  // squared norm of the chunk
+  {
+    double qn = 0.0;
+    for (int64_t i = p0 + threadIdx.x; i < p1; i += blockDim.x) {
+      const float4 x = ww[i];
+      qn += (double)x.x * x.x + (double)x.y * x.y + (double)x.z * x.z + (double)x.w * x.w;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) qn += __shfl_xor_sync(0xffffffffu, qn, o);
+    double* wsum = reinterpret_cast<double*>(&hsh[0]);
+    if (lane == 0) wsum[warp] = qn;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int k = 0; k < 8; ++k) t += wsum[k];
+      npart = t;
     }
   }
+  cl.sync();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < CS; ++k) t += *cl.map_shared_rank(&npart, k);
+    hn = sqrt(t);
+  }
+  // no CTA may leave while another still reads its shared memory
+  cl.sync();
+  {
+    const double inv = hn > 0 ? 1.0 / hn : 0.0;
+    float4* vn = const_cast<float4*>(V0) + (int64_t)(a.j + 1) * vstride;
+    for (int64_t i = p0 + threadIdx.x; i < p1; i += blockDim.x) {
+      const float4 x = ww[i];
+      vn[i] = make_float4((float)(x.x * inv), (float)(x.y * inv), (float)(x.z * inv),
+                          (float)(x.w * inv));
+    }
+  }
+  if (q != 0 || threadIdx.x != 0) return;
+  givens_column(a.j, a.m, s, a.hacc, hn, a.Hm, a.cs_, a.sn, a.g, a.res);
+  if (a.active[s] && a.kk[s] == 0) {
+    const double v = a.res[s];
+    if (!(v == v)) {
+      a.bad[s] = 1;
+      a.kk[s] = a.j + 1;
+    } else if (v <= a.tol) {
+      a.kk[s] = a.j + 1;
+    }
+  }
+  __threadfence();
+  if (atomicAdd(a.ticket, 1u) != (unsigned)a.r - 1) return;
+  // the last cluster of the step: every right-hand side's kk is visible
+  __threadfence();
+  bool all = true;
+  for (int k = 0; k < a.r; ++k) {
+    if (!a.active[k]) continue;
+    if (((volatile int*)a.kk)[k] == 0) all = false;
+  }
+  if (all) {
+    *a.jstop = a.j + 1;
+    *a.stop = 1;
+  }
+  *a.ticket = 0u;
 }
 
 // g[s] = beta[s] e1
@@ -2481,24 +2435,41 @@ struct LockWork {
   int *mask, *kk;
   void* mwork;
   float2* near32;  // complex64 copy of the near blocks (nnzb x 16), or null
-  // fused Arnoldi step (arnoldi_tail_kernel): P CTAs
-  int P;
-  double2 *tpart, *th;
-  double* tnpart;
-  int* flags;      // [0] stop, [1] steps at stop, [2] barrier timeout, [4..5] barrier
+  // fused Arnoldi step (arnoldi_tail_kernel): tcs CTAs per right-hand side
+  int tcs;
+  int* flags;      // [0] stop, [1] steps at stop, [8] finished-cluster ticket
   int* bad;        // [r] residual estimate not a number
 };
 
-// CTAs of the fused Arnoldi step: about one per 1024 vector entries (the
-// Krylov basis is read from L2 by every CTA's SM), at least 32 and at most
-// one per SM, and at least 32 entries per CTA
-static int tail_ctas(int64_t N, int r) {
-  int dev = 0, nsm = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
-    nsm = 1;
-  const int64_t want = std::max<int64_t>(32, (int64_t)r * N / 1024);
-  return (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)nsm, want, (N + 31) / 32}));
+// CTAs per right-hand side in the fused Arnoldi step (its cluster size): a
+// power of two with at least about 640 vector entries per CTA, at most 16
+// (more than 8 is a non-portable cluster size, taken only where the device
+// can run such a cluster of this kernel)
+static int tail_cluster(int64_t N) {
+  static int cmax = 0;
+  if (cmax == 0) {
+    cmax = 8;
+    if (cudaFuncSetAttribute(arnoldi_tail_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+        cudaSuccess) {
+      cudaLaunchConfig_t lc = {};
+      lc.gridDim = dim3(16, 1);
+      lc.blockDim = dim3(256);
+      cudaLaunchAttribute la[1];
+      la[0].id = cudaLaunchAttributeClusterDimension;
+      la[0].val.clusterDim.x = 16;
+      la[0].val.clusterDim.y = 1;
+      la[0].val.clusterDim.z = 1;
+      lc.attrs = la;
+      lc.numAttrs = 1;
+      int ncl = 0;
+      if (cudaOccupancyMaxActiveClusters(&ncl, arnoldi_tail_kernel, &lc) == cudaSuccess && ncl > 0)
+        cmax = 16;
+    }
+    cudaGetLastError();
+  }
+  int c = 1;
+  while (c < cmax && N > (int64_t)640 * c) c *= 2;
+  return c;
 }
 
 static size_t lock_bytes(int64_t N, int r, int m, int64_t nnzb) {
@@ -2520,10 +2491,6 @@ static size_t lock_bytes(int64_t N, int r, int m, int64_t nnzb) {
   add((size_t)r * 4);
   if (r >= 2) add(mrhs_work_bytes(N, r));
   if (nnzb > 0) add((size_t)nnzb * 16 * 8);
-  const int P = tail_ctas(N, r);
-  add((size_t)P * r * (m + 1) * 16);
-  add((size_t)r * (m + 1) * 16);
-  add((size_t)P * r * 8);
   add(64 * 4);
   add((size_t)r * 4);
   return b + 1024;
@@ -2567,10 +2534,7 @@ static LockWork carve_lock(char* p, int64_t N, int r, int m, int64_t nnzb) {
   W.kk = (int*)take((size_t)r * 4);
   W.mwork = r >= 2 ? take(mrhs_work_bytes(N, r)) : nullptr;
   W.near32 = nnzb > 0 ? (float2*)take((size_t)nnzb * 16 * 8) : nullptr;
-  W.P = tail_ctas(N, r);
-  W.tpart = (double2*)take((size_t)W.P * r * (m + 1) * 16);
-  W.th = (double2*)take((size_t)r * (m + 1) * 16);
-  W.tnpart = (double*)take((size_t)W.P * r * 8);
+  W.tcs = tail_cluster(N);
   W.flags = (int*)take(64 * 4);
   W.bad = (int*)take((size_t)r * 4);
   return W;
@@ -2638,10 +2602,15 @@ static mueller_status lock_gmres(const InnerOp& I, LockWork& W, double tol, int 
   std::vector<double> beta(r), bn(r, 1.0);
   mueller_status st = MUELLER_OK;
   MU_CUDA(cudaMemsetAsync(W.d32, 0, (size_t)r * N * 8, s));
-  for (int cycle = 0; iters < maxit; ++cycle) {
-    // residual of the inner system: w = rhs - A d
-    if ((st = lock_matvec(I, W, W.d32, W.W, s))) return st;
-    { Prof prof_("resid_b_kernel", s); resid_b_kernel<<<nblk((int64_t)r * N, 256), 256, 0, s>>>(W.rhs32, W.W, (int64_t)r * N); }
+  bool converged = false;
+  for (int cycle = 0; iters < maxit && !converged; ++cycle) {
+    // residual of the inner system: w = rhs - A d (d = 0 in the first cycle)
+    if (cycle == 0) {
+      MU_CUDA(cudaMemcpyAsync(W.W, W.rhs32, (size_t)r * N * 8, cudaMemcpyDeviceToDevice, s));
+    } else {
+      if ((st = lock_matvec(I, W, W.d32, W.W, s))) return st;
+      { Prof prof_("resid_b_kernel", s); resid_b_kernel<<<nblk((int64_t)r * N, 256), 256, 0, s>>>(W.rhs32, W.W, (int64_t)r * N); }
+    }
     for (int k = 0; k < r; ++k) mask[k] = active[k];
     MU_CUDA(cudaMemcpyAsync(W.mask, mask.data(), r * 4, cudaMemcpyHostToDevice, s));
     if ((st = lock_norms<float2>(W, W.W, W.beta, W.mask, s))) return st;
@@ -2676,12 +2645,10 @@ static mueller_status lock_gmres(const InnerOp& I, LockWork& W, double tol, int 
       ta.N = N;
       ta.r = r;
       ta.m = m;
-      ta.part = W.tpart;
-      ta.h = W.th;
-      ta.npart = W.tnpart;
+      ta.cs = W.tcs;
       ta.hacc = W.hacc;
       ta.Hm = W.Hm;
-      ta.cs = W.cs;
+      ta.cs_ = W.cs;
       ta.sn = W.sn;
       ta.g = W.g;
       ta.res = W.res;
@@ -2691,33 +2658,40 @@ static mueller_status lock_gmres(const InnerOp& I, LockWork& W, double tol, int 
       ta.tol = tol;
       ta.stop = W.flags;
       ta.jstop = W.flags + 1;
-      ta.err = W.flags + 2;
-      ta.bar = (unsigned*)(W.flags + 4);
-      ta.direct = (r * (m + 1) <= kTailDirect && (int64_t)W.P * r * (m + 1) <= 16384) ? 1 : 0;
+      ta.ticket = (unsigned*)(W.flags + 8);
+      cudaLaunchConfig_t lc = {};
+      lc.gridDim = dim3(W.tcs, r);
+      lc.blockDim = dim3(256);
+      lc.stream = s;
+      cudaLaunchAttribute la[1];
+      la[0].id = cudaLaunchAttributeClusterDimension;
+      la[0].val.clusterDim.x = W.tcs;
+      la[0].val.clusterDim.y = 1;
+      la[0].val.clusterDim.z = 1;
+      lc.attrs = la;
+      lc.numAttrs = 1;
       int queued = 0, hf[3] = {0, 0, 0};
       for (int j = 0; j < m && iters + queued < maxit; ++j) {
         const float2* Vj = W.V + (int64_t)j * r * N;
         if ((st = lock_precond(I, W, Vj, W.Zt, s, stop))) return st;
         if ((st = lock_matvec(I, W, W.Zt, W.W, s, stop))) return st;
         ta.j = j;
-        void* args[] = {&ta};
         {
           Prof prof_("arnoldi_tail_kernel", s);
-          MU_CUDA(cudaLaunchCooperativeKernel((const void*)arnoldi_tail_kernel, dim3(W.P), dim3(256),
-                                              args, 0, s));
+          MU_CUDA(cudaLaunchKernelEx(&lc, arnoldi_tail_kernel, ta));
         }
         ++queued;
         if ((j + 1) % kSync == 0 || j == m - 1 || iters + queued >= maxit) {
           MU_CUDA(cudaMemcpyAsync(hf, W.flags, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
           MU_CUDA(cudaStreamSynchronize(s));
-          if (hf[2]) {
-            set_error("GMRES: a grid barrier of the Arnoldi step timed out");
-            return MUELLER_ERR_TIMEOUT;
-          }
           if (hf[0]) break;
         }
       }
       const int done = hf[0] ? hf[1] : queued;
+      // every active right-hand side met the tolerance on its Arnoldi
+      // estimate: the cycle's update ends the inner solve (the outer FP64
+      // residual checks the result; a shortfall costs one more refinement)
+      converged = hf[0] != 0;
       iters += done;
       jlast = done - 1;
       MU_CUDA(cudaMemcpyAsync(kk.data(), W.kk, (size_t)r * 4, cudaMemcpyDeviceToHost, s));
@@ -2745,7 +2719,10 @@ static mueller_status lock_gmres(const InnerOp& I, LockWork& W, double tol, int 
           if (kk[k] == 0 && (hbuf[k] <= tol || !(hbuf[k] == hbuf[k]))) kk[k] = j + 1;
           if (kk[k] == 0) all = false;
         }
-        if (all) break;
+        if (all) {
+          converged = true;
+          break;
+        }
       }
     }
     int kmax = 0;
