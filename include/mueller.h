@@ -508,7 +508,7 @@ mueller_status mueller_far_field(mueller_mesh* mesh, const mueller_params* param
  *     r * (n_tri * q_regular + n_theta * n_phi + n_dir)) is rejected with
  *     INVALID_ARG and a message naming the size.  The level-3 sphere (1280
  *     triangles, q_regular = 6) with the default 48 x 96 sphere rule needs
- *     about 1.07 MB per right-hand side: up to 15 right-hand sides fit, 16
+ *     about 0.97 MB per right-hand side: up to 17 right-hand sides fit, 18
  *     are refused.
  *   - the mesh must already hold the point geometry for params (call
  *     mueller_assemble or mueller_far_field with the same params first), else

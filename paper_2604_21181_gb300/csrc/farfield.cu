@@ -128,29 +128,38 @@ __device__ __forceinline__ void block_sum12(double (*red)[256], const double* ac
   }
 }
 
+// F(r) from the twelve sums (N~ re/im, L~ re/im per component) of one
+// direction
+__device__ __forceinline__ void far_store(const double* sum, double rx, double ry, double rz,
+                                          double ka, double2* __restrict__ F_out) {
+  double Nr[3], Ni[3], Lr[3], Li[3];
+  for (int a = 0; a < 3; ++a) {
+    Nr[a] = sum[2 * a];
+    Ni[a] = sum[2 * a + 1];
+    Lr[a] = sum[6 + 2 * a];
+    Li[a] = sum[7 + 2 * a];
+  }
+  const double r[3] = {rx, ry, rz};
+  const double rNr = r[0] * Nr[0] + r[1] * Nr[1] + r[2] * Nr[2];
+  const double rNi = r[0] * Ni[0] + r[1] * Ni[1] + r[2] * Ni[2];
+  const double cLr[3] = {r[1] * Lr[2] - r[2] * Lr[1], r[2] * Lr[0] - r[0] * Lr[2], r[0] * Lr[1] - r[1] * Lr[0]};
+  const double cLi[3] = {r[1] * Li[2] - r[2] * Li[1], r[2] * Li[0] - r[0] * Li[2], r[0] * Li[1] - r[1] * Li[0]};
+  const double pre = ka / (4.0 * 3.14159265358979323846);  // i k / 4 pi -> multiply by i
+  for (int a = 0; a < 3; ++a) {
+    const double vr = Nr[a] - r[a] * rNr - cLr[a];
+    const double vi = Ni[a] - r[a] * rNi - cLi[a];
+    F_out[a] = make_double2(-pre * vi, pre * vr);
+  }
+}
+
 __device__ __forceinline__ void far_finish(double (*red)[256], const double* acc, double rx,
                                            double ry, double rz, double ka,
                                            double2* __restrict__ F_out) {
   block_sum12(red, acc);
   if (threadIdx.x == 0) {
-    double Nr[3], Ni[3], Lr[3], Li[3];
-    for (int a = 0; a < 3; ++a) {
-      Nr[a] = red[2 * a][0];
-      Ni[a] = red[2 * a + 1][0];
-      Lr[a] = red[6 + 2 * a][0];
-      Li[a] = red[7 + 2 * a][0];
-    }
-    const double r[3] = {rx, ry, rz};
-    const double rNr = r[0] * Nr[0] + r[1] * Nr[1] + r[2] * Nr[2];
-    const double rNi = r[0] * Ni[0] + r[1] * Ni[1] + r[2] * Ni[2];
-    const double cLr[3] = {r[1] * Lr[2] - r[2] * Lr[1], r[2] * Lr[0] - r[0] * Lr[2], r[0] * Lr[1] - r[1] * Lr[0]};
-    const double cLi[3] = {r[1] * Li[2] - r[2] * Li[1], r[2] * Li[0] - r[0] * Li[2], r[0] * Li[1] - r[1] * Li[0]};
-    const double pre = ka / (4.0 * 3.14159265358979323846);  // i k / 4 pi -> multiply by i
-    for (int a = 0; a < 3; ++a) {
-      const double vr = Nr[a] - r[a] * rNr - cLr[a];
-      const double vi = Ni[a] - r[a] * rNi - cLi[a];
-      F_out[a] = make_double2(-pre * vi, pre * vr);
-    }
+    double sum[12];
+    for (int c = 0; c < 12; ++c) sum[c] = red[c][0];
+    far_store(sum, rx, ry, rz, ka, F_out);
   }
 }
 
@@ -207,22 +216,21 @@ __global__ void __launch_bounds__(256) far_kernel(int64_t np, const double* __re
 
 inline unsigned far_grid(int64_t nd_eval) { return (unsigned)((nd_eval + kFarDT - 1) / kFarDT); }
 
-// The forward direction (index 0 of each RHS's direction list) of every RHS:
-// one direction has too little work for one CTA, so CTA (g, s) sums the
-// partials of point chunk g of RHS s and far_fwd_finish_kernel adds the
-// chunks up and forms F.
+// The forward direction (k-hat of each RHS, read from its incident wave inc
+// [r][6]; index 0 of its far-field list) of every RHS: one direction has too
+// little work for one CTA, so CTA (g, s) sums the partials of point chunk g
+// of RHS s and far_fwd_finish_kernel adds the chunks up and forms F.
 constexpr int kFwdChunks = 64;
 __global__ void __launch_bounds__(256) far_fwd_part_kernel(int64_t np, const double* __restrict__ qd,
                                                            const double2* __restrict__ rec,
-                                                           const double* __restrict__ dirs,
-                                                           int64_t nd, double ka,
-                                                           double* __restrict__ part) {
+                                                           const double* __restrict__ inc,
+                                                           double ka, double* __restrict__ part) {
   __shared__ double2 tab[kCisN];
   __shared__ double red[12][256];
   cis_fill(tab);
   __syncthreads();
   const int s = blockIdx.y, g = blockIdx.x, G = gridDim.x;
-  const double* dd = dirs + (int64_t)s * nd * 3;
+  const double* dd = inc + (int64_t)s * 6;
   const double rk0 = -ka * dd[0], rk1 = -ka * dd[1], rk2 = -ka * dd[2];
   const int64_t chunk = (np + G - 1) / G, t0 = (int64_t)g * chunk;
   const int64_t t1 = t0 + chunk < np ? t0 + chunk : np;
@@ -245,7 +253,7 @@ __global__ void __launch_bounds__(256) far_fwd_part_kernel(int64_t np, const dou
 }
 
 __global__ void __launch_bounds__(256) far_fwd_finish_kernel(const double* __restrict__ part, int G,
-                                                             const double* __restrict__ dirs,
+                                                             const double* __restrict__ inc,
                                                              int64_t nd, double ka,
                                                              double2* __restrict__ F) {
   __shared__ double red[12][256];
@@ -254,7 +262,7 @@ __global__ void __launch_bounds__(256) far_fwd_finish_kernel(const double* __res
 #pragma unroll
   for (int c = 0; c < 12; ++c)
     acc[c] = (int)threadIdx.x < G ? part[((int64_t)s * G + threadIdx.x) * 12 + c] : 0.0;
-  const double* dd = dirs + (int64_t)s * nd * 3;
+  const double* dd = inc + (int64_t)s * 6;
   far_finish(red, acc, dd[0], dd[1], dd[2], ka, F + (int64_t)s * nd * 3);
 }
 
@@ -282,24 +290,26 @@ __host__ __device__ __forceinline__ void sphere_pair(int64_t p, int n_theta, int
 //   F(d_k1) += (v.x e.x - v.y e.y, v.x e.y + v.y e.x),
 //   F(d_k2) += (v.x e.x + v.y e.y, v.y e.x - v.x e.y),
 // summed as the four sums of v.x e.x, v.y e.y, v.x e.y, v.y e.x (4 FMAs per
-// component for both directions).  A CTA takes DP pairs and RS right-hand
-// sides (blockIdx.y: right-hand sides RS*y ..).  dirs and F point at the
-// sphere block (index k) of right-hand side 0; F of right-hand side s is
-// F + s * f_stride, its currents rec + s * np * 6.
-constexpr int kFarDP = 2;   // one right-hand side: pairs per CTA
-constexpr int kFarMRS = 2;  // several: right-hand sides per CTA (one pair)
+// component for both directions).  A warp takes DP pairs and RS right-hand
+// sides (blockIdx.y: right-hand sides RS*y ..), its lanes stride over the
+// points and its sums meet by shuffles, so no CTA-wide reduction stalls the
+// CTA's other pairs.  dirs and F point at the sphere block (index k) of
+// right-hand side 0; F of right-hand side s is F + s * f_stride, its
+// currents rec + s * np * 6.
+constexpr int kFarMRS = 4;  // several right-hand sides: per warp (one pair each)
+constexpr int kFarWarps = 8;
 template <int DP, int RS>
-__global__ void __launch_bounds__(256, 2) far_pair_kernel(int64_t np, const double* __restrict__ qd,
-                                                       const double2* __restrict__ rec, int r,
-                                                       const double* __restrict__ dirs,
-                                                       int n_theta, int n_phi, double ka,
-                                                       double2* __restrict__ F, int64_t f_stride) {
+__global__ void __launch_bounds__(32 * kFarWarps, RS > 2 ? 1 : 2) far_pair_kernel(
+    int64_t np, const double* __restrict__ qd, const double2* __restrict__ rec, int r,
+    const double* __restrict__ dirs, int n_theta, int n_phi, double ka, double2* __restrict__ F,
+    int64_t f_stride) {
   __shared__ double2 tab[kCisN];
-  __shared__ double red[12][256];
   cis_fill(tab);
   __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t npairs = (int64_t)n_theta * n_phi / 2;
-  const int64_t p0 = (int64_t)blockIdx.x * DP;
+  const int64_t p0 = ((int64_t)blockIdx.x * kFarWarps + warp) * DP;
+  if (p0 >= npairs) return;  // whole warps; no CTA barrier follows
   const int s0 = blockIdx.y * RS;
   double rk[DP][3];
 #pragma unroll
@@ -318,7 +328,7 @@ __global__ void __launch_bounds__(256, 2) far_pair_kernel(int64_t np, const doub
       for (int h = 0; h < 4; ++h)
 #pragma unroll
         for (int c = 0; c < 6; ++c) acc[q][k][h][c] = 0.0;
-  for (int64_t t = threadIdx.x; t < np; t += blockDim.x) {
+  for (int64_t t = lane; t < np; t += 32) {
     const double* qp = qd + t * QD_STRIDE;
     const double y0 = qp[0], y1 = qp[1], y2 = qp[2];
     double2 e[DP];
@@ -344,28 +354,39 @@ __global__ void __launch_bounds__(256, 2) far_pair_kernel(int64_t np, const doub
     }
   }
 #pragma unroll
-  for (int q = 0; q < DP; ++q) {
-    if (p0 + q < npairs) {
-      int64_t kk[2];
-      sphere_pair(p0 + q, n_theta, n_phi, kk[0], kk[1]);
+  for (int q = 0; q < DP; ++q)
 #pragma unroll
-      for (int k = 0; k < RS; ++k) {
-        if (s0 + k < r) {
+    for (int k = 0; k < RS; ++k)
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            double a[12];
+      for (int h = 0; h < 4; ++h)
 #pragma unroll
-            for (int c = 0; c < 6; ++c) {
-              const double xx = acc[q][k][0][c], yy = acc[q][k][1][c];
-              const double xy = acc[q][k][2][c], yx = acc[q][k][3][c];
-              a[2 * c] = h ? xx + yy : xx - yy;
-              a[2 * c + 1] = h ? yx - xy : xy + yx;
-            }
-            const double* dd = dirs + 3 * kk[h];
-            far_finish(red, a, dd[0], dd[1], dd[2], ka, F + (s0 + k) * f_stride + kk[h] * 3);
-            __syncthreads();
-          }
+        for (int c = 0; c < 6; ++c) {
+          double v = acc[q][k][h][c];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          acc[q][k][h][c] = v;
         }
+  if (lane != 0) return;
+#pragma unroll
+  for (int q = 0; q < DP; ++q) {
+    if (p0 + q >= npairs) continue;
+    int64_t kk[2];
+    sphere_pair(p0 + q, n_theta, n_phi, kk[0], kk[1]);
+#pragma unroll
+    for (int k = 0; k < RS; ++k) {
+      if (s0 + k >= r) continue;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        double a[12];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          const double xx = acc[q][k][0][c], yy = acc[q][k][1][c];
+          const double xy = acc[q][k][2][c], yx = acc[q][k][3][c];
+          a[2 * c] = h ? xx + yy : xx - yy;
+          a[2 * c + 1] = h ? yx - xy : xy + yx;
+        }
+        const double* dd = dirs + 3 * kk[h];
+        far_store(a, dd[0], dd[1], dd[2], ka, F + (s0 + k) * f_stride + kk[h] * 3);
       }
     }
   }
@@ -476,34 +497,32 @@ __global__ void copy_user_dirs_kernel(const double2* __restrict__ Fall, int64_t 
 // written in exact antipodal pairs (sphere_pair), the second direction of
 // each pair the negated first (Gauss-Legendre nodes are symmetric, up to
 // the rounding of their computation).
-std::vector<double> far_dirs(int r, const double* inc, int n_theta, int n_phi,
+std::vector<double> far_dirs(const double* inc, int n_theta, int n_phi,
                              const std::vector<double>& gth, const double* dirs, int64_t ndir) {
   const int64_t nsph = (int64_t)n_theta * n_phi, nd = 1 + nsph + ndir;
-  std::vector<double> hd((size_t)r * nd * 3);
-  for (int sidx = 0; sidx < r; ++sidx) {
-    double* o = hd.data() + (size_t)sidx * nd * 3;
-    o[0] = inc[6 * sidx];
-    o[1] = inc[6 * sidx + 1];
-    o[2] = inc[6 * sidx + 2];
-    for (int it = 0; it < n_theta; ++it) {
-      const double ct = 2.0 * gth[it] - 1.0, st = sqrt(fmax(0.0, 1.0 - ct * ct));
-      for (int ip = 0; ip < n_phi; ++ip) {
-        const double ph = 2.0 * 3.14159265358979323846 * ip / n_phi;
-        double* dd = o + 3 * (1 + (int64_t)it * n_phi + ip);
-        dd[0] = st * cos(ph);
-        dd[1] = st * sin(ph);
-        dd[2] = ct;
-      }
+  std::vector<double> hd((size_t)nd * 3);
+  double* o = hd.data();
+  o[0] = inc[0];
+  o[1] = inc[1];
+  o[2] = inc[2];
+  for (int it = 0; it < n_theta; ++it) {
+    const double ct = 2.0 * gth[it] - 1.0, st = sqrt(fmax(0.0, 1.0 - ct * ct));
+    for (int ip = 0; ip < n_phi; ++ip) {
+      const double ph = 2.0 * 3.14159265358979323846 * ip / n_phi;
+      double* dd = o + 3 * (1 + (int64_t)it * n_phi + ip);
+      dd[0] = st * cos(ph);
+      dd[1] = st * sin(ph);
+      dd[2] = ct;
     }
-    if (n_phi % 2 == 0)
-      for (int64_t p = 0; p < nsph / 2; ++p) {
-        int64_t k1, k2;
-        sphere_pair(p, n_theta, n_phi, k1, k2);
-        for (int a = 0; a < 3; ++a) o[3 * (1 + k2) + a] = -o[3 * (1 + k1) + a];
-      }
-    for (int64_t d = 0; d < ndir; ++d)
-      for (int a = 0; a < 3; ++a) o[3 * (1 + nsph + d) + a] = dirs[3 * d + a];
   }
+  if (n_phi % 2 == 0)
+    for (int64_t p = 0; p < nsph / 2; ++p) {
+      int64_t k1, k2;
+      sphere_pair(p, n_theta, n_phi, k1, k2);
+      for (int a = 0; a < 3; ++a) o[3 * (1 + k2) + a] = -o[3 * (1 + k1) + a];
+    }
+  for (int64_t d = 0; d < ndir; ++d)
+    for (int a = 0; a < 3; ++a) o[3 * (1 + nsph + d) + a] = dirs[3 * d + a];
   return hd;
 }
 
@@ -520,7 +539,7 @@ mueller_status far_one_rhs(int64_t np, const double* qd, const double2* rec, con
     return MUELLER_OK;
   }
   const int64_t npairs = nsph / 2;
-  { Prof prof_("far_pair_kernel", s); far_pair_kernel<kFarDP, 1><<<(unsigned)((npairs + kFarDP - 1) / kFarDP), 256, 0, s>>>(
+  { Prof prof_("far_pair_kernel", s); far_pair_kernel<1, 1><<<(unsigned)((npairs + kFarWarps - 1) / kFarWarps), 32 * kFarWarps, 0, s>>>(
       np, qd, rec, 1, dirs + 3, n_theta, n_phi, ka, F + 3, 0); }
   if (ndir > 0)
     { Prof prof_("far_kernel", s); far_kernel<kFarDT><<<far_grid(ndir), 256, 0, s>>>(np, qd, rec, dirs + 3 * (1 + nsph), ndir, ka,
@@ -542,7 +561,7 @@ mueller_status far_shared(int64_t np, const double* qd, const double2* rec, int 
   int64_t d0 = 1;
   if (n_phi % 2 == 0) {
     Prof prof_("far_pair_kernel", s);
-    far_pair_kernel<1, kFarMRS><<<dim3((unsigned)(nsph / 2), (unsigned)((r + kFarMRS - 1) / kFarMRS)), 256, 0, s>>>(
+    far_pair_kernel<1, kFarMRS><<<dim3((unsigned)((nsph / 2 + kFarWarps - 1) / kFarWarps), (unsigned)((r + kFarMRS - 1) / kFarMRS)), 32 * kFarWarps, 0, s>>>(
         np, qd, rec, r, dirs + 3, n_theta, n_phi, ka, F + 3, nd * 3);
     d0 = 1 + nsph;
   }
@@ -556,10 +575,10 @@ mueller_status far_shared(int64_t np, const double* qd, const double2* rec, int 
 }
 
 // the forward direction of all r right-hand sides (part: r x kFwdChunks x 12)
-mueller_status far_fwd(int64_t np, const double* qd, const double2* rec, const double* dirs,
+mueller_status far_fwd(int64_t np, const double* qd, const double2* rec, const double* inc,
                        int64_t nd, int r, double ka, double* part, double2* F, cudaStream_t s) {
-  { Prof prof_("far_fwd_part_kernel", s); far_fwd_part_kernel<<<dim3(kFwdChunks, (unsigned)r), 256, 0, s>>>(np, qd, rec, dirs, nd, ka, part); }
-  { Prof prof_("far_fwd_finish_kernel", s); far_fwd_finish_kernel<<<(unsigned)r, 256, 0, s>>>(part, kFwdChunks, dirs, nd, ka, F); }
+  { Prof prof_("far_fwd_part_kernel", s); far_fwd_part_kernel<<<dim3(kFwdChunks, (unsigned)r), 256, 0, s>>>(np, qd, rec, inc, ka, part); }
+  { Prof prof_("far_fwd_finish_kernel", s); far_fwd_finish_kernel<<<(unsigned)r, 256, 0, s>>>(part, kFwdChunks, inc, nd, ka, F); }
   MU_CHECK_LAUNCH("far_fwd");
   return MUELLER_OK;
 }
@@ -577,7 +596,7 @@ mueller_status far_field(mueller_mesh* m, const PhysConsts& P, int Q, const void
   gauss_legendre_unit(n_theta, gth, wth);
   const int64_t nsph = (int64_t)n_theta * n_phi;
   const int64_t nd = 1 + nsph + ndir;
-  const std::vector<double> hd = far_dirs(r, inc, n_theta, n_phi, gth, dirs, ndir);
+  const std::vector<double> hd = far_dirs(inc, n_theta, n_phi, gth, dirs, ndir);
   double phi[MAX_Q * 6];
   for (int p = 0; p < Q; ++p) {
     const double l0 = 1.0 - rule.xi[p] - rule.eta[p], l1 = rule.xi[p], l2 = rule.eta[p];
@@ -621,7 +640,7 @@ mueller_status far_field(mueller_mesh* m, const PhysConsts& P, int Q, const void
   if (!st) {
     { Prof prof_("currents_kernel", s); currents_kernel<<<dim3(nblk_pts, r), 256, 0, s>>>(m->nt, Q, m->qd64, m->T, (const double2*)X, r,
                                                        N, dphi, rec, cab); }
-    st = far_fwd(np, m->qd64, rec, ddirs, nd, r, P.ka, (double*)(buf + o_part), Fall, s);
+    st = far_fwd(np, m->qd64, rec, dinc, nd, r, P.ka, (double*)(buf + o_part), Fall, s);
     if (!st) st = far_shared(np, m->qd64, rec, r, ddirs, nd, n_theta, n_phi, ndir, P.ka, Fall, s);
     if (!st) {
       { Prof prof_("xs_kernel", s); xs_kernel<<<r, 256, 0, s>>>(Fall, nd, n_theta, n_phi, dwth, dinc, P.ka, cab, (int)nblk_pts, dxs); }
@@ -701,7 +720,7 @@ mueller_status far_field_noalloc(mueller_mesh* m, const PhysConsts& P, int Q, co
     return o;
   };
   const size_t o_rec = al((size_t)r * np * 6 * 16);
-  const size_t o_dirs = al((size_t)r * nd * 3 * 8);
+  const size_t o_dirs = al((size_t)nd * 3 * 8);
   const size_t o_F = al((size_t)r * nd * 3 * 16);
   const size_t o_wth = al(wth.size() * 8);
   const size_t o_inc = al((size_t)r * 6 * 8);
@@ -719,7 +738,7 @@ mueller_status far_field_noalloc(mueller_mesh* m, const PhysConsts& P, int Q, co
   char* buf = nullptr;
   mueller_status st = far_scratch_address((void**)&buf);
   if (st) return st;
-  const std::vector<double> hd = far_dirs(r, inc, n_theta, n_phi, gth, dirs, ndir);
+  const std::vector<double> hd = far_dirs(inc, n_theta, n_phi, gth, dirs, ndir);
   double phi[MAX_Q * 6];
   for (int p = 0; p < Q; ++p) {
     const double l0 = 1.0 - rule.xi[p] - rule.eta[p], l1 = rule.xi[p], l2 = rule.eta[p];
@@ -750,7 +769,7 @@ mueller_status far_field_noalloc(mueller_mesh* m, const PhysConsts& P, int Q, co
   if (e == cudaSuccess) e = cudaMemcpyAsync(dphi, phi, sizeof(double) * Q * 6, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return drain(cuda_fail(e, "far-field (allocation-free) setup"));
   { Prof prof_("currents_kernel", s); currents_kernel<<<dim3(nblk_pts, r), 256, 0, s>>>(m->nt, Q, m->qd64, m->T, (const double2*)X, r, N, dphi, rec, cab); }
-  st = far_fwd(np, m->qd64, rec, ddirs, nd, r, P.ka, (double*)(buf + o_part), Fall, s);
+  st = far_fwd(np, m->qd64, rec, dinc, nd, r, P.ka, (double*)(buf + o_part), Fall, s);
   if (st) return drain(st);
   st = far_shared(np, m->qd64, rec, r, ddirs, nd, n_theta, n_phi, ndir, P.ka, Fall, s);
   if (st) return drain(st);
