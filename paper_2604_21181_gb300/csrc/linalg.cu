@@ -454,32 +454,36 @@ __global__ void __launch_bounds__(256) lu_panel_kernel(CT* __restrict__ A, int64
 // afterwards, in the order they were chosen (the same matrix as swapping
 // whole rows at each step), unless 'defer' leaves them to lu_swap_trsm_kernel.
 // Pivot: first row maximising |Re| + |Im|.
+// barrier of the panel's nthr threads (a multiple of 32; id 9: the
+// tile groups of lu_step_kernel use 1 .. 8)
+__device__ __forceinline__ void panel_bar(int nthr) {
+  asm volatile("bar.sync 9, %0;" ::"r"(nthr) : "memory");
+}
+
 template <class CT, int W>
-__global__ void __launch_bounds__(1024) lu_panel_smem_kernel(CT* __restrict__ A, int64_t d,
-                                                             const int32_t* __restrict__ sz,
-                                                             int k0, int32_t* __restrict__ piv,
-                                                             int32_t* __restrict__ status,
-                                                             int defer) {
+__device__ __forceinline__ void lu_panel_smem_body(CT* __restrict__ A, int64_t d,
+                                                   const int32_t* __restrict__ sz, int k0,
+                                                   int32_t* __restrict__ piv,
+                                                   int32_t* __restrict__ status, int defer,
+                                                   int b, unsigned char* lu_smem, int nthr) {
   using RT = decltype(CT{}.x);
   constexpr int LD = W + 1;
-  extern __shared__ __align__(16) unsigned char lu_smem[];
   __shared__ RT wv[32];
   __shared__ int wi[32];
   __shared__ int sp[W];
   __shared__ CT srpv;
-  const int b = blockIdx.x;
   const int n = sz[b];
-  if (k0 >= n) return;
+  if (k0 >= n || (int)threadIdx.x >= nthr) return;
   const int w = min(W, n - k0);
   const int rows = n - k0;
   const int t = threadIdx.x;
   CT* P = (CT*)lu_smem;  // [rows][LD]
   CT* M = A + (int64_t)b * d * d;
-  for (int e = t; e < rows * w; e += blockDim.x) {
+  for (int e = t; e < rows * w; e += nthr) {
     const int i = e / w, j = e - i * w;
     P[i * LD + j] = M[(int64_t)(k0 + i) * d + k0 + j];
   }
-  __syncthreads();
+  panel_bar(nthr);
   for (int k = 0; k < w; ++k) {
     RT v = -1;
     int vi = rows;
@@ -500,9 +504,9 @@ __global__ void __launch_bounds__(1024) lu_panel_smem_kernel(CT* __restrict__ A,
       wv[t >> 5] = v;
       wi[t >> 5] = vi;
     }
-    __syncthreads();
+    panel_bar(nthr);
     if (t < 32) {
-      const int nw = (int)(blockDim.x >> 5);
+      const int nw = (nthr >> 5);
       v = t < nw ? wv[t] : (RT)-1;
       vi = t < nw ? wi[t] : rows;
 #pragma unroll
@@ -528,14 +532,14 @@ __global__ void __launch_bounds__(1024) lu_panel_smem_kernel(CT* __restrict__ A,
         piv[(int64_t)b * d + k0 + k] = k0 + vi;
       }
     }
-    __syncthreads();
+    panel_bar(nthr);
     const int p = sp[k];
     if (p != k && t < w) {
       const CT x = P[k * LD + t];
       P[k * LD + t] = P[p * LD + t];
       P[p * LD + t] = x;
     }
-    __syncthreads();
+    panel_bar(nthr);
     const CT rpv = srpv;  // multipliers by the pivot's reciprocal
     if (t > k && t < rows) {
       CT* row = P + t * LD;
@@ -549,14 +553,14 @@ __global__ void __launch_bounds__(1024) lu_panel_smem_kernel(CT* __restrict__ A,
         row[j].y -= l.x * u.y + l.y * u.x;
       }
     }
-    __syncthreads();
+    panel_bar(nthr);
   }
-  for (int e = t; e < rows * w; e += blockDim.x) {
+  for (int e = t; e < rows * w; e += nthr) {
     const int i = e / w, j = e - i * w;
     M[(int64_t)(k0 + i) * d + k0 + j] = P[i * LD + j];
   }
   if (defer) return;
-  for (int c = t; c < n; c += blockDim.x) {
+  for (int c = t; c < n; c += nthr) {
     if (c >= k0 && c < k0 + w) continue;
     for (int k = 0; k < w; ++k) {
       const int p = sp[k];
@@ -566,6 +570,123 @@ __global__ void __launch_bounds__(1024) lu_panel_smem_kernel(CT* __restrict__ A,
         M[(int64_t)(k0 + p) * d + c] = x;
       }
     }
+  }
+}
+
+template <class CT, int W>
+__global__ void __launch_bounds__(1024) lu_panel_smem_kernel(CT* __restrict__ A, int64_t d,
+                                                             const int32_t* __restrict__ sz,
+                                                             int k0, int32_t* __restrict__ piv,
+                                                             int32_t* __restrict__ status,
+                                                             int defer) {
+  extern __shared__ __align__(16) unsigned char lu_smem[];
+  lu_panel_smem_body<CT, W>(A, d, sz, k0, piv, status, defer, blockIdx.x, lu_smem, blockDim.x);
+}
+
+// One step of the blocked LU in one launch.  The dynamic shared memory
+// (kLuStepSmem) admits one CTA per SM, so no two CTAs share an SM's FP64
+// pipe.  CTAs 0 .. nb-1 first factor panel k1 of their block (rows in shared
+// memory, swaps held back); then each group of 64 threads of every CTA takes
+// 32 x 32 tiles of the trailing update of panel k0 over columns [c0, d) one
+// at a time from a queue (an atomic counter) and synchronises with a barrier
+// of its own, so the tiles spread over all SMs whether there are many or
+// few.  The panel's columns [k1, k1 + W) were updated before this launch and
+// lie outside [c0, d), so the two roles touch disjoint entries and never
+// wait on each other.  Without a panel (k1 < 0) every CTA only takes tiles.
+constexpr int kLuStepThreads = 512;
+constexpr size_t kLuStepSmem = 140 * 1024;
+__device__ __forceinline__ void group_bar(int id) {
+  asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory");
+}
+template <int W>
+__global__ void __launch_bounds__(kLuStepThreads) lu_step_kernel(
+    double2* __restrict__ A, int64_t d, const int32_t* __restrict__ sz, int k0, int k1,
+    int64_t c0, int nb, int32_t* __restrict__ piv, int32_t* __restrict__ status,
+    unsigned* __restrict__ queue) {
+  extern __shared__ __align__(16) unsigned char lu_smem[];
+  if (k1 >= 0 && (int)blockIdx.x < nb) {
+    // one thread per panel row (whole warps): fewer threads in the column
+    // reductions of the short late panels
+    const int rows = (int)(d - k1);
+    const int nthr = max(32, min((int)blockDim.x, (rows + 31) / 32 * 32));
+    lu_panel_smem_body<double2, W>(A, d, sz, k1, piv, status, 1, blockIdx.x, lu_smem, nthr);
+    __syncthreads();  // the shared memory is the tiles' from here on
+  }
+  constexpr int TN = 32, JN = TN / 8;
+  const int64_t r0 = k0 + W;
+  const int64_t rt_n = (d - r0 + 31) / 32, ct_n = (d - c0 + TN - 1) / TN;
+  const int64_t per_b = rt_n * ct_n;
+  const unsigned tiles = (unsigned)((int64_t)nb * per_b);
+  if (rt_n <= 0 || ct_n <= 0) return;
+  const int grp = threadIdx.x >> 6, lt = threadIdx.x & 63;
+  const int ty = lt / 8, tx = lt % 8;
+  typedef double2 RowA[W + 1];
+  typedef double2 RowB[TN + 1];
+  RowA* sA = reinterpret_cast<RowA*>(lu_smem + (size_t)grp * (32 * (W + 1) + W * (TN + 1)) * sizeof(double2));
+  RowB* sB = reinterpret_cast<RowB*>(reinterpret_cast<double2*>(sA) + 32 * (W + 1));
+  __shared__ unsigned tb[kLuStepThreads / 64];
+  const int bar = 1 + grp;  // barrier 0 is __syncthreads'
+  for (;;) {
+    if (lt == 0) tb[grp] = atomicAdd(queue, 1u);
+    group_bar(bar);
+    const unsigned tile = tb[grp];
+    if (tile >= tiles) break;  // uniform over the group
+    const int b = (int)(tile / per_b);
+    const int64_t rem = (int64_t)tile - (int64_t)b * per_b;
+    const int n = sz[b];
+    const int64_t c1 = mn64(d, n);
+    const int64_t tr = r0 + (rem / ct_n) * 32, tc = c0 + (rem % ct_n) * TN;
+    const bool act = !(k0 >= n || tr >= n || tc >= c1);
+    const int w = act ? min(W, n - k0) : 0;
+    double2* M = A + (int64_t)b * d * d;
+    if (act) {
+      for (int t = lt; t < 32 * W; t += 64) {
+        const int i = t / W, k = t % W;
+        const int64_t gr = tr + i;
+        sA[i][k] = (gr < n && k < w) ? M[gr * d + k0 + k] : make_double2(0.0, 0.0);
+      }
+      for (int t = lt; t < W * TN; t += 64) {
+        const int k = t / TN, j = t % TN;
+        const int64_t gc = tc + j;
+        sB[k][j] = (gc < c1 && k < w) ? M[(int64_t)(k0 + k) * d + gc] : make_double2(0.0, 0.0);
+      }
+    }
+    group_bar(bar);
+    if (act) {
+      double2 acc[4][JN];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < JN; ++j) acc[i][j] = make_double2(0.0, 0.0);
+#pragma unroll 4
+      for (int k = 0; k < W; ++k) {
+        double2 av[4], bv[JN];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) av[i] = sA[ty + 8 * i][k];
+#pragma unroll
+        for (int j = 0; j < JN; ++j) bv[j] = sB[k][tx + 8 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < JN; ++j) {
+            acc[i][j].x = fma(av[i].x, bv[j].x, fma(-av[i].y, bv[j].y, acc[i][j].x));
+            acc[i][j].y = fma(av[i].x, bv[j].y, fma(av[i].y, bv[j].x, acc[i][j].y));
+          }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < JN; ++j) {
+          const int64_t gr = tr + ty + 8 * i, gc = tc + tx + 8 * j;
+          if (gr < n && gc < c1) {
+            double2 v = M[gr * d + gc];
+            v.x -= acc[i][j].x;
+            v.y -= acc[i][j].y;
+            M[gr * d + gc] = v;
+          }
+        }
+    }
+    group_bar(bar);  // before the group's next tile loads and queue read
   }
 }
 
@@ -1968,10 +2089,9 @@ static mueller_status lu_update(double2* A, int64_t d, int nb, const int32_t* sz
 // In-place FP64 LU with partial pivoting of nb blocks of size d (active
 // sizes sz_dev), right-looking in panels of LUW columns with a look-ahead of
 // one panel.  Per panel k0: its row swaps reach the other columns and the
-// row panel of U is solved (one kernel); then the side stream updates the
-// columns of panel k0+LUW and factors it (its swaps held back) while the
-// caller's stream updates the remaining columns, so that the panel starts
-// on the SMs the bulk update's last wave leaves free.
+// row panel of U is solved (one kernel); the columns of panel k0+LUW are
+// updated; then the side stream factors that panel (its swaps held back)
+// while the caller's stream updates the remaining columns.
 // Then, if inv, the inverses in 'inv' (d x d per block).
 template <class CT>
 static mueller_status batched_lu_inverse(CT* A, int64_t d, int nb, const int32_t* sz_dev,
@@ -1980,19 +2100,55 @@ static mueller_status batched_lu_inverse(CT* A, int64_t d, int nb, const int32_t
   static_assert(sizeof(CT) == 16, "the block LU is FP64");
   cudaStream_t s2 = nullptr;
   mueller_status st = side_stream(&s2);
+  // one tile-queue counter per panel step
+  const int nsteps = (int)((d + LUW - 1) / LUW);
+  unsigned* queue = nullptr;
+  if (!st) {
+    cudaError_t e = cudaMallocAsync((void**)&queue, (size_t)nsteps * sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(queue, 0, (size_t)nsteps * sizeof(unsigned), s);
+    if (e != cudaSuccess) st = cuda_fail(e, "LU tile queues");
+  }
+  int nsm = 0, dev = 0;
+  if (!st && (cudaGetDevice(&dev) != cudaSuccess ||
+              cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess))
+    nsm = 148;
+  if (!st) {
+    cudaError_t e = cudaFuncSetAttribute(lu_step_kernel<LUW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kLuStepSmem);
+    if (e != cudaSuccess) st = cuda_fail(e, "LU step kernel attributes");
+  }
   if (!st) st = lu_panel(A, d, nb, sz_dev, 0, piv, status, 1, s);
-  for (int k0 = 0; !st && k0 < d; k0 += LUW) {
+  for (int k0 = 0, step = 0; !st && k0 < d; k0 += LUW, ++step) {
     { Prof prof_("lu_swap_trsm_kernel", s); lu_swap_trsm_kernel<LUW><<<dim3(nblk(d, 128), nb), 128, 0, s>>>(A, d, sz_dev, k0, piv); }
     MU_CHECK_LAUNCH("lu_swap_trsm_kernel");
     const int k1 = k0 + LUW;
     if (k1 >= d) break;
+    // the next panel's columns first, alone on the GPU: FP64-bound CTAs that
+    // share an SM slow down together, so next to the bulk update this small
+    // update would last as long as the bulk update and hold the panel back
+    st = lu_update<LUW>(A, d, nb, sz_dev, k0, k1, k1 + LUW, s);
+    if (st) break;
+    if (d - k1 <= kLuStepThreads) {
+      // panel k1 and the rest of update k0 in one launch, on separate SMs
+      const int64_t c0 = k1 + LUW;
+      const unsigned grid = (unsigned)std::max(nsm, nb);
+      {
+        Prof prof_("lu_step_kernel", s);
+        lu_step_kernel<LUW><<<grid, kLuStepThreads, kLuStepSmem, s>>>(A, d, sz_dev, k0, k1, c0, nb,
+                                                                      piv, status, queue + step);
+      }
+      MU_CHECK_LAUNCH("lu_step_kernel");
+      continue;
+    }
+    // panels too tall for one CTA's threads: the panel on the side stream
+    // while the caller's stream updates the remaining columns
     st = stream_order(s, s2);
-    if (!st) st = lu_update<LUW>(A, d, nb, sz_dev, k0, k1, k1 + LUW, s2);
     if (!st) st = lu_panel(A, d, nb, sz_dev, k1, piv, status, 1, s2);
-    const mueller_status su = lu_update<32>(A, d, nb, sz_dev, k0, k1 + LUW, -1, s);
+    const mueller_status su = st ? st : lu_update<32>(A, d, nb, sz_dev, k0, k1 + LUW, -1, s);
     const mueller_status sj = stream_order(s2, s);
     if (!st) st = su ? su : sj;
   }
+  if (queue) cudaFreeAsync(queue, s);
   if (st || !inv) return st;
   return block_inverse<CT>(A, d, nb, sz_dev, piv, inv, s);
 }
