@@ -72,9 +72,11 @@ def parse(argv=None):
     # one untimed invocation of part of the path on a sphere, for profiler
     # captures (ncu -k <kernel> ... python bench.py --profile-case assemble)
     ap.add_argument("--profile-case", default=None,
-                    choices=["assemble", "assemble64", "precond", "solve", "mrhs"])
+                    choices=["assemble", "assemble64", "precond", "solve", "mrhs", "farfield",
+                             "shapegrad"])
     ap.add_argument("--level", type=int, default=2, help="--profile-case: icosphere level")
-    ap.add_argument("--rhs", type=int, default=16, help="--profile-case mrhs: right-hand sides")
+    ap.add_argument("--rhs", type=int, default=16,
+                    help="--profile-case mrhs, farfield: right-hand sides")
     ap.add_argument("--block", type=int, default=256, help="--profile-case: cluster size B")
     return ap.parse_args(argv)
 
@@ -798,23 +800,42 @@ def profile_case(args):
       precond     mixed assembly + block-Jacobi build (FP64 LU, FP32 inverse)
       solve       mixed assembly + block-Jacobi + one GMRES-IR solve
       mrhs        mixed assembly + one tensor-core product of --rhs vectors
+      farfield    mixed assembly + block-Jacobi + GMRES-IR solve of --rhs
+                  Fibonacci incidences + their far fields (48 x 96 sphere rule)
+      shapegrad   the level-L spheroid of axis ratio 1.5 (eps_r = 3 + 0.2i,
+                  k_a = 3): FP64 forward state and one reverse-mode product
+                  of the node-coordinate gradient (adjoint solve, VJP kernels)
     """
     import torch
 
     import paper_2604_21181_gb300 as mu
 
+    if args.profile_case == "shapegrad":
+        xyz, tri6 = workloads.spheroid_p2(args.level, 1.0, 1.5)
+        p = mu.Params(ka=3.0, eps_r=(3.0, 0.2), q_regular=6, ssq_order=5, frame_rule=0)
+        mesh = mu.Mesh(xyz, tri6)
+        mesh.tangent_frame(0, out=False)
+        _, state = mu.grad.forward_state(mesh, p, workloads.plane_wave())
+        mu.grad.vjp(state, np.ones(3), material=False)
+        torch.cuda.synchronize()
+        print("ok", args.profile_case, "level", args.level, "N", mesh.N)
+        return
     xyz, tri6 = workloads.icosphere_p2(args.level)
     p = mu.Params(ka=5.0, eps_r=(2.25, 0.0), q_regular=6, ssq_order=5)
     mesh = mu.Mesh(xyz, tri6)
     mesh.tangent_frame(p.frame_rule, out=False)
     inc = workloads.plane_wave()
+    if args.profile_case == "farfield":
+        inc = workloads.fibonacci_plane_waves((args.rhs + 1) // 2)[:args.rhs]
     dtype = mu.MUELLER_C128 if args.profile_case == "assemble64" else mu.MUELLER_C64_NEAR64
     Z, near, B = mu.assemble(mesh, p, dtype, inc=inc)
     op = mu.Operator(mesh, Z, near, dtype)
-    if args.profile_case in ("precond", "solve"):
+    if args.profile_case in ("precond", "solve", "farfield"):
         mu.precond_build(op, args.block)
-    if args.profile_case == "solve":
-        mu.solve(op, B, mu.SolverOpts(mode=mu.SOLVE_GMRES_IR, restart=50, tol=1e-8))
+    if args.profile_case in ("solve", "farfield"):
+        X, _ = mu.solve(op, B, mu.SolverOpts(mode=mu.SOLVE_GMRES_IR, restart=50, tol=1e-8))
+    if args.profile_case == "farfield":
+        mu.far_field(mesh, p, X, inc)
     if args.profile_case == "mrhs":
         g = torch.Generator().manual_seed(1)
         X = torch.randn((args.rhs, mesh.N), dtype=torch.complex64, generator=g).cuda()
