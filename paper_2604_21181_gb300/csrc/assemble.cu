@@ -39,6 +39,7 @@ static int g_uploaded_dev = -1;
 mueller_status upload_rules(const TriangleRule& rule, int ns) {
   int dev = 0;
   MU_CUDA(cudaGetDevice(&dev));
+  MU_CUDA(cis64_table_ready());  // the radial functions' exp(i theta) table
   if (rule.q == g_uploaded_q && ns == g_uploaded_ns && dev == g_uploaded_dev) return MUELLER_OK;
   double phi[MAX_Q * 6];
   float phif[MAX_Q * 6];

@@ -1106,6 +1106,7 @@ static mueller_status shape_finish(mueller_mesh* m, const RuleC& rc, ShapeWork& 
 
 mueller_status zshape_vjp(mueller_mesh* m, const PhysConsts& P, int Q, int ns, const void* lam,
                           const void* x, double* grad, cudaStream_t s) {
+  MU_CUDA(cis64_table_ready());  // the radial functions' exp(i theta) table
   TriangleRule rule;
   if (!triangle_rule(Q, rule)) {
     set_error("q_regular must be 6 or 12");
