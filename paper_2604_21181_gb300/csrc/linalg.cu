@@ -588,9 +588,9 @@ __global__ void __launch_bounds__(1024) lu_panel_smem_kernel(CT* __restrict__ A,
 // pipe.  CTAs 0 .. nb-1 first factor panel k1 of their block (rows in shared
 // memory, swaps held back); then each group of 64 threads of every CTA takes
 // 32 x 32 tiles of the trailing update of panel k0 over columns [c0, d) one
-// at a time from a queue (an atomic counter) and synchronises with a barrier
-// of its own, so the tiles spread over all SMs whether there are many or
-// few.  The panel's columns [k1, k1 + W) were updated before this launch and
+// at a time (the first one assigned so that the tiles spread over the SMs,
+// the others from a queue, an atomic counter) and synchronises with a
+// barrier of its own.  The panel's columns [k1, k1 + W) were updated before this launch and
 // lie outside [c0, d), so the two roles touch disjoint entries and never
 // wait on each other.  Without a panel (k1 < 0) every CTA only takes tiles.
 constexpr int kLuStepThreads = 512;
@@ -626,8 +626,18 @@ __global__ void __launch_bounds__(kLuStepThreads) lu_step_kernel(
   RowB* sB = reinterpret_cast<RowB*>(reinterpret_cast<double2*>(sA) + 32 * (W + 1));
   __shared__ unsigned tb[kLuStepThreads / 64];
   const int bar = 1 + grp;  // barrier 0 is __syncthreads'
+  // The first tile of each group of the CTAs without a panel is assigned
+  // statically, tile g * (G - np) + (c - np) to group g of CTA c, so that few
+  // tiles spread over the SMs instead of filling the first SMs to ask; the
+  // rest come from the queue (tickets after the static ones).
+  const unsigned npan = k1 >= 0 ? (unsigned)min(nb, (int)gridDim.x) : 0u;
+  const unsigned nfree = gridDim.x - npan;
+  const unsigned nstatic = nfree * (kLuStepThreads / 64);
+  bool stat = blockIdx.x >= npan;
   for (;;) {
-    if (lt == 0) tb[grp] = atomicAdd(queue, 1u);
+    if (lt == 0) tb[grp] = stat ? (unsigned)grp * nfree + (blockIdx.x - npan)
+                                : nstatic + atomicAdd(queue, 1u);
+    stat = false;
     group_bar(bar);
     const unsigned tile = tb[grp];
     if (tile >= tiles) break;  // uniform over the group
