@@ -137,7 +137,7 @@ class ClockSampler:
 # DRAM bytes (read + written) per touching pair of the touching kernel's
 # launches, from its ncu capture on the level-2 sphere (4100 touching pairs);
 # None while the kernel has changed since that capture.
-TOUCH_DRAM_PER_PAIR = 58.578e6 / 4100
+TOUCH_DRAM_PER_PAIR = 59.044e6 / 4100
 
 
 def touching_points(n_tri: int, n_touch: int, ns: int) -> float:
