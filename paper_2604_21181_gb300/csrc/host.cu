@@ -15,6 +15,7 @@
 #include <mutex>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -339,31 +340,53 @@ mueller_status mueller_mesh_load(const double* xyz, int64_t nn, const int32_t* t
     for (int64_t e = 0; e < nt; ++e)
       for (int k = 0; k < 6; ++k) n2e[fill[T[6 * e + k]]++] = (int32_t)((e << 3) | k);
   }
+  // host threads for the table passes below: each takes a contiguous range
+  // of elements or rows, and the tables do not depend on the thread count
+  const int64_t nthreads = std::max<int64_t>(
+      1, std::min<int64_t>({(int64_t)std::thread::hardware_concurrency(), 16, nn / 256}));
+  auto run = [&](auto&& fn) {
+    if (nthreads == 1) {
+      fn((int64_t)0);
+      return;
+    }
+    std::vector<std::thread> pool;
+    pool.reserve(nthreads);
+    for (int64_t t = 0; t < nthreads; ++t) pool.emplace_back(fn, t);
+    for (std::thread& th : pool) th.join();
+  };
   // ---- touching pairs (sorted by ex, then ey)
   std::vector<TouchPair> tp;
   {
-    std::vector<int32_t> cand;
-    std::vector<int32_t> seen(nt, -1);
-    std::vector<uint64_t> bits((nt + 63) / 64 + 1, 0);
-    for (int64_t ex = 0; ex < nt; ++ex) {
-      cand.clear();
-      for (int k = 0; k < 3; ++k) {
-        int32_t v = T[6 * ex + k];
-        for (int32_t q = ptr[v]; q < ptr[v + 1]; ++q) {
-          const int32_t ey = n2e[q] >> 3;
-          if (seen[ey] != (int32_t)ex) {
-            seen[ey] = (int32_t)ex;
-            cand.push_back(ey);
+    std::vector<std::vector<TouchPair>> part(nthreads);
+    run([&](int64_t t) {
+      const int64_t e0 = nt * t / nthreads, e1 = nt * (t + 1) / nthreads;
+      std::vector<int32_t> cand;
+      std::vector<int32_t> seen(nt, -1);
+      std::vector<uint64_t> bits((nt + 63) / 64 + 1, 0);
+      for (int64_t ex = e0; ex < e1; ++ex) {
+        cand.clear();
+        for (int k = 0; k < 3; ++k) {
+          int32_t v = T[6 * ex + k];
+          for (int32_t q = ptr[v]; q < ptr[v + 1]; ++q) {
+            const int32_t ey = n2e[q] >> 3;
+            if (seen[ey] != (int32_t)ex) {
+              seen[ey] = (int32_t)ex;
+              cand.push_back(ey);
+            }
           }
         }
+        sort_ids(cand.data(), cand.size(), bits.data());
+        for (int32_t ey : cand) {
+          int32_t packed;
+          int cls = classify_pair(T + 6 * ex, T + 6 * ey, packed);
+          if (cls > 0) part[t].push_back({(int32_t)ex, ey, cls, packed});
+        }
       }
-      sort_ids(cand.data(), cand.size(), bits.data());
-      for (int32_t ey : cand) {
-        int32_t packed;
-        int cls = classify_pair(T + 6 * ex, T + 6 * ey, packed);
-        if (cls > 0) tp.push_back({(int32_t)ex, ey, cls, packed});
-      }
-    }
+    });
+    size_t total = 0;
+    for (const auto& v : part) total += v.size();
+    tp.reserve(total);
+    for (const auto& v : part) tp.insert(tp.end(), v.begin(), v.end());
   }
   m->n_touch = (int64_t)tp.size();
   // launch order of the touching kernel: coincident and common-edge pairs,
@@ -378,52 +401,71 @@ mueller_status mueller_mesh_load(const double* xyz, int64_t nn, const int32_t* t
   // ---- near-part block layout: node pairs of the touching element pairs.
   // Row by row: the columns of test node ni are the nodes of every trial
   // element touching an element that holds ni (deduplicated with a stamp
-  // array, without branches, then sorted), and the slot of (pair, i, j) is
-  // found through a column -> position array valid for the current row.
+  // array, then sorted), and the slot of (pair, i, j) is found through a
+  // column -> position array valid for the current row.
   std::vector<int64_t> pfirst(nt + 1, 0);  // tp is sorted by ex
   for (const TouchPair& q : tp) pfirst[q.ex + 1]++;
   for (int64_t e = 0; e < nt; ++e) pfirst[e + 1] += pfirst[e];
   std::vector<int32_t> slot((size_t)m->n_touch * 36);
   {
-    std::vector<int32_t> stamp(nn, -1), pos(nn, 0);
-    std::vector<uint64_t> bits((nn + 63) / 64 + 1, 0);
-    int64_t row_max = 0;  // candidate columns of the longest row
-    for (int64_t ni = 0; ni < nn; ++ni) {
-      int64_t c = 0;
-      for (int32_t q = ptr[ni]; q < ptr[ni + 1]; ++q) {
-        const int64_t ex = n2e[q] >> 3;
-        c += 6 * (pfirst[ex + 1] - pfirst[ex]);
+    // Rows are independent: phase 1 finds each row's sorted columns, phase 2
+    // (after the prefix sum of the row lengths) places them and fills the
+    // slots of the row's (pair, i) entries, which no other row writes.
+    std::vector<std::vector<int32_t>> cols(nthreads);
+    std::vector<int32_t> len_of(nn, 0);
+    auto range = [&](int64_t t, int64_t& r0, int64_t& r1) {
+      r0 = nn * t / nthreads;
+      r1 = nn * (t + 1) / nthreads;
+    };
+    auto phase1 = [&](int64_t t) {
+      int64_t r0, r1;
+      range(t, r0, r1);
+      std::vector<int32_t> stamp(nn, -1), row;
+      std::vector<uint64_t> bits((nn + 63) / 64 + 1, 0);
+      std::vector<int32_t>& out = cols[t];
+      for (int64_t ni = r0; ni < r1; ++ni) {
+        row.clear();
+        for (int32_t q = ptr[ni]; q < ptr[ni + 1]; ++q) {
+          const int64_t ex = n2e[q] >> 3;
+          for (int64_t p = pfirst[ex]; p < pfirst[ex + 1]; ++p)
+            for (int j = 0; j < 6; ++j) {
+              const int32_t nj = T[6 * tp[p].ey + j];
+              if (stamp[nj] != (int32_t)ni) {
+                stamp[nj] = (int32_t)ni;
+                row.push_back(nj);
+              }
+            }
+        }
+        sort_ids(row.data(), row.size(), bits.data());
+        out.insert(out.end(), row.begin(), row.end());
+        len_of[ni] = (int32_t)row.size();
       }
-      row_max = std::max(row_max, c);
-    }
-    std::vector<int32_t> row((size_t)row_max + 1);
+    };
+    run(phase1);
     m->near_rowptr_h.assign(nn + 1, 0);
-    m->near_col_h.clear();
-    m->near_col_h.reserve((size_t)nn * 64);
-    for (int64_t ni = 0; ni < nn; ++ni) {
-      const size_t start = m->near_col_h.size();
-      size_t len = 0;
-      for (int32_t q = ptr[ni]; q < ptr[ni + 1]; ++q) {
-        const int64_t ex = n2e[q] >> 3;
-        for (int64_t p = pfirst[ex]; p < pfirst[ex + 1]; ++p)
-          for (int j = 0; j < 6; ++j) {
-            const int32_t nj = T[6 * tp[p].ey + j];
-            row[len] = nj;
-            len += stamp[nj] != (int32_t)ni;
-            stamp[nj] = (int32_t)ni;
-          }
+    for (int64_t ni = 0; ni < nn; ++ni) m->near_rowptr_h[ni + 1] = m->near_rowptr_h[ni] + len_of[ni];
+    m->near_col_h.assign((size_t)m->near_rowptr_h[nn], 0);
+    auto phase2 = [&](int64_t t) {
+      int64_t r0, r1;
+      range(t, r0, r1);
+      std::vector<int32_t> pos(nn, 0);
+      const int32_t* src = cols[t].data();
+      for (int64_t ni = r0; ni < r1; ++ni) {
+        const int32_t start = m->near_rowptr_h[ni], len = len_of[ni];
+        for (int32_t k = 0; k < len; ++k) {
+          m->near_col_h[(size_t)start + k] = src[k];
+          pos[src[k]] = start + k;
+        }
+        src += len;
+        for (int32_t q = ptr[ni]; q < ptr[ni + 1]; ++q) {
+          const int64_t ex = n2e[q] >> 3;
+          const int i = n2e[q] & 7;
+          for (int64_t p = pfirst[ex]; p < pfirst[ex + 1]; ++p)
+            for (int j = 0; j < 6; ++j) slot[(size_t)p * 36 + i * 6 + j] = pos[T[6 * tp[p].ey + j]];
+        }
       }
-      sort_ids(row.data(), len, bits.data());
-      m->near_col_h.insert(m->near_col_h.end(), row.begin(), row.begin() + len);
-      m->near_rowptr_h[ni + 1] = (int32_t)m->near_col_h.size();
-      for (size_t k = start; k < m->near_col_h.size(); ++k) pos[m->near_col_h[k]] = (int32_t)k;
-      for (int32_t q = ptr[ni]; q < ptr[ni + 1]; ++q) {
-        const int64_t ex = n2e[q] >> 3;
-        const int i = n2e[q] & 7;
-        for (int64_t p = pfirst[ex]; p < pfirst[ex + 1]; ++p)
-          for (int j = 0; j < 6; ++j) slot[(size_t)p * 36 + i * 6 + j] = pos[T[6 * tp[p].ey + j]];
-      }
-    }
+    };
+    run(phase2);
     m->nnzb = m->near_rowptr_h[nn];
   }
   if (flags & MUELLER_MESH_HOST_ONLY) {
