@@ -142,17 +142,32 @@ static mueller_status validate(const double* xyz, int64_t nn, const int32_t* T, 
     int64_t tri;
     int32_t from, mid;
   };
-  std::vector<Use> uses;
-  uses.reserve((size_t)3 * nt);
+  // ordered by (lo, hi, tri): a counting sort on lo (the uses of one lo come
+  // in increasing tri), then an insertion sort on hi inside each short bucket
   const int emid[3] = {3, 4, 5};
+  std::vector<int64_t> first(nn + 1, 0);
   for (int64_t e = 0; e < nt; ++e)
-    for (int k = 0; k < 3; ++k) {
-      int32_t a = T[6 * e + k], b = T[6 * e + (k + 1) % 3];
-      uses.push_back({std::min(a, b), std::max(a, b), e, a, T[6 * e + emid[k]]});
+    for (int k = 0; k < 3; ++k) first[std::min(T[6 * e + k], T[6 * e + (k + 1) % 3]) + 1]++;
+  for (int64_t i = 0; i < nn; ++i) first[i + 1] += first[i];
+  std::vector<Use> uses((size_t)3 * nt);
+  {
+    std::vector<int64_t> fill(first.begin(), first.end() - 1);
+    for (int64_t e = 0; e < nt; ++e)
+      for (int k = 0; k < 3; ++k) {
+        const int32_t a = T[6 * e + k], b = T[6 * e + (k + 1) % 3];
+        uses[fill[std::min(a, b)]++] = {std::min(a, b), std::max(a, b), e, a, T[6 * e + emid[k]]};
+      }
+  }
+  for (int64_t i = 0; i < nn; ++i)
+    for (int64_t k = first[i] + 1; k < first[i + 1]; ++k) {
+      const Use x = uses[k];
+      int64_t j = k;
+      while (j > first[i] && (uses[j - 1].hi > x.hi || (uses[j - 1].hi == x.hi && uses[j - 1].tri > x.tri))) {
+        uses[j] = uses[j - 1];
+        --j;
+      }
+      uses[j] = x;
     }
-  std::sort(uses.begin(), uses.end(), [](const Use& x, const Use& y) {
-    return x.lo != y.lo ? x.lo < y.lo : (x.hi != y.hi ? x.hi < y.hi : x.tri < y.tri);
-  });
   for (size_t k = 0; k < uses.size();) {
     size_t l = k;
     while (l < uses.size() && uses[l].lo == uses[k].lo && uses[l].hi == uses[k].hi) ++l;
