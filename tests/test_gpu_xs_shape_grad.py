@@ -12,7 +12,8 @@ method), term by term and whole:
   x against central differences of far_field on displaced meshes;
 * grad.shape_gradient against the oracle's gradient (central differences of
   its own dense pipeline) on the level-1 spheroid, at sampled nodes away from
-  the frame rule's switch, for the paper's and the polar frame rule;
+  the frame rule's switch, for the paper's and the polar frame rule, and a
+  magnetic lossy scatterer (mu_r = 1.4 + 0.1i);
 * on the level-3 spheroid of axis ratio 1.5 (eps_r = 3 + 0.2i, k_a = 3,
   the paper's frame rule): adjoint_gradients against central differences
   with step 1e-6 of full FP64 solves at displaced nodes (measured within
@@ -174,16 +175,20 @@ def test_partials_geometry_derivative_at_fixed_currents(partials_case):
             assert np.abs(an - fd).max() <= 1e-6 * np.abs(c["gfix"]).max(), (k, d, an, fd)
 
 
-@pytest.mark.parametrize("rule", [0, 1])
-def test_shape_gradient_matches_oracle(rule):
+MAGNETIC = dict(ka=1.5, eps_r=(2.5, 0.3), mu_r=(1.4, 0.1))
+
+
+@pytest.mark.parametrize("rule,phys", [(0, PHYS), (1, PHYS), (1, MAGNETIC)],
+                         ids=["paper_rule", "polar_rule", "polar_rule_magnetic_lossy"])
+def test_shape_gradient_matches_oracle(rule, phys):
     xyz, tri6 = workloads.spheroid_p2(1, 1.0, 1.5)
-    p = _params(rule)
+    p = _params(rule, phys)
     m = mu.Mesh(xyz, tri6)
     m.tangent_frame(rule, out=False)
     xs, state = mu.grad.forward_state(m, p, INC)
     grad = mu.grad.shape_gradient(state)
     assert grad.shape == (3, len(xyz), 3) and np.all(np.isfinite(grad))
-    pw = dict(PHYS, q_regular=6, ssq_order=4)
+    pw = dict(phys, q_regular=6, ssq_order=4)
     nodes = _sample_nodes(xyz, tri6, rule, 5, seed=rule + 20)
     Go = oracle.cross_section_coordinate_gradient(xyz, tri6, pw, INC, nodes=nodes,
                                                   frame_rule=rule)  # (k, 3 coords, 3 outputs)
