@@ -590,9 +590,10 @@ __global__ void __launch_bounds__(1024) lu_panel_smem_kernel(CT* __restrict__ A,
 // 32 x 32 tiles of the trailing update of panel k0 over columns [c0, d) one
 // at a time (the first one assigned so that the tiles spread over the SMs,
 // the others from a queue, an atomic counter) and synchronises with a
-// barrier of its own.  The panel's columns [k1, k1 + W) were updated before this launch and
-// lie outside [c0, d), so the two roles touch disjoint entries and never
-// wait on each other.  Without a panel (k1 < 0) every CTA only takes tiles.
+// barrier of its own.  The panel's columns [k1, k1 + W) were updated before
+// this launch and lie outside [c0, d), so the two roles touch disjoint
+// entries and never wait on each other.  Without a panel (k1 < 0) every CTA
+// only takes tiles.
 constexpr int kLuStepThreads = 512;
 constexpr size_t kLuStepSmem = 140 * 1024;
 __device__ __forceinline__ void group_bar(int id) {
