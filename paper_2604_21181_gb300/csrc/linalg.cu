@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <vector>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -209,6 +210,94 @@ __global__ void __launch_bounds__(256) gemv_c64_kernel(int64_t N, const float4* 
       reinterpret_cast<double2*>(yv_)[s * ys + row0 + lane] = make_double2(vr, vi);
   }
 }
+
+// Y = Z X for r complex128 vectors with the stored complex64 Z widened to
+// FP64 (the refinement residual of several right-hand sides).  Each warp
+// owns 2 rows and RS vectors (blockIdx.y: vectors RS*y ..), so every Z
+// entry is read and widened once for RS vectors, and the complex products
+// take the 3M form: with s_z = z.x + z.y and s_x = x.x + x.y (XS, formed
+// once per vector entry by xsum_kernel)
+//   Re(z x) = z.x x.x - z.y x.y,   Im(z x) = s_z s_x - z.x x.x - z.y x.y,
+// three FP64 multiply-adds per entry and vector instead of four (the FP64
+// pipe bounds this product).  Its rounding error is bounded like that of
+// the usual form up to a small constant (normwise; Higham, Accuracy and
+// Stability of Numerical Algorithms, Sec. 23.2.4).
+template <int RS>
+__global__ void __launch_bounds__(64) gemv_c64_f64_3m_kernel(int64_t N,
+                                                             const float4* __restrict__ Z4,
+                                                             int64_t ldz,
+                                                             const double2* __restrict__ X,
+                                                             const double* __restrict__ XS,
+                                                             double2* __restrict__ Y, int r) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t row0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * 2;
+  const int s0 = blockIdx.y * RS;
+  if (row0 >= N || s0 >= r) return;
+  const int nr = (int)mn64(2, N - row0);
+  double pxx[2][RS], pyy[2][RS], pss[2][RS];
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+#pragma unroll
+    for (int q = 0; q < RS; ++q) pxx[k][q] = pyy[k][q] = pss[k][q] = 0.0;
+  const int64_t npair = N / 2;  // full float4 pairs (N even)
+  const int64_t ld4 = ldz / 2;
+  for (int64_t c2 = lane; c2 < npair; c2 += 32) {
+    double zx[2][2], zy[2][2], zs[2][2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (k < nr) z4 = __ldg(Z4 + (row0 + k) * ld4 + c2);
+      zx[k][0] = f2d_int(z4.x);
+      zy[k][0] = f2d_int(z4.y);
+      zx[k][1] = f2d_int(z4.z);
+      zy[k][1] = f2d_int(z4.w);
+      zs[k][0] = zx[k][0] + zy[k][0];
+      zs[k][1] = zx[k][1] + zy[k][1];
+    }
+#pragma unroll
+    for (int q = 0; q < RS; ++q) {
+      if (s0 + q < r) {
+        const double2* xd = X + (int64_t)(s0 + q) * N + 2 * c2;
+        const double2 a = __ldg(xd), b = __ldg(xd + 1);
+        const double2 sv = __ldg(reinterpret_cast<const double2*>(XS + (int64_t)(s0 + q) * N) + c2);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          pxx[k][q] = fma(zx[k][0], a.x, fma(zx[k][1], b.x, pxx[k][q]));
+          pyy[k][q] = fma(zy[k][0], a.y, fma(zy[k][1], b.y, pyy[k][q]));
+          pss[k][q] = fma(zs[k][0], sv.x, fma(zs[k][1], sv.y, pss[k][q]));
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+#pragma unroll
+    for (int q = 0; q < RS; ++q)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        pxx[k][q] += __shfl_xor_sync(0xffffffffu, pxx[k][q], o);
+        pyy[k][q] += __shfl_xor_sync(0xffffffffu, pyy[k][q], o);
+        pss[k][q] += __shfl_xor_sync(0xffffffffu, pss[k][q], o);
+      }
+  if (lane != 0) return;
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+#pragma unroll
+    for (int q = 0; q < RS; ++q)
+      if (k < nr && s0 + q < r)
+        Y[(int64_t)(s0 + q) * N + row0 + k] =
+            make_double2(pxx[k][q] - pyy[k][q], pss[k][q] - pxx[k][q] - pyy[k][q]);
+}
+
+// XS[i] = X[i].x + X[i].y (the vectors' sums of the 3M products)
+__global__ void xsum_kernel(const double2* __restrict__ X, double* __restrict__ XS, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double2 v = X[i];
+    XS[i] = v.x + v.y;
+  }
+}
+constexpr int kResidRS = 4;  // vectors per warp of the several-vector FP64 product
 
 // y = Z x (complex64, FP32 accumulation) for a Z whose lower-right quadrant
 // is minus the upper-left one (Z11 = -Z00 = -(i/omega) K1, Eq.
@@ -583,10 +672,100 @@ __global__ void __launch_bounds__(1024) lu_panel_smem_kernel(CT* __restrict__ A,
   lu_panel_smem_body<CT, W>(A, d, sz, k0, piv, status, defer, blockIdx.x, lu_smem, blockDim.x);
 }
 
+// One 32 x TN tile of the trailing update, C -= A B with A the tile's rows
+// of the panel columns [k0, k0 + W) and B the panel's rows of the tile's
+// columns, staged in shared memory together with the sums s = x + y of
+// every entry.  The complex products take the 3M form (three real products
+// instead of four): Re(ab) = a.x b.x - a.y b.y and
+// Im(ab) = s_a s_b - a.x b.x - a.y b.y, so the contraction costs three FP64
+// multiply-adds per complex multiply-add; the sums cost one addition per
+// staged entry.  Its rounding error is bounded like that of the usual form
+// up to a small constant (normwise; Higham, Accuracy and Stability of
+// Numerical Algorithms, Sec. 23.2.4).
+template <int W, int TN>
+struct Tile3M {
+  double2 a[32][W + 1];
+  double as[32][W + 1];
+  double2 b[W][TN + 1];
+  double bs[W][TN + 1];
+};
+
+// stage the tile with rows [tr, tr + 32), columns [tc, tc + TN) of block M
+// (active size n, columns below c1, panel width w); GT threads, lt = rank
+template <int W, int TN, int GT>
+__device__ __forceinline__ void tile3m_load(Tile3M<W, TN>& T, const double2* __restrict__ M,
+                                            int64_t d, int64_t tr, int64_t tc, int k0, int n,
+                                            int64_t c1, int w, int lt) {
+  for (int t = lt; t < 32 * W; t += GT) {
+    const int i = t / W, k = t % W;
+    const int64_t gr = tr + i;
+    const double2 v = (gr < n && k < w) ? M[gr * d + k0 + k] : make_double2(0.0, 0.0);
+    T.a[i][k] = v;
+    T.as[i][k] = v.x + v.y;
+  }
+  for (int t = lt; t < W * TN; t += GT) {
+    const int k = t / TN, j = t % TN;
+    const int64_t gc = tc + j;
+    const double2 v = (gc < c1 && k < w) ? M[(int64_t)(k0 + k) * d + gc] : make_double2(0.0, 0.0);
+    T.b[k][j] = v;
+    T.bs[k][j] = v.x + v.y;
+  }
+}
+
+// C -= A B for the staged tile: thread lt owns rows ty + 8 i (i < 4) and
+// columns tx + (TN / JN) j (j < JN) of the tile, 8 * TN / JN threads
+template <int W, int TN, int JN>
+__device__ __forceinline__ void tile3m_update(const Tile3M<W, TN>& T, double2* __restrict__ M,
+                                              int64_t d, int64_t tr, int64_t tc, int n,
+                                              int64_t c1, int lt) {
+  constexpr int CX = TN / JN;
+  const int ty = lt / CX, tx = lt % CX;
+  double pxx[4][JN], pyy[4][JN], pss[4][JN];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < JN; ++j) pxx[i][j] = pyy[i][j] = pss[i][j] = 0.0;
+#pragma unroll 4
+  for (int k = 0; k < W; ++k) {
+    double2 av[4], bv[JN];
+    double as[4], bs[JN];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      av[i] = T.a[ty + 8 * i][k];
+      as[i] = T.as[ty + 8 * i][k];
+    }
+#pragma unroll
+    for (int j = 0; j < JN; ++j) {
+      bv[j] = T.b[k][tx + CX * j];
+      bs[j] = T.bs[k][tx + CX * j];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < JN; ++j) {
+        pxx[i][j] = fma(av[i].x, bv[j].x, pxx[i][j]);
+        pyy[i][j] = fma(av[i].y, bv[j].y, pyy[i][j]);
+        pss[i][j] = fma(as[i], bs[j], pss[i][j]);
+      }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < JN; ++j) {
+      const int64_t gr = tr + ty + 8 * i, gc = tc + tx + CX * j;
+      if (gr < n && gc < c1) {
+        double2 v = M[gr * d + gc];
+        v.x -= pxx[i][j] - pyy[i][j];
+        v.y -= pss[i][j] - pxx[i][j] - pyy[i][j];
+        M[gr * d + gc] = v;
+      }
+    }
+}
+
 // One step of the blocked LU in one launch.  The dynamic shared memory
 // (kLuStepSmem) admits one CTA per SM, so no two CTAs share an SM's FP64
 // pipe.  CTAs 0 .. nb-1 first factor panel k1 of their block (rows in shared
-// memory, swaps held back); then each group of 64 threads of every CTA takes
+// memory, swaps held back); then each group of 128 threads of every CTA takes
 // 32 x 32 tiles of the trailing update of panel k0 over columns [c0, d) one
 // at a time (the first one assigned so that the tiles spread over the SMs,
 // the others from a queue, an atomic counter) and synchronises with a
@@ -595,9 +774,12 @@ __global__ void __launch_bounds__(1024) lu_panel_smem_kernel(CT* __restrict__ A,
 // entries and never wait on each other.  Without a panel (k1 < 0) every CTA
 // only takes tiles.
 constexpr int kLuStepThreads = 512;
+constexpr int kLuGroup = 128;  // threads per tile group (4 x 2 outputs each)
 constexpr size_t kLuStepSmem = 140 * 1024;
+static_assert(sizeof(Tile3M<LUW, 32>) * (kLuStepThreads / kLuGroup) <= kLuStepSmem,
+              "the tile groups' staging must fit in the step kernel's shared memory");
 __device__ __forceinline__ void group_bar(int id) {
-  asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory");
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(kLuGroup) : "memory");
 }
 template <int W>
 __global__ void __launch_bounds__(kLuStepThreads) lu_step_kernel(
@@ -613,19 +795,15 @@ __global__ void __launch_bounds__(kLuStepThreads) lu_step_kernel(
     lu_panel_smem_body<double2, W>(A, d, sz, k1, piv, status, 1, blockIdx.x, lu_smem, nthr);
     __syncthreads();  // the shared memory is the tiles' from here on
   }
-  constexpr int TN = 32, JN = TN / 8;
+  constexpr int TN = 32, GT = kLuGroup;
   const int64_t r0 = k0 + W;
   const int64_t rt_n = (d - r0 + 31) / 32, ct_n = (d - c0 + TN - 1) / TN;
   const int64_t per_b = rt_n * ct_n;
   const unsigned tiles = (unsigned)((int64_t)nb * per_b);
   if (rt_n <= 0 || ct_n <= 0) return;
-  const int grp = threadIdx.x >> 6, lt = threadIdx.x & 63;
-  const int ty = lt / 8, tx = lt % 8;
-  typedef double2 RowA[W + 1];
-  typedef double2 RowB[TN + 1];
-  RowA* sA = reinterpret_cast<RowA*>(lu_smem + (size_t)grp * (32 * (W + 1) + W * (TN + 1)) * sizeof(double2));
-  RowB* sB = reinterpret_cast<RowB*>(reinterpret_cast<double2*>(sA) + 32 * (W + 1));
-  __shared__ unsigned tb[kLuStepThreads / 64];
+  const int grp = threadIdx.x / GT, lt = threadIdx.x % GT;
+  Tile3M<W, TN>& T = reinterpret_cast<Tile3M<W, TN>*>(lu_smem)[grp];
+  __shared__ unsigned tb[kLuStepThreads / GT];
   const int bar = 1 + grp;  // barrier 0 is __syncthreads'
   // The first tile of each group of the CTAs without a panel is assigned
   // statically, tile g * (G - np) + (c - np) to group g of CTA c, so that few
@@ -633,7 +811,7 @@ __global__ void __launch_bounds__(kLuStepThreads) lu_step_kernel(
   // rest come from the queue (tickets after the static ones).
   const unsigned npan = k1 >= 0 ? (unsigned)min(nb, (int)gridDim.x) : 0u;
   const unsigned nfree = gridDim.x - npan;
-  const unsigned nstatic = nfree * (kLuStepThreads / 64);
+  const unsigned nstatic = nfree * (kLuStepThreads / GT);
   bool stat = blockIdx.x >= npan;
   for (;;) {
     if (lt == 0) tb[grp] = stat ? (unsigned)grp * nfree + (blockIdx.x - npan)
@@ -650,53 +828,9 @@ __global__ void __launch_bounds__(kLuStepThreads) lu_step_kernel(
     const bool act = !(k0 >= n || tr >= n || tc >= c1);
     const int w = act ? min(W, n - k0) : 0;
     double2* M = A + (int64_t)b * d * d;
-    if (act) {
-      for (int t = lt; t < 32 * W; t += 64) {
-        const int i = t / W, k = t % W;
-        const int64_t gr = tr + i;
-        sA[i][k] = (gr < n && k < w) ? M[gr * d + k0 + k] : make_double2(0.0, 0.0);
-      }
-      for (int t = lt; t < W * TN; t += 64) {
-        const int k = t / TN, j = t % TN;
-        const int64_t gc = tc + j;
-        sB[k][j] = (gc < c1 && k < w) ? M[(int64_t)(k0 + k) * d + gc] : make_double2(0.0, 0.0);
-      }
-    }
+    if (act) tile3m_load<W, TN, GT>(T, M, d, tr, tc, k0, n, c1, w, lt);
     group_bar(bar);
-    if (act) {
-      double2 acc[4][JN];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < JN; ++j) acc[i][j] = make_double2(0.0, 0.0);
-#pragma unroll 4
-      for (int k = 0; k < W; ++k) {
-        double2 av[4], bv[JN];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) av[i] = sA[ty + 8 * i][k];
-#pragma unroll
-        for (int j = 0; j < JN; ++j) bv[j] = sB[k][tx + 8 * j];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < JN; ++j) {
-            acc[i][j].x = fma(av[i].x, bv[j].x, fma(-av[i].y, bv[j].y, acc[i][j].x));
-            acc[i][j].y = fma(av[i].x, bv[j].y, fma(av[i].y, bv[j].x, acc[i][j].y));
-          }
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < JN; ++j) {
-          const int64_t gr = tr + ty + 8 * i, gc = tc + tx + 8 * j;
-          if (gr < n && gc < c1) {
-            double2 v = M[gr * d + gc];
-            v.x -= acc[i][j].x;
-            v.y -= acc[i][j].y;
-            M[gr * d + gc] = v;
-          }
-        }
-    }
+    if (act) tile3m_update<W, TN, 2>(T, M, d, tr, tc, n, c1, lt);
     group_bar(bar);  // before the group's next tile loads and queue read
   }
 }
@@ -757,6 +891,154 @@ __global__ void trsm_tile_kernel(const CT* __restrict__ A, CT* __restrict__ B, i
 #pragma unroll
   for (int i = 0; i < W; ++i)
     if (i < w) X[(int64_t)(k0 + i) * ldb + c] = v[i];
+}
+
+// Explicit inverses of the blocks from their complex64 LU factors (unit
+// lower L and upper U in A, the row swaps in piv) in one launch.  CTA
+// (x, b) computes the CW columns j0 = x CW .. j0 + CW - 1 of
+// M = U^{-1} L^{-1} of block b, i.e. solves L U m_j = e_j, by forward and
+// back substitution in tiles of 32 rows.  Thread t holds rows t, t + 512, ..
+// (RPT of them) of those columns in registers.  Per tile: the tile's rows go
+// to shared memory, where warp w finishes column w of them (lanes over the
+// rows, the substitution within the 32 x 32 diagonal tile by shuffles);
+// then every row outside the tile subtracts the tile's contribution, its
+// factor entries read as 16-byte loads.  Column j of L^{-1} is zero above
+// row j, so the forward pass starts at the tile of the CTA's first column.
+// With P e_c = e_pi(c) for the recorded swaps (P A = L U), the inverse
+// U^{-1} L^{-1} P has column c equal to column pi(c) of M.
+constexpr int kInvCW = 16;        // columns of M per CTA (= warps per CTA)
+constexpr int kInvThreads = 512;  // 32 * kInvCW
+template <int RPT>
+__global__ void __launch_bounds__(kInvThreads, RPT == 1 ? 2 : 1) block_inverse_cols_kernel(
+    const float2* __restrict__ A, int64_t d, const int32_t* __restrict__ sz,
+    const int32_t* __restrict__ piv, float2* __restrict__ inv) {
+  constexpr int CW = kInvCW;
+  __shared__ __align__(16) float2 sT[32][CW];  // the current tile's rows
+  __shared__ float2 sD[32][33];                // its diagonal block of L or U
+  __shared__ int sPiv[kInvThreads * RPT];
+  __shared__ int sTarget[CW];
+  const int b = blockIdx.y;
+  const int n = sz[b];
+  const int j0 = blockIdx.x * CW;
+  if (j0 >= n) return;  // uniform over the CTA
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const float2* F = A + (int64_t)b * d * d;
+  for (int k = t; k < n; k += kInvThreads) sPiv[k] = piv[(int64_t)b * d + k];
+  if (t < CW) sTarget[t] = -1;
+  __syncthreads();
+  // targets: the inverse's column c with pi(c) = j0 + jj
+  for (int c = t; c < n; c += kInvThreads) {
+    int pos = c;
+    for (int k = 0; k < n; ++k) {
+      const int p = sPiv[k];
+      pos = pos == k ? p : (pos == p ? k : pos);
+    }
+    if (pos >= j0 && pos < j0 + CW) sTarget[pos - j0] = c;
+  }
+  float2 x[RPT][CW];
+#pragma unroll
+  for (int q = 0; q < RPT; ++q)
+#pragma unroll
+    for (int jj = 0; jj < CW; ++jj)
+      x[q][jj] = make_float2(t + q * kInvThreads == j0 + jj ? 1.f : 0.f, 0.f);
+  const int ntile = (n + 31) / 32;
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool lower = pass == 0;
+    const int t_first = lower ? j0 / 32 : ntile - 1;
+    const int t_end = lower ? ntile : -1;
+    const int t_step = lower ? 1 : -1;
+    for (int tile = t_first; tile != t_end; tile += t_step) {
+      const int r = tile * 32;
+      const int kn = min(32, n - r);
+      const int ow = (r % kInvThreads) / 32, oq = r / kInvThreads;  // owner warp, slot
+      // 1. the tile's rows to sT, its diagonal block to sD (identity outside n)
+      if (warp == ow) {
+#pragma unroll
+        for (int q = 0; q < RPT; ++q)
+          if (q == oq) {
+#pragma unroll
+            for (int jj = 0; jj < CW; ++jj) sT[lane][jj] = x[q][jj];
+          }
+      }
+      for (int e = t; e < 32 * 32; e += kInvThreads) {
+        const int i = e / 32, k = e % 32;
+        sD[i][k] = (i < kn && k < kn) ? F[(int64_t)(r + i) * d + r + k]
+                                      : make_float2(i == k ? 1.f : 0.f, 0.f);
+      }
+      __syncthreads();
+      // 2. the diagonal block: warp w finishes column w (lane = row)
+      {
+        float2 v = sT[lane][warp];
+        if (lower) {
+          for (int k = 0; k < 31; ++k) {
+            const float vx = __shfl_sync(0xffffffffu, v.x, k), vy = __shfl_sync(0xffffffffu, v.y, k);
+            if (lane > k) {
+              const float2 l = sD[lane][k];
+              v.x -= l.x * vx - l.y * vy;
+              v.y -= l.x * vy + l.y * vx;
+            }
+          }
+        } else {
+          for (int k = 31; k >= 0; --k) {
+            if (lane == k) v = cdivT(v, sD[k][k]);
+            const float vx = __shfl_sync(0xffffffffu, v.x, k), vy = __shfl_sync(0xffffffffu, v.y, k);
+            if (lane < k) {
+              const float2 u = sD[lane][k];
+              v.x -= u.x * vx - u.y * vy;
+              v.y -= u.x * vy + u.y * vx;
+            }
+          }
+        }
+        sT[lane][warp] = v;
+      }
+      __syncthreads();
+      // 3. the tile's rows back to their owner; every other row subtracts
+      //    F[row, r:r+kn) times the tile (rows below for L, above for U)
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        const int row = t + q * kInvThreads;
+        if (row >= n) continue;
+        if (row >= r && row < r + 32) {
+#pragma unroll
+          for (int jj = 0; jj < CW; ++jj) x[q][jj] = sT[row - r][jj];
+          continue;
+        }
+        if (lower ? row < r + 32 : row >= r) continue;
+        const float4* f4 = reinterpret_cast<const float4*>(F + (int64_t)row * d + r);
+#pragma unroll 2
+        for (int k2 = 0; k2 < 16; ++k2) {
+          if (2 * k2 >= kn) break;
+          const float4 ff = __ldg(f4 + k2);  // entries k = 2 k2, 2 k2 + 1
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int k = 2 * k2 + h;
+            const float fx = h ? ff.z : ff.x, fy = h ? ff.w : ff.y;
+            const float4* tk = reinterpret_cast<const float4*>(&sT[k][0]);
+#pragma unroll
+            for (int j2 = 0; j2 < CW / 2; ++j2) {
+              const float4 tv = tk[j2];
+              x[q][2 * j2].x -= fx * tv.x - fy * tv.y;
+              x[q][2 * j2].y -= fx * tv.y + fy * tv.x;
+              x[q][2 * j2 + 1].x -= fx * tv.z - fy * tv.w;
+              x[q][2 * j2 + 1].y -= fx * tv.w + fy * tv.z;
+            }
+          }
+        }
+      }
+      __syncthreads();  // before the next tile overwrites sT and sD
+    }
+  }
+  float2* O = inv + (int64_t)b * d * d;
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int row = t + q * kInvThreads;
+    if (row >= n) continue;
+#pragma unroll
+    for (int jj = 0; jj < CW; ++jj) {
+      const int c = sTarget[jj];
+      if (j0 + jj < n && c >= 0) O[(int64_t)row * d + c] = x[q][jj];
+    }
+  }
 }
 
 // C[r0:r1, c0:c1] -= A[r0:r1, k0:k0+w] * Bm[k0:k0+w, c0:c1] per block:
@@ -878,22 +1160,19 @@ __global__ void lu_swap_trsm_kernel(double2* __restrict__ A, int64_t d,
 
 // FP64 trailing update of the block LU: A[r0:n, c0:c1) -= A[r0:n, k0:k0+w)
 // A[k0:k0+w, c0:c1), r0 = k0 + W, over all blocks.  32 x TN output tiles,
-// 64 threads with 4 x TN/8 complex accumulators; CTAs stride over the tiles
-// when the grid is smaller than the tile count.  The FP64 pipe (two DFMA
-// per clock per SM) bounds every tile shape, so small tiles cost nothing and
-// mask less of the late, narrow updates.
+// 64 threads with 4 x TN/8 outputs each (3M products, tile3m_update); CTAs
+// stride over the tiles when the grid is smaller than the tile count.  The
+// FP64 pipe (two DFMA per clock per SM) bounds every tile shape, so small
+// tiles cost nothing and mask less of the late, narrow updates.
 template <int W, int TN>
 __global__ void __launch_bounds__(64) lu_update_kernel(double2* __restrict__ A, int64_t d,
                                                        const int32_t* __restrict__ sz, int k0,
                                                        int64_t c0, int64_t c1_cap, int nb) {
-  constexpr int JN = TN / 8;
   const int64_t r0 = k0 + W;
   const int64_t cend = c1_cap < 0 ? d : c1_cap;
   const int64_t rt_n = (d - r0 + 31) / 32, ct_n = (cend - c0 + TN - 1) / TN;
   const int64_t per_b = rt_n * ct_n, tiles = (int64_t)nb * per_b;
-  __shared__ double2 sA[32][W + 1];
-  __shared__ double2 sB[W][TN + 1];
-  const int ty = threadIdx.x / 8, tx = threadIdx.x % 8;
+  __shared__ Tile3M<W, TN> T;
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int b = (int)(tile / per_b);
     const int64_t rem = tile - (int64_t)b * per_b;
@@ -903,50 +1182,10 @@ __global__ void __launch_bounds__(64) lu_update_kernel(double2* __restrict__ A, 
     if (k0 >= n || tr >= n || tc >= c1) continue;  // uniform over the CTA
     const int w = min(W, n - k0);
     double2* M = A + (int64_t)b * d * d;
-    for (int t = threadIdx.x; t < 32 * W; t += 64) {
-      const int i = t / W, k = t % W;
-      const int64_t gr = tr + i;
-      sA[i][k] = (gr < n && k < w) ? M[gr * d + k0 + k] : make_double2(0.0, 0.0);
-    }
-    for (int t = threadIdx.x; t < W * TN; t += 64) {
-      const int k = t / TN, j = t % TN;
-      const int64_t gc = tc + j;
-      sB[k][j] = (gc < c1 && k < w) ? M[(int64_t)(k0 + k) * d + gc] : make_double2(0.0, 0.0);
-    }
+    tile3m_load<W, TN, 64>(T, M, d, tr, tc, k0, n, c1, w, threadIdx.x);
     __syncthreads();
-    double2 acc[4][JN];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < JN; ++j) acc[i][j] = make_double2(0.0, 0.0);
-#pragma unroll 4
-    for (int k = 0; k < W; ++k) {
-      double2 a[4], bb[JN];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = sA[ty + 8 * i][k];
-#pragma unroll
-      for (int j = 0; j < JN; ++j) bb[j] = sB[k][tx + 8 * j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < JN; ++j) {
-          acc[i][j].x = fma(a[i].x, bb[j].x, fma(-a[i].y, bb[j].y, acc[i][j].x));
-          acc[i][j].y = fma(a[i].x, bb[j].y, fma(a[i].y, bb[j].x, acc[i][j].y));
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < JN; ++j) {
-        const int64_t gr = tr + ty + 8 * i, gc = tc + tx + 8 * j;
-        if (gr < n && gc < c1) {
-          double2 v = M[gr * d + gc];
-          v.x -= acc[i][j].x;
-          v.y -= acc[i][j].y;
-          M[gr * d + gc] = v;
-        }
-      }
-    __syncthreads();  // before the next tile's loads overwrite sA, sB
+    tile3m_update<W, TN, TN / 8>(T, M, d, tr, tc, n, c1, threadIdx.x);
+    __syncthreads();  // before the next tile's loads overwrite the staging
   }
 }
 
@@ -1921,9 +2160,20 @@ mueller_status op_matvec(const mueller_operator* op, const void* X, void* Y, int
     MU_CHECK_LAUNCH("gemv_c128_kernel");
   } else {
     // FP64-bound: small blocks (2 warps, 4 rows) spread the rows evenly over the SMs
-    dim3 grid(nblk(N, 4), r);
-    { Prof prof_("gemv_c64_kernel<double>", s); gemv_c64_kernel<double><<<grid, 64, 0, s>>>(N, (const float4*)op->Z_dev, op->ldz, X, Y, N, N, r, nullptr); }
-    MU_CHECK_LAUNCH("gemv_c64_kernel<double>");
+    if (r >= 2) {
+      // several vectors: each Z entry read once for kResidRS of them, 3M products
+      double* xs = nullptr;
+      MU_CUDA(cudaMallocAsync((void**)&xs, (size_t)r * N * sizeof(double), s));
+      { Prof prof_("xsum_kernel", s); xsum_kernel<<<nblk((int64_t)r * N, 256), 256, 0, s>>>((const double2*)X, xs, (int64_t)r * N); }
+      dim3 grid(nblk(N, 4), (unsigned)((r + kResidRS - 1) / kResidRS));
+      { Prof prof_("gemv_c64_f64_3m_kernel", s); gemv_c64_f64_3m_kernel<kResidRS><<<grid, 64, 0, s>>>(N, (const float4*)op->Z_dev, op->ldz, (const double2*)X, xs, (double2*)Y, r); }
+      const cudaError_t le = cudaGetLastError();
+      cudaFreeAsync(xs, s);
+      if (le != cudaSuccess) return cuda_fail(le, "gemv_c64_f64_3m_kernel");
+    } else {
+      { Prof prof_("gemv_c64_kernel<double>", s); gemv_c64_kernel<double><<<dim3(nblk(N, 4), 1), 64, 0, s>>>(N, (const float4*)op->Z_dev, op->ldz, X, Y, N, N, r, nullptr); }
+      MU_CHECK_LAUNCH("gemv_c64_kernel<double>");
+    }
     dim3 g2(nblk(m->nn, 8), r);
     { Prof prof_("near_spmv_kernel<double2, double2>", s); near_spmv_kernel<double2, double2><<<g2, 256, 0, s>>>(m->nn, m->near_rowptr, m->near_col,
                                                           (const double2*)op->near_dev,
@@ -2168,6 +2418,20 @@ static mueller_status batched_lu_inverse(CT* A, int64_t d, int nb, const int32_t
 template <class CT>
 static mueller_status block_inverse(const CT* A, int64_t d, int nb, const int32_t* sz_dev,
                                     const int32_t* piv, CT* inv, cudaStream_t s) {
+  if constexpr (std::is_same<CT, float2>::value) {
+    if (d <= 2 * kInvThreads) {  // one launch (block_inverse_cols_kernel)
+      const dim3 grid((unsigned)nblk(d, kInvCW), (unsigned)nb);
+      {
+        Prof prof_("block_inverse_cols_kernel", s);
+        if (d <= kInvThreads)
+          block_inverse_cols_kernel<1><<<grid, kInvThreads, 0, s>>>(A, d, sz_dev, piv, inv);
+        else
+          block_inverse_cols_kernel<2><<<grid, kInvThreads, 0, s>>>(A, d, sz_dev, piv, inv);
+      }
+      MU_CHECK_LAUNCH("block_inverse_cols_kernel");
+      return MUELLER_OK;
+    }
+  }
   { Prof prof_("perm_identity_kernel", s); perm_identity_kernel<CT><<<dim3(nblk(d, 128), nb), 128, 0, s>>>(inv, d, sz_dev, piv); }
   MU_CHECK_LAUNCH("perm_identity_kernel");
   for (int k0 = 0; k0 < d; k0 += NBK) {  // forward: L (unit lower)
