@@ -188,8 +188,16 @@ const char* mueller_status_string(mueller_status s);
  * orders (21-bit keys in the node bounding box scaled by its largest extent,
  * x in the least significant bit, ties by original index; elements keyed by
  * the centroid of their corners), classifies the touching element pairs
- * (shared corners: 3 coincident, 2 common edge, 1 common vertex) and uploads
- * everything to the device on 'stream'.
+ * (shared corners: 3 coincident, 2 common edge, 1 common vertex), lays out
+ * the near-part blocks and uploads everything to the device.  The node and
+ * element arrays are uploaded on 'stream' before the call returns; the
+ * touching pairs and the near layout are built and uploaded by a host thread
+ * of the library after it returns, so that the frame, point-geometry and
+ * regular-pair launches of the caller need not wait for them.  Every call
+ * that reads them (mueller_mesh_get_info, mueller_mesh_touching,
+ * mueller_mesh_near_layout, mueller_near_bytes, the touching-pair part of
+ * mueller_assemble, and the calls after it) waits for that thread first and
+ * returns its error, if it had one; mueller_mesh_free waits for it too.
  *   xyz   host, n_nodes x 3 float64, read only, copied.
  *   tri6  host, n_tri x 6 int32 node ids, read only, copied.
  *   flags MUELLER_MESH_KEEP_ORDER: keep the input order (no Morton

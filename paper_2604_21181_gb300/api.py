@@ -255,8 +255,11 @@ class Mesh:
         self.h = h
         self._lib = lib
         self.frame_rule = None
-        info = self.info()
-        self.nn, self.nt, self.N = info["n_nodes"], info["n_tri"], info["n_dof"]
+        # sizes from the arrays: mueller_mesh_get_info would wait for the
+        # touching pairs and the near layout, which the library builds on a
+        # host thread while the frame and the regular pairs are launched
+        self.nn, self.nt = self.xyz.shape[0], self.tri6.shape[0]
+        self.N = 4 * self.nn
 
     def info(self) -> dict:
         i = CMeshInfo()

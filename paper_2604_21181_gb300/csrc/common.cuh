@@ -5,7 +5,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/mueller.h"
@@ -103,9 +105,18 @@ struct mueller_mesh {
   // small device scratch
   int32_t* d_flags = nullptr;      // status words
   double* d_scal = nullptr;        // 64 doubles
+  // the host thread that builds the touching pairs and the near layout
+  // (and uploads them) after mueller_mesh_load returns; mu::mesh_tables
+  // joins it
+  mutable std::thread tables_thread;
+  mutable std::mutex tables_mu;
+  mueller_status tables_st = MUELLER_OK;
+  std::string tables_msg;
 };
 
 namespace mu {
+// The host tables of m (touching pairs, near layout) are ready; their status.
+mueller_status mesh_tables(const mueller_mesh* m);
 // ----------------------------------------------------------- launchers
 // geometry.cu
 mueller_status launch_frame(mueller_mesh* m, int frame_rule, cudaStream_t s);

@@ -259,6 +259,151 @@ static mueller_status upload(Tp** dst, const Tp* src, size_t n, cudaStream_t s) 
   return MUELLER_OK;
 }
 
+// Touching-pair classification, the touching kernel's launch order and the
+// near-part block layout of a loaded mesh (its host tables).
+static void build_tables(mueller_mesh* m, const std::vector<int32_t>& ptr,
+                         const std::vector<int32_t>& n2e, std::vector<TouchPair>& tp,
+                         std::vector<int32_t>& order, std::vector<int32_t>& slot) {
+  const int64_t nn = m->nn, nt = m->nt;
+  const int32_t* T = m->T_h.data();
+  // host threads for the table passes below: each takes a contiguous range
+  // of elements or rows, and the tables do not depend on the thread count
+  const int64_t nthreads = std::max<int64_t>(
+      1, std::min<int64_t>({(int64_t)std::thread::hardware_concurrency(), 16, nn / 256}));
+  auto run = [&](auto&& fn) {
+    if (nthreads == 1) {
+      fn((int64_t)0);
+      return;
+    }
+    std::vector<std::thread> pool;
+    pool.reserve(nthreads);
+    for (int64_t t = 0; t < nthreads; ++t) pool.emplace_back(fn, t);
+    for (std::thread& th : pool) th.join();
+  };
+  // ---- touching pairs (sorted by ex, then ey)
+  tp.clear();
+  {
+    std::vector<std::vector<TouchPair>> part(nthreads);
+    run([&](int64_t t) {
+      const int64_t e0 = nt * t / nthreads, e1 = nt * (t + 1) / nthreads;
+      std::vector<int32_t> cand;
+      std::vector<int32_t> seen(nt, -1);
+      std::vector<uint64_t> bits((nt + 63) / 64 + 1, 0);
+      for (int64_t ex = e0; ex < e1; ++ex) {
+        cand.clear();
+        for (int k = 0; k < 3; ++k) {
+          int32_t v = T[6 * ex + k];
+          for (int32_t q = ptr[v]; q < ptr[v + 1]; ++q) {
+            const int32_t ey = n2e[q] >> 3;
+            if (seen[ey] != (int32_t)ex) {
+              seen[ey] = (int32_t)ex;
+              cand.push_back(ey);
+            }
+          }
+        }
+        sort_ids(cand.data(), cand.size(), bits.data());
+        for (int32_t ey : cand) {
+          int32_t packed;
+          int cls = classify_pair(T + 6 * ex, T + 6 * ey, packed);
+          if (cls > 0) part[t].push_back({(int32_t)ex, ey, cls, packed});
+        }
+      }
+    });
+    size_t total = 0;
+    for (const auto& v : part) total += v.size();
+    tp.reserve(total);
+    for (const auto& v : part) tp.insert(tp.end(), v.begin(), v.end());
+  }
+  m->n_touch = (int64_t)tp.size();
+  // launch order of the touching kernel: coincident and common-edge pairs,
+  // then the common-vertex pairs (which use shared-memory tables)
+  order.clear();
+  order.reserve(tp.size());
+  for (int pass = 0; pass < 2; ++pass)
+    for (size_t q = 0; q < tp.size(); ++q)
+      if ((tp[q].cls == 1) == (pass == 1)) order.push_back((int32_t)q);
+  m->n_touch_ce = 0;
+  for (const TouchPair& q : tp) m->n_touch_ce += q.cls != 1;
+  // ---- near-part block layout: node pairs of the touching element pairs.
+  // Row by row: the columns of test node ni are the nodes of every trial
+  // element touching an element that holds ni (deduplicated with a stamp
+  // array, then sorted), and the slot of (pair, i, j) is found through a
+  // column -> position array valid for the current row.
+  std::vector<int64_t> pfirst(nt + 1, 0);  // tp is sorted by ex
+  for (const TouchPair& q : tp) pfirst[q.ex + 1]++;
+  for (int64_t e = 0; e < nt; ++e) pfirst[e + 1] += pfirst[e];
+  slot.assign((size_t)m->n_touch * 36, 0);
+  {
+    // Rows are independent: phase 1 finds each row's sorted columns, phase 2
+    // (after the prefix sum of the row lengths) places them and fills the
+    // slots of the row's (pair, i) entries, which no other row writes.
+    std::vector<std::vector<int32_t>> cols(nthreads);
+    std::vector<int32_t> len_of(nn, 0);
+    auto range = [&](int64_t t, int64_t& r0, int64_t& r1) {
+      r0 = nn * t / nthreads;
+      r1 = nn * (t + 1) / nthreads;
+    };
+    auto phase1 = [&](int64_t t) {
+      int64_t r0, r1;
+      range(t, r0, r1);
+      std::vector<int32_t> stamp(nn, -1), row;
+      std::vector<uint64_t> bits((nn + 63) / 64 + 1, 0);
+      std::vector<int32_t>& out = cols[t];
+      for (int64_t ni = r0; ni < r1; ++ni) {
+        row.clear();
+        for (int32_t q = ptr[ni]; q < ptr[ni + 1]; ++q) {
+          const int64_t ex = n2e[q] >> 3;
+          for (int64_t p = pfirst[ex]; p < pfirst[ex + 1]; ++p)
+            for (int j = 0; j < 6; ++j) {
+              const int32_t nj = T[6 * tp[p].ey + j];
+              if (stamp[nj] != (int32_t)ni) {
+                stamp[nj] = (int32_t)ni;
+                row.push_back(nj);
+              }
+            }
+        }
+        sort_ids(row.data(), row.size(), bits.data());
+        out.insert(out.end(), row.begin(), row.end());
+        len_of[ni] = (int32_t)row.size();
+      }
+    };
+    run(phase1);
+    m->near_rowptr_h.assign(nn + 1, 0);
+    for (int64_t ni = 0; ni < nn; ++ni) m->near_rowptr_h[ni + 1] = m->near_rowptr_h[ni] + len_of[ni];
+    m->near_col_h.assign((size_t)m->near_rowptr_h[nn], 0);
+    auto phase2 = [&](int64_t t) {
+      int64_t r0, r1;
+      range(t, r0, r1);
+      std::vector<int32_t> pos(nn, 0);
+      const int32_t* src = cols[t].data();
+      for (int64_t ni = r0; ni < r1; ++ni) {
+        const int32_t start = m->near_rowptr_h[ni], len = len_of[ni];
+        for (int32_t k = 0; k < len; ++k) {
+          m->near_col_h[(size_t)start + k] = src[k];
+          pos[src[k]] = start + k;
+        }
+        src += len;
+        for (int32_t q = ptr[ni]; q < ptr[ni + 1]; ++q) {
+          const int64_t ex = n2e[q] >> 3;
+          const int i = n2e[q] & 7;
+          for (int64_t p = pfirst[ex]; p < pfirst[ex + 1]; ++p)
+            for (int j = 0; j < 6; ++j) slot[(size_t)p * 36 + i * 6 + j] = pos[T[6 * tp[p].ey + j]];
+        }
+      }
+    };
+    run(phase2);
+    m->nnzb = m->near_rowptr_h[nn];
+  }
+}
+
+// The host tables of a mesh are ready (their thread joined); their status.
+mueller_status mesh_tables(const mueller_mesh* m) {
+  std::lock_guard<std::mutex> g(m->tables_mu);
+  if (m->tables_thread.joinable()) m->tables_thread.join();
+  if (m->tables_st) return fail(m->tables_st, m->tables_msg);
+  return MUELLER_OK;
+}
+
 }  // namespace mu
 
 using namespace mu;
@@ -288,6 +433,7 @@ const char* mueller_status_string(mueller_status s) {
 
 void mueller_mesh_free(mueller_mesh* m) {
   if (!m) return;
+  mesh_tables(m);  // the table thread writes into m
   void* ptrs[] = {m->X, m->T, m->n2e_ptr, m->n2e, m->frame, m->qd64, m->qd32, m->tp,
                   m->near_rowptr, m->near_col, m->tp_slot, m->tp_order, m->d_flags, m->d_scal};
   for (void* p : ptrs)
@@ -355,170 +501,69 @@ mueller_status mueller_mesh_load(const double* xyz, int64_t nn, const int32_t* t
     for (int64_t e = 0; e < nt; ++e)
       for (int k = 0; k < 6; ++k) n2e[fill[T[6 * e + k]]++] = (int32_t)((e << 3) | k);
   }
-  // host threads for the table passes below: each takes a contiguous range
-  // of elements or rows, and the tables do not depend on the thread count
-  const int64_t nthreads = std::max<int64_t>(
-      1, std::min<int64_t>({(int64_t)std::thread::hardware_concurrency(), 16, nn / 256}));
-  auto run = [&](auto&& fn) {
-    if (nthreads == 1) {
-      fn((int64_t)0);
-      return;
-    }
-    std::vector<std::thread> pool;
-    pool.reserve(nthreads);
-    for (int64_t t = 0; t < nthreads; ++t) pool.emplace_back(fn, t);
-    for (std::thread& th : pool) th.join();
-  };
-  // ---- touching pairs (sorted by ex, then ey)
-  std::vector<TouchPair> tp;
-  {
-    std::vector<std::vector<TouchPair>> part(nthreads);
-    run([&](int64_t t) {
-      const int64_t e0 = nt * t / nthreads, e1 = nt * (t + 1) / nthreads;
-      std::vector<int32_t> cand;
-      std::vector<int32_t> seen(nt, -1);
-      std::vector<uint64_t> bits((nt + 63) / 64 + 1, 0);
-      for (int64_t ex = e0; ex < e1; ++ex) {
-        cand.clear();
-        for (int k = 0; k < 3; ++k) {
-          int32_t v = T[6 * ex + k];
-          for (int32_t q = ptr[v]; q < ptr[v + 1]; ++q) {
-            const int32_t ey = n2e[q] >> 3;
-            if (seen[ey] != (int32_t)ex) {
-              seen[ey] = (int32_t)ex;
-              cand.push_back(ey);
-            }
-          }
-        }
-        sort_ids(cand.data(), cand.size(), bits.data());
-        for (int32_t ey : cand) {
-          int32_t packed;
-          int cls = classify_pair(T + 6 * ex, T + 6 * ey, packed);
-          if (cls > 0) part[t].push_back({(int32_t)ex, ey, cls, packed});
-        }
-      }
-    });
-    size_t total = 0;
-    for (const auto& v : part) total += v.size();
-    tp.reserve(total);
-    for (const auto& v : part) tp.insert(tp.end(), v.begin(), v.end());
-  }
-  m->n_touch = (int64_t)tp.size();
-  // launch order of the touching kernel: coincident and common-edge pairs,
-  // then the common-vertex pairs (which use shared-memory tables)
-  std::vector<int32_t> order;
-  order.reserve(tp.size());
-  for (int pass = 0; pass < 2; ++pass)
-    for (size_t q = 0; q < tp.size(); ++q)
-      if ((tp[q].cls == 1) == (pass == 1)) order.push_back((int32_t)q);
-  m->n_touch_ce = 0;
-  for (const TouchPair& q : tp) m->n_touch_ce += q.cls != 1;
-  // ---- near-part block layout: node pairs of the touching element pairs.
-  // Row by row: the columns of test node ni are the nodes of every trial
-  // element touching an element that holds ni (deduplicated with a stamp
-  // array, then sorted), and the slot of (pair, i, j) is found through a
-  // column -> position array valid for the current row.
-  std::vector<int64_t> pfirst(nt + 1, 0);  // tp is sorted by ex
-  for (const TouchPair& q : tp) pfirst[q.ex + 1]++;
-  for (int64_t e = 0; e < nt; ++e) pfirst[e + 1] += pfirst[e];
-  std::vector<int32_t> slot((size_t)m->n_touch * 36);
-  {
-    // Rows are independent: phase 1 finds each row's sorted columns, phase 2
-    // (after the prefix sum of the row lengths) places them and fills the
-    // slots of the row's (pair, i) entries, which no other row writes.
-    std::vector<std::vector<int32_t>> cols(nthreads);
-    std::vector<int32_t> len_of(nn, 0);
-    auto range = [&](int64_t t, int64_t& r0, int64_t& r1) {
-      r0 = nn * t / nthreads;
-      r1 = nn * (t + 1) / nthreads;
-    };
-    auto phase1 = [&](int64_t t) {
-      int64_t r0, r1;
-      range(t, r0, r1);
-      std::vector<int32_t> stamp(nn, -1), row;
-      std::vector<uint64_t> bits((nn + 63) / 64 + 1, 0);
-      std::vector<int32_t>& out = cols[t];
-      for (int64_t ni = r0; ni < r1; ++ni) {
-        row.clear();
-        for (int32_t q = ptr[ni]; q < ptr[ni + 1]; ++q) {
-          const int64_t ex = n2e[q] >> 3;
-          for (int64_t p = pfirst[ex]; p < pfirst[ex + 1]; ++p)
-            for (int j = 0; j < 6; ++j) {
-              const int32_t nj = T[6 * tp[p].ey + j];
-              if (stamp[nj] != (int32_t)ni) {
-                stamp[nj] = (int32_t)ni;
-                row.push_back(nj);
-              }
-            }
-        }
-        sort_ids(row.data(), row.size(), bits.data());
-        out.insert(out.end(), row.begin(), row.end());
-        len_of[ni] = (int32_t)row.size();
-      }
-    };
-    run(phase1);
-    m->near_rowptr_h.assign(nn + 1, 0);
-    for (int64_t ni = 0; ni < nn; ++ni) m->near_rowptr_h[ni + 1] = m->near_rowptr_h[ni] + len_of[ni];
-    m->near_col_h.assign((size_t)m->near_rowptr_h[nn], 0);
-    auto phase2 = [&](int64_t t) {
-      int64_t r0, r1;
-      range(t, r0, r1);
-      std::vector<int32_t> pos(nn, 0);
-      const int32_t* src = cols[t].data();
-      for (int64_t ni = r0; ni < r1; ++ni) {
-        const int32_t start = m->near_rowptr_h[ni], len = len_of[ni];
-        for (int32_t k = 0; k < len; ++k) {
-          m->near_col_h[(size_t)start + k] = src[k];
-          pos[src[k]] = start + k;
-        }
-        src += len;
-        for (int32_t q = ptr[ni]; q < ptr[ni + 1]; ++q) {
-          const int64_t ex = n2e[q] >> 3;
-          const int i = n2e[q] & 7;
-          for (int64_t p = pfirst[ex]; p < pfirst[ex + 1]; ++p)
-            for (int j = 0; j < 6; ++j) slot[(size_t)p * 36 + i * 6 + j] = pos[T[6 * tp[p].ey + j]];
-        }
-      }
-    };
-    run(phase2);
-    m->nnzb = m->near_rowptr_h[nn];
-  }
   if (flags & MUELLER_MESH_HOST_ONLY) {
     m->host_only = true;
+    std::vector<TouchPair> tp;
+    std::vector<int32_t> order, slot;
+    build_tables(m, ptr, n2e, tp, order, slot);
     m->tp_h = std::move(tp);
     m->tp_slot_h = std::move(slot);
     *out = m;
     return MUELLER_OK;
   }
-  // ---- upload
+  // ---- upload of what the frame, the point geometry and the regular pairs read
   st = upload(&m->X, m->X_h.data(), m->X_h.size(), s);
   if (!st) st = upload(&m->T, m->T_h.data(), m->T_h.size(), s);
   if (!st) st = upload(&m->n2e_ptr, ptr.data(), ptr.size(), s);
   if (!st) st = upload(&m->n2e, n2e.data(), n2e.size(), s);
-  if (!st) st = upload(&m->tp, tp.data(), tp.size(), s);
-  if (!st) st = upload(&m->near_rowptr, m->near_rowptr_h.data(), m->near_rowptr_h.size(), s);
-  if (!st) st = upload(&m->near_col, m->near_col_h.data(), m->near_col_h.size(), s);
-  if (!st) st = upload(&m->tp_slot, slot.data(), slot.size(), s);
-  if (!st) st = upload(&m->tp_order, order.data(), order.size(), s);
+  int dev = 0;
   if (!st) {
     cudaError_t e = cudaMalloc((void**)&m->d_flags, 64 * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc((void**)&m->d_scal, 64 * sizeof(double));
     if (e == cudaSuccess) e = cudaMemsetAsync(m->d_flags, 0, 64 * sizeof(int32_t), s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host vectors above are temporaries
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // ptr and n2e move on below
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e != cudaSuccess) st = cuda_fail(e, "mesh upload");
   }
   if (st) {
     mueller_mesh_free(m);
     return st;
   }
-  m->tp_h = std::move(tp);
-  m->tp_slot_h = std::move(slot);
+  // ---- the host tables and their upload on a host thread of their own, so
+  // that the caller's frame, point-geometry and regular-pair launches need
+  // not wait for them; every call that reads them joins it first
+  // (mesh_tables), and its status and message surface there.
+  m->tables_thread = std::thread([m, dev, ptr = std::move(ptr), n2e = std::move(n2e)]() {
+    std::vector<TouchPair> tp;
+    std::vector<int32_t> order, slot;
+    build_tables(m, ptr, n2e, tp, order, slot);
+    mueller_status st = MUELLER_OK;
+    cudaStream_t ts = nullptr;
+    cudaError_t e = cudaSetDevice(dev);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking);
+    if (e != cudaSuccess) st = cuda_fail(e, "mesh table stream");
+    if (!st) st = upload(&m->tp, tp.data(), tp.size(), ts);
+    if (!st) st = upload(&m->near_rowptr, m->near_rowptr_h.data(), m->near_rowptr_h.size(), ts);
+    if (!st) st = upload(&m->near_col, m->near_col_h.data(), m->near_col_h.size(), ts);
+    if (!st) st = upload(&m->tp_slot, slot.data(), slot.size(), ts);
+    if (!st) st = upload(&m->tp_order, order.data(), order.size(), ts);
+    if (ts) {
+      e = cudaStreamSynchronize(ts);
+      if (!st && e != cudaSuccess) st = cuda_fail(e, "mesh table upload");
+      cudaStreamDestroy(ts);
+    }
+    m->tp_h = std::move(tp);
+    m->tp_slot_h = std::move(slot);
+    m->tables_st = st;
+    if (st) m->tables_msg = mueller_last_error();
+  });
   *out = m;
   return MUELLER_OK;
 }
 
 mueller_status mueller_mesh_get_info(const mueller_mesh* m, mueller_mesh_info* info) {
   if (!m || !info) return fail(MUELLER_ERR_INVALID_ARG, "NULL argument");
+  if (mueller_status ts_ = mesh_tables(m)) return ts_;
   info->n_nodes = m->nn;
   info->n_tri = m->nt;
   info->n_dof = 4 * m->nn;
@@ -560,6 +605,7 @@ mueller_status mueller_quadrature_rule(int32_t kind, int32_t n, double* a, doubl
 mueller_status mueller_mesh_touching(const mueller_mesh* m, int32_t* ex, int32_t* ey, int32_t* cls,
                                      int32_t* relabel) {
   if (!m) return fail(MUELLER_ERR_INVALID_ARG, "mesh is NULL");
+  if (mueller_status ts_ = mesh_tables(m)) return ts_;
   for (size_t q = 0; q < m->tp_h.size(); ++q) {
     const TouchPair& t = m->tp_h[q];
     if (ex) ex[q] = t.ex;
@@ -573,6 +619,7 @@ mueller_status mueller_mesh_touching(const mueller_mesh* m, int32_t* ex, int32_t
 mueller_status mueller_mesh_near_layout(const mueller_mesh* m, int32_t* rowptr, int32_t* col,
                                         int32_t* slot) {
   if (!m) return fail(MUELLER_ERR_INVALID_ARG, "mesh is NULL");
+  if (mueller_status ts_ = mesh_tables(m)) return ts_;
   if (rowptr) std::copy(m->near_rowptr_h.begin(), m->near_rowptr_h.end(), rowptr);
   if (col) std::copy(m->near_col_h.begin(), m->near_col_h.end(), col);
   if (slot) std::copy(m->tp_slot_h.begin(), m->tp_slot_h.end(), slot);
@@ -599,7 +646,8 @@ mueller_status mueller_tangent_frame(mueller_mesh* m, int32_t frame_rule, double
 }
 
 size_t mueller_near_bytes(const mueller_mesh* m) {
-  return m ? (size_t)m->nnzb * 16 * 2 * sizeof(double) : 0;
+  if (!m || mesh_tables(m)) return 0;
+  return (size_t)m->nnzb * 16 * 2 * sizeof(double);
 }
 
 // Incident waves: rows (k-hat, p-hat) of orthonormal real vectors; far-field
@@ -694,7 +742,6 @@ mueller_status mueller_assemble(mueller_mesh* m, const mueller_params* p, int32_
   PhysConsts P = make_phys(p);
   size_t esz = dtype == MUELLER_C128 ? 16 : 8;
   MU_CUDA(cudaMemsetAsync(Z, 0, (size_t)N * ldz * esz, s));
-  if (dtype == MUELLER_C64_NEAR64) MU_CUDA(cudaMemsetAsync(near, 0, mueller_near_bytes(m), s));
   double* inc_dev = nullptr;
   if (B) {
     MU_CUDA(cudaMemsetAsync(B, 0, (size_t)r * N * 16, s));
@@ -708,10 +755,18 @@ mueller_status mueller_assemble(mueller_mesh* m, const mueller_params* p, int32_
   if (!st) st = side_stream(&s2);
   if (!st) st = stream_order(s, s2);
   if (!st) {
-    st = launch_touching(m, P, p->q_regular, p->ssq_order, dtype, Z, ldz, near, s2);
-    const mueller_status st2 = launch_regular(m, P, p->q_regular, dtype, Z, ldz, s);
+    // the regular pairs need no host tables: they are launched before the
+    // wait for the mesh's table thread, the touching pairs (and the zeroing
+    // of the near blocks they add into) after it
+    st = launch_regular(m, P, p->q_regular, dtype, Z, ldz, s);
+    if (!st) st = mesh_tables(m);
+    if (!st && dtype == MUELLER_C64_NEAR64) {
+      cudaError_t e = cudaMemsetAsync(near, 0, mueller_near_bytes(m), s2);
+      if (e != cudaSuccess) st = cuda_fail(e, "cudaMemsetAsync(near)");
+    }
+    if (!st) st = launch_touching(m, P, p->q_regular, p->ssq_order, dtype, Z, ldz, near, s2);
     const mueller_status sj = stream_order(s2, s);
-    if (!st) st = st2 ? st2 : sj;
+    if (!st) st = sj;
   }
   if (!st) st = launch_mass_rhs(m, P, p->q_regular, dtype, Z, ldz, near, B, inc_dev, B ? r : 0, s);
   if (!st) st = launch_mirror_k1(N, dtype, Z, ldz, s);
@@ -722,6 +777,7 @@ mueller_status mueller_assemble(mueller_mesh* m, const mueller_params* p, int32_
 mueller_status mueller_dz_matvec(mueller_mesh* m, const mueller_params* p, int32_t which,
                                  const void* X, void* Y, void* stream) {
   if (!m || !X || !Y) return fail(MUELLER_ERR_INVALID_ARG, "NULL argument");
+  if (mueller_status ts_ = mesh_tables(m)) return ts_;
   mueller_status st = check_params(p);
   if (st) return st;
   if (which != 1 && which != 2) return fail(MUELLER_ERR_INVALID_ARG, "which must be 1 (eps_r) or 2 (mu_r)");
@@ -740,6 +796,7 @@ mueller_status mueller_dz_matvec(mueller_mesh* m, const mueller_params* p, int32
 mueller_status mueller_zshape_vjp(mueller_mesh* m, const mueller_params* p, const void* lam,
                                   const void* X, double* grad, void* stream) {
   if (!m || !lam || !X || !grad) return fail(MUELLER_ERR_INVALID_ARG, "NULL argument");
+  if (mueller_status ts_ = mesh_tables(m)) return ts_;
   mueller_status st = check_params(p);
   if (st) return st;
   if (m->host_only) return fail(MUELLER_ERR_STATE, kHostOnlyMsg);
@@ -755,6 +812,7 @@ mueller_status mueller_zshape_vjp(mueller_mesh* m, const mueller_params* p, cons
 mueller_status mueller_rhs_shape_vjp(mueller_mesh* m, const mueller_params* p, const void* lam,
                                      const double* inc, double* grad, void* stream) {
   if (!m || !lam || !inc || !grad) return fail(MUELLER_ERR_INVALID_ARG, "NULL argument");
+  if (mueller_status ts_ = mesh_tables(m)) return ts_;
   mueller_status st = check_params(p);
   if (st) return st;
   if ((st = check_inc(inc, 1))) return st;
@@ -773,6 +831,7 @@ mueller_status mueller_cross_section_partials(mueller_mesh* m, const mueller_par
                                               int32_t n_phi, void* G, double* grad, double* xs,
                                               void* stream) {
   if (!m || !X || !inc || !G || !grad) return fail(MUELLER_ERR_INVALID_ARG, "NULL argument");
+  if (mueller_status ts_ = mesh_tables(m)) return ts_;
   mueller_status st = check_params(p);
   if (st) return st;
   if ((st = check_inc(inc, 1))) return st;
@@ -808,6 +867,7 @@ mueller_status mueller_assemble_batch(int32_t n_bodies, mueller_mesh* const* mes
     const mueller_params* p = params + b;
     const std::string who = "body " + std::to_string(b) + ": ";
     if (!m) return fail(MUELLER_ERR_INVALID_ARG, who + "mesh is NULL");
+    if (mueller_status ts_ = mesh_tables(m)) return ts_;
     mueller_status st = check_params(p);
     if (st) return st;
     if (p->q_regular != q || p->ssq_order != ns)
@@ -860,6 +920,7 @@ size_t mueller_precond_bytes(int64_t n_dof, int64_t block) {
 mueller_status mueller_precond_build(const mueller_operator* op, int64_t block, void* P,
                                      void* stream) {
   if (!op || !op->mesh || !op->Z_dev || !P) return fail(MUELLER_ERR_INVALID_ARG, "NULL argument");
+  if (mueller_status ts_ = mesh_tables(op->mesh)) return ts_;
   if (block < 1) return fail(MUELLER_ERR_INVALID_ARG, "block must be >= 1");
   if (op->dtype == MUELLER_C64_NEAR64 && !op->near_dev)
     return fail(MUELLER_ERR_INVALID_ARG, "operator lacks its near part");
@@ -875,6 +936,7 @@ mueller_status mueller_precond_build_batch(int32_t n, const mueller_operator* op
     const std::string who = "body " + std::to_string(b) + ": ";
     const mueller_operator* op = &ops[b];
     if (!op->mesh || !op->Z_dev || !precond_dev[b]) return fail(MUELLER_ERR_INVALID_ARG, who + "NULL argument");
+    if (mueller_status ts_ = mesh_tables(op->mesh)) return ts_;
     if (blocks[b] < 1) return fail(MUELLER_ERR_INVALID_ARG, who + "block must be >= 1");
     if (op->dtype != MUELLER_C128 && op->dtype != MUELLER_C64_NEAR64)
       return fail(MUELLER_ERR_INVALID_ARG, who + "unknown operator dtype");
@@ -887,7 +949,7 @@ mueller_status mueller_precond_build_batch(int32_t n, const mueller_operator* op
 
 size_t mueller_solve_workspace_bytes(const mueller_operator* op, int32_t r,
                                      const mueller_solver_opts* o) {
-  if (!op || !o || r < 1) return 0;
+  if (!op || !o || r < 1 || (op->mesh && mesh_tables(op->mesh))) return 0;
   return solve_work(op, r, o);
 }
 
@@ -896,6 +958,7 @@ mueller_status mueller_solve(const mueller_operator* op, const void* B, void* X,
                              size_t work_bytes, void* stream) {
   if (!op || !op->mesh || !op->Z_dev || !B || !X || !o || !info)
     return fail(MUELLER_ERR_INVALID_ARG, "NULL argument");
+  if (mueller_status ts_ = mesh_tables(op->mesh)) return ts_;
   if (r < 1) return fail(MUELLER_ERR_INVALID_ARG, "r must be >= 1");
   if (o->mode < 0 || o->mode > 2) return fail(MUELLER_ERR_INVALID_ARG, "unknown solve mode");
   if (o->mode != MUELLER_SOLVE_DENSE_LU && (o->restart < 1 || o->maxit < 1 || !(o->tol > 0)))
@@ -927,6 +990,7 @@ size_t mueller_matvec_workspace_bytes(const mueller_operator* op, int32_t r) {
 mueller_status mueller_matvec(const mueller_operator* op, const void* X, void* Y, int32_t r,
                               void* work, size_t work_bytes, void* stream) {
   if (!op || !op->mesh || !op->Z_dev || !X || !Y) return fail(MUELLER_ERR_INVALID_ARG, "NULL argument");
+  if (mueller_status ts_ = mesh_tables(op->mesh)) return ts_;
   if (r < 1) return fail(MUELLER_ERR_INVALID_ARG, "r must be >= 1");
   if (op->dtype == MUELLER_C64_NEAR64 && !op->near_dev)
     return fail(MUELLER_ERR_INVALID_ARG, "operator lacks its near part");
@@ -945,6 +1009,7 @@ size_t mueller_matvec_mrhs_workspace_bytes(const mueller_operator* op, int32_t r
 mueller_status mueller_matvec_mrhs(const mueller_operator* op, const void* X, void* Y, int32_t r,
                                    void* work, size_t work_bytes, void* stream) {
   if (!op || !op->mesh || !op->Z_dev || !X || !Y) return fail(MUELLER_ERR_INVALID_ARG, "NULL argument");
+  if (mueller_status ts_ = mesh_tables(op->mesh)) return ts_;
   if (op->dtype != MUELLER_C64_NEAR64 || !op->near_dev)
     return fail(MUELLER_ERR_INVALID_ARG, "the tensor-core product needs a C64_NEAR64 operator");
   if (op->mesh->host_only) return fail(MUELLER_ERR_STATE, kHostOnlyMsg);
@@ -965,6 +1030,7 @@ mueller_status mueller_far_field(mueller_mesh* m, const mueller_params* p, const
                                  void* F, double* xs, int32_t n_theta, int32_t n_phi,
                                  void* stream) {
   if (!m || !X || !inc || !xs) return fail(MUELLER_ERR_INVALID_ARG, "NULL argument");
+  if (mueller_status ts_ = mesh_tables(m)) return ts_;
   mueller_status st = check_params(p);
   if (st) return st;
   if (r < 1 || ndir < 0 || (ndir > 0 && (!dirs || !F))) return fail(MUELLER_ERR_INVALID_ARG, "bad r/n_dir");
@@ -1024,6 +1090,7 @@ mueller_status mueller_far_field_noalloc(mueller_mesh* m, const mueller_params* 
                                          const double* dirs, int64_t ndir, void* F, double* xs,
                                          int32_t n_theta, int32_t n_phi, void* stream) {
   if (!m || !X || !inc || !xs) return fail(MUELLER_ERR_INVALID_ARG, "NULL argument");
+  if (mueller_status ts_ = mesh_tables(m)) return ts_;
   mueller_status st = check_params(p);
   if (st) return st;
   if (r < 1 || ndir < 0 || (ndir > 0 && (!dirs || !F))) return fail(MUELLER_ERR_INVALID_ARG, "bad r/n_dir");

@@ -893,28 +893,97 @@ __global__ void trsm_tile_kernel(const CT* __restrict__ A, CT* __restrict__ B, i
     if (i < w) X[(int64_t)(k0 + i) * ldb + c] = v[i];
 }
 
+// Inverses of the 32 x 32 diagonal tiles of every block's complex64 LU
+// factors (the unit lower L and the upper U), rows and columns beyond the
+// block's active size taken from the identity: CTA (tile, block, lu) with
+// thread j computing column j by substitution.  Tinv holds [nb][ntile][2]
+// tiles of 32 x 32 (row-major).
+__global__ void __launch_bounds__(32) tile_inverse_kernel(const float2* __restrict__ A, int64_t d,
+                                                          const int32_t* __restrict__ sz,
+                                                          int ntile, float2* __restrict__ Tinv) {
+  __shared__ float2 sD[32][33];
+  const int tile = blockIdx.x, b = blockIdx.y, lu = blockIdx.z;
+  const int n = sz[b], r = tile * 32;
+  if (r >= n) return;
+  const int kn = min(32, n - r);
+  const int j = threadIdx.x;
+  const float2* F = A + (int64_t)b * d * d;
+  for (int i = 0; i < 32; ++i)
+    sD[i][j] = (i < kn && j < kn) ? F[(int64_t)(r + i) * d + r + j] : make_float2(i == j ? 1.f : 0.f, 0.f);
+  __syncwarp();
+  float2 x[32];
+  if (lu == 0) {  // L (unit lower)
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      float2 a = make_float2(i == j ? 1.f : 0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < i; ++k) {
+        const float2 l = sD[i][k];
+        a.x -= l.x * x[k].x - l.y * x[k].y;
+        a.y -= l.x * x[k].y + l.y * x[k].x;
+      }
+      x[i] = a;
+    }
+  } else {  // U (upper)
+#pragma unroll
+    for (int i = 31; i >= 0; --i) {
+      float2 a = make_float2(i == j ? 1.f : 0.f, 0.f);
+#pragma unroll
+      for (int k = i + 1; k < 32; ++k) {
+        const float2 u = sD[i][k];
+        a.x -= u.x * x[k].x - u.y * x[k].y;
+        a.y -= u.x * x[k].y + u.y * x[k].x;
+      }
+      x[i] = cdivT(a, sD[i][i]);
+    }
+  }
+  float2* O = Tinv + (((int64_t)b * ntile + tile) * 2 + lu) * 1024;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) O[i * 32 + j] = x[i];
+}
+
 // Explicit inverses of the blocks from their complex64 LU factors (unit
-// lower L and upper U in A, the row swaps in piv) in one launch.  CTA
-// (x, b) computes the CW columns j0 = x CW .. j0 + CW - 1 of
-// M = U^{-1} L^{-1} of block b, i.e. solves L U m_j = e_j, by forward and
-// back substitution in tiles of 32 rows.  Thread t holds rows t, t + 512, ..
-// (RPT of them) of those columns in registers.  Per tile: the tile's rows go
-// to shared memory, where warp w finishes column w of them (lanes over the
-// rows, the substitution within the 32 x 32 diagonal tile by shuffles);
-// then every row outside the tile subtracts the tile's contribution, its
-// factor entries read as 16-byte loads.  Column j of L^{-1} is zero above
-// row j, so the forward pass starts at the tile of the CTA's first column.
-// With P e_c = e_pi(c) for the recorded swaps (P A = L U), the inverse
-// U^{-1} L^{-1} P has column c equal to column pi(c) of M.
+// lower L and upper U in A, the row swaps in piv, the diagonal tiles'
+// inverses in Tinv) in one launch.  CTA (x, b) computes the CW columns
+// j0 = x CW .. j0 + CW - 1 of M = U^{-1} L^{-1} of block b, i.e. solves
+// L U m_j = e_j, by forward and back substitution in tiles of 32 rows.
+// Thread t holds rows t, t + 512, .. (RPT of them) of those columns in
+// registers.  Per tile: the tile's rows go to shared memory and are
+// multiplied by the inverse of the diagonal tile (thread (lane, warp) gives
+// row lane of column warp); then every row outside the tile subtracts the
+// tile's contribution, its factor entries read as 16-byte loads.  Column j of
+// L^{-1} is zero above row j, so the forward pass starts at the tile of the
+// CTA's first column.  With P e_c = e_pi(c) for the recorded swaps
+// (P A = L U), the inverse U^{-1} L^{-1} P has column c equal to column
+// pi(c) of M.
 constexpr int kInvCW = 16;        // columns of M per CTA (= warps per CTA)
 constexpr int kInvThreads = 512;  // 32 * kInvCW
+
+// the tile after (pass, tile): forward tiles up to the last, then backward
+__device__ __forceinline__ bool tile_after(int& pass, int& tile, int ntile) {
+  if (pass == 0) {
+    if (tile + 1 < ntile) {
+      ++tile;
+    } else {
+      pass = 1;
+      tile = ntile - 1;
+    }
+    return true;
+  }
+  if (tile == 0) return false;
+  --tile;
+  return true;
+}
+
 template <int RPT>
 __global__ void __launch_bounds__(kInvThreads, RPT == 1 ? 2 : 1) block_inverse_cols_kernel(
     const float2* __restrict__ A, int64_t d, const int32_t* __restrict__ sz,
-    const int32_t* __restrict__ piv, float2* __restrict__ inv) {
+    const int32_t* __restrict__ piv, const float2* __restrict__ Tinv, int ntile_max,
+    float2* __restrict__ inv) {
   constexpr int CW = kInvCW;
-  __shared__ __align__(16) float2 sT[32][CW];  // the current tile's rows
-  __shared__ float2 sD[32][33];                // its diagonal block of L or U
+  __shared__ __align__(16) float2 sT[32][CW];   // the tile's rows
+  __shared__ __align__(16) float2 sT2[32][CW];  // the same, finished
+  __shared__ float2 sD[32][33];                 // inverse of the diagonal tile
   __shared__ int sPiv[kInvThreads * RPT];
   __shared__ int sTarget[CW];
   const int b = blockIdx.y;
@@ -923,8 +992,20 @@ __global__ void __launch_bounds__(kInvThreads, RPT == 1 ? 2 : 1) block_inverse_c
   if (j0 >= n) return;  // uniform over the CTA
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const float2* F = A + (int64_t)b * d * d;
+  const float2* TI = Tinv + (int64_t)b * ntile_max * 2 * 1024;
   for (int k = t; k < n; k += kInvThreads) sPiv[k] = piv[(int64_t)b * d + k];
   if (t < CW) sTarget[t] = -1;
+  const int ntile = (n + 31) / 32;
+  float2 dg[2];
+  // two entries of the diagonal inverse of tile (pass, tile), loaded one
+  // tile ahead
+  auto fetch = [&](int pass, int tile) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+      dg[h] = __ldg(TI + ((int64_t)tile * 2 + pass) * 1024 + t + h * kInvThreads);
+  };
+  int pass = 0, tile = j0 / 32;
+  fetch(pass, tile);
   __syncthreads();
   // targets: the inverse's column c with pi(c) = j0 + jj
   for (int c = t; c < n; c += kInvThreads) {
@@ -941,92 +1022,76 @@ __global__ void __launch_bounds__(kInvThreads, RPT == 1 ? 2 : 1) block_inverse_c
 #pragma unroll
     for (int jj = 0; jj < CW; ++jj)
       x[q][jj] = make_float2(t + q * kInvThreads == j0 + jj ? 1.f : 0.f, 0.f);
-  const int ntile = (n + 31) / 32;
-  for (int pass = 0; pass < 2; ++pass) {
+  for (;;) {
     const bool lower = pass == 0;
-    const int t_first = lower ? j0 / 32 : ntile - 1;
-    const int t_end = lower ? ntile : -1;
-    const int t_step = lower ? 1 : -1;
-    for (int tile = t_first; tile != t_end; tile += t_step) {
-      const int r = tile * 32;
-      const int kn = min(32, n - r);
-      const int ow = (r % kInvThreads) / 32, oq = r / kInvThreads;  // owner warp, slot
-      // 1. the tile's rows to sT, its diagonal block to sD (identity outside n)
-      if (warp == ow) {
+    const int r = tile * 32, kn = min(32, n - r);
+    const int ow = (r % kInvThreads) / 32, oq = r / kInvThreads;  // owner warp, slot
+    // 1. the tile's rows and the diagonal tile's inverse to shared memory
+    if (warp == ow) {
 #pragma unroll
-        for (int q = 0; q < RPT; ++q)
-          if (q == oq) {
+      for (int q = 0; q < RPT; ++q)
+        if (q == oq) {
 #pragma unroll
-            for (int jj = 0; jj < CW; ++jj) sT[lane][jj] = x[q][jj];
-          }
-      }
-      for (int e = t; e < 32 * 32; e += kInvThreads) {
-        const int i = e / 32, k = e % 32;
-        sD[i][k] = (i < kn && k < kn) ? F[(int64_t)(r + i) * d + r + k]
-                                      : make_float2(i == k ? 1.f : 0.f, 0.f);
-      }
-      __syncthreads();
-      // 2. the diagonal block: warp w finishes column w (lane = row)
-      {
-        float2 v = sT[lane][warp];
-        if (lower) {
-          for (int k = 0; k < 31; ++k) {
-            const float vx = __shfl_sync(0xffffffffu, v.x, k), vy = __shfl_sync(0xffffffffu, v.y, k);
-            if (lane > k) {
-              const float2 l = sD[lane][k];
-              v.x -= l.x * vx - l.y * vy;
-              v.y -= l.x * vy + l.y * vx;
-            }
-          }
-        } else {
-          for (int k = 31; k >= 0; --k) {
-            if (lane == k) v = cdivT(v, sD[k][k]);
-            const float vx = __shfl_sync(0xffffffffu, v.x, k), vy = __shfl_sync(0xffffffffu, v.y, k);
-            if (lane < k) {
-              const float2 u = sD[lane][k];
-              v.x -= u.x * vx - u.y * vy;
-              v.y -= u.x * vy + u.y * vx;
-            }
-          }
+          for (int jj = 0; jj < CW; ++jj) sT[lane][jj] = x[q][jj];
         }
-        sT[lane][warp] = v;
-      }
-      __syncthreads();
-      // 3. the tile's rows back to their owner; every other row subtracts
-      //    F[row, r:r+kn) times the tile (rows below for L, above for U)
-#pragma unroll
-      for (int q = 0; q < RPT; ++q) {
-        const int row = t + q * kInvThreads;
-        if (row >= n) continue;
-        if (row >= r && row < r + 32) {
-#pragma unroll
-          for (int jj = 0; jj < CW; ++jj) x[q][jj] = sT[row - r][jj];
-          continue;
-        }
-        if (lower ? row < r + 32 : row >= r) continue;
-        const float4* f4 = reinterpret_cast<const float4*>(F + (int64_t)row * d + r);
-#pragma unroll 2
-        for (int k2 = 0; k2 < 16; ++k2) {
-          if (2 * k2 >= kn) break;
-          const float4 ff = __ldg(f4 + k2);  // entries k = 2 k2, 2 k2 + 1
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int k = 2 * k2 + h;
-            const float fx = h ? ff.z : ff.x, fy = h ? ff.w : ff.y;
-            const float4* tk = reinterpret_cast<const float4*>(&sT[k][0]);
-#pragma unroll
-            for (int j2 = 0; j2 < CW / 2; ++j2) {
-              const float4 tv = tk[j2];
-              x[q][2 * j2].x -= fx * tv.x - fy * tv.y;
-              x[q][2 * j2].y -= fx * tv.y + fy * tv.x;
-              x[q][2 * j2 + 1].x -= fx * tv.z - fy * tv.w;
-              x[q][2 * j2 + 1].y -= fx * tv.w + fy * tv.z;
-            }
-          }
-        }
-      }
-      __syncthreads();  // before the next tile overwrites sT and sD
     }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int e = t + h * kInvThreads;
+      sD[e / 32][e % 32] = dg[h];
+    }
+    __syncthreads();
+    // 2. finished rows: row lane of column warp of (diagonal tile)^-1 sT
+    {
+      float2 v = make_float2(0.f, 0.f);
+#pragma unroll 8
+      for (int k = 0; k < 32; ++k) {
+        const float2 a = sD[lane][k], xk = sT[k][warp];
+        v.x += a.x * xk.x - a.y * xk.y;
+        v.y += a.x * xk.y + a.y * xk.x;
+      }
+      sT2[lane][warp] = v;
+    }
+    __syncthreads();
+    // 3. the tile's rows back to their owners; the rows below (L) or above
+    //    (U) subtract F[row, r:r+kn) times the tile
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int row = t + q * kInvThreads;
+      if (row >= n) continue;
+      if (row >= r && row < r + 32) {
+#pragma unroll
+        for (int jj = 0; jj < CW; ++jj) x[q][jj] = sT2[row - r][jj];
+        continue;
+      }
+      if (lower ? row < r + 32 : row >= r) continue;
+      const float4* f4 = reinterpret_cast<const float4*>(F + (int64_t)row * d + r);
+#pragma unroll
+      for (int k2 = 0; k2 < 16; ++k2) {
+        if (2 * k2 >= kn) break;
+        const float4 ff = __ldg(f4 + k2);  // entries k = 2 k2, 2 k2 + 1
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int k = 2 * k2 + h;
+          if (k >= kn) break;
+          const float fx = h ? ff.z : ff.x, fy = h ? ff.w : ff.y;
+          const float4* tk = reinterpret_cast<const float4*>(&sT2[k][0]);
+#pragma unroll
+          for (int j2 = 0; j2 < CW / 2; ++j2) {
+            const float4 tv = tk[j2];
+            x[q][2 * j2].x -= fx * tv.x - fy * tv.y;
+            x[q][2 * j2].y -= fx * tv.y + fy * tv.x;
+            x[q][2 * j2 + 1].x -= fx * tv.z - fy * tv.w;
+            x[q][2 * j2 + 1].y -= fx * tv.w + fy * tv.z;
+          }
+        }
+      }
+    }
+    // the next tile's diagonal inverse, in flight across the barrier
+    const bool more = tile_after(pass, tile, ntile);
+    if (more) fetch(pass, tile);
+    __syncthreads();  // before the next tile overwrites sT, sT2 and sD
+    if (!more) break;
   }
   float2* O = inv + (int64_t)b * d * d;
 #pragma unroll
@@ -1119,6 +1184,7 @@ __global__ void lu_swap_trsm_kernel(double2* __restrict__ A, int64_t d,
                                     const int32_t* __restrict__ sz, int k0,
                                     const int32_t* __restrict__ piv) {
   __shared__ double2 T[W][W];
+  __shared__ double Ts[W][W];
   const int b = blockIdx.y;
   const int n = sz[b];
   if (k0 >= n) return;
@@ -1127,7 +1193,9 @@ __global__ void lu_swap_trsm_kernel(double2* __restrict__ A, int64_t d,
   double2* M = A + (int64_t)b * d * d;
   for (int e = threadIdx.x; e < W * W; e += blockDim.x) {
     const int i = e / W, j = e % W;
-    T[i][j] = (i < w && j < w) ? M[(int64_t)(k0 + i) * d + k0 + j] : make_double2(0.0, 0.0);
+    const double2 l = (i < w && j < w) ? M[(int64_t)(k0 + i) * d + k0 + j] : make_double2(0.0, 0.0);
+    T[i][j] = l;
+    Ts[i][j] = l.x + l.y;
   }
   __syncthreads();
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1142,17 +1210,27 @@ __global__ void lu_swap_trsm_kernel(double2* __restrict__ A, int64_t d,
     }
   }
   if (c < k0 + w) return;
+  // forward substitution with the 3M products (tile3m_update): the sums of
+  // v[j] are formed once it is final, those of L in shared memory
   double2 v[W];
+  double vs[W];
 #pragma unroll
   for (int i = 0; i < W; ++i) v[i] = i < w ? M[(int64_t)(k0 + i) * d + c] : make_double2(0.0, 0.0);
+  vs[0] = v[0].x + v[0].y;
 #pragma unroll
-  for (int i = 1; i < W; ++i)
+  for (int i = 1; i < W; ++i) {
+    double pxx = 0.0, pyy = 0.0, pss = 0.0;
 #pragma unroll
     for (int j = 0; j < i; ++j) {
       const double2 l = T[i][j];
-      v[i].x -= l.x * v[j].x - l.y * v[j].y;
-      v[i].y -= l.x * v[j].y + l.y * v[j].x;
+      pxx = fma(l.x, v[j].x, pxx);
+      pyy = fma(l.y, v[j].y, pyy);
+      pss = fma(Ts[i][j], vs[j], pss);
     }
+    v[i].x -= pxx - pyy;
+    v[i].y -= pss - pxx - pyy;
+    vs[i] = v[i].x + v[i].y;
+  }
 #pragma unroll
   for (int i = 0; i < W; ++i)
     if (i < w) M[(int64_t)(k0 + i) * d + c] = v[i];
@@ -2380,7 +2458,9 @@ static mueller_status batched_lu_inverse(CT* A, int64_t d, int nb, const int32_t
   }
   if (!st) st = lu_panel(A, d, nb, sz_dev, 0, piv, status, 1, s);
   for (int k0 = 0, step = 0; !st && k0 < d; k0 += LUW, ++step) {
-    { Prof prof_("lu_swap_trsm_kernel", s); lu_swap_trsm_kernel<LUW><<<dim3(nblk(d, 128), nb), 128, 0, s>>>(A, d, sz_dev, k0, piv); }
+    // one warp per 32 columns: the FP64 work of the triangular solves spreads
+    // over all SMs
+    { Prof prof_("lu_swap_trsm_kernel", s); lu_swap_trsm_kernel<LUW><<<dim3(nblk(d, 32), nb), 32, 0, s>>>(A, d, sz_dev, k0, piv); }
     MU_CHECK_LAUNCH("lu_swap_trsm_kernel");
     const int k1 = k0 + LUW;
     if (k1 >= d) break;
@@ -2419,16 +2499,23 @@ template <class CT>
 static mueller_status block_inverse(const CT* A, int64_t d, int nb, const int32_t* sz_dev,
                                     const int32_t* piv, CT* inv, cudaStream_t s) {
   if constexpr (std::is_same<CT, float2>::value) {
-    if (d <= 2 * kInvThreads) {  // one launch (block_inverse_cols_kernel)
-      const dim3 grid((unsigned)nblk(d, kInvCW), (unsigned)nb);
-      {
+    if (d <= 2 * kInvThreads) {  // diagonal tiles' inverses, then one launch for the rest
+      const int ntile = (int)nblk(d, 32);
+      float2* Tinv = nullptr;
+      MU_CUDA(cudaMallocAsync((void**)&Tinv, (size_t)nb * ntile * 2 * 1024 * sizeof(float2), s));
+      { Prof prof_("tile_inverse_kernel", s); tile_inverse_kernel<<<dim3(ntile, nb, 2), 32, 0, s>>>(A, d, sz_dev, ntile, Tinv); }
+      cudaError_t le = cudaGetLastError();
+      if (le == cudaSuccess) {
+        const dim3 grid((unsigned)nblk(d, kInvCW), (unsigned)nb);
         Prof prof_("block_inverse_cols_kernel", s);
         if (d <= kInvThreads)
-          block_inverse_cols_kernel<1><<<grid, kInvThreads, 0, s>>>(A, d, sz_dev, piv, inv);
+          block_inverse_cols_kernel<1><<<grid, kInvThreads, 0, s>>>(A, d, sz_dev, piv, Tinv, ntile, inv);
         else
-          block_inverse_cols_kernel<2><<<grid, kInvThreads, 0, s>>>(A, d, sz_dev, piv, inv);
+          block_inverse_cols_kernel<2><<<grid, kInvThreads, 0, s>>>(A, d, sz_dev, piv, Tinv, ntile, inv);
+        le = cudaGetLastError();
       }
-      MU_CHECK_LAUNCH("block_inverse_cols_kernel");
+      cudaFreeAsync(Tinv, s);
+      if (le != cudaSuccess) return cuda_fail(le, "block inverse kernels");
       return MUELLER_OK;
     }
   }
