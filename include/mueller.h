@@ -401,7 +401,11 @@ size_t mueller_near_bytes(const mueller_mesh* mesh);
  * ceil((N/2)/block) contiguous clusters I_m (the last one smaller); block m
  * is the 2|I_m| x 2|I_m| restriction of the operator to I_m in both halves
  * (all four quadrants).  Each block is factorised by LU with partial
- * pivoting in FP64 and stored as its explicit inverse (complex128).
+ * pivoting in FP64 and stored as its explicit inverse: complex128 for a
+ * C128 operator, complex64 (formed from the FP64 factors) for a
+ * C64_NEAR64 operator.  Layout: the inverses [nb][d][d] row-major,
+ * d = 2 min(block, N/2), entries beyond a block's own size zero; then the
+ * nb block sizes (int32).
  *   precond_dev  caller-owned, mueller_precond_bytes(N, block) bytes.
  *   status_dev   optional device int32: set to the first singular block + 1.
  * The operator's precond_dev/block fields are ignored.

@@ -453,6 +453,22 @@ __device__ __forceinline__ CT cdivT(CT a, CT b) {
   const auto den = b.x * b.x + b.y * b.y;
   return CT{(a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den};
 }
+// a -= b c and a += b c (complex) as four multiply-adds: written out, the
+// compiler would form each part as a product, a multiply-add and an addition
+template <class CT>
+__device__ __forceinline__ void cfms(CT& a, CT b, CT c) {
+  a.x = fma(-b.x, c.x, a.x);
+  a.x = fma(b.y, c.y, a.x);
+  a.y = fma(-b.x, c.y, a.y);
+  a.y = fma(-b.y, c.x, a.y);
+}
+template <class CT>
+__device__ __forceinline__ void cfma(CT& a, CT b, CT c) {
+  a.x = fma(b.x, c.x, a.x);
+  a.x = fma(-b.y, c.y, a.x);
+  a.y = fma(b.x, c.y, a.y);
+  a.y = fma(b.y, c.x, a.y);
+}
 __device__ __forceinline__ double2 cdiv2(double2 a, double2 b) {
   const double den = b.x * b.x + b.y * b.y;
   return make_double2((a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den);
@@ -527,8 +543,7 @@ __global__ void __launch_bounds__(256) lu_panel_kernel(CT* __restrict__ A, int64
       for (int j = k + 1; j < kend; ++j) {
         const CT u = M[(int64_t)k * d + j];
         CT a = M[(int64_t)i * d + j];
-        a.x -= l.x * u.x - l.y * u.y;
-        a.y -= l.x * u.y + l.y * u.x;
+        cfms(a, l, u);
         M[(int64_t)i * d + j] = a;
       }
     }
@@ -638,8 +653,7 @@ __device__ __forceinline__ void lu_panel_smem_body(CT* __restrict__ A, int64_t d
       row[k] = l;
       for (int j = k + 1; j < w; ++j) {
         const CT u = prow[j];
-        row[j].x -= l.x * u.x - l.y * u.y;
-        row[j].y -= l.x * u.y + l.y * u.x;
+        cfms(row[j], l, u);
       }
     }
     panel_bar(nthr);
@@ -682,21 +696,21 @@ __global__ void __launch_bounds__(1024) lu_panel_smem_kernel(CT* __restrict__ A,
 // staged entry.  Its rounding error is bounded like that of the usual form
 // up to a small constant (normwise; Higham, Accuracy and Stability of
 // Numerical Algorithms, Sec. 23.2.4).
-template <int W, int TN>
+template <int W, int TN, int TR = 32>
 struct Tile3M {
-  double2 a[32][W + 1];
-  double as[32][W + 1];
+  double2 a[TR][W + 1];
+  double as[TR][W + 1];
   double2 b[W][TN + 1];
   double bs[W][TN + 1];
 };
 
-// stage the tile with rows [tr, tr + 32), columns [tc, tc + TN) of block M
+// stage the tile with rows [tr, tr + TR), columns [tc, tc + TN) of block M
 // (active size n, columns below c1, panel width w); GT threads, lt = rank
-template <int W, int TN, int GT>
-__device__ __forceinline__ void tile3m_load(Tile3M<W, TN>& T, const double2* __restrict__ M,
+template <int W, int TN, int GT, int TR = 32>
+__device__ __forceinline__ void tile3m_load(Tile3M<W, TN, TR>& T, const double2* __restrict__ M,
                                             int64_t d, int64_t tr, int64_t tc, int k0, int n,
                                             int64_t c1, int w, int lt) {
-  for (int t = lt; t < 32 * W; t += GT) {
+  for (int t = lt; t < TR * W; t += GT) {
     const int i = t / W, k = t % W;
     const int64_t gr = tr + i;
     const double2 v = (gr < n && k < w) ? M[gr * d + k0 + k] : make_double2(0.0, 0.0);
@@ -712,25 +726,25 @@ __device__ __forceinline__ void tile3m_load(Tile3M<W, TN>& T, const double2* __r
   }
 }
 
-// C -= A B for the staged tile: thread lt owns rows ty + 8 i (i < 4) and
-// columns tx + (TN / JN) j (j < JN) of the tile, 8 * TN / JN threads
-template <int W, int TN, int JN>
-__device__ __forceinline__ void tile3m_update(const Tile3M<W, TN>& T, double2* __restrict__ M,
+// C -= A B for the staged tile: thread lt owns rows ty + 8 i (i < TR / 8)
+// and columns tx + (TN / JN) j (j < JN) of the tile, 8 * TN / JN threads
+template <int W, int TN, int JN, int TR = 32>
+__device__ __forceinline__ void tile3m_update(const Tile3M<W, TN, TR>& T, double2* __restrict__ M,
                                               int64_t d, int64_t tr, int64_t tc, int n,
                                               int64_t c1, int lt) {
-  constexpr int CX = TN / JN;
+  constexpr int CX = TN / JN, RI = TR / 8;
   const int ty = lt / CX, tx = lt % CX;
-  double pxx[4][JN], pyy[4][JN], pss[4][JN];
+  double pxx[RI][JN], pyy[RI][JN], pss[RI][JN];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < RI; ++i)
 #pragma unroll
     for (int j = 0; j < JN; ++j) pxx[i][j] = pyy[i][j] = pss[i][j] = 0.0;
 #pragma unroll 4
   for (int k = 0; k < W; ++k) {
-    double2 av[4], bv[JN];
-    double as[4], bs[JN];
+    double2 av[RI], bv[JN];
+    double as[RI], bs[JN];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < RI; ++i) {
       av[i] = T.a[ty + 8 * i][k];
       as[i] = T.as[ty + 8 * i][k];
     }
@@ -740,7 +754,7 @@ __device__ __forceinline__ void tile3m_update(const Tile3M<W, TN>& T, double2* _
       bs[j] = T.bs[k][tx + CX * j];
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < RI; ++i)
 #pragma unroll
       for (int j = 0; j < JN; ++j) {
         pxx[i][j] = fma(av[i].x, bv[j].x, pxx[i][j]);
@@ -749,7 +763,7 @@ __device__ __forceinline__ void tile3m_update(const Tile3M<W, TN>& T, double2* _
       }
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < RI; ++i)
 #pragma unroll
     for (int j = 0; j < JN; ++j) {
       const int64_t gr = tr + ty + 8 * i, gc = tc + tx + CX * j;
@@ -871,8 +885,7 @@ __global__ void trsm_tile_kernel(const CT* __restrict__ A, CT* __restrict__ B, i
 #pragma unroll
       for (int j = 0; j < i; ++j) {
         const CT l = T[i][j];
-        v[i].x -= l.x * v[j].x - l.y * v[j].y;
-        v[i].y -= l.x * v[j].y + l.y * v[j].x;
+        cfms(v[i], l, v[j]);
       }
   } else {
 #pragma unroll
@@ -881,8 +894,7 @@ __global__ void trsm_tile_kernel(const CT* __restrict__ A, CT* __restrict__ B, i
 #pragma unroll
         for (int j = i + 1; j < W; ++j) {
           const CT u = T[i][j];
-          v[i].x -= u.x * v[j].x - u.y * v[j].y;
-          v[i].y -= u.x * v[j].y + u.y * v[j].x;
+          cfms(v[i], u, v[j]);
         }
         v[i] = cdivT(v[i], T[i][i]);
       }
@@ -919,8 +931,7 @@ __global__ void __launch_bounds__(32) tile_inverse_kernel(const float2* __restri
 #pragma unroll
       for (int k = 0; k < i; ++k) {
         const float2 l = sD[i][k];
-        a.x -= l.x * x[k].x - l.y * x[k].y;
-        a.y -= l.x * x[k].y + l.y * x[k].x;
+        cfms(a, l, x[k]);
       }
       x[i] = a;
     }
@@ -931,8 +942,7 @@ __global__ void __launch_bounds__(32) tile_inverse_kernel(const float2* __restri
 #pragma unroll
       for (int k = i + 1; k < 32; ++k) {
         const float2 u = sD[i][k];
-        a.x -= u.x * x[k].x - u.y * x[k].y;
-        a.y -= u.x * x[k].y + u.y * x[k].x;
+        cfms(a, u, x[k]);
       }
       x[i] = cdivT(a, sD[i][i]);
     }
@@ -1047,8 +1057,7 @@ __global__ void __launch_bounds__(kInvThreads, RPT == 1 ? 2 : 1) block_inverse_c
 #pragma unroll 8
       for (int k = 0; k < 32; ++k) {
         const float2 a = sD[lane][k], xk = sT[k][warp];
-        v.x += a.x * xk.x - a.y * xk.y;
-        v.y += a.x * xk.y + a.y * xk.x;
+        cfma(v, a, xk);
       }
       sT2[lane][warp] = v;
     }
@@ -1079,10 +1088,9 @@ __global__ void __launch_bounds__(kInvThreads, RPT == 1 ? 2 : 1) block_inverse_c
 #pragma unroll
           for (int j2 = 0; j2 < CW / 2; ++j2) {
             const float4 tv = tk[j2];
-            x[q][2 * j2].x -= fx * tv.x - fy * tv.y;
-            x[q][2 * j2].y -= fx * tv.y + fy * tv.x;
-            x[q][2 * j2 + 1].x -= fx * tv.z - fy * tv.w;
-            x[q][2 * j2 + 1].y -= fx * tv.w + fy * tv.z;
+            const float2 f2 = make_float2(fx, fy);
+            cfms(x[q][2 * j2], f2, make_float2(tv.x, tv.y));
+            cfms(x[q][2 * j2 + 1], f2, make_float2(tv.z, tv.w));
           }
         }
       }
@@ -1178,11 +1186,14 @@ __global__ void __launch_bounds__(256) gemm_update_kernel(const CT* __restrict__
 // After panel [k0, k0+W) is factored: its row swaps (recorded in piv, in
 // order) applied to every column outside the panel, and for the columns
 // right of it the row panel of U, U12 = L11^{-1} A12 (L11 unit lower from
-// the panel).  One thread per column.
+// the panel).  One thread per column, one warp per CTA (the FP64 work of
+// the solves spreads over all SMs).  (Composing the swaps into one gather of
+// the at most 2W rows they reach, per warp, made the kernel slower: 34 vs
+// 27 us per launch at level 3.)
 template <int W>
-__global__ void lu_swap_trsm_kernel(double2* __restrict__ A, int64_t d,
-                                    const int32_t* __restrict__ sz, int k0,
-                                    const int32_t* __restrict__ piv) {
+__global__ void __launch_bounds__(32) lu_swap_trsm_kernel(double2* __restrict__ A, int64_t d,
+                                                          const int32_t* __restrict__ sz, int k0,
+                                                          const int32_t* __restrict__ piv) {
   __shared__ double2 T[W][W];
   __shared__ double Ts[W][W];
   const int b = blockIdx.y;
@@ -1237,32 +1248,32 @@ __global__ void lu_swap_trsm_kernel(double2* __restrict__ A, int64_t d,
 }
 
 // FP64 trailing update of the block LU: A[r0:n, c0:c1) -= A[r0:n, k0:k0+w)
-// A[k0:k0+w, c0:c1), r0 = k0 + W, over all blocks.  32 x TN output tiles,
-// 64 threads with 4 x TN/8 outputs each (3M products, tile3m_update); CTAs
+// A[k0:k0+w, c0:c1), r0 = k0 + W, over all blocks.  TR x TN output tiles,
+// 64 threads with TR/8 x TN/8 outputs each (3M products, tile3m_update); CTAs
 // stride over the tiles when the grid is smaller than the tile count.  The
 // FP64 pipe (two DFMA per clock per SM) bounds every tile shape, so small
 // tiles cost nothing and mask less of the late, narrow updates.
-template <int W, int TN>
+template <int W, int TN, int TR>
 __global__ void __launch_bounds__(64) lu_update_kernel(double2* __restrict__ A, int64_t d,
                                                        const int32_t* __restrict__ sz, int k0,
                                                        int64_t c0, int64_t c1_cap, int nb) {
   const int64_t r0 = k0 + W;
   const int64_t cend = c1_cap < 0 ? d : c1_cap;
-  const int64_t rt_n = (d - r0 + 31) / 32, ct_n = (cend - c0 + TN - 1) / TN;
+  const int64_t rt_n = (d - r0 + TR - 1) / TR, ct_n = (cend - c0 + TN - 1) / TN;
   const int64_t per_b = rt_n * ct_n, tiles = (int64_t)nb * per_b;
-  __shared__ Tile3M<W, TN> T;
+  __shared__ Tile3M<W, TN, TR> T;
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int b = (int)(tile / per_b);
     const int64_t rem = tile - (int64_t)b * per_b;
     const int n = sz[b];
     const int64_t c1 = mn64(cend, n);
-    const int64_t tr = r0 + (rem / ct_n) * 32, tc = c0 + (rem % ct_n) * TN;
+    const int64_t tr = r0 + (rem / ct_n) * TR, tc = c0 + (rem % ct_n) * TN;
     if (k0 >= n || tr >= n || tc >= c1) continue;  // uniform over the CTA
     const int w = min(W, n - k0);
     double2* M = A + (int64_t)b * d * d;
-    tile3m_load<W, TN, 64>(T, M, d, tr, tc, k0, n, c1, w, threadIdx.x);
+    tile3m_load<W, TN, 64, TR>(T, M, d, tr, tc, k0, n, c1, w, threadIdx.x);
     __syncthreads();
-    tile3m_update<W, TN, TN / 8>(T, M, d, tr, tc, n, c1, threadIdx.x);
+    tile3m_update<W, TN, TN / 8, TR>(T, M, d, tr, tc, n, c1, threadIdx.x);
     __syncthreads();  // before the next tile's loads overwrite the staging
   }
 }
@@ -2414,13 +2425,13 @@ static mueller_status lu_panel(double2* A, int64_t d, int nb, const int32_t* sz_
 // persistent CTAs per SM, which leaves room for the panel beside it, was
 // slower: the panel then shares its SM's FP64 pipe and the chain of panels
 // becomes the critical path.)
-template <int TN>
+template <int TN, int TR = 32>
 static mueller_status lu_update(double2* A, int64_t d, int nb, const int32_t* sz_dev, int k0,
                                 int64_t c0, int64_t c1, cudaStream_t s) {
   const int64_t rows = d - (k0 + LUW), cols = (c1 < 0 ? d : c1) - c0;
   if (rows <= 0 || cols <= 0) return MUELLER_OK;
-  const int64_t grid = nb * nblk(rows, 32) * nblk(cols, TN);
-  { Prof prof_("lu_update_kernel", s); lu_update_kernel<LUW, TN><<<(unsigned)grid, 64, 0, s>>>(A, d, sz_dev, k0, c0, c1, nb); }
+  const int64_t grid = nb * nblk(rows, TR) * nblk(cols, TN);
+  { Prof prof_("lu_update_kernel", s); lu_update_kernel<LUW, TN, TR><<<(unsigned)grid, 64, 0, s>>>(A, d, sz_dev, k0, c0, c1, nb); }
   MU_CHECK_LAUNCH("lu_update_kernel");
   return MUELLER_OK;
 }
@@ -2467,7 +2478,7 @@ static mueller_status batched_lu_inverse(CT* A, int64_t d, int nb, const int32_t
     // the next panel's columns first, alone on the GPU: FP64-bound CTAs that
     // share an SM slow down together, so next to the bulk update this small
     // update would last as long as the bulk update and hold the panel back
-    st = lu_update<LUW>(A, d, nb, sz_dev, k0, k1, k1 + LUW, s);
+    st = lu_update<LUW, 16>(A, d, nb, sz_dev, k0, k1, k1 + LUW, s);
     if (st) break;
     if (d - k1 <= kLuStepThreads) {
       // panel k1 and the rest of update k0 in one launch, on separate SMs
@@ -2498,6 +2509,9 @@ static mueller_status batched_lu_inverse(CT* A, int64_t d, int nb, const int32_t
 template <class CT>
 static mueller_status block_inverse(const CT* A, int64_t d, int nb, const int32_t* sz_dev,
                                     const int32_t* piv, CT* inv, cudaStream_t s) {
+  // entries outside a block's active size are zero (the kernels below write
+  // the active part only)
+  MU_CUDA(cudaMemsetAsync(inv, 0, (size_t)nb * d * d * sizeof(CT), s));
   if constexpr (std::is_same<CT, float2>::value) {
     if (d <= 2 * kInvThreads) {  // diagonal tiles' inverses, then one launch for the rest
       const int ntile = (int)nblk(d, 32);
