@@ -352,6 +352,21 @@ mueller_status mueller_zshape_vjp(mueller_mesh* mesh, const mueller_params* para
                                   void* stream);
 
 /*
+ * mueller_zshape_vjp_multi -- mueller_zshape_vjp for r adjoint vectors at
+ * once (the gradients of several outputs at one solution x): the regular-pair
+ * and remainder passes evaluate each point pair's radial functions once for
+ * up to three of them.
+ *   lam_dev  complex128, r x N (vector o at lam_dev + o N); read only.
+ *   r        >= 1.
+ *   grad     host, r x n_nodes x 3 (vector o's gradient at grad + 3 o n_nodes),
+ *            the node order of the mesh's input; overwritten.  Synchronising.
+ * Errors: as mueller_zshape_vjp, and INVALID_ARG for r < 1.
+ */
+mueller_status mueller_zshape_vjp_multi(mueller_mesh* mesh, const mueller_params* params,
+                                        const void* lam_dev, int32_t r, const void* X_dev,
+                                        double* grad, void* stream);
+
+/*
  * mueller_rhs_shape_vjp -- the gradient of Re lam^H b(X) with respect to
  * the node coordinates X, b the plane-wave right-hand side of Eqs. (rhs_E),
  * (rhs_H) for the incident wave inc (host, 6: k-hat, p-hat, orthonormal):

@@ -29,6 +29,7 @@ from .api import (  # noqa: F401
     assemble_batch,
     dz_matvec,
     zshape_vjp,
+    zshape_vjp_multi,
     rhs_shape_vjp,
     cross_section_partials,
     far_field,

@@ -84,7 +84,8 @@ EXPORTS = [
     "mueller_profile_enable", "mueller_profile_reset", "mueller_launch_count",
     "mueller_profile_get", "mueller_profile_names", "mueller_far_field_noalloc",
     "mueller_matvec_mrhs", "mueller_matvec_mrhs_workspace_bytes", "mueller_assemble_batch",
-    "mueller_precond_build_batch", "mueller_zshape_vjp", "mueller_rhs_shape_vjp",
+    "mueller_precond_build_batch", "mueller_zshape_vjp", "mueller_zshape_vjp_multi",
+    "mueller_rhs_shape_vjp",
     "mueller_cross_section_partials",
 ]
 
@@ -118,6 +119,7 @@ def load_library(build_if_missing: bool = True):
         "mueller_assemble": (C.c_int, [vp, C.POINTER(CParams), i32, vp, i64, vp, vp, dp, i32, vp]),
         "mueller_dz_matvec": (C.c_int, [vp, C.POINTER(CParams), i32, vp, vp, vp]),
         "mueller_zshape_vjp": (C.c_int, [vp, C.POINTER(CParams), vp, vp, dp, vp]),
+        "mueller_zshape_vjp_multi": (C.c_int, [vp, C.POINTER(CParams), vp, i32, vp, dp, vp]),
         "mueller_rhs_shape_vjp": (C.c_int, [vp, C.POINTER(CParams), vp, dp, dp, vp]),
         "mueller_cross_section_partials": (C.c_int, [vp, C.POINTER(CParams), vp, dp, i32, i32, vp,
                                                      dp, dp, vp]),
@@ -362,6 +364,24 @@ def zshape_vjp(mesh: Mesh, params: Params, lam, X, stream=None):
     p = params.c()
     _check(mesh._lib.mueller_zshape_vjp(mesh.h, C.byref(p), _ptr(lam), _ptr(X), _dp(g),
                                         _stream(stream)))
+    return g
+
+
+def zshape_vjp_multi(mesh: Mesh, params: Params, lam, X, stream=None):
+    """mueller_zshape_vjp_multi: the gradients of Re lam_o^H Z(X) x for the
+    rows lam_o of lam (r, N), numpy (r, n_nodes, 3) in the input node order."""
+    torch = _torch()
+    lam = _dev(lam, torch.complex128, "lam")
+    if lam.dim() == 1:
+        lam = lam.reshape(1, -1)
+    X = _dev(X, torch.complex128, "X").reshape(-1)
+    r = lam.shape[0]
+    if lam.shape[1] != mesh.N or X.numel() != mesh.N:
+        raise ValueError("lam must be (r, N) and X of length N")
+    g = np.zeros((r, mesh.nn, 3))
+    p = params.c()
+    _check(mesh._lib.mueller_zshape_vjp_multi(mesh.h, C.byref(p), _ptr(lam), int(r), _ptr(X),
+                                              _dp(g), _stream(stream)))
     return g
 
 

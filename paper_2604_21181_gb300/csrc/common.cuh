@@ -190,7 +190,7 @@ PhysConsts make_phys(const mueller_params* p);
 // shape_grad.cu: grad (host, n_nodes x 3, input node order) += the gradient
 // of Re lam^H Z(X) x with respect to the node coordinates
 mueller_status zshape_vjp(mueller_mesh* m, const PhysConsts& P, int Q, int ns, const void* lam,
-                          const void* x, double* grad, cudaStream_t s);
+                          const void* x, int r, double* grad, cudaStream_t s);
 // grad (host, n_nodes x 3) += the gradient of Re lam^H b(X)
 mueller_status rhs_shape_vjp(mueller_mesh* m, const PhysConsts& P, int Q, const void* lam,
                              const double* inc, double* grad, cudaStream_t s);

@@ -777,12 +777,12 @@ mueller_status mueller_assemble(mueller_mesh* m, const mueller_params* p, int32_
 mueller_status mueller_dz_matvec(mueller_mesh* m, const mueller_params* p, int32_t which,
                                  const void* X, void* Y, void* stream) {
   if (!m || !X || !Y) return fail(MUELLER_ERR_INVALID_ARG, "NULL argument");
-  if (mueller_status ts_ = mesh_tables(m)) return ts_;
   mueller_status st = check_params(p);
   if (st) return st;
   if (which != 1 && which != 2) return fail(MUELLER_ERR_INVALID_ARG, "which must be 1 (eps_r) or 2 (mu_r)");
   if (p->frame_rule != m->frame_rule || !m->has_frame)
     return fail(MUELLER_ERR_STATE, "call mueller_tangent_frame with params->frame_rule first");
+  if (mueller_status ts_ = mesh_tables(m)) return ts_;
   cudaStream_t s = (cudaStream_t)stream;
   st = ensure_geometry(m, p->q_regular, s);
   if (st) return st;
@@ -793,32 +793,38 @@ mueller_status mueller_dz_matvec(mueller_mesh* m, const mueller_params* p, int32
   return launch_dz_matvec(m, make_phys(p), p->q_regular, p->ssq_order, which, X, Y, s);
 }
 
-mueller_status mueller_zshape_vjp(mueller_mesh* m, const mueller_params* p, const void* lam,
-                                  const void* X, double* grad, void* stream) {
+mueller_status mueller_zshape_vjp_multi(mueller_mesh* m, const mueller_params* p, const void* lam,
+                                        int32_t r, const void* X, double* grad, void* stream) {
   if (!m || !lam || !X || !grad) return fail(MUELLER_ERR_INVALID_ARG, "NULL argument");
-  if (mueller_status ts_ = mesh_tables(m)) return ts_;
+  if (r < 1) return fail(MUELLER_ERR_INVALID_ARG, "r must be >= 1");
   mueller_status st = check_params(p);
   if (st) return st;
   if (m->host_only) return fail(MUELLER_ERR_STATE, kHostOnlyMsg);
   if (p->frame_rule != m->frame_rule || !m->has_frame)
     return fail(MUELLER_ERR_STATE, "call mueller_tangent_frame with params->frame_rule first");
+  if (mueller_status ts_ = mesh_tables(m)) return ts_;
   cudaStream_t s = (cudaStream_t)stream;
   st = ensure_geometry(m, p->q_regular, s);
   if (st) return st;
-  std::fill(grad, grad + 3 * m->nn, 0.0);
-  return zshape_vjp(m, make_phys(p), p->q_regular, p->ssq_order, lam, X, grad, s);
+  std::fill(grad, grad + (size_t)r * 3 * m->nn, 0.0);
+  return zshape_vjp(m, make_phys(p), p->q_regular, p->ssq_order, lam, X, r, grad, s);
+}
+
+mueller_status mueller_zshape_vjp(mueller_mesh* m, const mueller_params* p, const void* lam,
+                                  const void* X, double* grad, void* stream) {
+  return mueller_zshape_vjp_multi(m, p, lam, 1, X, grad, stream);
 }
 
 mueller_status mueller_rhs_shape_vjp(mueller_mesh* m, const mueller_params* p, const void* lam,
                                      const double* inc, double* grad, void* stream) {
   if (!m || !lam || !inc || !grad) return fail(MUELLER_ERR_INVALID_ARG, "NULL argument");
-  if (mueller_status ts_ = mesh_tables(m)) return ts_;
   mueller_status st = check_params(p);
   if (st) return st;
   if ((st = check_inc(inc, 1))) return st;
   if (m->host_only) return fail(MUELLER_ERR_STATE, kHostOnlyMsg);
   if (p->frame_rule != m->frame_rule || !m->has_frame)
     return fail(MUELLER_ERR_STATE, "call mueller_tangent_frame with params->frame_rule first");
+  if (mueller_status ts_ = mesh_tables(m)) return ts_;
   cudaStream_t s = (cudaStream_t)stream;
   st = ensure_geometry(m, p->q_regular, s);
   if (st) return st;
@@ -831,7 +837,6 @@ mueller_status mueller_cross_section_partials(mueller_mesh* m, const mueller_par
                                               int32_t n_phi, void* G, double* grad, double* xs,
                                               void* stream) {
   if (!m || !X || !inc || !G || !grad) return fail(MUELLER_ERR_INVALID_ARG, "NULL argument");
-  if (mueller_status ts_ = mesh_tables(m)) return ts_;
   mueller_status st = check_params(p);
   if (st) return st;
   if ((st = check_inc(inc, 1))) return st;
@@ -840,6 +845,7 @@ mueller_status mueller_cross_section_partials(mueller_mesh* m, const mueller_par
   if (m->host_only) return fail(MUELLER_ERR_STATE, kHostOnlyMsg);
   if (p->frame_rule != m->frame_rule || !m->has_frame)
     return fail(MUELLER_ERR_STATE, "call mueller_tangent_frame with params->frame_rule first");
+  if (mueller_status ts_ = mesh_tables(m)) return ts_;
   cudaStream_t s = (cudaStream_t)stream;
   st = ensure_geometry(m, p->q_regular, s);
   if (st) return st;
@@ -920,11 +926,11 @@ size_t mueller_precond_bytes(int64_t n_dof, int64_t block) {
 mueller_status mueller_precond_build(const mueller_operator* op, int64_t block, void* P,
                                      void* stream) {
   if (!op || !op->mesh || !op->Z_dev || !P) return fail(MUELLER_ERR_INVALID_ARG, "NULL argument");
-  if (mueller_status ts_ = mesh_tables(op->mesh)) return ts_;
   if (block < 1) return fail(MUELLER_ERR_INVALID_ARG, "block must be >= 1");
   if (op->dtype == MUELLER_C64_NEAR64 && !op->near_dev)
     return fail(MUELLER_ERR_INVALID_ARG, "operator lacks its near part");
   if (op->mesh->host_only) return fail(MUELLER_ERR_STATE, kHostOnlyMsg);
+  if (mueller_status ts_ = mesh_tables(op->mesh)) return ts_;
   return precond_build(op, block, P, (cudaStream_t)stream);
 }
 
@@ -958,7 +964,6 @@ mueller_status mueller_solve(const mueller_operator* op, const void* B, void* X,
                              size_t work_bytes, void* stream) {
   if (!op || !op->mesh || !op->Z_dev || !B || !X || !o || !info)
     return fail(MUELLER_ERR_INVALID_ARG, "NULL argument");
-  if (mueller_status ts_ = mesh_tables(op->mesh)) return ts_;
   if (r < 1) return fail(MUELLER_ERR_INVALID_ARG, "r must be >= 1");
   if (o->mode < 0 || o->mode > 2) return fail(MUELLER_ERR_INVALID_ARG, "unknown solve mode");
   if (o->mode != MUELLER_SOLVE_DENSE_LU && (o->restart < 1 || o->maxit < 1 || !(o->tol > 0)))
@@ -974,6 +979,7 @@ mueller_status mueller_solve(const mueller_operator* op, const void* B, void* X,
     return fail(MUELLER_ERR_INVALID_ARG,
                 "the adjoint operator needs a complex128 operator and MUELLER_SOLVE_GMRES");
   if (op->mesh->host_only) return fail(MUELLER_ERR_STATE, kHostOnlyMsg);
+  if (mueller_status ts_ = mesh_tables(op->mesh)) return ts_;
   size_t need = solve_work(op, r, o);
   if (work && work_bytes < need) return fail(MUELLER_ERR_INVALID_ARG, "workspace too small");
   auto t0 = std::chrono::steady_clock::now();
@@ -990,13 +996,13 @@ size_t mueller_matvec_workspace_bytes(const mueller_operator* op, int32_t r) {
 mueller_status mueller_matvec(const mueller_operator* op, const void* X, void* Y, int32_t r,
                               void* work, size_t work_bytes, void* stream) {
   if (!op || !op->mesh || !op->Z_dev || !X || !Y) return fail(MUELLER_ERR_INVALID_ARG, "NULL argument");
-  if (mueller_status ts_ = mesh_tables(op->mesh)) return ts_;
   if (r < 1) return fail(MUELLER_ERR_INVALID_ARG, "r must be >= 1");
   if (op->dtype == MUELLER_C64_NEAR64 && !op->near_dev)
     return fail(MUELLER_ERR_INVALID_ARG, "operator lacks its near part");
   if ((op->flags & MUELLER_OP_ADJOINT) && op->dtype != MUELLER_C128)
     return fail(MUELLER_ERR_INVALID_ARG, "the adjoint operator needs a complex128 operator");
   if (op->mesh->host_only) return fail(MUELLER_ERR_STATE, kHostOnlyMsg);
+  if (mueller_status ts_ = mesh_tables(op->mesh)) return ts_;
   if (work && work_bytes < op_matvec_work(op, r)) return fail(MUELLER_ERR_INVALID_ARG, "workspace too small");
   return op_matvec(op, X, Y, r, work, work_bytes, (cudaStream_t)stream);
 }
@@ -1009,10 +1015,10 @@ size_t mueller_matvec_mrhs_workspace_bytes(const mueller_operator* op, int32_t r
 mueller_status mueller_matvec_mrhs(const mueller_operator* op, const void* X, void* Y, int32_t r,
                                    void* work, size_t work_bytes, void* stream) {
   if (!op || !op->mesh || !op->Z_dev || !X || !Y) return fail(MUELLER_ERR_INVALID_ARG, "NULL argument");
-  if (mueller_status ts_ = mesh_tables(op->mesh)) return ts_;
   if (op->dtype != MUELLER_C64_NEAR64 || !op->near_dev)
     return fail(MUELLER_ERR_INVALID_ARG, "the tensor-core product needs a C64_NEAR64 operator");
   if (op->mesh->host_only) return fail(MUELLER_ERR_STATE, kHostOnlyMsg);
+  if (mueller_status ts_ = mesh_tables(op->mesh)) return ts_;
   const int64_t N = 4 * op->mesh->nn;
   if (r < 1 || r > 128) return fail(MUELLER_ERR_INVALID_ARG, "r must be in 1..128");
   if (!work || work_bytes < mrhs_work_bytes(N, r))
@@ -1030,13 +1036,13 @@ mueller_status mueller_far_field(mueller_mesh* m, const mueller_params* p, const
                                  void* F, double* xs, int32_t n_theta, int32_t n_phi,
                                  void* stream) {
   if (!m || !X || !inc || !xs) return fail(MUELLER_ERR_INVALID_ARG, "NULL argument");
-  if (mueller_status ts_ = mesh_tables(m)) return ts_;
   mueller_status st = check_params(p);
   if (st) return st;
   if (r < 1 || ndir < 0 || (ndir > 0 && (!dirs || !F))) return fail(MUELLER_ERR_INVALID_ARG, "bad r/n_dir");
   if (n_theta < 2 || n_phi < 3 || n_theta > 512 || n_phi > 1024)
     return fail(MUELLER_ERR_INVALID_ARG, "n_theta in 2..512, n_phi in 3..1024");
   if ((st = check_inc(inc, r)) || (st = check_dirs(dirs, ndir))) return st;
+  if (mueller_status ts_ = mesh_tables(m)) return ts_;
   cudaStream_t s = (cudaStream_t)stream;
   st = ensure_geometry(m, p->q_regular, s);
   if (st) return st;
@@ -1090,7 +1096,6 @@ mueller_status mueller_far_field_noalloc(mueller_mesh* m, const mueller_params* 
                                          const double* dirs, int64_t ndir, void* F, double* xs,
                                          int32_t n_theta, int32_t n_phi, void* stream) {
   if (!m || !X || !inc || !xs) return fail(MUELLER_ERR_INVALID_ARG, "NULL argument");
-  if (mueller_status ts_ = mesh_tables(m)) return ts_;
   mueller_status st = check_params(p);
   if (st) return st;
   if (r < 1 || ndir < 0 || (ndir > 0 && (!dirs || !F))) return fail(MUELLER_ERR_INVALID_ARG, "bad r/n_dir");
@@ -1102,6 +1107,7 @@ mueller_status mueller_far_field_noalloc(mueller_mesh* m, const mueller_params* 
   if (!m->has_frame || p->frame_rule != m->frame_rule || m->qd_q != p->q_regular)
     return fail(MUELLER_ERR_STATE, "call mueller_assemble (or mueller_far_field) with these "
                                    "params on this mesh first");
+  if (mueller_status ts_ = mesh_tables(m)) return ts_;
   return far_field_noalloc(m, make_phys(p), p->q_regular, X, r, inc, dirs, ndir, F, xs, n_theta,
                            n_phi, (cudaStream_t)stream);
 }

@@ -24,6 +24,7 @@
 // Gram-Schmidt side are piecewise constant and contribute nothing.
 #include <math.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
@@ -230,15 +231,18 @@ __device__ __forceinline__ void pair_coef(const double2* L, const double2* X, do
 }
 
 // One point pair (p of the test element, q of the trial element) of
-// Re lam^H Z x: value and gradient with respect to the test-point record
-// (SIDE 0) or the trial-point record (SIDE 1), added into g[19]
-// (x 0-2, n 3-5, t1 6-8, t2 9-11, s1 12-14, s2 15-17, W 18).
-template <int SIDE>
+// Re lam_o^H Z x for R adjoint vectors lam_o: value and gradient with respect
+// to the test-point record (SIDE 0) or the trial-point record (SIDE 1), added
+// into g[o][19] (x 0-2, n 3-5, t1 6-8, t2 9-11, s1 12-14, s2 15-17, W 18).
+// Lt[o]: the 4 fields of conj(lam_o) at the test point, Xq: those of x at
+// the trial point.  The radial functions and their derivatives, which do not
+// depend on lam, are evaluated once for the R vectors.
+template <int SIDE, int R>
 __device__ void pair_point_vjp(const KConst<double>& K, const double* px, const double* qy,
-                               bool remainder, const cx<double> A1[4], const cx<double> Ae[4],
-                               const cx<double> Am[4], double* g) {
-  const d3 R = sub(ld3(px), ld3(qy));
-  const double r2 = dot(R, R);
+                               bool remainder, const double2* const* Lt, const double2* Xq,
+                               double iw, double (*g)[19]) {
+  const d3 Rv = sub(ld3(px), ld3(qy));
+  const double r2 = dot(Rv, Rv);
   const double Wp = px[18], Wq = qy[18], W = Wp * Wq;
   PairGeo G;
   G.n = ld3(px + 3);
@@ -254,59 +258,77 @@ __device__ void pair_point_vjp(const KConst<double>& K, const double* px, const 
     const cx<double> ki3 = cmul(ki2, cmk(K.ki_re, K.ki_im));
     const double inv6pi = 1.0 / (6.0 * kPi);
     const cx<double> lim = cmk(ki3.im * inv6pi, (ka3 - ki3.re) * inv6pi);
-    double V = 0.0;
-    for (int a = 0; a < 2; ++a)
-      for (int b = 0; b < 2; ++b) {
-        const double c = cmul(A1[2 * a + b], lim).re;
-        const double st = dot(G.s[a], G.u[b]);
-        V += c * st;
-        if (SIDE == 0)
-          acc3s(g + 12 + 3 * a, c * W, G.u[b]);
-        else
-          acc3s(g + 6 + 3 * b, c * W, G.s[a]);
-      }
-    g[18] += V * (SIDE == 0 ? Wq : Wp);
+    for (int o = 0; o < R; ++o) {
+      cx<double> A1[4], Ae[4], Am[4];
+      pair_coef(Lt[o], Xq, iw, A1, Ae, Am);
+      double V = 0.0;
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+          const double c = cmul(A1[2 * a + b], lim).re;
+          const double st = dot(G.s[a], G.u[b]);
+          V += c * st;
+          if (SIDE == 0)
+            acc3s(g[o] + 12 + 3 * a, c * W, G.u[b]);
+          else
+            acc3s(g[o] + 6 + 3 * b, c * W, G.s[a]);
+        }
+      g[o][18] += V * (SIDE == 0 ? Wq : Wp);
+    }
     return;
   }
   const double r = sqrt(r2);
-  const d3 h = scl(1.0 / r, R);
+  const d3 h = scl(1.0 / r, Rv);
   cx<double> f[4], df[4];
   radial_d(K, r, remainder, f, df);
-  double c1[4], c2[4], cG[4], dc1[4], dc2[4], dcG[4];
-  for (int k = 0; k < 4; ++k) {
-    c1[k] = cmul(A1[k], f[0]).re;
-    c2[k] = cmul(A1[k], f[1]).re;
-    cG[k] = cmul(Ae[k], f[2]).re + cmul(Am[k], f[3]).re;
-    dc1[k] = cmul(A1[k], df[0]).re;
-    dc2[k] = cmul(A1[k], df[1]).re;
-    dcG[k] = cmul(Ae[k], df[2]).re + cmul(Am[k], df[3]).re;
-  }
-  d3 gR, gs[2], gtx[2], gn, gty[2];
-  const double V = kernel_vjp(G, h, r, c1, c2, cG, dc1, dc2, dcG, gR, gs, gtx, gn, gty);
-  if (SIDE == 0) {
-    acc3s(g, W, gR);
-    acc3s(g + 3, W, gn);
-    for (int a = 0; a < 2; ++a) {
-      acc3s(g + 6 + 3 * a, W, gtx[a]);
-      acc3s(g + 12 + 3 * a, W, gs[a]);
+#pragma unroll 1
+  for (int o = 0; o < R; ++o) {
+    cx<double> A1[4], Ae[4], Am[4];
+    pair_coef(Lt[o], Xq, iw, A1, Ae, Am);
+    double c1[4], c2[4], cG[4], dc1[4], dc2[4], dcG[4];
+    for (int k = 0; k < 4; ++k) {
+      c1[k] = cmul(A1[k], f[0]).re;
+      c2[k] = cmul(A1[k], f[1]).re;
+      cG[k] = cmul(Ae[k], f[2]).re + cmul(Am[k], f[3]).re;
+      dc1[k] = cmul(A1[k], df[0]).re;
+      dc2[k] = cmul(A1[k], df[1]).re;
+      dcG[k] = cmul(Ae[k], df[2]).re + cmul(Am[k], df[3]).re;
     }
-    g[18] += V * Wq;
-  } else {
-    acc3s(g, -W, gR);
-    for (int b = 0; b < 2; ++b) acc3s(g + 6 + 3 * b, W, gty[b]);
-    g[18] += V * Wp;
+    d3 gR, gs[2], gtx[2], gn, gty[2];
+    const double V = kernel_vjp(G, h, r, c1, c2, cG, dc1, dc2, dcG, gR, gs, gtx, gn, gty);
+    double* go = g[o];
+    if (SIDE == 0) {
+      acc3s(go, W, gR);
+      acc3s(go + 3, W, gn);
+      for (int a = 0; a < 2; ++a) {
+        acc3s(go + 6 + 3 * a, W, gtx[a]);
+        acc3s(go + 12 + 3 * a, W, gs[a]);
+      }
+      go[18] += V * Wq;
+    } else {
+      acc3s(go, -W, gR);
+      for (int b = 0; b < 2; ++b) acc3s(go + 6 + 3 * b, W, gty[b]);
+      go[18] += V * Wp;
+    }
   }
 }
+
+// The point-field and record-adjoint arrays of up to kVjpR adjoint vectors
+// (one pt_fields / radj set per vector; x is the same for all of them).
+constexpr int kVjpR = 3;
+struct VjpSet {
+  const double2* Lp[kVjpR];
+  double* radj[kVjpR];
+};
 
 // Regular pairs and the remainder of touching pairs, SIDE 0: CTA per test
 // element e, warp w <-> test point w, lanes over the trial elements; SIDE 1:
 // CTA per trial element, warp <-> trial point, lanes over test elements.
-// The point-record adjoints of the CTA's element are added into radj.
-template <int SIDE>
+// The point-record adjoints of the CTA's element are added into radj of
+// each of the R adjoint vectors.
+template <int SIDE, int R>
 __global__ void __launch_bounds__(32 * MAX_Q) pair_vjp_kernel(
     int64_t nt, int Q, const double* __restrict__ qd, const int32_t* __restrict__ T,
-    const double2* __restrict__ Lp, const double2* __restrict__ Xp, KConst<double> K,
-    double* __restrict__ radj) {
+    VjpSet V, const double2* __restrict__ Xp, KConst<double> K) {
   const int64_t e = blockIdx.x;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (w >= Q) return;
@@ -315,37 +337,35 @@ __global__ void __launch_bounds__(32 * MAX_Q) pair_vjp_kernel(
   for (int c = 0; c < 19; ++c) rec[c] = own[c];
   int32_t te[3];
   for (int k = 0; k < 3; ++k) te[k] = T[6 * e + k];
-  const double2* Lown = Lp + (e * Q + w) * 4;
-  const double2* Xown = Xp + (e * Q + w) * 4;
-  double2 Lo[4], Xo[4];
+  double2 Lo[R][4], Xo[4];
   for (int k = 0; k < 4; ++k) {
-    Lo[k] = Lown[k];
-    Xo[k] = Xown[k];
+    Xo[k] = Xp[(e * Q + w) * 4 + k];
+    for (int o = 0; o < R; ++o) Lo[o][k] = V.Lp[o][(e * Q + w) * 4 + k];
   }
   const double iw = 1.0 / K.ka;
-  double g[19];
-  for (int c = 0; c < 19; ++c) g[c] = 0.0;
+  double g[R][19];
+  for (int o = 0; o < R; ++o)
+    for (int c = 0; c < 19; ++c) g[o][c] = 0.0;
   for (int64_t f = lane; f < nt; f += 32) {
     int32_t tf[3];
     for (int k = 0; k < 3; ++k) tf[k] = T[6 * f + k];
     const bool touch = share_corner_d(te, tf);
     for (int q = 0; q < Q; ++q) {
       const double* other = qd + (f * Q + q) * QD_STRIDE;
-      cx<double> A1[4], Ae[4], Am[4];
-      if (SIDE == 0) {
-        pair_coef(Lo, Xp + (f * Q + q) * 4, iw, A1, Ae, Am);
-        pair_point_vjp<0>(K, rec, other, touch, A1, Ae, Am, g);
-      } else {
-        pair_coef(Lp + (f * Q + q) * 4, Xo, iw, A1, Ae, Am);
-        pair_point_vjp<1>(K, other, rec, touch, A1, Ae, Am, g);
-      }
+      const double2* Lt[R];
+      for (int o = 0; o < R; ++o) Lt[o] = SIDE == 0 ? Lo[o] : V.Lp[o] + (f * Q + q) * 4;
+      if (SIDE == 0)
+        pair_point_vjp<0, R>(K, rec, other, touch, Lt, Xp + (f * Q + q) * 4, iw, g);
+      else
+        pair_point_vjp<1, R>(K, other, rec, touch, Lt, Xo, iw, g);
     }
   }
-  for (int c = 0; c < 19; ++c) {
-    double v = g[c];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) radj[(e * Q + w) * 19 + c] += v;
-  }
+  for (int o = 0; o < R; ++o)
+    for (int c = 0; c < 19; ++c) {
+      double v = g[o][c];
+      for (int s = 16; s > 0; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
+      if (lane == 0) V.radj[o][(e * Q + w) * 19 + c] += v;
+    }
 }
 
 // Mass term (Eq. mass_matrix; coincident pairs): Z01 += a_eps M, Z10 +=
@@ -1104,8 +1124,12 @@ static mueller_status shape_finish(mueller_mesh* m, const RuleC& rc, ShapeWork& 
   return MUELLER_OK;
 }
 
+// The gradients of Re lam_o^H Z(X) x for r adjoint vectors lam_o (lam: r x N,
+// contiguous), into grad + o * nn * 3.  The regular-pair and remainder kernels
+// take up to kVjpR vectors per launch, so that each point pair's radial
+// functions serve all of them; the other passes run per vector.
 mueller_status zshape_vjp(mueller_mesh* m, const PhysConsts& P, int Q, int ns, const void* lam,
-                          const void* x, double* grad, cudaStream_t s) {
+                          const void* x, int r, double* grad, cudaStream_t s) {
   MU_CUDA(cis64_table_ready());  // the radial functions' exp(i theta) table
   TriangleRule rule;
   if (!triangle_rule(Q, rule)) {
@@ -1113,9 +1137,11 @@ mueller_status zshape_vjp(mueller_mesh* m, const PhysConsts& P, int Q, int ns, c
     return MUELLER_ERR_INVALID_ARG;
   }
   const RuleC rc = rule_c(rule);
-  ShapeWork W;
-  mueller_status st = shape_alloc(m, Q, W, s);
   const int64_t N = 4 * m->nn, H = N / 2;
+  const double2* L = (const double2*)lam;
+  std::vector<ShapeWork> W(r);
+  mueller_status st = MUELLER_OK;
+  for (int o = 0; o < r && !st; ++o) st = shape_alloc(m, Q, W[o], s);
   KConst<double> K;
   K.ka = P.ka;
   K.ki_re = P.ki_re;
@@ -1125,13 +1151,38 @@ mueller_status zshape_vjp(mueller_mesh* m, const PhysConsts& P, int Q, int ns, c
   K.mu_re = P.mu_re;
   K.mu_im = P.mu_im;
   K.sing = 0.0;
-  if (!st) {
-    { Prof prof_("pt_fields_kernel", s); pt_fields_kernel<<<nblk(m->nt * Q, 128), 128, 0, s>>>(m->nt, rc, m->T, (const double2*)lam, (const double2*)x, H, W.Lp, W.Xp); }
-    { Prof prof_("pair_vjp_kernel<0>", s); pair_vjp_kernel<0><<<(unsigned)m->nt, 32 * Q, 0, s>>>(m->nt, Q, m->qd64, m->T, W.Lp, W.Xp, K, W.radj); }
-    { Prof prof_("pair_vjp_kernel<1>", s); pair_vjp_kernel<1><<<(unsigned)m->nt, 32 * Q, 0, s>>>(m->nt, Q, m->qd64, m->T, W.Lp, W.Xp, K, W.radj); }
-    { Prof prof_("mass_vjp_kernel", s); mass_vjp_kernel<<<nblk(m->nt * Q, 128), 128, 0, s>>>(m->nt * Q, W.Lp, W.Xp, 0.5 * (1.0 + P.eps_re), 0.5 * P.eps_im, 0.5 * (1.0 + P.mu_re), 0.5 * P.mu_im, W.radj); }
+  for (int o = 0; o < r && !st; ++o) {
+    { Prof prof_("pt_fields_kernel", s); pt_fields_kernel<<<nblk(m->nt * Q, 128), 128, 0, s>>>(m->nt, rc, m->T, L + o * N, (const double2*)x, H, W[o].Lp, W[o].Xp); }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) st = cuda_fail(e, "pt_fields_kernel");
+  }
+  for (int o0 = 0; o0 < r && !st; o0 += kVjpR) {
+    const int R = std::min(kVjpR, r - o0);
+    VjpSet V = {};
+    for (int o = 0; o < R; ++o) {
+      V.Lp[o] = W[o0 + o].Lp;
+      V.radj[o] = W[o0 + o].radj;
+    }
+    const double2* Xp = W[o0].Xp;
+    {
+      Prof prof_("pair_vjp_kernel<0>", s);
+      if (R == 1) pair_vjp_kernel<0, 1><<<(unsigned)m->nt, 32 * Q, 0, s>>>(m->nt, Q, m->qd64, m->T, V, Xp, K);
+      else if (R == 2) pair_vjp_kernel<0, 2><<<(unsigned)m->nt, 32 * Q, 0, s>>>(m->nt, Q, m->qd64, m->T, V, Xp, K);
+      else pair_vjp_kernel<0, 3><<<(unsigned)m->nt, 32 * Q, 0, s>>>(m->nt, Q, m->qd64, m->T, V, Xp, K);
+    }
+    {
+      Prof prof_("pair_vjp_kernel<1>", s);
+      if (R == 1) pair_vjp_kernel<1, 1><<<(unsigned)m->nt, 32 * Q, 0, s>>>(m->nt, Q, m->qd64, m->T, V, Xp, K);
+      else if (R == 2) pair_vjp_kernel<1, 2><<<(unsigned)m->nt, 32 * Q, 0, s>>>(m->nt, Q, m->qd64, m->T, V, Xp, K);
+      else pair_vjp_kernel<1, 3><<<(unsigned)m->nt, 32 * Q, 0, s>>>(m->nt, Q, m->qd64, m->T, V, Xp, K);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) st = cuda_fail(e, "pair adjoint kernels");
+  }
+  for (int o = 0; o < r && !st; ++o) {
+    { Prof prof_("mass_vjp_kernel", s); mass_vjp_kernel<<<nblk(m->nt * Q, 128), 128, 0, s>>>(m->nt * Q, W[o].Lp, W[o].Xp, 0.5 * (1.0 + P.eps_re), 0.5 * P.eps_im, 0.5 * (1.0 + P.mu_re), 0.5 * P.mu_im, W[o].radj); }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) st = cuda_fail(e, "mass_vjp_kernel");
   }
   if (!st && m->n_touch > 0) {
     GLC gl;
@@ -1146,13 +1197,15 @@ mueller_status zshape_vjp(mueller_mesh* m, const PhysConsts& P, int Q, int ns, c
     const cx<double> c1 = crs(1.0 / (8.0 * kPi), cmk(P.ka * P.ka - ki2.re, -ki2.im));
     const cx<double> ce = crs(-kC4pi, cmk(1.0 - P.eps_re, -P.eps_im));
     const cx<double> cm = crs(-kC4pi, cmk(1.0 - P.mu_re, -P.mu_im));
-    { Prof prof_("ss_vjp_kernel<0>", s); ss_vjp_kernel<0><<<(unsigned)m->n_touch, SST, 0, s>>>(m->tp, m->X, m->T, m->frame, (const double2*)lam, (const double2*)x, H, gl, c1, ce, cm, 1.0 / P.ka, W.eadj); }
-    { Prof prof_("ss_vjp_kernel<1>", s); ss_vjp_kernel<1><<<(unsigned)m->n_touch, SST, 0, s>>>(m->tp, m->X, m->T, m->frame, (const double2*)lam, (const double2*)x, H, gl, c1, ce, cm, 1.0 / P.ka, W.eadj); }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) st = cuda_fail(e, "Sauter-Schwab adjoint kernels");
+    for (int o = 0; o < r && !st; ++o) {
+      { Prof prof_("ss_vjp_kernel<0>", s); ss_vjp_kernel<0><<<(unsigned)m->n_touch, SST, 0, s>>>(m->tp, m->X, m->T, m->frame, L + o * N, (const double2*)x, H, gl, c1, ce, cm, 1.0 / P.ka, W[o].eadj); }
+      { Prof prof_("ss_vjp_kernel<1>", s); ss_vjp_kernel<1><<<(unsigned)m->n_touch, SST, 0, s>>>(m->tp, m->X, m->T, m->frame, L + o * N, (const double2*)x, H, gl, c1, ce, cm, 1.0 / P.ka, W[o].eadj); }
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) st = cuda_fail(e, "Sauter-Schwab adjoint kernels");
+    }
   }
-  if (!st) st = shape_finish(m, rc, W, grad, s);
-  shape_free(W, s);
+  for (int o = 0; o < r && !st; ++o) st = shape_finish(m, rc, W[o], grad + (size_t)o * m->nn * 3, s);
+  for (ShapeWork& w : W) shape_free(w, s);
   return st;
 }
 

@@ -184,9 +184,9 @@ def adjoint_gradients(state, n_theta=48, n_phi=96, material=True, shape=True, ti
         lap("material_ms")
     if not shape:
         return J, None
+    gz = api.zshape_vjp_multi(mesh, params, lam, X[0])  # the three outputs in one pass
     for o in range(3):
-        grad[o] += 2.0 * (api.rhs_shape_vjp(mesh, params, lam[o], inc[0])
-                          - api.zshape_vjp(mesh, params, lam[o], X[0]))
+        grad[o] += 2.0 * (api.rhs_shape_vjp(mesh, params, lam[o], inc[0]) - gz[o])
     lap("shape_ms")
     return J, grad
 

@@ -56,6 +56,9 @@ def test_null_handles_are_rejected(lib):
     assert lib.mueller_assemble(None, C.byref(p), api.MUELLER_C128, None, 0, None, None, None,
                                 0, None) == INVALID_ARG
     assert lib.mueller_dz_matvec(None, C.byref(p), 1, None, None, None) == INVALID_ARG
+    g = np.zeros(3)
+    assert lib.mueller_zshape_vjp(None, C.byref(p), None, None, _dp(g), None) == INVALID_ARG
+    assert lib.mueller_zshape_vjp_multi(None, C.byref(p), None, 1, None, _dp(g), None) == INVALID_ARG
     inc = np.zeros((1, 6))
     xs = np.zeros((1, 3))
     assert lib.mueller_far_field(None, C.byref(p), None, 1, _dp(inc), None, 0, None, _dp(xs),
@@ -108,6 +111,13 @@ def test_far_field_sizes_are_checked(lib, fake, r, ndir, n_theta, n_phi):
     for fn in (lib.mueller_far_field, lib.mueller_far_field_noalloc):
         assert fn(h, C.byref(p), h, r, _dp(inc), None, ndir, None, _dp(xs), n_theta, n_phi,
                   None) == INVALID_ARG
+
+
+def test_zshape_vjp_multi_needs_a_vector(lib, fake):
+    _, h = fake
+    p = _params()
+    g = np.zeros(3)
+    assert lib.mueller_zshape_vjp_multi(h, C.byref(p), h, 0, h, _dp(g), None) == INVALID_ARG
 
 
 def test_dz_matvec_parameter_index_is_checked(lib, fake):

@@ -81,3 +81,25 @@ def test_zshape_vjp_matches_central_differences(name):
             fd[a, d] = (_s(xp, tri6, p, lam, x) - _s(xm, tri6, p, lam, x)) / (2 * h)
     err = np.abs(G[nodes] - fd).max() / np.abs(fd).max()
     assert err <= 1e-6, (err, G[nodes], fd)
+
+
+@pytest.mark.parametrize("r", [2, 3, 5])
+def test_zshape_vjp_multi_equals_one_vector_at_a_time(r):
+    """mueller_zshape_vjp_multi (several adjoint vectors per pass; the radial
+    functions of each point pair shared by up to three of them) gives each
+    vector's gradient as mueller_zshape_vjp alone does, to rounding."""
+    xyz, tri6 = workloads.spheroid_p2(1, 1.0, 1.5)
+    p = mu.Params(ka=2.0, eps_r=(3.0, 0.2), mu_r=(1.2, 0.05), q_regular=6, ssq_order=4,
+                  frame_rule=1)
+    m = mu.Mesh(xyz, tri6)
+    m.tangent_frame(1, out=False)
+    mu.assemble(m, p, mu.MUELLER_C128)
+    g = torch.Generator().manual_seed(5)
+    lam = torch.randn((r, m.N), dtype=torch.complex128, generator=g).cuda()
+    x = torch.randn(m.N, dtype=torch.complex128, generator=g).cuda()
+    G = mu.zshape_vjp_multi(m, p, lam, x)
+    assert G.shape == (r, len(xyz), 3)
+    for o in range(r):
+        G1 = mu.zshape_vjp(m, p, lam[o], x)
+        err = np.abs(G[o] - G1).max() / np.abs(G1).max()
+        assert err <= 1e-12, (o, err)
