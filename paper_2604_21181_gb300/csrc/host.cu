@@ -12,9 +12,12 @@
 #include <chrono>
 #include <complex>
 #include <map>
+#include <memory>
 #include <mutex>
+#include <new>
 #include <numeric>
 #include <string>
+#include <system_error>
 #include <thread>
 #include <vector>
 
@@ -533,22 +536,36 @@ mueller_status mueller_mesh_load(const double* xyz, int64_t nn, const int32_t* t
   // that the caller's frame, point-geometry and regular-pair launches need
   // not wait for them; every call that reads them joins it first
   // (mesh_tables), and its status and message surface there.
-  m->tables_thread = std::thread([m, dev, ptr = std::move(ptr), n2e = std::move(n2e)]() {
+  struct Inputs {
+    std::vector<int32_t> ptr, n2e;
+  };
+  auto in = std::make_shared<Inputs>();
+  in->ptr = std::move(ptr);
+  in->n2e = std::move(n2e);
+  auto work = [m, dev, in]() {
     std::vector<TouchPair> tp;
     std::vector<int32_t> order, slot;
-    build_tables(m, ptr, n2e, tp, order, slot);
     mueller_status st = MUELLER_OK;
+    try {
+      build_tables(m, in->ptr, in->n2e, tp, order, slot);
+    } catch (const std::bad_alloc&) {
+      st = fail(MUELLER_ERR_OOM, "host memory for the touching pairs and the near layout");
+    } catch (const std::exception& x) {  // e.g. no host thread for the table passes
+      st = fail(MUELLER_ERR_OOM, std::string("host resources for the mesh tables: ") + x.what());
+    }
     cudaStream_t ts = nullptr;
-    cudaError_t e = cudaSetDevice(dev);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking);
-    if (e != cudaSuccess) st = cuda_fail(e, "mesh table stream");
+    if (!st) {
+      cudaError_t e = cudaSetDevice(dev);
+      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking);
+      if (e != cudaSuccess) st = cuda_fail(e, "mesh table stream");
+    }
     if (!st) st = upload(&m->tp, tp.data(), tp.size(), ts);
     if (!st) st = upload(&m->near_rowptr, m->near_rowptr_h.data(), m->near_rowptr_h.size(), ts);
     if (!st) st = upload(&m->near_col, m->near_col_h.data(), m->near_col_h.size(), ts);
     if (!st) st = upload(&m->tp_slot, slot.data(), slot.size(), ts);
     if (!st) st = upload(&m->tp_order, order.data(), order.size(), ts);
     if (ts) {
-      e = cudaStreamSynchronize(ts);
+      const cudaError_t e = cudaStreamSynchronize(ts);
       if (!st && e != cudaSuccess) st = cuda_fail(e, "mesh table upload");
       cudaStreamDestroy(ts);
     }
@@ -556,7 +573,12 @@ mueller_status mueller_mesh_load(const double* xyz, int64_t nn, const int32_t* t
     m->tp_slot_h = std::move(slot);
     m->tables_st = st;
     if (st) m->tables_msg = mueller_last_error();
-  });
+  };
+  try {
+    m->tables_thread = std::thread(work);
+  } catch (const std::system_error&) {
+    work();  // no thread to be had: build the tables here
+  }
   *out = m;
   return MUELLER_OK;
 }
