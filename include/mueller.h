@@ -215,6 +215,19 @@ mueller_status mueller_mesh_load(const double* xyz, int64_t n_nodes, const int32
                                  mueller_mesh** out);
 void mueller_mesh_free(mueller_mesh* mesh);
 mueller_status mueller_mesh_get_info(const mueller_mesh* mesh, mueller_mesh_info* info);
+/*
+ * mueller_point_records -- the point geometry of the regular rule (Sec. 3.3)
+ * that the assembly and the far field use: per element (the mesh's element
+ * order) and rule point, 19 doubles: x (3), the unit normal n (3), the
+ * continuous frame t1, t2 (3 each), the co-normals s1 = t1 x n, s2 = t2 x n
+ * (3 each), and the rule weight times the surface Jacobian.  For tests and
+ * inspection.
+ *   q_regular  6 or 12: the rule of the last mueller_assemble / mueller_far_field
+ *              on this mesh (else STATE).
+ *   out        host, n_tri x q_regular x 19 doubles.  Synchronous.
+ * Errors: INVALID_ARG, STATE, CUDA.
+ */
+mueller_status mueller_point_records(const mueller_mesh* mesh, int32_t q_regular, double* out);
 /* host outputs: node_perm[n_nodes], elem_perm[n_tri] (new -> old); either may be NULL */
 mueller_status mueller_mesh_perm(const mueller_mesh* mesh, int32_t* node_perm,
                                  int32_t* elem_perm);

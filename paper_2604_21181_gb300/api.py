@@ -85,6 +85,7 @@ EXPORTS = [
     "mueller_profile_get", "mueller_profile_names", "mueller_far_field_noalloc",
     "mueller_matvec_mrhs", "mueller_matvec_mrhs_workspace_bytes", "mueller_assemble_batch",
     "mueller_precond_build_batch", "mueller_zshape_vjp", "mueller_zshape_vjp_multi",
+    "mueller_point_records",
     "mueller_rhs_shape_vjp",
     "mueller_cross_section_partials",
 ]
@@ -120,6 +121,7 @@ def load_library(build_if_missing: bool = True):
         "mueller_dz_matvec": (C.c_int, [vp, C.POINTER(CParams), i32, vp, vp, vp]),
         "mueller_zshape_vjp": (C.c_int, [vp, C.POINTER(CParams), vp, vp, dp, vp]),
         "mueller_zshape_vjp_multi": (C.c_int, [vp, C.POINTER(CParams), vp, i32, vp, dp, vp]),
+        "mueller_point_records": (C.c_int, [vp, i32, dp]),
         "mueller_rhs_shape_vjp": (C.c_int, [vp, C.POINTER(CParams), vp, dp, dp, vp]),
         "mueller_cross_section_partials": (C.c_int, [vp, C.POINTER(CParams), vp, dp, i32, i32, vp,
                                                      dp, dp, vp]),
@@ -299,6 +301,13 @@ class Mesh:
         _check(self._lib.mueller_tangent_frame(self.h, int(frame_rule), _ptr(fr), _stream(stream)))
         self.frame_rule = int(frame_rule)
         return fr
+
+    def point_records(self, q_regular: int = 6):
+        """mueller_point_records: (n_tri, q_regular, 19) records x, n, t1, t2,
+        s1, s2, weight * Jacobian of the regular rule, element order of the mesh."""
+        out = np.zeros((self.nt, int(q_regular), 19))
+        _check(self._lib.mueller_point_records(self.h, int(q_regular), _dp(out)))
+        return out
 
     def near_bytes(self) -> int:
         return int(self._lib.mueller_near_bytes(self.h))

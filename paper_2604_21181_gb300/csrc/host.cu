@@ -648,6 +648,20 @@ mueller_status mueller_mesh_near_layout(const mueller_mesh* m, int32_t* rowptr, 
   return MUELLER_OK;
 }
 
+mueller_status mueller_point_records(const mueller_mesh* m, int32_t q_regular, double* out) {
+  if (!m || !out) return fail(MUELLER_ERR_INVALID_ARG, "NULL argument");
+  if (m->host_only) return fail(MUELLER_ERR_STATE, kHostOnlyMsg);
+  if (!m->has_frame || m->qd_q != q_regular || !m->qd64)
+    return fail(MUELLER_ERR_STATE, "no point geometry for this rule: call mueller_assemble or "
+                                   "mueller_far_field with it first");
+  const int64_t n = m->nt * q_regular;
+  std::vector<double> rec((size_t)n * QD_STRIDE);
+  MU_CUDA(cudaMemcpy(rec.data(), m->qd64, rec.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  for (int64_t t = 0; t < n; ++t)
+    std::copy(rec.begin() + t * QD_STRIDE, rec.begin() + t * QD_STRIDE + 19, out + t * 19);
+  return MUELLER_OK;
+}
+
 mueller_status mueller_tangent_frame(mueller_mesh* m, int32_t frame_rule, double* frame_dev,
                                      void* stream) {
   if (!m) return fail(MUELLER_ERR_INVALID_ARG, "mesh is NULL");

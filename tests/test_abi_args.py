@@ -59,6 +59,7 @@ def test_null_handles_are_rejected(lib):
     g = np.zeros(3)
     assert lib.mueller_zshape_vjp(None, C.byref(p), None, None, _dp(g), None) == INVALID_ARG
     assert lib.mueller_zshape_vjp_multi(None, C.byref(p), None, 1, None, _dp(g), None) == INVALID_ARG
+    assert lib.mueller_point_records(None, 6, _dp(g)) == INVALID_ARG
     inc = np.zeros((1, 6))
     xs = np.zeros((1, 3))
     assert lib.mueller_far_field(None, C.byref(p), None, 1, _dp(inc), None, 0, None, _dp(xs),
