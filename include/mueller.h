@@ -367,8 +367,8 @@ mueller_status mueller_zshape_vjp(mueller_mesh* mesh, const mueller_params* para
 /*
  * mueller_zshape_vjp_multi -- mueller_zshape_vjp for r adjoint vectors at
  * once (the gradients of several outputs at one solution x): the regular-pair
- * and remainder passes evaluate each point pair's radial functions once for
- * up to three of them.
+ * and remainder passes evaluate each point pair's radial functions, and the
+ * Sauter-Schwab passes each point's geometry, once for up to three of them.
  *   lam_dev  complex128, r x N (vector o at lam_dev + o N); read only.
  *   r        >= 1.
  *   grad     host, r x n_nodes x 3 (vector o's gradient at grad + 3 o n_nodes),

@@ -511,14 +511,20 @@ __device__ __forceinline__ void ss_point_geo(const d3* CX, const d3* CU1, const 
   g.t2 = scl(g.sig, m);
 }
 
-template <int SIDE>
+// R adjoint vectors per CTA (lam[o], eadj[o]): the two points' geometry and
+// the trial-side field of x are evaluated once per point for all of them.
+struct SsVjpSet {
+  const double2* lam[kVjpR];
+  double* eadj[kVjpR];
+};
+
+template <int SIDE, int R>
 __global__ void __launch_bounds__(SST) ss_vjp_kernel(
     const TouchPair* __restrict__ tp, const double* __restrict__ X, const int32_t* __restrict__ T,
-    const double* __restrict__ frame, const double2* __restrict__ lam,
-    const double2* __restrict__ xv, int64_t H, GLC gl, cx<double> c1, cx<double> ce,
-    cx<double> cm, double iw, double* __restrict__ eadj) {
+    const double* __restrict__ frame, SsVjpSet V, const double2* __restrict__ xv, int64_t H,
+    GLC gl, cx<double> c1, cx<double> ce, cx<double> cm, double iw) {
   __shared__ d3 sC[2][3][6];  // [side][X, T1, T2][monomial]
-  __shared__ double2 sL[6][4], sXv[6][4];  // conj lam at the test nodes, x at the trial nodes
+  __shared__ double2 sL[R][6][4], sXv[6][4];  // conj lam at the test nodes, x at the trial nodes
   const TouchPair P = tp[blockIdx.x];
   const int tid = threadIdx.x;
   if (tid < 18) {
@@ -533,8 +539,10 @@ __global__ void __launch_bounds__(SST) ss_vjp_kernel(
   if (tid >= 32 && tid < 32 + 24) {
     const int i = (tid - 32) / 4, k = (tid - 32) % 4;  // k = 2h + a
     const int h = k >> 1, a = k & 1;
-    const double2 l = lam[h * H + 2 * (int64_t)T[6 * P.ex + i] + a];
-    sL[i][k] = make_double2(l.x, -l.y);
+    for (int o = 0; o < R; ++o) {
+      const double2 l = V.lam[o][h * H + 2 * (int64_t)T[6 * P.ex + i] + a];
+      sL[o][i][k] = make_double2(l.x, -l.y);
+    }
     sXv[i][k] = xv[h * H + 2 * (int64_t)T[6 * P.ey + i] + a];
   }
   __syncthreads();
@@ -550,8 +558,9 @@ __global__ void __launch_bounds__(SST) ss_vjp_kernel(
   const int nreg = P.cls == 3 ? 6 : (P.cls == 2 ? 5 : 2);
   const int ns = gl.ns;
   const int64_t npts = (int64_t)nreg * ns * ns * ns * ns;
-  double acc[36];
-  for (int k = 0; k < 36; ++k) acc[k] = 0.0;
+  double acc[R][36];
+  for (int o = 0; o < R; ++o)
+    for (int k = 0; k < 36; ++k) acc[o][k] = 0.0;
   for (int64_t pt = tid; pt < npts; pt += SST) {
     double xu, xvv, yu, yv, w;
     ss_point(P.cls, ns, pt, gl.x, gl.w, xu, xvv, yu, yv, w);
@@ -561,36 +570,19 @@ __global__ void __launch_bounds__(SST) ss_vjp_kernel(
     SSPoint gx, gy;
     ss_point_geo(sC[0][0], sC[0][1], sC[0][2], xi, eta, gx);
     ss_point_geo(sC[1][0], sC[1][1], sC[1][2], yxi, yeta, gy);
-    // gamma_c from lam (test side) and x (trial side) at the points
-    cx<double> Lx[4], Xy[4];
+    // x (trial side) at the point; lam (test side) per vector below
+    cx<double> Xy[4];
     for (int k = 0; k < 4; ++k) {
-      Lx[k] = cmk(0.0, 0.0);
       Xy[k] = cmk(0.0, 0.0);
       for (int i = 0; i < 6; ++i) {
-        Lx[k].re += gx.N[i] * sL[i][k].x;
-        Lx[k].im += gx.N[i] * sL[i][k].y;
         Xy[k].re += gy.N[i] * sXv[i][k].x;
         Xy[k].im += gy.N[i] * sXv[i][k].y;
       }
     }
-    double c1v[4], c2v[4], cGv[4], d1v[4], d2v[4], dGv[4];
-    const d3 R = sub(gx.x, gy.x);
-    const double r = sqrt(dot(R, R));
-    const d3 h = scl(1.0 / r, R);
+    const d3 Rv = sub(gx.x, gy.x);
+    const double r = sqrt(dot(Rv, Rv));
+    const d3 h = scl(1.0 / r, Rv);
     const double ir = 1.0 / r, ir2 = ir * ir;
-    for (int a = 0; a < 2; ++a)
-      for (int b = 0; b < 2; ++b) {
-        const int ab = 2 * a + b;
-        const cx<double> d = csub(cmul(Lx[a], Xy[b]), cmul(Lx[2 + a], Xy[2 + b]));
-        const cx<double> g1 = cmul(c1, cmk(-iw * d.im, iw * d.re));
-        const double G2 = cmul(ce, cmul(Lx[a], Xy[2 + b])).re + cmul(cm, cmul(Lx[2 + a], Xy[b])).re;
-        c1v[ab] = g1.re * ir;
-        c2v[ab] = g1.re * ir;
-        cGv[ab] = G2 * ir2;
-        d1v[ab] = -g1.re * ir2;
-        d2v[ab] = -g1.re * ir2;
-        dGv[ab] = -2.0 * G2 * ir2 * ir;
-      }
     PairGeo G;
     G.n = gx.n;
     G.t[0] = gx.t1;
@@ -599,71 +591,103 @@ __global__ void __launch_bounds__(SST) ss_vjp_kernel(
     G.s[1] = scl(gx.sig, gx.t1);   // s2 = t2 x n = sig t1
     G.u[0] = gy.t1;
     G.u[1] = gy.t2;
-    d3 gR, gs[2], gtx[2], gn, gty[2];
-    const double V = kernel_vjp(G, h, r, c1v, c2v, cGv, d1v, d2v, dGv, gR, gs, gtx, gn, gty);
     const double Wt = w * gx.J * gy.J;
-    GeoRev o;
     double m[6];
-    if (SIDE == 0) {
-      // s1 = -sig t2, s2 = sig t1
-      d3 gt1 = add(scl(Wt, gtx[0]), scl(Wt * gx.sig, gs[1]));
-      d3 gt2 = add(scl(Wt, gtx[1]), scl(-Wt * gx.sig, gs[0]));
-      o = geo_reverse(gx.a1, gx.a2, gx.u1, gx.n, gx.t1, gx.J, gx.sig, scl(Wt, gR), scl(Wt, gn),
-                      gt1, gt2, V * w * gy.J);
+    if (SIDE == 0)
       mono6(xi, eta, m);
-    } else {
-      o = geo_reverse(gy.a1, gy.a2, gy.u1, gy.n, gy.t1, gy.J, gy.sig, scl(-Wt, gR), mk(0, 0, 0),
-                      scl(Wt, gty[0]), scl(Wt, gty[1]), V * w * gx.J);
+    else
       mono6(yxi, yeta, m);
-    }
-    // x = sum m_k CX_k, a1 = CX1 + 2 xi CX3 + eta CX4, a2 = CX2 + xi CX4 + 2 eta CX5
-    const double s = SIDE == 0 ? xi : yxi, t = SIDE == 0 ? eta : yeta;
-    d3 gC[6];
-    for (int k = 0; k < 6; ++k) gC[k] = scl(m[k], o.gx);
-    gC[1] = add(gC[1], o.ga1);
-    gC[3] = add(gC[3], scl(2.0 * s, o.ga1));
-    gC[4] = add(gC[4], add(scl(t, o.ga1), scl(s, o.ga2)));
-    gC[2] = add(gC[2], o.ga2);
-    gC[5] = add(gC[5], scl(2.0 * t, o.ga2));
-    for (int k = 0; k < 6; ++k) {
-      acc[3 * k] += gC[k].x;
-      acc[3 * k + 1] += gC[k].y;
-      acc[3 * k + 2] += gC[k].z;
-      acc[18 + 3 * k] += m[k] * o.gu1.x;
-      acc[18 + 3 * k + 1] += m[k] * o.gu1.y;
-      acc[18 + 3 * k + 2] += m[k] * o.gu1.z;
+    const double sa = SIDE == 0 ? xi : yxi, ta = SIDE == 0 ? eta : yeta;
+#pragma unroll 1
+    for (int o = 0; o < R; ++o) {
+      cx<double> Lx[4];
+      for (int k = 0; k < 4; ++k) {
+        Lx[k] = cmk(0.0, 0.0);
+        for (int i = 0; i < 6; ++i) {
+          Lx[k].re += gx.N[i] * sL[o][i][k].x;
+          Lx[k].im += gx.N[i] * sL[o][i][k].y;
+        }
+      }
+      // gamma_c from lam (test side) and x (trial side) at the points
+      double c1v[4], c2v[4], cGv[4], d1v[4], d2v[4], dGv[4];
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+          const int ab = 2 * a + b;
+          const cx<double> d = csub(cmul(Lx[a], Xy[b]), cmul(Lx[2 + a], Xy[2 + b]));
+          const cx<double> g1 = cmul(c1, cmk(-iw * d.im, iw * d.re));
+          const double G2 = cmul(ce, cmul(Lx[a], Xy[2 + b])).re + cmul(cm, cmul(Lx[2 + a], Xy[b])).re;
+          c1v[ab] = g1.re * ir;
+          c2v[ab] = g1.re * ir;
+          cGv[ab] = G2 * ir2;
+          d1v[ab] = -g1.re * ir2;
+          d2v[ab] = -g1.re * ir2;
+          dGv[ab] = -2.0 * G2 * ir2 * ir;
+        }
+      d3 gR, gs[2], gtx[2], gn, gty[2];
+      const double Vv = kernel_vjp(G, h, r, c1v, c2v, cGv, d1v, d2v, dGv, gR, gs, gtx, gn, gty);
+      GeoRev rv;
+      if (SIDE == 0) {
+        // s1 = -sig t2, s2 = sig t1
+        d3 gt1 = add(scl(Wt, gtx[0]), scl(Wt * gx.sig, gs[1]));
+        d3 gt2 = add(scl(Wt, gtx[1]), scl(-Wt * gx.sig, gs[0]));
+        rv = geo_reverse(gx.a1, gx.a2, gx.u1, gx.n, gx.t1, gx.J, gx.sig, scl(Wt, gR), scl(Wt, gn),
+                         gt1, gt2, Vv * w * gy.J);
+      } else {
+        rv = geo_reverse(gy.a1, gy.a2, gy.u1, gy.n, gy.t1, gy.J, gy.sig, scl(-Wt, gR), mk(0, 0, 0),
+                         scl(Wt, gty[0]), scl(Wt, gty[1]), Vv * w * gx.J);
+      }
+      // x = sum m_k CX_k, a1 = CX1 + 2 xi CX3 + eta CX4, a2 = CX2 + xi CX4 + 2 eta CX5
+      d3 gC[6];
+      for (int k = 0; k < 6; ++k) gC[k] = scl(m[k], rv.gx);
+      gC[1] = add(gC[1], rv.ga1);
+      gC[3] = add(gC[3], scl(2.0 * sa, rv.ga1));
+      gC[4] = add(gC[4], add(scl(ta, rv.ga1), scl(sa, rv.ga2)));
+      gC[2] = add(gC[2], rv.ga2);
+      gC[5] = add(gC[5], scl(2.0 * ta, rv.ga2));
+      double* ac = acc[o];
+      for (int k = 0; k < 6; ++k) {
+        ac[3 * k] += gC[k].x;
+        ac[3 * k + 1] += gC[k].y;
+        ac[3 * k + 2] += gC[k].z;
+        ac[18 + 3 * k] += m[k] * rv.gu1.x;
+        ac[18 + 3 * k + 1] += m[k] * rv.gu1.y;
+        ac[18 + 3 * k + 2] += m[k] * rv.gu1.z;
+      }
     }
   }
-  // CTA sums of the 36 monomial-coefficient adjoints: warp sums, then the
-  // SST / 32 warps' partials
+  // CTA sums of the 36 monomial-coefficient adjoints per vector: warp sums,
+  // then the SST / 32 warps' partials
   __shared__ double wsum[SST / 32][36];
   __shared__ double sum[36];
   const int lane = tid & 31, warp = tid >> 5;
-  for (int k = 0; k < 36; ++k) {
-    double v = acc[k];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) wsum[warp][k] = v;
-  }
-  __syncthreads();
-  if (tid < 36) {
-    double v = 0.0;
-    for (int q = 0; q < SST / 32; ++q) v += wsum[q][tid];
-    sum[tid] = v;
-  }
-  __syncthreads();
-  // monomial coefficients c = P v (p2_coef) -> nodal values: adj v = P^T adj c
-  if (tid < 6) {
-    const int fld = tid / 3, d = tid % 3;  // fld 0: positions, 1: nodal t1
-    double gc[6], gv[6];
-    for (int k = 0; k < 6; ++k) gc[k] = sum[18 * fld + 3 * k + d];
-    gv[0] = gc[0] - 3.0 * gc[1] - 3.0 * gc[2] + 2.0 * gc[3] + 4.0 * gc[4] + 2.0 * gc[5];
-    gv[1] = -gc[1] + 2.0 * gc[3];
-    gv[2] = -gc[2] + 2.0 * gc[5];
-    gv[3] = 4.0 * gc[1] - 4.0 * gc[3] - 4.0 * gc[4];
-    gv[4] = 4.0 * gc[4];
-    gv[5] = 4.0 * gc[2] - 4.0 * gc[4] - 4.0 * gc[5];
-    const int64_t e = SIDE == 0 ? P.ex : P.ey;
-    for (int k = 0; k < 6; ++k) atomicAdd(eadj + e * 54 + 18 * fld + 3 * k + d, gv[k]);
+  for (int o = 0; o < R; ++o) {
+    for (int k = 0; k < 36; ++k) {
+      double v = acc[o][k];
+      for (int q = 16; q > 0; q >>= 1) v += __shfl_xor_sync(0xffffffffu, v, q);
+      if (lane == 0) wsum[warp][k] = v;
+    }
+    __syncthreads();
+    if (tid < 36) {
+      double v = 0.0;
+      for (int q = 0; q < SST / 32; ++q) v += wsum[q][tid];
+      sum[tid] = v;
+    }
+    __syncthreads();
+    // monomial coefficients c = P v (p2_coef) -> nodal values: adj v = P^T adj c
+    if (tid < 6) {
+      const int fld = tid / 3, d = tid % 3;  // fld 0: positions, 1: nodal t1
+      double gc[6], gv[6];
+      for (int k = 0; k < 6; ++k) gc[k] = sum[18 * fld + 3 * k + d];
+      gv[0] = gc[0] - 3.0 * gc[1] - 3.0 * gc[2] + 2.0 * gc[3] + 4.0 * gc[4] + 2.0 * gc[5];
+      gv[1] = -gc[1] + 2.0 * gc[3];
+      gv[2] = -gc[2] + 2.0 * gc[5];
+      gv[3] = 4.0 * gc[1] - 4.0 * gc[3] - 4.0 * gc[4];
+      gv[4] = 4.0 * gc[4];
+      gv[5] = 4.0 * gc[2] - 4.0 * gc[4] - 4.0 * gc[5];
+      const int64_t e = SIDE == 0 ? P.ex : P.ey;
+      for (int k = 0; k < 6; ++k) atomicAdd(V.eadj[o] + e * 54 + 18 * fld + 3 * k + d, gv[k]);
+    }
+    __syncthreads();  // before the next vector's partials overwrite wsum and sum
   }
 }
 
@@ -1197,9 +1221,27 @@ mueller_status zshape_vjp(mueller_mesh* m, const PhysConsts& P, int Q, int ns, c
     const cx<double> c1 = crs(1.0 / (8.0 * kPi), cmk(P.ka * P.ka - ki2.re, -ki2.im));
     const cx<double> ce = crs(-kC4pi, cmk(1.0 - P.eps_re, -P.eps_im));
     const cx<double> cm = crs(-kC4pi, cmk(1.0 - P.mu_re, -P.mu_im));
-    for (int o = 0; o < r && !st; ++o) {
-      { Prof prof_("ss_vjp_kernel<0>", s); ss_vjp_kernel<0><<<(unsigned)m->n_touch, SST, 0, s>>>(m->tp, m->X, m->T, m->frame, L + o * N, (const double2*)x, H, gl, c1, ce, cm, 1.0 / P.ka, W[o].eadj); }
-      { Prof prof_("ss_vjp_kernel<1>", s); ss_vjp_kernel<1><<<(unsigned)m->n_touch, SST, 0, s>>>(m->tp, m->X, m->T, m->frame, L + o * N, (const double2*)x, H, gl, c1, ce, cm, 1.0 / P.ka, W[o].eadj); }
+    for (int o0 = 0; o0 < r && !st; o0 += kVjpR) {
+      const int R = std::min(kVjpR, r - o0);
+      SsVjpSet V = {};
+      for (int o = 0; o < R; ++o) {
+        V.lam[o] = L + (o0 + o) * N;
+        V.eadj[o] = W[o0 + o].eadj;
+      }
+      const unsigned g = (unsigned)m->n_touch;
+      const double2* xv = (const double2*)x;
+      {
+        Prof prof_("ss_vjp_kernel<0>", s);
+        if (R == 1) ss_vjp_kernel<0, 1><<<g, SST, 0, s>>>(m->tp, m->X, m->T, m->frame, V, xv, H, gl, c1, ce, cm, 1.0 / P.ka);
+        else if (R == 2) ss_vjp_kernel<0, 2><<<g, SST, 0, s>>>(m->tp, m->X, m->T, m->frame, V, xv, H, gl, c1, ce, cm, 1.0 / P.ka);
+        else ss_vjp_kernel<0, 3><<<g, SST, 0, s>>>(m->tp, m->X, m->T, m->frame, V, xv, H, gl, c1, ce, cm, 1.0 / P.ka);
+      }
+      {
+        Prof prof_("ss_vjp_kernel<1>", s);
+        if (R == 1) ss_vjp_kernel<1, 1><<<g, SST, 0, s>>>(m->tp, m->X, m->T, m->frame, V, xv, H, gl, c1, ce, cm, 1.0 / P.ka);
+        else if (R == 2) ss_vjp_kernel<1, 2><<<g, SST, 0, s>>>(m->tp, m->X, m->T, m->frame, V, xv, H, gl, c1, ce, cm, 1.0 / P.ka);
+        else ss_vjp_kernel<1, 3><<<g, SST, 0, s>>>(m->tp, m->X, m->T, m->frame, V, xv, H, gl, c1, ce, cm, 1.0 / P.ka);
+      }
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) st = cuda_fail(e, "Sauter-Schwab adjoint kernels");
     }
