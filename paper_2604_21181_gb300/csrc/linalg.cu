@@ -2440,8 +2440,10 @@ static mueller_status lu_update(double2* A, int64_t d, int nb, const int32_t* sz
 // sizes sz_dev), right-looking in panels of LUW columns with a look-ahead of
 // one panel.  Per panel k0: its row swaps reach the other columns and the
 // row panel of U is solved (one kernel); the columns of panel k0+LUW are
-// updated; then the side stream factors that panel (its swaps held back)
-// while the caller's stream updates the remaining columns.
+// updated; then that panel is factored (its swaps held back) while the
+// remaining columns take the trailing update: in one lu_step_kernel launch
+// on separate SMs when the panel's rows fit one CTA (d - k1 <= 512), else on
+// the side stream next to the caller's stream.
 // Then, if inv, the inverses in 'inv' (d x d per block).
 template <class CT>
 static mueller_status batched_lu_inverse(CT* A, int64_t d, int nb, const int32_t* sz_dev,
